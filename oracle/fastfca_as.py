@@ -1,0 +1,191 @@
+"""FP64 CPU oracle of FastFCA-AS (Ito & Nakatani, arXiv 1805.09498, Sec. 4).
+
+TEST INFRASTRUCTURE ONLY. Only tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this module; the library never does.
+It shares no code with the CUDA path.
+
+Plain NumPy, float64 / complex128, vectorised over (n, f) with no blocking,
+fusion or reordering beyond what each equation states. Every function names
+the equation it follows.
+
+Layouts (mic-planar, as in the synthetic generator):
+    y   [I, F, N] complex   mixture y(n,f)                 (Sec. 2)
+    v   [J, F, N] real      source power spectra v_j(n,f)  (Eq. fullrank)
+    lam [F, J, I] real      lam[f, j, i] = [Lambda_j(f)]_ii (Eq. diagconst)
+    P   [F, I, I] complex   P[f, a, i] = [P(f)]_{a i}; column i is p_i
+
+Readings taken where the paper is silent (listed with reasons in the design
+notes): the M-step updates v first (with the current Lambda) and then
+Lambda (with the new v); the K fixed-point sweeps update all columns of P
+simultaneously from P^{-H} of the previous sweep; the log-likelihood keeps
+the -I ln(pi) constant of the circular complex Gaussian density.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+LN_PI = np.log(np.pi)
+
+
+@dataclass
+class OpCounter:
+    """Counts the matrix inversions / multiplications performed (Sec. 3.4, 4.5)."""
+    inversions: int = 0
+    multiplications: int = 0
+
+    def reset(self):
+        self.inversions = 0
+        self.multiplications = 0
+
+
+COUNTER = OpCounter()
+
+
+# ---------------------------------------------------------------- E-step ----
+def basis_transform(y, P):
+    """y~(n,f) = P(f)^H y(n,f): the transformed observation in Eq. mutilde0."""
+    return np.einsum("fai,afn->ifn", P.conj(), y)
+
+
+def model_variances(v, lam):
+    """sigma_i(n,f) = sum_j v_j(n,f) [Lambda_j(f)]_ii: the diagonal matrix
+    sum_k v_k Lambda_k inverted in Eqs. mutilde0 / Phitilde0 and in Eq. FPI."""
+    return np.einsum("jfn,fji->ifn", v, lam)
+
+
+def e_step(y, v, lam, P):
+    """Posterior mean and covariance in the transformed basis.
+
+    Eq. mutilde0: mu~_j = v_j Lambda_j (sum_k v_k Lambda_k)^{-1} y~
+    Eq. Phitilde0: Phi~_j = v_j Lambda_j - v_j Lambda_j (sum_k v_k Lambda_k)^{-1} v_j Lambda_j
+    All matrices are diagonal, so both are entrywise.  Returns
+    mu [J, I, F, N] complex and phi [J, I, F, N] real (the diagonal of Phi~_j).
+    """
+    yt = basis_transform(y, P)
+    sigma = model_variances(v, lam)
+    vl = v[:, None, :, :] * lam.transpose(1, 2, 0)[:, :, :, None]   # v_j [Lambda_j]_ii
+    mu = vl / sigma[None] * yt[None]
+    phi = vl - vl * vl / sigma[None]
+    return mu, phi
+
+
+# ---------------------------------------------------------------- M-step ----
+def m_step_v(mu, phi, lam):
+    """Eq. updatev: v_j <- (1/I) tr(Lambda_j^{-1} (diag(|mu~_j|^2) + Phi~_j))."""
+    I = mu.shape[1]
+    q = np.abs(mu) ** 2 + phi
+    return np.einsum("jifn,fji->jfn", q, 1.0 / lam) / I
+
+
+def m_step_lambda(mu, phi, v):
+    """Eq. Lambdaupdate: Lambda_j <- (1/N) sum_n (diag(|mu~_j|^2) + Phi~_j) / v_j."""
+    N = mu.shape[3]
+    q = np.abs(mu) ** 2 + phi
+    return np.einsum("jifn->fji", q / v[:, None, :, :]) / N
+
+
+# ------------------------------------------------------ fixed point for P ----
+def weighted_covariances(y, v, lam):
+    """V_i(f) = (1/N) sum_n y(n,f) y(n,f)^H / sigma_i(n,f), the matrix inverted
+    in Eq. FPI.  Returns V [F, I(i), I, I]."""
+    N = y.shape[2]
+    sigma = model_variances(v, lam)
+    return np.einsum("afn,bfn,ifn->fiab", y, y.conj(), 1.0 / sigma) / N
+
+
+def fixed_point_P(P, V, K=1, counter=COUNTER):
+    """Eq. FPI, iterated K times: p_i <- V_i^{-1} [P^{-H}]_i for every column i.
+
+    Each sweep computes P^{-H} once from the previous sweep's P and updates
+    all columns from it (one fixed-point map, Eq. vecP), which is I+1 matrix
+    inversions per frequency per sweep (Sec. 4.5).
+    """
+    F, I, _ = P.shape
+    P = P.copy()
+    for _ in range(K):
+        PinvH = np.linalg.inv(P).conj().transpose(0, 2, 1)
+        counter.inversions += F
+        Pn = np.empty_like(P)
+        for i in range(I):
+            Pn[:, :, i] = np.linalg.solve(V[:, i], PinvH[:, :, i][..., None])[..., 0]
+            counter.inversions += F
+        P = Pn
+    return P
+
+
+def grad_P_conj(y, v, lam, P):
+    """Eq. partialP: dL2/dP(f)^* = N P^{-H} - sum_n y y^H P D^{-1},
+    D = sum_j v_j Lambda_j.  Column i of the sum is N V_i p_i."""
+    N = y.shape[2]
+    V = weighted_covariances(y, v, lam)
+    PinvH = np.linalg.inv(P).conj().transpose(0, 2, 1)
+    VP = np.einsum("fiab,fbi->fai", V, P)
+    return N * (PinvH - VP)
+
+
+# --------------------------------------------------------- log-likelihood ----
+def loglik_terms(y, v, lam, P):
+    """Per-(n,f) value of ln N(y; 0, P^{-H} D P^{-1}) in Eq. L2, D = sum_j v_j Lambda_j.
+
+    For R = P^{-H} D P^{-1}: ln det R = sum_i ln sigma_i - ln |det P|^2 and
+    y^H R^{-1} y = y^H P D^{-1} P^H y = sum_i |y~_i|^2 / sigma_i, so
+    ln N = -I ln(pi) + ln|det P|^2 - sum_i (ln sigma_i + |y~_i|^2 / sigma_i).
+    Returns [F, N].
+    """
+    I = y.shape[0]
+    yt = basis_transform(y, P)
+    sigma = model_variances(v, lam)
+    _, logabsdet = np.linalg.slogdet(P)
+    return (-I * LN_PI + 2.0 * logabsdet[:, None]
+            - np.sum(np.log(sigma) + np.abs(yt) ** 2 / sigma, axis=0))
+
+
+def loglik(y, v, lam, P):
+    """Eq. L2: L2(Psi) = sum_{n,f} ln N(y(n,f); 0, sum_j v_j P^{-H} Lambda_j P^{-1})."""
+    return float(np.sum(loglik_terms(y, v, lam, P)))
+
+
+# ----------------------------------------------------------- the hybrid ----
+def em_half(y, v, lam, P):
+    """Step 1 of the hybrid algorithm (Sec. 4.4): one EM iteration for
+    (v, Lambda): E-step (Eqs. mutilde0, Phitilde0), then Eq. updatev with the
+    current Lambda, then Eq. Lambdaupdate with the new v."""
+    mu, phi = e_step(y, v, lam, P)
+    v_new = m_step_v(mu, phi, lam)
+    lam_new = m_step_lambda(mu, phi, v_new)
+    return v_new, lam_new
+
+
+def hybrid_iteration(y, v, lam, P, K=1, counter=COUNTER):
+    """One iteration of the hybrid algorithm (Sec. 4.4): the EM half, then the
+    fixed-point update of P (Eq. FPI, K sweeps) with the new v and Lambda."""
+    v, lam = em_half(y, v, lam, P)
+    V = weighted_covariances(y, v, lam)
+    P = fixed_point_P(P, V, K, counter)
+    return v, lam, P
+
+
+def iterate(y, v, lam, P, iters, K=1, counter=COUNTER):
+    """Run `iters` hybrid iterations.  Returns (v, lam, P, trace) where
+    trace[t] is L2 of the state entering iteration t and trace[iters] is L2
+    of the final state (length iters + 1)."""
+    trace = []
+    for _ in range(iters):
+        trace.append(loglik(y, v, lam, P))
+        v, lam, P = hybrid_iteration(y, v, lam, P, K, counter)
+    trace.append(loglik(y, v, lam, P))
+    return v, lam, P, np.array(trace)
+
+
+# ----------------------------------------------------------------- Wiener ----
+def wiener(y, v, lam, P):
+    """Multichannel Wiener filter, Eq. MMSE0, with R_j of Eq. covmodelprop.
+
+    x^_j = R_j (sum_k R_k)^{-1} y = P^{-H} mu~_j with mu~_j from Eq. mutilde0
+    (mu~_j = P^H mu_j).  Returns [J, I, F, N] complex.
+    """
+    mu, _ = e_step(y, v, lam, P)
+    PinvH = np.linalg.inv(P).conj().transpose(0, 2, 1)
+    return np.einsum("fab,jbfn->jafn", PinvH, mu)
