@@ -1,0 +1,153 @@
+/*
+ * ffca.h - C ABI of the GB300 FastFCA-AS library (libffca.so).
+ *
+ * FastFCA-AS (Ito & Nakatani, "FastFCA-AS: joint diagonalization based
+ * acceleration of full-rank spatial covariance analysis for separating any
+ * number of sources", arXiv 1805.09498) estimates, for an STFT mixture
+ * y(n,f) in C^I of J sources, the parameters of the jointly diagonalised
+ * full-rank spatial covariance model (Sec. 4.1, Eq. diagconst)
+ *     R_j(n,f) = v_j(n,f) P(f)^{-H} Lambda_j(f) P(f)^{-1}
+ * by maximising the log-likelihood L2 (Eq. L2) with the hybrid algorithm of
+ * Sec. 4.4: one EM iteration for (v, Lambda) (Eqs. mutilde0, Phitilde0,
+ * updatev, Lambdaupdate), then K fixed-point sweeps for P (Eq. FPI).  It
+ * also exposes the conventional FCA EM (Sec. 3.3) as a baseline.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers in the descriptors are DEVICE pointers owned by the
+ *    caller.  The library never allocates or frees device memory; it borrows
+ *    the pointers for the lifetime of the context and updates parameters in
+ *    place.  The only host allocation is the small context object.
+ *  - Work is enqueued on the caller's CUDA stream (desc.stream, a
+ *    cudaStream_t; NULL = legacy default stream).  Calls that return host
+ *    values (a trace, a log-likelihood, a status) synchronise that stream.
+ *  - Errors are returned as ffca_status codes; nothing is thrown across the
+ *    ABI and no device code traps.  Device-side failures (non-finite values,
+ *    singular per-frequency systems) are latched in a status word inside the
+ *    workspace and reported by the next synchronising call.
+ *
+ * Layouts ("mic-planar"; ld = frame stride, ld >= N and ld % 4 == 0):
+ *  - y      [I][F][ld] complex  mixture y(n,f) (some texts call it x(n,f));
+ *                               interleaved (re, im); complex128 for
+ *                               FFCA_PREC_FP64, complex64 for FFCA_PREC_MIXED
+ *  - v      [J][F][ld] real     source power spectra v_j(n,f) > 0; double
+ *                               for FP64, float for MIXED; in/out
+ *  - lambda [F][J][I] double    diagonal of Lambda_j(f), > 0; in/out
+ *  - P      [F][I][I] complex128 row-major: P[f][a][i] = [P(f)]_{a,i}, so
+ *                               column i is p_i of Eq. FPI; in/out
+ * Base pointers must be 16-byte aligned.  Frames n >= N of each row are
+ * padding: they are read but never used; v's padding is written back
+ * unchanged and the Wiener output's padding is set to zero.
+ *
+ * Precision (ffca_precision):
+ *  - FFCA_PREC_FP64:  every per-(n,f) operation and reduction in FP64.
+ *  - FFCA_PREC_MIXED: per-(n,f) arithmetic in FP32 on complex64/float data;
+ *    reductions over n are compensated (Kahan / TwoSum double-float) in FP32
+ *    and finished in FP64; Lambda, P, the per-frequency I x I solves and the
+ *    log-likelihood totals are FP64.
+ *
+ * Supported shapes: 1 <= I <= 4, 1 <= J <= 6 (FFCA_ERR_UNSUPPORTED
+ * otherwise), N >= 1, F >= 0 (F == 0 is a no-op).
+ */
+#ifndef FFCA_H
+#define FFCA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FFCA_OK = 0,
+  FFCA_ERR_ARG = 1,         /* invalid argument: sizes, null/misaligned pointers, stride */
+  FFCA_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+  FFCA_ERR_NONFINITE = 3,   /* a non-finite or non-positive Lambda / log-likelihood appeared */
+  FFCA_ERR_SINGULAR = 4,    /* a per-frequency I x I system (P or V_i) was singular */
+  FFCA_ERR_TIMEOUT = 5,     /* reserved: a bounded device-side wait ran out */
+  FFCA_ERR_INTERNAL = 6,    /* library bug */
+  FFCA_ERR_UNSUPPORTED = 7  /* (I, J) outside the compiled set */
+} ffca_status;
+
+typedef enum { FFCA_PREC_FP64 = 0, FFCA_PREC_MIXED = 1 } ffca_precision;
+
+/* Problem and state of one FastFCA-AS estimation (device pointers). */
+typedef struct {
+  int I;                  /* microphones, 1..4 */
+  int J;                  /* sources, 1..6 */
+  int F;                  /* frequency bins, >= 0 */
+  int N;                  /* frames, >= 1 */
+  int ld;                 /* frame stride of y, v and the Wiener output; >= N, multiple of 4 */
+  int K;                  /* fixed-point sweeps per iteration (the paper uses K = 1), >= 1 */
+  int prec;               /* ffca_precision */
+  const void* y;          /* [I][F][ld] complex, read only */
+  void* v;                /* [J][F][ld] real, in/out */
+  double* lambda;         /* [F][J][I], in/out */
+  double* P;              /* [F][I][I] complex128 interleaved, in/out */
+  void* workspace;        /* device scratch, ffca_workspace_size() bytes, 256-byte aligned */
+  size_t workspace_bytes;
+  void* stream;           /* cudaStream_t */
+} ffca_desc;
+
+typedef struct ffca_ctx ffca_ctx;
+
+/* Bytes of device workspace the descriptor needs on the current device
+ * (partial sums, counters, per-frequency scalars, the trace).  Returns 0 if
+ * the descriptor's sizes are invalid. */
+size_t ffca_workspace_size(const ffca_desc* desc);
+
+/* Validate the descriptor, plan the launch grid for the current device and
+ * clear the workspace (enqueued on desc->stream).  On success *out receives
+ * a context to pass to the calls below and to release with ffca_destroy. */
+ffca_status ffca_init(ffca_ctx** out, const ffca_desc* desc);
+
+/* Run `iters` >= 0 hybrid iterations (Sec. 4.4) in place on (v, lambda, P).
+ * Each iteration: pass A (E-step, Eq. updatev, Eq. Lambdaupdate, L2 of the
+ * entering state), then pass B (V_i of Eq. FPI) with the per-frequency FP64
+ * fixed-point update of P (K sweeps, (I+1)K small inversions per frequency).
+ * ll_trace: host array of iters + 1 doubles or NULL.  When given, ll_trace[t]
+ * receives L2 (Eq. L2, natural log, including -I ln(pi) per point) of the
+ * state entering iteration t and ll_trace[iters] that of the final state;
+ * the call then synchronises and returns the latched device status.  When
+ * NULL the work is only enqueued (errors surface at the next sync call). */
+ffca_status ffca_iterate(ffca_ctx* ctx, int iters, double* ll_trace);
+
+/* L2 (Eq. L2) of the current state, synchronously, into *ll (host). */
+ffca_status ffca_loglik(ffca_ctx* ctx, double* ll);
+
+/* Multichannel Wiener filter (Eq. MMSE0 with Eq. covmodelprop):
+ * out[j][a][f][n] = [P^{-H} diag(v_j lambda_j / sigma) P^H y(n,f)]_a with
+ * sigma_i = sum_j v_j lambda_ji.  out: device, [J][I][F][ld] complex of the
+ * precision's type, caller-owned; padding frames are written as zero.
+ * Enqueued only. */
+ffca_status ffca_wiener(ffca_ctx* ctx, void* out);
+
+/* Wait for the context's stream and return the latched device status. */
+ffca_status ffca_sync(ffca_ctx* ctx);
+
+/* Frequency index of the first latched device error (-1 if none); valid
+ * after a synchronising call returned an error. */
+int ffca_error_frequency(const ffca_ctx* ctx);
+
+/* Number of per-frequency I x I inversions the fixed-point update has
+ * performed since ffca_init ((I+1) F K per iteration, Sec. 4.5).  Syncs. */
+ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
+
+/* Host-buffer transfers for callers whose data live in host memory: copy
+ * y, v, lambda and P (same layouts as the device arrays; any may be NULL to
+ * skip it) from host to the context's device arrays, or v, lambda and P back
+ * to host.  Enqueued on the context stream; ffca_download synchronises.
+ * Pinned (page-locked) host memory gives asynchronous, full-speed copies. */
+ffca_status ffca_upload(ffca_ctx* ctx, const void* y_host, const void* v_host,
+                        const double* lambda_host, const double* P_host);
+ffca_status ffca_download(ffca_ctx* ctx, void* v_host, double* lambda_host, double* P_host);
+
+/* Release the context (host memory only; the device arrays stay the caller's). */
+void ffca_destroy(ffca_ctx* ctx);
+
+const char* ffca_status_str(ffca_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFCA_H */

@@ -1,0 +1,359 @@
+// C ABI of the FastFCA-AS library: validation, launch planning, workspace
+// carving and the per-iteration launch sequence.  See include/ffca.h.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+
+#include "ffca.h"
+#include "ffca_dispatch.h"
+#include "ffca_fastfca.cuh"
+
+using namespace ffca;
+
+namespace ffca {
+
+const FastKernels* fast_kernels(int prec, int I, int J) {
+  if (prec == 0) {
+    switch (I) {
+      case 1: return fast_kernels_p0_i1(J);
+      case 2: return fast_kernels_p0_i2(J);
+      case 3: return fast_kernels_p0_i3(J);
+      case 4: return fast_kernels_p0_i4(J);
+    }
+  } else if (prec == 1) {
+    switch (I) {
+      case 1: return fast_kernels_p1_i1(J);
+      case 2: return fast_kernels_p1_i2(J);
+      case 3: return fast_kernels_p1_i3(J);
+      case 4: return fast_kernels_p1_i4(J);
+    }
+  }
+  return nullptr;
+}
+
+}  // namespace ffca
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Plan {
+  Partition pA, pB, pW;
+  size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB;
+  size_t bytes;
+};
+
+ffca_status check_shape(const ffca_desc* d) {
+  if (!d) return FFCA_ERR_ARG;
+  if (d->prec != FFCA_PREC_FP64 && d->prec != FFCA_PREC_MIXED) return FFCA_ERR_ARG;
+  if (d->F < 0 || d->N < 1 || d->ld < d->N || (d->ld % 4) != 0 || d->K < 1) return FFCA_ERR_ARG;
+  if (d->I < 1 || d->J < 1) return FFCA_ERR_ARG;
+  if (d->I > 4 || d->J > 6) return FFCA_ERR_UNSUPPORTED;
+  return FFCA_OK;
+}
+
+ffca_status check_pointers(const ffca_desc* d) {
+  if (d->F == 0) return FFCA_OK;
+  auto al = [](const void* p, uintptr_t a) { return p && (reinterpret_cast<uintptr_t>(p) % a) == 0; };
+  if (!al(d->y, 16) || !al(d->v, 16) || !al(d->lambda, 8) || !al(d->P, 16)) return FFCA_ERR_ARG;
+  if (!al(d->workspace, kAlign)) return FFCA_ERR_ARG;
+  return FFCA_OK;
+}
+
+ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FFCA_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  int occA = 0, occB = 0, occW = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k->estep_update, kBlock, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k->wcov, kBlock, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occW, k->wiener, kBlock, 0) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  if (occA < 1 || occB < 1 || occW < 1) return FFCA_ERR_INTERNAL;
+  const int FU = d->prec == FFCA_PREC_FP64 ? 1 : 2;
+  const int Uf = (d->N + FU - 1) / FU;
+  const int F = d->F > 0 ? d->F : 1;
+  p->pA = make_partition(F, Uf, nsm * occA);
+  p->pB = make_partition(F, Uf, nsm * occB);
+  // the Wiener pass also covers the padding frames (it writes them as zero)
+  p->pW = make_partition(F, d->ld / FU, nsm * occW);
+  p->pA.F = p->pB.F = p->pW.F = d->F;
+  const int I = d->I, J = d->J;
+  size_t off = kAlign;  // status words, global counters, inversion count
+  p->off_cntA = off; off = align_up(off + sizeof(unsigned) * F);
+  p->off_cntB = off; off = align_up(off + sizeof(unsigned) * F);
+  p->off_logdet = off; off = align_up(off + sizeof(double) * F);
+  p->off_llf = off; off = align_up(off + sizeof(double) * F);
+  p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
+  p->off_pinvH = off; off = align_up(off + sizeof(double) * 2 * I * I * (size_t)F);
+  p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)F * p->pA.max_slots * (J * I + 1));
+  p->off_partB = off; off = align_up(off + sizeof(double) * (size_t)F * p->pB.max_slots * I * I * I);
+  p->bytes = off;
+  return FFCA_OK;
+}
+
+}  // namespace
+
+struct ffca_ctx {
+  ffca_desc d;
+  const FastKernels* kern;
+  Plan plan;
+  cudaStream_t stream;
+  char* ws;
+  unsigned* status;
+  unsigned* gcntA;
+  unsigned* gcntB;
+  unsigned long long* ops;
+  int err_f;
+};
+
+namespace {
+
+FastArgs base_args(const ffca_ctx* c) {
+  FastArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.I = c->d.I;
+  a.J = c->d.J;
+  a.F = c->d.F;
+  a.N = c->d.N;
+  a.ld = c->d.ld;
+  a.K = c->d.K;
+  a.y = c->d.y;
+  a.v = c->d.v;
+  a.lam = c->d.lambda;
+  a.P = c->d.P;
+  a.logdet = reinterpret_cast<double*>(c->ws + c->plan.off_logdet);
+  a.llf = reinterpret_cast<double*>(c->ws + c->plan.off_llf);
+  a.trace = reinterpret_cast<double*>(c->ws + c->plan.off_trace);
+  a.status = c->status;
+  a.ops = c->ops;
+  return a;
+}
+
+FastArgs pass_a_args(const ffca_ctx* c, int slot) {
+  FastArgs a = base_args(c);
+  a.part = c->plan.pA;
+  a.part_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partA);
+  a.cnt = reinterpret_cast<unsigned*>(c->ws + c->plan.off_cntA);
+  a.gcnt = c->gcntA;
+  a.trace_slot = slot;
+  return a;
+}
+
+FastArgs pass_b_args(const ffca_ctx* c) {
+  FastArgs a = base_args(c);
+  a.part = c->plan.pB;
+  a.part_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partB);
+  a.cnt = reinterpret_cast<unsigned*>(c->ws + c->plan.off_cntB);
+  a.gcnt = c->gcntB;
+  return a;
+}
+
+ffca_status launch(const void* fn, int grid, int block, FastArgs& a, cudaStream_t s) {
+  void* args[] = {&a};
+  if (cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s) != cudaSuccess) return FFCA_ERR_CUDA;
+  return FFCA_OK;
+}
+
+ffca_status launch_prep(const ffca_ctx* c, bool want_pinv) {
+  FastArgs a = base_args(c);
+  a.pinvH = want_pinv ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
+  const int grid = (c->d.F + 127) / 128;
+  return launch(c->kern->prep, grid, 128, a, c->stream);
+}
+
+ffca_status read_status(ffca_ctx* c) {
+  unsigned h[2] = {0, 0};
+  if (cudaMemcpyAsync(h, c->status, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
+  if (h[0] != 0) {
+    c->err_f = (int)h[1];
+    return (ffca_status)h[0];
+  }
+  c->err_f = -1;
+  return FFCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ffca_workspace_size(const ffca_desc* d) {
+  if (check_shape(d) != FFCA_OK) return 0;
+  const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
+  if (!k) return 0;
+  Plan p;
+  if (make_plan(d, k, &p) != FFCA_OK) return 0;
+  return p.bytes;
+}
+
+ffca_status ffca_init(ffca_ctx** out, const ffca_desc* d) {
+  if (!out) return FFCA_ERR_ARG;
+  *out = nullptr;
+  ffca_status st = check_shape(d);
+  if (st != FFCA_OK) return st;
+  if ((st = check_pointers(d)) != FFCA_OK) return st;
+  const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
+  if (!k) return FFCA_ERR_UNSUPPORTED;
+  Plan p;
+  if ((st = make_plan(d, k, &p)) != FFCA_OK) return st;
+  if (d->F > 0 && d->workspace_bytes < p.bytes) return FFCA_ERR_ARG;
+  ffca_ctx* c = static_cast<ffca_ctx*>(std::calloc(1, sizeof(ffca_ctx)));
+  if (!c) return FFCA_ERR_INTERNAL;
+  c->d = *d;
+  c->kern = k;
+  c->plan = p;
+  c->stream = static_cast<cudaStream_t>(d->stream);
+  c->ws = static_cast<char*>(d->workspace);
+  c->status = reinterpret_cast<unsigned*>(c->ws);
+  c->gcntA = reinterpret_cast<unsigned*>(c->ws + 16);
+  c->gcntB = reinterpret_cast<unsigned*>(c->ws + 20);
+  c->ops = reinterpret_cast<unsigned long long*>(c->ws + 32);
+  c->err_f = -1;
+  if (d->F > 0 && cudaMemsetAsync(c->ws, 0, p.bytes, c->stream) != cudaSuccess) {
+    std::free(c);
+    return FFCA_ERR_CUDA;
+  }
+  *out = c;
+  return FFCA_OK;
+}
+
+ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
+  if (!c || iters < 0) return FFCA_ERR_ARG;
+  if (c->d.F == 0) {
+    if (ll_trace)
+      for (int t = 0; t <= iters; ++t) ll_trace[t] = 0.0;
+    return FFCA_OK;
+  }
+  ffca_status st = launch_prep(c, false);
+  if (st != FFCA_OK) return st;
+  const double* dtrace = reinterpret_cast<const double*>(c->ws + c->plan.off_trace);
+  int flushed = 0;  // first trace index not yet copied to the host
+  for (int t = 0; t <= iters; ++t) {
+    const int slot = t % kTraceCap;
+    if (t < iters) {
+      FastArgs a = pass_a_args(c, slot);
+      if ((st = launch(c->kern->estep_update, a.part.nblocks, kBlock, a, c->stream)) != FFCA_OK) return st;
+      FastArgs b = pass_b_args(c);
+      if ((st = launch(c->kern->wcov, b.part.nblocks, kBlock, b, c->stream)) != FFCA_OK) return st;
+    } else if (ll_trace) {
+      FastArgs a = pass_a_args(c, slot);
+      if ((st = launch(c->kern->estep_eval, a.part.nblocks, kBlock, a, c->stream)) != FFCA_OK) return st;
+    }
+    if (ll_trace && (slot == kTraceCap - 1 || t == iters)) {
+      const int n = t - flushed + 1;
+      if (cudaMemcpyAsync(ll_trace + flushed, dtrace, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                          c->stream) != cudaSuccess)
+        return FFCA_ERR_CUDA;
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
+      flushed = t + 1;
+    }
+  }
+  if (ll_trace) return read_status(c);
+  return cudaGetLastError() == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
+}
+
+ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
+  if (!c || !ll) return FFCA_ERR_ARG;
+  if (c->d.F == 0) {
+    *ll = 0.0;
+    return FFCA_OK;
+  }
+  ffca_status st = launch_prep(c, false);
+  if (st != FFCA_OK) return st;
+  FastArgs a = pass_a_args(c, 0);
+  if ((st = launch(c->kern->estep_eval, a.part.nblocks, kBlock, a, c->stream)) != FFCA_OK) return st;
+  if (cudaMemcpyAsync(ll, a.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  return read_status(c);
+}
+
+ffca_status ffca_wiener(ffca_ctx* c, void* out) {
+  if (!c) return FFCA_ERR_ARG;
+  if (c->d.F == 0) return FFCA_OK;
+  if (!out || (reinterpret_cast<uintptr_t>(out) % 16) != 0) return FFCA_ERR_ARG;
+  ffca_status st = launch_prep(c, true);
+  if (st != FFCA_OK) return st;
+  FastArgs a = base_args(c);
+  a.part = c->plan.pW;
+  a.pinvH = reinterpret_cast<double*>(c->ws + c->plan.off_pinvH);
+  a.out = out;
+  return launch(c->kern->wiener, a.part.nblocks, kBlock, a, c->stream);
+}
+
+ffca_status ffca_sync(ffca_ctx* c) {
+  if (!c) return FFCA_ERR_ARG;
+  if (c->d.F == 0) return cudaStreamSynchronize(c->stream) == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
+  return read_status(c);
+}
+
+int ffca_error_frequency(const ffca_ctx* c) { return c ? c->err_f : -1; }
+
+ffca_status ffca_inversion_count(ffca_ctx* c, unsigned long long* count) {
+  if (!c || !count) return FFCA_ERR_ARG;
+  if (c->d.F == 0) {
+    *count = 0;
+    return FFCA_OK;
+  }
+  if (cudaMemcpyAsync(count, c->ops, sizeof(*count), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
+}
+
+ffca_status ffca_upload(ffca_ctx* c, const void* y_host, const void* v_host, const double* lam_host,
+                        const double* P_host) {
+  if (!c) return FFCA_ERR_ARG;
+  const ffca_desc& d = c->d;
+  const size_t rsz = d.prec == FFCA_PREC_FP64 ? 8 : 4;
+  const size_t ybytes = (size_t)d.I * d.F * d.ld * 2 * rsz;
+  const size_t vbytes = (size_t)d.J * d.F * d.ld * rsz;
+  const size_t lbytes = (size_t)d.F * d.J * d.I * sizeof(double);
+  const size_t pbytes = (size_t)d.F * d.I * d.I * 2 * sizeof(double);
+  auto cp = [&](void* dst, const void* src, size_t n) {
+    return (src == nullptr || n == 0 ||
+            cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream) == cudaSuccess);
+  };
+  if (!cp(const_cast<void*>(d.y), y_host, ybytes) || !cp(d.v, v_host, vbytes) ||
+      !cp(d.lambda, lam_host, lbytes) || !cp(d.P, P_host, pbytes))
+    return FFCA_ERR_CUDA;
+  return FFCA_OK;
+}
+
+ffca_status ffca_download(ffca_ctx* c, void* v_host, double* lam_host, double* P_host) {
+  if (!c) return FFCA_ERR_ARG;
+  const ffca_desc& d = c->d;
+  const size_t rsz = d.prec == FFCA_PREC_FP64 ? 8 : 4;
+  const size_t vbytes = (size_t)d.J * d.F * d.ld * rsz;
+  const size_t lbytes = (size_t)d.F * d.J * d.I * sizeof(double);
+  const size_t pbytes = (size_t)d.F * d.I * d.I * 2 * sizeof(double);
+  auto cp = [&](void* dst, const void* src, size_t n) {
+    return (dst == nullptr || n == 0 ||
+            cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, c->stream) == cudaSuccess);
+  };
+  if (!cp(v_host, d.v, vbytes) || !cp(lam_host, d.lambda, lbytes) || !cp(P_host, d.P, pbytes))
+    return FFCA_ERR_CUDA;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
+}
+
+void ffca_destroy(ffca_ctx* c) { std::free(c); }
+
+const char* ffca_status_str(ffca_status s) {
+  switch (s) {
+    case FFCA_OK: return "ok";
+    case FFCA_ERR_ARG: return "invalid argument";
+    case FFCA_ERR_CUDA: return "CUDA error";
+    case FFCA_ERR_NONFINITE: return "non-finite or non-positive value";
+    case FFCA_ERR_SINGULAR: return "singular per-frequency system";
+    case FFCA_ERR_TIMEOUT: return "device wait timed out";
+    case FFCA_ERR_INTERNAL: return "internal error";
+    case FFCA_ERR_UNSUPPORTED: return "unsupported (I, J)";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,29 @@
+// Host-side table of the compiled kernel instantiations.
+#pragma once
+
+namespace ffca {
+
+// Every FastFCA-AS kernel takes one FastArgs by value.
+struct FastKernels {
+  const void* estep_update;  // pass A with the M-step
+  const void* estep_eval;    // pass A, log-likelihood only
+  const void* wcov;          // pass B with the fixed-point update of P
+  const void* wiener;
+  const void* prep;          // per-frequency ln|det P|^2 and P^{-H}
+};
+
+// prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.
+const FastKernels* fast_kernels(int prec, int I, int J);
+
+#define FFCA_DECLARE_TABLE(P, I) const FastKernels* fast_kernels_p##P##_i##I(int J);
+FFCA_DECLARE_TABLE(0, 1)
+FFCA_DECLARE_TABLE(0, 2)
+FFCA_DECLARE_TABLE(0, 3)
+FFCA_DECLARE_TABLE(0, 4)
+FFCA_DECLARE_TABLE(1, 1)
+FFCA_DECLARE_TABLE(1, 2)
+FFCA_DECLARE_TABLE(1, 3)
+FFCA_DECLARE_TABLE(1, 4)
+#undef FFCA_DECLARE_TABLE
+
+}  // namespace ffca

@@ -1,0 +1,596 @@
+// FastFCA-AS kernels (Ito & Nakatani, Sec. 4.4).
+//
+//   k_estep   pass A: y~ = P^H y, sigma_i = sum_j v_j lambda_ji, the posterior
+//             powers q_ji = |mu~_ji|^2 + phi~_ji (Eqs. mutilde0, Phitilde0),
+//             the v update written in place (Eq. updatev), the Lambda
+//             numerators sum_n q_ji / v_j^new (Eq. Lambdaupdate) and the
+//             per-frame log-likelihood terms of the entering state (Eq. L2).
+//             The last CTA to finish a frequency finalises Lambda(f); the
+//             last frequency finalises the scalar log-likelihood.
+//   k_wcov    pass B: V_i(f) = (1/N) sum_n y y^H / sigma_i with the new v and
+//             Lambda (Eq. FPI); the last CTA of a frequency runs the FP64
+//             fixed-point update of P(f) (K sweeps) and ln|det P(f)|^2.
+//   k_wiener  x^_j = P^{-H} diag(v_j lambda_j / sigma) P^H y (Eq. MMSE0).
+//   k_prep    per frequency: ln|det P|^2 and P^{-H} (FP64).
+//
+// Layouts: y [I][F][ld] complex (float2 or double2), v [J][F][ld] real,
+// lambda [F][J][I] double, P [F][I][I] complex double row-major.  Both
+// streaming passes read whole 16-byte vector units: two frames of a c64 mic
+// row, or one frame of a c128 row.
+#pragma once
+
+#include "ffca_common.cuh"
+
+namespace ffca {
+
+constexpr int kTraceCap = 4096;  // device-side log-likelihood trace slots
+constexpr double kLnPi = 1.1447298858494002;
+
+struct FastArgs {
+  Partition part;
+  int I, J, F, N, ld, K;
+  const void* y;
+  void* v;
+  double* lam;
+  double* P;
+  double* part_buf;          // [F][max_slots][NV] partial sums of one pass
+  unsigned* cnt;             // [F] arrival counters of that pass
+  unsigned* gcnt;            // global arrival counter of that pass
+  double* logdet;            // [F] ln|det P(f)|^2 of the current P
+  double* llf;               // [F] per-frequency log-likelihood
+  double* trace;             // [kTraceCap]
+  int trace_slot;
+  unsigned* status;          // [2] first error code, its frequency
+  unsigned long long* ops;   // matrix inversions performed by the P update
+  double* pinvH;             // [F][I][I] complex, P^{-H} (Wiener)
+  void* out;                 // Wiener output [J][I][F][ld] complex
+};
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using Y = float4;  // two c64 frames
+  using V = float2;  // two real frames
+  static constexpr int FU = 2;
+};
+template <>
+struct Vec<double> {
+  using Y = double2;  // one c128 frame
+  using V = double;   // one real frame
+  static constexpr int FU = 1;
+};
+
+__device__ inline cpx<float> yframe(const float4& u, int e) {
+  return e == 0 ? mk(u.x, u.y) : mk(u.z, u.w);
+}
+__device__ inline cpx<double> yframe(const double2& u, int) { return mk(u.x, u.y); }
+__device__ inline float vframe(const float2& u, int e) { return e == 0 ? u.x : u.y; }
+__device__ inline double vframe(double u, int) { return u; }
+__device__ inline void vset(float2& u, int e, float x) {
+  if (e == 0) u.x = x; else u.y = x;
+}
+__device__ inline void vset(double& u, int, double x) { u = x; }
+__device__ inline void yset(float4& u, int e, cpx<float> z) {
+  if (e == 0) { u.x = z.re; u.y = z.im; } else { u.z = z.re; u.w = z.im; }
+}
+__device__ inline void yset(double2& u, int, cpx<double> z) { u.x = z.re; u.y = z.im; }
+
+constexpr int kUnits = 2;  // vector units per thread per loop trip
+
+// Sum the partial slots of frequency f for value t in slot order (deterministic).
+__device__ inline double sum_slots(const double* part_buf, int f, int nslots, int max_slots,
+                                   int NV, int t) {
+  const double* p = part_buf + ((size_t)f * max_slots) * NV + t;
+  double s = 0.0;
+  for (int k = 0; k < nslots; ++k) s += __ldcg(p + (size_t)k * NV);
+  return s;
+}
+
+// The last frequency finaliser adds the per-frequency log-likelihoods in
+// frequency order (one warp, fixed tree) into the trace slot.
+__device__ inline void finalize_trace(const FastArgs& a) {
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int f = threadIdx.x; f < a.F; f += 32) s += __ldcg(a.llf + f);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) a.trace[a.trace_slot] = s;
+  }
+}
+
+// -------------------------------------------------------------- pass A
+template <typename T, int I, int J, bool UPDATE>
+__global__ void __launch_bounds__(kBlock) k_estep(FastArgs a) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  constexpr int FU = Vec<T>::FU;
+  constexpr int NV = UPDATE ? J * I + 1 : 1;  // Lambda numerators, then loglik
+  constexpr int LL = NV - 1;
+
+  __shared__ typename BlockReduce<T, NV>::Smem red;
+  __shared__ double sP[I][I][2];
+  __shared__ double sLam[J][I];
+  __shared__ int sflag;
+
+  const Partition pt = a.part;
+  const long long total = (long long)pt.F * pt.Uf;
+  const long long u0 = (long long)blockIdx.x * pt.upb;
+  const long long u1 = min(u0 + pt.upb, total);
+  const long long row = a.ld / FU;  // vector units per (mic or source, f) row
+  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
+  VV* __restrict__ v = reinterpret_cast<VV*>(a.v);
+
+  for (long long u = u0; u < u1;) {
+    const int f = (int)(u / pt.Uf);
+    const int k0 = (int)(u - (long long)f * pt.Uf);
+    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+
+    if (threadIdx.x < I * I) {
+      const int r = threadIdx.x / I, c = threadIdx.x % I;
+      sP[r][c][0] = a.P[((size_t)f * I * I + threadIdx.x) * 2];
+      sP[r][c][1] = a.P[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+    }
+    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
+    __syncthreads();
+
+    cpx<T> Pc[I][I];  // P(f), used as conj(P_ai) in y~_i = sum_a conj(P_ai) y_a
+    T lam[J][I], ilam[J][I];
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c) Pc[r][c] = mk<T>((T)sP[r][c][0], (T)sP[r][c][1]);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int i = 0; i < I; ++i) {
+        lam[j][i] = (T)sLam[j][i];
+        ilam[j][i] = recip(lam[j][i]);
+      }
+
+    Acc<T> acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t].zero();
+
+    for (int kb = k0 + threadIdx.x; kb < k1; kb += kBlock * kUnits) {
+      VY yu[kUnits][I];
+      VV vu[kUnits][J];
+#pragma unroll
+      for (int q = 0; q < kUnits; ++q) {
+        const int k = kb + q * kBlock;
+        if (k < k1) {
+#pragma unroll
+          for (int m = 0; m < I; ++m) yu[q][m] = y[((size_t)m * pt.F + f) * row + k];
+#pragma unroll
+          for (int j = 0; j < J; ++j) vu[q][j] = v[((size_t)j * pt.F + f) * row + k];
+        }
+      }
+      T grp[NV];
+#pragma unroll
+      for (int t = 0; t < NV; ++t) grp[t] = (T)0;
+
+#pragma unroll
+      for (int q = 0; q < kUnits; ++q) {
+        const int k = kb + q * kBlock;
+        if (k >= k1) continue;
+#pragma unroll
+        for (int e = 0; e < FU; ++e) {
+          const int n = k * FU + e;
+          if (n >= a.N) continue;
+          cpx<T> yt[I];
+#pragma unroll
+          for (int i = 0; i < I; ++i) {
+            cpx<T> s = mk<T>(0, 0);
+#pragma unroll
+            for (int m = 0; m < I; ++m) cfmac(s, Pc[m][i], yframe(yu[q][m], e));
+            yt[i] = s;
+          }
+          T vv[J];
+#pragma unroll
+          for (int j = 0; j < J; ++j) vv[j] = vframe(vu[q][j], e);
+          T sig[I], rs[I], e2[I];
+          T ll = (T)0;
+#pragma unroll
+          for (int i = 0; i < I; ++i) {
+            T s = vv[0] * lam[0][i];
+#pragma unroll
+            for (int j = 1; j < J; ++j) s = fma(vv[j], lam[j][i], s);
+            sig[i] = s;
+            rs[i] = recip(s);
+            e2[i] = cabs2(yt[i]);
+            ll += logx(s) + e2[i] * rs[i];
+          }
+          grp[LL] += ll;
+          if constexpr (UPDATE) {
+            T qv[J][I];
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+              T vn = (T)0;
+#pragma unroll
+              for (int i = 0; i < I; ++i) {
+                const T aji = vv[j] * lam[j][i];          // v_j [Lambda_j]_ii
+                const T g = aji * rs[i];                   // Wiener gain
+                const T phi = fma(-aji, g, aji);           // Eq. Phitilde0
+                const T qq = fma(g * g, e2[i], phi);       // |mu~|^2 + phi~
+                qv[j][i] = qq;
+                vn = fma(qq, ilam[j][i], vn);
+              }
+              vn *= (T)(1.0 / I);                          // Eq. updatev
+              vset(vu[q][j], e, vn);
+              const T rv = recip(vn);
+#pragma unroll
+              for (int i = 0; i < I; ++i) grp[j * I + i] = fma(qv[j][i], rv, grp[j * I + i]);
+            }
+          }
+        }
+        if constexpr (UPDATE) {
+#pragma unroll
+          for (int j = 0; j < J; ++j) v[((size_t)j * pt.F + f) * row + k] = vu[q][j];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NV; ++t) acc[t].add(grp[t]);
+    }
+
+    T hi[NV], lo[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      hi[t] = acc[t].value_hi();
+      lo[t] = acc[t].value_lo();
+    }
+    const int slot = (int)blockIdx.x - pt.first_block(f);
+    BlockReduce<T, NV>::run(hi, lo, red,
+                            a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
+
+    if (arrive_last(a.cnt + f, (unsigned)pt.nslots(f), &sflag)) {
+      const int ns = pt.nslots(f);
+      if (threadIdx.x < NV) {
+        const int t = threadIdx.x;
+        const double tot = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, t);
+        if (t == LL) {
+          const double lf = -(double)I * a.N * kLnPi + (double)a.N * __ldcg(a.logdet + f) - tot;
+          if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
+          a.llf[f] = lf;
+        } else {
+          const double lnew = tot / a.N;                  // Eq. Lambdaupdate
+          if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
+          a.lam[(size_t)f * J * I + t] = lnew;
+        }
+      }
+      if (arrive_last(a.gcnt, (unsigned)pt.F, &sflag)) finalize_trace(a);
+    }
+    __syncthreads();
+    u += k1 - k0;
+  }
+}
+
+// -------------------------------------------------------------- pass B
+// Packed Hermitian V_i: I real diagonal entries, then (re, im) of the
+// entries above the diagonal in row order; I^2 reals per i.
+template <int I>
+__device__ inline void unpack_herm(const double* src, cpx<double> (&V)[I][I]) {
+  int m = I;
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    V[r][r] = mk(src[r], 0.0);
+#pragma unroll
+    for (int c = r + 1; c < I; ++c) {
+      V[r][c] = mk(src[m], src[m + 1]);
+      V[c][r] = mk(src[m], -src[m + 1]);
+      m += 2;
+    }
+  }
+}
+
+// FP64 fixed-point update of P(f) (Eq. FPI, K sweeps) from the finalised
+// V_i in shared memory.  Lane 0 inverts P, lanes i < I solve column i.
+template <int I>
+__device__ void p_update(const FastArgs& a, int f, const double* sV, double (*sPn)[I][2],
+                         double (*sQ)[I][2], int* sbad) {
+  const int lane = threadIdx.x;  // called by warp 0 only
+  if (lane == 0) *sbad = 0;
+  if (lane < I * I) {
+    sPn[lane / I][lane % I][0] = a.P[((size_t)f * I * I + lane) * 2];
+    sPn[lane / I][lane % I][1] = a.P[((size_t)f * I * I + lane) * 2 + 1];
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < a.K; ++sweep) {
+    if (lane == 0) {
+      cpx<double> A[I][I];
+#pragma unroll
+      for (int r = 0; r < I; ++r)
+#pragma unroll
+        for (int c = 0; c < I; ++c) A[r][c] = mk(sPn[r][c][0], sPn[r][c][1]);
+      double ld2;
+      if (!gj_inverse<I>(A, ld2)) *sbad = 1;
+      // Q = (P^{-1})^H: Q[r][c] = conj(Pinv[c][r])
+#pragma unroll
+      for (int r = 0; r < I; ++r)
+#pragma unroll
+        for (int c = 0; c < I; ++c) {
+          sQ[r][c][0] = A[c][r].re;
+          sQ[r][c][1] = -A[c][r].im;
+        }
+    }
+    __syncwarp();
+    if (lane < I) {
+      const int i = lane;
+      cpx<double> V[I][I], b[I], x[I];
+      unpack_herm<I>(sV + i * I * I, V);
+#pragma unroll
+      for (int r = 0; r < I; ++r) b[r] = mk(sQ[r][i][0], sQ[r][i][1]);
+      if (!chol_solve<I>(V, b, x)) *sbad = 1;
+#pragma unroll
+      for (int r = 0; r < I; ++r) {
+        sPn[r][i][0] = x[r].re;
+        sPn[r][i][1] = x[r].im;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    cpx<double> A[I][I];
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c) A[r][c] = mk(sPn[r][c][0], sPn[r][c][1]);
+    double ld2 = 0.0;
+    if (!gj_inverse<I>(A, ld2)) *sbad = 1;
+    a.logdet[f] = ld2;
+    atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
+    if (*sbad) raise_status(a.status, kDevSingular, f);
+  }
+  __syncwarp();
+  if (lane < I * I) {
+    a.P[((size_t)f * I * I + lane) * 2] = sPn[lane / I][lane % I][0];
+    a.P[((size_t)f * I * I + lane) * 2 + 1] = sPn[lane / I][lane % I][1];
+  }
+}
+
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(kBlock) k_wcov(FastArgs a) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  constexpr int FU = Vec<T>::FU;
+  constexpr int I2 = I * I;
+  constexpr int NV = I * I2;
+
+  __shared__ typename BlockReduce<T, NV>::Smem red;
+  __shared__ double sLam[J][I];
+  __shared__ double sV[NV];
+  __shared__ double sPn[I][I][2];
+  __shared__ double sQ[I][I][2];
+  __shared__ int sflag, sbad;
+
+  const Partition pt = a.part;
+  const long long total = (long long)pt.F * pt.Uf;
+  const long long u0 = (long long)blockIdx.x * pt.upb;
+  const long long u1 = min(u0 + pt.upb, total);
+  const long long row = a.ld / FU;
+  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
+  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
+
+  for (long long u = u0; u < u1;) {
+    const int f = (int)(u / pt.Uf);
+    const int k0 = (int)(u - (long long)f * pt.Uf);
+    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+
+    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
+    __syncthreads();
+    T lam[J][I];
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int i = 0; i < I; ++i) lam[j][i] = (T)sLam[j][i];
+
+    Acc<T> acc[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) acc[t].zero();
+
+    for (int kb = k0 + threadIdx.x; kb < k1; kb += kBlock * kUnits) {
+      VY yu[kUnits][I];
+      VV vu[kUnits][J];
+#pragma unroll
+      for (int q = 0; q < kUnits; ++q) {
+        const int k = kb + q * kBlock;
+        if (k < k1) {
+#pragma unroll
+          for (int m = 0; m < I; ++m) yu[q][m] = y[((size_t)m * pt.F + f) * row + k];
+#pragma unroll
+          for (int j = 0; j < J; ++j) vu[q][j] = v[((size_t)j * pt.F + f) * row + k];
+        }
+      }
+      T grp[NV];
+#pragma unroll
+      for (int t = 0; t < NV; ++t) grp[t] = (T)0;
+#pragma unroll
+      for (int q = 0; q < kUnits; ++q) {
+        const int k = kb + q * kBlock;
+        if (k >= k1) continue;
+#pragma unroll
+        for (int e = 0; e < FU; ++e) {
+          const int n = k * FU + e;
+          if (n >= a.N) continue;
+          cpx<T> ym[I];
+#pragma unroll
+          for (int m = 0; m < I; ++m) ym[m] = yframe(yu[q][m], e);
+          T w[I];
+#pragma unroll
+          for (int i = 0; i < I; ++i) {
+            T s = vframe(vu[q][0], e) * lam[0][i];
+#pragma unroll
+            for (int j = 1; j < J; ++j) s = fma(vframe(vu[q][j], e), lam[j][i], s);
+            w[i] = recip(s);
+          }
+          // y y^H, packed: diagonal |y_r|^2, then y_r conj(y_c) for r < c
+          T pk[I2];
+          {
+            int m = I;
+#pragma unroll
+            for (int r = 0; r < I; ++r) {
+              pk[r] = cabs2(ym[r]);
+#pragma unroll
+              for (int c = r + 1; c < I; ++c) {
+                pk[m] = fma(ym[r].re, ym[c].re, ym[r].im * ym[c].im);
+                pk[m + 1] = fma(ym[r].im, ym[c].re, -ym[r].re * ym[c].im);
+                m += 2;
+              }
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < I; ++i)
+#pragma unroll
+            for (int m = 0; m < I2; ++m) grp[i * I2 + m] = fma(w[i], pk[m], grp[i * I2 + m]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < NV; ++t) acc[t].add(grp[t]);
+    }
+
+    T hi[NV], lo[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+      hi[t] = acc[t].value_hi();
+      lo[t] = acc[t].value_lo();
+    }
+    const int slot = (int)blockIdx.x - pt.first_block(f);
+    BlockReduce<T, NV>::run(hi, lo, red, a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
+
+    if (arrive_last(a.cnt + f, (unsigned)pt.nslots(f), &sflag)) {
+      const int ns = pt.nslots(f);
+      for (int t = threadIdx.x; t < NV; t += kBlock) {
+        const double s = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, t) / a.N;
+        if (!isfinite(s)) raise_status(a.status, kDevNonfinite, f);
+        sV[t] = s;
+      }
+      __syncthreads();
+      if (threadIdx.x < 32) p_update<I>(a, f, sV, sPn, sQ, &sbad);
+    }
+    __syncthreads();
+    u += k1 - k0;
+  }
+}
+
+// -------------------------------------------------------------- prep
+// Per frequency (one thread each): ln|det P|^2 and P^{-H} of the current P.
+template <int I>
+__global__ void k_prep(FastArgs a) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= a.F) return;
+  cpx<double> A[I][I];
+#pragma unroll
+  for (int r = 0; r < I; ++r)
+#pragma unroll
+    for (int c = 0; c < I; ++c)
+      A[r][c] = mk(a.P[((size_t)f * I * I + r * I + c) * 2], a.P[((size_t)f * I * I + r * I + c) * 2 + 1]);
+  double ld2 = 0.0;
+  if (!gj_inverse<I>(A, ld2)) raise_status(a.status, kDevSingular, f);
+  a.logdet[f] = ld2;
+  if (a.pinvH) {
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c) {  // (P^{-1})^H [r][c] = conj(Pinv[c][r])
+        a.pinvH[((size_t)f * I * I + r * I + c) * 2] = A[c][r].re;
+        a.pinvH[((size_t)f * I * I + r * I + c) * 2 + 1] = -A[c][r].im;
+      }
+  }
+}
+
+// -------------------------------------------------------------- Wiener
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(kBlock) k_wiener(FastArgs a) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  constexpr int FU = Vec<T>::FU;
+  __shared__ double sP[I][I][2], sQ[I][I][2];
+  __shared__ double sLam[J][I];
+
+  const Partition pt = a.part;
+  const long long total = (long long)pt.F * pt.Uf;
+  const long long u0 = (long long)blockIdx.x * pt.upb;
+  const long long u1 = min(u0 + pt.upb, total);
+  const long long row = a.ld / FU;
+  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
+  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
+  VY* __restrict__ out = reinterpret_cast<VY*>(a.out);
+
+  for (long long u = u0; u < u1;) {
+    const int f = (int)(u / pt.Uf);
+    const int k0 = (int)(u - (long long)f * pt.Uf);
+    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+    __syncthreads();
+    if (threadIdx.x < I * I) {
+      const int r = threadIdx.x / I, c = threadIdx.x % I;
+      sP[r][c][0] = a.P[((size_t)f * I * I + threadIdx.x) * 2];
+      sP[r][c][1] = a.P[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+      sQ[r][c][0] = a.pinvH[((size_t)f * I * I + threadIdx.x) * 2];
+      sQ[r][c][1] = a.pinvH[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+    }
+    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
+    __syncthreads();
+    cpx<T> Pc[I][I], Q[I][I];
+    T lam[J][I];
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c) {
+        Pc[r][c] = mk<T>((T)sP[r][c][0], (T)sP[r][c][1]);
+        Q[r][c] = mk<T>((T)sQ[r][c][0], (T)sQ[r][c][1]);
+      }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int i = 0; i < I; ++i) lam[j][i] = (T)sLam[j][i];
+
+    for (int k = k0 + threadIdx.x; k < k1; k += kBlock) {
+      VY yu[I];
+      VV vu[J];
+#pragma unroll
+      for (int m = 0; m < I; ++m) yu[m] = y[((size_t)m * pt.F + f) * row + k];
+#pragma unroll
+      for (int j = 0; j < J; ++j) vu[j] = v[((size_t)j * pt.F + f) * row + k];
+      VY o[J][I];
+#pragma unroll
+      for (int e = 0; e < FU; ++e) {
+        const bool valid = k * FU + e < a.N;
+        cpx<T> yt[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          cpx<T> s = mk<T>(0, 0);
+#pragma unroll
+          for (int m = 0; m < I; ++m) cfmac(s, Pc[m][i], yframe(yu[m], e));
+          yt[i] = s;
+        }
+        T rs[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          T s = vframe(vu[0], e) * lam[0][i];
+#pragma unroll
+          for (int j = 1; j < J; ++j) s = fma(vframe(vu[j], e), lam[j][i], s);
+          rs[i] = recip(s);
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          cpx<T> z[I];
+#pragma unroll
+          for (int i = 0; i < I; ++i) z[i] = cscale(yt[i], vframe(vu[j], e) * lam[j][i] * rs[i]);
+#pragma unroll
+          for (int r = 0; r < I; ++r) {
+            cpx<T> s = mk<T>(0, 0);
+#pragma unroll
+            for (int i = 0; i < I; ++i) cfma(s, Q[r][i], z[i]);
+            yset(o[j][r], e, valid ? s : mk<T>(0, 0));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int r = 0; r < I; ++r) out[(((size_t)j * I + r) * pt.F + f) * row + k] = o[j][r];
+    }
+    u += k1 - k0;
+  }
+}
+
+}  // namespace ffca

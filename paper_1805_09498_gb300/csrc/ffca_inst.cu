@@ -1,0 +1,48 @@
+// Explicit instantiations of the FastFCA-AS kernels for one precision and
+// one microphone count, J = 1..6.  Compiled once per (FFCA_PREC, FFCA_I).
+#include "ffca_dispatch.h"
+#include "ffca_fastfca.cuh"
+
+#ifndef FFCA_PREC
+#error "FFCA_PREC must be defined (0 = FP64, 1 = mixed)"
+#endif
+#ifndef FFCA_I
+#error "FFCA_I must be defined"
+#endif
+
+namespace ffca {
+
+#if FFCA_PREC == 0
+using Real = double;
+#else
+using Real = float;
+#endif
+
+template <int J>
+static const FastKernels* table_entry() {
+  static const FastKernels k = {
+      (const void*)k_estep<Real, FFCA_I, J, true>,
+      (const void*)k_estep<Real, FFCA_I, J, false>,
+      (const void*)k_wcov<Real, FFCA_I, J>,
+      (const void*)k_wiener<Real, FFCA_I, J>,
+      (const void*)k_prep<FFCA_I>,
+  };
+  return &k;
+}
+
+#define FFCA_CAT2(a, b, c, d) a##b##c##d
+#define FFCA_CAT(a, b, c, d) FFCA_CAT2(a, b, c, d)
+
+const FastKernels* FFCA_CAT(fast_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
+  switch (J) {
+    case 1: return table_entry<1>();
+    case 2: return table_entry<2>();
+    case 3: return table_entry<3>();
+    case 4: return table_entry<4>();
+    case 5: return table_entry<5>();
+    case 6: return table_entry<6>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace ffca

@@ -1,0 +1,261 @@
+"""Thin Python binding of libffca.so (argument marshalling only).
+
+The functions keep the C names of include/ffca.h; every step of the
+estimation runs in the CUDA library.  PyTorch supplies device memory and the
+stream.  There is no fallback: if libffca.so is missing or cannot be loaded
+the binding raises.
+
+Typical use (device tensors, mic-planar layouts, ld = padded frame stride):
+
+    est = FastFCA(y, v, lam, P, N=N)          # y [I,F,ld] complex, v [J,F,ld] real
+    trace = est.iterate(20)                    # numpy array, iters + 1 values of L2
+    out = est.wiener()                         # [J,I,F,ld] complex
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffca.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ffca.h")
+
+FFCA_OK = 0
+FFCA_PREC_FP64 = 0
+FFCA_PREC_MIXED = 1
+STATUS_NAMES = {0: "FFCA_OK", 1: "FFCA_ERR_ARG", 2: "FFCA_ERR_CUDA", 3: "FFCA_ERR_NONFINITE",
+                4: "FFCA_ERR_SINGULAR", 5: "FFCA_ERR_TIMEOUT", 6: "FFCA_ERR_INTERNAL",
+                7: "FFCA_ERR_UNSUPPORTED"}
+
+
+class FFCAError(RuntimeError):
+    def __init__(self, status: int, what: str, frequency: int = -1):
+        self.status = status
+        self.frequency = frequency
+        name = STATUS_NAMES.get(status, str(status))
+        extra = f" at frequency {frequency}" if frequency >= 0 else ""
+        super().__init__(f"{what}: {name}{extra}")
+
+
+class ffca_desc(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int), ("J", ctypes.c_int), ("F", ctypes.c_int),
+                ("N", ctypes.c_int), ("ld", ctypes.c_int), ("K", ctypes.c_int),
+                ("prec", ctypes.c_int),
+                ("y", ctypes.c_void_p), ("v", ctypes.c_void_p), ("lambda_", ctypes.c_void_p),
+                ("P", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libffca.so (built by paper_1805_09498_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1805_09498_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    vp, ci, dp = ctypes.c_void_p, ctypes.c_int, P(ctypes.c_double)
+    sigs = {
+        "ffca_workspace_size": (ctypes.c_size_t, [P(ffca_desc)]),
+        "ffca_init": (ci, [P(vp), P(ffca_desc)]),
+        "ffca_iterate": (ci, [vp, ci, dp]),
+        "ffca_loglik": (ci, [vp, dp]),
+        "ffca_wiener": (ci, [vp, vp]),
+        "ffca_sync": (ci, [vp]),
+        "ffca_error_frequency": (ci, [vp]),
+        "ffca_inversion_count": (ci, [vp, P(ctypes.c_ulonglong)]),
+        "ffca_upload": (ci, [vp, vp, vp, vp, vp]),
+        "ffca_download": (ci, [vp, vp, vp, vp]),
+        "ffca_destroy": (None, [vp]),
+        "ffca_status_str": (ctypes.c_char_p, [ci]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/ffca.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ffca_[a-z0-9_]+)\s*\(", text)))
+
+
+# ------------------------------------------------------------ C-named calls
+def ffca_workspace_size(desc: ffca_desc) -> int:
+    return int(lib().ffca_workspace_size(ctypes.byref(desc)))
+
+
+def ffca_init(desc: ffca_desc) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = lib().ffca_init(ctypes.byref(ctx), ctypes.byref(desc))
+    if st != FFCA_OK:
+        raise FFCAError(st, "ffca_init")
+    return ctx
+
+
+def _check(ctx, st, what):
+    if st != FFCA_OK:
+        raise FFCAError(st, what, lib().ffca_error_frequency(ctx))
+
+
+def ffca_iterate(ctx, iters: int, trace: bool = True):
+    """Returns the L2 trace (numpy, iters + 1) when trace, else None (enqueue only)."""
+    if trace:
+        buf = np.zeros(iters + 1, dtype=np.float64)
+        st = lib().ffca_iterate(ctx, iters, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        _check(ctx, st, "ffca_iterate")
+        return buf
+    _check(ctx, lib().ffca_iterate(ctx, iters, None), "ffca_iterate")
+    return None
+
+
+def ffca_loglik(ctx) -> float:
+    out = ctypes.c_double()
+    _check(ctx, lib().ffca_loglik(ctx, ctypes.byref(out)), "ffca_loglik")
+    return out.value
+
+
+def ffca_wiener(ctx, out_ptr: int) -> None:
+    _check(ctx, lib().ffca_wiener(ctx, ctypes.c_void_p(out_ptr)), "ffca_wiener")
+
+
+def ffca_sync(ctx) -> None:
+    _check(ctx, lib().ffca_sync(ctx), "ffca_sync")
+
+
+def ffca_inversion_count(ctx) -> int:
+    out = ctypes.c_ulonglong()
+    _check(ctx, lib().ffca_inversion_count(ctx, ctypes.byref(out)), "ffca_inversion_count")
+    return out.value
+
+
+def ffca_upload(ctx, y_host=0, v_host=0, lam_host=0, P_host=0) -> None:
+    _check(ctx, lib().ffca_upload(ctx, y_host or None, v_host or None, lam_host or None,
+                                  P_host or None), "ffca_upload")
+
+
+def ffca_download(ctx, v_host=0, lam_host=0, P_host=0) -> None:
+    _check(ctx, lib().ffca_download(ctx, v_host or None, lam_host or None, P_host or None),
+           "ffca_download")
+
+
+def ffca_destroy(ctx) -> None:
+    lib().ffca_destroy(ctx)
+
+
+def ffca_status_str(status: int) -> str:
+    return lib().ffca_status_str(status).decode()
+
+
+# ------------------------------------------------------------ torch wrapper
+def padded_ld(N: int) -> int:
+    """Smallest frame stride the library accepts (>= N, multiple of 4)."""
+    return (N + 3) // 4 * 4
+
+
+class FastFCA:
+    """FastFCA-AS estimation state on one GPU, borrowed from torch tensors.
+
+    y   [I, F, ld] complex64 (mixed precision) or complex128 (FP64), CUDA
+    v   [J, F, ld] float32 / float64 (matching y), updated in place
+    lam [F, J, I] float64, updated in place
+    P   [F, I, I] complex128, updated in place
+    N   frames actually used (default ld)
+    """
+
+    def __init__(self, y, v, lam, P, N: int | None = None, K: int = 1, stream=None):
+        import torch
+        if not y.is_cuda:
+            raise ValueError("FastFCA needs CUDA tensors")
+        if y.dtype == torch.complex64:
+            prec, vdt = FFCA_PREC_MIXED, torch.float32
+        elif y.dtype == torch.complex128:
+            prec, vdt = FFCA_PREC_FP64, torch.float64
+        else:
+            raise TypeError("y must be complex64 or complex128")
+        if v.dtype != vdt or lam.dtype != torch.float64 or P.dtype != torch.complex128:
+            raise TypeError("dtypes: v matches y's precision, lam float64, P complex128")
+        for t in (y, v, lam, P):
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+        I, F, ld = y.shape
+        J = v.shape[0]
+        if v.shape != (J, F, ld) or lam.shape != (F, J, I) or P.shape != (F, I, I):
+            raise ValueError("inconsistent shapes")
+        self.I, self.J, self.F, self.ld = I, J, F, ld
+        self.N = ld if N is None else int(N)
+        self.prec = prec
+        self.y, self.v, self.lam, self.P = y, v, lam, P
+        s = stream if stream is not None else torch.cuda.current_stream(y.device)
+        self.stream = s
+        d = ffca_desc(I=I, J=J, F=F, N=self.N, ld=ld, K=K, prec=prec,
+                      y=y.data_ptr(), v=v.data_ptr(), lambda_=lam.data_ptr(), P=P.data_ptr(),
+                      workspace=None, workspace_bytes=0, stream=s.cuda_stream)
+        nbytes = ffca_workspace_size(d)
+        if nbytes == 0 and F > 0:
+            raise FFCAError(1, "ffca_workspace_size (invalid or unsupported shape)")
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=y.device)
+        d.workspace = self.workspace.data_ptr()
+        d.workspace_bytes = nbytes
+        self.desc = d
+        self.ctx = ffca_init(d)
+
+    def iterate(self, iters: int, trace: bool = True):
+        return ffca_iterate(self.ctx, iters, trace)
+
+    def loglik(self) -> float:
+        return ffca_loglik(self.ctx)
+
+    def wiener(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.J, self.I, self.F, self.ld), dtype=self.y.dtype,
+                              device=self.y.device)
+        ffca_wiener(self.ctx, out.data_ptr())
+        return out
+
+    def sync(self):
+        ffca_sync(self.ctx)
+
+    def inversion_count(self) -> int:
+        return ffca_inversion_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ffca_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def to_device(problem_y, v, lam, P, prec: str = "mixed", device="cuda", ld: int | None = None):
+    """Copy numpy arrays (mic-planar, unpadded) into padded CUDA tensors of
+    the precision's types.  Returns (y, v, lam, P, N)."""
+    import torch
+    I, F, N = problem_y.shape
+    J = v.shape[0]
+    ld = padded_ld(N) if ld is None else ld
+    cdt, rdt = (torch.complex64, torch.float32) if prec == "mixed" else (torch.complex128, torch.float64)
+    yt = torch.zeros((I, F, ld), dtype=cdt)
+    yt[:, :, :N] = torch.from_numpy(np.ascontiguousarray(problem_y)).to(cdt)
+    vt = torch.ones((J, F, ld), dtype=rdt)
+    vt[:, :, :N] = torch.from_numpy(np.ascontiguousarray(v)).to(rdt)
+    return (yt.to(device), vt.to(device),
+            torch.from_numpy(np.ascontiguousarray(lam, dtype=np.float64)).to(device),
+            torch.from_numpy(np.ascontiguousarray(P, dtype=np.complex128)).to(device), N)
