@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""FastFCA-AS throughput on one GB300 (or N, one process per GPU).
+
+Workload (one step): the long-duration mixture I = J = 3 mics/sources,
+F = 513 bins, N = 20000 frames, complex64 storage, mixed precision (FP32
+per-point arithmetic with compensated reductions, FP64 P(f) solves and
+log-likelihood), 50 hybrid iterations with the L2 trace, then the Wiener
+filter.  Metric: TF-point-iterations per second = N F iterations / time.
+Inputs (y 246 MB, v 123 MB) exceed the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+independently seeded mixture (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1805_09498_gb300.synth import CONFIGS, make_problem  # noqa: E402
+
+METRIC = "FastFCA-AS TF-point-iters/s (FP32+FP64 vs FP64 plain) and HBM roofline frac"
+UNIT = "TF-point-iters/s"
+WORKLOAD = "long_mixed"
+CPU_SAMPLE_F = 16          # frequencies of the oracle's CPU sample
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _csrc_hash() -> str:
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_1805_09498_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for f in sorted(os.listdir(d)):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as fh:
+            t = json.load(fh)
+    except OSError:
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    if not k or t.get("csrc_sha") != _csrc_hash():
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples, kept for a [t0, t1] window."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, index: int):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100",
+                                       "-i", str(index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self, t0: float, t1: float):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        rows = []
+        for line in out.splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(c[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + c[0].split(".")[1]) if "." in c[0] else 0.0
+                rows.append((ts, float(c[2]), float(c[3]), c[6:10]))
+            except (ValueError, IndexError):
+                continue
+        win = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15] or rows[-3:]
+        if not win:
+            return None
+        reasons = sorted({self.NAMES[i] for r in win for i, s in enumerate(r[3]) if s == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in win), "sm_max_mhz": max(r[2] for r in win),
+                "reasons": reasons, "samples": len(win)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank, local = int(os.environ["RANK"]), int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, ws, local, dist
+
+
+def _max_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sample_freqs(F: int, S: int) -> np.ndarray:
+    return np.unique(np.linspace(0, F - 1, S).round().astype(int))
+
+
+# ---------------------------------------------------------------- ours
+def run_ours(args, cfg, rank, ws, local, dist):
+    import torch
+
+    from paper_1805_09498_gb300 import build as _build
+    from paper_1805_09498_gb300 import ffca
+    _build.build()
+    I, J, F, N, iters = cfg["I"], cfg["J"], cfg["F"], cfg["N"], cfg["iters"]
+    dev = torch.device("cuda", local)
+    p = make_problem(I, J, F, N, seed=rank, alpha=cfg["alpha"], kappa=cfg["kappa"])
+    yd, vd, lamd, Pd, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed", device=dev)
+    v_init, lam_init, P_init = vd.clone(), lamd.clone(), Pd.clone()
+    est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+    ld = yd.shape[2]
+    out = torch.empty((J, I, F, ld), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # accuracy leg input: the full estimation from the initial state
+    tr_acc = est.iterate(iters)
+    fs = _sample_freqs(F, CPU_SAMPLE_F)
+    gpu_state = (vd[:, fs, :N].double().cpu().numpy(), lamd[fs].cpu().numpy(), Pd[fs].cpu().numpy())
+
+    # the plain FP64 GPU form on the same mixture (a few iterations)
+    fp64 = None
+    if rank == 0:
+        y64, v64, l64, P64, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64", device=dev)
+        e64 = ffca.FastFCA(y64, v64, l64, P64, N=N)
+        e64.iterate(1, trace=False)
+        it64 = 5
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        e64.iterate(it64, trace=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        fp64 = {"value": N * F * it64 / (ms64 * 1e-3), "unit": UNIT, "iters_timed": it64,
+                "ms_per_iter": ms64 / it64}
+        e64.close()
+        del y64, v64, l64, P64
+        torch.cuda.empty_cache()
+
+    vd.copy_(v_init); lamd.copy_(lam_init); Pd.copy_(P_init)
+
+    def step():
+        est.iterate(iters)      # trace copied back: the step's D2H result
+        est.wiener(out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    kt = ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, False)
+    clk = clocks.stop(t0, t1)
+    ms_max = _max_over_ranks(ms, dist)
+    units_per_step = N * F * iters
+    value = ws * units_per_step * args.steps / (ms_max * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers
+    y_h = torch.empty(yd.shape, dtype=yd.dtype, pin_memory=True); y_h.copy_(yd)
+    v_h = torch.empty(vd.shape, dtype=vd.dtype, pin_memory=True); v_h.copy_(v_init)
+    l_h = torch.empty(lamd.shape, dtype=lamd.dtype, pin_memory=True); l_h.copy_(lam_init)
+    P_h = torch.empty(Pd.shape, dtype=Pd.dtype, pin_memory=True); P_h.copy_(P_init)
+    o_h = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+    vo_h = torch.empty_like(v_h, pin_memory=True)
+    lo_h = torch.empty_like(l_h, pin_memory=True)
+    Po_h = torch.empty_like(P_h, pin_memory=True)
+
+    def e2e_step():
+        ffca.ffca_upload(est.ctx, y_h.data_ptr(), v_h.data_ptr(), l_h.data_ptr(), P_h.data_ptr())
+        est.iterate(iters)
+        ffca.ffca_wiener_host(est.ctx, out.data_ptr(), o_h.data_ptr())
+        ffca.ffca_download(est.ctx, vo_h.data_ptr(), lo_h.data_ptr(), Po_h.data_ptr())
+
+    for _ in range(2):
+        e2e_step()
+    e2e_steps = max(3, min(args.steps, 20))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    h1 = time.perf_counter()
+    e2e_s = _max_over_ranks(h1 - h0, dist)
+    nbytes = lambda t: t.numel() * t.element_size()  # noqa: E731
+    e2e = {"value": ws * units_per_step * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes(y_h) + nbytes(v_h) + nbytes(l_h) + nbytes(P_h),
+           "d2h_bytes_per_step": nbytes(o_h) + nbytes(vo_h) + nbytes(lo_h) + nbytes(Po_h)
+           + 8 * (iters + 1)}
+    est.close()
+
+    if rank != 0:
+        return None
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / mean duration
+    peaks, peak_src = _peaks()
+    c, r = 8, 4
+    bytes_per_tf = {"estep": I * c + 2 * J * r, "wcov": I * c + J * r}
+    kernels = {}
+    for k, bpt in bytes_per_tf.items():
+        kms, kn = kt[k]
+        if kn:
+            avg = kms / kn
+            kernels[k] = {"launches": kn, "avg_us": avg * 1e3, "bytes_per_launch": bpt * N * F,
+                          "achieved_gbs": bpt * N * F / (avg * 1e-3) / 1e9}
+    dom = max(kernels, key=lambda k: kt[k][0])
+    kname = {"estep": "k_estep", "wcov": "k_wcov"}[dom]
+    roof = {"bound": "hbm", "kernel": kname, "achieved": kernels[dom]["achieved_gbs"],
+            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": kernels[dom]["achieved_gbs"] / peaks["hbm_gbs"],
+            "traffic": _ncu_traffic(kname), "peak_source": peak_src}
+
+    cpu = None
+    if ws == 1:
+        cpu = cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_acc)
+
+    launches = int(sum(n for _, n in kt.values()))
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: I={I} J={J} F={F} N={N}, c64 storage, mixed "
+                               f"FP32/FP64, {iters} iterations + Wiener per step",
+                   "iters_per_step": iters, "l2": "inputs 369 MB > 129 MB L2 (no flush)",
+                   "state": "parameters carried from step to step",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": roof, "kernels": kernels,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps,
+        "clocks": clk, "fp64_gpu": fp64,
+        "speedup_mixed_vs_fp64_gpu": (value / ws / fp64["value"]) if fp64 else None,
+    }
+
+
+def cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_gpu):
+    """The FP64 oracle on a bounded sample of the workload (CPU_SAMPLE_F
+    frequencies, all frames, all iterations), timed on the host, and the
+    GPU result's error against it on those frequencies."""
+    from oracle import fastfca_as as ffa
+    from oracle.fastfca_as import OpCounter
+    iters, N = cfg["iters"], cfg["N"]
+    t = time.perf_counter()
+    v, lam, P, tr = ffa.iterate(p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs], iters,
+                                counter=OpCounter())
+    dt = time.perf_counter() - t
+
+    def relerr(a, b, ax):
+        a = np.moveaxis(a, ax, 0).reshape(len(fs), -1)
+        b = np.moveaxis(b, ax, 0).reshape(len(fs), -1)
+        return float(np.max(np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)))
+
+    vg, lg, Pg = gpu_state
+    err = {"v": relerr(vg, v, 1), "lambda": relerr(lg, lam, 0), "P": relerr(Pg, P, 0),
+           "loglik_per_point": abs(ffa.loglik(p.y[:, fs], vg, lg, Pg) - tr[-1]) / (len(fs) * N),
+           "measure": f"after {iters} iterations from the same initial state, on the sampled "
+                      "frequencies; normwise relative error per frequency (max)"}
+    return {"value": len(fs) * N * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(fs)} of {cfg['F']} frequencies x {N} frames x {iters} iterations "
+                      "(numpy FP64, one thread)", "seconds": dt, "error_vs_oracle": err}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, cfg, rank, ws):
+    """The FP64 oracle on the host cores as the reference arm: each step is one
+    hybrid iteration with its L2 on a sample of the workload's frequencies."""
+    if rank != 0:
+        return None
+    from oracle import fastfca_as as ffa
+    from oracle.fastfca_as import OpCounter
+    I, J, F, N = cfg["I"], cfg["J"], cfg["F"], cfg["N"]
+    p = make_problem(I, J, F, N, seed=0, alpha=cfg["alpha"], kappa=cfg["kappa"])
+    fs = _sample_freqs(F, CPU_SAMPLE_F)
+    y, v, lam, P = p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs]
+    cnt = OpCounter()
+
+    def step(v, lam, P):
+        ffa.loglik(y, v, lam, P)
+        return ffa.hybrid_iteration(y, v, lam, P, 1, cnt)
+
+    for _ in range(args.warmup):
+        v, lam, P = step(v, lam, P)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        v, lam, P = step(v, lam, P)
+    dt = time.perf_counter() - t
+    value = len(fs) * N * args.steps / dt
+    sample = (f"{len(fs)} of {F} frequencies x {N} frames, one hybrid iteration + L2 per step "
+              "(numpy FP64, one thread)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: I={I} J={J} F={F} N={N}", "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    args = ap.parse_args()
+    cfg = CONFIGS[WORKLOAD]
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        res = run_reference(args, cfg, rank, ws)
+    else:
+        rank, ws, local, dist = _dist()
+        res = run_ours(args, cfg, rank, ws, local, dist)
+        if dist is not None:
+            dist.destroy_process_group()
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -141,6 +141,27 @@ ffca_status ffca_upload(ffca_ctx* ctx, const void* y_host, const void* v_host,
                         const double* lambda_host, const double* P_host);
 ffca_status ffca_download(ffca_ctx* ctx, void* v_host, double* lambda_host, double* P_host);
 
+/* Multichannel Wiener filter for host-memory callers: runs ffca_wiener into
+ * the caller's device buffer out_dev ([J][I][F][ld] complex) and copies it to
+ * out_host (same layout), then synchronises. */
+ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
+
+/* Kernel kinds reported by ffca_timing_read. */
+#define FFCA_KERNEL_PREP 0      /* per-frequency ln|det P|^2 and P^{-H} */
+#define FFCA_KERNEL_ESTEP 1     /* pass A with the M-step */
+#define FFCA_KERNEL_LOGLIK 2    /* pass A, log-likelihood only */
+#define FFCA_KERNEL_WCOV 3      /* pass B with the fixed-point update of P */
+#define FFCA_KERNEL_WIENER 4
+#define FFCA_KERNEL_KINDS 5
+
+/* Profiling: while enabled, each kernel the context launches is bracketed by
+ * two CUDA events on the context stream.  ffca_timing_read synchronises,
+ * writes per kind the summed device milliseconds (ms) and the number of
+ * launches (launches; counted whether or not timing is enabled) since the
+ * last read, and resets both.  Either output may be NULL. */
+ffca_status ffca_timing_enable(ffca_ctx* ctx, int enable);
+ffca_status ffca_timing_read(ffca_ctx* ctx, double* ms, unsigned long long* launches);
+
 /* Release the context (host memory only; the device arrays stay the caller's). */
 void ffca_destroy(ffca_ctx* ctx);
 

@@ -98,6 +98,11 @@ ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
 
 }  // namespace
 
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t start, stop;
+};
+
 struct ffca_ctx {
   ffca_desc d;
   const FastKernels* kern;
@@ -109,6 +114,11 @@ struct ffca_ctx {
   unsigned* gcntB;
   unsigned long long* ops;
   int err_f;
+  // profiling
+  int timing;
+  unsigned long long launches[FFCA_KERNEL_KINDS];
+  TimedLaunch* timed;
+  size_t ntimed, captimed;
 };
 
 namespace {
@@ -153,17 +163,47 @@ FastArgs pass_b_args(const ffca_ctx* c) {
   return a;
 }
 
-ffca_status launch(const void* fn, int grid, int block, FastArgs& a, cudaStream_t s) {
+ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, FastArgs& a) {
   void* args[] = {&a};
-  if (cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, s) != cudaSuccess) return FFCA_ERR_CUDA;
+  TimedLaunch* t = nullptr;
+  if (c->timing) {
+    if (c->ntimed == c->captimed) {
+      size_t cap = c->captimed ? 2 * c->captimed : 256;
+      void* p = std::realloc(c->timed, cap * sizeof(TimedLaunch));
+      if (!p) return FFCA_ERR_INTERNAL;
+      c->timed = static_cast<TimedLaunch*>(p);
+      c->captimed = cap;
+    }
+    t = &c->timed[c->ntimed];
+    t->kind = kind;
+    if (cudaEventCreate(&t->start) != cudaSuccess) return FFCA_ERR_CUDA;
+    if (cudaEventCreate(&t->stop) != cudaSuccess) {
+      cudaEventDestroy(t->start);
+      return FFCA_ERR_CUDA;
+    }
+    ++c->ntimed;
+    if (cudaEventRecord(t->start, c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
+  }
+  if (cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, c->stream) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  ++c->launches[kind];
+  if (t && cudaEventRecord(t->stop, c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
   return FFCA_OK;
 }
 
-ffca_status launch_prep(const ffca_ctx* c, bool want_pinv) {
+ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   FastArgs a = base_args(c);
   a.pinvH = want_pinv ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
   const int grid = (c->d.F + 127) / 128;
-  return launch(c->kern->prep, grid, 128, a, c->stream);
+  return launch(c, FFCA_KERNEL_PREP, c->kern->prep, grid, 128, a);
+}
+
+void drop_timed(ffca_ctx* c) {
+  for (size_t k = 0; k < c->ntimed; ++k) {
+    cudaEventDestroy(c->timed[k].start);
+    cudaEventDestroy(c->timed[k].stop);
+  }
+  c->ntimed = 0;
 }
 
 ffca_status read_status(ffca_ctx* c) {
@@ -238,12 +278,15 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
     const int slot = t % kTraceCap;
     if (t < iters) {
       FastArgs a = pass_a_args(c, slot);
-      if ((st = launch(c->kern->estep_update, a.part.nblocks, kBlock, a, c->stream)) != FFCA_OK) return st;
+      if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, a.part.nblocks, kBlock, a)) != FFCA_OK)
+        return st;
       FastArgs b = pass_b_args(c);
-      if ((st = launch(c->kern->wcov, b.part.nblocks, kBlock, b, c->stream)) != FFCA_OK) return st;
+      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, b.part.nblocks, kBlock, b)) != FFCA_OK)
+        return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
-      if ((st = launch(c->kern->estep_eval, a.part.nblocks, kBlock, a, c->stream)) != FFCA_OK) return st;
+      if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kBlock, a)) != FFCA_OK)
+        return st;
     }
     if (ll_trace && (slot == kTraceCap - 1 || t == iters)) {
       const int n = t - flushed + 1;
@@ -267,7 +310,8 @@ ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
   ffca_status st = launch_prep(c, false);
   if (st != FFCA_OK) return st;
   FastArgs a = pass_a_args(c, 0);
-  if ((st = launch(c->kern->estep_eval, a.part.nblocks, kBlock, a, c->stream)) != FFCA_OK) return st;
+  if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kBlock, a)) != FFCA_OK)
+    return st;
   if (cudaMemcpyAsync(ll, a.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
     return FFCA_ERR_CUDA;
   return read_status(c);
@@ -283,7 +327,43 @@ ffca_status ffca_wiener(ffca_ctx* c, void* out) {
   a.part = c->plan.pW;
   a.pinvH = reinterpret_cast<double*>(c->ws + c->plan.off_pinvH);
   a.out = out;
-  return launch(c->kern->wiener, a.part.nblocks, kBlock, a, c->stream);
+  return launch(c, FFCA_KERNEL_WIENER, c->kern->wiener, a.part.nblocks, kBlock, a);
+}
+
+ffca_status ffca_wiener_host(ffca_ctx* c, void* out_dev, void* out_host) {
+  if (!c || !out_host) return FFCA_ERR_ARG;
+  ffca_status st = ffca_wiener(c, out_dev);
+  if (st != FFCA_OK) return st;
+  const size_t rsz = c->d.prec == FFCA_PREC_FP64 ? 8 : 4;
+  const size_t bytes = (size_t)c->d.J * c->d.I * c->d.F * c->d.ld * 2 * rsz;
+  if (bytes && cudaMemcpyAsync(out_host, out_dev, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return FFCA_ERR_CUDA;
+  return read_status(c);
+}
+
+ffca_status ffca_timing_enable(ffca_ctx* c, int enable) {
+  if (!c) return FFCA_ERR_ARG;
+  c->timing = enable ? 1 : 0;
+  return FFCA_OK;
+}
+
+ffca_status ffca_timing_read(ffca_ctx* c, double* ms, unsigned long long* launches) {
+  if (!c) return FFCA_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
+  double tot[FFCA_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  ffca_status st = FFCA_OK;
+  for (size_t k = 0; k < c->ntimed; ++k) {
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, c->timed[k].start, c->timed[k].stop) != cudaSuccess) st = FFCA_ERR_CUDA;
+    tot[c->timed[k].kind] += e;
+  }
+  drop_timed(c);
+  for (int k = 0; k < FFCA_KERNEL_KINDS; ++k) {
+    if (ms) ms[k] = tot[k];
+    if (launches) launches[k] = c->launches[k];
+    c->launches[k] = 0;
+  }
+  return st;
 }
 
 ffca_status ffca_sync(ffca_ctx* c) {
@@ -340,7 +420,12 @@ ffca_status ffca_download(ffca_ctx* c, void* v_host, double* lam_host, double* P
   return cudaStreamSynchronize(c->stream) == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
 }
 
-void ffca_destroy(ffca_ctx* c) { std::free(c); }
+void ffca_destroy(ffca_ctx* c) {
+  if (!c) return;
+  drop_timed(c);
+  std::free(c->timed);
+  std::free(c);
+}
 
 const char* ffca_status_str(ffca_status s) {
   switch (s) {

@@ -74,6 +74,9 @@ def lib() -> ctypes.CDLL:
         "ffca_inversion_count": (ci, [vp, P(ctypes.c_ulonglong)]),
         "ffca_upload": (ci, [vp, vp, vp, vp, vp]),
         "ffca_download": (ci, [vp, vp, vp, vp]),
+        "ffca_wiener_host": (ci, [vp, vp, vp]),
+        "ffca_timing_enable": (ci, [vp, ci]),
+        "ffca_timing_read": (ci, [vp, dp, P(ctypes.c_ulonglong)]),
         "ffca_destroy": (None, [vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
     }
@@ -149,6 +152,26 @@ def ffca_upload(ctx, y_host=0, v_host=0, lam_host=0, P_host=0) -> None:
 def ffca_download(ctx, v_host=0, lam_host=0, P_host=0) -> None:
     _check(ctx, lib().ffca_download(ctx, v_host or None, lam_host or None, P_host or None),
            "ffca_download")
+
+
+def ffca_wiener_host(ctx, out_dev_ptr: int, out_host_ptr: int) -> None:
+    _check(ctx, lib().ffca_wiener_host(ctx, ctypes.c_void_p(out_dev_ptr),
+                                       ctypes.c_void_p(out_host_ptr)), "ffca_wiener_host")
+
+
+KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener")
+
+
+def ffca_timing_enable(ctx, enable: bool) -> None:
+    _check(ctx, lib().ffca_timing_enable(ctx, int(bool(enable))), "ffca_timing_enable")
+
+
+def ffca_timing_read(ctx):
+    """{kind: (device ms summed, launches)} since the last read."""
+    ms = (ctypes.c_double * len(KERNEL_KINDS))()
+    n = (ctypes.c_ulonglong * len(KERNEL_KINDS))()
+    _check(ctx, lib().ffca_timing_read(ctx, ms, n), "ffca_timing_read")
+    return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def ffca_destroy(ctx) -> None:

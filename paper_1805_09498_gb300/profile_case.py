@@ -1,0 +1,40 @@
+"""A fixed, small FastFCA-AS run for kernel profiling (e.g. under ncu).
+
+    python -m paper_1805_09498_gb300.profile_case [--N 8000] [--iters 3] [--prec mixed]
+
+Default: I = J = 3, F = 513, N = 8000 frames (y 98 MB + v 49 MB in the mixed
+path: larger than the 129 MB L2 together, a few hundred MB on the device),
+`iters` hybrid iterations followed by one Wiener pass.
+"""
+from __future__ import annotations
+
+import argparse
+
+from . import build as _build
+from . import ffca
+from .synth import make_problem
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--I", type=int, default=3)
+    ap.add_argument("--J", type=int, default=3)
+    ap.add_argument("--F", type=int, default=513)
+    ap.add_argument("--N", type=int, default=8000)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--prec", choices=("mixed", "fp64"), default="mixed")
+    a = ap.parse_args()
+    import torch
+    _build.build()
+    p = make_problem(a.I, a.J, a.F, a.N, seed=0)
+    yd, vd, lamd, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec=a.prec)
+    est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+    tr = est.iterate(a.iters)
+    est.wiener()
+    torch.cuda.synchronize()
+    est.close()
+    print("profile case done; L2 trace:", tr[0], "->", tr[-1])
+
+
+if __name__ == "__main__":
+    main()
