@@ -162,6 +162,28 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
 ffca_status ffca_timing_enable(ffca_ctx* ctx, int enable);
 ffca_status ffca_timing_read(ffca_ctx* ctx, double* ms, unsigned long long* launches);
 
+/* Hybrid iterations for callers that cannot allocate any memory (the paper
+ * has no counterpart; this is an interface for embedding).  A real-time
+ * audio thread must not call cudaMalloc, which can block and synchronise the
+ * device, and a plugin or a system with a fixed memory map may have no
+ * allocator at hand.  This call allocates nothing, neither device nor host
+ * memory: the context lives on its stack and its scratch is a static array of
+ * FFCA_NOALLOC_SCRATCH_BYTES bytes in the library image, which every GPU that
+ * loads libffca.so keeps until the process exits.
+ *  - desc: as for ffca_init; desc->workspace and desc->workspace_bytes are
+ *    ignored.  Problems whose workspace (ffca_workspace_size) exceeds
+ *    FFCA_NOALLOC_SCRATCH_BYTES are rejected with FFCA_ERR_ARG.
+ *  - iters, ll_trace: as for ffca_iterate.  The call always synchronises
+ *    desc->stream and returns the device status.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the one array, and each starts by clearing it.  Calls
+ *    that overlap on the GPU (other threads, other streams) race; serialise
+ *    them. */
+#define FFCA_NOALLOC_SCRATCH_BYTES (8u << 20)
+ffca_status ffca_iterate_noalloc(const ffca_desc* desc, int iters, double* ll_trace);
+
 /* Release the context (host memory only; the device arrays stay the caller's). */
 void ffca_destroy(ffca_ctx* ctx);
 

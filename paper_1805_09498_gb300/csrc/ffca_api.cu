@@ -2,6 +2,7 @@
 // carving and the per-iteration launch sequence.  See include/ffca.h.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -442,3 +443,81 @@ const char* ffca_status_str(ffca_status s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Iteration without any allocation.
+//
+// Some callers cannot allocate device memory at the point where they run the
+// estimation: a real-time audio thread (hearing aid, online enhancement) must
+// not call cudaMalloc, which can block and synchronise the device; a plugin
+// inside a host application may have no allocator of its own; a system with a
+// fixed, pre-planned memory map may forbid late allocations.  For them,
+// ffca_iterate_noalloc takes its scratch (partial sums, arrival counters,
+// status word, trace) from the array below, which is part of the library
+// image: every GPU that loads the library holds it until the process exits.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = FFCA_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device.  In host
+// code the symbol itself is only a host-side stand-in, never a device address.
+std::atomic<void*> g_noalloc_addr[kMaxDevices];
+
+ffca_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FFCA_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return FFCA_ERR_UNSUPPORTED;
+  void* p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FFCA_ERR_CUDA;
+    g_noalloc_addr[dev].store(p, std::memory_order_release);
+  }
+  *out = p;
+  return FFCA_OK;
+}
+
+}  // namespace
+
+extern "C" ffca_status ffca_iterate_noalloc(const ffca_desc* d, int iters, double* ll_trace) {
+  if (iters < 0) return FFCA_ERR_ARG;
+  ffca_status st = check_shape(d);
+  if (st != FFCA_OK) return st;
+  const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
+  if (!k) return FFCA_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  if ((st = noalloc_scratch(&scratch)) != FFCA_OK) return st;
+  ffca_desc dd = *d;
+  dd.workspace = scratch;
+  dd.workspace_bytes = kNoallocScratchBytes;
+  if ((st = check_pointers(&dd)) != FFCA_OK) return st;
+  Plan p;
+  if ((st = make_plan(&dd, k, &p)) != FFCA_OK) return st;
+  if (p.bytes > kNoallocScratchBytes) return FFCA_ERR_ARG;  // problem too large for the fixed scratch
+  // The context lives on this call's stack; nothing is allocated.
+  ffca_ctx c;
+  std::memset(&c, 0, sizeof(c));
+  c.d = dd;
+  c.kern = k;
+  c.plan = p;
+  c.stream = static_cast<cudaStream_t>(dd.stream);
+  c.ws = static_cast<char*>(scratch);
+  c.status = reinterpret_cast<unsigned*>(c.ws);
+  c.gcntA = reinterpret_cast<unsigned*>(c.ws + 16);
+  c.gcntB = reinterpret_cast<unsigned*>(c.ws + 20);
+  c.ops = reinterpret_cast<unsigned long long*>(c.ws + 32);
+  c.err_f = -1;
+  if (dd.F == 0) {
+    if (ll_trace)
+      for (int t = 0; t <= iters; ++t) ll_trace[t] = 0.0;
+    return FFCA_OK;
+  }
+  // The previous call left its partials, counters and status in the shared
+  // scratch: the counters and the status word must start at zero.
+  if (cudaMemsetAsync(c.ws, 0, p.bytes, c.stream) != cudaSuccess) return FFCA_ERR_CUDA;
+  st = ffca_iterate(&c, iters, ll_trace);
+  if (st != FFCA_OK) return st;
+  return read_status(&c);
+}

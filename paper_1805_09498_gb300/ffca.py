@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         "ffca_wiener_host": (ci, [vp, vp, vp]),
         "ffca_timing_enable": (ci, [vp, ci]),
         "ffca_timing_read": (ci, [vp, dp, P(ctypes.c_ulonglong)]),
+        "ffca_iterate_noalloc": (ci, [P(ffca_desc), ci, dp]),
         "ffca_destroy": (None, [vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
     }
@@ -172,6 +173,16 @@ def ffca_timing_read(ctx):
     n = (ctypes.c_ulonglong * len(KERNEL_KINDS))()
     _check(ctx, lib().ffca_timing_read(ctx, ms, n), "ffca_timing_read")
     return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def ffca_iterate_noalloc(desc: ffca_desc, iters: int):
+    """Allocation-free iterations (static library scratch); returns the L2 trace."""
+    buf = np.zeros(iters + 1, dtype=np.float64)
+    st = lib().ffca_iterate_noalloc(ctypes.byref(desc), iters,
+                                    buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != FFCA_OK:
+        raise FFCAError(st, "ffca_iterate_noalloc")
+    return buf
 
 
 def ffca_destroy(ctx) -> None:
