@@ -102,7 +102,7 @@ ffca_status ffca_init(ffca_ctx** out, const ffca_desc* desc);
 
 /* Run `iters` >= 0 hybrid iterations (Sec. 4.4) in place on (v, lambda, P).
  * Each iteration: pass A (E-step, Eq. updatev, Eq. Lambdaupdate, L2 of the
- * entering state), then pass B (V_i of Eq. FPI) with the per-frequency FP64
+ * entering state), pass B (V_i of Eq. FPI), then the per-frequency FP64
  * fixed-point update of P (K sweeps, (I+1)K small inversions per frequency).
  * ll_trace: host array of iters + 1 doubles or NULL.  When given, ll_trace[t]
  * receives L2 (Eq. L2, natural log, including -I ln(pi) per point) of the
@@ -150,9 +150,10 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
 #define FFCA_KERNEL_PREP 0      /* per-frequency ln|det P|^2 and P^{-H} */
 #define FFCA_KERNEL_ESTEP 1     /* pass A with the M-step */
 #define FFCA_KERNEL_LOGLIK 2    /* pass A, log-likelihood only */
-#define FFCA_KERNEL_WCOV 3      /* pass B with the fixed-point update of P */
+#define FFCA_KERNEL_WCOV 3      /* pass B: weighted covariance partial sums */
 #define FFCA_KERNEL_WIENER 4
-#define FFCA_KERNEL_KINDS 5
+#define FFCA_KERNEL_PSOLVE 5    /* per-frequency FP64 fixed-point update of P */
+#define FFCA_KERNEL_KINDS 6
 
 /* Profiling: while enabled, each kernel the context launches is bracketed by
  * two CUDA events on the context stream.  ffca_timing_read synchronises,

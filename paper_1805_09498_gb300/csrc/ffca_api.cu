@@ -284,6 +284,9 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
       FastArgs b = pass_b_args(c);
       if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, b.part.nblocks, kBlock, b)) != FFCA_OK)
         return st;
+      const int gs = (c->d.F + kSolveWarps - 1) / kSolveWarps;
+      if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, gs, 32 * kSolveWarps, b)) != FFCA_OK)
+        return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
       if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kBlock, a)) != FFCA_OK)
@@ -351,7 +354,7 @@ ffca_status ffca_timing_enable(ffca_ctx* c, int enable) {
 ffca_status ffca_timing_read(ffca_ctx* c, double* ms, unsigned long long* launches) {
   if (!c) return FFCA_ERR_ARG;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
-  double tot[FFCA_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  double tot[FFCA_KERNEL_KINDS] = {};
   ffca_status st = FFCA_OK;
   for (size_t k = 0; k < c->ntimed; ++k) {
     float e = 0.f;

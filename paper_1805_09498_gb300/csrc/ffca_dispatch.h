@@ -7,7 +7,8 @@ namespace ffca {
 struct FastKernels {
   const void* estep_update;  // pass A with the M-step
   const void* estep_eval;    // pass A, log-likelihood only
-  const void* wcov;          // pass B with the fixed-point update of P
+  const void* wcov;          // pass B: weighted covariance partial sums
+  const void* psolve;        // per-frequency fixed-point update of P
   const void* wiener;
   const void* prep;          // per-frequency ln|det P|^2 and P^{-H}
 };

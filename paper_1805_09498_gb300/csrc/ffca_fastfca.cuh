@@ -8,7 +8,8 @@
 //             The last CTA to finish a frequency finalises Lambda(f); the
 //             last frequency finalises the scalar log-likelihood.
 //   k_wcov    pass B: V_i(f) = (1/N) sum_n y y^H / sigma_i with the new v and
-//             Lambda (Eq. FPI); the last CTA of a frequency runs the FP64
+//             Lambda (Eq. FPI), reduced over n into per-frequency slots.
+//   k_psolve  per frequency (one warp): V_i from the slots, then the FP64
 //             fixed-point update of P(f) (K sweeps) and ln|det P(f)|^2.
 //   k_wiener  x^_j = P^{-H} diag(v_j lambda_j / sigma) P^H y (Eq. MMSE0).
 //   k_prep    per frequency: ln|det P|^2 and P^{-H} (FP64).
@@ -287,7 +288,7 @@ __device__ inline void unpack_herm(const double* src, cpx<double> (&V)[I][I]) {
 template <int I>
 __device__ void p_update(const FastArgs& a, int f, const double* sV, double (*sPn)[I][2],
                          double (*sQ)[I][2], int* sbad) {
-  const int lane = threadIdx.x;  // called by warp 0 only
+  const int lane = threadIdx.x & 31;  // called by one full warp
   if (lane == 0) *sbad = 0;
   if (lane < I * I) {
     sPn[lane / I][lane % I][0] = a.P[((size_t)f * I * I + lane) * 2];
@@ -357,10 +358,6 @@ __global__ void __launch_bounds__(kBlock) k_wcov(FastArgs a) {
 
   __shared__ typename BlockReduce<T, NV>::Smem red;
   __shared__ double sLam[J][I];
-  __shared__ double sV[NV];
-  __shared__ double sPn[I][I][2];
-  __shared__ double sQ[I][I][2];
-  __shared__ int sflag, sbad;
 
   const Partition pt = a.part;
   const long long total = (long long)pt.F * pt.Uf;
@@ -383,9 +380,11 @@ __global__ void __launch_bounds__(kBlock) k_wcov(FastArgs a) {
 #pragma unroll
       for (int i = 0; i < I; ++i) lam[j][i] = (T)sLam[j][i];
 
-    Acc<T> acc[NV];
+    // Per-thread sums over this segment's frames (a few dozen at most at
+    // full size); the tree across threads below is compensated.
+    T acc[NV];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t].zero();
+    for (int t = 0; t < NV; ++t) acc[t] = (T)0;
 
     for (int kb = k0 + threadIdx.x; kb < k1; kb += kBlock * kUnits) {
       VY yu[kUnits][I];
@@ -400,9 +399,6 @@ __global__ void __launch_bounds__(kBlock) k_wcov(FastArgs a) {
           for (int j = 0; j < J; ++j) vu[q][j] = v[((size_t)j * pt.F + f) * row + k];
         }
       }
-      T grp[NV];
-#pragma unroll
-      for (int t = 0; t < NV; ++t) grp[t] = (T)0;
 #pragma unroll
       for (int q = 0; q < kUnits; ++q) {
         const int k = kb + q * kBlock;
@@ -440,35 +436,44 @@ __global__ void __launch_bounds__(kBlock) k_wcov(FastArgs a) {
 #pragma unroll
           for (int i = 0; i < I; ++i)
 #pragma unroll
-            for (int m = 0; m < I2; ++m) grp[i * I2 + m] = fma(w[i], pk[m], grp[i * I2 + m]);
+            for (int m = 0; m < I2; ++m) acc[i * I2 + m] = fma(w[i], pk[m], acc[i * I2 + m]);
         }
       }
-#pragma unroll
-      for (int t = 0; t < NV; ++t) acc[t].add(grp[t]);
     }
 
-    T hi[NV], lo[NV];
+    T lo[NV];
 #pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      hi[t] = acc[t].value_hi();
-      lo[t] = acc[t].value_lo();
-    }
+    for (int t = 0; t < NV; ++t) lo[t] = (T)0;
     const int slot = (int)blockIdx.x - pt.first_block(f);
-    BlockReduce<T, NV>::run(hi, lo, red, a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
-
-    if (arrive_last(a.cnt + f, (unsigned)pt.nslots(f), &sflag)) {
-      const int ns = pt.nslots(f);
-      for (int t = threadIdx.x; t < NV; t += kBlock) {
-        const double s = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, t) / a.N;
-        if (!isfinite(s)) raise_status(a.status, kDevNonfinite, f);
-        sV[t] = s;
-      }
-      __syncthreads();
-      if (threadIdx.x < 32) p_update<I>(a, f, sV, sPn, sQ, &sbad);
-    }
-    __syncthreads();
+    BlockReduce<T, NV>::run(acc, lo, red, a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
     u += k1 - k0;
   }
+}
+
+// -------------------------------------------------------------- P solve
+// One warp per frequency: sum pass B's slots into V_i (FP64, slot order),
+// then the fixed-point update of P(f) and ln|det P(f)|^2.
+constexpr int kSolveWarps = 4;
+
+template <int I>
+__global__ void __launch_bounds__(32 * kSolveWarps) k_psolve(FastArgs a) {
+  constexpr int NV = I * I * I;
+  __shared__ double sV[kSolveWarps][NV];
+  __shared__ double sPn[kSolveWarps][I][I][2];
+  __shared__ double sQ[kSolveWarps][I][I][2];
+  __shared__ int sbad[kSolveWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kSolveWarps + warp;
+  if (f >= a.F) return;  // whole warps only
+  const Partition pt = a.part;
+  const int ns = pt.nslots(f);
+  for (int t = lane; t < NV; t += 32) {
+    const double s = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, t) / a.N;
+    if (!isfinite(s)) raise_status(a.status, kDevNonfinite, f);
+    sV[warp][t] = s;
+  }
+  __syncwarp();
+  p_update<I>(a, f, sV[warp], sPn[warp], sQ[warp], &sbad[warp]);
 }
 
 // -------------------------------------------------------------- prep
