@@ -190,6 +190,11 @@ void ffca_destroy(ffca_ctx* ctx);
 
 const char* ffca_status_str(ffca_status s);
 
+/* Text of the last CUDA call the library saw fail in the calling thread
+ * ("" if none): which call, and CUDA's message.  Valid until the next
+ * failure in that thread. */
+const char* ffca_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,11 +5,12 @@
 #include <atomic>
 #include <cstdint>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 
 #include "ffca.h"
 #include "ffca_dispatch.h"
-#include "ffca_fastfca.cuh"
+#include "ffca_stream.cuh"
 
 using namespace ffca;
 
@@ -39,6 +40,15 @@ const FastKernels* fast_kernels(int prec, int I, int J) {
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// Text of the last failed CUDA call in this thread (for ffca_last_error).
+thread_local char g_last_error[256] = "";
+
+bool cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return true;
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+  return false;
+}
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Plan {
@@ -66,17 +76,38 @@ ffca_status check_pointers(const ffca_desc* d) {
 
 ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
   int dev = 0, nsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FFCA_ERR_CUDA;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+  if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return FFCA_ERR_CUDA;
+  if (!cuda_ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute"))
     return FFCA_ERR_CUDA;
+  // the streaming passes take more than the default 48 KB of dynamic shared memory
+  for (const void* fn : {k->estep_update, k->estep_eval, k->wcov})
+    if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->stream_smem),
+                 "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"))
+      return FFCA_ERR_CUDA;
   int occA = 0, occB = 0, occW = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k->estep_update, kBlock, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k->wcov, kBlock, 0) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occW, k->wiener, kBlock, 0) != cudaSuccess)
+  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k->estep_update, kStreamThreads,
+                                                             k->stream_smem), "occupancy(pass A)") ||
+      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k->wcov, kStreamThreads, k->stream_smem),
+               "occupancy(pass B)") ||
+      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occW, k->wiener, kBlock, 0), "occupancy(Wiener)"))
     return FFCA_ERR_CUDA;
-  if (occA < 1 || occB < 1 || occW < 1) return FFCA_ERR_INTERNAL;
+  if (occA < 1 || occB < 1 || occW < 1) {
+    cudaFuncAttributes fa;
+    std::memset(&fa, 0, sizeof(fa));
+    cudaFuncGetAttributes(&fa, occA < 1 ? k->estep_update : k->wcov);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    std::snprintf(g_last_error, sizeof(g_last_error),
+                  "no resident CTA: occupancy A=%d B=%d W=%d; regs=%d maxThreads=%d static=%zu "
+                  "maxDynamic=%d requested=%d optin=%d",
+                  occA, occB, occW, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
+                  fa.maxDynamicSharedSizeBytes, k->stream_smem, optin);
+    return FFCA_ERR_INTERNAL;
+  }
   const int FU = d->prec == FFCA_PREC_FP64 ? 1 : 2;
-  const int Uf = (d->N + FU - 1) / FU;
+  // vector units per frequency, rounded up to even so that every tile of v
+  // starts on a 16-byte boundary (ld % 4 == 0 keeps this inside the row)
+  const int Uf = ((d->N + FU - 1) / FU + 1) / 2 * 2;
   const int F = d->F > 0 ? d->F : 1;
   p->pA = make_partition(F, Uf, nsm * occA);
   p->pB = make_partition(F, Uf, nsm * occB);
@@ -164,7 +195,8 @@ FastArgs pass_b_args(const ffca_ctx* c) {
   return a;
 }
 
-ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, FastArgs& a) {
+ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, FastArgs& a,
+                   size_t smem = 0) {
   void* args[] = {&a};
   TimedLaunch* t = nullptr;
   if (c->timing) {
@@ -185,7 +217,7 @@ ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, F
     ++c->ntimed;
     if (cudaEventRecord(t->start, c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
   }
-  if (cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, c->stream) != cudaSuccess)
+  if (!cuda_ok(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, c->stream), "cudaLaunchKernel"))
     return FFCA_ERR_CUDA;
   ++c->launches[kind];
   if (t && cudaEventRecord(t->stop, c->stream) != cudaSuccess) return FFCA_ERR_CUDA;
@@ -279,17 +311,20 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
     const int slot = t % kTraceCap;
     if (t < iters) {
       FastArgs a = pass_a_args(c, slot);
-      if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, a.part.nblocks, kBlock, a)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, a.part.nblocks, kStreamThreads, a,
+                      c->kern->stream_smem)) != FFCA_OK)
         return st;
       FastArgs b = pass_b_args(c);
-      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, b.part.nblocks, kBlock, b)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, b.part.nblocks, kStreamThreads, b,
+                      c->kern->stream_smem)) != FFCA_OK)
         return st;
       const int gs = (c->d.F + kSolveWarps - 1) / kSolveWarps;
       if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, gs, 32 * kSolveWarps, b)) != FFCA_OK)
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
-      if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kBlock, a)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kStreamThreads, a,
+                      c->kern->stream_smem)) != FFCA_OK)
         return st;
     }
     if (ll_trace && (slot == kTraceCap - 1 || t == iters)) {
@@ -314,7 +349,8 @@ ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
   ffca_status st = launch_prep(c, false);
   if (st != FFCA_OK) return st;
   FastArgs a = pass_a_args(c, 0);
-  if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kBlock, a)) != FFCA_OK)
+  if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kStreamThreads, a,
+                      c->kern->stream_smem)) != FFCA_OK)
     return st;
   if (cudaMemcpyAsync(ll, a.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
     return FFCA_ERR_CUDA;
@@ -430,6 +466,8 @@ void ffca_destroy(ffca_ctx* c) {
   std::free(c->timed);
   std::free(c);
 }
+
+const char* ffca_last_error(void) { return g_last_error; }
 
 const char* ffca_status_str(ffca_status s) {
   switch (s) {

@@ -16,6 +16,7 @@ enum DevStatus : unsigned {
   kDevOk = 0,
   kDevNonfinite = 3,
   kDevSingular = 4,
+  kDevTimeout = 5,
 };
 
 // First error wins; its frequency index is kept beside it.
@@ -121,16 +122,26 @@ __device__ inline void df_add(float& ah, float& al, float bh, float bl) {
   al = e - (ah - s);
 }
 
-// Block-wide reduction of NV per-thread pairs (hi, lo) in a fixed order.
+// Barrier over the threads taking part in a reduction: the whole CTA, or
+// only the consumer warps of a warp-specialised CTA (named barrier 1).
+template <int NTHREADS, bool NAMED>
+__device__ inline void group_sync() {
+  if constexpr (NAMED) {
+    asm volatile("bar.sync 1, %0;" ::"n"(NTHREADS) : "memory");
+  } else {
+    __syncthreads();
+  }
+}
+
+// Reduction of NV per-thread pairs (hi, lo) over NW warps in a fixed order.
 // FP32 pairs are combined with double-float additions (compensated); FP64
-// values with plain additions.  Thread t < NV ends up holding value t
-// (hi + lo) as a double in `out`.  Must be called by all threads.
-template <typename T, int NV>
+// values with plain additions.  Thread t < NV writes value t (hi + lo) as a
+// double to out[t].  Must be called by all NW warps.
+template <typename T, int NV, int NW = kWarps, bool NAMED = false>
 struct BlockReduce {
-  // scratch: kWarps * NV pairs
   struct Smem {
-    T hi[kWarps][NV];
-    T lo[kWarps][NV];
+    T hi[NW][NV];
+    T lo[NW][NV];
   };
 
   __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& sm, double* out) {
@@ -149,29 +160,26 @@ struct BlockReduce {
         sm.lo[warp][k] = l;
       }
     }
-    __syncthreads();
+    group_sync<32 * NW, NAMED>();
     if (threadIdx.x < NV) {
       const int k = threadIdx.x;
       T h = sm.hi[0][k], l = sm.lo[0][k];
 #pragma unroll
-      for (int w = 1; w < kWarps; ++w) combine(h, l, sm.hi[w][k], sm.lo[w][k]);
+      for (int w = 1; w < NW; ++w) combine(h, l, sm.hi[w][k], sm.lo[w][k]);
       out[k] = (double)h + (double)l;
     }
-    __syncthreads();
+    group_sync<32 * NW, NAMED>();
   }
 
-  __device__ static inline void combine(T& h, T& l, T oh, T ol);
+  __device__ static inline void combine(T& h, T& l, T oh, T ol) {
+    if constexpr (sizeof(T) == 4) {
+      df_add(h, l, oh, ol);
+    } else {
+      h += oh;
+      l += ol;
+    }
+  }
 };
-
-template <typename T, int NV>
-__device__ inline void BlockReduce<T, NV>::combine(T& h, T& l, T oh, T ol) {
-  if constexpr (sizeof(T) == 4) {
-    df_add(h, l, oh, ol);
-  } else {
-    h += oh;
-    l += ol;
-  }
-}
 
 // ------------------------------------------------------------ partition
 // The (f, unit) plane, flattened f-major, is cut into equal contiguous
@@ -204,6 +212,7 @@ inline Partition make_partition(int F, int Uf, int max_blocks) {
   long long nb = want < max_blocks ? want : max_blocks;
   if (nb < 1) nb = 1;
   p.upb = (total + nb - 1) / nb;
+  p.upb = (p.upb + 1) / 2 * 2;  // even: every range starts on a 16-byte boundary of v
   p.nblocks = (int)((total + p.upb - 1) / p.upb);
   if (p.nblocks < 1) p.nblocks = 1;
   // the range of one frequency spans at most ceil(Uf / upb) + 1 CTAs
@@ -212,17 +221,20 @@ inline Partition make_partition(int F, int Uf, int max_blocks) {
 }
 
 // Arrival counter: returns true in exactly one CTA, the last of `expected`
-// to arrive.  Every thread must call it after writing its partials.
+// to arrive.  Every participating thread (the CTA, or its NTHREADS consumer
+// threads with NAMED) must call it after writing its partials.  Nothing
+// waits on other CTAs.
+template <int NTHREADS = kBlock, bool NAMED = false>
 __device__ inline bool arrive_last(unsigned* counter, unsigned expected, int* flag_smem) {
   __threadfence();
-  __syncthreads();
+  group_sync<NTHREADS, NAMED>();
   if (threadIdx.x == 0) {
     unsigned prev = atomicAdd(counter, 1u);
     bool last = (prev == expected - 1);
     if (last) *counter = 0u;  // ready for the next launch
     *flag_smem = last ? 1 : 0;
   }
-  __syncthreads();
+  group_sync<NTHREADS, NAMED>();
   bool last = *flag_smem != 0;
   if (last) __threadfence();
   return last;

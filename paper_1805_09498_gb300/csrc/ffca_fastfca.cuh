@@ -1,23 +1,15 @@
-// FastFCA-AS kernels (Ito & Nakatani, Sec. 4.4).
+// FastFCA-AS kernels (Ito & Nakatani, Sec. 4.4), except the two streaming
+// passes (k_estep, k_wcov), which live in ffca_stream.cuh.
 //
-//   k_estep   pass A: y~ = P^H y, sigma_i = sum_j v_j lambda_ji, the posterior
-//             powers q_ji = |mu~_ji|^2 + phi~_ji (Eqs. mutilde0, Phitilde0),
-//             the v update written in place (Eq. updatev), the Lambda
-//             numerators sum_n q_ji / v_j^new (Eq. Lambdaupdate) and the
-//             per-frame log-likelihood terms of the entering state (Eq. L2).
-//             The last CTA to finish a frequency finalises Lambda(f); the
-//             last frequency finalises the scalar log-likelihood.
-//   k_wcov    pass B: V_i(f) = (1/N) sum_n y y^H / sigma_i with the new v and
-//             Lambda (Eq. FPI), reduced over n into per-frequency slots.
 //   k_psolve  per frequency (one warp): V_i from the slots, then the FP64
 //             fixed-point update of P(f) (K sweeps) and ln|det P(f)|^2.
 //   k_wiener  x^_j = P^{-H} diag(v_j lambda_j / sigma) P^H y (Eq. MMSE0).
 //   k_prep    per frequency: ln|det P|^2 and P^{-H} (FP64).
 //
 // Layouts: y [I][F][ld] complex (float2 or double2), v [J][F][ld] real,
-// lambda [F][J][I] double, P [F][I][I] complex double row-major.  Both
-// streaming passes read whole 16-byte vector units: two frames of a c64 mic
-// row, or one frame of a c128 row.
+// lambda [F][J][I] double, P [F][I][I] complex double row-major.  The
+// streaming kernels read whole 16-byte vector units of y: two frames of a c64
+// mic row, or one frame of a c128 row.
 #pragma once
 
 #include "ffca_common.cuh"
@@ -100,172 +92,7 @@ __device__ inline void finalize_trace(const FastArgs& a) {
   }
 }
 
-// -------------------------------------------------------------- pass A
-template <typename T, int I, int J, bool UPDATE>
-__global__ void __launch_bounds__(kBlock) k_estep(FastArgs a) {
-  using VY = typename Vec<T>::Y;
-  using VV = typename Vec<T>::V;
-  constexpr int FU = Vec<T>::FU;
-  constexpr int NV = UPDATE ? J * I + 1 : 1;  // Lambda numerators, then loglik
-  constexpr int LL = NV - 1;
-
-  __shared__ typename BlockReduce<T, NV>::Smem red;
-  __shared__ double sP[I][I][2];
-  __shared__ double sLam[J][I];
-  __shared__ int sflag;
-
-  const Partition pt = a.part;
-  const long long total = (long long)pt.F * pt.Uf;
-  const long long u0 = (long long)blockIdx.x * pt.upb;
-  const long long u1 = min(u0 + pt.upb, total);
-  const long long row = a.ld / FU;  // vector units per (mic or source, f) row
-  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
-  VV* __restrict__ v = reinterpret_cast<VV*>(a.v);
-
-  for (long long u = u0; u < u1;) {
-    const int f = (int)(u / pt.Uf);
-    const int k0 = (int)(u - (long long)f * pt.Uf);
-    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
-
-    if (threadIdx.x < I * I) {
-      const int r = threadIdx.x / I, c = threadIdx.x % I;
-      sP[r][c][0] = a.P[((size_t)f * I * I + threadIdx.x) * 2];
-      sP[r][c][1] = a.P[((size_t)f * I * I + threadIdx.x) * 2 + 1];
-    }
-    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
-    __syncthreads();
-
-    cpx<T> Pc[I][I];  // P(f), used as conj(P_ai) in y~_i = sum_a conj(P_ai) y_a
-    T lam[J][I], ilam[J][I];
-#pragma unroll
-    for (int r = 0; r < I; ++r)
-#pragma unroll
-      for (int c = 0; c < I; ++c) Pc[r][c] = mk<T>((T)sP[r][c][0], (T)sP[r][c][1]);
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-      for (int i = 0; i < I; ++i) {
-        lam[j][i] = (T)sLam[j][i];
-        ilam[j][i] = recip(lam[j][i]);
-      }
-
-    Acc<T> acc[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t].zero();
-
-    for (int kb = k0 + threadIdx.x; kb < k1; kb += kBlock * kUnits) {
-      VY yu[kUnits][I];
-      VV vu[kUnits][J];
-#pragma unroll
-      for (int q = 0; q < kUnits; ++q) {
-        const int k = kb + q * kBlock;
-        if (k < k1) {
-#pragma unroll
-          for (int m = 0; m < I; ++m) yu[q][m] = y[((size_t)m * pt.F + f) * row + k];
-#pragma unroll
-          for (int j = 0; j < J; ++j) vu[q][j] = v[((size_t)j * pt.F + f) * row + k];
-        }
-      }
-      T grp[NV];
-#pragma unroll
-      for (int t = 0; t < NV; ++t) grp[t] = (T)0;
-
-#pragma unroll
-      for (int q = 0; q < kUnits; ++q) {
-        const int k = kb + q * kBlock;
-        if (k >= k1) continue;
-#pragma unroll
-        for (int e = 0; e < FU; ++e) {
-          const int n = k * FU + e;
-          if (n >= a.N) continue;
-          cpx<T> yt[I];
-#pragma unroll
-          for (int i = 0; i < I; ++i) {
-            cpx<T> s = mk<T>(0, 0);
-#pragma unroll
-            for (int m = 0; m < I; ++m) cfmac(s, Pc[m][i], yframe(yu[q][m], e));
-            yt[i] = s;
-          }
-          T vv[J];
-#pragma unroll
-          for (int j = 0; j < J; ++j) vv[j] = vframe(vu[q][j], e);
-          T sig[I], rs[I], e2[I];
-          T ll = (T)0;
-#pragma unroll
-          for (int i = 0; i < I; ++i) {
-            T s = vv[0] * lam[0][i];
-#pragma unroll
-            for (int j = 1; j < J; ++j) s = fma(vv[j], lam[j][i], s);
-            sig[i] = s;
-            rs[i] = recip(s);
-            e2[i] = cabs2(yt[i]);
-            ll += logx(s) + e2[i] * rs[i];
-          }
-          grp[LL] += ll;
-          if constexpr (UPDATE) {
-            T qv[J][I];
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-              T vn = (T)0;
-#pragma unroll
-              for (int i = 0; i < I; ++i) {
-                const T aji = vv[j] * lam[j][i];          // v_j [Lambda_j]_ii
-                const T g = aji * rs[i];                   // Wiener gain
-                const T phi = fma(-aji, g, aji);           // Eq. Phitilde0
-                const T qq = fma(g * g, e2[i], phi);       // |mu~|^2 + phi~
-                qv[j][i] = qq;
-                vn = fma(qq, ilam[j][i], vn);
-              }
-              vn *= (T)(1.0 / I);                          // Eq. updatev
-              vset(vu[q][j], e, vn);
-              const T rv = recip(vn);
-#pragma unroll
-              for (int i = 0; i < I; ++i) grp[j * I + i] = fma(qv[j][i], rv, grp[j * I + i]);
-            }
-          }
-        }
-        if constexpr (UPDATE) {
-#pragma unroll
-          for (int j = 0; j < J; ++j) v[((size_t)j * pt.F + f) * row + k] = vu[q][j];
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < NV; ++t) acc[t].add(grp[t]);
-    }
-
-    T hi[NV], lo[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      hi[t] = acc[t].value_hi();
-      lo[t] = acc[t].value_lo();
-    }
-    const int slot = (int)blockIdx.x - pt.first_block(f);
-    BlockReduce<T, NV>::run(hi, lo, red,
-                            a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
-
-    if (arrive_last(a.cnt + f, (unsigned)pt.nslots(f), &sflag)) {
-      const int ns = pt.nslots(f);
-      if (threadIdx.x < NV) {
-        const int t = threadIdx.x;
-        const double tot = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, t);
-        if (t == LL) {
-          const double lf = -(double)I * a.N * kLnPi + (double)a.N * __ldcg(a.logdet + f) - tot;
-          if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
-          a.llf[f] = lf;
-        } else {
-          const double lnew = tot / a.N;                  // Eq. Lambdaupdate
-          if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
-          a.lam[(size_t)f * J * I + t] = lnew;
-        }
-      }
-      if (arrive_last(a.gcnt, (unsigned)pt.F, &sflag)) finalize_trace(a);
-    }
-    __syncthreads();
-    u += k1 - k0;
-  }
-}
-
-// -------------------------------------------------------------- pass B
+// -------------------------------------------------------------- P update
 // Packed Hermitian V_i: I real diagonal entries, then (re, im) of the
 // entries above the diagonal in row order; I^2 reals per i.
 template <int I>
@@ -345,108 +172,6 @@ __device__ void p_update(const FastArgs& a, int f, const double* sV, double (*sP
   if (lane < I * I) {
     a.P[((size_t)f * I * I + lane) * 2] = sPn[lane / I][lane % I][0];
     a.P[((size_t)f * I * I + lane) * 2 + 1] = sPn[lane / I][lane % I][1];
-  }
-}
-
-template <typename T, int I, int J>
-__global__ void __launch_bounds__(kBlock) k_wcov(FastArgs a) {
-  using VY = typename Vec<T>::Y;
-  using VV = typename Vec<T>::V;
-  constexpr int FU = Vec<T>::FU;
-  constexpr int I2 = I * I;
-  constexpr int NV = I * I2;
-
-  __shared__ typename BlockReduce<T, NV>::Smem red;
-  __shared__ double sLam[J][I];
-
-  const Partition pt = a.part;
-  const long long total = (long long)pt.F * pt.Uf;
-  const long long u0 = (long long)blockIdx.x * pt.upb;
-  const long long u1 = min(u0 + pt.upb, total);
-  const long long row = a.ld / FU;
-  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
-  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
-
-  for (long long u = u0; u < u1;) {
-    const int f = (int)(u / pt.Uf);
-    const int k0 = (int)(u - (long long)f * pt.Uf);
-    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
-
-    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
-    __syncthreads();
-    T lam[J][I];
-#pragma unroll
-    for (int j = 0; j < J; ++j)
-#pragma unroll
-      for (int i = 0; i < I; ++i) lam[j][i] = (T)sLam[j][i];
-
-    // Per-thread sums over this segment's frames (a few dozen at most at
-    // full size); the tree across threads below is compensated.
-    T acc[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) acc[t] = (T)0;
-
-    for (int kb = k0 + threadIdx.x; kb < k1; kb += kBlock * kUnits) {
-      VY yu[kUnits][I];
-      VV vu[kUnits][J];
-#pragma unroll
-      for (int q = 0; q < kUnits; ++q) {
-        const int k = kb + q * kBlock;
-        if (k < k1) {
-#pragma unroll
-          for (int m = 0; m < I; ++m) yu[q][m] = y[((size_t)m * pt.F + f) * row + k];
-#pragma unroll
-          for (int j = 0; j < J; ++j) vu[q][j] = v[((size_t)j * pt.F + f) * row + k];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kUnits; ++q) {
-        const int k = kb + q * kBlock;
-        if (k >= k1) continue;
-#pragma unroll
-        for (int e = 0; e < FU; ++e) {
-          const int n = k * FU + e;
-          if (n >= a.N) continue;
-          cpx<T> ym[I];
-#pragma unroll
-          for (int m = 0; m < I; ++m) ym[m] = yframe(yu[q][m], e);
-          T w[I];
-#pragma unroll
-          for (int i = 0; i < I; ++i) {
-            T s = vframe(vu[q][0], e) * lam[0][i];
-#pragma unroll
-            for (int j = 1; j < J; ++j) s = fma(vframe(vu[q][j], e), lam[j][i], s);
-            w[i] = recip(s);
-          }
-          // y y^H, packed: diagonal |y_r|^2, then y_r conj(y_c) for r < c
-          T pk[I2];
-          {
-            int m = I;
-#pragma unroll
-            for (int r = 0; r < I; ++r) {
-              pk[r] = cabs2(ym[r]);
-#pragma unroll
-              for (int c = r + 1; c < I; ++c) {
-                pk[m] = fma(ym[r].re, ym[c].re, ym[r].im * ym[c].im);
-                pk[m + 1] = fma(ym[r].im, ym[c].re, -ym[r].re * ym[c].im);
-                m += 2;
-              }
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < I; ++i)
-#pragma unroll
-            for (int m = 0; m < I2; ++m) acc[i * I2 + m] = fma(w[i], pk[m], acc[i * I2 + m]);
-        }
-      }
-    }
-
-    T lo[NV];
-#pragma unroll
-    for (int t = 0; t < NV; ++t) lo[t] = (T)0;
-    const int slot = (int)blockIdx.x - pt.first_block(f);
-    BlockReduce<T, NV>::run(acc, lo, red, a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
-    u += k1 - k0;
   }
 }
 

@@ -1,7 +1,7 @@
 // Explicit instantiations of the FastFCA-AS kernels for one precision and
 // one microphone count, J = 1..6.  Compiled once per (FFCA_PREC, FFCA_I).
 #include "ffca_dispatch.h"
-#include "ffca_fastfca.cuh"
+#include "ffca_stream.cuh"
 
 #ifndef FFCA_PREC
 #error "FFCA_PREC must be defined (0 = FP64, 1 = mixed)"
@@ -21,6 +21,7 @@ using Real = float;
 template <int J>
 static const FastKernels* table_entry() {
   static const FastKernels k = {
+      Tile<FFCA_I, J>::SMEM,
       (const void*)k_estep<Real, FFCA_I, J, true>,
       (const void*)k_estep<Real, FFCA_I, J, false>,
       (const void*)k_wcov<Real, FFCA_I, J>,

@@ -37,6 +37,10 @@ class FFCAError(RuntimeError):
         self.frequency = frequency
         name = STATUS_NAMES.get(status, str(status))
         extra = f" at frequency {frequency}" if frequency >= 0 else ""
+        if status in (2, 6) and _lib is not None:
+            detail = _lib.ffca_last_error().decode()
+            if detail:
+                extra += f" ({detail})"
         super().__init__(f"{what}: {name}{extra}")
 
 
@@ -80,6 +84,7 @@ def lib() -> ctypes.CDLL:
         "ffca_iterate_noalloc": (ci, [P(ffca_desc), ci, dp]),
         "ffca_destroy": (None, [vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
+        "ffca_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -239,7 +244,8 @@ class FastFCA:
                       workspace=None, workspace_bytes=0, stream=s.cuda_stream)
         nbytes = ffca_workspace_size(d)
         if nbytes == 0 and F > 0:
-            raise FFCAError(1, "ffca_workspace_size (invalid or unsupported shape)")
+            raise FFCAError(1, "ffca_workspace_size (invalid shape or CUDA failure: "
+                               + lib().ffca_last_error().decode() + ")")
         self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=y.device)
         d.workspace = self.workspace.data_ptr()
         d.workspace_bytes = nbytes
