@@ -258,7 +258,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
             avg = kms / kn
             kernels[k] = {"launches": kn, "avg_us": avg * 1e3, "bytes_per_launch": bpt * N * F,
                           "achieved_gbs": bpt * N * F / (avg * 1e-3) / 1e9}
-    for k in ("psolve", "loglik", "wiener", "prep"):
+    for k in ("psolve", "afinal", "loglik", "wiener", "prep"):
         kms, kn = kt[k]
         if kn:
             kernels[k] = {"launches": kn, "avg_us": kms / kn * 1e3}

@@ -153,7 +153,8 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
 #define FFCA_KERNEL_WCOV 3      /* pass B: weighted covariance partial sums */
 #define FFCA_KERNEL_WIENER 4
 #define FFCA_KERNEL_PSOLVE 5    /* per-frequency FP64 fixed-point update of P */
-#define FFCA_KERNEL_KINDS 6
+#define FFCA_KERNEL_AFINAL 6    /* per-frequency finalise of pass A: Lambda, log-likelihood */
+#define FFCA_KERNEL_KINDS 7
 
 /* Profiling: while enabled, each kernel the context launches is bracketed by
  * two CUDA events on the context stream.  ffca_timing_read synchronises,

@@ -53,7 +53,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Plan {
   Partition pA, pB, pW;
-  size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB;
+  size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
 };
 
@@ -122,8 +122,11 @@ ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
   p->off_llf = off; off = align_up(off + sizeof(double) * F);
   p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
   p->off_pinvH = off; off = align_up(off + sizeof(double) * 2 * I * I * (size_t)F);
-  p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)F * p->pA.max_slots * (J * I + 1));
+  p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)F * p->pA.max_slots * (J * I + 2));
   p->off_partB = off; off = align_up(off + sizeof(double) * (size_t)F * p->pB.max_slots * I * I * I);
+  p->off_tabA = off; off = align_up(off + (size_t)F * k->params_a_bytes);
+  p->off_tabB = off; off = align_up(off + (size_t)F * k->params_b_bytes);
+  p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)F * J * I);
   p->bytes = off;
   return FFCA_OK;
 }
@@ -173,6 +176,9 @@ FastArgs base_args(const ffca_ctx* c) {
   a.trace = reinterpret_cast<double*>(c->ws + c->plan.off_trace);
   a.status = c->status;
   a.ops = c->ops;
+  a.tabA = c->ws + c->plan.off_tabA;
+  a.tabB = c->ws + c->plan.off_tabB;
+  a.inv_n = 1.0 / c->d.N;
   return a;
 }
 
@@ -186,12 +192,16 @@ FastArgs pass_a_args(const ffca_ctx* c, int slot) {
   return a;
 }
 
-FastArgs pass_b_args(const ffca_ctx* c) {
+FastArgs pass_b_args(const ffca_ctx* c, int slot) {
   FastArgs a = base_args(c);
   a.part = c->plan.pB;
   a.part_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partB);
   a.cnt = reinterpret_cast<unsigned*>(c->ws + c->plan.off_cntB);
   a.gcnt = c->gcntB;
+  a.trace_slot = slot;
+  a.prev_part = c->plan.pA;
+  a.prev_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partA);
+  a.lam_next = reinterpret_cast<double*>(c->ws + c->plan.off_lamnext);
   return a;
 }
 
@@ -227,9 +237,11 @@ ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, F
 ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   FastArgs a = base_args(c);
   a.pinvH = want_pinv ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
-  const int grid = (c->d.F + 127) / 128;
-  return launch(c, FFCA_KERNEL_PREP, c->kern->prep, grid, 128, a);
+  const int G = 32 / c->d.I;  // frequencies per warp
+  return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a);
 }
+
+int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
 
 void drop_timed(ffca_ctx* c) {
   for (size_t k = 0; k < c->ntimed; ++k) {
@@ -314,17 +326,20 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
       if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, a.part.nblocks, kStreamThreads, a,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
-      FastArgs b = pass_b_args(c);
+      FastArgs b = pass_b_args(c, slot);
       if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, b.part.nblocks, kStreamThreads, b,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
-      const int gs = (c->d.F + kSolveWarps - 1) / kSolveWarps;
-      if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, gs, 32 * kSolveWarps, b)) != FFCA_OK)
+      const int G = 32 / c->d.I;  // frequencies per warp
+      if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b)) != FFCA_OK)
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
       if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kStreamThreads, a,
                       c->kern->stream_smem)) != FFCA_OK)
+        return st;
+      if ((st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) !=
+          FFCA_OK)
         return st;
     }
     if (ll_trace && (slot == kTraceCap - 1 || t == iters)) {
@@ -351,6 +366,8 @@ ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
   FastArgs a = pass_a_args(c, 0);
   if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kStreamThreads, a,
                       c->kern->stream_smem)) != FFCA_OK)
+    return st;
+  if ((st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) != FFCA_OK)
     return st;
   if (cudaMemcpyAsync(ll, a.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
     return FFCA_ERR_CUDA;

@@ -222,11 +222,13 @@ inline Partition make_partition(int F, int Uf, int max_blocks) {
 
 // Arrival counter: returns true in exactly one CTA, the last of `expected`
 // to arrive.  Every participating thread (the CTA, or its NTHREADS consumer
-// threads with NAMED) must call it after writing its partials.  Nothing
+// threads with NAMED) must call it; the threads below `writers` (those that
+// wrote data the last CTA will read) fence their writes first.  Nothing
 // waits on other CTAs.
 template <int NTHREADS = kBlock, bool NAMED = false>
-__device__ inline bool arrive_last(unsigned* counter, unsigned expected, int* flag_smem) {
-  __threadfence();
+__device__ inline bool arrive_last(unsigned* counter, unsigned expected, int* flag_smem,
+                                   int writers = NTHREADS) {
+  if ((int)threadIdx.x < writers) __threadfence();
   group_sync<NTHREADS, NAMED>();
   if (threadIdx.x == 0) {
     unsigned prev = atomicAdd(counter, 1u);
@@ -241,111 +243,68 @@ __device__ inline bool arrive_last(unsigned* counter, unsigned expected, int* fl
 }
 
 // ------------------------------------------------------------ FP64 solves
-// In-place inverse of a complex I x I matrix (row-major) by Gauss-Jordan
-// elimination with partial pivoting.  Also returns ln|det A|^2.  Returns
-// false if a pivot is zero or not finite.
+// Determinant of the (I-1) x (I-1) minor of the complex I x I matrix A that
+// leaves out row r and column c (I <= 4).
 template <int I>
-__device__ inline bool gj_inverse(cpx<double> (&A)[I][I], double& logabsdet2) {
-  cpx<double> B[I][I];
+__device__ inline cpx<double> minor_det(const cpx<double> (&A)[I][I], int r, int c) {
+  if constexpr (I == 1) {
+    return mk(1.0, 0.0);
+  } else {
+    int rows[I - 1], cols[I - 1];
+#pragma unroll
+    for (int k = 0, nr = 0, nc = 0; k < I; ++k) {
+      if (k != r) rows[nr++] = k;
+      if (k != c) cols[nc++] = k;
+    }
+    if constexpr (I == 2) {
+      return A[rows[0]][cols[0]];
+    } else if constexpr (I == 3) {
+      return csub(cmul(A[rows[0]][cols[0]], A[rows[1]][cols[1]]), cmul(A[rows[0]][cols[1]], A[rows[1]][cols[0]]));
+    } else {
+      static_assert(I == 4, "I <= 4");
+      auto e = [&](int rr, int cc) { return A[rows[rr]][cols[cc]]; };
+      cpx<double> d = cmul(e(0, 0), csub(cmul(e(1, 1), e(2, 2)), cmul(e(1, 2), e(2, 1))));
+      d = csub(d, cmul(e(0, 1), csub(cmul(e(1, 0), e(2, 2)), cmul(e(1, 2), e(2, 0)))));
+      return cadd(d, cmul(e(0, 2), csub(cmul(e(1, 0), e(2, 1)), cmul(e(1, 1), e(2, 0)))));
+    }
+  }
+}
+
+// Column i of the cofactor matrix of A: C_ri, r = 0..I-1.  Expanding the
+// determinant along column i gives det A = sum_r A_ri C_ri, and row i of the
+// inverse is (A^{-1})_ir = C_ri / det A.
+template <int I>
+__device__ inline cpx<double> column_cofactors(const cpx<double> (&A)[I][I], int i, cpx<double> (&C)[I]) {
+  cpx<double> det = mk(0.0, 0.0);
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const cpx<double> m = minor_det<I>(A, r, i);
+    C[r] = ((r + i) & 1) ? mk(-m.re, -m.im) : m;
+    det = cadd(det, cmul(A[r][i], C[r]));
+  }
+  return det;
+}
+
+// Determinant and full cofactor matrix of a complex I x I matrix with
+// compile-time indexing only (registers, no local memory): det A by the first
+// row, C_rc = (-1)^(r+c) minor_rc.  A^{-1} = C^T / det A.
+template <int I>
+__device__ inline cpx<double> cofactors(const cpx<double> (&A)[I][I], cpx<double> (&C)[I][I]) {
 #pragma unroll
   for (int r = 0; r < I; ++r)
-#pragma unroll
-    for (int c = 0; c < I; ++c) B[r][c] = mk<double>(r == c ? 1.0 : 0.0, 0.0);
-  logabsdet2 = 0.0;
-#pragma unroll
-  for (int k = 0; k < I; ++k) {
-    // pivot search in column k (rows k..I-1)
-    int piv = k;
-    double best = cabs2(A[k][k]);
-#pragma unroll
-    for (int r = k + 1; r < I; ++r) {
-      double m = cabs2(A[r][k]);
-      if (m > best) { best = m; piv = r; }
-    }
-    if (!(best > 0.0) || !isfinite(best)) return false;
-    if (piv != k) {
-#pragma unroll
-      for (int c = 0; c < I; ++c) {
-        // swap rows k and piv with compile-time indices only
-#pragma unroll
-        for (int r = k + 1; r < I; ++r) {
-          if (r == piv) {
-            cpx<double> t = A[k][c]; A[k][c] = A[r][c]; A[r][c] = t;
-            t = B[k][c]; B[k][c] = B[r][c]; B[r][c] = t;
-          }
-        }
-      }
-    }
-    logabsdet2 += log(best);
-    const double inv = 1.0 / best;
-    const cpx<double> pinv = mk<double>(A[k][k].re * inv, -A[k][k].im * inv);  // 1 / A[k][k]
 #pragma unroll
     for (int c = 0; c < I; ++c) {
-      A[k][c] = cmul(A[k][c], pinv);
-      B[k][c] = cmul(B[k][c], pinv);
+      const cpx<double> m = minor_det<I>(A, r, c);
+      C[r][c] = ((r + c) & 1) ? mk(-m.re, -m.im) : m;
     }
+  cpx<double> det = mk(0.0, 0.0);
 #pragma unroll
-    for (int r = 0; r < I; ++r) {
-      if (r == k) continue;
-      const cpx<double> m = A[r][k];
-#pragma unroll
-      for (int c = 0; c < I; ++c) {
-        A[r][c] = csub(A[r][c], cmul(m, A[k][c]));
-        B[r][c] = csub(B[r][c], cmul(m, B[k][c]));
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < I; ++r)
-#pragma unroll
-    for (int c = 0; c < I; ++c) A[r][c] = B[r][c];
-  return true;
+  for (int c = 0; c < I; ++c) det = cadd(det, cmul(A[0][c], C[0][c]));
+  return det;
 }
 
-// Solve V x = b for Hermitian positive definite V (full storage, row-major)
-// by a Cholesky factorisation V = L L^H.  Returns false if V is not
-// numerically positive definite: a pivot at or below kCholRtol times its
-// diagonal entry (rank deficiency shows up as a pivot at rounding level).
+// Relative threshold below which a positive definite determinant or pivot is
+// treated as rank deficient (rounding level in FP64).
 constexpr double kCholRtol = 1e-14;
-
-template <int I>
-__device__ inline bool chol_solve(const cpx<double> (&V)[I][I], const cpx<double> (&b)[I],
-                                  cpx<double> (&x)[I]) {
-  cpx<double> L[I][I];
-  double dinv[I];
-#pragma unroll
-  for (int j = 0; j < I; ++j) {
-    double d = V[j][j].re;
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= cabs2(L[j][k]);
-    if (!(d > kCholRtol * V[j][j].re) || !isfinite(d)) return false;
-    const double ljj = sqrt(d);
-    L[j][j] = mk<double>(ljj, 0.0);
-    dinv[j] = 1.0 / ljj;
-#pragma unroll
-    for (int i = j + 1; i < I; ++i) {
-      cpx<double> s = V[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s = csub(s, cmul(L[i][k], cconj(L[j][k])));
-      L[i][j] = cscale(s, dinv[j]);
-    }
-  }
-  cpx<double> z[I];
-#pragma unroll
-  for (int i = 0; i < I; ++i) {  // L z = b
-    cpx<double> s = b[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) s = csub(s, cmul(L[i][k], z[k]));
-    z[i] = cscale(s, dinv[i]);
-  }
-#pragma unroll
-  for (int i = I - 1; i >= 0; --i) {  // L^H x = z
-    cpx<double> s = z[i];
-#pragma unroll
-    for (int k = i + 1; k < I; ++k) s = csub(s, cmul(cconj(L[k][i]), x[k]));
-    x[i] = cscale(s, dinv[i]);
-  }
-  return true;
-}
 
 }  // namespace ffca

@@ -11,7 +11,10 @@ struct FastKernels {
   const void* wcov;          // pass B: weighted covariance partial sums
   const void* psolve;        // per-frequency fixed-point update of P
   const void* wiener;
-  const void* prep;          // per-frequency ln|det P|^2 and P^{-H}
+  const void* prep;          // per-frequency ln|det P|^2, P^{-H}, pass-A parameters
+  const void* afinal_eval;   // log-likelihood-only pass A finalise: per-frequency L2, trace
+  int params_a_bytes;        // bytes per frequency of the pass-A parameter table
+  int params_b_bytes;        // bytes per frequency of the pass-B parameter table
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

@@ -37,7 +37,35 @@ struct FastArgs {
   unsigned long long* ops;   // matrix inversions performed by the P update
   double* pinvH;             // [F][I][I] complex, P^{-H} (Wiener)
   void* out;                 // Wiener output [J][I][F][ld] complex
+  void* tabA;                // [F] ParamsA: P(f) and Lambda(f) in the per-point precision
+  void* tabB;                // [F] ParamsB: Lambda(f) in the per-point precision
+  double inv_n;              // 1 / N
+  double* lam_next;          // [F][J][I] the new Lambda, written during pass B, committed by k_psolve
+  Partition prev_part;       // pass B reads pass A's slots: their partition
+  const double* prev_buf;    // and buffer
 };
+
+// Per-frequency parameters in the per-point precision T, laid out as they
+// travel to the streaming kernels (one bulk copy per tile, 16-byte padded).
+template <typename T, int I, int J>
+struct ParamsA {  // pass A: P(f) and Lambda(f)
+  T pre[I][I], pim[I][I];
+  T lam[J][I];
+  static constexpr int BYTES = (int)((sizeof(T) * (2 * I * I + J * I) + 15) / 16 * 16);
+};
+template <typename T, int I, int J>
+struct ParamsB {  // pass B: the new Lambda(f)
+  T lam[J][I];
+  static constexpr int BYTES = (int)((sizeof(T) * J * I + 15) / 16 * 16);
+};
+template <typename T, int I, int J>
+__device__ inline ParamsA<T, I, J>* tab_a(const FastArgs& a, int f) {
+  return reinterpret_cast<ParamsA<T, I, J>*>(static_cast<char*>(a.tabA) + (size_t)f * ParamsA<T, I, J>::BYTES);
+}
+template <typename T, int I, int J>
+__device__ inline ParamsB<T, I, J>* tab_b(const FastArgs& a, int f) {
+  return reinterpret_cast<ParamsB<T, I, J>*>(static_cast<char*>(a.tabB) + (size_t)f * ParamsB<T, I, J>::BYTES);
+}
 
 template <typename T>
 struct Vec;
@@ -80,15 +108,68 @@ __device__ inline double sum_slots(const double* part_buf, int f, int nslots, in
   return s;
 }
 
-// The last frequency finaliser adds the per-frequency log-likelihoods in
-// frequency order (one warp, fixed tree) into the trace slot.
+// Sum of the per-frequency log-likelihoods in a fixed order (one warp; each
+// lane keeps four running sums so that four loads are in flight at a time)
+// into the trace slot.
 __device__ inline void finalize_trace(const FastArgs& a) {
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int f = threadIdx.x; f < a.F; f += 32) s += __ldcg(a.llf + f);
+  const int lane = threadIdx.x & 31;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int f = lane; f < a.F; f += 128) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (threadIdx.x == 0) a.trace[a.trace_slot] = s;
+    for (int u = 0; u < 4; ++u)
+      if (f + 32 * u < a.F) s[u] += __ldcg(a.llf + f + 32 * u);
+  }
+  double t = (s[0] + s[1]) + (s[2] + s[3]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if (lane == 0) a.trace[a.trace_slot] = t;
+}
+
+// -------------------------------------------------------------- pass A finalise
+// One warp per frequency, after pass A: sum the slots (FP64, slot order) into
+// the new Lambda(f) (Eq. Lambdaupdate: lambda_ji I sum_n t_ji / s_j / N, see
+// k_estep; used with UPDATE only) and the frequency's log-likelihood (Eq. L2);
+// the last warp to finish adds the frequencies' log-likelihoods into the
+// trace.  Inside an iteration pass B's producer does this work instead; the
+// log-likelihood-only pass uses this kernel.
+constexpr int kFinalWarps = 4;
+
+template <typename T, int I, int J, bool UPDATE>
+__global__ void __launch_bounds__(32 * kFinalWarps) k_afinal(FastArgs a) {
+  constexpr int NA = UPDATE ? J * I : 0;
+  constexpr int NV = NA + 2;
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * kFinalWarps + (threadIdx.x >> 5);
+  if (f >= a.F) return;  // whole warps only
+  const Partition pt = a.part;
+  const int ns = pt.nslots(f);
+  if (lane < NA) {
+    const int j = lane / I, i = lane % I;
+    const double tot = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, lane);
+    double* lp = a.lam + (size_t)f * J * I + lane;
+    const double lnew = *lp * ((double)I * a.inv_n) * tot;
+    if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
+    *lp = lnew;
+    tab_a<T, I, J>(a, f)->lam[j][i] = (T)lnew;
+    tab_b<T, I, J>(a, f)->lam[j][i] = (T)lnew;
+  } else if (lane == NA) {
+    const double quad = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, NA);
+    const double lg2 = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, NA + 1);
+    const double lf = -(double)I * a.N * kLnPi + (double)a.N * a.logdet[f] - quad - 0.69314718055994530942 * lg2;
+    if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
+    a.llf[f] = lf;
+    __threadfence();
+  }
+  __syncwarp();
+  unsigned last = 0;
+  if (lane == 0) {
+    last = atomicAdd(a.gcnt, 1u) == (unsigned)a.F - 1;
+    if (last) *a.gcnt = 0u;  // ready for the next launch
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence();
+    finalize_trace(a);
   }
 }
 
@@ -110,120 +191,199 @@ __device__ inline void unpack_herm(const double* src, cpx<double> (&V)[I][I]) {
   }
 }
 
-// FP64 fixed-point update of P(f) (Eq. FPI, K sweeps) from the finalised
-// V_i in shared memory.  Lane 0 inverts P, lanes i < I solve column i.
+// -------------------------------------------------------------- P solve
+// The per-frequency FP64 kernels put 32 / I frequencies in one warp, lane
+// (g, i) owning column i of frequency g: FP64 throughput on this part is a
+// small fraction of FP32 and a warp instruction costs the same with 3 or 32
+// active lanes, so filling the lanes is what makes these kernels fast.
 template <int I>
-__device__ void p_update(const FastArgs& a, int f, const double* sV, double (*sPn)[I][2],
-                         double (*sQ)[I][2], int* sbad) {
-  const int lane = threadIdx.x & 31;  // called by one full warp
-  if (lane == 0) *sbad = 0;
-  if (lane < I * I) {
-    sPn[lane / I][lane % I][0] = a.P[((size_t)f * I * I + lane) * 2];
-    sPn[lane / I][lane % I][1] = a.P[((size_t)f * I * I + lane) * 2 + 1];
-  }
-  __syncwarp();
-  for (int sweep = 0; sweep < a.K; ++sweep) {
-    if (lane == 0) {
-      cpx<double> A[I][I];
-#pragma unroll
-      for (int r = 0; r < I; ++r)
-#pragma unroll
-        for (int c = 0; c < I; ++c) A[r][c] = mk(sPn[r][c][0], sPn[r][c][1]);
-      double ld2;
-      if (!gj_inverse<I>(A, ld2)) *sbad = 1;
-      // Q = (P^{-1})^H: Q[r][c] = conj(Pinv[c][r])
-#pragma unroll
-      for (int r = 0; r < I; ++r)
-#pragma unroll
-        for (int c = 0; c < I; ++c) {
-          sQ[r][c][0] = A[c][r].re;
-          sQ[r][c][1] = -A[c][r].im;
-        }
-    }
-    __syncwarp();
-    if (lane < I) {
-      const int i = lane;
-      cpx<double> V[I][I], b[I], x[I];
-      unpack_herm<I>(sV + i * I * I, V);
-#pragma unroll
-      for (int r = 0; r < I; ++r) b[r] = mk(sQ[r][i][0], sQ[r][i][1]);
-      if (!chol_solve<I>(V, b, x)) *sbad = 1;
-#pragma unroll
-      for (int r = 0; r < I; ++r) {
-        sPn[r][i][0] = x[r].re;
-        sPn[r][i][1] = x[r].im;
-      }
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    cpx<double> A[I][I];
-#pragma unroll
-    for (int r = 0; r < I; ++r)
-#pragma unroll
-      for (int c = 0; c < I; ++c) A[r][c] = mk(sPn[r][c][0], sPn[r][c][1]);
-    double ld2 = 0.0;
-    if (!gj_inverse<I>(A, ld2)) *sbad = 1;
-    a.logdet[f] = ld2;
-    atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
-    if (*sbad) raise_status(a.status, kDevSingular, f);
-  }
-  __syncwarp();
-  if (lane < I * I) {
-    a.P[((size_t)f * I * I + lane) * 2] = sPn[lane / I][lane % I][0];
-    a.P[((size_t)f * I * I + lane) * 2 + 1] = sPn[lane / I][lane % I][1];
-  }
+struct Lanes {
+  static constexpr int G = 32 / I;  // frequencies per warp
+};
+
+__device__ inline cpx<double> shfl_c(cpx<double> z, int src) {
+  return mk(__shfl_sync(0xffffffffu, z.re, src), __shfl_sync(0xffffffffu, z.im, src));
 }
 
-// -------------------------------------------------------------- P solve
-// One warp per frequency: sum pass B's slots into V_i (FP64, slot order),
-// then the fixed-point update of P(f) and ln|det P(f)|^2.
-constexpr int kSolveWarps = 4;
-
+// Gather the full P of this lane's frequency from the I lanes that own its
+// columns (lane g*I + c holds column c).
 template <int I>
-__global__ void __launch_bounds__(32 * kSolveWarps) k_psolve(FastArgs a) {
+__device__ inline void gather_columns(const cpx<double> (&col)[I], int g, cpx<double> (&A)[I][I]) {
+#pragma unroll
+  for (int c = 0; c < I; ++c)
+#pragma unroll
+    for (int r = 0; r < I; ++r) A[r][c] = shfl_c(col[r], g * I + c);
+}
+
+// After pass B, per frequency: commit the new Lambda (computed during pass B)
+// to lambda and the pass-A table; sum pass B's slots into V_i (FP64, slot
+// order); the fixed-point update of P(f) (Eq. FPI, K sweeps, all columns from
+// the same P^{-H}) into P and the pass-A table; finally the last warp adds
+// the frequencies' log-likelihoods (also written during pass B) into the
+// trace.  FP64 latency on this part is long (an FMA ~64 cycles, a division
+// ~350), so the kernel keeps its dependency chains short: no log (pass A
+// computes ln|det P|^2 on the side), the inverses by cofactors (independent,
+// shallow products) with one division per sweep, register-only indexing.
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
+  constexpr int G = Lanes<I>::G;
   constexpr int NV = I * I * I;
-  __shared__ double sV[kSolveWarps][NV];
-  __shared__ double sPn[kSolveWarps][I][I][2];
-  __shared__ double sQ[kSolveWarps][I][I][2];
-  __shared__ int sbad[kSolveWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int f = blockIdx.x * kSolveWarps + warp;
-  if (f >= a.F) return;  // whole warps only
+  const int lane = threadIdx.x;
+  const int g = lane / I, i = lane % I;
+  const int f0 = blockIdx.x * G + g;
+  const bool active = g < G && f0 < a.F;
+  const int f = active ? f0 : 0;  // idle lanes shadow frequency 0 and write nothing
   const Partition pt = a.part;
   const int ns = pt.nslots(f);
-  for (int t = lane; t < NV; t += 32) {
-    const double s = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, t) / a.N;
-    if (!isfinite(s)) raise_status(a.status, kDevNonfinite, f);
-    sV[warp][t] = s;
-  }
-  __syncwarp();
-  p_update<I>(a, f, sV[warp], sPn[warp], sQ[warp], &sbad[warp]);
-}
 
-// -------------------------------------------------------------- prep
-// Per frequency (one thread each): ln|det P|^2 and P^{-H} of the current P.
-template <int I>
-__global__ void k_prep(FastArgs a) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= a.F) return;
+  if (active && a.lam_next) {
+    ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const double l = a.lam_next[(size_t)f * J * I + j * I + i];
+      a.lam[(size_t)f * J * I + j * I + i] = l;
+      ta->lam[j][i] = (T)l;
+    }
+  }
+
+  cpx<double> V[I][I];
+  {
+    // slot by slot, all I^2 values of V_i at once: the loads of a slot are in flight together
+    double pk[I * I];
+#pragma unroll
+    for (int m = 0; m < I * I; ++m) pk[m] = 0.0;
+    const double* base = a.part_buf + ((size_t)f * pt.max_slots) * NV + i * I * I;
+    for (int k = 0; k < ns; ++k)
+#pragma unroll
+      for (int m = 0; m < I * I; ++m) pk[m] += __ldcg(base + (size_t)k * NV + m);
+#pragma unroll
+    for (int m = 0; m < I * I; ++m) pk[m] *= a.inv_n;
+    unpack_herm<I>(pk, V);
+  }
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < I; ++r)
+#pragma unroll
+    for (int c = 0; c < I; ++c) bad |= !isfinite(V[r][c].re) || !isfinite(V[r][c].im);
+  if (active && bad) raise_status(a.status, kDevNonfinite, f);
+
   cpx<double> A[I][I];
 #pragma unroll
   for (int r = 0; r < I; ++r)
 #pragma unroll
     for (int c = 0; c < I; ++c)
       A[r][c] = mk(a.P[((size_t)f * I * I + r * I + c) * 2], a.P[((size_t)f * I * I + r * I + c) * 2 + 1]);
-  double ld2 = 0.0;
-  if (!gj_inverse<I>(A, ld2)) raise_status(a.status, kDevSingular, f);
-  a.logdet[f] = ld2;
-  if (a.pinvH) {
+
+  // V_i^{-1} = adj(V_i) / det V_i with adj(V) = C_V^T (cofactors, once per
+  // iteration), so that one division per sweep remains on the critical path:
+  //   p_i = V_i^{-1} [P^{-H}]_i = adj(V_i) conj(C_P[., i]) / (det V_i conj(det P))
+  // since [P^{-H}]_{r i} = conj((P^{-1})_{i r}) = conj(C_P[r][i]) / conj(det P).
+  cpx<double> CV[I][I];
+  const double detV = cofactors<I>(V, CV).re;  // real for Hermitian V
+  double diagprod = 1.0;
 #pragma unroll
-    for (int r = 0; r < I; ++r)
+  for (int r = 0; r < I; ++r) diagprod *= V[r][r].re;
+  // Hadamard: 0 < det V <= prod V_rr for positive definite V; a ratio at
+  // rounding level means rank deficiency
+  bool singular = !(detV > kCholRtol * diagprod) || !isfinite(detV);
+  for (int sweep = 0; sweep < a.K; ++sweep) {
+    cpx<double> C[I][I];
+    const cpx<double> detP = cofactors<I>(A, C);
+    cpx<double> num[I];
 #pragma unroll
-      for (int c = 0; c < I; ++c) {  // (P^{-1})^H [r][c] = conj(Pinv[c][r])
-        a.pinvH[((size_t)f * I * I + r * I + c) * 2] = A[c][r].re;
-        a.pinvH[((size_t)f * I * I + r * I + c) * 2 + 1] = -A[c][r].im;
+    for (int r = 0; r < I; ++r) {
+      cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < I; ++q) {
+        cpx<double> cqi = C[q][0];  // column i of C_P, selected by predicate
+#pragma unroll
+        for (int c = 1; c < I; ++c)
+          if (c == i) cqi = C[q][c];
+        cfma(s, CV[q][r], cconj(cqi));  // adj(V)_{rq} = CV_{qr}
       }
+      num[r] = s;
+    }
+    const cpx<double> den = mk(detV * detP.re, -detV * detP.im);  // det V conj(det P)
+    const double d2 = cabs2(den);
+    singular |= !(cabs2(detP) > 0.0) || !isfinite(d2);
+    const double inv = 1.0 / d2;
+    const cpx<double> rden = mk(den.re * inv, -den.im * inv);
+    cpx<double> col[I];
+#pragma unroll
+    for (int r = 0; r < I; ++r) col[r] = cmul(num[r], rden);
+    gather_columns<I>(col, g, A);
+  }
+  if (active) {
+    ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      cpx<double> ari = A[r][0];
+#pragma unroll
+      for (int c = 1; c < I; ++c)
+        if (c == i) ari = A[r][c];
+      a.P[((size_t)f * I * I + r * I + i) * 2] = ari.re;
+      a.P[((size_t)f * I * I + r * I + i) * 2 + 1] = ari.im;
+      ta->pre[r][i] = (T)ari.re;
+      ta->pim[r][i] = (T)ari.im;
+    }
+    if (singular) raise_status(a.status, kDevSingular, f);
+    if (i == 0) atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
+  }
+  // the trace: the last warp adds the per-frequency log-likelihoods
+  if (a.trace) {
+    unsigned last = 0;
+    if (lane == 0) {
+      last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
+      if (last) *a.gcnt = 0u;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      finalize_trace(a);
+    }
+  }
+}
+
+// -------------------------------------------------------------- prep
+// ln|det P|^2 and, if requested, P^{-H} of the current P (FP64, cofactors;
+// lane (g, i) computes column i of P^{-H} of frequency g), and the pass-A
+// parameter table from the current P and Lambda.
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(32) k_prep(FastArgs a) {
+  constexpr int G = Lanes<I>::G;
+  const int lane = threadIdx.x;
+  const int g = lane / I, i = lane % I;
+  const int f = blockIdx.x * G + g;
+  if (g >= G || f >= a.F) return;
+  cpx<double> A[I][I];
+#pragma unroll
+  for (int r = 0; r < I; ++r)
+#pragma unroll
+    for (int c = 0; c < I; ++c)
+      A[r][c] = mk(a.P[((size_t)f * I * I + r * I + c) * 2], a.P[((size_t)f * I * I + r * I + c) * 2 + 1]);
+  ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    ta->pre[r][i] = (T)A[r][i].re;
+    ta->pim[r][i] = (T)A[r][i].im;
+  }
+#pragma unroll
+  for (int j = 0; j < J; ++j) ta->lam[j][i] = (T)a.lam[(size_t)f * J * I + j * I + i];
+  cpx<double> C[I];
+  const cpx<double> det = column_cofactors<I>(A, i, C);
+  const double d2 = cabs2(det);
+  const bool ok = d2 > 0.0 && isfinite(d2);
+  if (!ok) raise_status(a.status, kDevSingular, f);
+  if (i == 0) a.logdet[f] = log(d2);
+  if (a.pinvH) {
+    const double inv = 1.0 / d2;
+    const cpx<double> rdet = mk(det.re * inv, -det.im * inv);
+#pragma unroll
+    for (int r = 0; r < I; ++r) {  // (P^{-H})_{r i} = conj((P^{-1})_{i r}) = conj(C_ri / det)
+      const cpx<double> q = cconj(cmul(C[r], rdet));
+      a.pinvH[((size_t)f * I * I + r * I + i) * 2] = q.re;
+      a.pinvH[((size_t)f * I * I + r * I + i) * 2 + 1] = q.im;
+    }
   }
 }
 

@@ -25,9 +25,12 @@ static const FastKernels* table_entry() {
       (const void*)k_estep<Real, FFCA_I, J, true>,
       (const void*)k_estep<Real, FFCA_I, J, false>,
       (const void*)k_wcov<Real, FFCA_I, J>,
-      (const void*)k_psolve<FFCA_I>,
+      (const void*)k_psolve<Real, FFCA_I, J>,
       (const void*)k_wiener<Real, FFCA_I, J>,
-      (const void*)k_prep<FFCA_I>,
+      (const void*)k_prep<Real, FFCA_I, J>,
+      (const void*)k_afinal<Real, FFCA_I, J, false>,
+      ParamsA<Real, FFCA_I, J>::BYTES,
+      ParamsB<Real, FFCA_I, J>::BYTES,
   };
   return &k;
 }

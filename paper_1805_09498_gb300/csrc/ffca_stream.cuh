@@ -13,12 +13,16 @@
 //   k_estep  pass A (Sec. 4.4.1): y~ = P^H y, sigma, the posterior powers
 //            q_ji (Eqs. mutilde0, Phitilde0), v updated in place (Eq. updatev),
 //            Lambda numerators (Eq. Lambdaupdate) and the log-likelihood
-//            terms of the entering state (Eq. L2).  The last CTA to finish a
-//            frequency finalises Lambda(f) and its log-likelihood; the last
-//            frequency finalises the scalar.
+//            terms of the entering state (Eq. L2), into per-frequency slots
+//            (finalised by k_afinal).
 //   k_wcov   pass B (Sec. 4.4.2): V_i(f) = (1/N) sum_n y y^H / sigma_i with
-//            the new v and Lambda (Eq. FPI), into per-frequency slots.
+//            the new v and Lambda (Eq. FPI), into per-frequency slots
+//            (finalised by k_psolve).
+// Neither kernel loads anything but its tiles: the per-frequency parameters
+// ride along in each stage, so no consumer waits on global memory.
 #pragma once
+
+#include <type_traits>
 
 #include "ffca_fastfca.cuh"
 
@@ -27,19 +31,31 @@ namespace ffca {
 // Eight warps per CTA (seven consumers, one producer): the register file is
 // split over four schedulers of 16 K registers, so two such CTAs fit an SM
 // at up to 128 registers per thread, one CTA at any count.
-constexpr int kConsumerWarps = 7;
+#ifndef FFCA_CONSUMER_WARPS
+#define FFCA_CONSUMER_WARPS 7
+#endif
+#ifndef FFCA_STAGES
+#define FFCA_STAGES 3
+#endif
+#ifndef FFCA_TILE_UNITS_PER_THREAD
+#define FFCA_TILE_UNITS_PER_THREAD 2
+#endif
+constexpr int kConsumerWarps = FFCA_CONSUMER_WARPS;
 constexpr int kConsumers = 32 * kConsumerWarps;
 constexpr int kStreamThreads = kConsumers + 32;  // + one producer warp
-constexpr int kStages = 3;
+constexpr int kStages = FFCA_STAGES;
 
 // A tile is up to T vector units of one frequency: I y rows of 16-byte units
 // and J v rows of 8-byte units, contiguous in global memory per row.  T is
-// one or two units per consumer thread (always even).
+// one or two units per consumer thread (always even).  Each stage also
+// carries the tile's per-frequency parameters (a ParamsA or ParamsB record),
+// so a consumer starting a new frequency finds them already in shared memory.
 template <int I, int J>
 struct Tile {
   static constexpr int UB = 16 * I + 8 * J;                      // bytes per unit over all rows
-  static constexpr int T = (UB <= 80 ? 2 : 1) * kConsumers;      // units per tile
-  static constexpr int STAGE = T * UB;                            // bytes per stage, multiple of 16
+  static constexpr int T = (UB <= 80 ? FFCA_TILE_UNITS_PER_THREAD : 1) * kConsumers;  // units per tile
+  static constexpr int PARAMS = ParamsA<double, I, J>::BYTES;     // room for either record
+  static constexpr int STAGE = T * UB + PARAMS;                   // bytes per stage, multiple of 16
   static constexpr int SMEM = kStages * STAGE + 2 * kStages * 8;  // + mbarriers
 };
 
@@ -123,25 +139,80 @@ struct Pipe {
   __device__ uint32_t empty(int s) const { return bars + 8 * (kStages + s); }
 };
 
+// Pass B's parameters for frequency f, computed by its producer from pass A's
+// slots (FP64): the new Lambda (Eq. Lambdaupdate, lambda_ji I sum_n t_ji/s_j / N
+// with the slot sums of k_estep) into the stage's parameter slot.  The CTA
+// that starts frequency f also stores the new Lambda (committed to lambda by
+// k_psolve, after every CTA of this pass has read the current one) and the
+// frequency's log-likelihood of the state entering the iteration (Eq. L2).
+template <typename T, int I, int J>
+__device__ void finalize_pass_a(const FastArgs& a, int f, ParamsB<T, I, J>* out, bool first) {
+  constexpr int NA = J * I;
+  constexpr int NV = NA + 2;
+  const Partition& pa = a.prev_part;
+  const int ns = pa.nslots(f);
+  const double* p = a.prev_buf + ((size_t)f * pa.max_slots) * NV;
+  double tot[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tot[q] = 0.0;
+  for (int k = 0; k < ns; ++k)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] += __ldcg(p + (size_t)k * NV + q);
+  const double scale = (double)I * a.inv_n;
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const double lnew = a.lam[(size_t)f * NA + q] * scale * tot[q];
+    bad |= !(lnew > 0.0) || !isfinite(lnew);
+    out->lam[q / I][q % I] = (T)lnew;
+    if (first) a.lam_next[(size_t)f * NA + q] = lnew;
+  }
+  if (first) {
+    const double lf = -(double)I * a.N * kLnPi + (double)a.N * __ldcg(a.logdet + f) - tot[NA] -
+                      0.69314718055994530942 * tot[NA + 1];
+    bad |= !isfinite(lf);
+    a.llf[f] = lf;
+    if (bad) raise_status(a.status, kDevNonfinite, f);
+  }
+}
+
 // Producer: one thread.  y units are 16 bytes, v units 8 bytes; ranges start
 // on even units, so every copy is 16-byte aligned and a multiple of 16 bytes.
-template <int I, int J>
+// Each stage also receives the tile's parameter record: copied from the
+// pass-A table (pass A), or computed from pass A's slots (pass B).
+template <typename T, int I, int J, bool PASS_B>
 __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long long u1, long long row,
                         volatile int* abort) {
   using TC = Tile<I, J>;
+  using PA = ParamsA<T, I, J>;
+  using PB = ParamsB<T, I, J>;
   const char* y = static_cast<const char*>(a.y);
   const char* v = static_cast<const char*>(a.v);
+  const char* tab = static_cast<const char*>(a.tabA);
   TileIter it(u0, u1, a.part.Uf, TC::T);
+  PB pb;
+  int pf = -1;
   int t = 0;
   while (it.next()) {
     const int s = t % kStages;
+    if (PASS_B && it.f != pf) {  // before waiting: overlaps the slot loads with the pipeline
+      finalize_pass_a<T, I, J>(a, it.f, &pb, a.part.first_block(it.f) == (int)blockIdx.x);
+      pf = it.f;
+    }
     if (t >= kStages && !*abort && !mbar_wait(pp.empty(s), ((t / kStages) - 1) & 1)) {
       raise_status(a.status, kDevTimeout, it.f);
       *abort = 1;
     }
     if (*abort) break;
-    const uint32_t st = smem_u32(pp.smem + (size_t)s * TC::STAGE);
-    mbar_expect_tx(pp.full(s), (unsigned)it.n * TC::UB);
+    unsigned char* stp = pp.smem + (size_t)s * TC::STAGE;
+    const uint32_t st = smem_u32(stp);
+    if constexpr (PASS_B) {
+      *reinterpret_cast<PB*>(stp + TC::T * TC::UB) = pb;  // visible to consumers with the arrive below
+      mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB));
+    } else {
+      mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB + PA::BYTES));
+      bulk_g2s(st + TC::T * TC::UB, tab + (size_t)it.f * PA::BYTES, (unsigned)PA::BYTES, pp.full(s));
+    }
 #pragma unroll
     for (int m = 0; m < I; ++m)
       bulk_g2s(st + m * TC::T * 16, y + (((size_t)m * a.F + it.f) * row + it.k) * 16,
@@ -154,6 +225,31 @@ __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long lo
   }
   // let the copies of the last stages land before this thread leaves
   for (int d = t > kStages ? t - kStages : 0; d < t; ++d) mbar_wait(pp.full(d % kStages), (d / kStages) & 1);
+}
+
+// Side work of pass A's producer warp (lanes 1..31, otherwise idle):
+// ln|det P(f)|^2 of the P entering this iteration, for the frequencies whose
+// first CTA this is (Eq. L2 needs it per frequency; FP64, off the streaming
+// path).
+template <int I>
+__device__ void side_logdet(const FastArgs& a, long long u0, long long u1) {
+  const int lane = threadIdx.x & 31;
+  const Partition& pt = a.part;
+  const int flo = (int)(u0 / pt.Uf), fhi = (int)((u1 - 1) / pt.Uf);
+  int nth = 0;
+  for (int f = flo; f <= fhi; ++f) {
+    if (pt.first_block(f) != (int)blockIdx.x) continue;
+    if (nth++ % 31 != lane - 1) continue;
+    cpx<double> A[I][I], C[I][I];
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c)
+        A[r][c] = mk(a.P[((size_t)f * I * I + r * I + c) * 2], a.P[((size_t)f * I * I + r * I + c) * 2 + 1]);
+    const double d2 = cabs2(cofactors<I>(A, C));
+    if (!(d2 > 0.0) || !isfinite(d2)) raise_status(a.status, kDevSingular, f);
+    a.logdet[f] = log(d2);
+  }
 }
 
 __device__ inline Pipe setup_pipe(unsigned char* smem, int stage_bytes, volatile int* abort) {
@@ -185,24 +281,99 @@ __device__ inline void consumer_release(const Pipe& pp, int t) {
   if ((threadIdx.x & 31) == 0) mbar_arrive(pp.empty(t % kStages));
 }
 
+// ------------------------------------------------------------ frame lanes
+// The frames of one vector unit are processed together: the two c64 frames
+// as one packed pair with Blackwell's f32x2 FMA / MUL / ADD (one instruction
+// for both frames), the single c128 frame as a plain double.
+struct F2 {
+  float2 v;
+};
+__device__ inline F2 operator+(F2 a, F2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ inline F2 operator*(F2 a, F2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ inline F2 vfma(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ inline F2 vrcp(F2 x) {  // hardware approximation + one Newton-Raphson step
+  F2 r = {make_float2(0.f, 0.f)};
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.v.x) : "f"(x.v.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.v.y) : "f"(x.v.y));
+  const F2 e = vfma(x * F2{make_float2(-1.f, -1.f)}, r, F2{make_float2(1.f, 1.f)});  // 1 - x r
+  return vfma(r, e, r);
+}
+__device__ inline F2 vlog2(F2 x) { return {make_float2(__log2f(x.v.x), __log2f(x.v.y))}; }
+
+struct D1 {
+  double v;
+};
+__device__ inline D1 operator+(D1 a, D1 b) { return {a.v + b.v}; }
+__device__ inline D1 operator*(D1 a, D1 b) { return {a.v * b.v}; }
+__device__ inline D1 vfma(D1 a, D1 b, D1 c) { return {fma(a.v, b.v, c.v)}; }
+__device__ inline D1 vrcp(D1 x) { return {1.0 / x.v}; }
+__device__ inline D1 vlog2(D1 x) { return {log2(x.v)}; }
+
+template <typename T>
+struct Lane;
+template <>
+struct Lane<float> {
+  using L = F2;
+  __device__ static L bc(float x) { return {make_float2(x, x)}; }
+  __device__ static void split(const float4& u, L& re, L& im) {
+    re = {make_float2(u.x, u.z)};
+    im = {make_float2(u.y, u.w)};
+  }
+  __device__ static L real(const float2& u) { return {u}; }
+  __device__ static float2 store(L x) { return x.v; }
+  // zero the lanes of frames at or beyond N (frame index n0 of lane 0)
+  __device__ static L keep(L x, int n0, int N) {
+    return {make_float2(n0 < N ? x.v.x : 0.f, n0 + 1 < N ? x.v.y : 0.f)};
+  }
+  __device__ static L pick(L fresh, L old, int n0, int N) {
+    return {make_float2(n0 < N ? fresh.v.x : old.v.x, n0 + 1 < N ? fresh.v.y : old.v.y)};
+  }
+  __device__ static double total(L x) { return (double)x.v.x + (double)x.v.y; }
+  __device__ static float hsum(L x) { return x.v.x + x.v.y; }
+};
+template <>
+struct Lane<double> {
+  using L = D1;
+  __device__ static L bc(double x) { return {x}; }
+  __device__ static void split(const double2& u, L& re, L& im) {
+    re = {u.x};
+    im = {u.y};
+  }
+  __device__ static L real(double u) { return {u}; }
+  __device__ static double store(L x) { return x.v; }
+  __device__ static L keep(L x, int n0, int N) { return {n0 < N ? x.v : 0.0}; }
+  __device__ static L pick(L fresh, L old, int n0, int N) { return {n0 < N ? fresh.v : old.v}; }
+  __device__ static double hsum(L x) { return x.v; }
+};
+
 // -------------------------------------------------------------- pass A
+// Per frame, with r_i = 1/sigma_i and a_ji = v_j lambda_ji, the posterior
+// power is q_ji = |mu~_ji|^2 + phi~_ji = a_ji t_ji with
+// t_ji = 1 + a_ji w_i, w_i = r_i (r_i |y~_i|^2 - 1) (Eqs. mutilde0,
+// Phitilde0).  Hence v_j^new = (1/I) sum_i q_ji / lambda_ji = v_j s_j / I with
+// s_j = sum_i t_ji (Eq. updatev), and the Lambda numerator
+// sum_n q_ji / v_j^new = I lambda_ji sum_n t_ji / s_j (Eq. Lambdaupdate): the
+// kernel accumulates sum_n t_ji / s_j and k_afinal scales it.  The
+// log-likelihood terms are sum_n sum_i (ln sigma_i + |y~_i|^2 r_i) (Eq. L2),
+// accumulated as the quadratic part and the base-2 log part.
 template <typename T, int I, int J, bool UPDATE>
 __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   using VY = typename Vec<T>::Y;
   using VV = typename Vec<T>::V;
+  using LN = Lane<T>;
+  using L = typename LN::L;
   using TC = Tile<I, J>;
-  using Red = BlockReduce<T, (UPDATE ? J * I + 1 : 1), kConsumerWarps, true>;
   constexpr int FU = Vec<T>::FU;
-  constexpr int NV = UPDATE ? J * I + 1 : 1;  // Lambda numerators, then loglik
-  constexpr int LL = NV - 1;
+  constexpr int NA = UPDATE ? J * I : 0;  // sum_n t_ji / s_j
+  constexpr int NV = NA + 2;              // then the quadratic and log2 parts of L2
+  using Red = BlockReduce<float, NV, kConsumerWarps, true>;
+  using RedD = BlockReduce<double, NV, kConsumerWarps, true>;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ typename Red::Smem red;
-  __shared__ double sP[I][I][2];
-  __shared__ double sLam[J][I];
-  __shared__ int sflag;
+  __shared__ typename std::conditional<sizeof(T) == 4, typename Red::Smem, typename RedD::Smem>::type red;
   __shared__ int sabort;
   volatile int* abort = &sabort;
+  using PA = ParamsA<T, I, J>;
 
   const Partition pt = a.part;
   const long long total = (long long)pt.F * pt.Uf;
@@ -212,140 +383,138 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   const Pipe pp = setup_pipe(smem, TC::STAGE, abort);
 
   if (threadIdx.x >= kConsumers) {
-    if (threadIdx.x == kConsumers) produce<I, J>(a, pp, u0, u1, row, abort);
+    if (threadIdx.x == kConsumers)
+      produce<T, I, J, false>(a, pp, u0, u1, row, abort);
+    else
+      side_logdet<I>(a, u0, u1);
     return;
   }
 
   VV* __restrict__ vg = reinterpret_cast<VV*>(a.v);
   const int tid = threadIdx.x;
-  cpx<T> Pc[I][I];  // P(f): y~_i = sum_m conj(P_mi) y_m
-  T lam[J][I], ilam[J][I];
-  Acc<T> acc[NV];
+  L pre[I][I], pim[I][I], lam[J][I];
+  L acc[NV];
 
   TileIter it(u0, u1, pt.Uf, TC::T);
   bool seg_new = true;
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
     if (seg_new) {
-      consumer_sync();  // the previous segment is done with sP / sLam
-      if (tid < I * I) {
-        sP[tid / I][tid % I][0] = a.P[((size_t)f * I * I + tid) * 2];
-        sP[tid / I][tid % I][1] = a.P[((size_t)f * I * I + tid) * 2 + 1];
-      }
-      if (tid < J * I) sLam[tid / I][tid % I] = a.lam[(size_t)f * J * I + tid];
-      consumer_sync();
 #pragma unroll
-      for (int r = 0; r < I; ++r)
-#pragma unroll
-        for (int c = 0; c < I; ++c) Pc[r][c] = mk<T>((T)sP[r][c][0], (T)sP[r][c][1]);
-#pragma unroll
-      for (int j = 0; j < J; ++j)
-#pragma unroll
-        for (int i = 0; i < I; ++i) {
-          lam[j][i] = (T)sLam[j][i];
-          ilam[j][i] = recip(lam[j][i]);
-        }
-#pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q].zero();
-      seg_new = false;
+      for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
     }
-
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % kStages) * TC::STAGE;
+      if (seg_new) {  // this frequency's P and Lambda arrived with the tile
+        const PA& sp = *reinterpret_cast<const PA*>(st + TC::T * TC::UB);
+#pragma unroll
+        for (int r = 0; r < I; ++r)
+#pragma unroll
+          for (int c = 0; c < I; ++c) {
+            pre[r][c] = LN::bc(sp.pre[r][c]);
+            pim[r][c] = LN::bc(sp.pim[r][c]);
+          }
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+          for (int i = 0; i < I; ++i) lam[j][i] = LN::bc(sp.lam[j][i]);
+      }
       const VY* ys = reinterpret_cast<const VY*>(st);
       const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
-      T grp[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) grp[q] = (T)0;
 #pragma unroll 1
       for (int q = tid; q < it.n; q += kConsumers) {
-        VY yu[I];
-        VV vu[J];
-#pragma unroll
-        for (int m = 0; m < I; ++m) yu[m] = ys[m * TC::T + q];
-#pragma unroll
-        for (int j = 0; j < J; ++j) vu[j] = vs[j * TC::T + q];
         const int k = it.k + q;
+        const int n0 = k * FU;
+        if (n0 >= a.N) continue;  // a unit of padding frames only
+        L yre[I], yim[I], nyre[I], vv[J];
 #pragma unroll
-        for (int e = 0; e < FU; ++e) {
-          if (k * FU + e >= a.N) continue;
-          cpx<T> yt[I];
+        for (int m = 0; m < I; ++m) {
+          LN::split(ys[m * TC::T + q], yre[m], yim[m]);
+          nyre[m] = yre[m] * LN::bc(-1);
+        }
 #pragma unroll
-          for (int i = 0; i < I; ++i) {
-            cpx<T> s = mk<T>(0, 0);
+        for (int j = 0; j < J; ++j) vv[j] = LN::real(vs[j * TC::T + q]);
+        const bool full = n0 + FU <= a.N;
+        L r[I], e2[I];
+        L quad = LN::bc(0), lg = LN::bc(0);
 #pragma unroll
-            for (int m = 0; m < I; ++m) cfmac(s, Pc[m][i], yframe(yu[m], e));
-            yt[i] = s;
+        for (int i = 0; i < I; ++i) {
+          // y~_i = sum_m conj(P_mi) y_m: re = Pr yr + Pi yi, im = Pr yi - Pi yr
+          L tr = pre[0][i] * yre[0], ti = pre[0][i] * yim[0];
+          tr = vfma(pim[0][i], yim[0], tr);
+          ti = vfma(pim[0][i], nyre[0], ti);
+#pragma unroll
+          for (int m = 1; m < I; ++m) {
+            tr = vfma(pre[m][i], yre[m], tr);
+            tr = vfma(pim[m][i], yim[m], tr);
+            ti = vfma(pre[m][i], yim[m], ti);
+            ti = vfma(pim[m][i], nyre[m], ti);
           }
-          T vv[J];
+          L sg = vv[0] * lam[0][i];
 #pragma unroll
-          for (int j = 0; j < J; ++j) vv[j] = vframe(vu[j], e);
-          T rs[I], e2[I];
-          T ll = (T)0;
+          for (int j = 1; j < J; ++j) sg = vfma(vv[j], lam[j][i], sg);
+          r[i] = vrcp(sg);
+          e2[i] = vfma(tr, tr, ti * ti);
+          quad = vfma(e2[i], r[i], quad);
+          lg = lg + vlog2(sg);
+        }
+        if (full) {
+          acc[NA] = acc[NA] + quad;
+          acc[NA + 1] = acc[NA + 1] + lg;
+        } else {
+          acc[NA] = acc[NA] + LN::keep(quad, n0, a.N);
+          acc[NA + 1] = acc[NA + 1] + LN::keep(lg, n0, a.N);
+        }
+        if constexpr (UPDATE) {
+          L w[I];
 #pragma unroll
-          for (int i = 0; i < I; ++i) {
-            T s = vv[0] * lam[0][i];
+          for (int i = 0; i < I; ++i) w[i] = r[i] * vfma(r[i], e2[i], LN::bc(-1));
 #pragma unroll
-            for (int j = 1; j < J; ++j) s = fma(vv[j], lam[j][i], s);
-            rs[i] = recip(s);
-            e2[i] = cabs2(yt[i]);
-            ll += logx(s) + e2[i] * rs[i];
-          }
-          grp[LL] += ll;
-          if constexpr (UPDATE) {
+          for (int j = 0; j < J; ++j) {
+            L tj[I];
+            L sj = LN::bc(0);
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-              T qv[I];
-              T vn = (T)0;
+            for (int i = 0; i < I; ++i) {
+              tj[i] = vfma(vv[j] * lam[j][i], w[i], LN::bc(1));
+              sj = sj + tj[i];
+            }
+            const L rs = vrcp(sj);
+            const L vn = vv[j] * sj * LN::bc((T)(1.0 / I));
+            if (full) {
 #pragma unroll
-              for (int i = 0; i < I; ++i) {
-                const T aji = vv[j] * lam[j][i];          // v_j [Lambda_j]_ii
-                const T g = aji * rs[i];                   // Wiener gain
-                const T phi = fma(-aji, g, aji);           // Eq. Phitilde0
-                qv[i] = fma(g * g, e2[i], phi);            // |mu~|^2 + phi~
-                vn = fma(qv[i], ilam[j][i], vn);
-              }
-              vn *= (T)(1.0 / I);                          // Eq. updatev
-              vset(vu[j], e, vn);
-              const T rv = recip(vn);
+              for (int i = 0; i < I; ++i) acc[j * I + i] = vfma(tj[i], rs, acc[j * I + i]);
+              vg[((size_t)j * pt.F + f) * row + k] = LN::store(vn);
+            } else {
 #pragma unroll
-              for (int i = 0; i < I; ++i) grp[j * I + i] = fma(qv[i], rv, grp[j * I + i]);
+              for (int i = 0; i < I; ++i) acc[j * I + i] = acc[j * I + i] + LN::keep(tj[i] * rs, n0, a.N);
+              vg[((size_t)j * pt.F + f) * row + k] = LN::store(LN::pick(vn, vv[j], n0, a.N));
             }
           }
         }
-        if constexpr (UPDATE) {
-#pragma unroll
-          for (int j = 0; j < J; ++j) vg[((size_t)j * pt.F + f) * row + k] = vu[j];
-        }
       }
-#pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q].add(grp[q]);
     }
+
+    seg_new = false;
     consumer_release(pp, t);
 
     if (it.seg_end) {
-      T hi[NV], lo[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        hi[q] = acc[q].value_hi();
-        lo[q] = acc[q].value_lo();
-      }
       const int slot = (int)blockIdx.x - pt.first_block(f);
-      Red::run(hi, lo, red, a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
-      if (arrive_last<kConsumers, true>(a.cnt + f, (unsigned)pt.nslots(f), &sflag)) {
-        if (tid < NV) {
-          const double tot = sum_slots(a.part_buf, f, pt.nslots(f), pt.max_slots, NV, tid);
-          if (tid == LL) {
-            const double lf = -(double)I * a.N * kLnPi + (double)a.N * __ldcg(a.logdet + f) - tot;
-            if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
-            a.llf[f] = lf;
-          } else {
-            const double lnew = tot / a.N;  // Eq. Lambdaupdate
-            if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
-            a.lam[(size_t)f * J * I + tid] = lnew;
-          }
+      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
+      if constexpr (sizeof(T) == 4) {
+        float hi[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);  // the two frame lanes, exactly
         }
-        if (arrive_last<kConsumers, true>(a.gcnt, (unsigned)pt.F, &sflag)) finalize_trace(a);
+        Red::run(hi, lo, red, out);
+      } else {
+        double hi[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          hi[q] = acc[q].v;
+          lo[q] = 0.0;
+        }
+        RedD::run(hi, lo, red, out);
       }
       seg_new = true;
     }
@@ -353,21 +522,27 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 }
 
 // -------------------------------------------------------------- pass B
+// V_i(f) partial sums: sum_n r_i y y^H with r_i = 1/sigma_i from the new v and
+// Lambda (Eq. FPI); y y^H packed as the real diagonal, then (re, im) of the
+// entries above it in row order.
 template <typename T, int I, int J>
 __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   using VY = typename Vec<T>::Y;
   using VV = typename Vec<T>::V;
+  using LN = Lane<T>;
+  using L = typename LN::L;
   using TC = Tile<I, J>;
   constexpr int FU = Vec<T>::FU;
   constexpr int I2 = I * I;
   constexpr int NV = I * I2;
-  using Red = BlockReduce<T, NV, kConsumerWarps, true>;
+  using Red = BlockReduce<float, NV, kConsumerWarps, true>;
+  using RedD = BlockReduce<double, NV, kConsumerWarps, true>;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ typename Red::Smem red;
-  __shared__ double sLam[J][I];
+  __shared__ typename std::conditional<sizeof(T) == 4, typename Red::Smem, typename RedD::Smem>::type red;
   __shared__ int sabort;
   volatile int* abort = &sabort;
+  using PB = ParamsB<T, I, J>;
 
   const Partition pt = a.part;
   const long long total = (long long)pt.F * pt.Uf;
@@ -377,88 +552,103 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   const Pipe pp = setup_pipe(smem, TC::STAGE, abort);
 
   if (threadIdx.x >= kConsumers) {
-    if (threadIdx.x == kConsumers) produce<I, J>(a, pp, u0, u1, row, abort);
+    if (threadIdx.x == kConsumers) produce<T, I, J, true>(a, pp, u0, u1, row, abort);
     return;
   }
 
   const int tid = threadIdx.x;
-  T lam[J][I];
-  // Per-thread sums over this segment's frames (a few dozen at most at full
-  // size); the tree across threads is compensated.
-  T acc[NV];
+  L lam[J][I];
+  L acc[NV];
 
   TileIter it(u0, u1, pt.Uf, TC::T);
   bool seg_new = true;
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
     if (seg_new) {
-      consumer_sync();
-      if (tid < J * I) sLam[tid / I][tid % I] = a.lam[(size_t)f * J * I + tid];
-      consumer_sync();
 #pragma unroll
-      for (int j = 0; j < J; ++j)
-#pragma unroll
-        for (int i = 0; i < I; ++i) lam[j][i] = (T)sLam[j][i];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q] = (T)0;
-      seg_new = false;
+      for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
     }
-
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % kStages) * TC::STAGE;
+      if (seg_new) {  // the new Lambda(f) arrived with the tile
+        const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+          for (int i = 0; i < I; ++i) lam[j][i] = LN::bc(sp.lam[j][i]);
+      }
       const VY* ys = reinterpret_cast<const VY*>(st);
       const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
 #pragma unroll 1
       for (int q = tid; q < it.n; q += kConsumers) {
-        VY yu[I];
-        VV vu[J];
-#pragma unroll
-        for (int m = 0; m < I; ++m) yu[m] = ys[m * TC::T + q];
-#pragma unroll
-        for (int j = 0; j < J; ++j) vu[j] = vs[j * TC::T + q];
         const int k = it.k + q;
+        const int n0 = k * FU;
+        if (n0 >= a.N) continue;
+        L yre[I], yim[I], nyre[I], vv[J];
 #pragma unroll
-        for (int e = 0; e < FU; ++e) {
-          if (k * FU + e >= a.N) continue;
-          cpx<T> ym[I];
-#pragma unroll
-          for (int m = 0; m < I; ++m) ym[m] = yframe(yu[m], e);
-          T w[I];
-#pragma unroll
-          for (int i = 0; i < I; ++i) {
-            T s = vframe(vu[0], e) * lam[0][i];
-#pragma unroll
-            for (int j = 1; j < J; ++j) s = fma(vframe(vu[j], e), lam[j][i], s);
-            w[i] = recip(s);
-          }
-          // y y^H, packed: diagonal |y_r|^2, then y_r conj(y_c) for r < c
-          T pk[I2];
-          int m = I;
-#pragma unroll
-          for (int r = 0; r < I; ++r) {
-            pk[r] = cabs2(ym[r]);
-#pragma unroll
-            for (int c = r + 1; c < I; ++c) {
-              pk[m] = fma(ym[r].re, ym[c].re, ym[r].im * ym[c].im);
-              pk[m + 1] = fma(ym[r].im, ym[c].re, -ym[r].re * ym[c].im);
-              m += 2;
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < I; ++i)
-#pragma unroll
-            for (int mm = 0; mm < I2; ++mm) acc[i * I2 + mm] = fma(w[i], pk[mm], acc[i * I2 + mm]);
+        for (int m = 0; m < I; ++m) {
+          LN::split(ys[m * TC::T + q], yre[m], yim[m]);
+          nyre[m] = yre[m] * LN::bc(-1);
         }
+#pragma unroll
+        for (int j = 0; j < J; ++j) vv[j] = LN::real(vs[j * TC::T + q]);
+        L w[I];
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          L sg = vv[0] * lam[0][i];
+#pragma unroll
+          for (int j = 1; j < J; ++j) sg = vfma(vv[j], lam[j][i], sg);
+          w[i] = vrcp(sg);
+        }
+        if (n0 + FU > a.N) {  // the ragged last unit: drop the frames beyond N
+#pragma unroll
+          for (int i = 0; i < I; ++i) w[i] = LN::keep(w[i], n0, a.N);
+#pragma unroll
+          for (int m = 0; m < I; ++m) {
+            yre[m] = LN::keep(yre[m], n0, a.N);
+            yim[m] = LN::keep(yim[m], n0, a.N);
+            nyre[m] = LN::keep(nyre[m], n0, a.N);
+          }
+        }
+        L pk[I2];
+        int m = I;
+#pragma unroll
+        for (int rr = 0; rr < I; ++rr) {
+          pk[rr] = vfma(yre[rr], yre[rr], yim[rr] * yim[rr]);
+#pragma unroll
+          for (int c = rr + 1; c < I; ++c) {
+            pk[m] = vfma(yre[rr], yre[c], yim[rr] * yim[c]);       // re(y_r conj(y_c))
+            pk[m + 1] = vfma(nyre[rr], yim[c], yim[rr] * yre[c]);  // im(y_r conj(y_c))
+            m += 2;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < I; ++i)
+#pragma unroll
+          for (int mm = 0; mm < I2; ++mm) acc[i * I2 + mm] = vfma(w[i], pk[mm], acc[i * I2 + mm]);
       }
     }
+
+    seg_new = false;
     consumer_release(pp, t);
 
     if (it.seg_end) {
-      T lo[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) lo[q] = (T)0;
       const int slot = (int)blockIdx.x - pt.first_block(f);
-      Red::run(acc, lo, red, a.part_buf + ((size_t)f * pt.max_slots + slot) * NV);
+      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
+      if constexpr (sizeof(T) == 4) {
+        float hi[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);
+        Red::run(hi, lo, red, out);
+      } else {
+        double hi[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          hi[q] = acc[q].v;
+          lo[q] = 0.0;
+        }
+        RedD::run(hi, lo, red, out);
+      }
       seg_new = true;
     }
   }

@@ -165,7 +165,7 @@ def ffca_wiener_host(ctx, out_dev_ptr: int, out_host_ptr: int) -> None:
                                        ctypes.c_void_p(out_host_ptr)), "ffca_wiener_host")
 
 
-KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener", "psolve")
+KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener", "psolve", "afinal")
 
 
 def ffca_timing_enable(ctx, enable: bool) -> None:
