@@ -41,6 +41,11 @@ namespace {
 
 constexpr size_t kAlign = 256;
 
+// CTAs of the streaming passes per resident CTA slot.
+#ifndef FFCA_GRID_WAVES
+#define FFCA_GRID_WAVES 1
+#endif
+
 // Text of the last failed CUDA call in this thread (for ffca_last_error).
 thread_local char g_last_error[256] = "";
 
@@ -85,9 +90,10 @@ ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
                  "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"))
       return FFCA_ERR_CUDA;
   int occA = 0, occB = 0, occW = 0;
-  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k->estep_update, kStreamThreads,
-                                                             k->stream_smem), "occupancy(pass A)") ||
-      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k->wcov, kStreamThreads, k->stream_smem),
+  const int sthreads = kGroupThreads * k->stream_groups;
+  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k->estep_update, sthreads, k->stream_smem),
+               "occupancy(pass A)") ||
+      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k->wcov, sthreads, k->stream_smem),
                "occupancy(pass B)") ||
       !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occW, k->wiener, kBlock, 0), "occupancy(Wiener)"))
     return FFCA_ERR_CUDA;
@@ -109,8 +115,9 @@ ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
   // starts on a 16-byte boundary (ld % 4 == 0 keeps this inside the row)
   const int Uf = ((d->N + FU - 1) / FU + 1) / 2 * 2;
   const int F = d->F > 0 ? d->F : 1;
-  p->pA = make_partition(F, Uf, nsm * occA);
-  p->pB = make_partition(F, Uf, nsm * occB);
+  // the streaming partitions count virtual blocks: stream_groups pipelines per CTA
+  p->pA = make_partition(F, Uf, nsm * occA * k->stream_groups * FFCA_GRID_WAVES);
+  p->pB = make_partition(F, Uf, nsm * occB * k->stream_groups * FFCA_GRID_WAVES);
   // the Wiener pass also covers the padding frames (it writes them as zero)
   p->pW = make_partition(F, d->ld / FU, nsm * occW);
   p->pA.F = p->pB.F = p->pW.F = d->F;
@@ -243,6 +250,12 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
 
 int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
 
+// CTAs of a streaming pass: each runs stream_groups virtual blocks of the partition.
+int stream_grid(const ffca_ctx* c, const Partition& p) {
+  return (p.nblocks + c->kern->stream_groups - 1) / c->kern->stream_groups;
+}
+int stream_threads(const ffca_ctx* c) { return kGroupThreads * c->kern->stream_groups; }
+
 void drop_timed(ffca_ctx* c) {
   for (size_t k = 0; k < c->ntimed; ++k) {
     cudaEventDestroy(c->timed[k].start);
@@ -323,11 +336,11 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
     const int slot = t % kTraceCap;
     if (t < iters) {
       FastArgs a = pass_a_args(c, slot);
-      if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, a.part.nblocks, kStreamThreads, a,
+      if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, stream_grid(c, a.part), stream_threads(c), a,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       FastArgs b = pass_b_args(c, slot);
-      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, b.part.nblocks, kStreamThreads, b,
+      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       const int G = 32 / c->d.I;  // frequencies per warp
@@ -335,7 +348,7 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
-      if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kStreamThreads, a,
+      if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, stream_grid(c, a.part), stream_threads(c), a,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       if ((st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) !=
@@ -364,7 +377,7 @@ ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
   ffca_status st = launch_prep(c, false);
   if (st != FFCA_OK) return st;
   FastArgs a = pass_a_args(c, 0);
-  if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, a.part.nblocks, kStreamThreads, a,
+  if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, stream_grid(c, a.part), stream_threads(c), a,
                       c->kern->stream_smem)) != FFCA_OK)
     return st;
   if ((st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) != FFCA_OK)

@@ -181,6 +181,75 @@ struct BlockReduce {
   }
 };
 
+// Reduction of NV per-thread pairs (hi, lo) over NW warps, for larger NV: a
+// butterfly reduce-scatter inside each warp (at level `off` every lane keeps
+// half of its remaining values and receives the partner's partial sums of
+// that half from lane ^ off), so that 31 exchanges reduce 32 values where a
+// tree per value needs 5 each; lane l ends with value l of its chunk.  The
+// NW warp results are then summed in shared memory in warp order.  FP32
+// pairs combine with double-float additions, FP64 values plainly.  Thread
+// t < NV writes value t to out[t] (as a double).  Called by all NW warps.
+template <typename T, int NV, int NW, bool NAMED>
+struct ButterflyReduce {
+  static constexpr int NC = (NV + 31) / 32;  // chunks of 32 values
+  static constexpr bool PAIR = sizeof(T) == 4;
+  struct Smem {
+    T hi[NW][NC * 32];
+    T lo[PAIR ? NW : 1][PAIR ? NC * 32 : 1];
+  };
+
+  __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& sm, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T h[32], l[32];
+#pragma unroll
+      for (int v = 0; v < 32; ++v) {
+        const int idx = c * 32 + v;
+        h[v] = idx < NV ? hi[idx] : (T)0;
+        l[v] = idx < NV ? lo[idx] : (T)0;
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int j = 0; j < off; ++j) {
+          T kh = up ? h[j + off] : h[j];
+          const T sh = up ? h[j] : h[j + off];
+          const T rh = __shfl_xor_sync(0xffffffffu, sh, off);
+          if constexpr (PAIR) {
+            T kl = up ? l[j + off] : l[j];
+            const T sl = up ? l[j] : l[j + off];
+            const T rl = __shfl_xor_sync(0xffffffffu, sl, off);
+            df_add(kh, kl, rh, rl);
+            l[j] = kl;
+          } else {
+            kh += rh;
+          }
+          h[j] = kh;
+        }
+      }
+      sm.hi[warp][c * 32 + lane] = h[0];
+      if constexpr (PAIR) sm.lo[warp][c * 32 + lane] = l[0];
+    }
+    group_sync<32 * NW, NAMED>();
+    for (int t = threadIdx.x; t < NV; t += 32 * NW) {
+      T h = sm.hi[0][t];
+      T l = PAIR ? sm.lo[0][t] : (T)0;
+#pragma unroll
+      for (int w = 1; w < NW; ++w) {
+        if constexpr (PAIR) {
+          df_add(h, l, sm.hi[w][t], sm.lo[w][t]);
+        } else {
+          h += sm.hi[w][t];
+        }
+      }
+      out[t] = (double)h + (double)l;
+    }
+    group_sync<32 * NW, NAMED>();
+  }
+};
+
 // ------------------------------------------------------------ partition
 // The (f, unit) plane, flattened f-major, is cut into equal contiguous
 // ranges, one per CTA of a grid sized to the resident CTA count.  A CTA walks

@@ -6,6 +6,7 @@ namespace ffca {
 // Every FastFCA-AS kernel takes one FastArgs by value.
 struct FastKernels {
   int stream_smem;           // dynamic shared memory of the streaming passes
+  int stream_groups;         // pipelines per CTA of the streaming passes (256 threads each)
   const void* estep_update;  // pass A with the M-step
   const void* estep_eval;    // pass A, log-likelihood only
   const void* wcov;          // pass B: weighted covariance partial sums

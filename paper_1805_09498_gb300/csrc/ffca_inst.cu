@@ -21,7 +21,8 @@ using Real = float;
 template <int J>
 static const FastKernels* table_entry() {
   static const FastKernels k = {
-      Tile<FFCA_I, J>::SMEM,
+      StreamGroups<Real, FFCA_I, J>::value * Tile<FFCA_I, J>::GROUP,
+      StreamGroups<Real, FFCA_I, J>::value,
       (const void*)k_estep<Real, FFCA_I, J, true>,
       (const void*)k_estep<Real, FFCA_I, J, false>,
       (const void*)k_wcov<Real, FFCA_I, J>,

@@ -1,14 +1,20 @@
 // Streaming passes of the FastFCA-AS iteration, staged through shared memory
 // by the bulk-copy (TMA) engine.
 //
-// Each CTA is warp-specialised: one producer thread issues, per tile, one
-// cp.async.bulk copy per mic row of y and per source row of v into one of
-// kStages shared-memory stages (completion counted in bytes on that stage's
-// "full" mbarrier); eight consumer warps wait on "full", compute from shared
-// memory and release the stage on its "empty" mbarrier.  Loads are thus kept
-// in flight independently of the consumers' registers.  Every wait is
-// bounded; on expiry the CTA latches FFCA_ERR_TIMEOUT, stops issuing, lets
-// its copies in flight land, and finishes without waiting again.
+// Each CTA runs one or two independent warp-specialised pipelines ("groups"),
+// each working through its own contiguous range of the (f, unit) plane (a
+// "virtual block" of the partition).  In a group one producer thread issues,
+// per tile, one cp.async.bulk copy per mic row of y and per source row of v
+// into one of kStages shared-memory stages (completion counted in bytes on
+// that stage's "full" mbarrier); seven consumer warps wait on "full", compute
+// from shared memory and release the stage on its "empty" mbarrier.  Loads
+// are thus kept in flight independently of the consumers' registers.  The
+// groups share one CTA (rather than being two CTAs per SM) because the warp
+// scheduler favours the warps of the CTA launched first: with separate CTAs
+// of equal work the second one finished ~15% later.  Group membership is
+// interleaved over warp indices so that every scheduler hosts both groups.
+// Every wait is bounded; on expiry the group latches FFCA_ERR_TIMEOUT, stops
+// issuing, lets its copies in flight land, and finishes without waiting.
 //
 //   k_estep  pass A (Sec. 4.4.1): y~ = P^H y, sigma, the posterior powers
 //            q_ji (Eqs. mutilde0, Phitilde0), v updated in place (Eq. updatev),
@@ -28,12 +34,13 @@
 
 namespace ffca {
 
-// Eight warps per CTA (seven consumers, one producer): the register file is
-// split over four schedulers of 16 K registers, so two such CTAs fit an SM
-// at up to 128 registers per thread, one CTA at any count.
+// Two groups of eight warps (seven consumers, one producer) per CTA: the
+// register file is split over four schedulers of 16 K registers, so the 16
+// warps fit at up to 128 registers per thread.
 #ifndef FFCA_CONSUMER_WARPS
 #define FFCA_CONSUMER_WARPS 7
 #endif
+
 #ifndef FFCA_STAGES
 #define FFCA_STAGES 3
 #endif
@@ -42,8 +49,39 @@ namespace ffca {
 #endif
 constexpr int kConsumerWarps = FFCA_CONSUMER_WARPS;
 constexpr int kConsumers = 32 * kConsumerWarps;
-constexpr int kStreamThreads = kConsumers + 32;  // + one producer warp
+constexpr int kGroupWarps = kConsumerWarps + 1;  // + one producer warp
+constexpr int kGroupThreads = 32 * kGroupWarps;
 constexpr int kStages = FFCA_STAGES;
+static_assert(kGroupWarps % 4 == 0, "groups interleave in units of four warps");
+
+// Pipelines per CTA: two where the per-point state fits 128 registers (the
+// 16 warps then share the register file), else one.
+template <typename T, int I, int J>
+struct StreamGroups {
+  static constexpr int value = (sizeof(T) == 4 && I <= 3 && J <= 3) ? 2 : 1;
+};
+
+// The role of a thread in its CTA.  Warp w belongs to group (w / 4) % G with
+// rank (w / (4 G)) * 4 + w % 4 in it; ranks below kConsumerWarps consume, the
+// last rank produces.
+struct Role {
+  int group;   // pipeline group within the CTA
+  int vb;      // virtual block: the partition range this group works on
+  int cwarp;   // rank of the warp in its group
+  int ctid;    // consumer thread index in the group (valid for consumers)
+  bool consumer;
+};
+template <int G>
+__device__ inline Role role() {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Role r;
+  r.group = (w / 4) % G;
+  r.cwarp = (w / (4 * G)) * 4 + w % 4;
+  r.vb = (int)blockIdx.x * G + r.group;
+  r.consumer = r.cwarp < kConsumerWarps;
+  r.ctid = r.cwarp * 32 + lane;
+  return r;
+}
 
 // A tile is up to T vector units of one frequency: I y rows of 16-byte units
 // and J v rows of 8-byte units, contiguous in global memory per row.  T is
@@ -56,14 +94,14 @@ struct Tile {
   static constexpr int T = (UB <= 80 ? FFCA_TILE_UNITS_PER_THREAD : 1) * kConsumers;  // units per tile
   static constexpr int PARAMS = ParamsA<double, I, J>::BYTES;     // room for either record
   static constexpr int STAGE = T * UB + PARAMS;                   // bytes per stage, multiple of 16
-  static constexpr int SMEM = kStages * STAGE + 2 * kStages * 8;  // + mbarriers
+  static constexpr int GROUP = kStages * STAGE + 2 * kStages * 8;  // + mbarriers
 };
 
-// Register cap of the streaming kernels: 128 lets two CTAs share an SM where
-// the per-point state fits (FP32, I <= 3, J <= 3); otherwise one CTA per SM.
+// Register cap of the streaming kernels: 128 for two groups per CTA, else
+// what one group of eight warps may use.
 template <typename T, int I, int J>
 struct StreamRegs {
-  static constexpr int value = (sizeof(T) == 4 && I <= 3 && J <= 3) ? 128 : 255;
+  static constexpr int value = StreamGroups<T, I, J>::value == 2 ? 128 : 255;
 };
 
 // ------------------------------------------------------------ primitives
@@ -110,7 +148,79 @@ __device__ inline void bulk_g2s(uint32_t dst, const void* src, unsigned bytes, u
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-__device__ inline void consumer_sync() { group_sync<kConsumers, true>(); }
+// Barrier over the consumer warps of one group (named barrier 1 + group).
+__device__ inline void consumer_sync(int group) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "n"(kConsumers) : "memory");
+}
+
+// Reduction of NV per-thread pairs (hi, lo) over a group's consumer warps: a
+// butterfly reduce-scatter inside each warp (at level `off` every lane keeps
+// half of its remaining values and receives the partner's partial sums of
+// that half from lane ^ off: 31 exchanges reduce 32 values where a tree per
+// value needs 5 each; lane l ends with value l of its chunk), then the warp
+// results summed in shared memory in warp order.  FP32 pairs combine with
+// double-float additions (compensated), FP64 values plainly.  Consumer
+// thread t < NV writes value t to out[t] (as a double).
+template <typename T, int NV>
+struct GroupReduce {
+  static constexpr int NC = (NV + 31) / 32;  // chunks of 32 values
+  static constexpr bool PAIR = sizeof(T) == 4;
+  struct Smem {
+    T hi[kConsumerWarps][NC * 32];
+    T lo[PAIR ? kConsumerWarps : 1][PAIR ? NC * 32 : 1];
+  };
+
+  __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& sm, double* out, const Role& r) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T h[32], l[32];
+#pragma unroll
+      for (int v = 0; v < 32; ++v) {
+        const int idx = c * 32 + v;
+        h[v] = idx < NV ? hi[idx] : (T)0;
+        l[v] = idx < NV ? lo[idx] : (T)0;
+      }
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int j = 0; j < off; ++j) {
+          T kh = up ? h[j + off] : h[j];
+          const T sh = up ? h[j] : h[j + off];
+          const T rh = __shfl_xor_sync(0xffffffffu, sh, off);
+          if constexpr (PAIR) {
+            T kl = up ? l[j + off] : l[j];
+            const T sl = up ? l[j] : l[j + off];
+            const T rl = __shfl_xor_sync(0xffffffffu, sl, off);
+            df_add(kh, kl, rh, rl);
+            l[j] = kl;
+          } else {
+            kh += rh;
+          }
+          h[j] = kh;
+        }
+      }
+      sm.hi[r.cwarp][c * 32 + lane] = h[0];
+      if constexpr (PAIR) sm.lo[r.cwarp][c * 32 + lane] = l[0];
+    }
+    consumer_sync(r.group);
+    for (int t = r.ctid; t < NV; t += kConsumers) {
+      T h = sm.hi[0][t];
+      T l = PAIR ? sm.lo[0][t] : (T)0;
+#pragma unroll
+      for (int w = 1; w < kConsumerWarps; ++w) {
+        if constexpr (PAIR) {
+          df_add(h, l, sm.hi[w][t], sm.lo[w][t]);
+        } else {
+          h += sm.hi[w][t];
+        }
+      }
+      out[t] = (double)h + (double)l;
+    }
+    consumer_sync(r.group);
+  }
+};
 
 // Walks a CTA's unit range [u0, u1) of the flattened (f, unit) plane as
 // tiles of at most T units that never cross a frequency.
@@ -182,7 +292,7 @@ __device__ void finalize_pass_a(const FastArgs& a, int f, ParamsB<T, I, J>* out,
 // pass-A table (pass A), or computed from pass A's slots (pass B).
 template <typename T, int I, int J, bool PASS_B>
 __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long long u1, long long row,
-                        volatile int* abort) {
+                        int vb, volatile int* abort) {
   using TC = Tile<I, J>;
   using PA = ParamsA<T, I, J>;
   using PB = ParamsB<T, I, J>;
@@ -196,7 +306,7 @@ __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long lo
   while (it.next()) {
     const int s = t % kStages;
     if (PASS_B && it.f != pf) {  // before waiting: overlaps the slot loads with the pipeline
-      finalize_pass_a<T, I, J>(a, it.f, &pb, a.part.first_block(it.f) == (int)blockIdx.x);
+      finalize_pass_a<T, I, J>(a, it.f, &pb, a.part.first_block(it.f) == vb);
       pf = it.f;
     }
     if (t >= kStages && !*abort && !mbar_wait(pp.empty(s), ((t / kStages) - 1) & 1)) {
@@ -232,13 +342,13 @@ __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long lo
 // first CTA this is (Eq. L2 needs it per frequency; FP64, off the streaming
 // path).
 template <int I>
-__device__ void side_logdet(const FastArgs& a, long long u0, long long u1) {
+__device__ void side_logdet(const FastArgs& a, long long u0, long long u1, int vb) {
   const int lane = threadIdx.x & 31;
   const Partition& pt = a.part;
   const int flo = (int)(u0 / pt.Uf), fhi = (int)((u1 - 1) / pt.Uf);
   int nth = 0;
   for (int f = flo; f <= fhi; ++f) {
-    if (pt.first_block(f) != (int)blockIdx.x) continue;
+    if (pt.first_block(f) != vb) continue;
     if (nth++ % 31 != lane - 1) continue;
     cpx<double> A[I][I], C[I][I];
 #pragma unroll
@@ -252,20 +362,30 @@ __device__ void side_logdet(const FastArgs& a, long long u0, long long u1) {
   }
 }
 
-__device__ inline Pipe setup_pipe(unsigned char* smem, int stage_bytes, volatile int* abort) {
-  Pipe pp;
-  pp.smem = smem;
-  pp.bars = smem_u32(smem + (size_t)kStages * stage_bytes);
+// Every group's stages and mbarriers, initialised by thread 0; returns this
+// thread's group pipe.
+template <int G>
+__device__ inline Pipe setup_pipe(unsigned char* smem, int stage_bytes, int group, volatile int* aborts) {
+  const size_t group_bytes = (size_t)kStages * stage_bytes + 2 * kStages * 8;
+  auto pipe_of = [&](int g) {
+    Pipe p;
+    p.smem = smem + g * group_bytes;
+    p.bars = smem_u32(p.smem + (size_t)kStages * stage_bytes);
+    return p;
+  };
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(pp.full(s), 1);
-      mbar_init(pp.empty(s), kConsumerWarps);
+    for (int g = 0; g < G; ++g) {
+      const Pipe p = pipe_of(g);
+      for (int s = 0; s < kStages; ++s) {
+        mbar_init(p.full(s), 1);
+        mbar_init(p.empty(s), kConsumerWarps);
+      }
+      aborts[g] = 0;
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *abort = 0;
   }
   __syncthreads();
-  return pp;
+  return pipe_of(group);
 }
 
 // Consumer side of one tile: wait for it unless the CTA has given up.
@@ -366,32 +486,34 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   constexpr int FU = Vec<T>::FU;
   constexpr int NA = UPDATE ? J * I : 0;  // sum_n t_ji / s_j
   constexpr int NV = NA + 2;              // then the quadratic and log2 parts of L2
-  using Red = BlockReduce<float, NV, kConsumerWarps, true>;
-  using RedD = BlockReduce<double, NV, kConsumerWarps, true>;
+  using Red = GroupReduce<T, NV>;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ typename std::conditional<sizeof(T) == 4, typename Red::Smem, typename RedD::Smem>::type red;
-  __shared__ int sabort;
-  volatile int* abort = &sabort;
+  constexpr int G = StreamGroups<T, I, J>::value;
+  __shared__ typename Red::Smem red_all[G];
+  __shared__ int aborts[G];
   using PA = ParamsA<T, I, J>;
 
+  const Role rl = role<G>();
+  volatile int* abort = &aborts[rl.group];
+  typename Red::Smem& red = red_all[rl.group];
   const Partition pt = a.part;
   const long long total = (long long)pt.F * pt.Uf;
-  const long long u0 = (long long)blockIdx.x * pt.upb;
+  const long long u0 = min((long long)rl.vb * pt.upb, total);
   const long long u1 = min(u0 + pt.upb, total);
   const long long row = a.ld / FU;  // vector units per (mic or source, f) row
-  const Pipe pp = setup_pipe(smem, TC::STAGE, abort);
+  const Pipe pp = setup_pipe<G>(smem, TC::STAGE, rl.group, aborts);
 
-  if (threadIdx.x >= kConsumers) {
-    if (threadIdx.x == kConsumers)
-      produce<T, I, J, false>(a, pp, u0, u1, row, abort);
-    else
-      side_logdet<I>(a, u0, u1);
+  if (!rl.consumer) {
+    if ((threadIdx.x & 31) == 0)
+      produce<T, I, J, false>(a, pp, u0, u1, row, rl.vb, abort);
+    else if (u1 > u0)
+      side_logdet<I>(a, u0, u1, rl.vb);
     return;
   }
 
   VV* __restrict__ vg = reinterpret_cast<VV*>(a.v);
-  const int tid = threadIdx.x;
+  const int tid = rl.ctid;
   L pre[I][I], pim[I][I], lam[J][I];
   L acc[NV];
 
@@ -498,7 +620,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     consumer_release(pp, t);
 
     if (it.seg_end) {
-      const int slot = (int)blockIdx.x - pt.first_block(f);
+      const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
       if constexpr (sizeof(T) == 4) {
         float hi[NV], lo[NV];
@@ -506,7 +628,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         for (int q = 0; q < NV; ++q) {
           two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);  // the two frame lanes, exactly
         }
-        Red::run(hi, lo, red, out);
+        Red::run(hi, lo, red, out, rl);
       } else {
         double hi[NV], lo[NV];
 #pragma unroll
@@ -514,7 +636,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           hi[q] = acc[q].v;
           lo[q] = 0.0;
         }
-        RedD::run(hi, lo, red, out);
+        Red::run(hi, lo, red, out, rl);
       }
       seg_new = true;
     }
@@ -535,28 +657,30 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   constexpr int FU = Vec<T>::FU;
   constexpr int I2 = I * I;
   constexpr int NV = I * I2;
-  using Red = BlockReduce<float, NV, kConsumerWarps, true>;
-  using RedD = BlockReduce<double, NV, kConsumerWarps, true>;
+  using Red = GroupReduce<T, NV>;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ typename std::conditional<sizeof(T) == 4, typename Red::Smem, typename RedD::Smem>::type red;
-  __shared__ int sabort;
-  volatile int* abort = &sabort;
+  constexpr int G = StreamGroups<T, I, J>::value;
+  __shared__ typename Red::Smem red_all[G];
+  __shared__ int aborts[G];
   using PB = ParamsB<T, I, J>;
 
+  const Role rl = role<G>();
+  volatile int* abort = &aborts[rl.group];
+  typename Red::Smem& red = red_all[rl.group];
   const Partition pt = a.part;
   const long long total = (long long)pt.F * pt.Uf;
-  const long long u0 = (long long)blockIdx.x * pt.upb;
+  const long long u0 = min((long long)rl.vb * pt.upb, total);
   const long long u1 = min(u0 + pt.upb, total);
   const long long row = a.ld / FU;
-  const Pipe pp = setup_pipe(smem, TC::STAGE, abort);
+  const Pipe pp = setup_pipe<G>(smem, TC::STAGE, rl.group, aborts);
 
-  if (threadIdx.x >= kConsumers) {
-    if (threadIdx.x == kConsumers) produce<T, I, J, true>(a, pp, u0, u1, row, abort);
+  if (!rl.consumer) {
+    if ((threadIdx.x & 31) == 0) produce<T, I, J, true>(a, pp, u0, u1, row, rl.vb, abort);
     return;
   }
 
-  const int tid = threadIdx.x;
+  const int tid = rl.ctid;
   L lam[J][I];
   L acc[NV];
 
@@ -633,13 +757,13 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
     consumer_release(pp, t);
 
     if (it.seg_end) {
-      const int slot = (int)blockIdx.x - pt.first_block(f);
+      const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
       if constexpr (sizeof(T) == 4) {
         float hi[NV], lo[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);
-        Red::run(hi, lo, red, out);
+        Red::run(hi, lo, red, out, rl);
       } else {
         double hi[NV], lo[NV];
 #pragma unroll
@@ -647,7 +771,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
           hi[q] = acc[q].v;
           lo[q] = 0.0;
         }
-        RedD::run(hi, lo, red, out);
+        Red::run(hi, lo, red, out, rl);
       }
       seg_new = true;
     }
