@@ -176,6 +176,30 @@ def run_ours(args, cfg, rank, ws, local, dist):
         del y64, v64, l64, P64
         torch.cuda.empty_cache()
 
+    # the conventional FCA EM baseline (Sec. 3.3) on the same mixture and precision
+    fca_line = None
+    if rank == 0:
+        Pinv = torch.linalg.inv(P_init)
+        S0 = (Pinv.conj().transpose(1, 2)[:, None] * lam_init[:, :, None, :].to(torch.complex128)
+              ) @ Pinv[:, None]
+        S0 = S0.contiguous()
+        vf = v_init.clone()
+        ef = ffca.FCA(yd, vf, S0, N=N)
+        ef.iterate(1, trace=False)
+        itf = 3
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        ef.iterate(itf, trace=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        msf = a.elapsed_time(b)
+        fca_line = {"value": N * F * itf / (msf * 1e-3), "unit": UNIT, "iters_timed": itf,
+                    "ms_per_iter": msf / itf, "precision": "mixed (same as the main line)"}
+        ef.close()
+        del vf, S0, Pinv
+        torch.cuda.empty_cache()
+
     vd.copy_(v_init); lamd.copy_(lam_init); Pd.copy_(P_init)
 
     def step():
@@ -288,6 +312,8 @@ def run_ours(args, cfg, rank, ws, local, dist):
         "gpu_launches_per_step": launches / args.steps,
         "clocks": clk, "fp64_gpu": fp64,
         "speedup_mixed_vs_fp64_gpu": (value / ws / fp64["value"]) if fp64 else None,
+        "fca_gpu": fca_line,
+        "speedup_vs_fca_gpu": (value / ws / fca_line["value"]) if fca_line else None,
     }
 
 

@@ -189,6 +189,47 @@ ffca_status ffca_iterate_noalloc(const ffca_desc* desc, int iters, double* ll_tr
 /* Release the context (host memory only; the device arrays stay the caller's). */
 void ffca_destroy(ffca_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Conventional FCA EM (Sec. 3.3 of the paper; the baseline FastFCA-AS is
+ * measured against).  Model (Eqs. srcmodel, fullrank): R_j(n,f) =
+ * v_j(n,f) S_j(f) with full Hermitian positive definite S_j(f).  Each
+ * iteration: per (n,f) the E-step of Eqs. MMSE and postquadexp with a full
+ * I x I inverse of R = sum_j R_j and the products R_j R^{-1}, (R_j R^{-1}) R_j;
+ * the v update of Eq. vupdate with the current S_j^{-1}; then per frequency
+ * S_j <- (1/N) sum_n (mu_j mu_j^H + Phi_j) / v_j (Eq. Supdate) in FP64.
+ * Same conventions (device pointers, caller's stream, status codes) and the
+ * same y / v layouts and precisions as FastFCA-AS. */
+typedef struct {
+  int I, J, F, N, ld;     /* as in ffca_desc (I 1..4, J 1..6) */
+  int prec;               /* ffca_precision */
+  const void* y;          /* [I][F][ld] complex, read only */
+  void* v;                /* [J][F][ld] real, in/out */
+  double* S;              /* [F][J][I][I] complex128 row-major, Hermitian PD, in/out */
+  void* workspace;        /* ffca_fca_workspace_size() bytes, 256-byte aligned */
+  size_t workspace_bytes;
+  void* stream;           /* cudaStream_t */
+} ffca_fca_desc;
+
+typedef struct ffca_fca_ctx ffca_fca_ctx;
+
+/* Workspace bytes for the descriptor on the current device (0 if invalid). */
+size_t ffca_fca_workspace_size(const ffca_fca_desc* desc);
+/* Validate, plan and clear the workspace; *out receives the context. */
+ffca_status ffca_fca_init(ffca_fca_ctx** out, const ffca_fca_desc* desc);
+/* `iters` EM iterations in place on (v, S); ll_trace as for ffca_iterate,
+ * with L1 (Eq. L1) in place of L2. */
+ffca_status ffca_fca_iterate(ffca_fca_ctx* ctx, int iters, double* ll_trace);
+/* L1 (Eq. L1) of the current state, synchronously. */
+ffca_status ffca_fca_loglik(ffca_fca_ctx* ctx, double* ll);
+/* Matrix inversions and matrix-matrix multiplications performed since
+ * ffca_fca_init, counted as Sec. 3.4 counts them: (J+N)F inversions and 2JNF
+ * multiplications per iteration.  Synchronises. */
+ffca_status ffca_fca_op_counts(ffca_fca_ctx* ctx, unsigned long long* inversions,
+                               unsigned long long* multiplications);
+/* Frequency of the first latched device error (-1 if none). */
+int ffca_fca_error_frequency(const ffca_fca_ctx* ctx);
+void ffca_fca_destroy(ffca_fca_ctx* ctx);
+
 const char* ffca_status_str(ffca_status s);
 
 /* Text of the last CUDA call the library saw fail in the calling thread

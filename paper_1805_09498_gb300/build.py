@@ -2,8 +2,8 @@
 
     python -m paper_1805_09498_gb300.build [--force] [--verbose]
 
-The FastFCA-AS kernel instantiations are split over one translation unit per
-(precision, I) pair so that they compile in parallel.
+The kernel instantiations are split over one translation unit per (method,
+precision, I) so that they compile in parallel.
 """
 from __future__ import annotations
 
@@ -36,11 +36,12 @@ def _nvcc():
 
 def _units():
     """(source, object, extra flags) for every translation unit."""
-    units = [("ffca_api.cu", "ffca_api.o", [])]
-    for prec in (0, 1):
-        for i in I_VALUES:
-            units.append(("ffca_inst.cu", f"ffca_inst_p{prec}_i{i}.o",
-                          [f"-DFFCA_PREC={prec}", f"-DFFCA_I={i}"]))
+    units = [("ffca_api.cu", "ffca_api.o", []), ("ffca_fca_api.cu", "ffca_fca_api.o", [])]
+    for part in (0, 1):  # FastFCA-AS, conventional FCA
+        for prec in (0, 1):
+            for i in I_VALUES:
+                units.append(("ffca_inst.cu", f"ffca_inst_k{part}_p{prec}_i{i}.o",
+                              [f"-DFFCA_PART={part}", f"-DFFCA_PREC={prec}", f"-DFFCA_I={i}"]))
     return units
 
 

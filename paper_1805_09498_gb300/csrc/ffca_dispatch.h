@@ -21,7 +21,20 @@ struct FastKernels {
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.
 const FastKernels* fast_kernels(int prec, int I, int J);
 
-#define FFCA_DECLARE_TABLE(P, I) const FastKernels* fast_kernels_p##P##_i##I(int J);
+// Conventional FCA EM baseline: every kernel takes one FcaArgs by value.
+struct FcaKernels {
+  const void* prep;
+  const void* em_update;
+  const void* em_eval;
+  const void* final_update;
+  const void* final_eval;
+  int params_bytes;  // bytes per frequency of the S_j, S_j^{-1} table
+};
+const FcaKernels* fca_kernels(int prec, int I, int J);
+
+#define FFCA_DECLARE_TABLE(P, I) \
+  const FastKernels* fast_kernels_p##P##_i##I(int J); \
+  const FcaKernels* fca_kernels_p##P##_i##I(int J);
 FFCA_DECLARE_TABLE(0, 1)
 FFCA_DECLARE_TABLE(0, 2)
 FFCA_DECLARE_TABLE(0, 3)

@@ -1,6 +1,8 @@
-// Explicit instantiations of the FastFCA-AS kernels for one precision and
-// one microphone count, J = 1..6.  Compiled once per (FFCA_PREC, FFCA_I).
+// Explicit instantiations of the FastFCA-AS kernels (FFCA_PART 0) or of the
+// conventional FCA kernels (FFCA_PART 1) for one precision and one
+// microphone count, J = 1..6.  Compiled once per (FFCA_PART, FFCA_PREC, FFCA_I).
 #include "ffca_dispatch.h"
+#include "ffca_fca.cuh"
 #include "ffca_stream.cuh"
 
 #ifndef FFCA_PREC
@@ -8,6 +10,9 @@
 #endif
 #ifndef FFCA_I
 #error "FFCA_I must be defined"
+#endif
+#ifndef FFCA_PART
+#error "FFCA_PART must be defined (0 = FastFCA-AS, 1 = FCA)"
 #endif
 
 namespace ffca {
@@ -18,6 +23,7 @@ using Real = double;
 using Real = float;
 #endif
 
+#if FFCA_PART == 0
 template <int J>
 static const FastKernels* table_entry() {
   static const FastKernels k = {
@@ -36,9 +42,28 @@ static const FastKernels* table_entry() {
   return &k;
 }
 
+#endif
+
+#if FFCA_PART == 1
+template <int J>
+static const FcaKernels* fca_entry() {
+  static const FcaKernels k = {
+      (const void*)k_fca_prep<Real, FFCA_I, J>,
+      (const void*)k_fca_em<Real, FFCA_I, J, true>,
+      (const void*)k_fca_em<Real, FFCA_I, J, false>,
+      (const void*)k_fca_final<Real, FFCA_I, J, true>,
+      (const void*)k_fca_final<Real, FFCA_I, J, false>,
+      FcaParams<Real, FFCA_I, J>::BYTES,
+  };
+  return &k;
+}
+
+#endif
+
 #define FFCA_CAT2(a, b, c, d) a##b##c##d
 #define FFCA_CAT(a, b, c, d) FFCA_CAT2(a, b, c, d)
 
+#if FFCA_PART == 0
 const FastKernels* FFCA_CAT(fast_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
   switch (J) {
     case 1: return table_entry<1>();
@@ -50,5 +75,21 @@ const FastKernels* FFCA_CAT(fast_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
     default: return nullptr;
   }
 }
+
+#endif
+
+#if FFCA_PART == 1
+const FcaKernels* FFCA_CAT(fca_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
+  switch (J) {
+    case 1: return fca_entry<1>();
+    case 2: return fca_entry<2>();
+    case 3: return fca_entry<3>();
+    case 4: return fca_entry<4>();
+    case 5: return fca_entry<5>();
+    case 6: return fca_entry<6>();
+    default: return nullptr;
+  }
+}
+#endif
 
 }  // namespace ffca

@@ -44,6 +44,14 @@ class FFCAError(RuntimeError):
         super().__init__(f"{what}: {name}{extra}")
 
 
+class ffca_fca_desc(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int), ("J", ctypes.c_int), ("F", ctypes.c_int),
+                ("N", ctypes.c_int), ("ld", ctypes.c_int), ("prec", ctypes.c_int),
+                ("y", ctypes.c_void_p), ("v", ctypes.c_void_p), ("S", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t),
+                ("stream", ctypes.c_void_p)]
+
+
 class ffca_desc(ctypes.Structure):
     _fields_ = [("I", ctypes.c_int), ("J", ctypes.c_int), ("F", ctypes.c_int),
                 ("N", ctypes.c_int), ("ld", ctypes.c_int), ("K", ctypes.c_int),
@@ -83,6 +91,13 @@ def lib() -> ctypes.CDLL:
         "ffca_timing_read": (ci, [vp, dp, P(ctypes.c_ulonglong)]),
         "ffca_iterate_noalloc": (ci, [P(ffca_desc), ci, dp]),
         "ffca_destroy": (None, [vp]),
+        "ffca_fca_workspace_size": (ctypes.c_size_t, [P(ffca_fca_desc)]),
+        "ffca_fca_init": (ci, [P(vp), P(ffca_fca_desc)]),
+        "ffca_fca_iterate": (ci, [vp, ci, dp]),
+        "ffca_fca_loglik": (ci, [vp, dp]),
+        "ffca_fca_op_counts": (ci, [vp, P(ctypes.c_ulonglong), P(ctypes.c_ulonglong)]),
+        "ffca_fca_error_frequency": (ci, [vp]),
+        "ffca_fca_destroy": (None, [vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
         "ffca_last_error": (ctypes.c_char_p, []),
     }
@@ -198,6 +213,51 @@ def ffca_status_str(status: int) -> str:
     return lib().ffca_status_str(status).decode()
 
 
+# ------------------------------------------------------------ conventional FCA
+def ffca_fca_workspace_size(desc: ffca_fca_desc) -> int:
+    return int(lib().ffca_fca_workspace_size(ctypes.byref(desc)))
+
+
+def ffca_fca_init(desc: ffca_fca_desc) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = lib().ffca_fca_init(ctypes.byref(ctx), ctypes.byref(desc))
+    if st != FFCA_OK:
+        raise FFCAError(st, "ffca_fca_init")
+    return ctx
+
+
+def _check_fca(ctx, st, what):
+    if st != FFCA_OK:
+        raise FFCAError(st, what, lib().ffca_fca_error_frequency(ctx))
+
+
+def ffca_fca_iterate(ctx, iters: int, trace: bool = True):
+    if trace:
+        buf = np.zeros(iters + 1, dtype=np.float64)
+        _check_fca(ctx, lib().ffca_fca_iterate(ctx, iters, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                   "ffca_fca_iterate")
+        return buf
+    _check_fca(ctx, lib().ffca_fca_iterate(ctx, iters, None), "ffca_fca_iterate")
+    return None
+
+
+def ffca_fca_loglik(ctx) -> float:
+    out = ctypes.c_double()
+    _check_fca(ctx, lib().ffca_fca_loglik(ctx, ctypes.byref(out)), "ffca_fca_loglik")
+    return out.value
+
+
+def ffca_fca_op_counts(ctx):
+    inv, mul = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    _check_fca(ctx, lib().ffca_fca_op_counts(ctx, ctypes.byref(inv), ctypes.byref(mul)),
+               "ffca_fca_op_counts")
+    return inv.value, mul.value
+
+
+def ffca_fca_destroy(ctx) -> None:
+    lib().ffca_fca_destroy(ctx)
+
+
 # ------------------------------------------------------------ torch wrapper
 def padded_ld(N: int) -> int:
     """Smallest frame stride the library accepts (>= N, multiple of 4)."""
@@ -299,3 +359,60 @@ def to_device(problem_y, v, lam, P, prec: str = "mixed", device="cuda", ld: int 
     return (yt.to(device), vt.to(device),
             torch.from_numpy(np.ascontiguousarray(lam, dtype=np.float64)).to(device),
             torch.from_numpy(np.ascontiguousarray(P, dtype=np.complex128)).to(device), N)
+
+
+class FCA:
+    """Conventional FCA EM state on one GPU, borrowed from torch tensors.
+
+    y [I, F, ld] complex64 / complex128 (CUDA), v [J, F, ld] float32 / float64
+    (in place), S [F, J, I, I] complex128 Hermitian positive definite (in place).
+    """
+
+    def __init__(self, y, v, S, N: int | None = None, stream=None):
+        import torch
+        if y.dtype == torch.complex64:
+            prec, vdt = FFCA_PREC_MIXED, torch.float32
+        elif y.dtype == torch.complex128:
+            prec, vdt = FFCA_PREC_FP64, torch.float64
+        else:
+            raise TypeError("y must be complex64 or complex128")
+        if v.dtype != vdt or S.dtype != torch.complex128:
+            raise TypeError("dtypes: v matches y's precision, S complex128")
+        I, F, ld = y.shape
+        J = v.shape[0]
+        if v.shape != (J, F, ld) or S.shape != (F, J, I, I):
+            raise ValueError("inconsistent shapes")
+        self.y, self.v, self.S = y, v, S
+        self.N = ld if N is None else int(N)
+        s = stream if stream is not None else torch.cuda.current_stream(y.device)
+        d = ffca_fca_desc(I=I, J=J, F=F, N=self.N, ld=ld, prec=prec, y=y.data_ptr(),
+                          v=v.data_ptr(), S=S.data_ptr(), workspace=None, workspace_bytes=0,
+                          stream=s.cuda_stream)
+        nbytes = ffca_fca_workspace_size(d)
+        if nbytes == 0 and F > 0:
+            raise FFCAError(1, "ffca_fca_workspace_size")
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=y.device)
+        d.workspace = self.workspace.data_ptr()
+        d.workspace_bytes = nbytes
+        self.desc = d
+        self.ctx = ffca_fca_init(d)
+
+    def iterate(self, iters: int, trace: bool = True):
+        return ffca_fca_iterate(self.ctx, iters, trace)
+
+    def loglik(self) -> float:
+        return ffca_fca_loglik(self.ctx)
+
+    def op_counts(self):
+        return ffca_fca_op_counts(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ffca_fca_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
