@@ -118,14 +118,15 @@ ffca_status ffca_loglik(ffca_ctx* ctx, double* ll);
  * out[j][a][f][n] = [P^{-H} diag(v_j lambda_j / sigma) P^H y(n,f)]_a with
  * sigma_i = sum_j v_j lambda_ji.  out: device, [J][I][F][ld] complex of the
  * precision's type, caller-owned; padding frames are written as zero.
- * Enqueued only. */
+ * Enqueued only.  FFCA_ERR_UNSUPPORTED for batch contexts. */
 ffca_status ffca_wiener(ffca_ctx* ctx, void* out);
 
 /* Wait for the context's stream and return the latched device status. */
 ffca_status ffca_sync(ffca_ctx* ctx);
 
 /* Frequency index of the first latched device error (-1 if none); valid
- * after a synchronising call returned an error. */
+ * after a synchronising call returned an error.  For a batch context the
+ * index is that of the problem, m F + f. */
 int ffca_error_frequency(const ffca_ctx* ctx);
 
 /* Number of per-frequency I x I inversions the fixed-point update has
@@ -136,6 +137,7 @@ ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
  * y, v, lambda and P (same layouts as the device arrays; any may be NULL to
  * skip it) from host to the context's device arrays, or v, lambda and P back
  * to host.  Enqueued on the context stream; ffca_download synchronises.
+ * Batch contexts use the batch layouts (rows of ld frames, M F problems).
  * Pinned (page-locked) host memory gives asynchronous, full-speed copies. */
 ffca_status ffca_upload(ffca_ctx* ctx, const void* y_host, const void* v_host,
                         const double* lambda_host, const double* P_host);
@@ -188,6 +190,55 @@ ffca_status ffca_iterate_noalloc(const ffca_desc* desc, int iters, double* ll_tr
 
 /* Release the context (host memory only; the device arrays stay the caller's). */
 void ffca_destroy(ffca_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent mixtures of uneven length (same I, J, F), run by
+ * the same kernels in one launch per pass: every (mixture, frequency) pair is
+ * one problem of the work partition.  The method couples nothing across
+ * frequencies (the log-likelihood of Eq. L2 and every update of Sec. 4 are
+ * per-frequency), so a batch is the same computation as M separate runs;
+ * the trace entry of an iteration is the sum of the M mixtures' L2.
+ * Mixtures are concatenated along the frame axis of y and v: mixture m
+ * occupies frames [frame_offset[m], frame_offset[m+1]) of each
+ * [mic or source][f] row, of which its first N[m] are used.  Parameters are
+ * stacked per mixture. */
+typedef struct {
+  int I, J, F;                    /* as in ffca_desc */
+  int M;                          /* mixtures, >= 1 */
+  int K;                          /* fixed-point sweeps per iteration */
+  int prec;                       /* ffca_precision */
+  const long long* frame_offset;  /* HOST [M+1]: 0 = off[0] <= ... <= off[M] = ld, each a multiple of 4 */
+  const int* N;                   /* HOST [M]: frames of mixture m, 1 <= N[m], round_up(N[m], 4) <= off[m+1] - off[m] */
+  long long ld;                   /* frame stride of the rows = frame_offset[M] (< 2^30) */
+  const void* y;                  /* device [I][F][ld] complex */
+  void* v;                        /* device [J][F][ld] real, in/out */
+  double* lambda;                 /* device [M][F][J][I], in/out */
+  double* P;                      /* device [M][F][I][I] complex128, in/out */
+  void* workspace;                /* ffca_batch_workspace_size() bytes, 256-byte aligned */
+  size_t workspace_bytes;
+  void* stream;                   /* cudaStream_t */
+} ffca_batch_desc;
+
+typedef struct ffca_ctx ffca_batch_ctx;
+
+/* Workspace bytes for the batch on the current device (0 if invalid). */
+size_t ffca_batch_workspace_size(const ffca_batch_desc* desc);
+/* Validate, plan, clear the workspace and upload the per-problem tables
+ * (host arrays are read during the call only; synchronises the stream). */
+ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* desc);
+/* `iters` hybrid iterations of every mixture.  ll_trace: host array of
+ * iters + 1 doubles (L2 summed over the mixtures, as ffca_iterate) or NULL. */
+ffca_status ffca_batch_iterate(ffca_batch_ctx* ctx, int iters, double* ll_trace);
+/* L2 of each mixture's current state into the host array ll[M]; synchronises. */
+ffca_status ffca_batch_loglik(ffca_batch_ctx* ctx, double* ll);
+/* With enable != 0, ffca_iterate / ffca_batch_iterate without a trace replay
+ * the whole launch sequence of the call from a CUDA graph, captured (on a
+ * private stream) on the first call for a given iteration count and
+ * launched on the context stream; per-kernel timing is not recorded for
+ * replays, launch counts are.  Works on single and batch contexts. */
+ffca_status ffca_set_graph(ffca_ctx* ctx, int enable);
+/* Release a batch context (host memory only; the graph, if any). */
+void ffca_batch_destroy(ffca_batch_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
  * Conventional FCA EM (Sec. 3.3 of the paper; the baseline FastFCA-AS is

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "ffca.h"
 #include "ffca_dispatch.h"
@@ -58,6 +59,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Plan {
   Partition pA, pB, pW;
+  size_t off_info, off_ustart, off_msum;  // batch: problem tables, per-mixture sums
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
 };
@@ -79,62 +81,78 @@ ffca_status check_pointers(const ffca_desc* d) {
   return FFCA_OK;
 }
 
-ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
-  int dev = 0, nsm = 0;
+struct Occupancy {
+  int nsm, occA, occB, occW;
+};
+
+// Resident CTAs per SM of the kernels (and the dynamic shared memory they
+// need set on them).
+ffca_status query_occupancy(const FastKernels* k, Occupancy* o) {
+  int dev = 0;
   if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return FFCA_ERR_CUDA;
-  if (!cuda_ok(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute"))
+  if (!cuda_ok(cudaDeviceGetAttribute(&o->nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute"))
     return FFCA_ERR_CUDA;
   // the streaming passes take more than the default 48 KB of dynamic shared memory
   for (const void* fn : {k->estep_update, k->estep_eval, k->wcov})
     if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->stream_smem),
                  "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"))
       return FFCA_ERR_CUDA;
-  int occA = 0, occB = 0, occW = 0;
+  o->occA = o->occB = o->occW = 0;
   const int sthreads = kGroupThreads * k->stream_groups;
-  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occA, k->estep_update, sthreads, k->stream_smem),
+  if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occA, k->estep_update, sthreads, k->stream_smem),
                "occupancy(pass A)") ||
-      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occB, k->wcov, sthreads, k->stream_smem),
+      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occB, k->wcov, sthreads, k->stream_smem),
                "occupancy(pass B)") ||
-      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occW, k->wiener, kBlock, 0), "occupancy(Wiener)"))
+      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occW, k->wiener, kBlock, 0), "occupancy(Wiener)"))
     return FFCA_ERR_CUDA;
-  if (occA < 1 || occB < 1 || occW < 1) {
+  if (o->occA < 1 || o->occB < 1 || o->occW < 1) {
     cudaFuncAttributes fa;
     std::memset(&fa, 0, sizeof(fa));
-    cudaFuncGetAttributes(&fa, occA < 1 ? k->estep_update : k->wcov);
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncGetAttributes(&fa, o->occA < 1 ? k->estep_update : k->wcov);
     std::snprintf(g_last_error, sizeof(g_last_error),
-                  "no resident CTA: occupancy A=%d B=%d W=%d; regs=%d maxThreads=%d static=%zu "
-                  "maxDynamic=%d requested=%d optin=%d",
-                  occA, occB, occW, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
-                  fa.maxDynamicSharedSizeBytes, k->stream_smem, optin);
+                  "no resident CTA: occupancy A=%d B=%d W=%d; regs=%d maxThreads=%d static=%zu requested=%d",
+                  o->occA, o->occB, o->occW, fa.numRegs, fa.maxThreadsPerBlock, fa.sharedSizeBytes,
+                  k->stream_smem);
     return FFCA_ERR_INTERNAL;
   }
+  return FFCA_OK;
+}
+
+// Workspace layout for P problems (partitions already made).
+void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
+  size_t off = kAlign;  // status words, global counters, inversion count
+  p->off_cntA = off; off = align_up(off + sizeof(unsigned) * P);
+  p->off_cntB = off; off = align_up(off + sizeof(unsigned) * P);
+  p->off_logdet = off; off = align_up(off + sizeof(double) * P);
+  p->off_llf = off; off = align_up(off + sizeof(double) * P);
+  p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
+  p->off_pinvH = off; off = align_up(off + sizeof(double) * 2 * I * I * (size_t)P);
+  p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2));
+  p->off_partB = off; off = align_up(off + sizeof(double) * (size_t)P * p->pB.max_slots * I * I * I);
+  p->off_tabA = off; off = align_up(off + (size_t)P * k->params_a_bytes);
+  p->off_tabB = off; off = align_up(off + (size_t)P * k->params_b_bytes);
+  p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)P * J * I);
+  p->off_info = p->off_ustart = p->off_msum = 0;
+  p->bytes = off;
+}
+
+ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
+  Occupancy o;
+  ffca_status st = query_occupancy(k, &o);
+  if (st != FFCA_OK) return st;
   const int FU = d->prec == FFCA_PREC_FP64 ? 1 : 2;
   // vector units per frequency, rounded up to even so that every tile of v
   // starts on a 16-byte boundary (ld % 4 == 0 keeps this inside the row)
   const int Uf = ((d->N + FU - 1) / FU + 1) / 2 * 2;
   const int F = d->F > 0 ? d->F : 1;
   // the streaming partitions count virtual blocks: stream_groups pipelines per CTA
-  p->pA = make_partition(F, Uf, nsm * occA * k->stream_groups * FFCA_GRID_WAVES);
-  p->pB = make_partition(F, Uf, nsm * occB * k->stream_groups * FFCA_GRID_WAVES);
+  p->pA = make_partition(F, Uf, o.nsm * o.occA * k->stream_groups * FFCA_GRID_WAVES, d->N);
+  p->pB = make_partition(F, Uf, o.nsm * o.occB * k->stream_groups * FFCA_GRID_WAVES, d->N);
   // the Wiener pass also covers the padding frames (it writes them as zero)
-  p->pW = make_partition(F, d->ld / FU, nsm * occW);
+  p->pW = make_partition(F, d->ld / FU, o.nsm * o.occW);
   p->pA.F = p->pB.F = p->pW.F = d->F;
-  const int I = d->I, J = d->J;
-  size_t off = kAlign;  // status words, global counters, inversion count
-  p->off_cntA = off; off = align_up(off + sizeof(unsigned) * F);
-  p->off_cntB = off; off = align_up(off + sizeof(unsigned) * F);
-  p->off_logdet = off; off = align_up(off + sizeof(double) * F);
-  p->off_llf = off; off = align_up(off + sizeof(double) * F);
-  p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
-  p->off_pinvH = off; off = align_up(off + sizeof(double) * 2 * I * I * (size_t)F);
-  p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)F * p->pA.max_slots * (J * I + 2));
-  p->off_partB = off; off = align_up(off + sizeof(double) * (size_t)F * p->pB.max_slots * I * I * I);
-  p->off_tabA = off; off = align_up(off + (size_t)F * k->params_a_bytes);
-  p->off_tabB = off; off = align_up(off + (size_t)F * k->params_b_bytes);
-  p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)F * J * I);
-  p->bytes = off;
+  p->pA.Fm = p->pB.Fm = p->pW.Fm = d->F;
+  layout(p, k, F, d->I, d->J);
   return FFCA_OK;
 }
 
@@ -146,9 +164,15 @@ struct TimedLaunch {
 };
 
 struct ffca_ctx {
-  ffca_desc d;
+  ffca_desc d;  // for a batch: F = problems (M F), N unused, ld = concatenated frames
   const FastKernels* kern;
   Plan plan;
+  int M;        // mixtures (1 for the single-mixture API)
+  int Fm;       // frequencies per mixture
+  // CUDA graph of the iteration loop (batch API)
+  int use_graph;
+  int graph_iters;
+  cudaGraphExec_t graph;
   cudaStream_t stream;
   char* ws;
   unsigned* status;
@@ -216,7 +240,7 @@ ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, F
                    size_t smem = 0) {
   void* args[] = {&a};
   TimedLaunch* t = nullptr;
-  if (c->timing) {
+  if (c->timing && !c->use_graph) {
     if (c->ntimed == c->captimed) {
       size_t cap = c->captimed ? 2 * c->captimed : 256;
       void* p = std::realloc(c->timed, cap * sizeof(TimedLaunch));
@@ -279,6 +303,96 @@ ffca_status read_status(ffca_ctx* c) {
 
 }  // namespace
 
+namespace {
+
+// The launches of `iters` iterations without trace copies (capturable).
+ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
+  ffca_status st = launch_prep(c, false);
+  if (st != FFCA_OK) return st;
+  for (int t = 0; t < iters; ++t) {
+    const int slot = t % kTraceCap;
+    FastArgs a = pass_a_args(c, slot);
+    if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, stream_grid(c, a.part), stream_threads(c), a,
+                     c->kern->stream_smem)) != FFCA_OK)
+      return st;
+    FastArgs b = pass_b_args(c, slot);
+    if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
+                     c->kern->stream_smem)) != FFCA_OK)
+      return st;
+    const int G = 32 / c->d.I;  // problems per warp
+    if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b)) != FFCA_OK) return st;
+  }
+  return FFCA_OK;
+}
+
+// Iterations replayed from a CUDA graph of the whole launch sequence,
+// captured on the first call for a given iteration count.
+ffca_status iterate_graph(ffca_ctx* c, int iters) {
+  if (!c->graph || c->graph_iters != iters) {
+    if (c->graph) {
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
+    // capture on a private stream (the legacy default stream cannot be
+    // captured); nothing runs during the capture, so no ordering is needed
+    cudaStream_t cap = nullptr;
+    if (!cuda_ok(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "cudaStreamCreateWithFlags"))
+      return FFCA_ERR_CUDA;
+    if (!cuda_ok(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture")) {
+      cudaStreamDestroy(cap);
+      return FFCA_ERR_CUDA;
+    }
+    const cudaStream_t user = c->stream;
+    c->stream = cap;
+    unsigned long long saved[FFCA_KERNEL_KINDS];
+    std::memcpy(saved, c->launches, sizeof(saved));
+    ffca_status st = enqueue_iterations(c, iters);
+    std::memcpy(c->launches, saved, sizeof(saved));  // captured, not yet run
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cap, &g);
+    c->stream = user;
+    cudaStreamDestroy(cap);
+    if (st != FFCA_OK || !cuda_ok(e, "cudaStreamEndCapture")) {
+      if (g) cudaGraphDestroy(g);
+      return st != FFCA_OK ? st : FFCA_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (!cuda_ok(ei, "cudaGraphInstantiate")) {
+      c->graph = nullptr;
+      return FFCA_ERR_CUDA;
+    }
+    c->graph_iters = iters;
+  }
+  if (!cuda_ok(cudaGraphLaunch(c->graph, c->stream), "cudaGraphLaunch")) return FFCA_ERR_CUDA;
+  c->launches[FFCA_KERNEL_PREP] += 1;
+  c->launches[FFCA_KERNEL_ESTEP] += iters;
+  c->launches[FFCA_KERNEL_WCOV] += iters;
+  c->launches[FFCA_KERNEL_PSOLVE] += iters;
+  return FFCA_OK;
+}
+
+// Per-mixture sums of the per-problem log-likelihoods (block m sums the F
+// problems of mixture m in a fixed order).
+__global__ void k_mixture_sums(const double* llf, int F, double* out) {
+  __shared__ double part[32];
+  const int m = blockIdx.x;
+  double s = 0.0;
+  for (int f = threadIdx.x; f < F; f += blockDim.x) s += __ldcg(llf + (size_t)m * F + f);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < blockDim.x / 32 ? part[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (threadIdx.x == 0) out[m] = t;
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t ffca_workspace_size(const ffca_desc* d) {
@@ -313,6 +427,8 @@ ffca_status ffca_init(ffca_ctx** out, const ffca_desc* d) {
   c->gcntB = reinterpret_cast<unsigned*>(c->ws + 20);
   c->ops = reinterpret_cast<unsigned long long*>(c->ws + 32);
   c->err_f = -1;
+  c->M = 1;
+  c->Fm = d->F;
   if (d->F > 0 && cudaMemsetAsync(c->ws, 0, p.bytes, c->stream) != cudaSuccess) {
     std::free(c);
     return FFCA_ERR_CUDA;
@@ -328,6 +444,7 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
       for (int t = 0; t <= iters; ++t) ll_trace[t] = 0.0;
     return FFCA_OK;
   }
+  if (c->use_graph && !ll_trace) return iterate_graph(c, iters);
   ffca_status st = launch_prep(c, false);
   if (st != FFCA_OK) return st;
   const double* dtrace = reinterpret_cast<const double*>(c->ws + c->plan.off_trace);
@@ -389,6 +506,7 @@ ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
 
 ffca_status ffca_wiener(ffca_ctx* c, void* out) {
   if (!c) return FFCA_ERR_ARG;
+  if (c->plan.off_info) return FFCA_ERR_UNSUPPORTED;  // batch contexts: not provided
   if (c->d.F == 0) return FFCA_OK;
   if (!out || (reinterpret_cast<uintptr_t>(out) % 16) != 0) return FFCA_ERR_ARG;
   ffca_status st = launch_prep(c, true);
@@ -402,6 +520,7 @@ ffca_status ffca_wiener(ffca_ctx* c, void* out) {
 
 ffca_status ffca_wiener_host(ffca_ctx* c, void* out_dev, void* out_host) {
   if (!c || !out_host) return FFCA_ERR_ARG;
+  if (c->plan.off_info) return FFCA_ERR_UNSUPPORTED;
   ffca_status st = ffca_wiener(c, out_dev);
   if (st != FFCA_OK) return st;
   const size_t rsz = c->d.prec == FFCA_PREC_FP64 ? 8 : 4;
@@ -460,8 +579,8 @@ ffca_status ffca_upload(ffca_ctx* c, const void* y_host, const void* v_host, con
   if (!c) return FFCA_ERR_ARG;
   const ffca_desc& d = c->d;
   const size_t rsz = d.prec == FFCA_PREC_FP64 ? 8 : 4;
-  const size_t ybytes = (size_t)d.I * d.F * d.ld * 2 * rsz;
-  const size_t vbytes = (size_t)d.J * d.F * d.ld * rsz;
+  const size_t ybytes = (size_t)d.I * c->Fm * d.ld * 2 * rsz;
+  const size_t vbytes = (size_t)d.J * c->Fm * d.ld * rsz;
   const size_t lbytes = (size_t)d.F * d.J * d.I * sizeof(double);
   const size_t pbytes = (size_t)d.F * d.I * d.I * 2 * sizeof(double);
   auto cp = [&](void* dst, const void* src, size_t n) {
@@ -478,7 +597,7 @@ ffca_status ffca_download(ffca_ctx* c, void* v_host, double* lam_host, double* P
   if (!c) return FFCA_ERR_ARG;
   const ffca_desc& d = c->d;
   const size_t rsz = d.prec == FFCA_PREC_FP64 ? 8 : 4;
-  const size_t vbytes = (size_t)d.J * d.F * d.ld * rsz;
+  const size_t vbytes = (size_t)d.J * c->Fm * d.ld * rsz;
   const size_t lbytes = (size_t)d.F * d.J * d.I * sizeof(double);
   const size_t pbytes = (size_t)d.F * d.I * d.I * 2 * sizeof(double);
   auto cp = [&](void* dst, const void* src, size_t n) {
@@ -492,6 +611,7 @@ ffca_status ffca_download(ffca_ctx* c, void* v_host, double* lam_host, double* P
 
 void ffca_destroy(ffca_ctx* c) {
   if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
   drop_timed(c);
   std::free(c->timed);
   std::free(c);
@@ -592,3 +712,170 @@ extern "C" ffca_status ffca_iterate_noalloc(const ffca_desc* d, int iters, doubl
   if (st != FFCA_OK) return st;
   return read_status(&c);
 }
+
+// ---------------------------------------------------------------------------
+// Batches of mixtures of uneven length: every (mixture, frequency) pair is
+// one problem of the ragged partition; the same kernels run all of them.
+namespace {
+
+ffca_status batch_check(const ffca_batch_desc* d) {
+  if (!d || !d->frame_offset || !d->N) return FFCA_ERR_ARG;
+  if (d->prec != FFCA_PREC_FP64 && d->prec != FFCA_PREC_MIXED) return FFCA_ERR_ARG;
+  if (d->M < 1 || d->F < 1 || d->K < 1 || d->I < 1 || d->J < 1) return FFCA_ERR_ARG;
+  if (d->I > 4 || d->J > 6) return FFCA_ERR_UNSUPPORTED;
+  if (d->frame_offset[0] != 0 || d->ld != d->frame_offset[d->M] || d->ld > (1ll << 30)) return FFCA_ERR_ARG;
+  if ((long long)d->M * d->F > (1ll << 30)) return FFCA_ERR_ARG;
+  for (int m = 0; m < d->M; ++m) {
+    const long long o0 = d->frame_offset[m], o1 = d->frame_offset[m + 1];
+    if (o0 % 4 != 0 || o1 % 4 != 0 || d->N[m] < 1 || (o1 - o0) < (long long)(d->N[m] + 3) / 4 * 4)
+      return FFCA_ERR_ARG;
+  }
+  return FFCA_OK;
+}
+
+ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, std::vector<ProbInfo>* info,
+                       std::vector<long long>* ustart) {
+  Occupancy o;
+  ffca_status st = query_occupancy(k, &o);
+  if (st != FFCA_OK) return st;
+  const int FU = d->prec == FFCA_PREC_FP64 ? 1 : 2;
+  const int P = d->M * d->F;
+  info->resize(P);
+  ustart->resize(P + 1);
+  long long u = 0;
+  for (int m = 0; m < d->M; ++m) {
+    const int Uf = ((d->N[m] + FU - 1) / FU + 1) / 2 * 2;  // even, inside the mixture's padded frames
+    for (int f = 0; f < d->F; ++f) {
+      const int q = m * d->F + f;
+      (*info)[q] = ProbInfo{d->frame_offset[m], f, d->N[m], 1.0 / d->N[m]};
+      (*ustart)[q] = u;
+      u += Uf;
+    }
+  }
+  (*ustart)[P] = u;
+  p->pA = make_partition_ragged(P, d->F, ustart->data(), o.nsm * o.occA * k->stream_groups);
+  p->pB = make_partition_ragged(P, d->F, ustart->data(), o.nsm * o.occB * k->stream_groups);
+  p->pW = make_partition(1, 2, 1);  // unused: the Wiener filter runs per mixture
+  layout(p, k, P, d->I, d->J);
+  size_t off = p->bytes;
+  p->off_info = off; off = align_up(off + sizeof(ProbInfo) * (size_t)P);
+  p->off_ustart = off; off = align_up(off + sizeof(long long) * (size_t)(P + 1));
+  p->off_msum = off; off = align_up(off + sizeof(double) * (size_t)d->M);
+  p->bytes = off;
+  return FFCA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ffca_batch_workspace_size(const ffca_batch_desc* d) {
+  if (batch_check(d) != FFCA_OK) return 0;
+  const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
+  if (!k) return 0;
+  Plan p;
+  std::vector<ProbInfo> info;
+  std::vector<long long> ustart;
+  if (batch_plan(d, k, &p, &info, &ustart) != FFCA_OK) return 0;
+  return p.bytes;
+}
+
+ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* d) {
+  if (!out) return FFCA_ERR_ARG;
+  *out = nullptr;
+  ffca_status st = batch_check(d);
+  if (st != FFCA_OK) return st;
+  auto al = [](const void* q, uintptr_t a) { return q && (reinterpret_cast<uintptr_t>(q) % a) == 0; };
+  if (!al(d->y, 16) || !al(d->v, 16) || !al(d->lambda, 8) || !al(d->P, 16) || !al(d->workspace, kAlign))
+    return FFCA_ERR_ARG;
+  const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
+  if (!k) return FFCA_ERR_UNSUPPORTED;
+  Plan p;
+  std::vector<ProbInfo> info;
+  std::vector<long long> ustart;
+  if ((st = batch_plan(d, k, &p, &info, &ustart)) != FFCA_OK) return st;
+  if (d->workspace_bytes < p.bytes) return FFCA_ERR_ARG;
+  ffca_ctx* c = static_cast<ffca_ctx*>(std::calloc(1, sizeof(ffca_ctx)));
+  if (!c) return FFCA_ERR_INTERNAL;
+  c->d.I = d->I;
+  c->d.J = d->J;
+  c->d.F = d->M * d->F;  // problems
+  c->d.N = 1;            // per-problem frame counts live in the tables
+  c->d.ld = (int)d->ld;
+  c->d.K = d->K;
+  c->d.prec = d->prec;
+  c->d.y = d->y;
+  c->d.v = d->v;
+  c->d.lambda = d->lambda;
+  c->d.P = d->P;
+  c->d.workspace = d->workspace;
+  c->d.workspace_bytes = d->workspace_bytes;
+  c->d.stream = d->stream;
+  c->kern = k;
+  c->plan = p;
+  c->M = d->M;
+  c->Fm = d->F;
+  c->stream = static_cast<cudaStream_t>(d->stream);
+  c->ws = static_cast<char*>(d->workspace);
+  c->status = reinterpret_cast<unsigned*>(c->ws);
+  c->gcntA = reinterpret_cast<unsigned*>(c->ws + 16);
+  c->gcntB = reinterpret_cast<unsigned*>(c->ws + 20);
+  c->ops = reinterpret_cast<unsigned long long*>(c->ws + 32);
+  c->err_f = -1;
+  const ProbInfo* dinfo = reinterpret_cast<const ProbInfo*>(c->ws + p.off_info);
+  const long long* dustart = reinterpret_cast<const long long*>(c->ws + p.off_ustart);
+  for (Partition* q : {&c->plan.pA, &c->plan.pB}) {
+    q->info = dinfo;
+    q->ustart = dustart;
+  }
+  // pageable source: the copies are staged before the calls return
+  if (!cuda_ok(cudaMemsetAsync(c->ws, 0, p.bytes, c->stream), "cudaMemsetAsync") ||
+      !cuda_ok(cudaMemcpyAsync(c->ws + p.off_info, info.data(), sizeof(ProbInfo) * info.size(),
+                               cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync(problems)") ||
+      !cuda_ok(cudaMemcpyAsync(c->ws + p.off_ustart, ustart.data(), sizeof(long long) * ustart.size(),
+                               cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync(unit starts)") ||
+      !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) {
+    std::free(c);
+    return FFCA_ERR_CUDA;
+  }
+  *out = c;
+  return FFCA_OK;
+}
+
+ffca_status ffca_batch_iterate(ffca_batch_ctx* c, int iters, double* ll_trace) {
+  if (!c || c->M < 1) return FFCA_ERR_ARG;
+  return ffca_iterate(c, iters, ll_trace);
+}
+
+ffca_status ffca_batch_loglik(ffca_batch_ctx* c, double* ll) {
+  if (!c || !ll || c->M < 1) return FFCA_ERR_ARG;
+  ffca_status st = launch_prep(c, false);
+  if (st != FFCA_OK) return st;
+  FastArgs a = pass_a_args(c, 0);
+  if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, stream_grid(c, a.part), stream_threads(c), a,
+                   c->kern->stream_smem)) != FFCA_OK)
+    return st;
+  if ((st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) != FFCA_OK)
+    return st;
+  double* msum = reinterpret_cast<double*>(c->ws + c->plan.off_msum);
+  k_mixture_sums<<<c->M, 256, 0, c->stream>>>(a.llf, c->Fm, msum);
+  if (!cuda_ok(cudaGetLastError(), "k_mixture_sums") ||
+      !cuda_ok(cudaMemcpyAsync(ll, msum, sizeof(double) * c->M, cudaMemcpyDeviceToHost, c->stream),
+               "cudaMemcpyAsync"))
+    return FFCA_ERR_CUDA;
+  return read_status(c);
+}
+
+void ffca_batch_destroy(ffca_batch_ctx* c) { ffca_destroy(c); }
+
+ffca_status ffca_set_graph(ffca_ctx* c, int enable) {
+  if (!c) return FFCA_ERR_ARG;
+  c->use_graph = enable ? 1 : 0;
+  if (!enable && c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return FFCA_OK;
+}
+
+}  // extern "C"

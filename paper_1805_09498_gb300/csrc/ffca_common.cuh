@@ -251,41 +251,104 @@ struct ButterflyReduce {
 };
 
 // ------------------------------------------------------------ partition
-// The (f, unit) plane, flattened f-major, is cut into equal contiguous
-// ranges, one per CTA of a grid sized to the resident CTA count.  A CTA walks
-// its range as segments of one frequency each; every frequency gets one
-// partial-sum slot per CTA that touches it.
-struct Partition {
-  int F;             // frequencies
-  int Uf;            // vector units per frequency
-  long long upb;     // units per CTA
-  int nblocks;       // grid size
-  int max_slots;     // max CTAs touching one frequency
-
-  __host__ __device__ inline int first_block(int f) const {
-    return (int)(((long long)f * Uf) / upb);
-  }
-  __host__ __device__ inline int last_block(int f) const {
-    return (int)(((long long)(f + 1) * Uf - 1) / upb);
-  }
-  __host__ __device__ inline int nslots(int f) const { return last_block(f) - first_block(f) + 1; }
+// Work is a list of independent problems, one per (mixture, frequency): the
+// problem's units (16-byte vector units of its frames) are contiguous in the
+// flattened unit space.  A single mixture is the uniform case (problem p =
+// frequency p, every problem N frames and Uf units, no tables); a batch of
+// mixtures of uneven length passes per-problem tables.  The unit space is
+// cut into equal contiguous ranges, one per CTA (or pipeline group) of a
+// grid sized to what is resident at once.  A CTA walks its range as segments
+// of one problem each; every problem gets one partial-sum slot per CTA that
+// touches it.
+struct ProbInfo {
+  long long frame_off;  // first frame of the problem's mixture along the ld axis (multiple of 4)
+  int f;                // frequency: the problem's rows are [mic or source][f]
+  int n;                // frames
+  double inv_n;         // 1 / n
 };
 
-inline Partition make_partition(int F, int Uf, int max_blocks) {
-  Partition p;
-  p.F = F;
-  p.Uf = Uf;
-  long long total = (long long)F * Uf;
+struct Partition {
+  int F;                    // problems
+  int Fm;                   // frequencies per mixture (row addressing)
+  int Uf;                   // uniform case: vector units per problem
+  int N;                    // uniform case: frames per problem
+  double inv_n_uniform;     // uniform case: 1 / N
+  const ProbInfo* info;     // ragged case: [F] (nullptr in the uniform case)
+  const long long* ustart;  // ragged case: [F + 1] first unit of each problem
+  long long total;          // units
+  long long upb;            // units per CTA
+  int nblocks;              // CTAs (pipeline groups) of the grid
+  int max_slots;            // max CTAs touching one problem
+
+  __host__ __device__ inline long long start(int p) const { return ustart ? ustart[p] : (long long)p * Uf; }
+  __host__ __device__ inline int units(int p) const { return (int)(start(p + 1) - start(p)); }
+  __host__ __device__ inline int first_block(int p) const { return (int)(start(p) / upb); }
+  __host__ __device__ inline int last_block(int p) const { return (int)((start(p + 1) - 1) / upb); }
+  __host__ __device__ inline int nslots(int p) const { return last_block(p) - first_block(p) + 1; }
+  __device__ inline int freq(int p) const { return info ? info[p].f : p; }
+  __device__ inline int frames(int p) const { return info ? info[p].n : N; }
+  __device__ inline long long frame_off(int p) const { return info ? info[p].frame_off : 0; }
+  __device__ inline double inv_n(int p) const { return info ? info[p].inv_n : inv_n_uniform; }
+  // the problem that holds unit u (0 <= u < total)
+  __device__ inline int problem_of(long long u) const {
+    if (!ustart) return (int)(u / Uf);
+    int lo = 0, hi = F - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (ustart[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+};
+
+inline void finish_partition(Partition& p, int max_blocks) {
   // at least one full CTA sweep of units per CTA, at most max_blocks CTAs
-  long long want = (total + kBlock - 1) / kBlock;
+  long long want = (p.total + kBlock - 1) / kBlock;
   long long nb = want < max_blocks ? want : max_blocks;
   if (nb < 1) nb = 1;
-  p.upb = (total + nb - 1) / nb;
+  p.upb = (p.total + nb - 1) / nb;
   p.upb = (p.upb + 1) / 2 * 2;  // even: every range starts on a 16-byte boundary of v
-  p.nblocks = (int)((total + p.upb - 1) / p.upb);
+  if (p.upb < 2) p.upb = 2;
+  p.nblocks = (int)((p.total + p.upb - 1) / p.upb);
   if (p.nblocks < 1) p.nblocks = 1;
-  // the range of one frequency spans at most ceil(Uf / upb) + 1 CTAs
+}
+
+// Uniform problems: F of Uf units and N frames each.
+inline Partition make_partition(int F, int Uf, int max_blocks, int N = 0) {
+  Partition p;
+  p.F = F;
+  p.Fm = F;
+  p.Uf = Uf;
+  p.N = N;
+  p.inv_n_uniform = N > 0 ? 1.0 / N : 0.0;
+  p.info = nullptr;
+  p.ustart = nullptr;
+  p.total = (long long)F * Uf;
+  finish_partition(p, max_blocks);
+  // the range of one problem spans at most ceil(Uf / upb) + 1 CTAs
   p.max_slots = (int)((Uf + p.upb - 1) / p.upb + 1);
+  return p;
+}
+
+// Ragged problems: ustart_host [F + 1] (host copy of the unit starts); the
+// device tables are attached by the caller.
+inline Partition make_partition_ragged(int F, int Fm, const long long* ustart_host, int max_blocks) {
+  Partition p;
+  p.F = F;
+  p.Fm = Fm;
+  p.Uf = 0;
+  p.N = 0;
+  p.inv_n_uniform = 0.0;
+  p.info = nullptr;
+  p.ustart = nullptr;
+  p.total = ustart_host[F];
+  finish_partition(p, max_blocks);
+  int ms = 1;
+  for (int q = 0; q < F; ++q) {
+    const int n = (int)((ustart_host[q + 1] - 1) / p.upb - ustart_host[q] / p.upb + 1);
+    if (n > ms) ms = n;
+  }
+  p.max_slots = ms;
   return p;
 }
 

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(32 * kFinalWarps) k_afinal(FastArgs a) {
     const int j = lane / I, i = lane % I;
     const double tot = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, lane);
     double* lp = a.lam + (size_t)f * J * I + lane;
-    const double lnew = *lp * ((double)I * a.inv_n) * tot;
+    const double lnew = *lp * ((double)I * pt.inv_n(f)) * tot;
     if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
     *lp = lnew;
     tab_a<T, I, J>(a, f)->lam[j][i] = (T)lnew;
@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(32 * kFinalWarps) k_afinal(FastArgs a) {
   } else if (lane == NA) {
     const double quad = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, NA);
     const double lg2 = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, NA + 1);
-    const double lf = -(double)I * a.N * kLnPi + (double)a.N * a.logdet[f] - quad - 0.69314718055994530942 * lg2;
+    const int n = pt.frames(f);
+    const double lf = -(double)I * n * kLnPi + (double)n * a.logdet[f] - quad - 0.69314718055994530942 * lg2;
     if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
     a.llf[f] = lf;
     __threadfence();
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
 #pragma unroll
       for (int m = 0; m < I * I; ++m) pk[m] += __ldcg(base + (size_t)k * NV + m);
 #pragma unroll
-    for (int m = 0; m < I * I; ++m) pk[m] *= a.inv_n;
+    for (int m = 0; m < I * I; ++m) pk[m] *= pt.inv_n(f);
     unpack_herm<I>(pk, V);
   }
   bool bad = false;

@@ -222,19 +222,23 @@ struct GroupReduce {
   }
 };
 
-// Walks a CTA's unit range [u0, u1) of the flattened (f, unit) plane as
-// tiles of at most T units that never cross a frequency.
+// Walks a CTA's unit range [u0, u1) of the flattened unit space as tiles of
+// at most T units that never cross a problem: tile (f = problem, k = first
+// unit within the problem, n units).
 struct TileIter {
+  const Partition* pt;
   long long u, u1;
-  int Uf, T;
+  int T;
   int f, k, n;
   bool seg_end;
-  __device__ TileIter(long long u0_, long long u1_, int Uf_, int T_) : u(u0_), u1(u1_), Uf(Uf_), T(T_) {}
+  __device__ TileIter(long long u0_, long long u1_, const Partition& pt_, int T_)
+      : pt(&pt_), u(u0_), u1(u1_), T(T_) {}
   __device__ bool next() {
     if (u >= u1) return false;
-    f = (int)(u / Uf);
-    k = (int)(u - (long long)f * Uf);
-    const int kend = (int)min((long long)Uf, k + (u1 - u));
+    f = pt->problem_of(u);
+    const long long s = pt->start(f);
+    k = (int)(u - s);
+    const int kend = (int)min((long long)pt->units(f), k + (u1 - u));
     n = min(T, kend - k);
     seg_end = (k + n == kend);
     u += n;
@@ -268,7 +272,7 @@ __device__ void finalize_pass_a(const FastArgs& a, int f, ParamsB<T, I, J>* out,
   for (int k = 0; k < ns; ++k)
 #pragma unroll
     for (int q = 0; q < NV; ++q) tot[q] += __ldcg(p + (size_t)k * NV + q);
-  const double scale = (double)I * a.inv_n;
+  const double scale = (double)I * a.part.inv_n(f);
   bool bad = false;
 #pragma unroll
   for (int q = 0; q < NA; ++q) {
@@ -278,7 +282,8 @@ __device__ void finalize_pass_a(const FastArgs& a, int f, ParamsB<T, I, J>* out,
     if (first) a.lam_next[(size_t)f * NA + q] = lnew;
   }
   if (first) {
-    const double lf = -(double)I * a.N * kLnPi + (double)a.N * __ldcg(a.logdet + f) - tot[NA] -
+    const int n = a.part.frames(f);
+    const double lf = -(double)I * n * kLnPi + (double)n * __ldcg(a.logdet + f) - tot[NA] -
                       0.69314718055994530942 * tot[NA + 1];
     bad |= !isfinite(lf);
     a.llf[f] = lf;
@@ -299,7 +304,9 @@ __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long lo
   const char* y = static_cast<const char*>(a.y);
   const char* v = static_cast<const char*>(a.v);
   const char* tab = static_cast<const char*>(a.tabA);
-  TileIter it(u0, u1, a.part.Uf, TC::T);
+  constexpr int FU = Vec<T>::FU;
+  const Partition& pt = a.part;
+  TileIter it(u0, u1, pt, TC::T);
   PB pb;
   int pf = -1;
   int t = 0;
@@ -323,13 +330,15 @@ __device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long lo
       mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB + PA::BYTES));
       bulk_g2s(st + TC::T * TC::UB, tab + (size_t)it.f * PA::BYTES, (unsigned)PA::BYTES, pp.full(s));
     }
+    const int fr = pt.freq(it.f);
+    const long long k = pt.frame_off(it.f) / FU + it.k;  // unit along the row
 #pragma unroll
     for (int m = 0; m < I; ++m)
-      bulk_g2s(st + m * TC::T * 16, y + (((size_t)m * a.F + it.f) * row + it.k) * 16,
-               (unsigned)it.n * 16, pp.full(s));
+      bulk_g2s(st + m * TC::T * 16, y + (((size_t)m * pt.Fm + fr) * row + k) * 16, (unsigned)it.n * 16,
+               pp.full(s));
 #pragma unroll
     for (int j = 0; j < J; ++j)
-      bulk_g2s(st + I * TC::T * 16 + j * TC::T * 8, v + (((size_t)j * a.F + it.f) * row + it.k) * 8,
+      bulk_g2s(st + I * TC::T * 16 + j * TC::T * 8, v + (((size_t)j * pt.Fm + fr) * row + k) * 8,
                (unsigned)it.n * 8, pp.full(s));
     ++t;
   }
@@ -345,7 +354,7 @@ template <int I>
 __device__ void side_logdet(const FastArgs& a, long long u0, long long u1, int vb) {
   const int lane = threadIdx.x & 31;
   const Partition& pt = a.part;
-  const int flo = (int)(u0 / pt.Uf), fhi = (int)((u1 - 1) / pt.Uf);
+  const int flo = pt.problem_of(u0), fhi = pt.problem_of(u1 - 1);
   int nth = 0;
   for (int f = flo; f <= fhi; ++f) {
     if (pt.first_block(f) != vb) continue;
@@ -498,7 +507,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   volatile int* abort = &aborts[rl.group];
   typename Red::Smem& red = red_all[rl.group];
   const Partition pt = a.part;
-  const long long total = (long long)pt.F * pt.Uf;
+  const long long total = pt.total;
   const long long u0 = min((long long)rl.vb * pt.upb, total);
   const long long u1 = min(u0 + pt.upb, total);
   const long long row = a.ld / FU;  // vector units per (mic or source, f) row
@@ -517,7 +526,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   L pre[I][I], pim[I][I], lam[J][I];
   L acc[NV];
 
-  TileIter it(u0, u1, pt.Uf, TC::T);
+  TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
@@ -525,6 +534,8 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
     }
+    const int Np = pt.frames(f);
+    VV* __restrict__ vrow = vg + (size_t)pt.freq(f) * row + pt.frame_off(f) / FU;  // + j Fm row below
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % kStages) * TC::STAGE;
       if (seg_new) {  // this frequency's P and Lambda arrived with the tile
@@ -547,7 +558,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
       for (int q = tid; q < it.n; q += kConsumers) {
         const int k = it.k + q;
         const int n0 = k * FU;
-        if (n0 >= a.N) continue;  // a unit of padding frames only
+        if (n0 >= Np) continue;  // a unit of padding frames only
         L yre[I], yim[I], nyre[I], vv[J];
 #pragma unroll
         for (int m = 0; m < I; ++m) {
@@ -556,7 +567,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         }
 #pragma unroll
         for (int j = 0; j < J; ++j) vv[j] = LN::real(vs[j * TC::T + q]);
-        const bool full = n0 + FU <= a.N;
+        const bool full = n0 + FU <= Np;
         L r[I], e2[I];
         L quad = LN::bc(0), lg = LN::bc(0);
 #pragma unroll
@@ -584,8 +595,8 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           acc[NA] = acc[NA] + quad;
           acc[NA + 1] = acc[NA + 1] + lg;
         } else {
-          acc[NA] = acc[NA] + LN::keep(quad, n0, a.N);
-          acc[NA + 1] = acc[NA + 1] + LN::keep(lg, n0, a.N);
+          acc[NA] = acc[NA] + LN::keep(quad, n0, Np);
+          acc[NA + 1] = acc[NA + 1] + LN::keep(lg, n0, Np);
         }
         if constexpr (UPDATE) {
           L w[I];
@@ -605,11 +616,11 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
             if (full) {
 #pragma unroll
               for (int i = 0; i < I; ++i) acc[j * I + i] = vfma(tj[i], rs, acc[j * I + i]);
-              vg[((size_t)j * pt.F + f) * row + k] = LN::store(vn);
+              vrow[(size_t)j * pt.Fm * row + k] = LN::store(vn);
             } else {
 #pragma unroll
-              for (int i = 0; i < I; ++i) acc[j * I + i] = acc[j * I + i] + LN::keep(tj[i] * rs, n0, a.N);
-              vg[((size_t)j * pt.F + f) * row + k] = LN::store(LN::pick(vn, vv[j], n0, a.N));
+              for (int i = 0; i < I; ++i) acc[j * I + i] = acc[j * I + i] + LN::keep(tj[i] * rs, n0, Np);
+              vrow[(size_t)j * pt.Fm * row + k] = LN::store(LN::pick(vn, vv[j], n0, Np));
             }
           }
         }
@@ -669,7 +680,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   volatile int* abort = &aborts[rl.group];
   typename Red::Smem& red = red_all[rl.group];
   const Partition pt = a.part;
-  const long long total = (long long)pt.F * pt.Uf;
+  const long long total = pt.total;
   const long long u0 = min((long long)rl.vb * pt.upb, total);
   const long long u1 = min(u0 + pt.upb, total);
   const long long row = a.ld / FU;
@@ -684,7 +695,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   L lam[J][I];
   L acc[NV];
 
-  TileIter it(u0, u1, pt.Uf, TC::T);
+  TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
@@ -692,6 +703,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
     }
+    const int Np = pt.frames(f);
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % kStages) * TC::STAGE;
       if (seg_new) {  // the new Lambda(f) arrived with the tile
@@ -707,7 +719,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
       for (int q = tid; q < it.n; q += kConsumers) {
         const int k = it.k + q;
         const int n0 = k * FU;
-        if (n0 >= a.N) continue;
+        if (n0 >= Np) continue;
         L yre[I], yim[I], nyre[I], vv[J];
 #pragma unroll
         for (int m = 0; m < I; ++m) {
@@ -724,14 +736,14 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
           for (int j = 1; j < J; ++j) sg = vfma(vv[j], lam[j][i], sg);
           w[i] = vrcp(sg);
         }
-        if (n0 + FU > a.N) {  // the ragged last unit: drop the frames beyond N
+        if (n0 + FU > Np) {  // the ragged last unit: drop the frames beyond N
 #pragma unroll
-          for (int i = 0; i < I; ++i) w[i] = LN::keep(w[i], n0, a.N);
+          for (int i = 0; i < I; ++i) w[i] = LN::keep(w[i], n0, Np);
 #pragma unroll
           for (int m = 0; m < I; ++m) {
-            yre[m] = LN::keep(yre[m], n0, a.N);
-            yim[m] = LN::keep(yim[m], n0, a.N);
-            nyre[m] = LN::keep(nyre[m], n0, a.N);
+            yre[m] = LN::keep(yre[m], n0, Np);
+            yim[m] = LN::keep(yim[m], n0, Np);
+            nyre[m] = LN::keep(nyre[m], n0, Np);
           }
         }
         L pk[I2];

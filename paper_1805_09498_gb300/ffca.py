@@ -61,6 +61,16 @@ class ffca_desc(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
 
 
+class ffca_batch_desc(ctypes.Structure):
+    _fields_ = [("I", ctypes.c_int), ("J", ctypes.c_int), ("F", ctypes.c_int),
+                ("M", ctypes.c_int), ("K", ctypes.c_int), ("prec", ctypes.c_int),
+                ("frame_offset", ctypes.POINTER(ctypes.c_longlong)),
+                ("N", ctypes.POINTER(ctypes.c_int)), ("ld", ctypes.c_longlong),
+                ("y", ctypes.c_void_p), ("v", ctypes.c_void_p), ("lambda_", ctypes.c_void_p),
+                ("P", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -91,6 +101,12 @@ def lib() -> ctypes.CDLL:
         "ffca_timing_read": (ci, [vp, dp, P(ctypes.c_ulonglong)]),
         "ffca_iterate_noalloc": (ci, [P(ffca_desc), ci, dp]),
         "ffca_destroy": (None, [vp]),
+        "ffca_batch_workspace_size": (ctypes.c_size_t, [P(ffca_batch_desc)]),
+        "ffca_batch_init": (ci, [P(vp), P(ffca_batch_desc)]),
+        "ffca_batch_iterate": (ci, [vp, ci, dp]),
+        "ffca_batch_loglik": (ci, [vp, dp]),
+        "ffca_set_graph": (ci, [vp, ci]),
+        "ffca_batch_destroy": (None, [vp]),
         "ffca_fca_workspace_size": (ctypes.c_size_t, [P(ffca_fca_desc)]),
         "ffca_fca_init": (ci, [P(vp), P(ffca_fca_desc)]),
         "ffca_fca_iterate": (ci, [vp, ci, dp]),
@@ -258,6 +274,42 @@ def ffca_fca_destroy(ctx) -> None:
     lib().ffca_fca_destroy(ctx)
 
 
+def ffca_batch_workspace_size(desc: ffca_batch_desc) -> int:
+    return int(lib().ffca_batch_workspace_size(ctypes.byref(desc)))
+
+
+def ffca_batch_init(desc: ffca_batch_desc) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = lib().ffca_batch_init(ctypes.byref(ctx), ctypes.byref(desc))
+    if st != FFCA_OK:
+        raise FFCAError(st, "ffca_batch_init")
+    return ctx
+
+
+def ffca_batch_iterate(ctx, iters: int, trace: bool = True):
+    """Run `iters` iterations of every mixture; the summed L2 trace or None."""
+    if trace:
+        buf = (ctypes.c_double * (iters + 1))()
+        _check(ctx, lib().ffca_batch_iterate(ctx, iters, buf), "ffca_batch_iterate")
+        return np.frombuffer(buf, dtype=np.float64).copy()
+    _check(ctx, lib().ffca_batch_iterate(ctx, iters, None), "ffca_batch_iterate")
+    return None
+
+
+def ffca_batch_loglik(ctx, M: int) -> np.ndarray:
+    buf = (ctypes.c_double * M)()
+    _check(ctx, lib().ffca_batch_loglik(ctx, buf), "ffca_batch_loglik")
+    return np.frombuffer(buf, dtype=np.float64).copy()
+
+
+def ffca_set_graph(ctx, enable: bool) -> None:
+    _check(ctx, lib().ffca_set_graph(ctx, 1 if enable else 0), "ffca_set_graph")
+
+
+def ffca_batch_destroy(ctx) -> None:
+    lib().ffca_batch_destroy(ctx)
+
+
 # ------------------------------------------------------------ torch wrapper
 def padded_ld(N: int) -> int:
     """Smallest frame stride the library accepts (>= N, multiple of 4)."""
@@ -315,6 +367,10 @@ class FastFCA:
     def iterate(self, iters: int, trace: bool = True):
         return ffca_iterate(self.ctx, iters, trace)
 
+    def set_graph(self, enable: bool = True):
+        """Replay trace-less iterate() calls from a CUDA graph."""
+        ffca_set_graph(self.ctx, enable)
+
     def loglik(self) -> float:
         return ffca_loglik(self.ctx)
 
@@ -359,6 +415,116 @@ def to_device(problem_y, v, lam, P, prec: str = "mixed", device="cuda", ld: int 
     return (yt.to(device), vt.to(device),
             torch.from_numpy(np.ascontiguousarray(lam, dtype=np.float64)).to(device),
             torch.from_numpy(np.ascontiguousarray(P, dtype=np.complex128)).to(device), N)
+
+
+def batch_offsets(Ns) -> np.ndarray:
+    """Frame offsets of mixtures of Ns frames concatenated along a row, each
+    padded to a multiple of 4 (the layout ffca_batch_desc expects)."""
+    off = np.zeros(len(Ns) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([padded_ld(int(n)) for n in Ns])
+    return off
+
+
+def batch_to_device(ys, vs, lams, Ps, prec: str = "mixed", device="cuda", pad_value=None):
+    """Concatenate per-mixture numpy arrays (y [I,F,N_m], v [J,F,N_m],
+    lam [F,J,I], P [F,I,I]) into the batch layout on the device.  Returns
+    (y, v, lam, P, Ns, offsets); padding frames hold pad_value (0 / 1 by
+    default for y / v)."""
+    import torch
+    Ns = [int(y.shape[2]) for y in ys]
+    off = batch_offsets(Ns)
+    I, F = ys[0].shape[:2]
+    J = vs[0].shape[0]
+    ld = int(off[-1])
+    cdt, rdt = (torch.complex64, torch.float32) if prec == "mixed" else (torch.complex128, torch.float64)
+    yt = torch.zeros((I, F, ld), dtype=cdt)
+    vt = torch.ones((J, F, ld), dtype=rdt)
+    if pad_value is not None:
+        yt.fill_(pad_value)
+        vt.fill_(pad_value)
+    for m, (y, v) in enumerate(zip(ys, vs)):
+        o, n = int(off[m]), Ns[m]
+        yt[:, :, o:o + n] = torch.from_numpy(np.ascontiguousarray(y)).to(cdt)
+        vt[:, :, o:o + n] = torch.from_numpy(np.ascontiguousarray(v)).to(rdt)
+    lam = torch.from_numpy(np.ascontiguousarray(np.stack(lams), dtype=np.float64))
+    P = torch.from_numpy(np.ascontiguousarray(np.stack(Ps), dtype=np.complex128))
+    return yt.to(device), vt.to(device), lam.to(device), P.to(device), Ns, off
+
+
+class FastFCABatch:
+    """FastFCA-AS estimation of M independent mixtures of uneven length in
+    one set of launches, borrowed from torch tensors.
+
+    y   [I, F, ld] complex64 / complex128, mixture m in frames
+        [offsets[m], offsets[m+1]) of every row, its first Ns[m] used
+    v   [J, F, ld] real (matching y), updated in place
+    lam [M, F, J, I] float64, P [M, F, I, I] complex128, updated in place
+    """
+
+    def __init__(self, y, v, lam, P, Ns, offsets=None, K: int = 1, stream=None, graph=False):
+        import torch
+        if not y.is_cuda:
+            raise ValueError("FastFCABatch needs CUDA tensors")
+        if y.dtype == torch.complex64:
+            prec, vdt = FFCA_PREC_MIXED, torch.float32
+        elif y.dtype == torch.complex128:
+            prec, vdt = FFCA_PREC_FP64, torch.float64
+        else:
+            raise TypeError("y must be complex64 or complex128")
+        if v.dtype != vdt or lam.dtype != torch.float64 or P.dtype != torch.complex128:
+            raise TypeError("dtypes: v matches y's precision, lam float64, P complex128")
+        for t in (y, v, lam, P):
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+        I, F, ld = y.shape
+        J = v.shape[0]
+        M = len(Ns)
+        if v.shape != (J, F, ld) or lam.shape != (M, F, J, I) or P.shape != (M, F, I, I):
+            raise ValueError("inconsistent shapes")
+        self.I, self.J, self.F, self.M, self.ld = I, J, F, M, ld
+        self.Ns = np.asarray(Ns, dtype=np.int32)
+        self.offsets = batch_offsets(Ns) if offsets is None else np.asarray(offsets, dtype=np.int64)
+        self.y, self.v, self.lam, self.P = y, v, lam, P
+        s = stream if stream is not None else torch.cuda.current_stream(y.device)
+        self.stream = s
+        self._off = (ctypes.c_longlong * (M + 1))(*[int(x) for x in self.offsets])
+        self._n = (ctypes.c_int * M)(*[int(x) for x in self.Ns])
+        d = ffca_batch_desc(I=I, J=J, F=F, M=M, K=K, prec=prec, frame_offset=self._off, N=self._n,
+                            ld=ld, y=y.data_ptr(), v=v.data_ptr(), lambda_=lam.data_ptr(),
+                            P=P.data_ptr(), workspace=None, workspace_bytes=0,
+                            stream=s.cuda_stream)
+        nbytes = ffca_batch_workspace_size(d)
+        if nbytes == 0:
+            raise FFCAError(1, "ffca_batch_workspace_size (invalid batch or CUDA failure: "
+                               + lib().ffca_last_error().decode() + ")")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=y.device)
+        d.workspace = self.workspace.data_ptr()
+        d.workspace_bytes = nbytes
+        self.desc = d
+        self.ctx = ffca_batch_init(d)
+        if graph:
+            ffca_set_graph(self.ctx, True)
+
+    def iterate(self, iters: int, trace: bool = True):
+        return ffca_batch_iterate(self.ctx, iters, trace)
+
+    def loglik(self) -> np.ndarray:
+        """L2 of every mixture (host array of M values)."""
+        return ffca_batch_loglik(self.ctx, self.M)
+
+    def sync(self):
+        ffca_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ffca_batch_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FCA:

@@ -32,7 +32,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "CONFIGS", "cn", "draw_P"]
+__all__ = ["Problem", "make_problem", "batch_lengths", "make_batch", "CONFIGS", "cn", "draw_P"]
 
 
 def cn(rng: np.random.Generator, shape) -> np.ndarray:
@@ -97,6 +97,17 @@ def make_problem(I: int, J: int, F: int, N: int, seed: int, alpha: float = 0.3,
     lam0 = lam * np.exp(0.3 * r2.standard_normal(lam.shape))
     v0 = v * np.exp(0.3 * r2.standard_normal(v.shape))
     return Problem(I, J, F, N, y, v, lam, P, v0, lam0, P0, x)
+
+
+def batch_lengths(M: int, N_min: int, N_max: int, seed: int) -> np.ndarray:
+    """M mixture lengths drawn uniformly from the integers [N_min, N_max]."""
+    return np.random.default_rng(seed).integers(N_min, N_max + 1, size=M)
+
+
+def make_batch(I: int, J: int, F: int, Ns, seed: int, alpha: float = 0.3,
+               kappa: float = 10.0) -> list[Problem]:
+    """Independent mixtures of lengths Ns; mixture m is make_problem(seed + 7919 m)."""
+    return [make_problem(I, J, F, int(n), seed + 7919 * m, alpha, kappa) for m, n in enumerate(Ns)]
 
 
 # Workloads: sizes, value distributions and precision of each measured case.
