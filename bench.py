@@ -29,7 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1805_09498_gb300.synth import CONFIGS, make_problem  # noqa: E402
+from paper_1805_09498_gb300.synth import (CONFIGS, batch_lengths, make_batch_device,  # noqa: E402
+                                          make_problem)
 
 METRIC = "FastFCA-AS TF-point-iters/s (FP32+FP64 vs FP64 plain) and HBM roofline frac"
 UNIT = "TF-point-iters/s"
@@ -267,9 +268,12 @@ def run_ours(args, cfg, rank, ws, local, dist):
            "d2h_bytes_per_step": nbytes(o_h) + nbytes(vo_h) + nbytes(lo_h) + nbytes(Po_h)
            + 8 * (iters + 1)}
     est.close()
+    del est, yd, vd, lamd, Pd, out, y_h, v_h, l_h, P_h, o_h, vo_h, lo_h, Po_h
+    torch.cuda.empty_cache()
 
     if rank != 0:
         return None
+    batched = run_batched(args, dev)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean duration
     peaks, peak_src = _peaks()
@@ -314,7 +318,114 @@ def run_ours(args, cfg, rank, ws, local, dist):
         "speedup_mixed_vs_fp64_gpu": (value / ws / fp64["value"]) if fp64 else None,
         "fca_gpu": fca_line,
         "speedup_vs_fca_gpu": (value / ws / fca_line["value"]) if fca_line else None,
+        "batched": batched,
     }
+
+
+def run_batched(args, dev):
+    """The batched workload: 256 mixtures of uneven length (I = 4, J = 3,
+    F = 257, N uniform in [200, 4000]), complex64, 20 iterations, run as one
+    batch (one launch per pass, the iteration loop replayed from a CUDA
+    graph) and, as the comparison, as 256 sequential plain-FP64 runs of the
+    single-mixture API on the same data.  Both timed with CUDA events."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    cfg = CONFIGS["batched"]
+    I, J, F, M, iters = cfg["I"], cfg["J"], cfg["F"], cfg["M"], cfg["iters"]
+    Ns = batch_lengths(M, cfg["N_min"], cfg["N_max"], seed=17)
+    y, v, lam, P, Ns, off = make_batch_device(I, J, F, Ns, seed=23, device=dev, alpha=cfg["alpha"],
+                                              kappa=cfg["kappa"])
+    v_init, lam_init, P_init = v.clone(), lam.clone(), P.clone()
+    units = int(np.sum(Ns)) * F * iters
+    stream = torch.cuda.current_stream(dev)
+    est = ffca.FastFCABatch(y, v, lam, P, Ns, graph=True)
+
+    def reset():
+        v.copy_(v_init); lam.copy_(lam_init); P.copy_(P_init)
+
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    for _ in range(max(args.warmup, 3)):
+        est.iterate(iters, trace=False)
+    reps = 5
+    ffca.ffca_timing_read(est.ctx)
+    ms = timed(lambda: est.iterate(iters, trace=False), reps)
+    launches = int(sum(n for _, n in ffca.ffca_timing_read(est.ctx).values())) // reps
+    # per-kernel times from one plain (non-graph) run with event timing
+    ffca.ffca_set_graph(est.ctx, False)
+    ffca.ffca_timing_enable(est.ctx, True)
+    est.iterate(iters, trace=False)
+    kt = ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, False)
+    tf = int(np.sum(Ns)) * F
+    kernels = {}
+    for k, bpt in (("estep", I * 8 + 2 * J * 4), ("wcov", I * 8 + J * 4), ("psolve", 0), ("prep", 0)):
+        kms, kn = kt[k]
+        if kn:
+            kernels[k] = {"launches": kn, "avg_us": kms / kn * 1e3}
+            if bpt:
+                kernels[k]["achieved_gbs"] = bpt * tf / (kms / kn * 1e-3) / 1e9
+    reset()
+    est.iterate(iters, trace=False)
+    ll_b = est.loglik()
+    torch.cuda.synchronize()
+    vb, lb, Pb = v.clone(), lam.clone(), P.clone()
+    est.close()
+
+    # 256 sequential plain-FP64 runs on the same data (FP64 copies of each mixture)
+    runs = []
+    yv, vv0 = ffca.batch_views(y, I, F, off), ffca.batch_views(v_init, J, F, off)
+    for m in range(M):
+        n = int(Ns[m])
+        ym = yv[m].to(torch.complex128).contiguous()
+        vm = vv0[m].to(torch.float64).contiguous()
+        lm, Pm = lam_init[m].clone(), P_init[m].clone()
+        runs.append((ffca.FastFCA(ym, vm, lm, Pm, N=n), ym, vm, lm, Pm, vm.clone()))
+
+    def seq():
+        for r in runs:
+            r[0].iterate(iters, trace=False)
+
+    seq()  # warm-up, then back to the initial state
+    for m, r in enumerate(runs):
+        r[2].copy_(r[5]); r[3].copy_(lam_init[m]); r[4].copy_(P_init[m])
+    ms_seq = timed(seq, 1)
+    # accuracy of the batched mixed-precision result against the FP64 runs
+    e = {"v": 0.0, "lambda": 0.0, "P": 0.0, "loglik_per_point": 0.0}
+    vbv = ffca.batch_views(vb, J, F, off)
+    for m, r in enumerate(runs):
+        n = int(Ns[m])
+        def rel(a_, b_):
+            a_ = a_.reshape(F, -1) if a_.dim() > 1 else a_
+            d = torch.linalg.vector_norm(a_ - b_.reshape(a_.shape), dim=-1)
+            return float((d / torch.linalg.vector_norm(b_.reshape(a_.shape), dim=-1)).max())
+        e["v"] = max(e["v"], rel(vbv[m][:, :, :n].double().permute(1, 0, 2).contiguous(),
+                                 r[2][:, :, :n].permute(1, 0, 2).contiguous()))
+        e["lambda"] = max(e["lambda"], rel(lb[m], r[3]))
+        e["P"] = max(e["P"], rel(Pb[m], r[4]))
+        e["loglik_per_point"] = max(e["loglik_per_point"], abs(ll_b[m] - r[0].loglik()) / (n * F))
+    e["measure"] = ("batched mixed precision vs the sequential FP64 runs, after 20 iterations from "
+                    "the same state; normwise relative error per frequency, max over mixtures")
+    for r in runs:
+        r[0].close()
+    del runs, yv, vv0, vbv, y, v, lam, P, v_init, lam_init, P_init, vb, lb, Pb
+    torch.cuda.empty_cache()
+    return {"workload": f"batched: M={M} mixtures, I={I} J={J} F={F}, N uniform in "
+                        f"[{cfg['N_min']}, {cfg['N_max']}] (total {int(np.sum(Ns))} frames), "
+                        f"c64, {iters} iterations",
+            "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms, "runs_timed": reps,
+            "graph": True, "gpu_launches_per_run": launches, "kernels": kernels,
+            "sequential_fp64": {"value": units / (ms_seq * 1e-3), "unit": UNIT, "ms_total": ms_seq,
+                                "runs": M},
+            "speedup_vs_sequential_fp64": ms_seq / ms, "error_vs_fp64": e}
 
 
 def cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_gpu):

@@ -198,20 +198,21 @@ void ffca_destroy(ffca_ctx* ctx);
  * frequencies (the log-likelihood of Eq. L2 and every update of Sec. 4 are
  * per-frequency), so a batch is the same computation as M separate runs;
  * the trace entry of an iteration is the sum of the M mixtures' L2.
- * Mixtures are concatenated along the frame axis of y and v: mixture m
- * occupies frames [frame_offset[m], frame_offset[m+1]) of each
- * [mic or source][f] row, of which its first N[m] are used.  Parameters are
- * stacked per mixture. */
+ * Mixture-major layout: mixture m has rows of ld_m = frame_offset[m+1] -
+ * frame_offset[m] frames (its first N[m] used); its y block [I][F][ld_m]
+ * starts at element I F frame_offset[m] of y, its v block [J][F][ld_m] at
+ * element J F frame_offset[m] of v, so the blocks of the M mixtures follow
+ * one another.  Parameters are stacked per mixture. */
 typedef struct {
   int I, J, F;                    /* as in ffca_desc */
   int M;                          /* mixtures, >= 1 */
   int K;                          /* fixed-point sweeps per iteration */
   int prec;                       /* ffca_precision */
-  const long long* frame_offset;  /* HOST [M+1]: 0 = off[0] <= ... <= off[M] = ld, each a multiple of 4 */
-  const int* N;                   /* HOST [M]: frames of mixture m, 1 <= N[m], round_up(N[m], 4) <= off[m+1] - off[m] */
-  long long ld;                   /* frame stride of the rows = frame_offset[M] (< 2^30) */
-  const void* y;                  /* device [I][F][ld] complex */
-  void* v;                        /* device [J][F][ld] real, in/out */
+  const long long* frame_offset;  /* HOST [M+1]: 0 = off[0] < ... < off[M] = ld, each a multiple of 4 */
+  const int* N;                   /* HOST [M]: frames of mixture m, 1 <= N[m] <= off[m+1] - off[m] */
+  long long ld;                   /* total row length = frame_offset[M] (< 2^30) */
+  const void* y;                  /* device: M blocks [I][F][ld_m] complex, I F ld elements */
+  void* v;                        /* device: M blocks [J][F][ld_m] real, J F ld elements, in/out */
   double* lambda;                 /* device [M][F][J][I], in/out */
   double* P;                      /* device [M][F][I][I] complex128, in/out */
   void* workspace;                /* ffca_batch_workspace_size() bytes, 256-byte aligned */

@@ -60,6 +60,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Plan {
   Partition pA, pB, pW;
   size_t off_info, off_ustart, off_msum;  // batch: problem tables, per-mixture sums
+  size_t off_bstartA, off_slotsA, off_bstartB, off_slotsB;  // batch: CTA ranges, slots per problem
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
 };
@@ -133,6 +134,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_tabB = off; off = align_up(off + (size_t)P * k->params_b_bytes);
   p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)P * J * I);
   p->off_info = p->off_ustart = p->off_msum = 0;
+  p->off_bstartA = p->off_slotsA = p->off_bstartB = p->off_slotsB = 0;
   p->bytes = off;
 }
 
@@ -316,6 +318,7 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
     FastArgs b = pass_b_args(c, slot);
+    b.trace = nullptr;  // no trace: k_psolve skips the sum over problems
     if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
@@ -457,6 +460,7 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       FastArgs b = pass_b_args(c, slot);
+      if (!ll_trace) b.trace = nullptr;  // k_psolve skips the sum over problems
       if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
@@ -727,40 +731,66 @@ ffca_status batch_check(const ffca_batch_desc* d) {
   if ((long long)d->M * d->F > (1ll << 30)) return FFCA_ERR_ARG;
   for (int m = 0; m < d->M; ++m) {
     const long long o0 = d->frame_offset[m], o1 = d->frame_offset[m + 1];
-    if (o0 % 4 != 0 || o1 % 4 != 0 || d->N[m] < 1 || (o1 - o0) < (long long)(d->N[m] + 3) / 4 * 4)
-      return FFCA_ERR_ARG;
+    if (o0 % 4 != 0 || o1 % 4 != 0 || d->N[m] < 1 || (o1 - o0) < d->N[m]) return FFCA_ERR_ARG;
   }
   return FFCA_OK;
 }
 
-ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, std::vector<ProbInfo>* info,
-                       std::vector<long long>* ustart) {
+// Host copies of a batch's device tables.
+struct BatchTables {
+  std::vector<ProbInfo> info;
+  std::vector<long long> ustart, bstartA, bstartB;
+  std::vector<int2> slotsA, slotsB;
+};
+
+// Fixed cost of a problem segment in a CTA (its reduction and parameter
+// hand-over), in frames of streaming work: the ragged partition balances
+// units + this per problem (measured on GB300 for the batched workload's
+// shapes: about 1.8 us in pass A and 2.6 us in pass B per segment).
+constexpr long long kSegCostFramesA = 1024;
+constexpr long long kSegCostFramesB = 2048;
+
+ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, BatchTables* t) {
   Occupancy o;
   ffca_status st = query_occupancy(k, &o);
   if (st != FFCA_OK) return st;
   const int FU = d->prec == FFCA_PREC_FP64 ? 1 : 2;
   const int P = d->M * d->F;
-  info->resize(P);
-  ustart->resize(P + 1);
+  t->info.resize(P);
+  t->ustart.resize(P + 1);
   long long u = 0;
   for (int m = 0; m < d->M; ++m) {
     const int Uf = ((d->N[m] + FU - 1) / FU + 1) / 2 * 2;  // even, inside the mixture's padded frames
     for (int f = 0; f < d->F; ++f) {
       const int q = m * d->F + f;
-      (*info)[q] = ProbInfo{d->frame_offset[m], f, d->N[m], 1.0 / d->N[m]};
-      (*ustart)[q] = u;
+      t->info[q] = ProbInfo{d->frame_offset[m], f, d->N[m], 1.0 / d->N[m],
+                            (int)(d->frame_offset[m + 1] - d->frame_offset[m])};
+      t->ustart[q] = u;
       u += Uf;
     }
   }
-  (*ustart)[P] = u;
-  p->pA = make_partition_ragged(P, d->F, ustart->data(), o.nsm * o.occA * k->stream_groups);
-  p->pB = make_partition_ragged(P, d->F, ustart->data(), o.nsm * o.occB * k->stream_groups);
+  t->ustart[P] = u;
+  const int maxA = o.nsm * o.occA * k->stream_groups, maxB = o.nsm * o.occB * k->stream_groups;
+  t->bstartA.resize(maxA + 1);
+  t->bstartB.resize(maxB + 1);
+  t->slotsA.resize(P);
+  t->slotsB.resize(P);
+  p->pA = make_partition_ragged(P, d->F, t->ustart.data(), maxA, kSegCostFramesA / FU, t->bstartA.data(),
+                                t->slotsA.data());
+  p->pB = make_partition_ragged(P, d->F, t->ustart.data(), maxB, kSegCostFramesB / FU, t->bstartB.data(),
+                                t->slotsB.data());
+  t->bstartA.resize(p->pA.nblocks + 1);
+  t->bstartB.resize(p->pB.nblocks + 1);
   p->pW = make_partition(1, 2, 1);  // unused: the Wiener filter runs per mixture
   layout(p, k, P, d->I, d->J);
   size_t off = p->bytes;
   p->off_info = off; off = align_up(off + sizeof(ProbInfo) * (size_t)P);
   p->off_ustart = off; off = align_up(off + sizeof(long long) * (size_t)(P + 1));
   p->off_msum = off; off = align_up(off + sizeof(double) * (size_t)d->M);
+  p->off_bstartA = off; off = align_up(off + sizeof(long long) * t->bstartA.size());
+  p->off_bstartB = off; off = align_up(off + sizeof(long long) * t->bstartB.size());
+  p->off_slotsA = off; off = align_up(off + sizeof(int2) * (size_t)P);
+  p->off_slotsB = off; off = align_up(off + sizeof(int2) * (size_t)P);
   p->bytes = off;
   return FFCA_OK;
 }
@@ -774,9 +804,8 @@ size_t ffca_batch_workspace_size(const ffca_batch_desc* d) {
   const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
   if (!k) return 0;
   Plan p;
-  std::vector<ProbInfo> info;
-  std::vector<long long> ustart;
-  if (batch_plan(d, k, &p, &info, &ustart) != FFCA_OK) return 0;
+  BatchTables t;
+  if (batch_plan(d, k, &p, &t) != FFCA_OK) return 0;
   return p.bytes;
 }
 
@@ -791,9 +820,8 @@ ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* d) {
   const FastKernels* k = fast_kernels(d->prec, d->I, d->J);
   if (!k) return FFCA_ERR_UNSUPPORTED;
   Plan p;
-  std::vector<ProbInfo> info;
-  std::vector<long long> ustart;
-  if ((st = batch_plan(d, k, &p, &info, &ustart)) != FFCA_OK) return st;
+  BatchTables t;
+  if ((st = batch_plan(d, k, &p, &t)) != FFCA_OK) return st;
   if (d->workspace_bytes < p.bytes) return FFCA_ERR_ARG;
   ffca_ctx* c = static_cast<ffca_ctx*>(std::calloc(1, sizeof(ffca_ctx)));
   if (!c) return FFCA_ERR_INTERNAL;
@@ -828,12 +856,21 @@ ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* d) {
     q->info = dinfo;
     q->ustart = dustart;
   }
-  // pageable source: the copies are staged before the calls return
+  c->plan.pA.bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartA);
+  c->plan.pB.bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartB);
+  c->plan.pA.slots = reinterpret_cast<const int2*>(c->ws + p.off_slotsA);
+  c->plan.pB.slots = reinterpret_cast<const int2*>(c->ws + p.off_slotsB);
+  auto up = [&](size_t off, const void* src, size_t n, const char* what) {
+    return cuda_ok(cudaMemcpyAsync(c->ws + off, src, n, cudaMemcpyHostToDevice, c->stream), what);
+  };
+  // pageable sources: the copies are staged before the calls return
   if (!cuda_ok(cudaMemsetAsync(c->ws, 0, p.bytes, c->stream), "cudaMemsetAsync") ||
-      !cuda_ok(cudaMemcpyAsync(c->ws + p.off_info, info.data(), sizeof(ProbInfo) * info.size(),
-                               cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync(problems)") ||
-      !cuda_ok(cudaMemcpyAsync(c->ws + p.off_ustart, ustart.data(), sizeof(long long) * ustart.size(),
-                               cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync(unit starts)") ||
+      !up(p.off_info, t.info.data(), sizeof(ProbInfo) * t.info.size(), "cudaMemcpyAsync(problems)") ||
+      !up(p.off_ustart, t.ustart.data(), sizeof(long long) * t.ustart.size(), "cudaMemcpyAsync(unit starts)") ||
+      !up(p.off_bstartA, t.bstartA.data(), sizeof(long long) * t.bstartA.size(), "cudaMemcpyAsync(ranges A)") ||
+      !up(p.off_bstartB, t.bstartB.data(), sizeof(long long) * t.bstartB.size(), "cudaMemcpyAsync(ranges B)") ||
+      !up(p.off_slotsA, t.slotsA.data(), sizeof(int2) * t.slotsA.size(), "cudaMemcpyAsync(slots A)") ||
+      !up(p.off_slotsB, t.slotsB.data(), sizeof(int2) * t.slotsB.size(), "cudaMemcpyAsync(slots B)") ||
       !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) {
     std::free(c);
     return FFCA_ERR_CUDA;

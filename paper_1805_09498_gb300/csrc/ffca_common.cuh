@@ -33,24 +33,24 @@ struct cpx {
 template <typename T>
 __host__ __device__ inline cpx<T> mk(T re, T im) { return cpx<T>{re, im}; }
 template <typename T>
-__device__ inline cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ inline cpx<T> cadd(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
 template <typename T>
-__device__ inline cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ inline cpx<T> csub(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
 template <typename T>
-__device__ inline cpx<T> cmul(cpx<T> a, cpx<T> b) {
+__host__ __device__ inline cpx<T> cmul(cpx<T> a, cpx<T> b) {
   return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
 }
 // conj(a) * b
 template <typename T>
-__device__ inline cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+__host__ __device__ inline cpx<T> cmulc(cpx<T> a, cpx<T> b) {
   return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
 }
 template <typename T>
-__device__ inline cpx<T> cconj(cpx<T> a) { return {a.re, -a.im}; }
+__host__ __device__ inline cpx<T> cconj(cpx<T> a) { return {a.re, -a.im}; }
 template <typename T>
-__device__ inline cpx<T> cscale(cpx<T> a, T s) { return {a.re * s, a.im * s}; }
+__host__ __device__ inline cpx<T> cscale(cpx<T> a, T s) { return {a.re * s, a.im * s}; }
 template <typename T>
-__device__ inline T cabs2(cpx<T> a) { return a.re * a.re + a.im * a.im; }
+__host__ __device__ inline T cabs2(cpx<T> a) { return a.re * a.re + a.im * a.im; }
 // acc += conj(a) * b
 template <typename T>
 __device__ inline void cfmac(cpx<T>& acc, cpx<T> a, cpx<T> b) {
@@ -261,10 +261,13 @@ struct ButterflyReduce {
 // of one problem each; every problem gets one partial-sum slot per CTA that
 // touches it.
 struct ProbInfo {
-  long long frame_off;  // first frame of the problem's mixture along the ld axis (multiple of 4)
-  int f;                // frequency: the problem's rows are [mic or source][f]
+  long long frame_off;  // sum of the row lengths of the earlier mixtures (multiple of 4): the
+                        // mixture's y block [I][Fm][ld] starts at frame I Fm frame_off, its v
+                        // block [J][Fm][ld] at J Fm frame_off
+  int f;                // frequency: the problem's rows are [mic or source][f] of its block
   int n;                // frames
   double inv_n;         // 1 / n
+  int ld;               // row length of the mixture's blocks (multiple of 4, >= n)
 };
 
 struct Partition {
@@ -275,19 +278,29 @@ struct Partition {
   double inv_n_uniform;     // uniform case: 1 / N
   const ProbInfo* info;     // ragged case: [F] (nullptr in the uniform case)
   const long long* ustart;  // ragged case: [F + 1] first unit of each problem
+  const long long* bstart;  // ragged case: [nblocks + 1] first unit of each CTA's range
+  const int2* slots;        // ragged case: [F] (first CTA, CTAs) touching each problem
   long long total;          // units
-  long long upb;            // units per CTA
+  long long upb;            // uniform case: units per CTA
   int nblocks;              // CTAs (pipeline groups) of the grid
   int max_slots;            // max CTAs touching one problem
 
   __host__ __device__ inline long long start(int p) const { return ustart ? ustart[p] : (long long)p * Uf; }
   __host__ __device__ inline int units(int p) const { return (int)(start(p + 1) - start(p)); }
-  __host__ __device__ inline int first_block(int p) const { return (int)(start(p) / upb); }
-  __host__ __device__ inline int last_block(int p) const { return (int)((start(p + 1) - 1) / upb); }
-  __host__ __device__ inline int nslots(int p) const { return last_block(p) - first_block(p) + 1; }
+  // the unit range [block_start(b), block_start(b + 1)) of CTA b (empty for b >= nblocks)
+  __device__ inline long long block_start(int b) const {
+    if (b >= nblocks) return total;
+    return bstart ? bstart[b] : min((long long)b * upb, total);
+  }
+  __device__ inline int first_block(int p) const { return slots ? slots[p].x : (int)(start(p) / upb); }
+  __device__ inline int nslots(int p) const {
+    return slots ? slots[p].y : (int)((start(p + 1) - 1) / upb) - (int)(start(p) / upb) + 1;
+  }
   __device__ inline int freq(int p) const { return info ? info[p].f : p; }
   __device__ inline int frames(int p) const { return info ? info[p].n : N; }
   __device__ inline long long frame_off(int p) const { return info ? info[p].frame_off : 0; }
+  // row length (frames) of problem p's blocks; ld_uniform in the uniform case
+  __device__ inline long long row_len(int p, long long ld_uniform) const { return info ? info[p].ld : ld_uniform; }
   __device__ inline double inv_n(int p) const { return info ? info[p].inv_n : inv_n_uniform; }
   // the problem that holds unit u (0 <= u < total)
   __device__ inline int problem_of(long long u) const {
@@ -323,6 +336,8 @@ inline Partition make_partition(int F, int Uf, int max_blocks, int N = 0) {
   p.inv_n_uniform = N > 0 ? 1.0 / N : 0.0;
   p.info = nullptr;
   p.ustart = nullptr;
+  p.bstart = nullptr;
+  p.slots = nullptr;
   p.total = (long long)F * Uf;
   finish_partition(p, max_blocks);
   // the range of one problem spans at most ceil(Uf / upb) + 1 CTAs
@@ -330,9 +345,14 @@ inline Partition make_partition(int F, int Uf, int max_blocks, int N = 0) {
   return p;
 }
 
-// Ragged problems: ustart_host [F + 1] (host copy of the unit starts); the
-// device tables are attached by the caller.
-inline Partition make_partition_ragged(int F, int Fm, const long long* ustart_host, int max_blocks) {
+// Ragged problems: ustart_host [F + 1] (host copy of the unit starts).  A
+// CTA's time is its units plus a fixed cost per problem it touches (the
+// segment's reduction and parameter hand-over), so the CTA ranges balance
+// cost = units + seg_cost per problem, not units alone: a run of short
+// problems gets fewer units.  Fills bstart_host [nblocks + 1] and
+// slots_host [F]; the device copies are attached by the caller.
+inline Partition make_partition_ragged(int F, int Fm, const long long* ustart_host, int max_blocks,
+                                       long long seg_cost, long long* bstart_host, int2* slots_host) {
   Partition p;
   p.F = F;
   p.Fm = Fm;
@@ -341,12 +361,35 @@ inline Partition make_partition_ragged(int F, int Fm, const long long* ustart_ho
   p.inv_n_uniform = 0.0;
   p.info = nullptr;
   p.ustart = nullptr;
+  p.bstart = nullptr;
+  p.slots = nullptr;
   p.total = ustart_host[F];
   finish_partition(p, max_blocks);
-  int ms = 1;
-  for (int q = 0; q < F; ++q) {
-    const int n = (int)((ustart_host[q + 1] - 1) / p.upb - ustart_host[q] / p.upb + 1);
-    if (n > ms) ms = n;
+  const int nb = p.nblocks;
+  // boundaries at equal steps of the cumulative cost, rounded down to even
+  // units, strictly increasing (every range non-empty)
+  const double C = (double)p.total + (double)seg_cost * F;
+  bstart_host[0] = 0;
+  int q = 0;
+  for (int b = 1; b < nb; ++b) {
+    const double x = C * b / nb;
+    while (q + 1 < F && (double)ustart_host[q + 1] + (double)seg_cost * (q + 1) <= x) ++q;
+    const double within = x - ((double)ustart_host[q] + (double)seg_cost * q) - (double)seg_cost;
+    long long u = ustart_host[q] + (within > 0.0 ? (long long)within : 0);
+    if (u > ustart_host[q + 1]) u = ustart_host[q + 1];
+    u = u / 2 * 2;
+    const long long lo = bstart_host[b - 1] + 2, hi = p.total - 2LL * (nb - b);
+    bstart_host[b] = u < lo ? lo : (u > hi ? hi : u);
+  }
+  bstart_host[nb] = p.total;
+  // first CTA and number of CTAs touching each problem
+  int b = 0, ms = 1;
+  for (int r = 0; r < F; ++r) {
+    while (bstart_host[b + 1] <= ustart_host[r]) ++b;
+    int e = b;
+    while (bstart_host[e + 1] < ustart_host[r + 1]) ++e;
+    slots_host[r] = make_int2(b, e - b + 1);
+    if (e - b + 1 > ms) ms = e - b + 1;
   }
   p.max_slots = ms;
   return p;
@@ -378,7 +421,7 @@ __device__ inline bool arrive_last(unsigned* counter, unsigned expected, int* fl
 // Determinant of the (I-1) x (I-1) minor of the complex I x I matrix A that
 // leaves out row r and column c (I <= 4).
 template <int I>
-__device__ inline cpx<double> minor_det(const cpx<double> (&A)[I][I], int r, int c) {
+__host__ __device__ inline cpx<double> minor_det(const cpx<double> (&A)[I][I], int r, int c) {
   if constexpr (I == 1) {
     return mk(1.0, 0.0);
   } else {
@@ -406,7 +449,7 @@ __device__ inline cpx<double> minor_det(const cpx<double> (&A)[I][I], int r, int
 // determinant along column i gives det A = sum_r A_ri C_ri, and row i of the
 // inverse is (A^{-1})_ir = C_ri / det A.
 template <int I>
-__device__ inline cpx<double> column_cofactors(const cpx<double> (&A)[I][I], int i, cpx<double> (&C)[I]) {
+__host__ __device__ inline cpx<double> column_cofactors(const cpx<double> (&A)[I][I], int i, cpx<double> (&C)[I]) {
   cpx<double> det = mk(0.0, 0.0);
 #pragma unroll
   for (int r = 0; r < I; ++r) {
@@ -417,22 +460,95 @@ __device__ inline cpx<double> column_cofactors(const cpx<double> (&A)[I][I], int
   return det;
 }
 
-// Determinant and full cofactor matrix of a complex I x I matrix with
-// compile-time indexing only (registers, no local memory): det A by the first
-// row, C_rc = (-1)^(r+c) minor_rc.  A^{-1} = C^T / det A.
-template <int I>
-__device__ inline cpx<double> cofactors(const cpx<double> (&A)[I][I], cpx<double> (&C)[I][I]) {
+// 2 x 2 minors of the row pair (r0, r1) of a complex 4 x 4 matrix, for the
+// six column pairs in the order (0,1) (0,2) (0,3) (1,2) (1,3) (2,3).
+__host__ __device__ inline void pair_minors4(const cpx<double> (&A)[4][4], int r0, int r1, cpx<double> (&m)[6]) {
+  int k = 0;
 #pragma unroll
-  for (int r = 0; r < I; ++r)
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = p + 1; q < 4; ++q) m[k++] = csub(cmul(A[r0][p], A[r1][q]), cmul(A[r0][q], A[r1][p]));
+}
+// index of the column pair (p, q), p < q, in that order
+__host__ __device__ constexpr int pair_index4(int p, int q) { return p == 0 ? q - 1 : (p == 1 ? q + 1 : 5); }
+
+// Determinant and full cofactor matrix of a complex I x I matrix with
+// compile-time indexing only (registers, no local memory), C_rc =
+// (-1)^(r+c) minor_rc, so that A^{-1} = C^T / det A.  I <= 3: every minor
+// directly.  I = 4: Laplace expansion by the row pairs (0,1) and (2,3): with
+// s the 2 x 2 minors of rows 0-1 and t those of rows 2-3, the 3 x 3 minor
+// leaving out row r and column c (other columns p < q < w) expands along the
+// remaining row of the other pair, e.g. minor_0c = A_1p t_qw - A_1q t_pw +
+// A_1w t_pq, and det A = sum over complementary column pairs of
+// +-s_pq t_(rest); 12 + 48 + 6 complex products instead of 16 separate 3 x 3
+// determinants.
+template <int I>
+__host__ __device__ inline cpx<double> cofactors(const cpx<double> (&A)[I][I], cpx<double> (&C)[I][I]) {
+  if constexpr (I == 4) {
+    cpx<double> s[6], t[6];
+    pair_minors4(A, 0, 1, s);
+    pair_minors4(A, 2, 3, t);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int p = c == 0 ? 1 : 0, q = c <= 1 ? 2 : 1, w = c == 3 ? 2 : 3;  // the other columns
+      const int iqw = pair_index4(q, w), ipw = pair_index4(p, w), ipq = pair_index4(p, q);
+      // rows 0 / 1 left out: expand along row 1 / 0 with the bottom minors
+      // rows 2 / 3 left out: expand along row 3 / 2 with the top minors
+      const int src[4] = {1, 0, 3, 2};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const cpx<double>* m = r < 2 ? t : s;
+        const int b = src[r];
+        cpx<double> d = cmul(A[b][p], m[iqw]);
+        d = csub(d, cmul(A[b][q], m[ipw]));
+        d = cadd(d, cmul(A[b][w], m[ipq]));
+        C[r][c] = ((r + c) & 1) ? mk(-d.re, -d.im) : d;
+      }
+    }
+    // det = s01 t23 - s02 t13 + s03 t12 + s12 t03 - s13 t02 + s23 t01
+    cpx<double> det = cmul(s[0], t[5]);
+    det = csub(det, cmul(s[1], t[4]));
+    det = cadd(det, cmul(s[2], t[3]));
+    det = cadd(det, cmul(s[3], t[2]));
+    det = csub(det, cmul(s[4], t[1]));
+    return cadd(det, cmul(s[5], t[0]));
+  } else {
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c) {
+        const cpx<double> m = minor_det<I>(A, r, c);
+        C[r][c] = ((r + c) & 1) ? mk(-m.re, -m.im) : m;
+      }
+    cpx<double> det = mk(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < I; ++c) det = cadd(det, cmul(A[0][c], C[0][c]));
+    return det;
+  }
+}
+
+// Determinant alone (the same expansions).
+template <int I>
+__host__ __device__ inline cpx<double> determinant(const cpx<double> (&A)[I][I]) {
+  if constexpr (I == 4) {
+    cpx<double> s[6], t[6];
+    pair_minors4(A, 0, 1, s);
+    pair_minors4(A, 2, 3, t);
+    cpx<double> det = cmul(s[0], t[5]);
+    det = csub(det, cmul(s[1], t[4]));
+    det = cadd(det, cmul(s[2], t[3]));
+    det = cadd(det, cmul(s[3], t[2]));
+    det = csub(det, cmul(s[4], t[1]));
+    return cadd(det, cmul(s[5], t[0]));
+  } else {
+    cpx<double> det = mk(0.0, 0.0);
 #pragma unroll
     for (int c = 0; c < I; ++c) {
-      const cpx<double> m = minor_det<I>(A, r, c);
-      C[r][c] = ((r + c) & 1) ? mk(-m.re, -m.im) : m;
+      const cpx<double> m = minor_det<I>(A, 0, c);
+      det = cadd(det, cmul(A[0][c], (c & 1) ? mk(-m.re, -m.im) : m));
     }
-  cpx<double> det = mk(0.0, 0.0);
-#pragma unroll
-  for (int c = 0; c < I; ++c) det = cadd(det, cmul(A[0][c], C[0][c]));
-  return det;
+    return det;
+  }
 }
 
 // Relative threshold below which a positive definite determinant or pivot is

@@ -109,17 +109,19 @@ __device__ inline double sum_slots(const double* part_buf, int f, int nslots, in
 }
 
 // Sum of the per-frequency log-likelihoods in a fixed order (one warp; each
-// lane keeps four running sums so that four loads are in flight at a time)
+// lane keeps eight running sums so that eight loads are in flight at a time)
 // into the trace slot.
 __device__ inline void finalize_trace(const FastArgs& a) {
   const int lane = threadIdx.x & 31;
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int f = lane; f < a.F; f += 128) {
+  double s[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u) s[u] = 0.0;
+  for (int f = lane; f < a.F; f += 256) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
       if (f + 32 * u < a.F) s[u] += __ldcg(a.llf + f + 32 * u);
   }
-  double t = (s[0] + s[1]) + (s[2] + s[3]);
+  double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
   if (lane == 0) a.trace[a.trace_slot] = t;
@@ -222,9 +224,11 @@ __device__ inline void gather_columns(const cpx<double> (&col)[I], int g, cpx<do
 // the same P^{-H}) into P and the pass-A table; finally the last warp adds
 // the frequencies' log-likelihoods (also written during pass B) into the
 // trace.  FP64 latency on this part is long (an FMA ~64 cycles, a division
-// ~350), so the kernel keeps its dependency chains short: no log (pass A
-// computes ln|det P|^2 on the side), the inverses by cofactors (independent,
-// shallow products) with one division per sweep, register-only indexing.
+// ~350) and its throughput low, so the kernel keeps its dependency chains
+// short and its operation count small: the inverses by cofactors
+// (independent, shallow products; 4 x 4 through shared 2 x 2 minors) with one
+// division per sweep, register-only indexing.  It ends with ln|det P|^2 of
+// the new P, which the next iteration's L2 needs (Eq. L2).
 template <typename T, int I, int J>
 __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
   constexpr int G = Lanes<I>::G;
@@ -328,7 +332,12 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
       ta->pim[r][i] = (T)ari.im;
     }
     if (singular) raise_status(a.status, kDevSingular, f);
-    if (i == 0) atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
+    if (i == 0) {
+      atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
+      const double d2 = cabs2(determinant<I>(A));
+      if (!(d2 > 0.0) || !isfinite(d2)) raise_status(a.status, kDevSingular, f);
+      a.logdet[f] = log(d2);
+    }
   }
   // the trace: the last warp adds the per-frequency log-likelihoods
   if (a.trace) {

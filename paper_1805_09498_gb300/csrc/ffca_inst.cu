@@ -27,7 +27,7 @@ using Real = float;
 template <int J>
 static const FastKernels* table_entry() {
   static const FastKernels k = {
-      StreamGroups<Real, FFCA_I, J>::value * Tile<FFCA_I, J>::GROUP,
+      Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
       StreamGroups<Real, FFCA_I, J>::value,
       (const void*)k_estep<Real, FFCA_I, J, true>,
       (const void*)k_estep<Real, FFCA_I, J, false>,

@@ -41,8 +41,10 @@ namespace ffca {
 #define FFCA_CONSUMER_WARPS 7
 #endif
 
-#ifndef FFCA_STAGES
-#define FFCA_STAGES 3
+// Stages per pipeline: as many as the shared-memory budget holds, at most
+// FFCA_MAX_STAGES (the bytes in flight per SM must cover the DRAM latency).
+#ifndef FFCA_MAX_STAGES
+#define FFCA_MAX_STAGES 8
 #endif
 #ifndef FFCA_TILE_UNITS_PER_THREAD
 #define FFCA_TILE_UNITS_PER_THREAD 2
@@ -51,7 +53,7 @@ constexpr int kConsumerWarps = FFCA_CONSUMER_WARPS;
 constexpr int kConsumers = 32 * kConsumerWarps;
 constexpr int kGroupWarps = kConsumerWarps + 1;  // + one producer warp
 constexpr int kGroupThreads = 32 * kGroupWarps;
-constexpr int kStages = FFCA_STAGES;
+constexpr int kStreamSmemBudget = 200 * 1024;    // dynamic shared memory per CTA
 static_assert(kGroupWarps % 4 == 0, "groups interleave in units of four warps");
 
 // Pipelines per CTA: two where the per-point state fits 128 registers (the
@@ -88,13 +90,22 @@ __device__ inline Role role() {
 // one or two units per consumer thread (always even).  Each stage also
 // carries the tile's per-frequency parameters (a ParamsA or ParamsB record),
 // so a consumer starting a new frequency finds them already in shared memory.
-template <int I, int J>
+template <typename R, int I, int J>
 struct Tile {
+  static constexpr int G = StreamGroups<R, I, J>::value;
   static constexpr int UB = 16 * I + 8 * J;                      // bytes per unit over all rows
-  static constexpr int T = (UB <= 80 ? FFCA_TILE_UNITS_PER_THREAD : 1) * kConsumers;  // units per tile
   static constexpr int PARAMS = ParamsA<double, I, J>::BYTES;     // room for either record
+  // FFCA_TILE_UNITS_PER_THREAD units per consumer thread where three stages
+  // of that size fit the budget, else one
+  static constexpr int T = ((kStreamSmemBudget / G) / (FFCA_TILE_UNITS_PER_THREAD * kConsumers * UB + PARAMS + 16) >= 3
+                                ? FFCA_TILE_UNITS_PER_THREAD
+                                : 1) *
+                           kConsumers;  // units per tile
   static constexpr int STAGE = T * UB + PARAMS;                   // bytes per stage, multiple of 16
-  static constexpr int GROUP = kStages * STAGE + 2 * kStages * 8;  // + mbarriers
+  static constexpr int S_FIT = (kStreamSmemBudget / G) / (STAGE + 16);
+  static constexpr int S = S_FIT < 2 ? 2 : (S_FIT > FFCA_MAX_STAGES ? FFCA_MAX_STAGES : S_FIT);  // stages
+  static constexpr int GROUP = S * STAGE + 2 * S * 8;             // + mbarriers
+  static_assert(G * GROUP <= 227 * 1024, "stages exceed the shared memory of a CTA");
 };
 
 // Register cap of the streaming kernels: 128 for two groups per CTA, else
@@ -225,20 +236,31 @@ struct GroupReduce {
 // Walks a CTA's unit range [u0, u1) of the flattened unit space as tiles of
 // at most T units that never cross a problem: tile (f = problem, k = first
 // unit within the problem, n units).
+// Tiles of the unit range [u0, u1): at most T units each, never crossing a
+// problem boundary.  The problem index is found once (binary search over the
+// unit starts) and then advanced as the range crosses into the next problem.
 struct TileIter {
   const Partition* pt;
   long long u, u1;
+  long long s, e;  // unit range of problem f
   int T;
   int f, k, n;
   bool seg_end;
   __device__ TileIter(long long u0_, long long u1_, const Partition& pt_, int T_)
-      : pt(&pt_), u(u0_), u1(u1_), T(T_) {}
+      : pt(&pt_), u(u0_), u1(u1_), T(T_) {
+    f = u < u1 ? pt->problem_of(u) : 0;
+    s = pt->start(f);
+    e = pt->start(f + 1);
+  }
   __device__ bool next() {
     if (u >= u1) return false;
-    f = pt->problem_of(u);
-    const long long s = pt->start(f);
+    if (u >= e) {  // ranges are contiguous: the next problem starts at e
+      ++f;
+      s = e;
+      e = pt->start(f + 1);
+    }
     k = (int)(u - s);
-    const int kend = (int)min((long long)pt->units(f), k + (u1 - u));
+    const int kend = (int)(min(e, u1) - s);
     n = min(T, kend - k);
     seg_end = (k + n == kend);
     u += n;
@@ -246,146 +268,167 @@ struct TileIter {
   }
 };
 
+template <int S>
 struct Pipe {
+  static constexpr int kStages = S;
   unsigned char* smem;
-  uint32_t bars;  // full[s] at bars + 8 s, empty[s] at bars + 8 (kStages + s)
+  uint32_t bars;  // full[s] at bars + 8 s, empty[s] at bars + 8 (S + s)
   __device__ uint32_t full(int s) const { return bars + 8 * s; }
-  __device__ uint32_t empty(int s) const { return bars + 8 * (kStages + s); }
+  __device__ uint32_t empty(int s) const { return bars + 8 * (S + s); }
 };
 
-// Pass B's parameters for frequency f, computed by its producer from pass A's
-// slots (FP64): the new Lambda (Eq. Lambdaupdate, lambda_ji I sum_n t_ji/s_j / N
-// with the slot sums of k_estep) into the stage's parameter slot.  The CTA
-// that starts frequency f also stores the new Lambda (committed to lambda by
-// k_psolve, after every CTA of this pass has read the current one) and the
-// frequency's log-likelihood of the state entering the iteration (Eq. L2).
-template <typename T, int I, int J>
-__device__ void finalize_pass_a(const FastArgs& a, int f, ParamsB<T, I, J>* out, bool first) {
+// Pass B's parameters for problem f, computed by its producer warp from pass
+// A's slots (FP64, one value per lane, slot order): the new Lambda (Eq.
+// Lambdaupdate, lambda_ji I sum_n t_ji / s_j / N with the slot sums of
+// k_estep); lane q < J I returns entry q.  The CTA that starts problem f also
+// stores the new Lambda (committed to lambda by k_psolve, after every CTA of
+// this pass has read the current one) and the problem's log-likelihood of
+// the state entering the iteration (Eq. L2).  The loads (FinIn) are issued
+// one problem ahead, so that their latency overlaps the tiles of the
+// current problem.  Called by all 32 lanes.
+struct FinIn {
+  double tot;  // lane q < J I + 2: slot sum of value q
+  double x;    // lane q < J I: current lambda entry q; lane J I: ln|det P|^2
+};
+
+template <int I, int J>
+__device__ inline FinIn finalize_load(const FastArgs& a, int f) {
   constexpr int NA = J * I;
   constexpr int NV = NA + 2;
+  static_assert(NV <= 32, "one value per lane");
+  const int lane = threadIdx.x & 31;
   const Partition& pa = a.prev_part;
   const int ns = pa.nslots(f);
   const double* p = a.prev_buf + ((size_t)f * pa.max_slots) * NV;
-  double tot[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) tot[q] = 0.0;
-  for (int k = 0; k < ns; ++k)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) tot[q] += __ldcg(p + (size_t)k * NV + q);
-  const double scale = (double)I * a.part.inv_n(f);
-  bool bad = false;
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    const double lnew = a.lam[(size_t)f * NA + q] * scale * tot[q];
-    bad |= !(lnew > 0.0) || !isfinite(lnew);
-    out->lam[q / I][q % I] = (T)lnew;
-    if (first) a.lam_next[(size_t)f * NA + q] = lnew;
-  }
-  if (first) {
-    const int n = a.part.frames(f);
-    const double lf = -(double)I * n * kLnPi + (double)n * __ldcg(a.logdet + f) - tot[NA] -
-                      0.69314718055994530942 * tot[NA + 1];
-    bad |= !isfinite(lf);
-    a.llf[f] = lf;
-    if (bad) raise_status(a.status, kDevNonfinite, f);
-  }
+  FinIn in{0.0, 0.0};
+  if (lane < NV)
+    for (int k = 0; k < ns; ++k) in.tot += __ldcg(p + (size_t)k * NV + lane);
+  if (lane < NA)
+    in.x = __ldcg(a.lam + (size_t)f * NA + lane);
+  else if (lane == NA)
+    in.x = __ldcg(a.logdet + f);
+  return in;
 }
 
-// Producer: one thread.  y units are 16 bytes, v units 8 bytes; ranges start
-// on even units, so every copy is 16-byte aligned and a multiple of 16 bytes.
-// Each stage also receives the tile's parameter record: copied from the
-// pass-A table (pass A), or computed from pass A's slots (pass B).
+template <typename T, int I, int J>
+__device__ T finalize_pass_a(const FastArgs& a, int f, const FinIn& in, bool first) {
+  constexpr int NA = J * I;
+  const int lane = threadIdx.x & 31;
+  const double lg = __shfl_sync(0xffffffffu, in.tot, NA + 1);
+  T out = (T)0;
+  bool bad = false;
+  if (lane < NA) {
+    const double lnew = in.x * ((double)I * a.part.inv_n(f)) * in.tot;
+    bad = !(lnew > 0.0) || !isfinite(lnew);
+    out = (T)lnew;
+    if (first) a.lam_next[(size_t)f * NA + lane] = lnew;
+  } else if (lane == NA && first) {
+    const int n = a.part.frames(f);
+    const double lf = -(double)I * n * kLnPi + (double)n * in.x - in.tot - 0.69314718055994530942 * lg;
+    bad = !isfinite(lf);
+    a.llf[f] = lf;
+  }
+  if (bad) raise_status(a.status, kDevNonfinite, f);
+  return out;
+}
+
+// Producer: one thread in pass A, the whole warp in pass B (lane 0 issues
+// the copies; the warp finalises pass A's sums of each new problem).  y units
+// are 16 bytes, v units 8 bytes; ranges start on even units, so every copy is
+// 16-byte aligned and a multiple of 16 bytes.  Each stage also receives the
+// tile's parameter record: copied from the pass-A table (pass A), or computed
+// from pass A's slots (pass B).
 template <typename T, int I, int J, bool PASS_B>
-__device__ void produce(const FastArgs& a, const Pipe& pp, long long u0, long long u1, long long row,
-                        int vb, volatile int* abort) {
-  using TC = Tile<I, J>;
+__device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, long long u0, long long u1,
+                        long long row, int vb, volatile int* abort) {
+  using TC = Tile<T, I, J>;
+  constexpr int kStages = TC::S;
   using PA = ParamsA<T, I, J>;
   using PB = ParamsB<T, I, J>;
+  constexpr int NA = J * I;
   const char* y = static_cast<const char*>(a.y);
   const char* v = static_cast<const char*>(a.v);
   const char* tab = static_cast<const char*>(a.tabA);
   constexpr int FU = Vec<T>::FU;
+  const bool leader = (threadIdx.x & 31) == 0;
   const Partition& pt = a.part;
   TileIter it(u0, u1, pt, TC::T);
-  PB pb;
+  T lam_q = (T)0;  // pass B: this lane's entry of the current problem's new Lambda
+  FinIn next_in{0.0, 0.0};
+  if (PASS_B && u1 > u0) next_in = finalize_load<I, J>(a, it.f);
   int pf = -1;
   int t = 0;
   while (it.next()) {
     const int s = t % kStages;
-    if (PASS_B && it.f != pf) {  // before waiting: overlaps the slot loads with the pipeline
-      finalize_pass_a<T, I, J>(a, it.f, &pb, a.part.first_block(it.f) == vb);
+    if (PASS_B && it.f != pf) {
+      const FinIn cur = next_in;
+      if (it.f + 1 < pt.F && pt.start(it.f + 1) < u1) next_in = finalize_load<I, J>(a, it.f + 1);
+      lam_q = finalize_pass_a<T, I, J>(a, it.f, cur, pt.first_block(it.f) == vb);
       pf = it.f;
     }
-    if (t >= kStages && !*abort && !mbar_wait(pp.empty(s), ((t / kStages) - 1) & 1)) {
-      raise_status(a.status, kDevTimeout, it.f);
-      *abort = 1;
+    int stop = 0;
+    if (leader) {
+      if (t >= kStages && !*abort && !mbar_wait(pp.empty(s), ((t / kStages) - 1) & 1)) {
+        raise_status(a.status, kDevTimeout, it.f);
+        *abort = 1;
+      }
+      stop = *abort;
     }
-    if (*abort) break;
+    if constexpr (PASS_B) stop = __shfl_sync(0xffffffffu, stop, 0);  // one decision for the warp
+    if (stop) break;
     unsigned char* stp = pp.smem + (size_t)s * TC::STAGE;
     const uint32_t st = smem_u32(stp);
     if constexpr (PASS_B) {
-      *reinterpret_cast<PB*>(stp + TC::T * TC::UB) = pb;  // visible to consumers with the arrive below
+      // lane q < J I stores its entry of the parameter record; the warp
+      // barrier orders these stores before lane 0's arrive, which releases
+      // them to the consumers together with the tile
+      if ((int)(threadIdx.x & 31) < NA)
+        (&reinterpret_cast<PB*>(stp + TC::T * TC::UB)->lam[0][0])[threadIdx.x & 31] = lam_q;
+      __syncwarp();
+      if (!leader) {
+        ++t;
+        continue;
+      }
       mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB));
     } else {
       mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB + PA::BYTES));
       bulk_g2s(st + TC::T * TC::UB, tab + (size_t)it.f * PA::BYTES, (unsigned)PA::BYTES, pp.full(s));
     }
-    const int fr = pt.freq(it.f);
-    const long long k = pt.frame_off(it.f) / FU + it.k;  // unit along the row
+    // rows of the problem's blocks (units): mic m at I Fm off + (m Fm + f) ld,
+    // source j at J Fm off + (j Fm + f) ld (frames / FU)
+    const long long rlen = pt.row_len(it.f, row * FU) / FU;
+    const long long off = pt.frame_off(it.f) / FU;
+    const long long r0 = (long long)pt.freq(it.f) * rlen + it.k;
 #pragma unroll
     for (int m = 0; m < I; ++m)
-      bulk_g2s(st + m * TC::T * 16, y + (((size_t)m * pt.Fm + fr) * row + k) * 16, (unsigned)it.n * 16,
-               pp.full(s));
+      bulk_g2s(st + m * TC::T * 16, y + ((size_t)I * pt.Fm * off + (size_t)m * pt.Fm * rlen + r0) * 16,
+               (unsigned)it.n * 16, pp.full(s));
 #pragma unroll
     for (int j = 0; j < J; ++j)
-      bulk_g2s(st + I * TC::T * 16 + j * TC::T * 8, v + (((size_t)j * pt.Fm + fr) * row + k) * 8,
-               (unsigned)it.n * 8, pp.full(s));
+      bulk_g2s(st + I * TC::T * 16 + j * TC::T * 8,
+               v + ((size_t)J * pt.Fm * off + (size_t)j * pt.Fm * rlen + r0) * 8, (unsigned)it.n * 8, pp.full(s));
     ++t;
   }
   // let the copies of the last stages land before this thread leaves
-  for (int d = t > kStages ? t - kStages : 0; d < t; ++d) mbar_wait(pp.full(d % kStages), (d / kStages) & 1);
-}
-
-// Side work of pass A's producer warp (lanes 1..31, otherwise idle):
-// ln|det P(f)|^2 of the P entering this iteration, for the frequencies whose
-// first CTA this is (Eq. L2 needs it per frequency; FP64, off the streaming
-// path).
-template <int I>
-__device__ void side_logdet(const FastArgs& a, long long u0, long long u1, int vb) {
-  const int lane = threadIdx.x & 31;
-  const Partition& pt = a.part;
-  const int flo = pt.problem_of(u0), fhi = pt.problem_of(u1 - 1);
-  int nth = 0;
-  for (int f = flo; f <= fhi; ++f) {
-    if (pt.first_block(f) != vb) continue;
-    if (nth++ % 31 != lane - 1) continue;
-    cpx<double> A[I][I], C[I][I];
-#pragma unroll
-    for (int r = 0; r < I; ++r)
-#pragma unroll
-      for (int c = 0; c < I; ++c)
-        A[r][c] = mk(a.P[((size_t)f * I * I + r * I + c) * 2], a.P[((size_t)f * I * I + r * I + c) * 2 + 1]);
-    const double d2 = cabs2(cofactors<I>(A, C));
-    if (!(d2 > 0.0) || !isfinite(d2)) raise_status(a.status, kDevSingular, f);
-    a.logdet[f] = log(d2);
-  }
+  if (leader)
+    for (int d = t > kStages ? t - kStages : 0; d < t; ++d) mbar_wait(pp.full(d % kStages), (d / kStages) & 1);
 }
 
 // Every group's stages and mbarriers, initialised by thread 0; returns this
 // thread's group pipe.
-template <int G>
-__device__ inline Pipe setup_pipe(unsigned char* smem, int stage_bytes, int group, volatile int* aborts) {
-  const size_t group_bytes = (size_t)kStages * stage_bytes + 2 * kStages * 8;
+template <int G, int S>
+__device__ inline Pipe<S> setup_pipe(unsigned char* smem, int stage_bytes, int group, volatile int* aborts) {
+  const size_t group_bytes = (size_t)S * stage_bytes + 2 * S * 8;
   auto pipe_of = [&](int g) {
-    Pipe p;
+    Pipe<S> p;
     p.smem = smem + g * group_bytes;
-    p.bars = smem_u32(p.smem + (size_t)kStages * stage_bytes);
+    p.bars = smem_u32(p.smem + (size_t)S * stage_bytes);
     return p;
   };
   if (threadIdx.x == 0) {
     for (int g = 0; g < G; ++g) {
-      const Pipe p = pipe_of(g);
-      for (int s = 0; s < kStages; ++s) {
+      const Pipe<S> p = pipe_of(g);
+      for (int s = 0; s < S; ++s) {
         mbar_init(p.full(s), 1);
         mbar_init(p.empty(s), kConsumerWarps);
       }
@@ -398,16 +441,18 @@ __device__ inline Pipe setup_pipe(unsigned char* smem, int stage_bytes, int grou
 }
 
 // Consumer side of one tile: wait for it unless the CTA has given up.
-__device__ inline bool consumer_acquire(const FastArgs& a, const Pipe& pp, int t, int f, volatile int* abort) {
+template <int S>
+__device__ inline bool consumer_acquire(const FastArgs& a, const Pipe<S>& pp, int t, int f, volatile int* abort) {
   if (*abort) return false;
-  if (mbar_wait(pp.full(t % kStages), (t / kStages) & 1)) return true;
+  if (mbar_wait(pp.full(t % S), (t / S) & 1)) return true;
   raise_status(a.status, kDevTimeout, f);
   *abort = 1;
   return false;
 }
-__device__ inline void consumer_release(const Pipe& pp, int t) {
+template <int S>
+__device__ inline void consumer_release(const Pipe<S>& pp, int t) {
   __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(pp.empty(t % kStages));
+  if ((threadIdx.x & 31) == 0) mbar_arrive(pp.empty(t % S));
 }
 
 // ------------------------------------------------------------ frame lanes
@@ -491,7 +536,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   using VV = typename Vec<T>::V;
   using LN = Lane<T>;
   using L = typename LN::L;
-  using TC = Tile<I, J>;
+  using TC = Tile<T, I, J>;
   constexpr int FU = Vec<T>::FU;
   constexpr int NA = UPDATE ? J * I : 0;  // sum_n t_ji / s_j
   constexpr int NV = NA + 2;              // then the quadratic and log2 parts of L2
@@ -507,17 +552,13 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   volatile int* abort = &aborts[rl.group];
   typename Red::Smem& red = red_all[rl.group];
   const Partition pt = a.part;
-  const long long total = pt.total;
-  const long long u0 = min((long long)rl.vb * pt.upb, total);
-  const long long u1 = min(u0 + pt.upb, total);
+  const long long u0 = pt.block_start(rl.vb);
+  const long long u1 = pt.block_start(rl.vb + 1);
   const long long row = a.ld / FU;  // vector units per (mic or source, f) row
-  const Pipe pp = setup_pipe<G>(smem, TC::STAGE, rl.group, aborts);
+  const Pipe<TC::S> pp = setup_pipe<G, TC::S>(smem, TC::STAGE, rl.group, aborts);
 
   if (!rl.consumer) {
-    if ((threadIdx.x & 31) == 0)
-      produce<T, I, J, false>(a, pp, u0, u1, row, rl.vb, abort);
-    else if (u1 > u0)
-      side_logdet<I>(a, u0, u1, rl.vb);
+    if ((threadIdx.x & 31) == 0) produce<T, I, J, false>(a, pp, u0, u1, row, rl.vb, abort);
     return;
   }
 
@@ -535,9 +576,10 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
       for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
     }
     const int Np = pt.frames(f);
-    VV* __restrict__ vrow = vg + (size_t)pt.freq(f) * row + pt.frame_off(f) / FU;  // + j Fm row below
+    const long long rlen = pt.row_len(f, row * FU) / FU;  // units per row of the problem's block
+    VV* __restrict__ vrow = vg + (size_t)J * pt.Fm * (pt.frame_off(f) / FU) + (size_t)pt.freq(f) * rlen;
     if (consumer_acquire(a, pp, t, f, abort)) {
-      const unsigned char* st = pp.smem + (size_t)(t % kStages) * TC::STAGE;
+      const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
       if (seg_new) {  // this frequency's P and Lambda arrived with the tile
         const PA& sp = *reinterpret_cast<const PA*>(st + TC::T * TC::UB);
 #pragma unroll
@@ -616,11 +658,11 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
             if (full) {
 #pragma unroll
               for (int i = 0; i < I; ++i) acc[j * I + i] = vfma(tj[i], rs, acc[j * I + i]);
-              vrow[(size_t)j * pt.Fm * row + k] = LN::store(vn);
+              vrow[(size_t)j * pt.Fm * rlen + k] = LN::store(vn);
             } else {
 #pragma unroll
               for (int i = 0; i < I; ++i) acc[j * I + i] = acc[j * I + i] + LN::keep(tj[i] * rs, n0, Np);
-              vrow[(size_t)j * pt.Fm * row + k] = LN::store(LN::pick(vn, vv[j], n0, Np));
+              vrow[(size_t)j * pt.Fm * rlen + k] = LN::store(LN::pick(vn, vv[j], n0, Np));
             }
           }
         }
@@ -664,7 +706,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   using VV = typename Vec<T>::V;
   using LN = Lane<T>;
   using L = typename LN::L;
-  using TC = Tile<I, J>;
+  using TC = Tile<T, I, J>;
   constexpr int FU = Vec<T>::FU;
   constexpr int I2 = I * I;
   constexpr int NV = I * I2;
@@ -680,20 +722,23 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   volatile int* abort = &aborts[rl.group];
   typename Red::Smem& red = red_all[rl.group];
   const Partition pt = a.part;
-  const long long total = pt.total;
-  const long long u0 = min((long long)rl.vb * pt.upb, total);
-  const long long u1 = min(u0 + pt.upb, total);
+  const long long u0 = pt.block_start(rl.vb);
+  const long long u1 = pt.block_start(rl.vb + 1);
   const long long row = a.ld / FU;
-  const Pipe pp = setup_pipe<G>(smem, TC::STAGE, rl.group, aborts);
+  const Pipe<TC::S> pp = setup_pipe<G, TC::S>(smem, TC::STAGE, rl.group, aborts);
 
-  if (!rl.consumer) {
-    if ((threadIdx.x & 31) == 0) produce<T, I, J, true>(a, pp, u0, u1, row, rl.vb, abort);
+  if (!rl.consumer) {  // the whole warp: its lanes finalise pass A's sums in parallel
+    produce<T, I, J, true>(a, pp, u0, u1, row, rl.vb, abort);
     return;
   }
 
   const int tid = rl.ctid;
   L lam[J][I];
-  L acc[NV];
+  // FP32 with I^3 > 32 sums: one float per value (both frames of a unit go
+  // into it) instead of a packed pair, which keeps the sums in registers
+  constexpr bool kNarrow = sizeof(T) == 4 && NV > 32;
+  using A = std::conditional_t<kNarrow, float, L>;
+  A acc[NV];
 
   TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
@@ -701,11 +746,14 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
     const int f = it.f;
     if (seg_new) {
 #pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
+      for (int q = 0; q < NV; ++q) {
+        if constexpr (kNarrow) acc[q] = 0.f;
+        else acc[q] = LN::bc(0);
+      }
     }
     const int Np = pt.frames(f);
     if (consumer_acquire(a, pp, t, f, abort)) {
-      const unsigned char* st = pp.smem + (size_t)(t % kStages) * TC::STAGE;
+      const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
       if (seg_new) {  // the new Lambda(f) arrived with the tile
         const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
 #pragma unroll
@@ -761,7 +809,12 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
 #pragma unroll
         for (int i = 0; i < I; ++i)
 #pragma unroll
-          for (int mm = 0; mm < I2; ++mm) acc[i * I2 + mm] = vfma(w[i], pk[mm], acc[i * I2 + mm]);
+          for (int mm = 0; mm < I2; ++mm) {
+            if constexpr (kNarrow)
+              acc[i * I2 + mm] = fmaf(w[i].v.y, pk[mm].v.y, fmaf(w[i].v.x, pk[mm].v.x, acc[i * I2 + mm]));
+            else
+              acc[i * I2 + mm] = vfma(w[i], pk[mm], acc[i * I2 + mm]);
+          }
       }
     }
 
@@ -771,7 +824,15 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
     if (it.seg_end) {
       const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
-      if constexpr (sizeof(T) == 4) {
+      if constexpr (kNarrow) {
+        float hi[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          hi[q] = acc[q];
+          lo[q] = 0.f;
+        }
+        Red::run(hi, lo, red, out, rl);
+      } else if constexpr (sizeof(T) == 4) {
         float hi[NV], lo[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);

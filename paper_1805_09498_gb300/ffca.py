@@ -418,18 +418,28 @@ def to_device(problem_y, v, lam, P, prec: str = "mixed", device="cuda", ld: int 
 
 
 def batch_offsets(Ns) -> np.ndarray:
-    """Frame offsets of mixtures of Ns frames concatenated along a row, each
-    padded to a multiple of 4 (the layout ffca_batch_desc expects)."""
+    """Row-length offsets of mixtures of Ns frames, each row padded to a
+    multiple of 4 (frame_offset of ffca_batch_desc)."""
     off = np.zeros(len(Ns) + 1, dtype=np.int64)
     off[1:] = np.cumsum([padded_ld(int(n)) for n in Ns])
     return off
 
 
+def batch_views(t, rows: int, F: int, offsets):
+    """The per-mixture blocks [rows, F, ld_m] of a batch tensor (views)."""
+    out = []
+    for m in range(len(offsets) - 1):
+        o, ldm = int(offsets[m]), int(offsets[m + 1] - offsets[m])
+        out.append(t[rows * F * o: rows * F * (o + ldm)].view(rows, F, ldm))
+    return out
+
+
 def batch_to_device(ys, vs, lams, Ps, prec: str = "mixed", device="cuda", pad_value=None):
-    """Concatenate per-mixture numpy arrays (y [I,F,N_m], v [J,F,N_m],
-    lam [F,J,I], P [F,I,I]) into the batch layout on the device.  Returns
-    (y, v, lam, P, Ns, offsets); padding frames hold pad_value (0 / 1 by
-    default for y / v)."""
+    """Pack per-mixture numpy arrays (y [I,F,N_m], v [J,F,N_m], lam [F,J,I],
+    P [F,I,I]) into the mixture-major batch layout on the device: flat y and
+    v holding the blocks [I,F,ld_m] and [J,F,ld_m] one after another.
+    Returns (y, v, lam, P, Ns, offsets); padding frames hold pad_value
+    (0 / 1 by default for y / v)."""
     import torch
     Ns = [int(y.shape[2]) for y in ys]
     off = batch_offsets(Ns)
@@ -437,15 +447,14 @@ def batch_to_device(ys, vs, lams, Ps, prec: str = "mixed", device="cuda", pad_va
     J = vs[0].shape[0]
     ld = int(off[-1])
     cdt, rdt = (torch.complex64, torch.float32) if prec == "mixed" else (torch.complex128, torch.float64)
-    yt = torch.zeros((I, F, ld), dtype=cdt)
-    vt = torch.ones((J, F, ld), dtype=rdt)
+    yt = torch.zeros(I * F * ld, dtype=cdt)
+    vt = torch.ones(J * F * ld, dtype=rdt)
     if pad_value is not None:
         yt.fill_(pad_value)
         vt.fill_(pad_value)
-    for m, (y, v) in enumerate(zip(ys, vs)):
-        o, n = int(off[m]), Ns[m]
-        yt[:, :, o:o + n] = torch.from_numpy(np.ascontiguousarray(y)).to(cdt)
-        vt[:, :, o:o + n] = torch.from_numpy(np.ascontiguousarray(v)).to(rdt)
+    for m, (yb, vb) in enumerate(zip(batch_views(yt, I, F, off), batch_views(vt, J, F, off))):
+        yb[:, :, :Ns[m]] = torch.from_numpy(np.ascontiguousarray(ys[m])).to(cdt)
+        vb[:, :, :Ns[m]] = torch.from_numpy(np.ascontiguousarray(vs[m])).to(rdt)
     lam = torch.from_numpy(np.ascontiguousarray(np.stack(lams), dtype=np.float64))
     P = torch.from_numpy(np.ascontiguousarray(np.stack(Ps), dtype=np.complex128))
     return yt.to(device), vt.to(device), lam.to(device), P.to(device), Ns, off
@@ -455,10 +464,11 @@ class FastFCABatch:
     """FastFCA-AS estimation of M independent mixtures of uneven length in
     one set of launches, borrowed from torch tensors.
 
-    y   [I, F, ld] complex64 / complex128, mixture m in frames
-        [offsets[m], offsets[m+1]) of every row, its first Ns[m] used
-    v   [J, F, ld] real (matching y), updated in place
+    y   flat complex64 / complex128: the blocks [I, F, ld_m] of the mixtures
+        one after another (ld_m = offsets[m+1] - offsets[m], first Ns[m] used)
+    v   flat real (matching y): the blocks [J, F, ld_m], updated in place
     lam [M, F, J, I] float64, P [M, F, I, I] complex128, updated in place
+    I, J, F are given (the flat arrays do not carry them).
     """
 
     def __init__(self, y, v, lam, P, Ns, offsets=None, K: int = 1, stream=None, graph=False):
@@ -476,14 +486,17 @@ class FastFCABatch:
         for t in (y, v, lam, P):
             if not t.is_contiguous():
                 raise ValueError("tensors must be contiguous")
-        I, F, ld = y.shape
-        J = v.shape[0]
         M = len(Ns)
-        if v.shape != (J, F, ld) or lam.shape != (M, F, J, I) or P.shape != (M, F, I, I):
-            raise ValueError("inconsistent shapes")
-        self.I, self.J, self.F, self.M, self.ld = I, J, F, M, ld
+        if lam.dim() != 4 or P.dim() != 4 or lam.shape[0] != M or P.shape[0] != M:
+            raise ValueError("lam [M, F, J, I] and P [M, F, I, I] expected")
+        _, F, J, I = lam.shape
         self.Ns = np.asarray(Ns, dtype=np.int32)
         self.offsets = batch_offsets(Ns) if offsets is None else np.asarray(offsets, dtype=np.int64)
+        ld = int(self.offsets[-1])
+        if y.dim() != 1 or v.dim() != 1 or y.numel() < I * F * ld or v.numel() < J * F * ld \
+                or P.shape != (M, F, I, I):
+            raise ValueError("inconsistent shapes")
+        self.I, self.J, self.F, self.M, self.ld = I, J, F, M, ld
         self.y, self.v, self.lam, self.P = y, v, lam, P
         s = stream if stream is not None else torch.cuda.current_stream(y.device)
         self.stream = s

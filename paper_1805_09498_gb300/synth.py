@@ -32,7 +32,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-__all__ = ["Problem", "make_problem", "batch_lengths", "make_batch", "CONFIGS", "cn", "draw_P"]
+__all__ = ["Problem", "make_problem", "batch_lengths", "make_batch", "make_batch_device", "CONFIGS",
+           "cn", "draw_P"]
 
 
 def cn(rng: np.random.Generator, shape) -> np.ndarray:
@@ -108,6 +109,58 @@ def make_batch(I: int, J: int, F: int, Ns, seed: int, alpha: float = 0.3,
                kappa: float = 10.0) -> list[Problem]:
     """Independent mixtures of lengths Ns; mixture m is make_problem(seed + 7919 m)."""
     return [make_problem(I, J, F, int(n), seed + 7919 * m, alpha, kappa) for m, n in enumerate(Ns)]
+
+
+def make_batch_device(I: int, J: int, F: int, Ns, seed: int, device, alpha: float = 0.3,
+                      kappa: float = 10.0, complex_dtype=None):
+    """The same model as make_problem for M mixtures, drawn on the device
+    (torch's generator) straight into the mixture-major batch layout: flat y
+    and v holding mixture m's blocks [I,F,ld_m] and [J,F,ld_m] one after
+    another, ld_m = off[m+1] - off[m] = Ns[m] rounded up to a multiple of 4.
+
+    Used where numpy would take minutes (hundreds of mixtures); the numbers
+    differ from make_problem's (another generator), the distributions are
+    the same.  Gamma(shape 1/2, scale 1) is drawn as z^2 / 2, z ~ N(0, 1).
+    Returns (y, v0, lam0 [M,F,J,I] f64, P0 [M,F,I,I] c128, Ns, off); padding
+    frames hold y = 0, v = 1.
+    """
+    import torch
+    cdt = torch.complex64 if complex_dtype is None else complex_dtype
+    rdt = torch.float32 if cdt == torch.complex64 else torch.float64
+    Ns = [int(n) for n in Ns]
+    M = len(Ns)
+    off = np.zeros(M + 1, dtype=np.int64)
+    off[1:] = np.cumsum([(n + 3) // 4 * 4 for n in Ns])
+    ld = int(off[-1])
+    rng = np.random.default_rng(seed)
+    P = draw_P(rng, M * F, I, alpha, kappa).reshape(M, F, I, I)
+    lam = np.exp(rng.standard_normal((M, F, J, I)))
+    r2 = np.random.default_rng(seed + 1000)
+    P0 = np.einsum("mfab,mfbc->mfac", P, np.eye(I) + 0.1 * cn(r2, (M, F, I, I)))
+    lam0 = lam * np.exp(0.3 * r2.standard_normal(lam.shape))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    PinvH = torch.from_numpy(np.linalg.inv(P).conj().swapaxes(-1, -2)).to(device)  # [M,F,I,I]
+    lam_d = torch.from_numpy(lam).to(device)
+    y = torch.zeros(I * F * ld, dtype=cdt, device=device)
+    v0 = torch.ones(J * F * ld, dtype=rdt, device=device)
+    s2 = float(np.sqrt(0.5))
+    for m in range(M):
+        o, n, ldm = int(off[m]), Ns[m], int(off[m + 1] - off[m])
+        yb = y[I * F * o: I * F * (o + ldm)].view(I, F, ldm)
+        vb = v0[J * F * o: J * F * (o + ldm)].view(J, F, ldm)
+        z = torch.randn((J, F, n), generator=g, device=device, dtype=torch.float64)
+        v = 0.5 * z * z                                                   # Gamma(0.5, 1)
+        ym = torch.zeros((F, I, n), dtype=torch.complex128, device=device)
+        for j in range(J):
+            std = torch.sqrt(v[j][:, None, :] * lam_d[m, :, j, :][:, :, None])   # [F, I, n]
+            re = torch.randn((F, I, n), generator=g, device=device, dtype=torch.float64)
+            im = torch.randn((F, I, n), generator=g, device=device, dtype=torch.float64)
+            ym += torch.matmul(PinvH[m], torch.complex(s2 * std * re, s2 * std * im))
+        yb[:, :, :n] = ym.permute(1, 0, 2).to(cdt)
+        xi = torch.randn((J, F, n), generator=g, device=device, dtype=torch.float64)
+        vb[:, :, :n] = (v * torch.exp(0.3 * xi)).to(rdt)
+    return (y, v0, torch.from_numpy(lam0).to(device), torch.from_numpy(P0).to(device), Ns, off)
 
 
 # Workloads: sizes, value distributions and precision of each measured case.

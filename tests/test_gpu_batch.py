@@ -39,8 +39,10 @@ def _run_batch(probs, iters, prec, K=1, graph=False, pad_value=None, trace=True)
     tr = est.iterate(iters, trace=trace)
     ll = est.loglik()
     torch.cuda.synchronize()
-    vh = v.double().cpu().numpy()
-    vs = [vh[:, :, off[m]:off[m] + Ns[m]] for m in range(len(Ns))]
+    vh = v.double().cpu()
+    J, F = probs[0].J, probs[0].F
+    vs = [b[:, :, :Ns[m]].numpy() for m, b in enumerate(ffca.batch_views(vh, J, F, off))]
+    vh = vh.numpy()
     out = dict(v=vs, lam=lam.cpu().numpy(), P=P.cpu().numpy(), trace=tr, ll=ll, vall=vh)
     est.close()
     return out
@@ -137,8 +139,8 @@ def test_graph_replay_is_bit_identical(prec):
 
 
 def test_padding_between_mixtures_is_ignored():
-    """NaN in every padding frame between and after the mixtures changes
-    nothing in the estimates (the padding is never read as data)."""
+    """NaN in every padding frame of every mixture's rows changes nothing in
+    the estimates (the padding is never read as data)."""
     probs = make_batch(3, 2, 4, [13, 50, 7], seed=4)
     a = _run_batch(probs, 2, "mixed")
     b = _run_batch(probs, 2, "mixed", pad_value=float("nan"))
@@ -167,9 +169,9 @@ def test_invalid_batches_are_rejected():
     with pytest.raises(ffca.FFCAError):
         ffca.FastFCABatch(y, v, lam, P, Ns, offsets=[0, 10, int(off[-1])])  # not a multiple of 4
     with pytest.raises(ffca.FFCAError):
-        ffca.FastFCABatch(y, v, lam, P, [13, 20], offsets=off)  # mixture 0 overruns its span
+        ffca.FastFCABatch(y, v, lam, P, [13, 20], offsets=off)  # mixture 0 overruns its rows
     est = ffca.FastFCABatch(y, v, lam, P, Ns)
-    out = torch.empty((2, 2, 3, y.shape[2]), dtype=y.dtype, device=y.device)
+    out = torch.empty((2, 2, 3, int(off[-1])), dtype=y.dtype, device=y.device)
     with pytest.raises(ffca.FFCAError) as ei:
         ffca.ffca_wiener(est.ctx, out.data_ptr())
     assert ei.value.status == 7
