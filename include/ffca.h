@@ -148,6 +148,33 @@ ffca_status ffca_download(ffca_ctx* ctx, void* v_host, double* lambda_host, doub
  * out_host (same layout), then synchronises. */
 ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
 
+/* ---------------------------------------------------------------------------
+ * Gradients (adjoint) at the context's current state (v, lambda, P), with the
+ * per-point posteriors recomputed in one streaming pass over y and v (no
+ * state is kept from the iterations), for two losses:
+ *
+ *   NLL = -L2 (Eq. L2, with the -I ln(pi) term), summed over the N frames
+ *         and the F bins;
+ *   SE  = sum_{j,a,n,f} |x^_ja(n,f) - s_ja(n,f)|^2, x^ the Wiener estimate
+ *         of ffca_wiener (Eq. MMSE0 with Eq. covmodelprop) and s given
+ *         reference source images.
+ *
+ * Outputs (device, caller-owned, overwritten):
+ *   dv    [J][F][ld] real of the precision's type: dLoss/dv_j(n,f) for n < N
+ *         (16-byte aligned; entries of frames >= N in the last vector units
+ *         are written as 0, frames beyond untouched)
+ *   dlam  [F][J][I] double: dLoss/dlambda_ji(f)
+ *   dP    [F][I][I] complex128: dLoss/dP(f)^*, the conjugate Wirtinger
+ *         derivative (for a real loss dLoss = 2 Re sum conj(dP) dP; the NLL
+ *         one is minus Eq. partialP's dL2/dP^*)
+ *   loss  host double or NULL: the loss value (the call then synchronises)
+ * s: device [J][I][F][ld] complex of the precision's type (the layout of the
+ * ffca_wiener output).  Enqueued on the context stream.  FFCA_ERR_UNSUPPORTED
+ * for batch contexts. */
+ffca_status ffca_nll_grad(ffca_ctx* ctx, void* dv, double* dlam, double* dP, double* loss);
+ffca_status ffca_wiener_se_grad(ffca_ctx* ctx, const void* s, void* dv, double* dlam, double* dP,
+                                double* loss);
+
 /* Kernel kinds reported by ffca_timing_read. */
 #define FFCA_KERNEL_PREP 0      /* per-frequency ln|det P|^2 and P^{-H} */
 #define FFCA_KERNEL_ESTEP 1     /* pass A with the M-step */
@@ -156,7 +183,9 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
 #define FFCA_KERNEL_WIENER 4
 #define FFCA_KERNEL_PSOLVE 5    /* per-frequency FP64 fixed-point update of P */
 #define FFCA_KERNEL_AFINAL 6    /* per-frequency finalise of pass A: Lambda, log-likelihood */
-#define FFCA_KERNEL_KINDS 7
+#define FFCA_KERNEL_ADJ 7       /* adjoint streaming pass (ffca_nll_grad, ffca_wiener_se_grad) */
+#define FFCA_KERNEL_ADJ_FINAL 8 /* adjoint per-frequency finalise */
+#define FFCA_KERNEL_KINDS 9
 
 /* Profiling: while enabled, each kernel the context launches is bracketed by
  * two CUDA events on the context stream.  ffca_timing_read synchronises,

@@ -37,7 +37,7 @@ def _nvcc():
 def _units():
     """(source, object, extra flags) for every translation unit."""
     units = [("ffca_api.cu", "ffca_api.o", []), ("ffca_fca_api.cu", "ffca_fca_api.o", [])]
-    for part in (0, 1):  # FastFCA-AS, conventional FCA
+    for part in (0, 1, 2):  # FastFCA-AS, conventional FCA, adjoint
         for prec in (0, 1):
             for i in I_VALUES:
                 units.append(("ffca_inst.cu", f"ffca_inst_k{part}_p{prec}_i{i}.o",

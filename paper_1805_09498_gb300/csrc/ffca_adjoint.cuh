@@ -1,0 +1,310 @@
+// Adjoint kernels: gradients of two losses of the model parameters
+// Psi = (v, Lambda, P) at fixed data, with the posteriors recomputed per
+// time-frequency point (nothing is stored from the iterations).
+//
+//   NLL = -L2 (Eq. L2), per point I ln(pi) - ln|det P|^2
+//         + sum_i (ln sigma_i + |y~_i|^2 / sigma_i), y~ = P^H y,
+//         sigma_i = sum_j v_j lambda_ji:
+//     t_i = 1/sigma_i - |y~_i|^2 / sigma_i^2
+//     dNLL/dv_j = sum_i lambda_ji t_i,  dNLL/dlambda_ji = sum_n v_j t_i,
+//     dNLL/dP^* = -N P^{-H} + sum_n y y^H P diag(1/sigma)   (minus Eq. partialP)
+//   SE = sum_{j,n} |x^_j - s_j|^2 with the Wiener estimate x^_j =
+//        Q (g_j * y~), Q = P^{-H}, g_ji = v_j lambda_ji / sigma_i (Eq. MMSE0
+//        with Eq. covmodelprop), s_j the reference source images:
+//     e_j = x^_j - s_j, b_j = Q^H e_j, G_ji = 2 Re(conj(b_ji) y~_i),
+//     h_i = sum_j G_ji g_ji, w_ji = (G_ji - h_i) / sigma_i
+//     dSE/dv_j = sum_i lambda_ji w_ji,  dSE/dlambda_ji = sum_n v_j w_ji,
+//     dSE/dP^* = sum_n sum_j (y (g_j * b_j)^H - x^_j b_j^H)
+// dP is the conjugate Wirtinger derivative: dLoss = 2 Re sum conj(dP) dP.
+//
+// k_adj streams y, v (and s) once: one CTA per contiguous unit range of the
+// uniform partition, 256 threads, per-thread sums over the range's frames of
+// each frequency, a block reduction per frequency segment into that
+// frequency's slot (deterministic, no atomics).  k_adj_final sums the slots
+// per frequency (FP64, slot order) and adds the closed-form terms.
+#pragma once
+
+#include "ffca_fastfca.cuh"
+
+namespace ffca {
+
+struct AdjArgs {
+  Partition part;        // uniform: F problems of Uf units (the N frames)
+  int F, N, ld;
+  const void* y;         // [I][F][ld] complex
+  const void* v;         // [J][F][ld] real
+  const double* lam;     // [F][J][I]
+  const double* P;       // [F][I][I] complex
+  const double* pinvH;   // [F][I][I] complex, P^{-H} (k_prep)
+  const double* logdet;  // [F] ln|det P|^2 (k_prep)
+  const void* s;         // SE: [J][I][F][ld] complex reference source images
+  void* dv;              // [J][F][ld] real: frames < N written (and the rest of their vector units as 0)
+  double* dlam;          // [F][J][I]
+  double* dP;            // [F][I][I] complex
+  double* part_buf;      // [F][max_slots][NV]
+  double* lossf;         // [F] per-frequency loss
+  double* loss;          // [1] total
+  unsigned* gcnt;        // arrival counter of k_adj_final
+  unsigned* status;
+};
+
+template <int I, int J, bool SE>
+struct AdjShape {
+  static constexpr int NA = J * I;          // dlambda
+  static constexpr int NP = 2 * I * I;      // dP^* (re, im), [a][i] row-major
+  static constexpr int NL = SE ? 1 : 2;     // SE | NLL: sum |y~|^2/sigma, sum log2 sigma
+  static constexpr int NV = NA + NP + NL;
+};
+
+template <typename T, int I, int J, bool SE>
+__global__ void __launch_bounds__(kBlock) k_adj(AdjArgs a) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  constexpr int FU = Vec<T>::FU;
+  using S = AdjShape<I, J, SE>;
+  constexpr int NA = S::NA, NV = S::NV;
+  using Red = ButterflyReduce<T, NV, kWarps, false>;
+  __shared__ typename Red::Smem red;
+  __shared__ double sP[I][I][2], sQ[I][I][2];
+  __shared__ double sLam[J][I];
+
+  const Partition pt = a.part;
+  const long long u0 = pt.block_start(blockIdx.x), u1 = pt.block_start(blockIdx.x + 1);
+  const long long row = a.ld / FU;
+  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
+  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
+  const VY* __restrict__ s = reinterpret_cast<const VY*>(a.s);
+  VV* __restrict__ dv = reinterpret_cast<VV*>(a.dv);
+
+  for (long long u = u0; u < u1;) {
+    const int f = (int)(u / pt.Uf);
+    const int k0 = (int)(u - (long long)f * pt.Uf);
+    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+    __syncthreads();
+    if (threadIdx.x < I * I) {
+      const int r = threadIdx.x / I, c = threadIdx.x % I;
+      sP[r][c][0] = a.P[((size_t)f * I * I + threadIdx.x) * 2];
+      sP[r][c][1] = a.P[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+      sQ[r][c][0] = a.pinvH[((size_t)f * I * I + threadIdx.x) * 2];
+      sQ[r][c][1] = a.pinvH[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+    }
+    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
+    __syncthreads();
+    T lam[J][I];
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int i = 0; i < I; ++i) lam[j][i] = (T)sLam[j][i];
+    auto Pc = [&](int r, int c) { return mk<T>((T)sP[r][c][0], (T)sP[r][c][1]); };
+    auto Qc = [&](int r, int c) { return mk<T>((T)sQ[r][c][0], (T)sQ[r][c][1]); };
+
+    T acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = (T)0;
+
+    for (int k = k0 + threadIdx.x; k < k1; k += kBlock) {
+      VY yu[I];
+      VV vu[J], dvu[J];
+#pragma unroll
+      for (int m = 0; m < I; ++m) yu[m] = y[((size_t)m * pt.F + f) * row + k];
+#pragma unroll
+      for (int j = 0; j < J; ++j) vu[j] = v[((size_t)j * pt.F + f) * row + k];
+#pragma unroll
+      for (int e = 0; e < FU; ++e) {
+        const bool valid = k * FU + e < a.N;
+        cpx<T> ym[I], yt[I];
+#pragma unroll
+        for (int m = 0; m < I; ++m) ym[m] = valid ? yframe(yu[m], e) : mk<T>(0, 0);
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          cpx<T> t = mk<T>(0, 0);
+#pragma unroll
+          for (int m = 0; m < I; ++m) cfmac(t, Pc(m, i), ym[m]);  // y~_i = sum_m conj(P_mi) y_m
+          yt[i] = t;
+        }
+        T vj[J], sg[I], r[I];
+#pragma unroll
+        for (int j = 0; j < J; ++j) vj[j] = valid ? vframe(vu[j], e) : (T)1;
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          T t = vj[0] * lam[0][i];
+#pragma unroll
+          for (int j = 1; j < J; ++j) t = fma(vj[j], lam[j][i], t);
+          sg[i] = t;
+          r[i] = recip(t);
+        }
+        const T z = valid ? (T)1 : (T)0;  // padding frames contribute nothing
+        if constexpr (!SE) {
+          T t[I];
+#pragma unroll
+          for (int i = 0; i < I; ++i) {
+            const T e2 = cabs2(yt[i]);
+            t[i] = z * r[i] * fma(-e2, r[i], (T)1);
+            acc[NV - 2] = fma(e2, r[i] * z, acc[NV - 2]);
+            acc[NV - 1] += z * (sizeof(T) == 4 ? (T)__log2f((float)sg[i]) : (T)log2((double)sg[i]));
+          }
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            T d = (T)0;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+              d = fma(lam[j][i], t[i], d);
+              acc[j * I + i] = fma(vj[j], t[i], acc[j * I + i]);
+            }
+            vset(dvu[j], e, d);
+          }
+          // column i of sum_n y y^H P diag(1/sigma): y conj(y~_i) / sigma_i
+#pragma unroll
+          for (int m = 0; m < I; ++m)
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+              const cpx<T> c = cmulc(yt[i], ym[m]);  // conj(y~_i) y_m
+              acc[NA + 2 * (m * I + i)] = fma(c.re, r[i], acc[NA + 2 * (m * I + i)]);
+              acc[NA + 2 * (m * I + i) + 1] = fma(c.im, r[i], acc[NA + 2 * (m * I + i) + 1]);
+            }
+        } else {
+          T g[J][I], G[J][I];
+          cpx<T> xh[J][I], b[J][I];
+          T se = (T)0;
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            VY su[I];
+#pragma unroll
+            for (int m = 0; m < I; ++m) su[m] = s[(((size_t)j * I + m) * pt.F + f) * row + k];
+#pragma unroll
+            for (int i = 0; i < I; ++i) g[j][i] = vj[j] * lam[j][i] * r[i];
+            cpx<T> err[I];
+#pragma unroll
+            for (int rr = 0; rr < I; ++rr) {  // x^_j = Q (g_j * y~)
+              cpx<T> x = mk<T>(0, 0);
+#pragma unroll
+              for (int i = 0; i < I; ++i) cfma(x, Qc(rr, i), cscale(yt[i], g[j][i]));
+              xh[j][rr] = x;
+              const cpx<T> sv = valid ? yframe(su[rr], e) : mk<T>(0, 0);
+              err[rr] = csub(x, sv);
+              se = fma(z, cabs2(err[rr]), se);
+            }
+#pragma unroll
+            for (int i = 0; i < I; ++i) {  // b_j = Q^H e_j
+              cpx<T> t = mk<T>(0, 0);
+#pragma unroll
+              for (int rr = 0; rr < I; ++rr) cfmac(t, Qc(rr, i), err[rr]);
+              b[j][i] = t;
+              const cpx<T> cb = cmulc(t, yt[i]);  // conj(b_ji) y~_i
+              G[j][i] = (T)2 * cb.re;
+            }
+          }
+          acc[NV - 1] += se;
+          T h[I];
+#pragma unroll
+          for (int i = 0; i < I; ++i) {
+            T t = (T)0;
+#pragma unroll
+            for (int j = 0; j < J; ++j) t = fma(G[j][i], g[j][i], t);
+            h[i] = t;
+          }
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            T d = (T)0;
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+              const T w = z * (G[j][i] - h[i]) * r[i];
+              d = fma(lam[j][i], w, d);
+              acc[j * I + i] = fma(vj[j], w, acc[j * I + i]);
+            }
+            vset(dvu[j], e, d);
+          }
+          // sum_j (y (g_j * b_j)^H - x^_j b_j^H): entry [a][c]
+#pragma unroll
+          for (int m = 0; m < I; ++m)
+#pragma unroll
+            for (int c = 0; c < I; ++c) {
+              cpx<T> t = mk<T>(0, 0);
+#pragma unroll
+              for (int j = 0; j < J; ++j) {
+                const cpx<T> bc = cconj(b[j][c]);
+                t = cadd(t, cmul(ym[m], cscale(bc, g[j][c])));
+                t = csub(t, cmul(xh[j][m], bc));
+              }
+              acc[NA + 2 * (m * I + c)] = fma(z, t.re, acc[NA + 2 * (m * I + c)]);
+              acc[NA + 2 * (m * I + c) + 1] = fma(z, t.im, acc[NA + 2 * (m * I + c) + 1]);
+            }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < J; ++j) dv[((size_t)j * pt.F + f) * row + k] = dvu[j];
+    }
+    // the segment's sums into slot (f, this CTA)
+    const int slot = (int)blockIdx.x - pt.first_block(f);
+    double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
+    T lo[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) lo[q] = (T)0;
+    Red::run(acc, lo, red, out);
+    u += k1 - k0;
+  }
+}
+
+// One warp per frequency: slot sums (FP64, slot order) into dlam, dP and the
+// frequency's loss; the last warp adds the losses.
+template <typename T, int I, int J, bool SE>
+__global__ void __launch_bounds__(128) k_adj_final(AdjArgs a) {
+  using S = AdjShape<I, J, SE>;
+  constexpr int NA = S::NA, NP = S::NP, NV = S::NV;
+  const int lane = threadIdx.x & 31;
+  const int f = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (f >= a.F) return;  // whole warps only
+  const Partition pt = a.part;
+  const int ns = pt.nslots(f);
+  const double* base = a.part_buf + (size_t)f * pt.max_slots * NV;
+  double lossv = 0.0;
+  for (int q = lane; q < NV; q += 32) {
+    double t = 0.0;
+    for (int k = 0; k < ns; ++k) t += __ldcg(base + (size_t)k * NV + q);
+    if (q < NA) {
+      a.dlam[(size_t)f * NA + q] = t;
+    } else if (q < NA + NP) {
+      const int idx = q - NA;  // 2 (m I + i) + part
+      if constexpr (!SE) t -= (double)a.N * a.pinvH[(size_t)f * I * I * 2 + idx];
+      a.dP[(size_t)f * I * I * 2 + idx] = t;
+    } else if constexpr (SE) {
+      lossv += t;
+    } else {
+      lossv += (q == NV - 2) ? t : 0.69314718055994530942 * t;
+    }
+  }
+  // lanes holding loss terms: NV - NL .. NV - 1
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lossv += __shfl_xor_sync(0xffffffffu, lossv, off);
+  if (lane == 0) {
+    double lf = lossv;
+    if constexpr (!SE) lf += (double)a.N * ((double)I * kLnPi - __ldcg(a.logdet + f));
+    if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
+    a.lossf[f] = lf;
+    __threadfence();
+  }
+  __syncwarp();
+  unsigned last = 0;
+  if (lane == 0) {
+    last = atomicAdd(a.gcnt, 1u) == (unsigned)a.F - 1;
+    if (last) *a.gcnt = 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence();
+    double sacc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sacc[u] = 0.0;
+    for (int g = lane; g < a.F; g += 256) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (g + 32 * u < a.F) sacc[u] += __ldcg(a.lossf + g + 32 * u);
+    }
+    double t = ((sacc[0] + sacc[1]) + (sacc[2] + sacc[3])) + ((sacc[4] + sacc[5]) + (sacc[6] + sacc[7]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) *a.loss = t;
+  }
+}
+
+}  // namespace ffca

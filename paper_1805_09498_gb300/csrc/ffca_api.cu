@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "ffca.h"
+#include "ffca_adjoint.cuh"
 #include "ffca_dispatch.h"
 #include "ffca_stream.cuh"
 
@@ -31,6 +32,25 @@ const FastKernels* fast_kernels(int prec, int I, int J) {
       case 2: return fast_kernels_p1_i2(J);
       case 3: return fast_kernels_p1_i3(J);
       case 4: return fast_kernels_p1_i4(J);
+    }
+  }
+  return nullptr;
+}
+
+const AdjKernels* adj_kernels(int prec, int I, int J) {
+  if (prec == 0) {
+    switch (I) {
+      case 1: return adj_kernels_p0_i1(J);
+      case 2: return adj_kernels_p0_i2(J);
+      case 3: return adj_kernels_p0_i3(J);
+      case 4: return adj_kernels_p0_i4(J);
+    }
+  } else if (prec == 1) {
+    switch (I) {
+      case 1: return adj_kernels_p1_i1(J);
+      case 2: return adj_kernels_p1_i2(J);
+      case 3: return adj_kernels_p1_i3(J);
+      case 4: return adj_kernels_p1_i4(J);
     }
   }
   return nullptr;
@@ -61,6 +81,7 @@ struct Plan {
   Partition pA, pB, pW;
   size_t off_info, off_ustart, off_msum;  // batch: problem tables, per-mixture sums
   size_t off_bstartA, off_slotsA, off_bstartB, off_slotsB;  // batch: CTA ranges, slots per problem
+  size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
 };
@@ -133,6 +154,10 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_tabA = off; off = align_up(off + (size_t)P * k->params_a_bytes);
   p->off_tabB = off; off = align_up(off + (size_t)P * k->params_b_bytes);
   p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)P * J * I);
+  // the adjoint kernels use pass A's partition; J I + 2 I^2 + 2 sums per slot at most
+  p->off_partAdj = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2 * I * I + 2));
+  p->off_lossf = off; off = align_up(off + sizeof(double) * (size_t)P);
+  p->off_loss = off; off = align_up(off + sizeof(double));
   p->off_info = p->off_ustart = p->off_msum = 0;
   p->off_bstartA = p->off_slotsA = p->off_bstartB = p->off_slotsB = 0;
   p->bytes = off;
@@ -238,8 +263,8 @@ FastArgs pass_b_args(const ffca_ctx* c, int slot) {
   return a;
 }
 
-ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, FastArgs& a,
-                   size_t smem = 0) {
+template <typename Args>
+ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, Args& a, size_t smem = 0) {
   void* args[] = {&a};
   TimedLaunch* t = nullptr;
   if (c->timing && !c->use_graph) {
@@ -394,6 +419,53 @@ __global__ void k_mixture_sums(const double* llf, int F, double* out) {
   }
 }
 
+// Gradients of NLL (se = false) or of the Wiener squared error (se = true)
+// at the context's current state: k_prep (P^{-H}, ln|det P|^2), the
+// streaming adjoint pass, the per-frequency finalisation.
+ffca_status adjoint(ffca_ctx* c, bool se, const void* s, void* dv, double* dlam, double* dP, double* loss) {
+  if (!c) return FFCA_ERR_ARG;
+  if (c->plan.off_info) return FFCA_ERR_UNSUPPORTED;  // batch contexts: not provided
+  if (c->d.F == 0) {
+    if (loss) *loss = 0.0;
+    return FFCA_OK;
+  }
+  auto al = [](const void* q, uintptr_t n) { return q && (reinterpret_cast<uintptr_t>(q) % n) == 0; };
+  if (!al(dv, 16) || !al(dlam, 8) || !al(dP, 16) || (se && !al(s, 16))) return FFCA_ERR_ARG;
+  const AdjKernels* k = adj_kernels(c->d.prec, c->d.I, c->d.J);
+  if (!k) return FFCA_ERR_UNSUPPORTED;
+  ffca_status st = launch_prep(c, true);
+  if (st != FFCA_OK) return st;
+  AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.part = c->plan.pA;
+  a.F = c->d.F;
+  a.N = c->d.N;
+  a.ld = c->d.ld;
+  a.y = c->d.y;
+  a.v = c->d.v;
+  a.lam = c->d.lambda;
+  a.P = c->d.P;
+  a.pinvH = reinterpret_cast<const double*>(c->ws + c->plan.off_pinvH);
+  a.logdet = reinterpret_cast<const double*>(c->ws + c->plan.off_logdet);
+  a.s = s;
+  a.dv = dv;
+  a.dlam = dlam;
+  a.dP = dP;
+  a.part_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partAdj);
+  a.lossf = reinterpret_cast<double*>(c->ws + c->plan.off_lossf);
+  a.loss = reinterpret_cast<double*>(c->ws + c->plan.off_loss);
+  a.gcnt = reinterpret_cast<unsigned*>(c->ws + 24);
+  a.status = c->status;
+  if ((st = launch(c, FFCA_KERNEL_ADJ, se ? k->se : k->nll, a.part.nblocks, kBlock, a)) != FFCA_OK) return st;
+  if ((st = launch(c, FFCA_KERNEL_ADJ_FINAL, se ? k->se_final : k->nll_final, (c->d.F + 3) / 4, 128, a)) !=
+      FFCA_OK)
+    return st;
+  if (!loss) return cudaGetLastError() == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
+  if (!cuda_ok(cudaMemcpyAsync(loss, a.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync"))
+    return FFCA_ERR_CUDA;
+  return read_status(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -532,6 +604,14 @@ ffca_status ffca_wiener_host(ffca_ctx* c, void* out_dev, void* out_host) {
   if (bytes && cudaMemcpyAsync(out_host, out_dev, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
     return FFCA_ERR_CUDA;
   return read_status(c);
+}
+
+ffca_status ffca_nll_grad(ffca_ctx* c, void* dv, double* dlam, double* dP, double* loss) {
+  return adjoint(c, false, nullptr, dv, dlam, dP, loss);
+}
+
+ffca_status ffca_wiener_se_grad(ffca_ctx* c, const void* s, void* dv, double* dlam, double* dP, double* loss) {
+  return adjoint(c, true, s, dv, dlam, dP, loss);
 }
 
 ffca_status ffca_timing_enable(ffca_ctx* c, int enable) {

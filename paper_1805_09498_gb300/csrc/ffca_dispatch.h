@@ -32,9 +32,21 @@ struct FcaKernels {
 };
 const FcaKernels* fca_kernels(int prec, int I, int J);
 
+// Adjoint kernels (gradients of NLL and of the Wiener squared error): every
+// kernel takes one AdjArgs by value.
+struct AdjKernels {
+  const void* nll;
+  const void* nll_final;
+  const void* se;
+  const void* se_final;
+  int nv_max;  // partial sums per slot (the larger loss)
+};
+const AdjKernels* adj_kernels(int prec, int I, int J);
+
 #define FFCA_DECLARE_TABLE(P, I) \
   const FastKernels* fast_kernels_p##P##_i##I(int J); \
-  const FcaKernels* fca_kernels_p##P##_i##I(int J);
+  const FcaKernels* fca_kernels_p##P##_i##I(int J); \
+  const AdjKernels* adj_kernels_p##P##_i##I(int J);
 FFCA_DECLARE_TABLE(0, 1)
 FFCA_DECLARE_TABLE(0, 2)
 FFCA_DECLARE_TABLE(0, 3)

@@ -1,6 +1,8 @@
-// Explicit instantiations of the FastFCA-AS kernels (FFCA_PART 0) or of the
-// conventional FCA kernels (FFCA_PART 1) for one precision and one
-// microphone count, J = 1..6.  Compiled once per (FFCA_PART, FFCA_PREC, FFCA_I).
+// Explicit instantiations of the FastFCA-AS kernels (FFCA_PART 0), of the
+// conventional FCA kernels (FFCA_PART 1) or of the adjoint kernels
+// (FFCA_PART 2) for one precision and one microphone count, J = 1..6.
+// Compiled once per (FFCA_PART, FFCA_PREC, FFCA_I).
+#include "ffca_adjoint.cuh"
 #include "ffca_dispatch.h"
 #include "ffca_fca.cuh"
 #include "ffca_stream.cuh"
@@ -12,7 +14,7 @@
 #error "FFCA_I must be defined"
 #endif
 #ifndef FFCA_PART
-#error "FFCA_PART must be defined (0 = FastFCA-AS, 1 = FCA)"
+#error "FFCA_PART must be defined (0 = FastFCA-AS, 1 = FCA, 2 = adjoint)"
 #endif
 
 namespace ffca {
@@ -60,6 +62,21 @@ static const FcaKernels* fca_entry() {
 
 #endif
 
+#if FFCA_PART == 2
+template <int J>
+static const AdjKernels* adj_entry() {
+  static const AdjKernels k = {
+      (const void*)k_adj<Real, FFCA_I, J, false>,
+      (const void*)k_adj_final<Real, FFCA_I, J, false>,
+      (const void*)k_adj<Real, FFCA_I, J, true>,
+      (const void*)k_adj_final<Real, FFCA_I, J, true>,
+      AdjShape<FFCA_I, J, false>::NV,
+  };
+  return &k;
+}
+
+#endif
+
 #define FFCA_CAT2(a, b, c, d) a##b##c##d
 #define FFCA_CAT(a, b, c, d) FFCA_CAT2(a, b, c, d)
 
@@ -87,6 +104,20 @@ const FcaKernels* FFCA_CAT(fca_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
     case 4: return fca_entry<4>();
     case 5: return fca_entry<5>();
     case 6: return fca_entry<6>();
+    default: return nullptr;
+  }
+}
+#endif
+
+#if FFCA_PART == 2
+const AdjKernels* FFCA_CAT(adj_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
+  switch (J) {
+    case 1: return adj_entry<1>();
+    case 2: return adj_entry<2>();
+    case 3: return adj_entry<3>();
+    case 4: return adj_entry<4>();
+    case 5: return adj_entry<5>();
+    case 6: return adj_entry<6>();
     default: return nullptr;
   }
 }

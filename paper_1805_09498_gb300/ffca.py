@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
         "ffca_timing_read": (ci, [vp, dp, P(ctypes.c_ulonglong)]),
         "ffca_iterate_noalloc": (ci, [P(ffca_desc), ci, dp]),
         "ffca_destroy": (None, [vp]),
+        "ffca_nll_grad": (ci, [vp, vp, vp, vp, dp]),
+        "ffca_wiener_se_grad": (ci, [vp, vp, vp, vp, vp, dp]),
         "ffca_batch_workspace_size": (ctypes.c_size_t, [P(ffca_batch_desc)]),
         "ffca_batch_init": (ci, [P(vp), P(ffca_batch_desc)]),
         "ffca_batch_iterate": (ci, [vp, ci, dp]),
@@ -196,7 +198,7 @@ def ffca_wiener_host(ctx, out_dev_ptr: int, out_host_ptr: int) -> None:
                                        ctypes.c_void_p(out_host_ptr)), "ffca_wiener_host")
 
 
-KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener", "psolve", "afinal")
+KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener", "psolve", "afinal", "adj", "adj_final")
 
 
 def ffca_timing_enable(ctx, enable: bool) -> None:
@@ -272,6 +274,23 @@ def ffca_fca_op_counts(ctx):
 
 def ffca_fca_destroy(ctx) -> None:
     lib().ffca_fca_destroy(ctx)
+
+
+def ffca_nll_grad(ctx, dv_ptr: int, dlam_ptr: int, dP_ptr: int) -> float:
+    """Gradients of NLL = -L2 into device buffers; returns NLL."""
+    out = ctypes.c_double()
+    _check(ctx, lib().ffca_nll_grad(ctx, ctypes.c_void_p(dv_ptr), ctypes.c_void_p(dlam_ptr),
+                                    ctypes.c_void_p(dP_ptr), ctypes.byref(out)), "ffca_nll_grad")
+    return out.value
+
+
+def ffca_wiener_se_grad(ctx, s_ptr: int, dv_ptr: int, dlam_ptr: int, dP_ptr: int) -> float:
+    """Gradients of the Wiener squared error against s into device buffers; returns it."""
+    out = ctypes.c_double()
+    _check(ctx, lib().ffca_wiener_se_grad(ctx, ctypes.c_void_p(s_ptr), ctypes.c_void_p(dv_ptr),
+                                          ctypes.c_void_p(dlam_ptr), ctypes.c_void_p(dP_ptr),
+                                          ctypes.byref(out)), "ffca_wiener_se_grad")
+    return out.value
 
 
 def ffca_batch_workspace_size(desc: ffca_batch_desc) -> int:
@@ -384,6 +403,27 @@ class FastFCA:
 
     def sync(self):
         ffca_sync(self.ctx)
+
+    def nll_grad(self):
+        """(NLL, dv, dlam, dPc) at the current state; dPc = dNLL/dP^*."""
+        import torch
+        dv = torch.zeros_like(self.v)
+        dlam = torch.empty_like(self.lam)
+        dP = torch.empty_like(self.P)
+        loss = ffca_nll_grad(self.ctx, dv.data_ptr(), dlam.data_ptr(), dP.data_ptr())
+        return loss, dv, dlam, dP
+
+    def wiener_se_grad(self, s):
+        """(SE, dv, dlam, dPc) of sum |x^ - s|^2 at the current state;
+        s [J, I, F, ld] complex of y's dtype."""
+        import torch
+        if s.dtype != self.y.dtype or s.shape != (self.J, self.I, self.F, self.ld) or not s.is_contiguous():
+            raise ValueError("s must be a contiguous [J, I, F, ld] tensor of y's dtype")
+        dv = torch.zeros_like(self.v)
+        dlam = torch.empty_like(self.lam)
+        dP = torch.empty_like(self.P)
+        loss = ffca_wiener_se_grad(self.ctx, s.data_ptr(), dv.data_ptr(), dlam.data_ptr(), dP.data_ptr())
+        return loss, dv, dlam, dP
 
     def inversion_count(self) -> int:
         return ffca_inversion_count(self.ctx)
@@ -595,3 +635,72 @@ class FCA:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ autograd
+def _autograd_functions():
+    import torch
+
+    def _state(y, v, lam, P, N):
+        # the library borrows contiguous detached copies; the iteration state
+        # of other contexts is not touched
+        return FastFCA(y, v.detach().contiguous().clone(), lam.detach().contiguous().clone(),
+                       P.detach().contiguous().clone(), N=N)
+
+    class NLL(torch.autograd.Function):
+        """NLL(v, lam, P) = -L2 (Eq. L2) on fixed data y; backward runs the
+        adjoint kernel (posteriors recomputed)."""
+
+        @staticmethod
+        def forward(ctx, v, lam, P, y, N):
+            est = _state(y, v, lam, P, N)
+            loss, dv, dlam, dP = est.nll_grad()
+            est.close()
+            ctx.save_for_backward(dv, dlam, dP)
+            return torch.tensor(loss, dtype=torch.float64, device=y.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            dv, dlam, dP = ctx.saved_tensors
+            # torch's gradient of a real loss in a complex input is 2 dL/dz^*
+            return g.to(dv.dtype) * dv, g * dlam, 2.0 * g * dP, None, None
+
+    class WienerSE(torch.autograd.Function):
+        """sum |x^_j - s_j|^2 of the Wiener estimate (Eq. MMSE0) against s."""
+
+        @staticmethod
+        def forward(ctx, v, lam, P, y, s, N):
+            est = _state(y, v, lam, P, N)
+            loss, dv, dlam, dP = est.wiener_se_grad(s)
+            est.close()
+            ctx.save_for_backward(dv, dlam, dP)
+            return torch.tensor(loss, dtype=torch.float64, device=y.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            dv, dlam, dP = ctx.saved_tensors
+            return g.to(dv.dtype) * dv, g * dlam, 2.0 * g * dP, None, None, None
+
+    return NLL, WienerSE
+
+
+_AUTOGRAD = None
+
+
+def nll(v, lam, P, y, N=None):
+    """Differentiable NLL = -L2 (Eq. L2) of (v, lam, P) on fixed data y
+    (layouts of FastFCA).  The gradients come from the adjoint kernel; they
+    are computed with the forward value (one streaming pass)."""
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _autograd_functions()
+    return _AUTOGRAD[0].apply(v, lam, P, y, N)
+
+
+def wiener_se(v, lam, P, y, s, N=None):
+    """Differentiable sum |x^_j - s_j|^2 of the Wiener estimate against the
+    reference images s [J, I, F, ld]."""
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        _AUTOGRAD = _autograd_functions()
+    return _AUTOGRAD[1].apply(v, lam, P, y, s, N)
