@@ -123,12 +123,25 @@ def _dist():
 
 
 def _max_over_ranks(x: float, dist) -> float:
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, ms_max: float, ws: int) -> float:
+    """Weak scaling: every rank processes its own units; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return ws * units_per_rank_step * steps / (ms_max * 1e-3)
+
+
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own mixture (independent problems, no exchange)."""
+    return rank
 
 
 def _sample_freqs(F: int, S: int) -> np.ndarray:
@@ -144,7 +157,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
     _build.build()
     I, J, F, N, iters = cfg["I"], cfg["J"], cfg["F"], cfg["N"], cfg["iters"]
     dev = torch.device("cuda", local)
-    p = make_problem(I, J, F, N, seed=rank, alpha=cfg["alpha"], kappa=cfg["kappa"])
+    p = make_problem(I, J, F, N, seed=rank_seed(rank), alpha=cfg["alpha"], kappa=cfg["kappa"])
     yd, vd, lamd, Pd, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed", device=dev)
     v_init, lam_init, P_init = vd.clone(), lamd.clone(), Pd.clone()
     est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
@@ -180,7 +193,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
     # the conventional FCA EM baseline (Sec. 3.3) on the same mixture and precision
     fca_line = None
     if rank == 0:
-        Pinv = torch.linalg.inv(P_init)
+        Pinv = torch.linalg.inv(P_init.cpu()).to(dev)  # setup only (CPU LAPACK)
         S0 = (Pinv.conj().transpose(1, 2)[:, None] * lam_init[:, :, None, :].to(torch.complex128)
               ) @ Pinv[:, None]
         S0 = S0.contiguous()
@@ -233,7 +246,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
     clk = clocks.stop(t0, t1)
     ms_max = _max_over_ranks(ms, dist)
     units_per_step = N * F * iters
-    value = ws * units_per_step * args.steps / (ms_max * 1e-3)
+    value = whole_job_rate(units_per_step, args.steps, ms_max, ws)
 
     # end to end through the C ABI with pinned host buffers
     y_h = torch.empty(yd.shape, dtype=yd.dtype, pin_memory=True); y_h.copy_(yd)
@@ -274,6 +287,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
     if rank != 0:
         return None
     batched = run_batched(args, dev)
+    adjoint = run_adjoint(dev)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean duration
     peaks, peak_src = _peaks()
@@ -319,7 +333,63 @@ def run_ours(args, cfg, rank, ws, local, dist):
         "fca_gpu": fca_line,
         "speedup_vs_fca_gpu": (value / ws / fca_line["value"]) if fca_line else None,
         "batched": batched,
+        "adjoint": adjoint,
     }
+
+
+def run_adjoint(dev):
+    """The adjoint workload: gradients of NLL = -L2 and of the Wiener
+    estimate's squared error against the known source images with respect to
+    (v, Lambda, P), I = J = 4, F = 257, N = 2000, FP32 per point (c64), the
+    posteriors recomputed in one streaming pass; error against the FP64
+    gradient oracle on sampled frequencies."""
+    import torch
+    from oracle import adjoint as adj
+    from paper_1805_09498_gb300 import ffca
+    cfg = CONFIGS["adjoint"]
+    I, J, F, N = cfg["I"], cfg["J"], cfg["F"], cfg["N"]
+    p = make_problem(I, J, F, N, seed=5, alpha=cfg["alpha"], kappa=cfg["kappa"], keep_images=True)
+    yd, vd, lamd, Pd, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed", device=dev)
+    s = torch.zeros((J, I, F, yd.shape[2]), dtype=torch.complex64)
+    s[..., :N] = torch.from_numpy(p.x).to(torch.complex64)
+    s = s.to(dev)
+    est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+    dv, dl, dP = torch.zeros_like(vd), torch.empty_like(lamd), torch.empty_like(Pd)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"adjoint: I={I} J={J} F={F} N={N}, c64 per point, FP64 per frequency"}
+    fs = _sample_freqs(F, 8)
+    for name, call, ref in (
+            ("nll", lambda: ffca.ffca_nll_grad(est.ctx, dv.data_ptr(), dl.data_ptr(), dP.data_ptr()),
+             lambda: adj.nll_grad(p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs])),
+            ("wiener_se", lambda: ffca.ffca_wiener_se_grad(est.ctx, s.data_ptr(), dv.data_ptr(),
+                                                           dl.data_ptr(), dP.data_ptr()),
+             lambda: adj.wiener_se_grad(p.y[:, fs], p.x[:, :, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs]))):
+        for _ in range(3):
+            call()
+        reps = 20
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            call()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        rv, rl, rP = ref()
+
+        def relerr(g, r, ax):
+            g = np.moveaxis(g, ax, 0).reshape(len(fs), -1)
+            r = np.moveaxis(r, ax, 0).reshape(len(fs), -1)
+            return float(np.max(np.linalg.norm(g - r, axis=1) / np.linalg.norm(r, axis=1)))
+        out[name] = {"value": N * F / (ms * 1e-3), "unit": "TF-points/s (loss + all gradients)",
+                     "ms_per_call": ms,
+                     "error_vs_oracle": {
+                         "v": relerr(dv[:, fs, :N].double().cpu().numpy(), rv, 1),
+                         "lambda": relerr(dl[fs].cpu().numpy(), rl, 0),
+                         "P": relerr(dP[fs].cpu().numpy(), rP, 0),
+                         "measure": f"{len(fs)} sampled frequencies, normwise relative per frequency (max)"}}
+    est.close()
+    return out
 
 
 def run_batched(args, dev):
@@ -405,8 +475,8 @@ def run_batched(args, dev):
         n = int(Ns[m])
         def rel(a_, b_):
             a_ = a_.reshape(F, -1) if a_.dim() > 1 else a_
-            d = torch.linalg.vector_norm(a_ - b_.reshape(a_.shape), dim=-1)
-            return float((d / torch.linalg.vector_norm(b_.reshape(a_.shape), dim=-1)).max())
+            nrm = lambda t: t.abs().pow(2).sum(-1).sqrt()  # noqa: E731
+            return float((nrm(a_ - b_.reshape(a_.shape)) / nrm(b_.reshape(a_.shape))).max())
         e["v"] = max(e["v"], rel(vbv[m][:, :, :n].double().permute(1, 0, 2).contiguous(),
                                  r[2][:, :, :n].permute(1, 0, 2).contiguous()))
         e["lambda"] = max(e["lambda"], rel(lb[m], r[3]))
