@@ -25,6 +25,7 @@ const FastKernels* fast_kernels(int prec, int I, int J) {
       case 2: return fast_kernels_p0_i2(J);
       case 3: return fast_kernels_p0_i3(J);
       case 4: return fast_kernels_p0_i4(J);
+      case 8: return fast_kernels_p0_i8(J);
     }
   } else if (prec == 1) {
     switch (I) {
@@ -32,6 +33,7 @@ const FastKernels* fast_kernels(int prec, int I, int J) {
       case 2: return fast_kernels_p1_i2(J);
       case 3: return fast_kernels_p1_i3(J);
       case 4: return fast_kernels_p1_i4(J);
+      case 8: return fast_kernels_p1_i8(J);
     }
   }
   return nullptr;
@@ -91,7 +93,7 @@ ffca_status check_shape(const ffca_desc* d) {
   if (d->prec != FFCA_PREC_FP64 && d->prec != FFCA_PREC_MIXED) return FFCA_ERR_ARG;
   if (d->F < 0 || d->N < 1 || d->ld < d->N || (d->ld % 4) != 0 || d->K < 1) return FFCA_ERR_ARG;
   if (d->I < 1 || d->J < 1) return FFCA_ERR_ARG;
-  if (d->I > 4 || d->J > 6) return FFCA_ERR_UNSUPPORTED;
+  if ((d->I > 4 && d->I != 8) || d->J > 6) return FFCA_ERR_UNSUPPORTED;
   return FFCA_OK;
 }
 
@@ -119,6 +121,11 @@ ffca_status query_occupancy(const FastKernels* k, Occupancy* o) {
     if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->stream_smem),
                  "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"))
       return FFCA_ERR_CUDA;
+  if (k->solve_smem > 0)
+    for (const void* fn : {k->psolve, k->prep})
+      if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->solve_smem),
+                   "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, solve)"))
+        return FFCA_ERR_CUDA;
   o->occA = o->occB = o->occW = 0;
   const int sthreads = kGroupThreads * k->stream_groups;
   if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occA, k->estep_update, sthreads, k->stream_smem),
@@ -296,7 +303,7 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   FastArgs a = base_args(c);
   a.pinvH = want_pinv ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
   const int G = 32 / c->d.I;  // frequencies per warp
-  return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a);
+  return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
 
 int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
@@ -348,7 +355,7 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
     const int G = 32 / c->d.I;  // problems per warp
-    if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b)) != FFCA_OK) return st;
+    if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
   }
   return FFCA_OK;
 }
@@ -537,7 +544,7 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       const int G = 32 / c->d.I;  // frequencies per warp
-      if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK)
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
@@ -806,7 +813,7 @@ ffca_status batch_check(const ffca_batch_desc* d) {
   if (!d || !d->frame_offset || !d->N) return FFCA_ERR_ARG;
   if (d->prec != FFCA_PREC_FP64 && d->prec != FFCA_PREC_MIXED) return FFCA_ERR_ARG;
   if (d->M < 1 || d->F < 1 || d->K < 1 || d->I < 1 || d->J < 1) return FFCA_ERR_ARG;
-  if (d->I > 4 || d->J > 6) return FFCA_ERR_UNSUPPORTED;
+  if ((d->I > 4 && d->I != 8) || d->J > 6) return FFCA_ERR_UNSUPPORTED;
   if (d->frame_offset[0] != 0 || d->ld != d->frame_offset[d->M] || d->ld > (1ll << 30)) return FFCA_ERR_ARG;
   if ((long long)d->M * d->F > (1ll << 30)) return FFCA_ERR_ARG;
   for (int m = 0; m < d->M; ++m) {

@@ -16,6 +16,7 @@ struct FastKernels {
   const void* afinal_eval;   // log-likelihood-only pass A finalise: per-frequency L2, trace
   int params_a_bytes;        // bytes per frequency of the pass-A parameter table
   int params_b_bytes;        // bytes per frequency of the pass-B parameter table
+  int solve_smem;            // dynamic shared memory of psolve and prep (I > 4), else 0
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.
@@ -51,10 +52,12 @@ FFCA_DECLARE_TABLE(0, 1)
 FFCA_DECLARE_TABLE(0, 2)
 FFCA_DECLARE_TABLE(0, 3)
 FFCA_DECLARE_TABLE(0, 4)
+FFCA_DECLARE_TABLE(0, 8)
 FFCA_DECLARE_TABLE(1, 1)
 FFCA_DECLARE_TABLE(1, 2)
 FFCA_DECLARE_TABLE(1, 3)
 FFCA_DECLARE_TABLE(1, 4)
+FFCA_DECLARE_TABLE(1, 8)
 #undef FFCA_DECLARE_TABLE
 
 }  // namespace ffca

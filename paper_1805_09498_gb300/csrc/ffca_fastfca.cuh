@@ -145,16 +145,17 @@ __global__ void __launch_bounds__(32 * kFinalWarps) k_afinal(FastArgs a) {
   if (f >= a.F) return;  // whole warps only
   const Partition pt = a.part;
   const int ns = pt.nslots(f);
-  if (lane < NA) {
-    const int j = lane / I, i = lane % I;
-    const double tot = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, lane);
-    double* lp = a.lam + (size_t)f * J * I + lane;
+  for (int q = lane; q < NA; q += 32) {
+    const int j = q / I, i = q % I;
+    const double tot = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, q);
+    double* lp = a.lam + (size_t)f * J * I + q;
     const double lnew = *lp * ((double)I * pt.inv_n(f)) * tot;
     if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
     *lp = lnew;
     tab_a<T, I, J>(a, f)->lam[j][i] = (T)lnew;
     tab_b<T, I, J>(a, f)->lam[j][i] = (T)lnew;
-  } else if (lane == NA) {
+  }
+  if (lane == NA % 32) {
     const double quad = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, NA);
     const double lg2 = sum_slots(a.part_buf, f, ns, pt.max_slots, NV, NA + 1);
     const int n = pt.frames(f);

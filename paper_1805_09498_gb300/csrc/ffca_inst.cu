@@ -3,6 +3,7 @@
 // (FFCA_PART 2) for one precision and one microphone count, J = 1..6.
 // Compiled once per (FFCA_PART, FFCA_PREC, FFCA_I).
 #include "ffca_adjoint.cuh"
+#include "ffca_big.cuh"
 #include "ffca_dispatch.h"
 #include "ffca_fca.cuh"
 #include "ffca_stream.cuh"
@@ -28,18 +29,32 @@ using Real = float;
 #if FFCA_PART == 0
 template <int J>
 static const FastKernels* table_entry() {
+  constexpr bool BIG = FFCA_I > 4;  // per-problem solves by elimination instead of cofactors
+  const void* psolve;
+  const void* prep;
+  const void* wiener;
+  if constexpr (BIG) {
+    psolve = (const void*)k_psolve_big<Real, FFCA_I, J>;
+    prep = (const void*)k_prep_big<Real, FFCA_I, J>;
+    wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
+  } else {
+    psolve = (const void*)k_psolve<Real, FFCA_I, J>;
+    prep = (const void*)k_prep<Real, FFCA_I, J>;
+    wiener = (const void*)k_wiener<Real, FFCA_I, J>;
+  }
   static const FastKernels k = {
       Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
       StreamGroups<Real, FFCA_I, J>::value,
       (const void*)k_estep<Real, FFCA_I, J, true>,
       (const void*)k_estep<Real, FFCA_I, J, false>,
       (const void*)k_wcov<Real, FFCA_I, J>,
-      (const void*)k_psolve<Real, FFCA_I, J>,
-      (const void*)k_wiener<Real, FFCA_I, J>,
-      (const void*)k_prep<Real, FFCA_I, J>,
+      psolve,
+      wiener,
+      prep,
       (const void*)k_afinal<Real, FFCA_I, J, false>,
       ParamsA<Real, FFCA_I, J>::BYTES,
       ParamsB<Real, FFCA_I, J>::BYTES,
+      BIG ? BigLane<FFCA_I>::SMEM : 0,
   };
   return &k;
 }

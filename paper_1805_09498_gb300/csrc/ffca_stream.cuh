@@ -97,15 +97,18 @@ struct Tile {
   static constexpr int PARAMS = ParamsA<double, I, J>::BYTES;     // room for either record
   // FFCA_TILE_UNITS_PER_THREAD units per consumer thread where three stages
   // of that size fit the budget, else one
-  static constexpr int T = ((kStreamSmemBudget / G) / (FFCA_TILE_UNITS_PER_THREAD * kConsumers * UB + PARAMS + 16) >= 3
+  static constexpr int T = (((kStreamSmemBudget - (I > 4 ? 32 * 1024 : 0)) / G) /
+                                    (FFCA_TILE_UNITS_PER_THREAD * kConsumers * UB + PARAMS + 16) >= 3
                                 ? FFCA_TILE_UNITS_PER_THREAD
                                 : 1) *
                            kConsumers;  // units per tile
   static constexpr int STAGE = T * UB + PARAMS;                   // bytes per stage, multiple of 16
-  static constexpr int S_FIT = (kStreamSmemBudget / G) / (STAGE + 16);
+  // I > 4: pass B's static reduction buffer (I^3 sums of 7 warps, two floats) takes ~29 KB
+  static constexpr int BUDGET = kStreamSmemBudget - (I > 4 ? 32 * 1024 : 0);
+  static constexpr int S_FIT = (BUDGET / G) / (STAGE + 16);
   static constexpr int S = S_FIT < 2 ? 2 : (S_FIT > FFCA_MAX_STAGES ? FFCA_MAX_STAGES : S_FIT);  // stages
   static constexpr int GROUP = S * STAGE + 2 * S * 8;             // + mbarriers
-  static_assert(G * GROUP <= 227 * 1024, "stages exceed the shared memory of a CTA");
+  static_assert(G * GROUP + (I > 4 ? 32 * 1024 : 0) <= 227 * 1024, "stages exceed the shared memory of a CTA");
 };
 
 // Register cap of the streaming kernels: 128 for two groups per CTA, else
@@ -286,50 +289,65 @@ struct Pipe {
 // the state entering the iteration (Eq. L2).  The loads (FinIn) are issued
 // one problem ahead, so that their latency overlaps the tiles of the
 // current problem.  Called by all 32 lanes.
+template <int I, int J>
 struct FinIn {
-  double tot;  // lane q < J I + 2: slot sum of value q
-  double x;    // lane q < J I: current lambda entry q; lane J I: ln|det P|^2
+  static constexpr int NC = (J * I + 2 + 31) / 32;  // values per lane
+  double tot[NC];  // value q = lane + 32 c < J I + 2: its slot sum
+  double x[NC];    // q < J I: current lambda entry q; q = J I: ln|det P|^2
 };
 
 template <int I, int J>
-__device__ inline FinIn finalize_load(const FastArgs& a, int f) {
+__device__ inline FinIn<I, J> finalize_load(const FastArgs& a, int f) {
   constexpr int NA = J * I;
   constexpr int NV = NA + 2;
-  static_assert(NV <= 32, "one value per lane");
+  using FI = FinIn<I, J>;
   const int lane = threadIdx.x & 31;
   const Partition& pa = a.prev_part;
   const int ns = pa.nslots(f);
   const double* p = a.prev_buf + ((size_t)f * pa.max_slots) * NV;
-  FinIn in{0.0, 0.0};
-  if (lane < NV)
-    for (int k = 0; k < ns; ++k) in.tot += __ldcg(p + (size_t)k * NV + lane);
-  if (lane < NA)
-    in.x = __ldcg(a.lam + (size_t)f * NA + lane);
-  else if (lane == NA)
-    in.x = __ldcg(a.logdet + f);
+  FI in;
+#pragma unroll
+  for (int c = 0; c < FI::NC; ++c) {
+    const int q = lane + 32 * c;
+    in.tot[c] = 0.0;
+    in.x[c] = 0.0;
+    if (q < NV)
+      for (int k = 0; k < ns; ++k) in.tot[c] += __ldcg(p + (size_t)k * NV + q);
+    if (q < NA)
+      in.x[c] = __ldcg(a.lam + (size_t)f * NA + q);
+    else if (q == NA)
+      in.x[c] = __ldcg(a.logdet + f);
+  }
   return in;
 }
 
+// Returns this lane's entries (q = lane + 32 c) of the new Lambda in out[c].
 template <typename T, int I, int J>
-__device__ T finalize_pass_a(const FastArgs& a, int f, const FinIn& in, bool first) {
+__device__ void finalize_pass_a(const FastArgs& a, int f, const FinIn<I, J>& in, bool first,
+                                T (&out)[FinIn<I, J>::NC]) {
   constexpr int NA = J * I;
+  using FI = FinIn<I, J>;
   const int lane = threadIdx.x & 31;
-  const double lg = __shfl_sync(0xffffffffu, in.tot, NA + 1);
-  T out = (T)0;
+  // the log2-sum lives at q = NA + 1: chunk (NA + 1) / 32, lane (NA + 1) % 32
+  const double lg = __shfl_sync(0xffffffffu, in.tot[(NA + 1) / 32], (NA + 1) % 32);
   bool bad = false;
-  if (lane < NA) {
-    const double lnew = in.x * ((double)I * a.part.inv_n(f)) * in.tot;
-    bad = !(lnew > 0.0) || !isfinite(lnew);
-    out = (T)lnew;
-    if (first) a.lam_next[(size_t)f * NA + lane] = lnew;
-  } else if (lane == NA && first) {
-    const int n = a.part.frames(f);
-    const double lf = -(double)I * n * kLnPi + (double)n * in.x - in.tot - 0.69314718055994530942 * lg;
-    bad = !isfinite(lf);
-    a.llf[f] = lf;
+#pragma unroll
+  for (int c = 0; c < FI::NC; ++c) {
+    const int q = lane + 32 * c;
+    out[c] = (T)0;
+    if (q < NA) {
+      const double lnew = in.x[c] * ((double)I * a.part.inv_n(f)) * in.tot[c];
+      bad |= !(lnew > 0.0) || !isfinite(lnew);
+      out[c] = (T)lnew;
+      if (first) a.lam_next[(size_t)f * NA + q] = lnew;
+    } else if (q == NA && first) {
+      const int n = a.part.frames(f);
+      const double lf = -(double)I * n * kLnPi + (double)n * in.x[c] - in.tot[c] - 0.69314718055994530942 * lg;
+      bad |= !isfinite(lf);
+      a.llf[f] = lf;
+    }
   }
   if (bad) raise_status(a.status, kDevNonfinite, f);
-  return out;
 }
 
 // Producer: one thread in pass A, the whole warp in pass B (lane 0 issues
@@ -353,17 +371,18 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
   const bool leader = (threadIdx.x & 31) == 0;
   const Partition& pt = a.part;
   TileIter it(u0, u1, pt, TC::T);
-  T lam_q = (T)0;  // pass B: this lane's entry of the current problem's new Lambda
-  FinIn next_in{0.0, 0.0};
+  using FI = FinIn<I, J>;
+  T lam_q[FI::NC];  // pass B: this lane's entries of the current problem's new Lambda
+  FI next_in;
   if (PASS_B && u1 > u0) next_in = finalize_load<I, J>(a, it.f);
   int pf = -1;
   int t = 0;
   while (it.next()) {
     const int s = t % kStages;
     if (PASS_B && it.f != pf) {
-      const FinIn cur = next_in;
+      const FI cur = next_in;
       if (it.f + 1 < pt.F && pt.start(it.f + 1) < u1) next_in = finalize_load<I, J>(a, it.f + 1);
-      lam_q = finalize_pass_a<T, I, J>(a, it.f, cur, pt.first_block(it.f) == vb);
+      finalize_pass_a<T, I, J>(a, it.f, cur, pt.first_block(it.f) == vb, lam_q);
       pf = it.f;
     }
     int stop = 0;
@@ -382,8 +401,11 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
       // lane q < J I stores its entry of the parameter record; the warp
       // barrier orders these stores before lane 0's arrive, which releases
       // them to the consumers together with the tile
-      if ((int)(threadIdx.x & 31) < NA)
-        (&reinterpret_cast<PB*>(stp + TC::T * TC::UB)->lam[0][0])[threadIdx.x & 31] = lam_q;
+#pragma unroll
+      for (int c = 0; c < FI::NC; ++c) {
+        const int q = (int)(threadIdx.x & 31) + 32 * c;
+        if (q < NA) (&reinterpret_cast<PB*>(stp + TC::T * TC::UB)->lam[0][0])[q] = lam_q[c];
+      }
       __syncwarp();
       if (!leader) {
         ++t;
@@ -564,8 +586,30 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 
   VV* __restrict__ vg = reinterpret_cast<VV*>(a.v);
   const int tid = rl.ctid;
-  L pre[I][I], pim[I][I], lam[J][I];
-  L acc[NV];
+  // I <= 4: P and Lambda in registers for the segment; I > 4 (BIG): read
+  // from the stage's parameter record at each use (I^2 complex values would
+  // not fit the register file)
+  constexpr bool BIG = I > 4;
+  constexpr int RI = BIG ? 1 : I, RJ = BIG ? 1 : J;
+  L pre_r[RI][RI], pim_r[RI][RI], lam_r[RJ][RI];
+  const PA* spc = nullptr;
+  auto PRE = [&](int m, int i) -> L {
+    if constexpr (BIG) return LN::bc(spc->pre[m][i]); else return pre_r[m][i];
+  };
+  auto PIM = [&](int m, int i) -> L {
+    if constexpr (BIG) return LN::bc(spc->pim[m][i]); else return pim_r[m][i];
+  };
+  auto LAM = [&](int j, int i) -> L {
+    if constexpr (BIG) return LN::bc(spc->lam[j][i]); else return lam_r[j][i];
+  };
+  // FP32 with more than 32 sums: one float per value (both frames of a unit
+  // go into it) instead of a packed pair
+  constexpr bool kNarrow = sizeof(T) == 4 && NV > 32;
+  using A = std::conditional_t<kNarrow, float, L>;
+  A acc[NV];
+  auto ACC = [&](int q, L x) {
+    if constexpr (kNarrow) acc[q] += x.v.x + x.v.y; else acc[q] = acc[q] + x;
+  };
 
   TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
@@ -573,26 +617,31 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     const int f = it.f;
     if (seg_new) {
 #pragma unroll
-      for (int q = 0; q < NV; ++q) acc[q] = LN::bc(0);
+      for (int q = 0; q < NV; ++q) {
+        if constexpr (kNarrow) acc[q] = 0.f;
+        else acc[q] = LN::bc(0);
+      }
     }
     const int Np = pt.frames(f);
     const long long rlen = pt.row_len(f, row * FU) / FU;  // units per row of the problem's block
     VV* __restrict__ vrow = vg + (size_t)J * pt.Fm * (pt.frame_off(f) / FU) + (size_t)pt.freq(f) * rlen;
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
-      if (seg_new) {  // this frequency's P and Lambda arrived with the tile
-        const PA& sp = *reinterpret_cast<const PA*>(st + TC::T * TC::UB);
+      spc = reinterpret_cast<const PA*>(st + TC::T * TC::UB);  // every stage carries the record
+      if constexpr (!BIG) {
+        if (seg_new) {  // this frequency's P and Lambda arrived with the tile
 #pragma unroll
-        for (int r = 0; r < I; ++r)
+          for (int r = 0; r < I; ++r)
 #pragma unroll
-          for (int c = 0; c < I; ++c) {
-            pre[r][c] = LN::bc(sp.pre[r][c]);
-            pim[r][c] = LN::bc(sp.pim[r][c]);
-          }
+            for (int c = 0; c < I; ++c) {
+              pre_r[r][c] = LN::bc(spc->pre[r][c]);
+              pim_r[r][c] = LN::bc(spc->pim[r][c]);
+            }
 #pragma unroll
-        for (int j = 0; j < J; ++j)
+          for (int j = 0; j < J; ++j)
 #pragma unroll
-          for (int i = 0; i < I; ++i) lam[j][i] = LN::bc(sp.lam[j][i]);
+            for (int i = 0; i < I; ++i) lam_r[j][i] = LN::bc(spc->lam[j][i]);
+        }
       }
       const VY* ys = reinterpret_cast<const VY*>(st);
       const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
@@ -615,30 +664,30 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 #pragma unroll
         for (int i = 0; i < I; ++i) {
           // y~_i = sum_m conj(P_mi) y_m: re = Pr yr + Pi yi, im = Pr yi - Pi yr
-          L tr = pre[0][i] * yre[0], ti = pre[0][i] * yim[0];
-          tr = vfma(pim[0][i], yim[0], tr);
-          ti = vfma(pim[0][i], nyre[0], ti);
+          L tr = PRE(0, i) * yre[0], ti = PRE(0, i) * yim[0];
+          tr = vfma(PIM(0, i), yim[0], tr);
+          ti = vfma(PIM(0, i), nyre[0], ti);
 #pragma unroll
           for (int m = 1; m < I; ++m) {
-            tr = vfma(pre[m][i], yre[m], tr);
-            tr = vfma(pim[m][i], yim[m], tr);
-            ti = vfma(pre[m][i], yim[m], ti);
-            ti = vfma(pim[m][i], nyre[m], ti);
+            tr = vfma(PRE(m, i), yre[m], tr);
+            tr = vfma(PIM(m, i), yim[m], tr);
+            ti = vfma(PRE(m, i), yim[m], ti);
+            ti = vfma(PIM(m, i), nyre[m], ti);
           }
-          L sg = vv[0] * lam[0][i];
+          L sg = vv[0] * LAM(0, i);
 #pragma unroll
-          for (int j = 1; j < J; ++j) sg = vfma(vv[j], lam[j][i], sg);
+          for (int j = 1; j < J; ++j) sg = vfma(vv[j], LAM(j, i), sg);
           r[i] = vrcp(sg);
           e2[i] = vfma(tr, tr, ti * ti);
           quad = vfma(e2[i], r[i], quad);
           lg = lg + vlog2(sg);
         }
         if (full) {
-          acc[NA] = acc[NA] + quad;
-          acc[NA + 1] = acc[NA + 1] + lg;
+          ACC(NA, quad);
+          ACC(NA + 1, lg);
         } else {
-          acc[NA] = acc[NA] + LN::keep(quad, n0, Np);
-          acc[NA + 1] = acc[NA + 1] + LN::keep(lg, n0, Np);
+          ACC(NA, LN::keep(quad, n0, Np));
+          ACC(NA + 1, LN::keep(lg, n0, Np));
         }
         if constexpr (UPDATE) {
           L w[I];
@@ -650,18 +699,21 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
             L sj = LN::bc(0);
 #pragma unroll
             for (int i = 0; i < I; ++i) {
-              tj[i] = vfma(vv[j] * lam[j][i], w[i], LN::bc(1));
+              tj[i] = vfma(vv[j] * LAM(j, i), w[i], LN::bc(1));
               sj = sj + tj[i];
             }
             const L rs = vrcp(sj);
             const L vn = vv[j] * sj * LN::bc((T)(1.0 / I));
             if (full) {
 #pragma unroll
-              for (int i = 0; i < I; ++i) acc[j * I + i] = vfma(tj[i], rs, acc[j * I + i]);
+              for (int i = 0; i < I; ++i) {
+                if constexpr (kNarrow) ACC(j * I + i, tj[i] * rs);
+                else acc[j * I + i] = vfma(tj[i], rs, acc[j * I + i]);
+              }
               vrow[(size_t)j * pt.Fm * rlen + k] = LN::store(vn);
             } else {
 #pragma unroll
-              for (int i = 0; i < I; ++i) acc[j * I + i] = acc[j * I + i] + LN::keep(tj[i] * rs, n0, Np);
+              for (int i = 0; i < I; ++i) ACC(j * I + i, LN::keep(tj[i] * rs, n0, Np));
               vrow[(size_t)j * pt.Fm * rlen + k] = LN::store(LN::pick(vn, vv[j], n0, Np));
             }
           }
@@ -675,7 +727,15 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     if (it.seg_end) {
       const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
-      if constexpr (sizeof(T) == 4) {
+      if constexpr (kNarrow) {
+        float hi[NV], lo[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          hi[q] = acc[q];
+          lo[q] = 0.f;
+        }
+        Red::run(hi, lo, red, out, rl);
+      } else if constexpr (sizeof(T) == 4) {
         float hi[NV], lo[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
@@ -691,6 +751,145 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         }
         Red::run(hi, lo, red, out, rl);
       }
+      seg_new = true;
+    }
+  }
+}
+
+// Pass B consumers for I > 4: the I^3 sums per point do not fit one thread's
+// registers, so consumer thread c owns the weight index i = c mod I and
+// accumulates V_i = sum_n y y^H / sigma_i (I^2 values, packed Hermitian) over
+// every (kConsumers / I)-th unit of each tile.  At a segment's end the lanes
+// of a warp with the same i (those equal mod I; I divides 32) are summed by
+// shuffles, then the warps through shared memory, in double-float.
+template <typename T, int I, int J, typename Red, int S>
+__device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long u0, long long u1, const Role& rl,
+                                 volatile int* abort, typename Red::Smem& red) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  using LN = Lane<T>;
+  using L = typename LN::L;
+  using TC = Tile<T, I, J>;
+  using PB = ParamsB<T, I, J>;
+  constexpr int FU = Vec<T>::FU;
+  constexpr int I2 = I * I;
+  constexpr int IG = kConsumers / I;  // unit lanes per weight index
+  static_assert(kConsumers % I == 0 && 32 % I == 0, "I must divide the consumer count and the warp");
+  const Partition& pt = a.part;
+  const int tid = rl.ctid, lane = threadIdx.x & 31;
+  const int myi = tid % I, ul = tid / I;
+  L lamv[J];
+  // FP32: one float per value (both frames of a unit go into it)
+  constexpr bool kNarrow = sizeof(T) == 4;
+  using A = std::conditional_t<kNarrow, float, L>;
+  A acc[I2];
+  auto ACC = [&](int q, L wv, L x) {
+    if constexpr (kNarrow) acc[q] = fmaf(wv.v.y, x.v.y, fmaf(wv.v.x, x.v.x, acc[q]));
+    else acc[q] = vfma(wv, x, acc[q]);
+  };
+  TileIter it(u0, u1, pt, TC::T);
+  bool seg_new = true;
+  for (int t = 0; it.next(); ++t) {
+    const int f = it.f;
+    if (seg_new) {
+#pragma unroll
+      for (int q = 0; q < I2; ++q) {
+        if constexpr (kNarrow) acc[q] = 0.f;
+        else acc[q] = LN::bc(0);
+      }
+    }
+    const int Np = pt.frames(f);
+    if (consumer_acquire(a, pp, t, f, abort)) {
+      const unsigned char* st = pp.smem + (size_t)(t % S) * TC::STAGE;
+      if (seg_new) {
+        const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
+#pragma unroll
+        for (int j = 0; j < J; ++j) lamv[j] = LN::bc(sp.lam[j][myi]);
+      }
+      const VY* ys = reinterpret_cast<const VY*>(st);
+      const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
+#pragma unroll 1
+      for (int q = ul; q < it.n; q += IG) {
+        const int n0 = (it.k + q) * FU;
+        if (n0 >= Np) continue;
+        L yre[I], yim[I];
+#pragma unroll
+        for (int m = 0; m < I; ++m) LN::split(ys[m * TC::T + q], yre[m], yim[m]);
+        L sg = LN::real(vs[q]) * lamv[0];
+#pragma unroll
+        for (int j = 1; j < J; ++j) sg = vfma(LN::real(vs[j * TC::T + q]), lamv[j], sg);
+        L w = vrcp(sg);
+        if (n0 + FU > Np) {  // the ragged last unit: drop the frames beyond N
+          w = LN::keep(w, n0, Np);
+#pragma unroll
+          for (int m = 0; m < I; ++m) {
+            yre[m] = LN::keep(yre[m], n0, Np);
+            yim[m] = LN::keep(yim[m], n0, Np);
+          }
+        }
+        int e = I;
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          ACC(r, w, vfma(yre[r], yre[r], yim[r] * yim[r]));
+#pragma unroll
+          for (int c = r + 1; c < I; ++c) {
+            // re(y_r conj(y_c)), im(y_r conj(y_c))
+            ACC(e, w, vfma(yre[r], yre[c], yim[r] * yim[c]));
+            ACC(e + 1, w, vfma(yim[r], yre[c], (yre[r] * yim[c]) * LN::bc(-1)));
+            e += 2;
+          }
+        }
+      }
+    }
+    seg_new = false;
+    consumer_release(pp, t);
+
+    if (it.seg_end) {
+      const int slot = rl.vb - pt.first_block(f);
+      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * (I * I2);
+      T h[I2], l[I2];
+#pragma unroll
+      for (int q = 0; q < I2; ++q) {
+        if constexpr (kNarrow) {
+          h[q] = acc[q];
+          l[q] = 0.f;
+        } else {
+          h[q] = acc[q].v;
+          l[q] = (T)0;
+        }
+      }
+#pragma unroll
+      for (int off = I; off < 32; off <<= 1)
+#pragma unroll
+        for (int q = 0; q < I2; ++q) {
+          const T rh = __shfl_xor_sync(0xffffffffu, h[q], off);
+          if constexpr (sizeof(T) == 4) {
+            const T rlo = __shfl_xor_sync(0xffffffffu, l[q], off);
+            df_add(h[q], l[q], rh, rlo);
+          } else {
+            h[q] += rh;
+          }
+        }
+      if (lane < I) {
+#pragma unroll
+        for (int q = 0; q < I2; ++q) {
+          red.hi[rl.cwarp][lane * I2 + q] = h[q];
+          if constexpr (sizeof(T) == 4) red.lo[rl.cwarp][lane * I2 + q] = l[q];
+        }
+      }
+      consumer_sync(rl.group);
+      for (int vq = tid; vq < I * I2; vq += kConsumers) {
+        T sh = red.hi[0][vq];
+        T sl = (T)0;
+        if constexpr (sizeof(T) == 4) sl = red.lo[0][vq];
+#pragma unroll
+        for (int w2 = 1; w2 < kConsumerWarps; ++w2) {
+          if constexpr (sizeof(T) == 4) df_add(sh, sl, red.hi[w2][vq], red.lo[w2][vq]);
+          else sh += red.hi[w2][vq];
+        }
+        out[vq] = (double)sh + (double)sl;
+      }
+      consumer_sync(rl.group);
       seg_new = true;
     }
   }
@@ -732,121 +931,125 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
     return;
   }
 
-  const int tid = rl.ctid;
-  L lam[J][I];
-  // FP32 with I^3 > 32 sums: one float per value (both frames of a unit go
-  // into it) instead of a packed pair, which keeps the sums in registers
-  constexpr bool kNarrow = sizeof(T) == 4 && NV > 32;
-  using A = std::conditional_t<kNarrow, float, L>;
-  A acc[NV];
+  if constexpr (I > 4) {
+    wcov_consume_big<T, I, J, Red, TC::S>(a, pp, u0, u1, rl, abort, red);
+  } else {
+    const int tid = rl.ctid;
+    L lam[J][I];
+    // FP32 with I^3 > 32 sums: one float per value (both frames of a unit go
+    // into it) instead of a packed pair, which keeps the sums in registers
+    constexpr bool kNarrow = sizeof(T) == 4 && NV > 32;
+    using A = std::conditional_t<kNarrow, float, L>;
+    A acc[NV];
 
-  TileIter it(u0, u1, pt, TC::T);
-  bool seg_new = true;
-  for (int t = 0; it.next(); ++t) {
-    const int f = it.f;
-    if (seg_new) {
-#pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        if constexpr (kNarrow) acc[q] = 0.f;
-        else acc[q] = LN::bc(0);
-      }
-    }
-    const int Np = pt.frames(f);
-    if (consumer_acquire(a, pp, t, f, abort)) {
-      const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
-      if (seg_new) {  // the new Lambda(f) arrived with the tile
-        const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
-#pragma unroll
-        for (int j = 0; j < J; ++j)
-#pragma unroll
-          for (int i = 0; i < I; ++i) lam[j][i] = LN::bc(sp.lam[j][i]);
-      }
-      const VY* ys = reinterpret_cast<const VY*>(st);
-      const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
-#pragma unroll 1
-      for (int q = tid; q < it.n; q += kConsumers) {
-        const int k = it.k + q;
-        const int n0 = k * FU;
-        if (n0 >= Np) continue;
-        L yre[I], yim[I], nyre[I], vv[J];
-#pragma unroll
-        for (int m = 0; m < I; ++m) {
-          LN::split(ys[m * TC::T + q], yre[m], yim[m]);
-          nyre[m] = yre[m] * LN::bc(-1);
+    TileIter it(u0, u1, pt, TC::T);
+    bool seg_new = true;
+    for (int t = 0; it.next(); ++t) {
+      const int f = it.f;
+      if (seg_new) {
+  #pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          if constexpr (kNarrow) acc[q] = 0.f;
+          else acc[q] = LN::bc(0);
         }
-#pragma unroll
-        for (int j = 0; j < J; ++j) vv[j] = LN::real(vs[j * TC::T + q]);
-        L w[I];
-#pragma unroll
-        for (int i = 0; i < I; ++i) {
-          L sg = vv[0] * lam[0][i];
-#pragma unroll
-          for (int j = 1; j < J; ++j) sg = vfma(vv[j], lam[j][i], sg);
-          w[i] = vrcp(sg);
+      }
+      const int Np = pt.frames(f);
+      if (consumer_acquire(a, pp, t, f, abort)) {
+        const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
+        if (seg_new) {  // the new Lambda(f) arrived with the tile
+          const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
+  #pragma unroll
+          for (int j = 0; j < J; ++j)
+  #pragma unroll
+            for (int i = 0; i < I; ++i) lam[j][i] = LN::bc(sp.lam[j][i]);
         }
-        if (n0 + FU > Np) {  // the ragged last unit: drop the frames beyond N
-#pragma unroll
-          for (int i = 0; i < I; ++i) w[i] = LN::keep(w[i], n0, Np);
-#pragma unroll
+        const VY* ys = reinterpret_cast<const VY*>(st);
+        const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
+  #pragma unroll 1
+        for (int q = tid; q < it.n; q += kConsumers) {
+          const int k = it.k + q;
+          const int n0 = k * FU;
+          if (n0 >= Np) continue;
+          L yre[I], yim[I], nyre[I], vv[J];
+  #pragma unroll
           for (int m = 0; m < I; ++m) {
-            yre[m] = LN::keep(yre[m], n0, Np);
-            yim[m] = LN::keep(yim[m], n0, Np);
-            nyre[m] = LN::keep(nyre[m], n0, Np);
+            LN::split(ys[m * TC::T + q], yre[m], yim[m]);
+            nyre[m] = yre[m] * LN::bc(-1);
           }
+  #pragma unroll
+          for (int j = 0; j < J; ++j) vv[j] = LN::real(vs[j * TC::T + q]);
+          L w[I];
+  #pragma unroll
+          for (int i = 0; i < I; ++i) {
+            L sg = vv[0] * lam[0][i];
+  #pragma unroll
+            for (int j = 1; j < J; ++j) sg = vfma(vv[j], lam[j][i], sg);
+            w[i] = vrcp(sg);
+          }
+          if (n0 + FU > Np) {  // the ragged last unit: drop the frames beyond N
+  #pragma unroll
+            for (int i = 0; i < I; ++i) w[i] = LN::keep(w[i], n0, Np);
+  #pragma unroll
+            for (int m = 0; m < I; ++m) {
+              yre[m] = LN::keep(yre[m], n0, Np);
+              yim[m] = LN::keep(yim[m], n0, Np);
+              nyre[m] = LN::keep(nyre[m], n0, Np);
+            }
+          }
+          L pk[I2];
+          int m = I;
+  #pragma unroll
+          for (int rr = 0; rr < I; ++rr) {
+            pk[rr] = vfma(yre[rr], yre[rr], yim[rr] * yim[rr]);
+  #pragma unroll
+            for (int c = rr + 1; c < I; ++c) {
+              pk[m] = vfma(yre[rr], yre[c], yim[rr] * yim[c]);       // re(y_r conj(y_c))
+              pk[m + 1] = vfma(nyre[rr], yim[c], yim[rr] * yre[c]);  // im(y_r conj(y_c))
+              m += 2;
+            }
+          }
+  #pragma unroll
+          for (int i = 0; i < I; ++i)
+  #pragma unroll
+            for (int mm = 0; mm < I2; ++mm) {
+              if constexpr (kNarrow)
+                acc[i * I2 + mm] = fmaf(w[i].v.y, pk[mm].v.y, fmaf(w[i].v.x, pk[mm].v.x, acc[i * I2 + mm]));
+              else
+                acc[i * I2 + mm] = vfma(w[i], pk[mm], acc[i * I2 + mm]);
+            }
         }
-        L pk[I2];
-        int m = I;
-#pragma unroll
-        for (int rr = 0; rr < I; ++rr) {
-          pk[rr] = vfma(yre[rr], yre[rr], yim[rr] * yim[rr]);
-#pragma unroll
-          for (int c = rr + 1; c < I; ++c) {
-            pk[m] = vfma(yre[rr], yre[c], yim[rr] * yim[c]);       // re(y_r conj(y_c))
-            pk[m + 1] = vfma(nyre[rr], yim[c], yim[rr] * yre[c]);  // im(y_r conj(y_c))
-            m += 2;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < I; ++i)
-#pragma unroll
-          for (int mm = 0; mm < I2; ++mm) {
-            if constexpr (kNarrow)
-              acc[i * I2 + mm] = fmaf(w[i].v.y, pk[mm].v.y, fmaf(w[i].v.x, pk[mm].v.x, acc[i * I2 + mm]));
-            else
-              acc[i * I2 + mm] = vfma(w[i], pk[mm], acc[i * I2 + mm]);
-          }
       }
-    }
 
-    seg_new = false;
-    consumer_release(pp, t);
+      seg_new = false;
+      consumer_release(pp, t);
 
-    if (it.seg_end) {
-      const int slot = rl.vb - pt.first_block(f);
-      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
-      if constexpr (kNarrow) {
-        float hi[NV], lo[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          hi[q] = acc[q];
-          lo[q] = 0.f;
+      if (it.seg_end) {
+        const int slot = rl.vb - pt.first_block(f);
+        double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
+        if constexpr (kNarrow) {
+          float hi[NV], lo[NV];
+  #pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            hi[q] = acc[q];
+            lo[q] = 0.f;
+          }
+          Red::run(hi, lo, red, out, rl);
+        } else if constexpr (sizeof(T) == 4) {
+          float hi[NV], lo[NV];
+  #pragma unroll
+          for (int q = 0; q < NV; ++q) two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);
+          Red::run(hi, lo, red, out, rl);
+        } else {
+          double hi[NV], lo[NV];
+  #pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            hi[q] = acc[q].v;
+            lo[q] = 0.0;
+          }
+          Red::run(hi, lo, red, out, rl);
         }
-        Red::run(hi, lo, red, out, rl);
-      } else if constexpr (sizeof(T) == 4) {
-        float hi[NV], lo[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);
-        Red::run(hi, lo, red, out, rl);
-      } else {
-        double hi[NV], lo[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          hi[q] = acc[q].v;
-          lo[q] = 0.0;
-        }
-        Red::run(hi, lo, red, out, rl);
+        seg_new = true;
       }
-      seg_new = true;
     }
   }
 }
