@@ -409,6 +409,9 @@ def run_batched(args, dev):
     units = int(np.sum(Ns)) * F * iters
     stream = torch.cuda.current_stream(dev)
     est = ffca.FastFCABatch(y, v, lam, P, Ns, graph=True)
+    # partition autotuning on real iterations (setup, not timed), then back to the initial state
+    cand_a, cand_b, ms_a, ms_b = est.autotune(rounds=2)
+    v.copy_(v_init); lam.copy_(lam_init); P.copy_(P_init)
 
     def reset():
         v.copy_(v_init); lam.copy_(lam_init); P.copy_(P_init)
@@ -493,6 +496,10 @@ def run_batched(args, dev):
                         f"c64, {iters} iterations",
             "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms, "runs_timed": reps,
             "graph": True, "gpu_launches_per_run": launches, "kernels": kernels,
+            "autotune": {"chosen": {"pass_a": cand_a, "pass_b": cand_b},
+                         "ms_per_candidate": {"pass_a": [round(x, 4) for x in ms_a],
+                                              "pass_b": [round(x, 4) for x in ms_b]},
+                         "candidates": "per-segment cost (frames) x grid waves; 0 = default"},
             "sequential_fp64": {"value": units / (ms_seq * 1e-3), "unit": UNIT, "ms_total": ms_seq,
                                 "runs": M},
             "speedup_vs_sequential_fp64": ms_seq / ms, "error_vs_fp64": e}

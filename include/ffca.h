@@ -267,6 +267,23 @@ ffca_status ffca_batch_loglik(ffca_batch_ctx* ctx, double* ll);
  * launched on the context stream; per-kernel timing is not recorded for
  * replays, launch counts are.  Works on single and batch contexts. */
 ffca_status ffca_set_graph(ffca_ctx* ctx, int enable);
+/* Batch work partitions: ffca_batch_config_count() candidates per streaming
+ * pass, each a choice of the per-problem cost the CTA ranges balance and of
+ * the grid size; candidate 0 is the default.  All candidates give the same
+ * estimates up to the order of the floating-point sums.
+ *
+ * ffca_batch_autotune runs rounds x ffca_batch_config_count() hybrid
+ * iterations of the batch (they advance the estimate like ffca_batch_iterate),
+ * candidate q on iteration q of each round, times pass A and pass B of each
+ * with CUDA events, and keeps the fastest candidate of each pass.  Outputs
+ * (any may be NULL): the chosen candidates, and per-candidate mean pass times
+ * in ms (host arrays of ffca_batch_config_count() doubles).  Synchronises.
+ * ffca_batch_set_config selects candidates directly (for reproducible
+ * summation order across runs). */
+int ffca_batch_config_count(void);
+ffca_status ffca_batch_autotune(ffca_batch_ctx* ctx, int rounds, int* cand_a, int* cand_b, double* ms_a,
+                                double* ms_b);
+ffca_status ffca_batch_set_config(ffca_batch_ctx* ctx, int cand_a, int cand_b);
 /* Release a batch context (host memory only; the graph, if any). */
 void ffca_batch_destroy(ffca_batch_ctx* ctx);
 

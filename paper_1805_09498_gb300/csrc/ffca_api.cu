@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "ffca.h"
@@ -64,6 +65,19 @@ namespace {
 
 constexpr size_t kAlign = 256;
 
+// Candidate partitions of a batch (ffca_batch_autotune): the fixed cost per
+// problem segment the CTA ranges balance, in frames of streaming work, and
+// the grid size in waves of resident CTAs.  Candidate 0 is the default: the
+// segment costs measured on GB300 for the batched workload's shapes (about
+// 1.8 us in pass A and 2.6 us in pass B per segment), one wave.
+struct PartCand {
+  long long seg_frames;
+  int waves;
+};
+constexpr int kCands = 6;
+constexpr PartCand kCandA[kCands] = {{1024, 1}, {0, 1}, {256, 1}, {4096, 1}, {1024, 2}, {4096, 2}};
+constexpr PartCand kCandB[kCands] = {{2048, 1}, {0, 1}, {512, 1}, {8192, 1}, {2048, 2}, {8192, 2}};
+
 // CTAs of the streaming passes per resident CTA slot.
 #ifndef FFCA_GRID_WAVES
 #define FFCA_GRID_WAVES 1
@@ -82,7 +96,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Plan {
   Partition pA, pB, pW;
   size_t off_info, off_ustart, off_msum;  // batch: problem tables, per-mixture sums
-  size_t off_bstartA, off_slotsA, off_bstartB, off_slotsB;  // batch: CTA ranges, slots per problem
+  size_t off_bstartA[kCands], off_slotsA[kCands], off_bstartB[kCands], off_slotsB[kCands];  // batch candidates
   size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
@@ -166,7 +180,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_lossf = off; off = align_up(off + sizeof(double) * (size_t)P);
   p->off_loss = off; off = align_up(off + sizeof(double));
   p->off_info = p->off_ustart = p->off_msum = 0;
-  p->off_bstartA = p->off_slotsA = p->off_bstartB = p->off_slotsB = 0;
+  for (int q = 0; q < kCands; ++q) p->off_bstartA[q] = p->off_slotsA[q] = p->off_bstartB[q] = p->off_slotsB[q] = 0;
   p->bytes = off;
 }
 
@@ -203,6 +217,9 @@ struct ffca_ctx {
   Plan plan;
   int M;        // mixtures (1 for the single-mixture API)
   int Fm;       // frequencies per mixture
+  // batch: the candidate partitions of each pass (device tables attached) and the ones in use
+  Partition candA[kCands], candB[kCands];
+  int curA, curB;
   // CUDA graph of the iteration loop (batch API)
   int use_graph;
   int graph_iters;
@@ -826,16 +843,11 @@ ffca_status batch_check(const ffca_batch_desc* d) {
 // Host copies of a batch's device tables.
 struct BatchTables {
   std::vector<ProbInfo> info;
-  std::vector<long long> ustart, bstartA, bstartB;
-  std::vector<int2> slotsA, slotsB;
+  std::vector<long long> ustart;
+  std::vector<long long> bstartA[kCands], bstartB[kCands];
+  std::vector<int2> slotsA[kCands], slotsB[kCands];
+  Partition candA[kCands], candB[kCands];
 };
-
-// Fixed cost of a problem segment in a CTA (its reduction and parameter
-// hand-over), in frames of streaming work: the ragged partition balances
-// units + this per problem (measured on GB300 for the batched workload's
-// shapes: about 1.8 us in pass A and 2.6 us in pass B per segment).
-constexpr long long kSegCostFramesA = 1024;
-constexpr long long kSegCostFramesB = 2048;
 
 ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, BatchTables* t) {
   Occupancy o;
@@ -857,29 +869,57 @@ ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, 
     }
   }
   t->ustart[P] = u;
-  const int maxA = o.nsm * o.occA * k->stream_groups, maxB = o.nsm * o.occB * k->stream_groups;
-  t->bstartA.resize(maxA + 1);
-  t->bstartB.resize(maxB + 1);
-  t->slotsA.resize(P);
-  t->slotsB.resize(P);
-  p->pA = make_partition_ragged(P, d->F, t->ustart.data(), maxA, kSegCostFramesA / FU, t->bstartA.data(),
-                                t->slotsA.data());
-  p->pB = make_partition_ragged(P, d->F, t->ustart.data(), maxB, kSegCostFramesB / FU, t->bstartB.data(),
-                                t->slotsB.data());
-  t->bstartA.resize(p->pA.nblocks + 1);
-  t->bstartB.resize(p->pB.nblocks + 1);
+  const int slotsA = o.nsm * o.occA * k->stream_groups, slotsB = o.nsm * o.occB * k->stream_groups;
+  int msA = 1, msB = 1;
+  for (int c = 0; c < kCands; ++c) {
+    const int maxA = slotsA * kCandA[c].waves, maxB = slotsB * kCandB[c].waves;
+    t->bstartA[c].resize(maxA + 1);
+    t->bstartB[c].resize(maxB + 1);
+    t->slotsA[c].resize(P);
+    t->slotsB[c].resize(P);
+    t->candA[c] = make_partition_ragged(P, d->F, t->ustart.data(), maxA, kCandA[c].seg_frames / FU,
+                                        t->bstartA[c].data(), t->slotsA[c].data());
+    t->candB[c] = make_partition_ragged(P, d->F, t->ustart.data(), maxB, kCandB[c].seg_frames / FU,
+                                        t->bstartB[c].data(), t->slotsB[c].data());
+    t->bstartA[c].resize(t->candA[c].nblocks + 1);
+    t->bstartB[c].resize(t->candB[c].nblocks + 1);
+    msA = std::max(msA, t->candA[c].max_slots);
+    msB = std::max(msB, t->candB[c].max_slots);
+  }
+  // one slot stride for every candidate: the buffers hold the largest
+  for (int c = 0; c < kCands; ++c) {
+    t->candA[c].max_slots = msA;
+    t->candB[c].max_slots = msB;
+  }
+  p->pA = t->candA[0];
+  p->pB = t->candB[0];
   p->pW = make_partition(1, 2, 1);  // unused: the Wiener filter runs per mixture
   layout(p, k, P, d->I, d->J);
   size_t off = p->bytes;
   p->off_info = off; off = align_up(off + sizeof(ProbInfo) * (size_t)P);
   p->off_ustart = off; off = align_up(off + sizeof(long long) * (size_t)(P + 1));
   p->off_msum = off; off = align_up(off + sizeof(double) * (size_t)d->M);
-  p->off_bstartA = off; off = align_up(off + sizeof(long long) * t->bstartA.size());
-  p->off_bstartB = off; off = align_up(off + sizeof(long long) * t->bstartB.size());
-  p->off_slotsA = off; off = align_up(off + sizeof(int2) * (size_t)P);
-  p->off_slotsB = off; off = align_up(off + sizeof(int2) * (size_t)P);
+  for (int c = 0; c < kCands; ++c) {
+    p->off_bstartA[c] = off; off = align_up(off + sizeof(long long) * t->bstartA[c].size());
+    p->off_bstartB[c] = off; off = align_up(off + sizeof(long long) * t->bstartB[c].size());
+    p->off_slotsA[c] = off; off = align_up(off + sizeof(int2) * (size_t)P);
+    p->off_slotsB[c] = off; off = align_up(off + sizeof(int2) * (size_t)P);
+  }
   p->bytes = off;
   return FFCA_OK;
+}
+
+// Switch a batch context to candidates (ia, ib); a captured graph holds the
+// old partitions and is dropped.
+void use_candidates(ffca_ctx* c, int ia, int ib) {
+  c->curA = ia;
+  c->curB = ib;
+  c->plan.pA = c->candA[ia];
+  c->plan.pB = c->candB[ib];
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
 }
 
 }  // namespace
@@ -939,29 +979,34 @@ ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* d) {
   c->err_f = -1;
   const ProbInfo* dinfo = reinterpret_cast<const ProbInfo*>(c->ws + p.off_info);
   const long long* dustart = reinterpret_cast<const long long*>(c->ws + p.off_ustart);
-  for (Partition* q : {&c->plan.pA, &c->plan.pB}) {
-    q->info = dinfo;
-    q->ustart = dustart;
-  }
-  c->plan.pA.bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartA);
-  c->plan.pB.bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartB);
-  c->plan.pA.slots = reinterpret_cast<const int2*>(c->ws + p.off_slotsA);
-  c->plan.pB.slots = reinterpret_cast<const int2*>(c->ws + p.off_slotsB);
   auto up = [&](size_t off, const void* src, size_t n, const char* what) {
     return cuda_ok(cudaMemcpyAsync(c->ws + off, src, n, cudaMemcpyHostToDevice, c->stream), what);
   };
   // pageable sources: the copies are staged before the calls return
-  if (!cuda_ok(cudaMemsetAsync(c->ws, 0, p.bytes, c->stream), "cudaMemsetAsync") ||
-      !up(p.off_info, t.info.data(), sizeof(ProbInfo) * t.info.size(), "cudaMemcpyAsync(problems)") ||
-      !up(p.off_ustart, t.ustart.data(), sizeof(long long) * t.ustart.size(), "cudaMemcpyAsync(unit starts)") ||
-      !up(p.off_bstartA, t.bstartA.data(), sizeof(long long) * t.bstartA.size(), "cudaMemcpyAsync(ranges A)") ||
-      !up(p.off_bstartB, t.bstartB.data(), sizeof(long long) * t.bstartB.size(), "cudaMemcpyAsync(ranges B)") ||
-      !up(p.off_slotsA, t.slotsA.data(), sizeof(int2) * t.slotsA.size(), "cudaMemcpyAsync(slots A)") ||
-      !up(p.off_slotsB, t.slotsB.data(), sizeof(int2) * t.slotsB.size(), "cudaMemcpyAsync(slots B)") ||
-      !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) {
+  bool ok = cuda_ok(cudaMemsetAsync(c->ws, 0, p.bytes, c->stream), "cudaMemsetAsync") &&
+            up(p.off_info, t.info.data(), sizeof(ProbInfo) * t.info.size(), "cudaMemcpyAsync(problems)") &&
+            up(p.off_ustart, t.ustart.data(), sizeof(long long) * t.ustart.size(), "cudaMemcpyAsync(unit starts)");
+  for (int q = 0; q < kCands && ok; ++q) {
+    c->candA[q] = t.candA[q];
+    c->candB[q] = t.candB[q];
+    for (Partition* pp : {&c->candA[q], &c->candB[q]}) {
+      pp->info = dinfo;
+      pp->ustart = dustart;
+    }
+    c->candA[q].bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartA[q]);
+    c->candB[q].bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartB[q]);
+    c->candA[q].slots = reinterpret_cast<const int2*>(c->ws + p.off_slotsA[q]);
+    c->candB[q].slots = reinterpret_cast<const int2*>(c->ws + p.off_slotsB[q]);
+    ok = up(p.off_bstartA[q], t.bstartA[q].data(), sizeof(long long) * t.bstartA[q].size(), "cudaMemcpyAsync(ranges A)") &&
+         up(p.off_bstartB[q], t.bstartB[q].data(), sizeof(long long) * t.bstartB[q].size(), "cudaMemcpyAsync(ranges B)") &&
+         up(p.off_slotsA[q], t.slotsA[q].data(), sizeof(int2) * t.slotsA[q].size(), "cudaMemcpyAsync(slots A)") &&
+         up(p.off_slotsB[q], t.slotsB[q].data(), sizeof(int2) * t.slotsB[q].size(), "cudaMemcpyAsync(slots B)");
+  }
+  if (!ok || !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) {
     std::free(c);
     return FFCA_ERR_CUDA;
   }
+  use_candidates(c, 0, 0);
   *out = c;
   return FFCA_OK;
 }
@@ -987,6 +1032,69 @@ ffca_status ffca_batch_loglik(ffca_batch_ctx* c, double* ll) {
       !cuda_ok(cudaMemcpyAsync(ll, msum, sizeof(double) * c->M, cudaMemcpyDeviceToHost, c->stream),
                "cudaMemcpyAsync"))
     return FFCA_ERR_CUDA;
+  return read_status(c);
+}
+
+ffca_status ffca_batch_set_config(ffca_batch_ctx* c, int cand_a, int cand_b) {
+  if (!c || c->M < 1 || cand_a < 0 || cand_a >= kCands || cand_b < 0 || cand_b >= kCands) return FFCA_ERR_ARG;
+  use_candidates(c, cand_a, cand_b);
+  return FFCA_OK;
+}
+
+int ffca_batch_config_count(void) { return kCands; }
+
+ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int* cand_b, double* ms_a,
+                                double* ms_b) {
+  if (!c || c->M < 1 || rounds < 1) return FFCA_ERR_ARG;
+  cudaEvent_t ev[kCands][3];
+  for (int q = 0; q < kCands; ++q)
+    for (int e = 0; e < 3; ++e)
+      if (!cuda_ok(cudaEventCreate(&ev[q][e]), "cudaEventCreate")) return FFCA_ERR_CUDA;
+  double ta[kCands] = {}, tb[kCands] = {};
+  ffca_status st = launch_prep(c, false);
+  for (int r = 0; r < rounds && st == FFCA_OK; ++r) {
+    for (int q = 0; q < kCands && st == FFCA_OK; ++q) {
+      use_candidates(c, q, q);
+      // one hybrid iteration, pass A and pass B bracketed by events
+      FastArgs a = pass_a_args(c, 0);
+      cudaEventRecord(ev[q][0], c->stream);
+      st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, stream_grid(c, a.part), stream_threads(c), a,
+                  c->kern->stream_smem);
+      cudaEventRecord(ev[q][1], c->stream);
+      FastArgs b = pass_b_args(c, 0);
+      b.trace = nullptr;
+      if (st == FFCA_OK)
+        st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
+                    c->kern->stream_smem);
+      cudaEventRecord(ev[q][2], c->stream);
+      const int G = 32 / c->d.I;
+      if (st == FFCA_OK)
+        st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem);
+    }
+    if (st == FFCA_OK && !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) st = FFCA_ERR_CUDA;
+    for (int q = 0; q < kCands && st == FFCA_OK; ++q) {
+      float x = 0.f, y = 0.f;
+      cudaEventElapsedTime(&x, ev[q][0], ev[q][1]);
+      cudaEventElapsedTime(&y, ev[q][1], ev[q][2]);
+      ta[q] += x;
+      tb[q] += y;
+    }
+  }
+  for (int q = 0; q < kCands; ++q)
+    for (int e = 0; e < 3; ++e) cudaEventDestroy(ev[q][e]);
+  if (st != FFCA_OK) return st;
+  int ba = 0, bb = 0;
+  for (int q = 1; q < kCands; ++q) {
+    if (ta[q] < ta[ba]) ba = q;
+    if (tb[q] < tb[bb]) bb = q;
+  }
+  use_candidates(c, ba, bb);
+  if (cand_a) *cand_a = ba;
+  if (cand_b) *cand_b = bb;
+  for (int q = 0; q < kCands; ++q) {
+    if (ms_a) ms_a[q] = ta[q] / rounds;
+    if (ms_b) ms_b[q] = tb[q] / rounds;
+  }
   return read_status(c);
 }
 

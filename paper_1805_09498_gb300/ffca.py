@@ -108,6 +108,9 @@ def lib() -> ctypes.CDLL:
         "ffca_batch_iterate": (ci, [vp, ci, dp]),
         "ffca_batch_loglik": (ci, [vp, dp]),
         "ffca_set_graph": (ci, [vp, ci]),
+        "ffca_batch_config_count": (ci, []),
+        "ffca_batch_autotune": (ci, [vp, ci, P(ci), P(ci), dp, dp]),
+        "ffca_batch_set_config": (ci, [vp, ci, ci]),
         "ffca_batch_destroy": (None, [vp]),
         "ffca_fca_workspace_size": (ctypes.c_size_t, [P(ffca_fca_desc)]),
         "ffca_fca_init": (ci, [P(vp), P(ffca_fca_desc)]),
@@ -319,6 +322,25 @@ def ffca_batch_loglik(ctx, M: int) -> np.ndarray:
     buf = (ctypes.c_double * M)()
     _check(ctx, lib().ffca_batch_loglik(ctx, buf), "ffca_batch_loglik")
     return np.frombuffer(buf, dtype=np.float64).copy()
+
+
+def ffca_batch_config_count() -> int:
+    return int(lib().ffca_batch_config_count())
+
+
+def ffca_batch_autotune(ctx, rounds: int = 1):
+    """Tune the batch's partitions on real iterations; returns
+    (cand_a, cand_b, ms_a[], ms_b[])."""
+    n = ffca_batch_config_count()
+    ca, cb = ctypes.c_int(), ctypes.c_int()
+    ma, mb = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+    _check(ctx, lib().ffca_batch_autotune(ctx, rounds, ctypes.byref(ca), ctypes.byref(cb), ma, mb),
+           "ffca_batch_autotune")
+    return ca.value, cb.value, list(ma), list(mb)
+
+
+def ffca_batch_set_config(ctx, cand_a: int, cand_b: int) -> None:
+    _check(ctx, lib().ffca_batch_set_config(ctx, cand_a, cand_b), "ffca_batch_set_config")
 
 
 def ffca_set_graph(ctx, enable: bool) -> None:
@@ -564,6 +586,14 @@ class FastFCABatch:
     def loglik(self) -> np.ndarray:
         """L2 of every mixture (host array of M values)."""
         return ffca_batch_loglik(self.ctx, self.M)
+
+    def autotune(self, rounds: int = 1):
+        """Pick the fastest work partition of each pass on real iterations
+        (rounds x ffca_batch_config_count() of them, advancing the estimate)."""
+        return ffca_batch_autotune(self.ctx, rounds)
+
+    def set_config(self, cand_a: int, cand_b: int):
+        ffca_batch_set_config(self.ctx, cand_a, cand_b)
 
     def sync(self):
         ffca_sync(self.ctx)

@@ -176,3 +176,56 @@ def test_invalid_batches_are_rejected():
         ffca.ffca_wiener(est.ctx, out.data_ptr())
     assert ei.value.status == 7
     est.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_autotune_iterations_are_iterations(prec):
+    """ffca_batch_autotune runs real hybrid iterations (one per candidate
+    partition); with two more ordinary iterations the state equals the
+    oracle's after the same total number of iterations."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    probs = make_batch(4, 3, 5, [300, 41, 1200, 96, 700], seed=13)
+    n_auto = ffca.ffca_batch_config_count()
+    refs = [ffa.iterate(p.y, p.v0, p.lam0, p.P0, n_auto + 2, counter=OpCounter()) for p in probs]
+    y, v, lam, P, Ns, off = ffca.batch_to_device([p.y for p in probs], [p.v0 for p in probs],
+                                                 [p.lam0 for p in probs], [p.P0 for p in probs], prec=prec)
+    est = ffca.FastFCABatch(y, v, lam, P, Ns)
+    ca, cb, ma, mb = est.autotune(rounds=1)
+    assert 0 <= ca < n_auto and 0 <= cb < n_auto and all(t > 0 for t in ma + mb)
+    est.iterate(2, trace=False)
+    ll = est.loglik()
+    torch.cuda.synchronize()
+    vh = v.double().cpu()
+    got = dict(v=[b[:, :, :Ns[m]].numpy() for m, b in enumerate(ffca.batch_views(vh, 3, 5, off))],
+               lam=lam.cpu().numpy(), P=P.cpu().numpy(), ll=ll,
+               trace=np.sum([r[3] for r in refs], axis=0))  # no trace from the tuning run
+    _check(prec, probs, refs, got)
+    est.close()
+
+
+def test_fixed_config_is_reproducible():
+    """Every candidate partition gives the oracle's result; a fixed candidate
+    gives the same bits on every run."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    probs = make_batch(3, 3, 4, [150, 900, 33], seed=14)
+    refs = [ffa.iterate(p.y, p.v0, p.lam0, p.P0, 3, counter=OpCounter()) for p in probs]
+    outs = {}
+    for cand in range(ffca.ffca_batch_config_count()):
+        for rep in range(2 if cand == 3 else 1):
+            y, v, lam, P, Ns, off = ffca.batch_to_device([p.y for p in probs], [p.v0 for p in probs],
+                                                         [p.lam0 for p in probs], [p.P0 for p in probs])
+            est = ffca.FastFCABatch(y, v, lam, P, Ns)
+            est.set_config(cand, cand)
+            tr = est.iterate(3)
+            ll = est.loglik()
+            torch.cuda.synchronize()
+            vh = v.double().cpu()
+            got = dict(v=[b[:, :, :Ns[m]].numpy() for m, b in enumerate(ffca.batch_views(vh, 3, 4, off))],
+                       lam=lam.cpu().numpy(), P=P.cpu().numpy(), ll=ll, trace=tr)
+            _check("mixed", probs, refs, got)
+            outs.setdefault(cand, []).append((vh.numpy(), got["lam"], got["P"]))
+            est.close()
+    a, b = outs[3]
+    assert all(np.array_equal(x, z) for x, z in zip(a, b))
