@@ -24,8 +24,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
-I_VALUES = (1, 2, 3, 4, 8)      # FastFCA-AS
-I_VALUES_SMALL = (1, 2, 3, 4)   # conventional FCA, adjoint
+I_VALUES = (1, 2, 3, 4, 8)      # FastFCA-AS, conventional FCA
+I_VALUES_SMALL = (1, 2, 3, 4)   # adjoint
 
 
 def _nvcc():
@@ -40,7 +40,7 @@ def _units():
     units = [("ffca_api.cu", "ffca_api.o", []), ("ffca_fca_api.cu", "ffca_fca_api.o", [])]
     for part in (0, 1, 2):  # FastFCA-AS, conventional FCA, adjoint
         for prec in (0, 1):
-            for i in (I_VALUES if part == 0 else I_VALUES_SMALL):
+            for i in (I_VALUES if part in (0, 1) else I_VALUES_SMALL):
                 units.append(("ffca_inst.cu", f"ffca_inst_k{part}_p{prec}_i{i}.o",
                               [f"-DFFCA_PART={part}", f"-DFFCA_PREC={prec}", f"-DFFCA_I={i}"]))
     return units

@@ -29,7 +29,10 @@ struct FcaKernels {
   const void* em_eval;
   const void* final_update;
   const void* final_eval;
-  int params_bytes;  // bytes per frequency of the S_j, S_j^{-1} table
+  int params_bytes;  // bytes per frequency of the S_j (, S_j^{-1}) table
+  int nv;            // partial sums per slot
+  int em_smem;       // dynamic shared memory of the EM pass
+  int final_block;   // threads per block of the finalise kernel (per frequency: 1 or a warp)
 };
 const FcaKernels* fca_kernels(int prec, int I, int J);
 

@@ -20,6 +20,7 @@ const FcaKernels* fca_kernels(int prec, int I, int J) {
       case 2: return fca_kernels_p0_i2(J);
       case 3: return fca_kernels_p0_i3(J);
       case 4: return fca_kernels_p0_i4(J);
+      case 8: return fca_kernels_p0_i8(J);
     }
   } else if (prec == 1) {
     switch (I) {
@@ -27,6 +28,7 @@ const FcaKernels* fca_kernels(int prec, int I, int J) {
       case 2: return fca_kernels_p1_i2(J);
       case 3: return fca_kernels_p1_i3(J);
       case 4: return fca_kernels_p1_i4(J);
+      case 8: return fca_kernels_p1_i8(J);
     }
   }
   return nullptr;
@@ -50,7 +52,7 @@ ffca_status fca_check_shape(const ffca_fca_desc* d) {
   if (d->prec != FFCA_PREC_FP64 && d->prec != FFCA_PREC_MIXED) return FFCA_ERR_ARG;
   if (d->F < 0 || d->N < 1 || d->ld < d->N || (d->ld % 4) != 0) return FFCA_ERR_ARG;
   if (d->I < 1 || d->J < 1) return FFCA_ERR_ARG;
-  if (d->I > 4 || d->J > 6) return FFCA_ERR_UNSUPPORTED;
+  if ((d->I > 4 && d->I != 8) || d->J > 6) return FFCA_ERR_UNSUPPORTED;
   return FFCA_OK;
 }
 
@@ -58,14 +60,18 @@ ffca_status fca_plan(const ffca_fca_desc* d, const FcaKernels* k, FcaPlan* p) {
   int dev = 0, nsm = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FFCA_ERR_CUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FFCA_ERR_CUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k->em_update, kBlock, 0) != cudaSuccess)
+  if (k->em_smem > 0)
+    for (const void* fn : {k->em_update, k->em_eval})
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->em_smem) != cudaSuccess)
+        return FFCA_ERR_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k->em_update, kBlock, k->em_smem) != cudaSuccess)
     return FFCA_ERR_CUDA;
   if (occ < 1) return FFCA_ERR_INTERNAL;
   const int FU = d->prec == FFCA_PREC_FP64 ? 1 : 2;
   const int F = d->F > 0 ? d->F : 1;
   p->p = make_partition(F, (d->N + FU - 1) / FU, nsm * occ);
   p->p.F = d->F;
-  const int NV = d->J * d->I * d->I + 1;
+  const int NV = k->nv;
   size_t off = kAlign;  // status words, counter, operation counts
   p->off_llf = off; off = align_up(off + sizeof(double) * F);
   p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
@@ -111,13 +117,17 @@ FcaArgs fca_args(const ffca_fca_ctx* c, int slot) {
   return a;
 }
 
-ffca_status fca_launch(const ffca_fca_ctx* c, const void* fn, int grid, int block, FcaArgs& a) {
+ffca_status fca_launch(const ffca_fca_ctx* c, const void* fn, int grid, int block, FcaArgs& a, size_t smem = 0) {
   void* args[] = {&a};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, c->stream) == cudaSuccess ? FFCA_OK
-                                                                                          : FFCA_ERR_CUDA;
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, c->stream) == cudaSuccess ? FFCA_OK
+                                                                                             : FFCA_ERR_CUDA;
 }
 
-int fca_final_grid(const ffca_fca_ctx* c) { return (c->d.F + kFinalThreads - 1) / kFinalThreads; }
+// one thread per frequency (small arrays) or one warp per frequency (I > 4)
+int fca_final_grid(const ffca_fca_ctx* c) {
+  const int per_block = c->k->final_block == 1 ? kFinalThreads : kFinalThreads / 32;
+  return (c->d.F + per_block - 1) / per_block;
+}
 
 ffca_status fca_status(ffca_fca_ctx* c) {
   unsigned h[2] = {0, 0};
@@ -130,7 +140,7 @@ ffca_status fca_status(ffca_fca_ctx* c) {
 // log-likelihood-only pass of the current state into trace slot `slot`
 ffca_status fca_eval(ffca_fca_ctx* c, int slot) {
   FcaArgs a = fca_args(c, slot);
-  ffca_status st = fca_launch(c, c->k->em_eval, a.part.nblocks, kBlock, a);
+  ffca_status st = fca_launch(c, c->k->em_eval, a.part.nblocks, kBlock, a, c->k->em_smem);
   if (st != FFCA_OK) return st;
   return fca_launch(c, c->k->final_eval, fca_final_grid(c), kFinalThreads, a);
 }
@@ -194,7 +204,7 @@ ffca_status ffca_fca_iterate(ffca_fca_ctx* c, int iters, double* ll_trace) {
     const int slot = t % kTraceCap;
     if (t < iters) {
       FcaArgs a = fca_args(c, slot);
-      if ((st = fca_launch(c, c->k->em_update, a.part.nblocks, kBlock, a)) != FFCA_OK) return st;
+      if ((st = fca_launch(c, c->k->em_update, a.part.nblocks, kBlock, a, c->k->em_smem)) != FFCA_OK) return st;
       if ((st = fca_launch(c, c->k->final_update, fca_final_grid(c), kFinalThreads, a)) != FFCA_OK) return st;
     } else if (ll_trace) {
       if ((st = fca_eval(c, slot)) != FFCA_OK) return st;

@@ -6,6 +6,7 @@
 #include "ffca_big.cuh"
 #include "ffca_dispatch.h"
 #include "ffca_fca.cuh"
+#include "ffca_fca_big.cuh"
 #include "ffca_stream.cuh"
 
 #ifndef FFCA_PREC
@@ -64,15 +65,34 @@ static const FastKernels* table_entry() {
 #if FFCA_PART == 1
 template <int J>
 static const FcaKernels* fca_entry() {
-  static const FcaKernels k = {
-      (const void*)k_fca_prep<Real, FFCA_I, J>,
-      (const void*)k_fca_em<Real, FFCA_I, J, true>,
-      (const void*)k_fca_em<Real, FFCA_I, J, false>,
-      (const void*)k_fca_final<Real, FFCA_I, J, true>,
-      (const void*)k_fca_final<Real, FFCA_I, J, false>,
-      FcaParams<Real, FFCA_I, J>::BYTES,
-  };
-  return &k;
+  if constexpr (FFCA_I > 4) {  // the rearranged form (one warp per source, per-frequency products)
+    using B = FcaBig<Real, FFCA_I, J>;
+    static const FcaKernels k = {
+        (const void*)k_fca_prep_big<Real, FFCA_I, J>,
+        (const void*)k_fca_em_big<Real, FFCA_I, J, true>,
+        (const void*)k_fca_em_big<Real, FFCA_I, J, false>,
+        (const void*)k_fca_final_big<Real, FFCA_I, J, true>,
+        (const void*)k_fca_final_big<Real, FFCA_I, J, false>,
+        FcaParamsBig<Real, FFCA_I, J>::BYTES,
+        B::NV,
+        B::SMEM,
+        128,
+    };
+    return &k;
+  } else {
+    static const FcaKernels k = {
+        (const void*)k_fca_prep<Real, FFCA_I, J>,
+        (const void*)k_fca_em<Real, FFCA_I, J, true>,
+        (const void*)k_fca_em<Real, FFCA_I, J, false>,
+        (const void*)k_fca_final<Real, FFCA_I, J, true>,
+        (const void*)k_fca_final<Real, FFCA_I, J, false>,
+        FcaParams<Real, FFCA_I, J>::BYTES,
+        J * FFCA_I * FFCA_I + 1,
+        0,
+        1,
+    };
+    return &k;
+  }
 }
 
 #endif

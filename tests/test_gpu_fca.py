@@ -104,3 +104,19 @@ def test_fca_and_fastfca_agree_from_joint_state():
     b = run_gpu(p.y, p.v0, p.lam0, p.P0, 1, "fp64")
     assert per_f_relerr(a[0], b[0], 1) <= 1e-10
     assert abs(a[2][0] - b[3][0]) <= 1e-10 * abs(b[3][0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(8, 6, 3, 37), (8, 2, 2, 300), (8, 6, 2, 1030)])
+def test_fca_large_array_matches_oracle(prec, shape):
+    """I = 8: the rearranged E/M steps (per-point Hermitian inverse kept, the
+    J products per frequency) against the oracle's literal Sec. 3.3 form."""
+    I, J, F, N = shape
+    p = make_problem(I, J, F, N, seed=600 + J, alpha=0.2, kappa=50.0)
+    S0 = fca.spatial_from_joint(p.P0, p.lam0)
+    ref = fca.iterate(p.y, p.v0, S0, 2, counter=OpCounter())
+    got = run_fca_gpu(p.y, p.v0, S0, 2, prec)
+    _check(prec, ref, got, N, F)
+    # operations as performed: one inversion of R per point, 2 J products per frequency
+    inv, mul = got[3]
+    assert inv == 2 * N * F and mul == 2 * 2 * J * F
