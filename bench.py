@@ -287,6 +287,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
     if rank != 0:
         return None
     batched = run_batched(args, dev)
+    large = run_large_array(args, dev)
     adjoint = run_adjoint(dev)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean duration
@@ -333,6 +334,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
         "fca_gpu": fca_line,
         "speedup_vs_fca_gpu": (value / ws / fca_line["value"]) if fca_line else None,
         "batched": batched,
+        "large_array": large,
         "adjoint": adjoint,
     }
 
@@ -389,6 +391,105 @@ def run_adjoint(dev):
                          "P": relerr(dP[fs].cpu().numpy(), rP, 0),
                          "measure": f"{len(fs)} sampled frequencies, normwise relative per frequency (max)"}}
     est.close()
+    return out
+
+
+def run_large_array(args, dev):
+    """The large-array workload: I = 8 mics, J = 6 sources, F = 513, N = 4000,
+    complex64, mixed precision, 30 iterations per run; beside it the plain
+    FP64 GPU form and the conventional FCA EM on the GPU (same data, same
+    precision as the main run, its comparison in the paper), and the error
+    against the FP64 oracle on sampled frequencies."""
+    import torch
+    from oracle import fastfca_as as ffa
+    from oracle.fastfca_as import OpCounter
+    from paper_1805_09498_gb300 import ffca
+    cfg = CONFIGS["large_array"]
+    I, J, F, N, iters = cfg["I"], cfg["J"], cfg["F"], cfg["N"], cfg["iters"]
+    p = make_problem(I, J, F, N, seed=1, alpha=cfg["alpha"], kappa=cfg["kappa"])
+    yd, vd, lamd, Pd, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed", device=dev)
+    v_init, lam_init, P_init = vd.clone(), lamd.clone(), Pd.clone()
+    stream = torch.cuda.current_stream(dev)
+    est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # accuracy: one full run from the initial state against the oracle
+    tr = est.iterate(iters)
+    fs = _sample_freqs(F, 3)
+    vg, lg, Pg = vd[:, fs, :N].double().cpu().numpy(), lamd[fs].cpu().numpy(), Pd[fs].cpu().numpy()
+    rv, rl, rP, rt = ffa.iterate(p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs], iters,
+                                 counter=OpCounter())
+
+    def relerr(a_, b_, ax):
+        a_ = np.moveaxis(a_, ax, 0).reshape(len(fs), -1)
+        b_ = np.moveaxis(b_, ax, 0).reshape(len(fs), -1)
+        return float(np.max(np.linalg.norm(a_ - b_, axis=1) / np.linalg.norm(b_, axis=1)))
+    err = {"v": relerr(vg, rv, 1), "lambda": relerr(lg, rl, 0), "P": relerr(Pg, rP, 0),
+           "loglik_per_point": abs(ffa.loglik(p.y[:, fs], vg, lg, Pg) - rt[-1]) / (len(fs) * N),
+           "measure": f"after {iters} iterations from the same initial state, on {len(fs)} sampled "
+                      "frequencies; normwise relative error per frequency (max)"}
+
+    for _ in range(max(args.warmup, 3)):
+        est.iterate(iters, trace=False)
+    reps = 5
+    ffca.ffca_timing_read(est.ctx)
+    ms = timed(lambda: est.iterate(iters), reps)
+    ffca.ffca_timing_read(est.ctx)  # drop the counts of the untimed runs
+    ffca.ffca_timing_enable(est.ctx, True)
+    est.iterate(iters)
+    kt = ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, False)
+    est.close()
+    kernels = {}
+    for k, bpt in (("estep", I * 8 + 2 * J * 4), ("wcov", I * 8 + J * 4), ("psolve", 0),
+                   ("afinal", 0), ("loglik", 0)):
+        kms, kn = kt[k]
+        if kn:
+            kernels[k] = {"launches": kn, "avg_us": kms / kn * 1e3}
+            if bpt:
+                kernels[k]["achieved_gbs"] = bpt * N * F / (kms / kn * 1e-3) / 1e9
+    units = N * F * iters
+    out = {"workload": f"large_array: I={I} J={J} F={F} N={N}, c64 storage, mixed FP32/FP64, "
+                       f"{iters} iterations with the L2 trace",
+           "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms, "runs_timed": reps,
+           "kernels": kernels, "error_vs_oracle": err}
+
+    # the plain FP64 GPU form on the same mixture
+    y64, v64, l64, P64, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64", device=dev)
+    e64 = ffca.FastFCA(y64, v64, l64, P64, N=N)
+    e64.iterate(1, trace=False)
+    it64 = 3
+    ms64 = timed(lambda: e64.iterate(it64, trace=False), 1)
+    e64.close()
+    del y64, v64, l64, P64
+    out["fp64_gpu"] = {"value": N * F * it64 / (ms64 * 1e-3), "unit": UNIT, "iters_timed": it64,
+                       "ms_per_iter": ms64 / it64}
+    out["speedup_mixed_vs_fp64_gpu"] = out["value"] / out["fp64_gpu"]["value"]
+
+    # conventional FCA EM on the GPU, same data and precision, from the same model
+    Pinv = torch.linalg.inv(P_init.cpu()).to(dev)  # setup only (CPU LAPACK)
+    S0 = ((Pinv.conj().transpose(1, 2)[:, None] * lam_init[:, :, None, :].to(torch.complex128))
+          @ Pinv[:, None]).contiguous()
+    vf = v_init.clone()
+    ef = ffca.FCA(yd, vf, S0, N=N)
+    ef.iterate(1, trace=False)
+    itf = 3
+    msf = timed(lambda: ef.iterate(itf, trace=False), 1)
+    ef.close()
+    out["fca_gpu"] = {"value": N * F * itf / (msf * 1e-3), "unit": UNIT, "iters_timed": itf,
+                      "ms_per_iter": msf / itf, "precision": "mixed (same as the FastFCA-AS run)"}
+    out["speedup_vs_fca_gpu"] = out["value"] / out["fca_gpu"]["value"]
+    del est, yd, vd, lamd, Pd, v_init, lam_init, P_init, vf, S0, Pinv
+    torch.cuda.empty_cache()
     return out
 
 

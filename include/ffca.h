@@ -45,8 +45,9 @@
  *    and finished in FP64; Lambda, P, the per-frequency I x I solves and the
  *    log-likelihood totals are FP64.
  *
- * Supported shapes: 1 <= I <= 4, 1 <= J <= 6 (FFCA_ERR_UNSUPPORTED
- * otherwise), N >= 1, F >= 0 (F == 0 is a no-op).
+ * Supported shapes: I in {1, 2, 3, 4, 8}, 1 <= J <= 6 (FFCA_ERR_UNSUPPORTED
+ * otherwise; the gradients take I <= 4 only), N >= 1, F >= 0 (F == 0 is a
+ * no-op).
  */
 #ifndef FFCA_H
 #define FFCA_H
@@ -72,7 +73,7 @@ typedef enum { FFCA_PREC_FP64 = 0, FFCA_PREC_MIXED = 1 } ffca_precision;
 
 /* Problem and state of one FastFCA-AS estimation (device pointers). */
 typedef struct {
-  int I;                  /* microphones, 1..4 */
+  int I;                  /* microphones: 1, 2, 3, 4 or 8 */
   int J;                  /* sources, 1..6 */
   int F;                  /* frequency bins, >= 0 */
   int N;                  /* frames, >= 1 */
@@ -170,7 +171,7 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
  *   loss  host double or NULL: the loss value (the call then synchronises)
  * s: device [J][I][F][ld] complex of the precision's type (the layout of the
  * ffca_wiener output).  Enqueued on the context stream.  FFCA_ERR_UNSUPPORTED
- * for batch contexts. */
+ * for batch contexts and for I = 8. */
 ffca_status ffca_nll_grad(ffca_ctx* ctx, void* dv, double* dlam, double* dP, double* loss);
 ffca_status ffca_wiener_se_grad(ffca_ctx* ctx, const void* s, void* dv, double* dlam, double* dP,
                                 double* loss);
@@ -298,7 +299,7 @@ void ffca_batch_destroy(ffca_batch_ctx* ctx);
  * Same conventions (device pointers, caller's stream, status codes) and the
  * same y / v layouts and precisions as FastFCA-AS. */
 typedef struct {
-  int I, J, F, N, ld;     /* as in ffca_desc (I 1..4, J 1..6) */
+  int I, J, F, N, ld;     /* as in ffca_desc (I 1..4 or 8, J 1..6) */
   int prec;               /* ffca_precision */
   const void* y;          /* [I][F][ld] complex, read only */
   void* v;                /* [J][F][ld] real, in/out */

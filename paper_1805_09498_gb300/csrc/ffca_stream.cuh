@@ -60,7 +60,7 @@ static_assert(kGroupWarps % 4 == 0, "groups interleave in units of four warps");
 // 16 warps then share the register file), else one.
 template <typename T, int I, int J>
 struct StreamGroups {
-  static constexpr int value = (sizeof(T) == 4 && I <= 3 && J <= 3) ? 2 : 1;
+  static constexpr int value = (sizeof(T) == 4 && I <= 4 && J <= 3) ? 2 : 1;
 };
 
 // The role of a thread in its CTA.  Warp w belongs to group (w / 4) % G with
@@ -236,38 +236,62 @@ struct GroupReduce {
   }
 };
 
-// Walks a CTA's unit range [u0, u1) of the flattened unit space as tiles of
-// at most T units that never cross a problem: tile (f = problem, k = first
-// unit within the problem, n units).
-// Tiles of the unit range [u0, u1): at most T units each, never crossing a
-// problem boundary.  The problem index is found once (binary search over the
-// unit starts) and then advanced as the range crosses into the next problem.
+// Tiles of a CTA's unit range [u0, u1) of the flattened unit space: at most
+// T units each, never crossing a problem boundary (tile = problem f, first
+// unit k within the problem, n units).  The problem index is found once
+// (binary search over the unit starts) and then stepped as the walk crosses
+// into the neighbouring problem.  Forward walks go from u0 up, reverse walks
+// from u1 down: pass A walks forward and pass B in reverse, so that each pass
+// starts on the units the previous pass touched last, which are still in
+// the 129 MB L2 (the two passes have the same ranges when their partitions
+// agree).  Tile starts stay even (16-byte aligned v rows): ranges, problem
+// starts and T are even.
 struct TileIter {
   const Partition* pt;
-  long long u, u1;
+  long long u, u0, u1;
   long long s, e;  // unit range of problem f
   int T;
   int f, k, n;
-  bool seg_end;
-  __device__ TileIter(long long u0_, long long u1_, const Partition& pt_, int T_)
-      : pt(&pt_), u(u0_), u1(u1_), T(T_) {
-    f = u < u1 ? pt->problem_of(u) : 0;
+  bool seg_end, rev;
+  __device__ TileIter(long long u0_, long long u1_, const Partition& pt_, int T_, bool rev_ = false)
+      : pt(&pt_), u(rev_ ? u1_ : u0_), u0(u0_), u1(u1_), T(T_), rev(rev_) {
+    f = u0 < u1 ? pt->problem_of(rev ? u1 - 1 : u0) : 0;
     s = pt->start(f);
     e = pt->start(f + 1);
   }
   __device__ bool next() {
-    if (u >= u1) return false;
-    if (u >= e) {  // ranges are contiguous: the next problem starts at e
-      ++f;
-      s = e;
-      e = pt->start(f + 1);
+    if (!rev) {
+      if (u >= u1) return false;
+      if (u >= e) {  // ranges are contiguous: the next problem starts at e
+        ++f;
+        s = e;
+        e = pt->start(f + 1);
+      }
+      k = (int)(u - s);
+      const int kend = (int)(min(e, u1) - s);
+      n = min(T, kend - k);
+      seg_end = (k + n == kend);
+      u += n;
+    } else {
+      if (u <= u0) return false;
+      if (u <= s) {  // the previous problem ends at s
+        --f;
+        e = s;
+        s = pt->start(f);
+      }
+      const int kbeg = (int)(max(s, u0) - s);
+      const int kend = (int)(u - s);
+      n = min(T, kend - kbeg);
+      k = kend - n;
+      seg_end = (k == kbeg);
+      u -= n;
     }
-    k = (int)(u - s);
-    const int kend = (int)(min(e, u1) - s);
-    n = min(T, kend - k);
-    seg_end = (k + n == kend);
-    u += n;
     return true;
+  }
+  // the problem the walk reaches after f, or -1 if f is its last
+  __device__ int after(int p) const {
+    if (!rev) return (p + 1 < pt->F && pt->start(p + 1) < u1) ? p + 1 : -1;
+    return (p > 0 && pt->start(p) > u0) ? p - 1 : -1;
   }
 };
 
@@ -370,7 +394,7 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
   constexpr int FU = Vec<T>::FU;
   const bool leader = (threadIdx.x & 31) == 0;
   const Partition& pt = a.part;
-  TileIter it(u0, u1, pt, TC::T);
+  TileIter it(u0, u1, pt, TC::T, PASS_B);
   using FI = FinIn<I, J>;
   T lam_q[FI::NC];  // pass B: this lane's entries of the current problem's new Lambda
   FI next_in;
@@ -381,7 +405,8 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
     const int s = t % kStages;
     if (PASS_B && it.f != pf) {
       const FI cur = next_in;
-      if (it.f + 1 < pt.F && pt.start(it.f + 1) < u1) next_in = finalize_load<I, J>(a, it.f + 1);
+      const int nf = it.after(it.f);
+      if (nf >= 0) next_in = finalize_load<I, J>(a, nf);
       finalize_pass_a<T, I, J>(a, it.f, cur, pt.first_block(it.f) == vb, lam_q);
       pf = it.f;
     }
@@ -787,7 +812,7 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
     if constexpr (kNarrow) acc[q] = fmaf(wv.v.y, x.v.y, fmaf(wv.v.x, x.v.x, acc[q]));
     else acc[q] = vfma(wv, x, acc[q]);
   };
-  TileIter it(u0, u1, pt, TC::T);
+  TileIter it(u0, u1, pt, TC::T, true);
   bool seg_new = true;
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
@@ -942,7 +967,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
     using A = std::conditional_t<kNarrow, float, L>;
     A acc[NV];
 
-    TileIter it(u0, u1, pt, TC::T);
+    TileIter it(u0, u1, pt, TC::T, true);
     bool seg_new = true;
     for (int t = 0; it.next(); ++t) {
       const int f = it.f;
