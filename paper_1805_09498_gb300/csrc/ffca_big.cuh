@@ -1,16 +1,24 @@
 // Per-problem FP64 kernels for arrays of more than four microphones
 // (I > 4), where the cofactor forms of the small kernels would take too many
-// operations: the same lane layout (lane (g, i) owns column i of problem g,
-// 32 / I problems per warp), with each lane's I x I matrices in its own slice
-// of shared memory (padded by one element so that the lanes' 16-byte
-// accesses fall in distinct banks).
+// operations.  Lane (g, c) of a warp owns column c of problem g (32 / I
+// problems per warp) and every matrix lives in registers, distributed by
+// columns over the problem's I lanes:
 //
-//   k_psolve_big  Eq. FPI: [P^{-H}]_i by Gaussian elimination with partial
-//                 pivoting of P^H x = e_i, then p_i = V_i^{-1} [P^{-H}]_i by
-//                 Cholesky (V_i Hermitian positive definite), K sweeps, all
-//                 columns from one P^{-H} per sweep; ln|det P|^2 of the new P
-//                 from the pivots of its elimination.
-//   k_prep_big    ln|det P|^2, the pass-A table and, if asked, P^{-H}.
+//   k_psolve_big  Eq. FPI: each lane factors its V_i = L D L^H (right-looking,
+//                 no square roots) and solves V_i p_i = [P^{-H}]_i with the
+//                 P^{-H} of the current P (kept in the workspace from the
+//                 step that made P); K sweeps, all columns from one P^{-H}
+//                 per sweep; then the in-place Gauss-Jordan inverse of the
+//                 new P^H gives ln|det P|^2 for the next log-likelihood and
+//                 the next P^{-H}.
+//   k_prep_big    ln|det P|^2, P^{-H} and the pass-A table of the current P.
+//
+// On this part an FP64 warp instruction occupies the SM's FP64 pipe for 16
+// cycles (2 FP64 FMAs per clock per SM), so the kernels count FP64
+// instructions: pivot choices use integer compares of the magnitudes' bit
+// patterns, the in-place inverse updates one I x I matrix per step (not an
+// augmented I x 2I one), and the inverse of P is carried from one step to
+// the next instead of being recomputed.
 #pragma once
 
 #include "ffca_fastfca.cuh"
@@ -19,99 +27,157 @@ namespace ffca {
 
 template <int I>
 struct BigLane {
-  static constexpr int LD = I * I + 1;  // complex elements per lane slice (padded)
-  static constexpr int SLICES = 2;      // elimination matrix, Cholesky factor
-  static constexpr int G = 32 / I;      // problems per warp
-  // per block (one warp): the lanes' slices and each problem's new P
-  static constexpr int SMEM = (32 * SLICES * LD + G * I * I) * (int)sizeof(cpx<double>);
+  static constexpr int G = 32 / I;  // problems per warp
+  static constexpr int LDM = I + 1; // padded row of the transpose buffer (conflict-free column reads)
+  // per block (one warp): each problem's I x I matrix, for transposes
+  static constexpr int SMEM = G * I * LDM * (int)sizeof(cpx<double>);
 };
 
-__device__ inline cpx<double> crecip(cpx<double> a) {
-  const double r = 1.0 / cabs2(a);
-  return mk(a.re * r, -a.im * r);
+// Pivot key: max(|re|, |im|) compared through the bit patterns of the
+// absolute values (monotonic for non-negative doubles), within a factor
+// sqrt(2) of |z|: enough to choose a partial pivot, with integer compares
+// instead of FP64 instructions.
+__device__ inline unsigned long long pivot_key(cpx<double> z) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(z.re) & 0x7fffffffffffffffull;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(z.im) & 0x7fffffffffffffffull;
+  return a > b ? a : b;
 }
 
-// LU with partial pivoting of the I x I matrix A (row-major, in place) and,
-// if b != nullptr, the solution of A x = b in place of b.  Returns
-// sum_k ln|u_kk|^2 = ln|det A|^2 (-inf for a zero pivot).
+// In-place Gauss-Jordan inverse with partial pivoting of the I x I complex
+// matrix whose column c lane (g, c) holds in a[] (rows 0..I-1); on return
+// a[] holds column c of the inverse.  Step k: the owner of column k picks
+// the pivot row p >= k, every lane swaps rows k and p of its column, the
+// pivot column is broadcast, and with t = a_k / pivot (t = 1 / pivot for the
+// owner) each lane sets a_k = t and a_r -= col_r t (r != k; the owner starts
+// from 0).  The row interchanges of steps k become column interchanges of
+// the result, undone in reverse order by one gather at the end.  Returns
+// |det|^2 as the product of the pivots' |.|^2 (0 if a pivot vanished).
 template <int I>
-__device__ double gauss_solve(cpx<double>* A, cpx<double>* b) {
-  double lg = 0.0;
+__device__ double gj_inverse_cols(cpx<double> (&a)[I], int g, int c) {
+  const unsigned full = 0xffffffffu;
+  int perm[I];
+  double det2 = 1.0;
+#pragma unroll
   for (int k = 0; k < I; ++k) {
+    const int owner = g * I + k;
     int p = k;
-    double best = cabs2(A[k * I + k]);
+    unsigned long long best = pivot_key(a[k]);
+#pragma unroll
     for (int r = k + 1; r < I; ++r) {
-      const double m = cabs2(A[r * I + k]);
+      const unsigned long long m = pivot_key(a[r]);
       if (m > best) {
         best = m;
         p = r;
       }
     }
-    if (!(best > 0.0)) return -INFINITY;
-    if (p != k) {
-      for (int c = k; c < I; ++c) {
-        const cpx<double> t = A[k * I + c];
-        A[k * I + c] = A[p * I + c];
-        A[p * I + c] = t;
-      }
-      if (b) {
-        const cpx<double> t = b[k];
-        b[k] = b[p];
-        b[p] = t;
-      }
-    }
-    lg += log(best);
-    const cpx<double> inv = crecip(A[k * I + k]);
+    p = __shfl_sync(full, p, owner);
+    perm[k] = p;
+#pragma unroll
     for (int r = k + 1; r < I; ++r) {
-      const cpx<double> m = cmul(A[r * I + k], inv);
-      for (int c = k + 1; c < I; ++c) A[r * I + c] = csub(A[r * I + c], cmul(m, A[k * I + c]));
-      if (b) b[r] = csub(b[r], cmul(m, b[k]));
+      if (r == p) {
+        const cpx<double> t = a[k];
+        a[k] = a[r];
+        a[r] = t;
+      }
     }
-  }
-  if (b) {
-    for (int k = I - 1; k >= 0; --k) {
-      cpx<double> s = b[k];
-      for (int c = k + 1; c < I; ++c) s = csub(s, cmul(A[k * I + c], b[c]));
-      b[k] = cmul(s, crecip(A[k * I + k]));
+    cpx<double> col[I];
+#pragma unroll
+    for (int r = 0; r < I; ++r) col[r] = shfl_c(a[r], owner);
+    const double d2 = cabs2(col[k]);
+    det2 *= d2;
+    const double rd = 1.0 / d2;
+    const cpx<double> inv = mk(col[k].re * rd, -col[k].im * rd);
+    const bool piv = (c == k);
+    const cpx<double> t = piv ? inv : cmul(a[k], inv);
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      if (r == k) continue;
+      cpx<double> v = piv ? mk(0.0, 0.0) : a[r];
+      cfma(v, mk(-col[r].re, -col[r].im), t);
+      a[r] = v;
     }
+    a[k] = t;
   }
-  return lg;
+  // column c of the result is column sigma(c) of the matrix before the
+  // interchanges: trace the swaps (k, perm[k]), applied for k = I-1 .. 0
+  int j = c;
+#pragma unroll
+  for (int k = 0; k < I; ++k) j = (j == k) ? perm[k] : (j == perm[k] ? k : j);
+#pragma unroll
+  for (int r = 0; r < I; ++r) a[r] = shfl_c(a[r], g * I + j);
+  return (det2 > 0.0 && isfinite(det2)) ? det2 : 0.0;
 }
 
-// Cholesky V = L L^H in place (lower triangle, row-major); false if a pivot
-// is at or below kCholRtol times its diagonal entry (rank deficient).
+// Index of the strictly lower entry (r, c), r > c, in packed row order.
+__host__ __device__ constexpr int lo_index(int r, int c) { return r * (r - 1) / 2 + c; }
+
+// V = L D L^H in place (right-looking, no square roots): on entry dv holds
+// the real diagonal and lo the strictly lower entries of the Hermitian V; on
+// return lo holds the unit lower factor L and rd the reciprocals of D.
+// Returns false if a pivot is at or below kCholRtol times its original
+// diagonal entry, or not finite (rank deficient or non-finite V).
 template <int I>
-__device__ bool cholesky(cpx<double>* V) {
+__device__ bool ldl_factor(double (&dv)[I], cpx<double> (&lo)[I * (I - 1) / 2], double (&rd)[I]) {
+  bool ok = true;
+#pragma unroll
   for (int k = 0; k < I; ++k) {
-    double d = V[k * I + k].re;
-    const double d0 = d;
-    for (int c = 0; c < k; ++c) d -= cabs2(V[k * I + c]);
-    if (!(d > kCholRtol * d0) || !isfinite(d)) return false;
-    const double lkk = sqrt(d);
-    V[k * I + k] = mk(lkk, 0.0);
-    const double rl = 1.0 / lkk;
-    for (int r = k + 1; r < I; ++r) {
-      cpx<double> s = V[r * I + k];
-      for (int c = 0; c < k; ++c) s = csub(s, cmul(V[r * I + c], cconj(V[k * I + c])));
-      V[r * I + k] = cscale(s, rl);
+    const double d = dv[k];
+    ok &= isfinite(d) && d > 0.0;
+    const double inv = 1.0 / d;
+    rd[k] = inv;
+    cpx<double> l[I];
+#pragma unroll
+    for (int r = k + 1; r < I; ++r) l[r] = cscale(lo[lo_index(r, k)], inv);
+#pragma unroll
+    for (int c = k + 1; c < I; ++c) {
+      const cpx<double> vck = lo[lo_index(c, k)];
+      dv[c] -= vck.re * l[c].re + vck.im * l[c].im;  // |V_ck|^2 / d
+#pragma unroll
+      for (int r = c + 1; r < I; ++r) {  // V_rc -= V_rk conj(l_c)
+        cpx<double>& v = lo[lo_index(r, c)];
+        const cpx<double> vrk = lo[lo_index(r, k)];
+        v = csub(v, cmul(vrk, cconj(l[c])));
+      }
     }
+#pragma unroll
+    for (int r = k + 1; r < I; ++r) lo[lo_index(r, k)] = l[r];
   }
-  return true;
+  return ok;
 }
 
-// x <- (L L^H)^{-1} x with the factor from cholesky().
+// x <- (L D L^H)^{-1} x with the factors of ldl_factor.
 template <int I>
-__device__ void chol_solve(const cpx<double>* L, cpx<double>* x) {
-  for (int k = 0; k < I; ++k) {  // L z = x
-    cpx<double> s = x[k];
-    for (int c = 0; c < k; ++c) s = csub(s, cmul(L[k * I + c], x[c]));
-    x[k] = cscale(s, 1.0 / L[k * I + k].re);
-  }
-  for (int k = I - 1; k >= 0; --k) {  // L^H p = z
-    cpx<double> s = x[k];
-    for (int r = k + 1; r < I; ++r) s = csub(s, cmul(cconj(L[r * I + k]), x[r]));
-    x[k] = cscale(s, 1.0 / L[k * I + k].re);
-  }
+__device__ void ldl_solve(const cpx<double> (&lo)[I * (I - 1) / 2], const double (&rd)[I], cpx<double> (&x)[I]) {
+#pragma unroll
+  for (int k = 0; k < I; ++k)  // L z = x
+#pragma unroll
+    for (int r = k + 1; r < I; ++r) cfma(x[r], mk(-lo[lo_index(r, k)].re, -lo[lo_index(r, k)].im), x[k]);
+#pragma unroll
+  for (int k = 0; k < I; ++k) x[k] = cscale(x[k], rd[k]);
+#pragma unroll
+  for (int k = I - 1; k >= 0; --k)  // L^H p = z
+#pragma unroll
+    for (int r = 0; r < k; ++r) {
+      const cpx<double> l = lo[lo_index(k, r)];  // (L^H)_rk = conj(L_kr)
+      cfma(x[r], mk(-l.re, l.im), x[k]);
+    }
+}
+
+// Column c of P^{-H} and ln|det P|^2 from the columns of P (lane (g, c)
+// holds column c of P in x[]): transpose through the problem's shared
+// buffer M (rows padded to LDM), conjugate into column c of P^H, invert.
+template <int I>
+__device__ double pinvh_from_columns(cpx<double> (&x)[I], cpx<double>* M, int g, int c, bool& singular) {
+  constexpr int LDM = BigLane<I>::LDM;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < I; ++r) M[r * LDM + c] = x[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < I; ++r) x[r] = cconj(M[c * LDM + r]);  // (P^H)_{rc} = conj(P_cr)
+  const double det2 = gj_inverse_cols<I>(x, g, c);
+  singular |= !(det2 > 0.0);
+  return det2;
 }
 
 template <typename T, int I, int J>
@@ -119,91 +185,99 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
   using BL = BigLane<I>;
   constexpr int G = BL::G;
   constexpr int NV = I * I * I;
+  constexpr int NL = I * (I - 1) / 2;
   extern __shared__ __align__(16) unsigned char big_smem[];
-  cpx<double>* lanes = reinterpret_cast<cpx<double>*>(big_smem);
   const int lane = threadIdx.x;
   const int g = lane / I, i = lane % I;
   const int f0 = blockIdx.x * G + g;
   const bool active = g < G && f0 < a.F;
   const int f = active ? f0 : 0;  // idle lanes shadow problem 0 and write nothing
-  cpx<double>* E = lanes + (size_t)lane * BL::SLICES * BL::LD;  // elimination matrix
-  cpx<double>* Lc = E + BL::LD;                                  // Cholesky factor of V_i
-  cpx<double>* Pn = lanes + (size_t)32 * BL::SLICES * BL::LD + (size_t)(g < G ? g : 0) * I * I;  // new P
+  cpx<double>* M = reinterpret_cast<cpx<double>*>(big_smem) + (size_t)(g < G ? g : 0) * I * BL::LDM;
   const Partition pt = a.part;
 
   if (active && a.lam_next) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
     for (int j = 0; j < J; ++j) {
       const double l = a.lam_next[(size_t)f * J * I + j * I + i];
       a.lam[(size_t)f * J * I + j * I + i] = l;
       ta->lam[j][i] = (T)l;
     }
   }
-  // V_i from the slots (packed Hermitian: diagonal, then (re, im) above it)
+  // column i of P^{-H} of the current P
+  cpx<double> x[I];
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const double2 q = __ldcg(reinterpret_cast<const double2*>(a.pinvH) + (size_t)f * I * I + r * I + i);
+    x[r] = mk(q.x, q.y);
+  }
+  // V_i from the slots (packed Hermitian: diagonal, then (re, im) above it in
+  // row order), slot by slot with 16-byte loads
+  double dv[I], rd[I];
+  cpx<double> lo[NL];
   {
+    double pk[I * I];
+#pragma unroll
+    for (int m = 0; m < I * I; ++m) pk[m] = 0.0;
     const int ns = pt.nslots(f);
-    const double* base = a.part_buf + ((size_t)f * pt.max_slots) * NV + i * I * I;
+    const double2* base = reinterpret_cast<const double2*>(a.part_buf + ((size_t)f * pt.max_slots) * NV + i * I * I);
+    for (int k = 0; k < ns; ++k)
+#pragma unroll
+      for (int m = 0; m < I * I / 2; ++m) {
+        const double2 q = __ldcg(base + (size_t)k * (NV / 2) + m);
+        pk[2 * m] += q.x;
+        pk[2 * m + 1] += q.y;
+      }
     const double sc = pt.inv_n(f);
-    auto slot_sum = [&](int m) {
-      double s = 0.0;
-      for (int k = 0; k < ns; ++k) s += __ldcg(base + (size_t)k * NV + m);
-      return s * sc;
-    };
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < I * I; ++m) {
+      pk[m] *= sc;
+      bad |= !isfinite(pk[m]);
+    }
+    if (active && bad) raise_status(a.status, kDevNonfinite, f);
+#pragma unroll
+    for (int r = 0; r < I; ++r) dv[r] = pk[r];
     int m = I;
-    for (int r = 0; r < I; ++r) {
-      Lc[r * I + r] = mk(slot_sum(r), 0.0);
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
       for (int c = r + 1; c < I; ++c) {
-        const cpx<double> z = mk(slot_sum(m), slot_sum(m + 1));
-        Lc[r * I + c] = z;
-        Lc[c * I + r] = cconj(z);
+        lo[lo_index(c, r)] = mk(pk[m], -pk[m + 1]);  // V_cr = conj(V_rc)
         m += 2;
       }
-    }
   }
-  bool bad = false;
-  for (int r = 0; r < I * I; ++r) bad |= !isfinite(Lc[r].re) || !isfinite(Lc[r].im);
-  if (active && bad) raise_status(a.status, kDevNonfinite, f);
-  bool singular = !cholesky<I>(Lc);
+  double d0[I];
+#pragma unroll
+  for (int r = 0; r < I; ++r) d0[r] = dv[r];
+  bool singular = !ldl_factor<I>(dv, lo, rd);
+#pragma unroll
+  for (int r = 0; r < I; ++r) singular |= !(dv[r] > kCholRtol * d0[r]);  // dv holds the pivots D
 
-  // current P of the problem, gathered in shared memory (lane (g, c) loads column c)
-  for (int r = 0; r < I; ++r)
-    Pn[r * I + i] = mk(a.P[((size_t)f * I * I + r * I + i) * 2], a.P[((size_t)f * I * I + r * I + i) * 2 + 1]);
-  __syncwarp();
-  cpx<double> x[I];
+  double det2 = 0.0;
   for (int sweep = 0; sweep < a.K; ++sweep) {
-    // [P^{-H}]_i: solve P^H x = e_i
-    for (int r = 0; r < I; ++r)
-      for (int c = 0; c < I; ++c) E[r * I + c] = cconj(Pn[c * I + r]);
-    for (int r = 0; r < I; ++r) x[r] = mk(r == i ? 1.0 : 0.0, 0.0);
-    double lg;
-    {
-      cpx<double> b[I];
-      for (int r = 0; r < I; ++r) b[r] = x[r];
-      lg = gauss_solve<I>(E, b);
-      for (int r = 0; r < I; ++r) x[r] = b[r];
-    }
-    singular |= !isfinite(lg);
-    if (!singular) chol_solve<I>(Lc, x);  // p_i = V_i^{-1} [P^{-H}]_i
-    __syncwarp();                         // every lane of the problem has read the old P
-    for (int r = 0; r < I; ++r) Pn[r * I + i] = x[r];
-    __syncwarp();
+    ldl_solve<I>(lo, rd, x);  // p_i = V_i^{-1} [P^{-H}]_i
+    if (sweep + 1 < a.K) pinvh_from_columns<I>(x, M, g, i, singular);  // P^{-H} of the intermediate P
   }
   if (active) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
     for (int r = 0; r < I; ++r) {
-      const cpx<double> pr = Pn[r * I + i];
-      a.P[((size_t)f * I * I + r * I + i) * 2] = pr.re;
-      a.P[((size_t)f * I * I + r * I + i) * 2 + 1] = pr.im;
-      ta->pre[r][i] = (T)pr.re;
-      ta->pim[r][i] = (T)pr.im;
+      reinterpret_cast<double2*>(a.P)[(size_t)f * I * I + r * I + i] = make_double2(x[r].re, x[r].im);
+      ta->pre[r][i] = (T)x[r].re;
+      ta->pim[r][i] = (T)x[r].im;
     }
+  }
+  // the next step's P^{-H} and ln|det P|^2 of the new P (Eq. L2)
+  det2 = pinvh_from_columns<I>(x, M, g, i, singular);
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+      reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(x[r].re, x[r].im);
     if (singular) raise_status(a.status, kDevSingular, f);
     if (i == 0) {
       atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
-      for (int r = 0; r < I * I; ++r) E[r] = Pn[r];
-      const double lg = gauss_solve<I>(E, nullptr);
-      if (!isfinite(lg)) raise_status(a.status, kDevSingular, f);
-      a.logdet[f] = lg;
+      a.logdet[f] = log(det2);
     }
   }
   if (a.trace) {
@@ -220,37 +294,42 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
   }
 }
 
+// ln|det P|^2, P^{-H} (always: the P step starts from it) and the pass-A
+// table of the current P and Lambda.
 template <typename T, int I, int J>
 __global__ void __launch_bounds__(32) k_prep_big(FastArgs a) {
   using BL = BigLane<I>;
   constexpr int G = BL::G;
-  extern __shared__ __align__(16) unsigned char big_smem[];
-  cpx<double>* lanes = reinterpret_cast<cpx<double>*>(big_smem);
   const int lane = threadIdx.x;
   const int g = lane / I, i = lane % I;
-  const int f = blockIdx.x * G + g;
-  if (g >= G || f >= a.F) return;
-  cpx<double>* E = lanes + (size_t)lane * BL::SLICES * BL::LD;
-  ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
-  for (int r = 0; r < I; ++r) {
-    ta->pre[r][i] = (T)a.P[((size_t)f * I * I + r * I + i) * 2];
-    ta->pim[r][i] = (T)a.P[((size_t)f * I * I + r * I + i) * 2 + 1];
-  }
-  for (int j = 0; j < J; ++j) ta->lam[j][i] = (T)a.lam[(size_t)f * J * I + j * I + i];
-  // P^H in the lane's slice; column i of P^{-H} solves P^H x = e_i
-  for (int r = 0; r < I; ++r)
-    for (int c = 0; c < I; ++c)
-      E[r * I + c] = mk(a.P[((size_t)f * I * I + c * I + r) * 2], -a.P[((size_t)f * I * I + c * I + r) * 2 + 1]);
-  cpx<double> b[I];
-  for (int r = 0; r < I; ++r) b[r] = mk(r == i ? 1.0 : 0.0, 0.0);
-  const double lg = gauss_solve<I>(E, b);  // ln|det P^H|^2 = ln|det P|^2
-  if (!isfinite(lg)) raise_status(a.status, kDevSingular, f);
-  if (i == 0) a.logdet[f] = lg;
-  if (a.pinvH) {
+  const int f0 = blockIdx.x * G + g;
+  const bool active = g < G && f0 < a.F;
+  const int f = active ? f0 : 0;
+  if (active) {
+    ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
     for (int r = 0; r < I; ++r) {
-      a.pinvH[((size_t)f * I * I + r * I + i) * 2] = b[r].re;
-      a.pinvH[((size_t)f * I * I + r * I + i) * 2 + 1] = b[r].im;
+      ta->pre[r][i] = (T)a.P[((size_t)f * I * I + r * I + i) * 2];
+      ta->pim[r][i] = (T)a.P[((size_t)f * I * I + r * I + i) * 2 + 1];
     }
+#pragma unroll
+    for (int j = 0; j < J; ++j) ta->lam[j][i] = (T)a.lam[(size_t)f * J * I + j * I + i];
+  }
+  // column i of P^H is the conjugate of row i of P
+  cpx<double> x[I];
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const double2 q = reinterpret_cast<const double2*>(a.P)[(size_t)f * I * I + i * I + r];
+    x[r] = mk(q.x, -q.y);
+  }
+  const double det2 = gj_inverse_cols<I>(x, g, i);
+  if (!active) return;
+  if (!(det2 > 0.0)) raise_status(a.status, kDevSingular, f);
+  if (i == 0) a.logdet[f] = log(det2);
+  if (a.pinvH) {
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+      reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(x[r].re, x[r].im);
   }
 }
 
