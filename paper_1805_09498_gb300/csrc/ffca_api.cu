@@ -284,7 +284,7 @@ FastArgs pass_b_args(const ffca_ctx* c, int slot) {
   a.prev_part = c->plan.pA;
   a.prev_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partA);
   a.lam_next = reinterpret_cast<double*>(c->ws + c->plan.off_lamnext);
-  // I > 4: the P step reads P^{-H} of the current P and leaves that of the new one
+  // the Gauss-Jordan / LDL^H P step reads P^{-H} of the current P and leaves that of the new one
   a.pinvH = reinterpret_cast<double*>(c->ws + c->plan.off_pinvH);
   return a;
 }
@@ -320,8 +320,8 @@ ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, A
 
 ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   FastArgs a = base_args(c);
-  // I > 4 always: the P step of the large arrays starts from P^{-H}
-  a.pinvH = (want_pinv || c->d.I > 4) ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
+  // always where the P step starts from P^{-H}
+  a.pinvH = (want_pinv || c->kern->pinv_step) ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
   const int G = 32 / c->d.I;  // frequencies per warp
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }

@@ -1,17 +1,19 @@
-// Per-problem FP64 kernels for arrays of more than four microphones
-// (I > 4), where the cofactor forms of the small kernels would take too many
-// operations.  Lane (g, c) of a warp owns column c of problem g (32 / I
-// problems per warp) and every matrix lives in registers, distributed by
-// columns over the problem's I lanes:
+// Per-problem FP64 kernels of the P step by elimination (used from four
+// microphones up, where the cofactor forms of k_psolve take more FP64
+// instructions), and the Wiener filter for more than four microphones.
+// Lane (g, c) of a warp owns column c of problem g (32 / I problems per
+// warp) and every matrix lives in registers, distributed by columns over
+// the problem's I lanes:
 //
-//   k_psolve_big  Eq. FPI: each lane factors its V_i = L D L^H (right-looking,
+//   k_psolve_ldl  Eq. FPI: each lane factors its V_i = L D L^H (right-looking,
 //                 no square roots) and solves V_i p_i = [P^{-H}]_i with the
 //                 P^{-H} of the current P (kept in the workspace from the
 //                 step that made P); K sweeps, all columns from one P^{-H}
 //                 per sweep; then the in-place Gauss-Jordan inverse of the
 //                 new P^H gives ln|det P|^2 for the next log-likelihood and
 //                 the next P^{-H}.
-//   k_prep_big    ln|det P|^2, P^{-H} and the pass-A table of the current P.
+//   k_prep_gj     ln|det P|^2, P^{-H} and the pass-A table of the current P.
+//   k_wiener_big  Eq. MMSE0 for I > 4.
 //
 // On this part an FP64 warp instruction occupies the SM's FP64 pipe for 16
 // cycles (2 FP64 FMAs per clock per SM), so the kernels count FP64
@@ -29,8 +31,9 @@ template <int I>
 struct BigLane {
   static constexpr int G = 32 / I;  // problems per warp
   static constexpr int LDM = I + 1; // padded row of the transpose buffer (conflict-free column reads)
-  // per block (one warp): each problem's I x I matrix, for transposes
-  static constexpr int SMEM = G * I * LDM * (int)sizeof(cpx<double>);
+  // per block (one warp): each problem's I x I matrix for transposes, plus
+  // one for the idle lanes (32 % I of them)
+  static constexpr int SMEM = (G + 1) * I * LDM * (int)sizeof(cpx<double>);
 };
 
 // Pivot key: max(|re|, |im|) compared through the bit patterns of the
@@ -181,7 +184,7 @@ __device__ double pinvh_from_columns(cpx<double> (&x)[I], cpx<double>* M, int g,
 }
 
 template <typename T, int I, int J>
-__global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
+__global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
   using BL = BigLane<I>;
   constexpr int G = BL::G;
   constexpr int NV = I * I * I;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
   const int f0 = blockIdx.x * G + g;
   const bool active = g < G && f0 < a.F;
   const int f = active ? f0 : 0;  // idle lanes shadow problem 0 and write nothing
-  cpx<double>* M = reinterpret_cast<cpx<double>*>(big_smem) + (size_t)(g < G ? g : 0) * I * BL::LDM;
+  cpx<double>* M = reinterpret_cast<cpx<double>*>(big_smem) + (size_t)(g < G ? g : G) * I * BL::LDM;
   const Partition pt = a.part;
 
   if (active && a.lam_next) {
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
     for (int j = 0; j < J; ++j) {
       const double l = a.lam_next[(size_t)f * J * I + j * I + i];
       a.lam[(size_t)f * J * I + j * I + i] = l;
-      ta->lam[j][i] = (T)l;
+      ta->set_lam(j, i, (T)l);
     }
   }
   // column i of P^{-H} of the current P
@@ -212,7 +215,8 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
     x[r] = mk(q.x, q.y);
   }
   // V_i from the slots (packed Hermitian: diagonal, then (re, im) above it in
-  // row order), slot by slot with 16-byte loads
+  // row order), slot by slot; 16-byte loads where the I^2 values of each i
+  // start on a 16-byte boundary (I^2 even), 8-byte loads otherwise
   double dv[I], rd[I];
   cpx<double> lo[NL];
   {
@@ -220,14 +224,21 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
 #pragma unroll
     for (int m = 0; m < I * I; ++m) pk[m] = 0.0;
     const int ns = pt.nslots(f);
-    const double2* base = reinterpret_cast<const double2*>(a.part_buf + ((size_t)f * pt.max_slots) * NV + i * I * I);
-    for (int k = 0; k < ns; ++k)
+    const double* base = a.part_buf + ((size_t)f * pt.max_slots) * NV + i * I * I;
+    for (int k = 0; k < ns; ++k) {
+      if constexpr ((I * I) % 2 == 0) {
+        const double2* b2 = reinterpret_cast<const double2*>(base + (size_t)k * NV);
 #pragma unroll
-      for (int m = 0; m < I * I / 2; ++m) {
-        const double2 q = __ldcg(base + (size_t)k * (NV / 2) + m);
-        pk[2 * m] += q.x;
-        pk[2 * m + 1] += q.y;
+        for (int m = 0; m < I * I / 2; ++m) {
+          const double2 q = __ldcg(b2 + m);
+          pk[2 * m] += q.x;
+          pk[2 * m + 1] += q.y;
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < I * I; ++m) pk[m] += __ldcg(base + (size_t)k * NV + m);
       }
+    }
     const double sc = pt.inv_n(f);
     bool bad = false;
 #pragma unroll
@@ -264,8 +275,7 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
 #pragma unroll
     for (int r = 0; r < I; ++r) {
       reinterpret_cast<double2*>(a.P)[(size_t)f * I * I + r * I + i] = make_double2(x[r].re, x[r].im);
-      ta->pre[r][i] = (T)x[r].re;
-      ta->pim[r][i] = (T)x[r].im;
+      ta->set_p(r, i, (T)x[r].re, (T)x[r].im);
     }
   }
   // the next step's P^{-H} and ln|det P|^2 of the new P (Eq. L2)
@@ -297,7 +307,7 @@ __global__ void __launch_bounds__(32) k_psolve_big(FastArgs a) {
 // ln|det P|^2, P^{-H} (always: the P step starts from it) and the pass-A
 // table of the current P and Lambda.
 template <typename T, int I, int J>
-__global__ void __launch_bounds__(32) k_prep_big(FastArgs a) {
+__global__ void __launch_bounds__(32) k_prep_gj(FastArgs a) {
   using BL = BigLane<I>;
   constexpr int G = BL::G;
   const int lane = threadIdx.x;
@@ -309,11 +319,10 @@ __global__ void __launch_bounds__(32) k_prep_big(FastArgs a) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
     for (int r = 0; r < I; ++r) {
-      ta->pre[r][i] = (T)a.P[((size_t)f * I * I + r * I + i) * 2];
-      ta->pim[r][i] = (T)a.P[((size_t)f * I * I + r * I + i) * 2 + 1];
+      ta->set_p(r, i, (T)a.P[((size_t)f * I * I + r * I + i) * 2], (T)a.P[((size_t)f * I * I + r * I + i) * 2 + 1]);
     }
 #pragma unroll
-    for (int j = 0; j < J; ++j) ta->lam[j][i] = (T)a.lam[(size_t)f * J * I + j * I + i];
+    for (int j = 0; j < J; ++j) ta->set_lam(j, i, (T)a.lam[(size_t)f * J * I + j * I + i]);
   }
   // column i of P^H is the conjugate of row i of P
   cpx<double> x[I];

@@ -16,7 +16,8 @@ struct FastKernels {
   const void* afinal_eval;   // log-likelihood-only pass A finalise: per-frequency L2, trace
   int params_a_bytes;        // bytes per frequency of the pass-A parameter table
   int params_b_bytes;        // bytes per frequency of the pass-B parameter table
-  int solve_smem;            // dynamic shared memory of psolve and prep (I > 4), else 0
+  int solve_smem;            // dynamic shared memory of psolve and prep
+  int pinv_step;             // 1: the P step starts from P^{-H} (prep computes it) and leaves the next one
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

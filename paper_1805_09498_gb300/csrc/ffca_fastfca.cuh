@@ -47,11 +47,40 @@ struct FastArgs {
 
 // Per-frequency parameters in the per-point precision T, laid out as they
 // travel to the streaming kernels (one bulk copy per tile, 16-byte padded).
+// Pass A's record holds P(f) and Lambda(f).  With DUP every value would be
+// stored twice, P as (re, re, im, im) per entry and Lambda as (l, l), for
+// loading packed f32x2 operands directly; measured slower for pass A at
+// I = 8 (109 us against 99 us with single values), so it is off.
 template <typename T, int I, int J>
-struct ParamsA {  // pass A: P(f) and Lambda(f)
-  T pre[I][I], pim[I][I];
-  T lam[J][I];
-  static constexpr int BYTES = (int)((sizeof(T) * (2 * I * I + J * I) + 15) / 16 * 16);
+struct ParamsA {
+  static constexpr bool DUP = false;
+  static constexpr int NP = (DUP ? 4 : 2) * I * I;  // P values
+  static constexpr int NL = (DUP ? 2 : 1) * J * I;  // Lambda values
+  T v[NP + NL];
+  static constexpr int BYTES = (int)((sizeof(T) * (NP + NL) + 15) / 16 * 16);
+  __device__ T pre(int r, int c) const { return DUP ? v[4 * (r * I + c)] : v[r * I + c]; }
+  __device__ T pim(int r, int c) const { return DUP ? v[4 * (r * I + c) + 2] : v[I * I + r * I + c]; }
+  __device__ T lam(int j, int i) const { return DUP ? v[NP + 2 * (j * I + i)] : v[NP + j * I + i]; }
+  __device__ void set_p(int r, int c, T re, T im) {
+    if constexpr (DUP) {
+      T* q = v + 4 * (r * I + c);
+      q[0] = re;
+      q[1] = re;
+      q[2] = im;
+      q[3] = im;
+    } else {
+      v[r * I + c] = re;
+      v[I * I + r * I + c] = im;
+    }
+  }
+  __device__ void set_lam(int j, int i, T l) {
+    if constexpr (DUP) {
+      v[NP + 2 * (j * I + i)] = l;
+      v[NP + 2 * (j * I + i) + 1] = l;
+    } else {
+      v[NP + j * I + i] = l;
+    }
+  }
 };
 template <typename T, int I, int J>
 struct ParamsB {  // pass B: the new Lambda(f)
@@ -152,7 +181,7 @@ __global__ void __launch_bounds__(32 * kFinalWarps) k_afinal(FastArgs a) {
     const double lnew = *lp * ((double)I * pt.inv_n(f)) * tot;
     if (!(lnew > 0.0) || !isfinite(lnew)) raise_status(a.status, kDevNonfinite, f);
     *lp = lnew;
-    tab_a<T, I, J>(a, f)->lam[j][i] = (T)lnew;
+    tab_a<T, I, J>(a, f)->set_lam(j, i, (T)lnew);
     tab_b<T, I, J>(a, f)->lam[j][i] = (T)lnew;
   }
   if (lane == NA % 32) {
@@ -248,7 +277,7 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
     for (int j = 0; j < J; ++j) {
       const double l = a.lam_next[(size_t)f * J * I + j * I + i];
       a.lam[(size_t)f * J * I + j * I + i] = l;
-      ta->lam[j][i] = (T)l;
+      ta->set_lam(j, i, (T)l);
     }
   }
 
@@ -329,8 +358,7 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
         if (c == i) ari = A[r][c];
       a.P[((size_t)f * I * I + r * I + i) * 2] = ari.re;
       a.P[((size_t)f * I * I + r * I + i) * 2 + 1] = ari.im;
-      ta->pre[r][i] = (T)ari.re;
-      ta->pim[r][i] = (T)ari.im;
+      ta->set_p(r, i, (T)ari.re, (T)ari.im);
     }
     if (singular) raise_status(a.status, kDevSingular, f);
     if (i == 0) {
@@ -375,11 +403,10 @@ __global__ void __launch_bounds__(32) k_prep(FastArgs a) {
   ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
   for (int r = 0; r < I; ++r) {
-    ta->pre[r][i] = (T)A[r][i].re;
-    ta->pim[r][i] = (T)A[r][i].im;
+    ta->set_p(r, i, (T)A[r][i].re, (T)A[r][i].im);
   }
 #pragma unroll
-  for (int j = 0; j < J; ++j) ta->lam[j][i] = (T)a.lam[(size_t)f * J * I + j * I + i];
+  for (int j = 0; j < J; ++j) ta->set_lam(j, i, (T)a.lam[(size_t)f * J * I + j * I + i]);
   cpx<double> C[I];
   const cpx<double> det = column_cofactors<I>(A, i, C);
   const double d2 = cabs2(det);

@@ -28,21 +28,28 @@ using Real = float;
 #endif
 
 #if FFCA_PART == 0
+// The P step by Gauss-Jordan and LDL^H (k_psolve_ldl, which carries P^{-H}
+// from one step to the next) from FFCA_LDL_MIN_I microphones up; below it
+// the cofactor forms of k_psolve.
+#ifndef FFCA_LDL_MIN_I
+#define FFCA_LDL_MIN_I 4
+#endif
 template <int J>
 static const FastKernels* table_entry() {
-  constexpr bool BIG = FFCA_I > 4;  // per-problem solves by elimination instead of cofactors
+  constexpr bool BIG = FFCA_I > 4;            // per-point parameters read from the stage, per-source Wiener
+  constexpr bool LDL = FFCA_I >= FFCA_LDL_MIN_I;
   const void* psolve;
   const void* prep;
   const void* wiener;
-  if constexpr (BIG) {
-    psolve = (const void*)k_psolve_big<Real, FFCA_I, J>;
-    prep = (const void*)k_prep_big<Real, FFCA_I, J>;
-    wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
+  if constexpr (LDL) {
+    psolve = (const void*)k_psolve_ldl<Real, FFCA_I, J>;
+    prep = (const void*)k_prep_gj<Real, FFCA_I, J>;
   } else {
     psolve = (const void*)k_psolve<Real, FFCA_I, J>;
     prep = (const void*)k_prep<Real, FFCA_I, J>;
-    wiener = (const void*)k_wiener<Real, FFCA_I, J>;
   }
+  if constexpr (BIG) wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
+  else wiener = (const void*)k_wiener<Real, FFCA_I, J>;
   static const FastKernels k = {
       Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
       StreamGroups<Real, FFCA_I, J>::value,
@@ -55,7 +62,8 @@ static const FastKernels* table_entry() {
       (const void*)k_afinal<Real, FFCA_I, J, false>,
       ParamsA<Real, FFCA_I, J>::BYTES,
       ParamsB<Real, FFCA_I, J>::BYTES,
-      BIG ? BigLane<FFCA_I>::SMEM : 0,
+      LDL ? BigLane<FFCA_I>::SMEM : 0,
+      LDL ? 1 : 0,
   };
   return &k;
 }

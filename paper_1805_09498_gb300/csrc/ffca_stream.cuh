@@ -102,7 +102,14 @@ struct Tile {
                                 ? FFCA_TILE_UNITS_PER_THREAD
                                 : 1) *
                            kConsumers;  // units per tile
-  static constexpr int STAGE = T * UB + PARAMS;                   // bytes per stage, multiple of 16
+  // stage layout: I y rows of YP 16-byte units (pitch skewed by one unit for
+  // I > 4, whose pass-B consumers read I rows at the same unit in one
+  // instruction: the skew puts them in distinct banks), J v rows of T
+  // 8-byte units, the parameter record
+  static constexpr int YP = T + (I > 4 ? 1 : 0);
+  static constexpr int VOFF = I * YP * 16;                        // byte offset of the v rows
+  static constexpr int ROFF = VOFF + J * T * 8;                   // byte offset of the record
+  static constexpr int STAGE = ROFF + PARAMS;                     // bytes per stage, multiple of 16
   // I > 4: pass B's static reduction buffer (I^3 sums of 7 warps, two floats) takes ~29 KB
   static constexpr int BUDGET = kStreamSmemBudget - (I > 4 ? 32 * 1024 : 0);
   static constexpr int S_FIT = (BUDGET / G) / (STAGE + 16);
@@ -429,7 +436,7 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
 #pragma unroll
       for (int c = 0; c < FI::NC; ++c) {
         const int q = (int)(threadIdx.x & 31) + 32 * c;
-        if (q < NA) (&reinterpret_cast<PB*>(stp + TC::T * TC::UB)->lam[0][0])[q] = lam_q[c];
+        if (q < NA) (&reinterpret_cast<PB*>(stp + TC::ROFF)->lam[0][0])[q] = lam_q[c];
       }
       __syncwarp();
       if (!leader) {
@@ -439,7 +446,7 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
       mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB));
     } else {
       mbar_expect_tx(pp.full(s), (unsigned)(it.n * TC::UB + PA::BYTES));
-      bulk_g2s(st + TC::T * TC::UB, tab + (size_t)it.f * PA::BYTES, (unsigned)PA::BYTES, pp.full(s));
+      bulk_g2s(st + TC::ROFF, tab + (size_t)it.f * PA::BYTES, (unsigned)PA::BYTES, pp.full(s));
     }
     // rows of the problem's blocks (units): mic m at I Fm off + (m Fm + f) ld,
     // source j at J Fm off + (j Fm + f) ld (frames / FU)
@@ -448,11 +455,11 @@ __device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, lon
     const long long r0 = (long long)pt.freq(it.f) * rlen + it.k;
 #pragma unroll
     for (int m = 0; m < I; ++m)
-      bulk_g2s(st + m * TC::T * 16, y + ((size_t)I * pt.Fm * off + (size_t)m * pt.Fm * rlen + r0) * 16,
+      bulk_g2s(st + m * TC::YP * 16, y + ((size_t)I * pt.Fm * off + (size_t)m * pt.Fm * rlen + r0) * 16,
                (unsigned)it.n * 16, pp.full(s));
 #pragma unroll
     for (int j = 0; j < J; ++j)
-      bulk_g2s(st + I * TC::T * 16 + j * TC::T * 8,
+      bulk_g2s(st + TC::VOFF + j * TC::T * 8,
                v + ((size_t)J * pt.Fm * off + (size_t)j * pt.Fm * rlen + r0) * 8, (unsigned)it.n * 8, pp.full(s));
     ++t;
   }
@@ -618,14 +625,18 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   constexpr int RI = BIG ? 1 : I, RJ = BIG ? 1 : J;
   L pre_r[RI][RI], pim_r[RI][RI], lam_r[RJ][RI];
   const PA* spc = nullptr;
-  auto PRE = [&](int m, int i) -> L {
-    if constexpr (BIG) return LN::bc(spc->pre[m][i]); else return pre_r[m][i];
-  };
-  auto PIM = [&](int m, int i) -> L {
-    if constexpr (BIG) return LN::bc(spc->pim[m][i]); else return pim_r[m][i];
+  // (re, im) of P_mi as frame-lane operands
+  auto PP = [&](int m, int i, L& pr, L& pi) {
+    if constexpr (BIG) {
+      pr = LN::bc(spc->pre(m, i));
+      pi = LN::bc(spc->pim(m, i));
+    } else {
+      pr = pre_r[m][i];
+      pi = pim_r[m][i];
+    }
   };
   auto LAM = [&](int j, int i) -> L {
-    if constexpr (BIG) return LN::bc(spc->lam[j][i]); else return lam_r[j][i];
+    if constexpr (BIG) return LN::bc(spc->lam(j, i)); else return lam_r[j][i];
   };
   // FP32 with more than 32 sums: one float per value (both frames of a unit
   // go into it) instead of a packed pair
@@ -652,24 +663,24 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     VV* __restrict__ vrow = vg + (size_t)J * pt.Fm * (pt.frame_off(f) / FU) + (size_t)pt.freq(f) * rlen;
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
-      spc = reinterpret_cast<const PA*>(st + TC::T * TC::UB);  // every stage carries the record
+      spc = reinterpret_cast<const PA*>(st + TC::ROFF);  // every stage carries the record
       if constexpr (!BIG) {
         if (seg_new) {  // this frequency's P and Lambda arrived with the tile
 #pragma unroll
           for (int r = 0; r < I; ++r)
 #pragma unroll
             for (int c = 0; c < I; ++c) {
-              pre_r[r][c] = LN::bc(spc->pre[r][c]);
-              pim_r[r][c] = LN::bc(spc->pim[r][c]);
+              pre_r[r][c] = LN::bc(spc->pre(r, c));
+              pim_r[r][c] = LN::bc(spc->pim(r, c));
             }
 #pragma unroll
           for (int j = 0; j < J; ++j)
 #pragma unroll
-            for (int i = 0; i < I; ++i) lam_r[j][i] = LN::bc(spc->lam[j][i]);
+            for (int i = 0; i < I; ++i) lam_r[j][i] = LN::bc(spc->lam(j, i));
         }
       }
       const VY* ys = reinterpret_cast<const VY*>(st);
-      const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
+      const VV* vs = reinterpret_cast<const VV*>(st + TC::VOFF);
 #pragma unroll 1
       for (int q = tid; q < it.n; q += kConsumers) {
         const int k = it.k + q;
@@ -678,7 +689,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         L yre[I], yim[I], nyre[I], vv[J];
 #pragma unroll
         for (int m = 0; m < I; ++m) {
-          LN::split(ys[m * TC::T + q], yre[m], yim[m]);
+          LN::split(ys[m * TC::YP + q], yre[m], yim[m]);
           nyre[m] = yre[m] * LN::bc(-1);
         }
 #pragma unroll
@@ -689,15 +700,18 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 #pragma unroll
         for (int i = 0; i < I; ++i) {
           // y~_i = sum_m conj(P_mi) y_m: re = Pr yr + Pi yi, im = Pr yi - Pi yr
-          L tr = PRE(0, i) * yre[0], ti = PRE(0, i) * yim[0];
-          tr = vfma(PIM(0, i), yim[0], tr);
-          ti = vfma(PIM(0, i), nyre[0], ti);
+          L pr, pi;
+          PP(0, i, pr, pi);
+          L tr = pr * yre[0], ti = pr * yim[0];
+          tr = vfma(pi, yim[0], tr);
+          ti = vfma(pi, nyre[0], ti);
 #pragma unroll
           for (int m = 1; m < I; ++m) {
-            tr = vfma(PRE(m, i), yre[m], tr);
-            tr = vfma(PIM(m, i), yim[m], tr);
-            ti = vfma(PRE(m, i), yim[m], ti);
-            ti = vfma(PIM(m, i), nyre[m], ti);
+            PP(m, i, pr, pi);
+            tr = vfma(pr, yre[m], tr);
+            tr = vfma(pi, yim[m], tr);
+            ti = vfma(pr, yim[m], ti);
+            ti = vfma(pi, nyre[m], ti);
           }
           L sg = vv[0] * LAM(0, i);
 #pragma unroll
@@ -782,11 +796,45 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 }
 
 // Pass B consumers for I > 4: the I^3 sums per point do not fit one thread's
-// registers, so consumer thread c owns the weight index i = c mod I and
-// accumulates V_i = sum_n y y^H / sigma_i (I^2 values, packed Hermitian) over
-// every (kConsumers / I)-th unit of each tile.  At a segment's end the lanes
-// of a warp with the same i (those equal mod I; I divides 32) are summed by
-// shuffles, then the warps through shared memory, in double-float.
+// registers, so each unit is shared by I = 8 threads that split the entries
+// of y y^H, not the weights: thread e of a unit accumulates the diagonal
+// entry |y_e|^2 and the off-diagonal entries y_r conj(y_c) of the pairs
+// p = 4e .. 4e+3 (row order over r < c; thread 7 only its diagonal), each
+// against all I weights 1/sigma_i.  Thread e forms sigma_e and 1/sigma_e for
+// the unit's frames and the I threads exchange them by shuffles, so every
+// weight is computed once.  An off-diagonal entry is accumulated as one
+// (re, im) pair per weight with the packed f32x2 FMA.  At a segment's end
+// the lanes with the same e (equal mod 8) are summed by shuffles, then the
+// warps through shared memory, in double-float; the values go out in the
+// packed Hermitian order of V_i (diagonal, then (re, im) above it).
+template <int I>
+struct BigEntries {
+  static constexpr int PAIRS = I * (I - 1) / 2;         // off-diagonal entries
+  static constexpr int SLOTS = (PAIRS + I - 1) / I;     // per thread (4 at I = 8)
+  static constexpr int NVT = I + 2 * I * SLOTS;         // values per thread: diagonal + slots
+  static_assert(I == 8, "the entry split is laid out for I = 8");
+  // packed-order index of pair p (row order over r < c) and its (r, c)
+  __device__ static void decode(int p, int& r, int& c) {
+    r = 0;
+    int q = p;
+    while (q >= I - 1 - r) {
+      q -= I - 1 - r;
+      ++r;
+    }
+    c = r + 1 + q;
+  }
+  // reduction index of thread e's value v (threads below I - 1 keep all NVT
+  // values, thread I - 1 only its I diagonal sums): I^3 indices in all
+  __device__ static int red_index(int e, int v) { return e * NVT + v; }
+  // output index (weight i, packed entry m) of reduction index x
+  __device__ static int out_index(int x) {
+    const int e = x / NVT, v = x % NVT;
+    if (v < I) return v * I * I + e;  // diagonal |y_e|^2 against weight v
+    const int k = (v - I) / (2 * I), i = ((v - I) % (2 * I)) / 2, comp = (v - I) % 2;
+    return i * I * I + I + 2 * (SLOTS * e + k) + comp;
+  }
+};
+
 template <typename T, int I, int J, typename Red, int S>
 __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long u0, long long u1, const Role& rl,
                                  volatile int* abort, typename Red::Smem& red) {
@@ -796,21 +844,29 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
   using L = typename LN::L;
   using TC = Tile<T, I, J>;
   using PB = ParamsB<T, I, J>;
+  using BE = BigEntries<I>;
+  using T2 = std::conditional_t<sizeof(T) == 4, float2, double2>;
   constexpr int FU = Vec<T>::FU;
-  constexpr int I2 = I * I;
-  constexpr int IG = kConsumers / I;  // unit lanes per weight index
+  constexpr int SL = BE::SLOTS;
+  constexpr int IG = kConsumers / I;  // units in flight per group
   static_assert(kConsumers % I == 0 && 32 % I == 0, "I must divide the consumer count and the warp");
   const Partition& pt = a.part;
   const int tid = rl.ctid, lane = threadIdx.x & 31;
-  const int myi = tid % I, ul = tid / I;
-  L lamv[J];
-  // FP32: one float per value (both frames of a unit go into it)
-  constexpr bool kNarrow = sizeof(T) == 4;
-  using A = std::conditional_t<kNarrow, float, L>;
-  A acc[I2];
-  auto ACC = [&](int q, L wv, L x) {
-    if constexpr (kNarrow) acc[q] = fmaf(wv.v.y, x.v.y, fmaf(wv.v.x, x.v.x, acc[q]));
-    else acc[q] = vfma(wv, x, acc[q]);
+  const int e = tid % I, ul = tid / I;
+  const int gl = lane & ~(I - 1);  // first lane of this unit's I threads
+  int sr[SL], sc[SL];
+#pragma unroll
+  for (int k = 0; k < SL; ++k) {
+    const int p = SL * e + k;
+    if (p < BE::PAIRS) BE::decode(p, sr[k], sc[k]);
+    else { sr[k] = 0; sc[k] = 1; }  // thread I - 1: unused slots
+  }
+  L lame[J];
+  L accd[I];        // diagonal |y_e|^2 / sigma_i, per frame lane
+  T2 acco[SL][I];   // off-diagonal (re, im) / sigma_i
+  auto fma2 = [](T w, T xr, T xi, T2 acc) -> T2 {
+    if constexpr (sizeof(T) == 4) return __ffma2_rn(make_float2(w, w), make_float2(xr, xi), acc);
+    else return make_double2(fma(w, xr, acc.x), fma(w, xi, acc.y));
   };
   TileIter it(u0, u1, pt, TC::T, true);
   bool seg_new = true;
@@ -818,50 +874,74 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
     const int f = it.f;
     if (seg_new) {
 #pragma unroll
-      for (int q = 0; q < I2; ++q) {
-        if constexpr (kNarrow) acc[q] = 0.f;
-        else acc[q] = LN::bc(0);
+      for (int i = 0; i < I; ++i) {
+        accd[i] = LN::bc(0);
+#pragma unroll
+        for (int k = 0; k < SL; ++k) acco[k][i] = T2{0, 0};
       }
     }
     const int Np = pt.frames(f);
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % S) * TC::STAGE;
       if (seg_new) {
-        const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
+        const PB& sp = *reinterpret_cast<const PB*>(st + TC::ROFF);
 #pragma unroll
-        for (int j = 0; j < J; ++j) lamv[j] = LN::bc(sp.lam[j][myi]);
+        for (int j = 0; j < J; ++j) lame[j] = LN::bc(sp.lam[j][e]);
       }
       const VY* ys = reinterpret_cast<const VY*>(st);
-      const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
+      const VV* vs = reinterpret_cast<const VV*>(st + TC::VOFF);
+      // every lane runs the same trips (the shuffles need the whole warp);
+      // units beyond the tile or frames beyond N get zero weight and data
 #pragma unroll 1
-      for (int q = ul; q < it.n; q += IG) {
+      for (int qb = 0; qb < it.n; qb += IG) {
+        const int q = qb + ul;  // < T: it.n <= T and T is a multiple of IG
         const int n0 = (it.k + q) * FU;
-        if (n0 >= Np) continue;
-        L yre[I], yim[I];
+        const bool unit_ok = q < it.n && n0 < Np;
+        L sg = LN::real(vs[q]) * lame[0];
 #pragma unroll
-        for (int m = 0; m < I; ++m) LN::split(ys[m * TC::T + q], yre[m], yim[m]);
-        L sg = LN::real(vs[q]) * lamv[0];
-#pragma unroll
-        for (int j = 1; j < J; ++j) sg = vfma(LN::real(vs[j * TC::T + q]), lamv[j], sg);
+        for (int j = 1; j < J; ++j) sg = vfma(LN::real(vs[j * TC::T + q]), lame[j], sg);
         L w = vrcp(sg);
-        if (n0 + FU > Np) {  // the ragged last unit: drop the frames beyond N
-          w = LN::keep(w, n0, Np);
+        w = unit_ok ? LN::keep(w, n0, Np) : LN::bc(0);
+        L wi[I];
+        if constexpr (sizeof(T) == 4) {
 #pragma unroll
-          for (int m = 0; m < I; ++m) {
-            yre[m] = LN::keep(yre[m], n0, Np);
-            yim[m] = LN::keep(yim[m], n0, Np);
-          }
+          for (int i = 0; i < I; ++i)
+            wi[i] = {make_float2(__shfl_sync(0xffffffffu, w.v.x, gl | i), __shfl_sync(0xffffffffu, w.v.y, gl | i))};
+        } else {
+#pragma unroll
+          for (int i = 0; i < I; ++i) wi[i] = {__shfl_sync(0xffffffffu, w.v, gl | i)};
         }
-        int e = I;
+        if (!unit_ok) continue;  // after the shuffles: nothing below involves other lanes
+        const bool ragged = n0 + FU > Np;
+        // the diagonal entry |y_e|^2 (per frame lane)
+        {
+          L yr, yi;
+          LN::split(ys[e * TC::YP + q], yr, yi);
+          if (ragged) {
+            yr = LN::keep(yr, n0, Np);
+            yi = LN::keep(yi, n0, Np);
+          }
+          const L d2 = vfma(yr, yr, yi * yi);
 #pragma unroll
-        for (int r = 0; r < I; ++r) {
-          ACC(r, w, vfma(yre[r], yre[r], yim[r] * yim[r]));
+          for (int i = 0; i < I; ++i) accd[i] = vfma(wi[i], d2, accd[i]);
+        }
 #pragma unroll
-          for (int c = r + 1; c < I; ++c) {
-            // re(y_r conj(y_c)), im(y_r conj(y_c))
-            ACC(e, w, vfma(yre[r], yre[c], yim[r] * yim[c]));
-            ACC(e + 1, w, vfma(yim[r], yre[c], (yre[r] * yim[c]) * LN::bc(-1)));
-            e += 2;
+        for (int k = 0; k < SL; ++k) {
+          const VY xu = ys[sr[k] * TC::YP + q];
+          const VY yu = ys[sc[k] * TC::YP + q];
+#pragma unroll
+          for (int fr = 0; fr < FU; ++fr) {
+            if (ragged && n0 + fr >= Np) continue;
+            const cpx<T> x = yframe(xu, fr), y = yframe(yu, fr);
+            const T pr = fma(x.re, y.re, x.im * y.im);   // re(y_r conj(y_c))
+            const T pi = fma(x.im, y.re, -(x.re * y.im)); // im(y_r conj(y_c))
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+              T wf;
+              if constexpr (sizeof(T) == 4) wf = fr == 0 ? wi[i].v.x : wi[i].v.y;
+              else wf = wi[i].v;
+              acco[k][i] = fma2(wf, pr, pi, acco[k][i]);
+            }
           }
         }
       }
@@ -871,48 +951,58 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
 
     if (it.seg_end) {
       const int slot = rl.vb - pt.first_block(f);
-      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * (I * I2);
-      T h[I2], l[I2];
+      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * (I * I * I);
+      T h[BE::NVT], l[BE::NVT];
 #pragma unroll
-      for (int q = 0; q < I2; ++q) {
-        if constexpr (kNarrow) {
-          h[q] = acc[q];
-          l[q] = 0.f;
+      for (int i = 0; i < I; ++i) {
+        if constexpr (sizeof(T) == 4) {
+          two_sum(accd[i].v.x, accd[i].v.y, h[i], l[i]);  // the two frame lanes, exactly
         } else {
-          h[q] = acc[q].v;
-          l[q] = (T)0;
+          h[i] = accd[i].v;
+          l[i] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k < SL; ++k) {
+          h[I + k * 2 * I + 2 * i] = acco[k][i].x;
+          h[I + k * 2 * I + 2 * i + 1] = acco[k][i].y;
+          l[I + k * 2 * I + 2 * i] = 0;
+          l[I + k * 2 * I + 2 * i + 1] = 0;
         }
       }
+      // the lanes with the same e: offsets I, 2 I, ... within the warp
 #pragma unroll
       for (int off = I; off < 32; off <<= 1)
 #pragma unroll
-        for (int q = 0; q < I2; ++q) {
-          const T rh = __shfl_xor_sync(0xffffffffu, h[q], off);
+        for (int v = 0; v < BE::NVT; ++v) {
+          const T rh = __shfl_xor_sync(0xffffffffu, h[v], off);
           if constexpr (sizeof(T) == 4) {
-            const T rlo = __shfl_xor_sync(0xffffffffu, l[q], off);
-            df_add(h[q], l[q], rh, rlo);
+            const T rlo = __shfl_xor_sync(0xffffffffu, l[v], off);
+            df_add(h[v], l[v], rh, rlo);
           } else {
-            h[q] += rh;
+            h[v] += rh;
           }
         }
       if (lane < I) {
+        const int nv = lane < I - 1 ? BE::NVT : I;
 #pragma unroll
-        for (int q = 0; q < I2; ++q) {
-          red.hi[rl.cwarp][lane * I2 + q] = h[q];
-          if constexpr (sizeof(T) == 4) red.lo[rl.cwarp][lane * I2 + q] = l[q];
+        for (int v = 0; v < BE::NVT; ++v) {
+          if (v < nv) {
+            red.hi[rl.cwarp][BE::red_index(lane, v)] = h[v];
+            if constexpr (sizeof(T) == 4) red.lo[rl.cwarp][BE::red_index(lane, v)] = l[v];
+          }
         }
       }
       consumer_sync(rl.group);
-      for (int vq = tid; vq < I * I2; vq += kConsumers) {
-        T sh = red.hi[0][vq];
+      for (int x = tid; x < I * I * I; x += kConsumers) {
+        T sh = red.hi[0][x];
         T sl = (T)0;
-        if constexpr (sizeof(T) == 4) sl = red.lo[0][vq];
+        if constexpr (sizeof(T) == 4) sl = red.lo[0][x];
 #pragma unroll
         for (int w2 = 1; w2 < kConsumerWarps; ++w2) {
-          if constexpr (sizeof(T) == 4) df_add(sh, sl, red.hi[w2][vq], red.lo[w2][vq]);
-          else sh += red.hi[w2][vq];
+          if constexpr (sizeof(T) == 4) df_add(sh, sl, red.hi[w2][x], red.lo[w2][x]);
+          else sh += red.hi[w2][x];
         }
-        out[vq] = (double)sh + (double)sl;
+        out[BE::out_index(x)] = (double)sh + (double)sl;
       }
       consumer_sync(rl.group);
       seg_new = true;
@@ -982,14 +1072,14 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
       if (consumer_acquire(a, pp, t, f, abort)) {
         const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
         if (seg_new) {  // the new Lambda(f) arrived with the tile
-          const PB& sp = *reinterpret_cast<const PB*>(st + TC::T * TC::UB);
+          const PB& sp = *reinterpret_cast<const PB*>(st + TC::ROFF);
   #pragma unroll
           for (int j = 0; j < J; ++j)
   #pragma unroll
             for (int i = 0; i < I; ++i) lam[j][i] = LN::bc(sp.lam[j][i]);
         }
         const VY* ys = reinterpret_cast<const VY*>(st);
-        const VV* vs = reinterpret_cast<const VV*>(st + I * TC::T * 16);
+        const VV* vs = reinterpret_cast<const VV*>(st + TC::VOFF);
   #pragma unroll 1
         for (int q = tid; q < it.n; q += kConsumers) {
           const int k = it.k + q;
@@ -998,7 +1088,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
           L yre[I], yim[I], nyre[I], vv[J];
   #pragma unroll
           for (int m = 0; m < I; ++m) {
-            LN::split(ys[m * TC::T + q], yre[m], yim[m]);
+            LN::split(ys[m * TC::YP + q], yre[m], yim[m]);
             nyre[m] = yre[m] * LN::bc(-1);
           }
   #pragma unroll
