@@ -16,7 +16,6 @@ independently seeded mixture (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -46,16 +45,6 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def _csrc_hash() -> str:
-    h = hashlib.sha256()
-    for d in (os.path.join(ROOT, "paper_1805_09498_gb300", "csrc"), os.path.join(ROOT, "include")):
-        for f in sorted(os.listdir(d)):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode())
-                h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
 def _ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources; else None."""
@@ -65,7 +54,8 @@ def _ncu_traffic(kernel: str):
     except OSError:
         return None
     k = t.get("kernels", {}).get(kernel)
-    if not k or t.get("csrc_sha") != _csrc_hash():
+    from paper_1805_09498_gb300.profile_traffic import sources_hash
+    if not k or t.get("csrc_sha") != sources_hash():
         return None
     return k.get("dram_bytes_per_launch")
 

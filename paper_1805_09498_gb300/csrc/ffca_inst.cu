@@ -32,7 +32,7 @@ using Real = float;
 // from one step to the next) from FFCA_LDL_MIN_I microphones up; below it
 // the cofactor forms of k_psolve.
 #ifndef FFCA_LDL_MIN_I
-#define FFCA_LDL_MIN_I 4
+#define FFCA_LDL_MIN_I 3
 #endif
 template <int J>
 static const FastKernels* table_entry() {

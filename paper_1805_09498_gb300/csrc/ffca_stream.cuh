@@ -174,65 +174,58 @@ __device__ inline void consumer_sync(int group) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "n"(kConsumers) : "memory");
 }
 
-// Reduction of NV per-thread pairs (hi, lo) over a group's consumer warps: a
-// butterfly reduce-scatter inside each warp (at level `off` every lane keeps
-// half of its remaining values and receives the partner's partial sums of
-// that half from lane ^ off: 31 exchanges reduce 32 values where a tree per
-// value needs 5 each; lane l ends with value l of its chunk), then the warp
-// results summed in shared memory in warp order.  FP32 pairs combine with
-// double-float additions (compensated), FP64 values plainly.  Consumer
-// thread t < NV writes value t to out[t] (as a double).
+// Reduction of NV per-thread values (hi + lo) over a group's consumer warps:
+// a butterfly reduce-scatter inside each warp (at level `off` every lane
+// keeps half of its remaining values and receives the partner's partial
+// sums of that half from lane ^ off: 31 exchanges reduce 32 values where a
+// tree per value needs 5 each; lane l ends with value l of its chunk), in
+// plain arithmetic (a pairwise tree of five levels), then the seven warp
+// results summed in shared memory in warp order, compensated in FP32
+// (double-float: TwoSum of each addition, errors carried), written as FP64.
+// A segment's per-thread sums cover few frames when problems are short (the
+// batched workload: ~4 units per thread), so this reduction runs about as
+// often as the per-point work; a compensated butterfly (two shuffles and a
+// double-float addition per exchange) made it half of pass B's instructions
+// there.  Consumer thread t < NV writes value t to out[t].
 template <typename T, int NV>
 struct GroupReduce {
   static constexpr int NC = (NV + 31) / 32;  // chunks of 32 values
   static constexpr bool PAIR = sizeof(T) == 4;
   struct Smem {
     T hi[kConsumerWarps][NC * 32];
-    T lo[PAIR ? kConsumerWarps : 1][PAIR ? NC * 32 : 1];
+    T lo[PAIR ? kConsumerWarps : 1][PAIR ? NC * 32 : 1];  // used by the I > 4 pass B
   };
 
   __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& sm, double* out, const Role& r) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      T h[32], l[32];
+      T h[32];
 #pragma unroll
       for (int v = 0; v < 32; ++v) {
         const int idx = c * 32 + v;
-        h[v] = idx < NV ? hi[idx] : (T)0;
-        l[v] = idx < NV ? lo[idx] : (T)0;
+        h[v] = idx < NV ? hi[idx] + lo[idx] : (T)0;
       }
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1) {
         const bool up = (lane & off) != 0;
 #pragma unroll
         for (int j = 0; j < off; ++j) {
-          T kh = up ? h[j + off] : h[j];
+          const T kh = up ? h[j + off] : h[j];
           const T sh = up ? h[j] : h[j + off];
-          const T rh = __shfl_xor_sync(0xffffffffu, sh, off);
-          if constexpr (PAIR) {
-            T kl = up ? l[j + off] : l[j];
-            const T sl = up ? l[j] : l[j + off];
-            const T rl = __shfl_xor_sync(0xffffffffu, sl, off);
-            df_add(kh, kl, rh, rl);
-            l[j] = kl;
-          } else {
-            kh += rh;
-          }
-          h[j] = kh;
+          h[j] = kh + __shfl_xor_sync(0xffffffffu, sh, off);
         }
       }
       sm.hi[r.cwarp][c * 32 + lane] = h[0];
-      if constexpr (PAIR) sm.lo[r.cwarp][c * 32 + lane] = l[0];
     }
     consumer_sync(r.group);
     for (int t = r.ctid; t < NV; t += kConsumers) {
       T h = sm.hi[0][t];
-      T l = PAIR ? sm.lo[0][t] : (T)0;
+      T l = (T)0;
 #pragma unroll
       for (int w = 1; w < kConsumerWarps; ++w) {
         if constexpr (PAIR) {
-          df_add(h, l, sm.hi[w][t], sm.lo[w][t]);
+          df_add(h, l, sm.hi[w][t], (T)0);
         } else {
           h += sm.hi[w][t];
         }
@@ -778,7 +771,8 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         float hi[NV], lo[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);  // the two frame lanes, exactly
+          hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
+          lo[q] = 0.f;
         }
         Red::run(hi, lo, red, out, rl);
       } else {
@@ -956,7 +950,8 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
 #pragma unroll
       for (int i = 0; i < I; ++i) {
         if constexpr (sizeof(T) == 4) {
-          two_sum(accd[i].v.x, accd[i].v.y, h[i], l[i]);  // the two frame lanes, exactly
+          h[i] = accd[i].v.x + accd[i].v.y;  // the two frame lanes
+          l[i] = 0.f;
         } else {
           h[i] = accd[i].v;
           l[i] = 0;
@@ -969,37 +964,27 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
           l[I + k * 2 * I + 2 * i + 1] = 0;
         }
       }
-      // the lanes with the same e: offsets I, 2 I, ... within the warp
+      // the lanes with the same e (offsets I, 2 I, ... within the warp), in
+      // plain arithmetic; the warps' sums then compensated, as GroupReduce
+#pragma unroll
+      for (int v = 0; v < BE::NVT; ++v) h[v] += l[v];
 #pragma unroll
       for (int off = I; off < 32; off <<= 1)
 #pragma unroll
-        for (int v = 0; v < BE::NVT; ++v) {
-          const T rh = __shfl_xor_sync(0xffffffffu, h[v], off);
-          if constexpr (sizeof(T) == 4) {
-            const T rlo = __shfl_xor_sync(0xffffffffu, l[v], off);
-            df_add(h[v], l[v], rh, rlo);
-          } else {
-            h[v] += rh;
-          }
-        }
+        for (int v = 0; v < BE::NVT; ++v) h[v] += __shfl_xor_sync(0xffffffffu, h[v], off);
       if (lane < I) {
         const int nv = lane < I - 1 ? BE::NVT : I;
 #pragma unroll
-        for (int v = 0; v < BE::NVT; ++v) {
-          if (v < nv) {
-            red.hi[rl.cwarp][BE::red_index(lane, v)] = h[v];
-            if constexpr (sizeof(T) == 4) red.lo[rl.cwarp][BE::red_index(lane, v)] = l[v];
-          }
-        }
+        for (int v = 0; v < BE::NVT; ++v)
+          if (v < nv) red.hi[rl.cwarp][BE::red_index(lane, v)] = h[v];
       }
       consumer_sync(rl.group);
       for (int x = tid; x < I * I * I; x += kConsumers) {
         T sh = red.hi[0][x];
         T sl = (T)0;
-        if constexpr (sizeof(T) == 4) sl = red.lo[0][x];
 #pragma unroll
         for (int w2 = 1; w2 < kConsumerWarps; ++w2) {
-          if constexpr (sizeof(T) == 4) df_add(sh, sl, red.hi[w2][x], red.lo[w2][x]);
+          if constexpr (sizeof(T) == 4) df_add(sh, sl, red.hi[w2][x], (T)0);
           else sh += red.hi[w2][x];
         }
         out[BE::out_index(x)] = (double)sh + (double)sl;
@@ -1111,27 +1096,28 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
               nyre[m] = LN::keep(nyre[m], n0, Np);
             }
           }
-          L pk[I2];
+          // each packed entry of y y^H, then at once its I weighted sums (the
+          // entry is live for one step only)
+          auto add = [&](int mm, L x) {
+  #pragma unroll
+            for (int i = 0; i < I; ++i) {
+              if constexpr (kNarrow)
+                acc[i * I2 + mm] = fmaf(w[i].v.y, x.v.y, fmaf(w[i].v.x, x.v.x, acc[i * I2 + mm]));
+              else
+                acc[i * I2 + mm] = vfma(w[i], x, acc[i * I2 + mm]);
+            }
+          };
           int m = I;
   #pragma unroll
           for (int rr = 0; rr < I; ++rr) {
-            pk[rr] = vfma(yre[rr], yre[rr], yim[rr] * yim[rr]);
+            add(rr, vfma(yre[rr], yre[rr], yim[rr] * yim[rr]));
   #pragma unroll
             for (int c = rr + 1; c < I; ++c) {
-              pk[m] = vfma(yre[rr], yre[c], yim[rr] * yim[c]);       // re(y_r conj(y_c))
-              pk[m + 1] = vfma(nyre[rr], yim[c], yim[rr] * yre[c]);  // im(y_r conj(y_c))
+              add(m, vfma(yre[rr], yre[c], yim[rr] * yim[c]));           // re(y_r conj(y_c))
+              add(m + 1, vfma(nyre[rr], yim[c], yim[rr] * yre[c]));      // im(y_r conj(y_c))
               m += 2;
             }
           }
-  #pragma unroll
-          for (int i = 0; i < I; ++i)
-  #pragma unroll
-            for (int mm = 0; mm < I2; ++mm) {
-              if constexpr (kNarrow)
-                acc[i * I2 + mm] = fmaf(w[i].v.y, pk[mm].v.y, fmaf(w[i].v.x, pk[mm].v.x, acc[i * I2 + mm]));
-              else
-                acc[i * I2 + mm] = vfma(w[i], pk[mm], acc[i * I2 + mm]);
-            }
         }
       }
 
@@ -1152,7 +1138,10 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
         } else if constexpr (sizeof(T) == 4) {
           float hi[NV], lo[NV];
   #pragma unroll
-          for (int q = 0; q < NV; ++q) two_sum(acc[q].v.x, acc[q].v.y, hi[q], lo[q]);
+          for (int q = 0; q < NV; ++q) {
+            hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
+            lo[q] = 0.f;
+          }
           Red::run(hi, lo, red, out, rl);
         } else {
           double hi[NV], lo[NV];
