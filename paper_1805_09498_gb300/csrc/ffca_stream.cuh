@@ -642,6 +642,9 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 
   TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
+  int Np = 0;               // the segment's problem: frames,
+  long long rlen = 0;       // units per row of its block,
+  VV* __restrict__ vrow = vg;  // and its v row 0 (looked up once per segment)
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
     if (seg_new) {
@@ -650,10 +653,10 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         if constexpr (kNarrow) acc[q] = 0.f;
         else acc[q] = LN::bc(0);
       }
+      Np = pt.frames(f);
+      rlen = pt.row_len(f, row * FU) / FU;
+      vrow = vg + (size_t)J * pt.Fm * (pt.frame_off(f) / FU) + (size_t)pt.freq(f) * rlen;
     }
-    const int Np = pt.frames(f);
-    const long long rlen = pt.row_len(f, row * FU) / FU;  // units per row of the problem's block
-    VV* __restrict__ vrow = vg + (size_t)J * pt.Fm * (pt.frame_off(f) / FU) + (size_t)pt.freq(f) * rlen;
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
       spc = reinterpret_cast<const PA*>(st + TC::ROFF);  // every stage carries the record
@@ -864,6 +867,7 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
   };
   TileIter it(u0, u1, pt, TC::T, true);
   bool seg_new = true;
+  int Np = 0;  // frames of the segment's problem (looked up once per segment)
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
     if (seg_new) {
@@ -873,8 +877,8 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
 #pragma unroll
         for (int k = 0; k < SL; ++k) acco[k][i] = T2{0, 0};
       }
+      Np = pt.frames(f);
     }
-    const int Np = pt.frames(f);
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % S) * TC::STAGE;
       if (seg_new) {
