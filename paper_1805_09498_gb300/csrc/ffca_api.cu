@@ -98,7 +98,7 @@ struct Plan {
   size_t off_info, off_ustart, off_msum;  // batch: problem tables, per-mixture sums
   size_t off_bstartA[kCands], off_slotsA[kCands], off_bstartB[kCands], off_slotsB[kCands];  // batch candidates
   size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
-  size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
+  size_t off_cntA, off_cntB, off_logdet, off_llf, off_tpart, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
 };
 
@@ -168,6 +168,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_cntB = off; off = align_up(off + sizeof(unsigned) * P);
   p->off_logdet = off; off = align_up(off + sizeof(double) * P);
   p->off_llf = off; off = align_up(off + sizeof(double) * P);
+  p->off_tpart = off; off = align_up(off + sizeof(double) * P);  // per-block trace sums of the P step
   p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
   p->off_pinvH = off; off = align_up(off + sizeof(double) * 2 * I * I * (size_t)P);
   p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2));
@@ -256,6 +257,7 @@ FastArgs base_args(const ffca_ctx* c) {
   a.logdet = reinterpret_cast<double*>(c->ws + c->plan.off_logdet);
   a.llf = reinterpret_cast<double*>(c->ws + c->plan.off_llf);
   a.trace = reinterpret_cast<double*>(c->ws + c->plan.off_trace);
+  a.tpart = reinterpret_cast<double*>(c->ws + c->plan.off_tpart);
   a.status = c->status;
   a.ops = c->ops;
   a.tabA = c->ws + c->plan.off_tabA;

@@ -166,11 +166,52 @@ __device__ void ldl_solve(const cpx<double> (&lo)[I * (I - 1) / 2], const double
     }
 }
 
-// Column c of P^{-H} and ln|det P|^2 from the columns of P (lane (g, c)
-// holds column c of P in x[]): transpose through the problem's shared
-// buffer M (rows padded to LDM), conjugate into column c of P^H, invert.
+// Column c of P^{-H} and |det P|^2 from the columns of P (lane (g, c) holds
+// column c of P in x[]), for I <= 4 by cofactors: one division instead of I
+// dependent pivot steps.  The lane gathers P with its columns rotated,
+// A[:, k] = P[:, (c + k) mod I], so that column c of the cofactor matrix is
+// column 0 of A's, up to the sign (-1)^(c (I-1-c)) of the rotation of the
+// other columns; then (P^{-H})_{rc} = conj(C_rc / det P) with det P the
+// expansion along column 0 of lane (g, 0), shared by the problem's lanes.
+template <int I>
+__device__ double pinvh_cofactors(cpx<double> (&x)[I], int g, int c, bool& singular) {
+  static_assert(I <= 4, "cofactor forms for I <= 4");
+  cpx<double> A[I][I];
+#pragma unroll
+  for (int k = 0; k < I; ++k) {
+    const int src = g * I + (c + k) % I;
+#pragma unroll
+    for (int r = 0; r < I; ++r) A[r][k] = shfl_c(x[r], src);
+  }
+  const bool flip = ((c * (I - 1 - c)) & 1) != 0;
+  cpx<double> C[I];
+  cpx<double> det = mk(0.0, 0.0);
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const cpx<double> m = minor_det<I>(A, r, 0);
+    C[r] = ((((r + c) & 1) != 0) != flip) ? mk(-m.re, -m.im) : m;
+    det = cadd(det, cmul(A[r][0], C[r]));
+  }
+  det = shfl_c(det, g * I);  // the expansion of lane (g, 0), for every lane of the problem
+  const double d2 = cabs2(det);
+  singular |= !(d2 > 0.0) || !isfinite(d2);
+  const double inv = 1.0 / d2;
+  const cpx<double> rdet = mk(det.re * inv, -det.im * inv);  // 1 / det
+#pragma unroll
+  for (int r = 0; r < I; ++r) x[r] = cconj(cmul(C[r], rdet));
+  return (d2 > 0.0 && isfinite(d2)) ? d2 : 0.0;
+}
+
+// Column c of P^{-H} and |det P|^2 from the columns of P (lane (g, c) holds
+// column c of P in x[]): for I <= 3 by cofactors (the shortest FP64
+// dependency chain: 18.7 against 20.4 us per long-mixture P step); else
+// transpose through the problem's shared buffer M (rows padded to LDM),
+// conjugate into column c of P^H, invert by Gauss-Jordan (fewer FP64
+// instructions from I = 4: the batched P step, bound by FP64 throughput,
+// takes 181 us against 219 us with the cofactors).
 template <int I>
 __device__ double pinvh_from_columns(cpx<double> (&x)[I], cpx<double>* M, int g, int c, bool& singular) {
+  if constexpr (I <= 3) return pinvh_cofactors<I>(x, g, c, singular);
   constexpr int LDM = BigLane<I>::LDM;
   __syncwarp();
 #pragma unroll
@@ -198,45 +239,56 @@ __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
   cpx<double>* M = reinterpret_cast<cpx<double>*>(big_smem) + (size_t)(g < G ? g : G) * I * BL::LDM;
   const Partition pt = a.part;
 
-  if (active && a.lam_next) {
-    ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+  // every global load first, all independent of one another: the new
+  // Lambda, column i of P^{-H} of the current P, and the slots of V_i
+  // (packed Hermitian: diagonal, then (re, im) above it in row order; 16-byte
+  // loads where the I^2 values of each i start on a 16-byte boundary)
+  double lnext[J];
+  if (a.lam_next) {
 #pragma unroll
-    for (int j = 0; j < J; ++j) {
-      const double l = a.lam_next[(size_t)f * J * I + j * I + i];
-      a.lam[(size_t)f * J * I + j * I + i] = l;
-      ta->set_lam(j, i, (T)l);
-    }
+    for (int j = 0; j < J; ++j) lnext[j] = __ldcg(a.lam_next + (size_t)f * J * I + j * I + i);
   }
-  // column i of P^{-H} of the current P
   cpx<double> x[I];
 #pragma unroll
   for (int r = 0; r < I; ++r) {
     const double2 q = __ldcg(reinterpret_cast<const double2*>(a.pinvH) + (size_t)f * I * I + r * I + i);
     x[r] = mk(q.x, q.y);
   }
-  // V_i from the slots (packed Hermitian: diagonal, then (re, im) above it in
-  // row order), slot by slot; 16-byte loads where the I^2 values of each i
-  // start on a 16-byte boundary (I^2 even), 8-byte loads otherwise
   double dv[I], rd[I];
   cpx<double> lo[NL];
   {
     double pk[I * I];
-#pragma unroll
-    for (int m = 0; m < I * I; ++m) pk[m] = 0.0;
-    const int ns = pt.nslots(f);
+    const int ns = pt.nslots(f);  // >= 1: every problem has a slot
     const double* base = a.part_buf + ((size_t)f * pt.max_slots) * NV + i * I * I;
-    for (int k = 0; k < ns; ++k) {
-      if constexpr ((I * I) % 2 == 0) {
-        const double2* b2 = reinterpret_cast<const double2*>(base + (size_t)k * NV);
+    if constexpr ((I * I) % 2 == 0) {
+      const double2* b2 = reinterpret_cast<const double2*>(base);
+#pragma unroll
+      for (int m = 0; m < I * I / 2; ++m) {
+        const double2 v2 = __ldcg(b2 + m);
+        pk[2 * m] = v2.x;
+        pk[2 * m + 1] = v2.y;
+      }
+      for (int k = 1; k < ns; ++k) {
 #pragma unroll
         for (int m = 0; m < I * I / 2; ++m) {
-          const double2 q = __ldcg(b2 + m);
-          pk[2 * m] += q.x;
-          pk[2 * m + 1] += q.y;
+          const double2 v2 = __ldcg(b2 + (size_t)k * (NV / 2) + m);
+          pk[2 * m] += v2.x;
+          pk[2 * m + 1] += v2.y;
         }
-      } else {
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < I * I; ++m) pk[m] = __ldcg(base + m);
+      for (int k = 1; k < ns; ++k)
 #pragma unroll
         for (int m = 0; m < I * I; ++m) pk[m] += __ldcg(base + (size_t)k * NV + m);
+    }
+    if (active && a.lam_next) {  // commit the new Lambda (computed during pass B)
+      ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        a.lam[(size_t)f * J * I + j * I + i] = lnext[j];
+        ta->set_lam(j, i, (T)lnext[j]);
       }
     }
     const double sc = pt.inv_n(f);
@@ -290,50 +342,42 @@ __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
       a.logdet[f] = log(det2);
     }
   }
-  if (a.trace) {
-    unsigned last = 0;
-    if (lane == 0) {
-      last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
-      if (last) *a.gcnt = 0u;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      finalize_trace(a);
-    }
-  }
+  // the trace: per-block sums of the problems' log-likelihoods, then the last block
+  if (a.trace) trace_by_blocks(a, (active && i == 0) ? __ldcg(a.llf + f) : 0.0);
 }
 
 // ln|det P|^2, P^{-H} (always: the P step starts from it) and the pass-A
-// table of the current P and Lambda.
+// table of the current P and Lambda.  P^{-H} is formed by the same routine
+// (pinvh_from_columns) as the P step's carried one, so iterating in one call
+// or in several gives the same bits.
 template <typename T, int I, int J>
 __global__ void __launch_bounds__(32) k_prep_gj(FastArgs a) {
   using BL = BigLane<I>;
   constexpr int G = BL::G;
+  extern __shared__ __align__(16) unsigned char big_smem[];
   const int lane = threadIdx.x;
   const int g = lane / I, i = lane % I;
   const int f0 = blockIdx.x * G + g;
   const bool active = g < G && f0 < a.F;
   const int f = active ? f0 : 0;
+  cpx<double>* M = reinterpret_cast<cpx<double>*>(big_smem) + (size_t)(g < G ? g : G) * I * BL::LDM;
+  cpx<double> x[I];  // column i of P
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const double2 q = reinterpret_cast<const double2*>(a.P)[(size_t)f * I * I + r * I + i];
+    x[r] = mk(q.x, q.y);
+  }
   if (active) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
-    for (int r = 0; r < I; ++r) {
-      ta->set_p(r, i, (T)a.P[((size_t)f * I * I + r * I + i) * 2], (T)a.P[((size_t)f * I * I + r * I + i) * 2 + 1]);
-    }
+    for (int r = 0; r < I; ++r) ta->set_p(r, i, (T)x[r].re, (T)x[r].im);
 #pragma unroll
     for (int j = 0; j < J; ++j) ta->set_lam(j, i, (T)a.lam[(size_t)f * J * I + j * I + i]);
   }
-  // column i of P^H is the conjugate of row i of P
-  cpx<double> x[I];
-#pragma unroll
-  for (int r = 0; r < I; ++r) {
-    const double2 q = reinterpret_cast<const double2*>(a.P)[(size_t)f * I * I + i * I + r];
-    x[r] = mk(q.x, -q.y);
-  }
-  const double det2 = gj_inverse_cols<I>(x, g, i);
+  bool singular = false;
+  const double det2 = pinvh_from_columns<I>(x, M, g, i, singular);
   if (!active) return;
-  if (!(det2 > 0.0)) raise_status(a.status, kDevSingular, f);
+  if (singular) raise_status(a.status, kDevSingular, f);
   if (i == 0) a.logdet[f] = log(det2);
   if (a.pinvH) {
 #pragma unroll

@@ -32,6 +32,7 @@ struct FastArgs {
   double* logdet;            // [F] ln|det P(f)|^2 of the current P
   double* llf;               // [F] per-frequency log-likelihood
   double* trace;             // [kTraceCap]
+  double* tpart;             // [blocks of the P step] per-block sums of llf for the trace
   int trace_slot;
   unsigned* status;          // [2] first error code, its frequency
   unsigned long long* ops;   // matrix inversions performed by the P update
@@ -137,23 +138,58 @@ __device__ inline double sum_slots(const double* part_buf, int f, int nslots, in
   return s;
 }
 
-// Sum of the per-frequency log-likelihoods in a fixed order (one warp; each
-// lane keeps eight running sums so that eight loads are in flight at a time)
-// into the trace slot.
-__device__ inline void finalize_trace(const FastArgs& a) {
+// Sum of the n values v[0..n) in a fixed order by one warp (lane l takes
+// v[l + 32 u] of each round of 512, all 16 loads of a round in flight at
+// once; a fixed tree over u, then over the lanes).  Returned in every lane.
+__device__ inline double warp_sum_fixed(const double* v, int n) {
   const int lane = threadIdx.x & 31;
-  double s[8];
+  double t = 0.0;
+  for (int b = 0; b < n; b += 512) {
+    double s[16];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) s[u] = 0.0;
-  for (int f = lane; f < a.F; f += 256) {
+    for (int u = 0; u < 16; ++u) {
+      const int k = b + lane + 32 * u;
+      s[u] = k < n ? __ldcg(v + k) : 0.0;
+    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (f + 32 * u < a.F) s[u] += __ldcg(a.llf + f + 32 * u);
+    for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+      for (int u = 0; u < w; ++u) s[u] += s[u + w];
+    t += s[0];
   }
-  double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-  if (lane == 0) a.trace[a.trace_slot] = t;
+  return t;
+}
+
+// Sum of the per-frequency log-likelihoods into the trace slot (one warp).
+__device__ inline void finalize_trace(const FastArgs& a) {
+  const double t = warp_sum_fixed(a.llf, a.F);
+  if ((threadIdx.x & 31) == 0) a.trace[a.trace_slot] = t;
+}
+
+// The trace from the P step's blocks (one warp each): every block adds the
+// log-likelihoods of its problems (own: this lane's share, summed over the
+// warp in a fixed tree) into tpart[block]; the last block to finish sums
+// the blocks' partial sums in block order into the trace slot.  No block
+// waits on another.
+__device__ inline void trace_by_blocks(const FastArgs& a, double own) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) own += __shfl_xor_sync(0xffffffffu, own, off);
+  unsigned last = 0;
+  if (lane == 0) {
+    a.tpart[blockIdx.x] = own;
+    __threadfence();
+    last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
+    if (last) *a.gcnt = 0u;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence();
+    const double t = warp_sum_fixed(a.tpart, gridDim.x);
+    if (lane == 0) a.trace[a.trace_slot] = t;
+  }
 }
 
 // -------------------------------------------------------------- pass A finalise
@@ -368,19 +404,8 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
       a.logdet[f] = log(d2);
     }
   }
-  // the trace: the last warp adds the per-frequency log-likelihoods
-  if (a.trace) {
-    unsigned last = 0;
-    if (lane == 0) {
-      last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
-      if (last) *a.gcnt = 0u;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last) {
-      __threadfence();
-      finalize_trace(a);
-    }
-  }
+  // the trace: per-block sums of the problems' log-likelihoods, then the last block
+  if (a.trace) trace_by_blocks(a, (active && i == 0) ? __ldcg(a.llf + f) : 0.0);
 }
 
 // -------------------------------------------------------------- prep
