@@ -187,16 +187,24 @@ __device__ inline void consumer_sync(int group) {
 // often as the per-point work; a compensated butterfly (two shuffles and a
 // double-float addition per exchange) made it half of pass B's instructions
 // there.  Consumer thread t < NV writes value t to out[t].
-template <typename T, int NV>
+// The warp partials alternate between two buffers from one segment to the
+// next (parity), so one barrier per segment suffices: a thread writes the
+// buffer of segment s + 2 only after the barrier of segment s + 1, which
+// every thread reaches after its reads of segment s.
+template <typename T, int NV, int NB = 2>
 struct GroupReduce {
   static constexpr int NC = (NV + 31) / 32;  // chunks of 32 values
   static constexpr bool PAIR = sizeof(T) == 4;
   struct Smem {
-    T hi[kConsumerWarps][NC * 32];
-    T lo[PAIR ? kConsumerWarps : 1][PAIR ? NC * 32 : 1];  // used by the I > 4 pass B
+    T hi[NB][kConsumerWarps][NC * 32];  // NB = 1: single buffer, two barriers per segment
   };
+  // single-buffered view (the I > 4 pass B, two barriers per segment)
+  __device__ static T (&one(Smem& sm))[kConsumerWarps][NC * 32] { return sm.hi[0]; }
 
-  __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& sm, double* out, const Role& r) {
+  __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& smem, double* out, const Role& r,
+                             int parity) {
+    static_assert(NB == 2, "run() alternates two buffers");
+    auto& sm = smem.hi[parity & 1];
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -216,23 +224,22 @@ struct GroupReduce {
           h[j] = kh + __shfl_xor_sync(0xffffffffu, sh, off);
         }
       }
-      sm.hi[r.cwarp][c * 32 + lane] = h[0];
+      sm[r.cwarp][c * 32 + lane] = h[0];
     }
     consumer_sync(r.group);
     for (int t = r.ctid; t < NV; t += kConsumers) {
-      T h = sm.hi[0][t];
+      T h = sm[0][t];
       T l = (T)0;
 #pragma unroll
       for (int w = 1; w < kConsumerWarps; ++w) {
         if constexpr (PAIR) {
-          df_add(h, l, sm.hi[w][t], (T)0);
+          df_add(h, l, sm[w][t], (T)0);
         } else {
-          h += sm.hi[w][t];
+          h += sm[w][t];
         }
       }
       out[t] = (double)h + (double)l;
     }
-    consumer_sync(r.group);
   }
 };
 
@@ -642,6 +649,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 
   TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
+  int nseg = 0;  // segments reduced so far (reduction buffer parity)
   int Np = 0;               // the segment's problem: frames,
   long long rlen = 0;       // units per row of its block,
   VV* __restrict__ vrow = vg;  // and its v row 0 (looked up once per segment)
@@ -769,7 +777,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           hi[q] = acc[q];
           lo[q] = 0.f;
         }
-        Red::run(hi, lo, red, out, rl);
+        Red::run(hi, lo, red, out, rl, nseg);
       } else if constexpr (sizeof(T) == 4) {
         float hi[NV], lo[NV];
 #pragma unroll
@@ -777,7 +785,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
           lo[q] = 0.f;
         }
-        Red::run(hi, lo, red, out, rl);
+        Red::run(hi, lo, red, out, rl, nseg);
       } else {
         double hi[NV], lo[NV];
 #pragma unroll
@@ -785,8 +793,9 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           hi[q] = acc[q].v;
           lo[q] = 0.0;
         }
-        Red::run(hi, lo, red, out, rl);
+        Red::run(hi, lo, red, out, rl, nseg);
       }
+      ++nseg;  // the next segment reduces through the other buffer
       seg_new = true;
     }
   }
@@ -980,16 +989,16 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
         const int nv = lane < I - 1 ? BE::NVT : I;
 #pragma unroll
         for (int v = 0; v < BE::NVT; ++v)
-          if (v < nv) red.hi[rl.cwarp][BE::red_index(lane, v)] = h[v];
+          if (v < nv) Red::one(red)[rl.cwarp][BE::red_index(lane, v)] = h[v];
       }
       consumer_sync(rl.group);
       for (int x = tid; x < I * I * I; x += kConsumers) {
-        T sh = red.hi[0][x];
+        T sh = Red::one(red)[0][x];
         T sl = (T)0;
 #pragma unroll
         for (int w2 = 1; w2 < kConsumerWarps; ++w2) {
-          if constexpr (sizeof(T) == 4) df_add(sh, sl, red.hi[w2][x], (T)0);
-          else sh += red.hi[w2][x];
+          if constexpr (sizeof(T) == 4) df_add(sh, sl, Red::one(red)[w2][x], (T)0);
+          else sh += Red::one(red)[w2][x];
         }
         out[BE::out_index(x)] = (double)sh + (double)sl;
       }
@@ -1013,7 +1022,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   constexpr int FU = Vec<T>::FU;
   constexpr int I2 = I * I;
   constexpr int NV = I * I2;
-  using Red = GroupReduce<T, NV>;
+  using Red = GroupReduce<T, NV, (I > 4 ? 1 : 2)>;
 
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int G = StreamGroups<T, I, J>::value;
@@ -1048,6 +1057,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
 
     TileIter it(u0, u1, pt, TC::T, true);
     bool seg_new = true;
+    int nseg = 0;  // segments reduced so far (reduction buffer parity)
     for (int t = 0; it.next(); ++t) {
       const int f = it.f;
       if (seg_new) {
@@ -1138,7 +1148,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
             hi[q] = acc[q];
             lo[q] = 0.f;
           }
-          Red::run(hi, lo, red, out, rl);
+          Red::run(hi, lo, red, out, rl, nseg);
         } else if constexpr (sizeof(T) == 4) {
           float hi[NV], lo[NV];
   #pragma unroll
@@ -1146,7 +1156,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
             hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
             lo[q] = 0.f;
           }
-          Red::run(hi, lo, red, out, rl);
+          Red::run(hi, lo, red, out, rl, nseg);
         } else {
           double hi[NV], lo[NV];
   #pragma unroll
@@ -1154,8 +1164,9 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
             hi[q] = acc[q].v;
             lo[q] = 0.0;
           }
-          Red::run(hi, lo, red, out, rl);
+          Red::run(hi, lo, red, out, rl, nseg);
         }
+        ++nseg;  // the next segment reduces through the other buffer
         seg_new = true;
       }
     }
