@@ -335,6 +335,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
     batched = run_batched(args, dev)
     large = run_large_array(args, dev)
     adjoint = run_adjoint(dev)
+    front = run_front_end(dev)
 
     # roofline of the dominant kernel: algorithmic bytes per launch / mean duration
     peaks, peak_src = _peaks()
@@ -382,6 +383,7 @@ def run_ours(args, cfg, rank, ws, local, dist):
         "batched": batched,
         "large_array": large,
         "adjoint": adjoint,
+        "stft_front_end": front,
     }
 
 
@@ -535,6 +537,48 @@ def run_large_array(args, dev):
                       "ms_per_iter": msf / itf, "precision": "mixed (same as the FastFCA-AS run)"}
     out["speedup_vs_fca_gpu"] = out["value"] / out["fca_gpu"]["value"]
     del est, yd, vd, lamd, Pd, v_init, lam_init, P_init, vf, S0, Pinv
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_front_end(dev):
+    """The STFT front end and overlap-add back end (Table 1 conditions) at the
+    long mixture's size: the STFT of I = 3 channels of (N - 1) 512 + 1024
+    samples (N = 20000 frames) and the inverse of the Wiener output's J I = 9
+    spectra; algorithmic bytes = samples read + spectra written (or back);
+    error against numpy's FFT on sampled frames."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    N, L, H = 20000, ffca.STFT_L, ffca.STFT_H
+    S = (N - 1) * H + L
+    g = torch.Generator(device=dev)
+    g.manual_seed(31)
+    x = torch.randn((3, S), generator=g, device=dev, dtype=torch.float32)
+    X, n = ffca.stft(x)
+    Xw = torch.randn((9, ffca.STFT_F, X.shape[2]), generator=g, device=dev, dtype=torch.complex64)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"STFT of 3 channels x {S} samples (N = {N} frames, F = 513) and inverse of 9 "
+                       "spectra of the same size, c64 / float32"}
+    for name, fn, byt in (("stft", lambda: ffca.stft(x), 3 * S * 4 + 3 * ffca.STFT_F * N * 8),
+                          ("istft", lambda: ffca.istft(Xw, n), 9 * ffca.STFT_F * N * 8 + 9 * (N + 1) * H * 4)):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(10):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        out[name] = {"ms": ms, "bytes": byt, "achieved_gbs": byt / (ms * 1e-3) / 1e9}
+    fr = [0, 1, 9999, N - 1]
+    xs = x.cpu().double().numpy()
+    w = np.sin(np.pi * np.arange(L) / L)
+    ref = np.stack([np.fft.rfft(xs[:, k * H: k * H + L] * w, axis=-1) for k in fr], axis=-1)
+    got = X[:, :, fr].cpu().numpy()
+    out["stft"]["error_vs_numpy_fft"] = float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+    del x, X, Xw
     torch.cuda.empty_cache()
     return out
 

@@ -329,6 +329,32 @@ ffca_status ffca_fca_op_counts(ffca_fca_ctx* ctx, unsigned long long* inversions
 int ffca_fca_error_frequency(const ffca_fca_ctx* ctx);
 void ffca_fca_destroy(ffca_fca_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * STFT front end and overlap-add back end with the paper's analysis
+ * conditions (Table 1: frame length L = 1024 samples, frame shift H = 512,
+ * square root of the Hann window; F = L/2 + 1 = 513 bins up to the Nyquist
+ * frequency, Sec. 2), so that time-domain mixtures enter and separated
+ * time-domain images leave the estimation API.  The window is the periodic
+ * Hann window's square root, w(t) = sin(pi t / L), so that analysis and
+ * synthesis windows together sum to one over the overlapping frames.
+ * Arithmetic in FP32 (complex64 spectra, float signals); every pointer is a
+ * DEVICE pointer owned by the caller; enqueued on `stream`.
+ *
+ * ffca_stft: x [C][S] float (C channels of S samples, 4-byte aligned) ->
+ *   out [C][F][ld] complex64 (16-byte aligned; the mic-planar layout of y in
+ *   ffca_desc), N = 1 + (S - L) / H frames (0 if S < L; frame n holds samples
+ *   n H .. n H + L - 1, no padding):
+ *     out[c][f][n] = sum_t w(t) x[c][n H + t] exp(-2 pi i f t / L);
+ *   frames N .. ld - 1 are written as zero.  ld >= N, ld % 4 == 0.
+ * ffca_istft: in [C][F][ld] complex64 (first N frames used) -> out [C][(N+1) H]
+ *   float: out[c][s] = sum_n w(s - n H) x_n(s - n H), x_n the inverse DFT
+ *   (1/L, Hermitian extension; the imaginary parts of bins 0 and L/2 are
+ *   ignored, as for the spectrum of a real signal) of frame n.  Samples H .. N H - 1, covered by
+ *   two frames, reconstruct the signal that ffca_stft analysed.
+ * FFCA_ERR_ARG on bad sizes, strides or alignment; C and N of 0 are no-ops. */
+ffca_status ffca_stft(const float* x, int C, long long S, void* out, int ld, void* stream);
+ffca_status ffca_istft(const void* in, int C, int N, int ld, float* out, void* stream);
+
 const char* ffca_status_str(ffca_status s);
 
 /* Text of the last CUDA call the library saw fail in the calling thread

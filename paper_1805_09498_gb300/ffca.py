@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
         "ffca_fca_op_counts": (ci, [vp, P(ctypes.c_ulonglong), P(ctypes.c_ulonglong)]),
         "ffca_fca_error_frequency": (ci, [vp]),
         "ffca_fca_destroy": (None, [vp]),
+        "ffca_stft": (ci, [vp, ci, ctypes.c_longlong, vp, ci, vp]),
+        "ffca_istft": (ci, [vp, ci, ci, ci, vp, vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
         "ffca_last_error": (ctypes.c_char_p, []),
     }
@@ -128,6 +130,48 @@ def lib() -> ctypes.CDLL:
         fn.argtypes = args
     _lib = L
     return L
+
+
+# ------------------------------------------------------------ STFT front / back end
+STFT_L, STFT_H = 1024, 512
+STFT_F = STFT_L // 2 + 1
+
+
+def stft_frames(S: int) -> int:
+    """Frames ffca_stft makes of S samples."""
+    return 1 + (S - STFT_L) // STFT_H if S >= STFT_L else 0
+
+
+def stft(x, ld: int | None = None, stream=None):
+    """ffca_stft: x [C, S] float32 CUDA -> (X [C, F, ld] complex64, N)."""
+    import torch
+    if not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous [C, S] float32 CUDA tensor")
+    C, S = x.shape
+    N = stft_frames(S)
+    ld = padded_ld(max(N, 1)) if ld is None else ld
+    out = torch.empty((C, STFT_F, ld), dtype=torch.complex64, device=x.device)
+    s = stream if stream is not None else torch.cuda.current_stream(x.device)
+    st = lib().ffca_stft(x.data_ptr(), C, S, out.data_ptr(), ld, s.cuda_stream)
+    if st != 0:
+        raise FFCAError(st, "ffca_stft")
+    return out, N
+
+
+def istft(X, N: int, stream=None):
+    """ffca_istft: X [C, F, ld] complex64 CUDA (first N frames) -> x [C, (N+1) H] float32."""
+    import torch
+    if not X.is_cuda or X.dtype != torch.complex64 or X.dim() != 3 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous [C, F, ld] complex64 CUDA tensor")
+    C, Fb, ld = X.shape
+    if Fb != STFT_F:
+        raise ValueError(f"X must have {STFT_F} bins")
+    out = torch.empty((C, (N + 1) * STFT_H if N else 0), dtype=torch.float32, device=X.device)
+    s = stream if stream is not None else torch.cuda.current_stream(X.device)
+    st = lib().ffca_istft(X.data_ptr(), C, N, ld, out.data_ptr(), s.cuda_stream)
+    if st != 0:
+        raise FFCAError(st, "ffca_istft")
+    return out
 
 
 def header_functions() -> list[str]:
