@@ -118,8 +118,10 @@ ffca_status ffca_loglik(ffca_ctx* ctx, double* ll);
 /* Multichannel Wiener filter (Eq. MMSE0 with Eq. covmodelprop):
  * out[j][a][f][n] = [P^{-H} diag(v_j lambda_j / sigma) P^H y(n,f)]_a with
  * sigma_i = sum_j v_j lambda_ji.  out: device, [J][I][F][ld] complex of the
- * precision's type, caller-owned; padding frames are written as zero.
- * Enqueued only.  FFCA_ERR_UNSUPPORTED for batch contexts. */
+ * precision's type, caller-owned; padding frames are written as zero.  For a
+ * batch context out holds the mixtures' blocks one after another, mixture m's
+ * block [J][I][F][ld_m] starting at element J I F frame_offset[m] (the layout
+ * of y and v in ffca_batch_desc).  Enqueued only. */
 ffca_status ffca_wiener(ffca_ctx* ctx, void* out);
 
 /* Wait for the context's stream and return the latched device status. */
@@ -145,8 +147,9 @@ ffca_status ffca_upload(ffca_ctx* ctx, const void* y_host, const void* v_host,
 ffca_status ffca_download(ffca_ctx* ctx, void* v_host, double* lambda_host, double* P_host);
 
 /* Multichannel Wiener filter for host-memory callers: runs ffca_wiener into
- * the caller's device buffer out_dev ([J][I][F][ld] complex) and copies it to
- * out_host (same layout), then synchronises. */
+ * the caller's device buffer out_dev ([J][I][F][ld] complex; a batch: J I F ld
+ * elements in total) and copies it to out_host (same layout), then
+ * synchronises. */
 ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
 
 /* ---------------------------------------------------------------------------

@@ -96,6 +96,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Plan {
   Partition pA, pB, pW;
   size_t off_info, off_ustart, off_msum;  // batch: problem tables, per-mixture sums
+  size_t off_ustartW, off_bstartW;        // batch: the Wiener pass's unit starts and block ranges
   size_t off_bstartA[kCands], off_slotsA[kCands], off_bstartB[kCands], off_slotsB[kCands];  // batch candidates
   size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_tpart, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
@@ -180,7 +181,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_partAdj = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2 * I * I + 2));
   p->off_lossf = off; off = align_up(off + sizeof(double) * (size_t)P);
   p->off_loss = off; off = align_up(off + sizeof(double));
-  p->off_info = p->off_ustart = p->off_msum = 0;
+  p->off_info = p->off_ustart = p->off_msum = p->off_ustartW = p->off_bstartW = 0;
   for (int q = 0; q < kCands; ++q) p->off_bstartA[q] = p->off_slotsA[q] = p->off_bstartB[q] = p->off_slotsB[q] = 0;
   p->bytes = off;
 }
@@ -198,7 +199,7 @@ ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
   p->pA = make_partition(F, Uf, o.nsm * o.occA * k->stream_groups * FFCA_GRID_WAVES, d->N);
   p->pB = make_partition(F, Uf, o.nsm * o.occB * k->stream_groups * FFCA_GRID_WAVES, d->N);
   // the Wiener pass also covers the padding frames (it writes them as zero)
-  p->pW = make_partition(F, d->ld / FU, o.nsm * o.occW);
+  p->pW = make_partition(F, d->ld / FU, o.nsm * o.occW, d->N);
   p->pA.F = p->pB.F = p->pW.F = d->F;
   p->pA.Fm = p->pB.Fm = p->pW.Fm = d->F;
   layout(p, k, F, d->I, d->J);
@@ -611,7 +612,6 @@ ffca_status ffca_loglik(ffca_ctx* c, double* ll) {
 
 ffca_status ffca_wiener(ffca_ctx* c, void* out) {
   if (!c) return FFCA_ERR_ARG;
-  if (c->plan.off_info) return FFCA_ERR_UNSUPPORTED;  // batch contexts: not provided
   if (c->d.F == 0) return FFCA_OK;
   if (!out || (reinterpret_cast<uintptr_t>(out) % 16) != 0) return FFCA_ERR_ARG;
   ffca_status st = launch_prep(c, true);
@@ -625,11 +625,11 @@ ffca_status ffca_wiener(ffca_ctx* c, void* out) {
 
 ffca_status ffca_wiener_host(ffca_ctx* c, void* out_dev, void* out_host) {
   if (!c || !out_host) return FFCA_ERR_ARG;
-  if (c->plan.off_info) return FFCA_ERR_UNSUPPORTED;
   ffca_status st = ffca_wiener(c, out_dev);
   if (st != FFCA_OK) return st;
   const size_t rsz = c->d.prec == FFCA_PREC_FP64 ? 8 : 4;
-  const size_t bytes = (size_t)c->d.J * c->d.I * c->d.F * c->d.ld * 2 * rsz;
+  // J I frequencies-per-mixture rows of ld frames (a batch: the mixtures' blocks, ld in total)
+  const size_t bytes = (size_t)c->d.J * c->d.I * c->Fm * c->d.ld * 2 * rsz;
   if (bytes && cudaMemcpyAsync(out_host, out_dev, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
     return FFCA_ERR_CUDA;
   return read_status(c);
@@ -849,6 +849,9 @@ ffca_status batch_check(const ffca_batch_desc* d) {
 struct BatchTables {
   std::vector<ProbInfo> info;
   std::vector<long long> ustart;
+  std::vector<long long> ustartW, bstartW;  // the Wiener pass: every frame of each row, padding included
+  std::vector<int2> slotsW;
+  Partition candW;
   std::vector<long long> bstartA[kCands], bstartB[kCands];
   std::vector<int2> slotsA[kCands], slotsB[kCands];
   Partition candA[kCands], candB[kCands];
@@ -874,6 +877,20 @@ ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, 
     }
   }
   t->ustart[P] = u;
+  // the Wiener pass covers the padding frames of each row too (it writes them as zero)
+  t->ustartW.resize(P + 1);
+  long long uw = 0;
+  for (int m = 0; m < d->M; ++m)
+    for (int f = 0; f < d->F; ++f) {
+      t->ustartW[m * d->F + f] = uw;
+      uw += (d->frame_offset[m + 1] - d->frame_offset[m]) / FU;
+    }
+  t->ustartW[P] = uw;
+  t->bstartW.resize(o.nsm * o.occW + 1);
+  t->slotsW.resize(P);
+  t->candW = make_partition_ragged(P, d->F, t->ustartW.data(), o.nsm * o.occW, 0, t->bstartW.data(),
+                                   t->slotsW.data());
+  t->bstartW.resize(t->candW.nblocks + 1);
   const int slotsA = o.nsm * o.occA * k->stream_groups, slotsB = o.nsm * o.occB * k->stream_groups;
   int msA = 1, msB = 1;
   for (int c = 0; c < kCands; ++c) {
@@ -898,11 +915,13 @@ ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, 
   }
   p->pA = t->candA[0];
   p->pB = t->candB[0];
-  p->pW = make_partition(1, 2, 1);  // unused: the Wiener filter runs per mixture
+  p->pW = t->candW;
   layout(p, k, P, d->I, d->J);
   size_t off = p->bytes;
   p->off_info = off; off = align_up(off + sizeof(ProbInfo) * (size_t)P);
   p->off_ustart = off; off = align_up(off + sizeof(long long) * (size_t)(P + 1));
+  p->off_ustartW = off; off = align_up(off + sizeof(long long) * (size_t)(P + 1));
+  p->off_bstartW = off; off = align_up(off + sizeof(long long) * t->bstartW.size());
   p->off_msum = off; off = align_up(off + sizeof(double) * (size_t)d->M);
   for (int c = 0; c < kCands; ++c) {
     p->off_bstartA[c] = off; off = align_up(off + sizeof(long long) * t->bstartA[c].size());
@@ -990,7 +1009,13 @@ ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* d) {
   // pageable sources: the copies are staged before the calls return
   bool ok = cuda_ok(cudaMemsetAsync(c->ws, 0, p.bytes, c->stream), "cudaMemsetAsync") &&
             up(p.off_info, t.info.data(), sizeof(ProbInfo) * t.info.size(), "cudaMemcpyAsync(problems)") &&
-            up(p.off_ustart, t.ustart.data(), sizeof(long long) * t.ustart.size(), "cudaMemcpyAsync(unit starts)");
+            up(p.off_ustart, t.ustart.data(), sizeof(long long) * t.ustart.size(), "cudaMemcpyAsync(unit starts)") &&
+            up(p.off_ustartW, t.ustartW.data(), sizeof(long long) * t.ustartW.size(), "cudaMemcpyAsync(Wiener units)") &&
+            up(p.off_bstartW, t.bstartW.data(), sizeof(long long) * t.bstartW.size(), "cudaMemcpyAsync(Wiener ranges)");
+  c->plan.pW.info = dinfo;
+  c->plan.pW.ustart = reinterpret_cast<const long long*>(c->ws + p.off_ustartW);
+  c->plan.pW.bstart = reinterpret_cast<const long long*>(c->ws + p.off_bstartW);
+  c->plan.pW.slots = nullptr;  // the Wiener pass sums nothing
   for (int q = 0; q < kCands && ok; ++q) {
     c->candA[q] = t.candA[q];
     c->candB[q] = t.candB[q];

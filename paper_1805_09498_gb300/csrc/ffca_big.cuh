@@ -398,18 +398,23 @@ __global__ void __launch_bounds__(kBlock) k_wiener_big(FastArgs a) {
   __shared__ T sLam[J][I];
 
   const Partition pt = a.part;
-  const long long total = (long long)pt.F * pt.Uf;
-  const long long u0 = (long long)blockIdx.x * pt.upb;
-  const long long u1 = min(u0 + pt.upb, total);
+  const long long u0 = pt.block_start(blockIdx.x);
+  const long long u1 = pt.block_start(blockIdx.x + 1);
   const long long row = a.ld / FU;
-  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
-  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
-  VY* __restrict__ out = reinterpret_cast<VY*>(a.out);
 
   for (long long u = u0; u < u1;) {
-    const int f = (int)(u / pt.Uf);
-    const int k0 = (int)(u - (long long)f * pt.Uf);
-    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+    const int f = pt.problem_of(u);
+    const long long us = pt.start(f);
+    const int k0 = (int)(u - us);
+    const int k1 = (int)(min(pt.start(f + 1), u1) - us);
+    const int Np = pt.frames(f);
+    const long long rlen = pt.row_len(f, row * FU) / FU;
+    const long long off = pt.frame_off(f) / FU;
+    const long long r0 = (long long)pt.freq(f) * rlen;
+    const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y) + (size_t)I * pt.Fm * off + r0;
+    const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v) + (size_t)J * pt.Fm * off + r0;
+    VY* __restrict__ out = reinterpret_cast<VY*>(a.out) + (size_t)J * I * pt.Fm * off + r0;
+    const size_t rstr = (size_t)pt.Fm * rlen;
     __syncthreads();
     for (int t = threadIdx.x; t < I * I; t += kBlock) {
       const int r = t / I, c = t % I;
@@ -423,11 +428,11 @@ __global__ void __launch_bounds__(kBlock) k_wiener_big(FastArgs a) {
       T rs[FU][I];
       VV vu[J];
 #pragma unroll
-      for (int j = 0; j < J; ++j) vu[j] = v[((size_t)j * pt.F + f) * row + k];
+      for (int j = 0; j < J; ++j) vu[j] = v[j * rstr + k];
       {
         VY yu[I];
 #pragma unroll
-        for (int m = 0; m < I; ++m) yu[m] = y[((size_t)m * pt.F + f) * row + k];
+        for (int m = 0; m < I; ++m) yu[m] = y[m * rstr + k];
 #pragma unroll
         for (int e = 0; e < FU; ++e) {
 #pragma unroll
@@ -448,7 +453,7 @@ __global__ void __launch_bounds__(kBlock) k_wiener_big(FastArgs a) {
         VY o[I];
 #pragma unroll
         for (int e = 0; e < FU; ++e) {
-          const bool valid = k * FU + e < a.N;
+          const bool valid = k * FU + e < Np;
           cpx<T> z[I];
 #pragma unroll
           for (int i = 0; i < I; ++i) z[i] = cscale(yt[e][i], vframe(vu[j], e) * sLam[j][i] * rs[e][i]);
@@ -461,7 +466,7 @@ __global__ void __launch_bounds__(kBlock) k_wiener_big(FastArgs a) {
           }
         }
 #pragma unroll
-        for (int r = 0; r < I; ++r) out[(((size_t)j * I + r) * pt.F + f) * row + k] = o[r];
+        for (int r = 0; r < I; ++r) out[(j * I + r) * rstr + k] = o[r];
       }
     }
     u += k1 - k0;

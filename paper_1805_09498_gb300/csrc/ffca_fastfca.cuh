@@ -460,18 +460,27 @@ __global__ void __launch_bounds__(kBlock) k_wiener(FastArgs a) {
   __shared__ double sLam[J][I];
 
   const Partition pt = a.part;
-  const long long total = (long long)pt.F * pt.Uf;
-  const long long u0 = (long long)blockIdx.x * pt.upb;
-  const long long u1 = min(u0 + pt.upb, total);
+  const long long u0 = pt.block_start(blockIdx.x);
+  const long long u1 = pt.block_start(blockIdx.x + 1);
   const long long row = a.ld / FU;
-  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
-  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
-  VY* __restrict__ out = reinterpret_cast<VY*>(a.out);
 
+  // the block's unit range, problem by problem (a problem's units cover all
+  // ld_m frames of its rows, padding included)
   for (long long u = u0; u < u1;) {
-    const int f = (int)(u / pt.Uf);
-    const int k0 = (int)(u - (long long)f * pt.Uf);
-    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+    const int f = pt.problem_of(u);
+    const long long us = pt.start(f);
+    const int k0 = (int)(u - us);
+    const int k1 = (int)(min(pt.start(f + 1), u1) - us);
+    const int Np = pt.frames(f);
+    const long long rlen = pt.row_len(f, row * FU) / FU;  // units per row of the problem's blocks
+    const long long off = pt.frame_off(f) / FU;
+    const long long r0 = (long long)pt.freq(f) * rlen;
+    // rows: mic m at I Fm off + m Fm rlen + r0, source j at J Fm off + j Fm rlen + r0,
+    // output (j, r) at J I Fm off + (j I + r) Fm rlen + r0
+    const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y) + (size_t)I * pt.Fm * off + r0;
+    const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v) + (size_t)J * pt.Fm * off + r0;
+    VY* __restrict__ out = reinterpret_cast<VY*>(a.out) + (size_t)J * I * pt.Fm * off + r0;
+    const size_t rstr = (size_t)pt.Fm * rlen;  // stride between the problem's rows
     __syncthreads();
     if (threadIdx.x < I * I) {
       const int r = threadIdx.x / I, c = threadIdx.x % I;
@@ -500,13 +509,13 @@ __global__ void __launch_bounds__(kBlock) k_wiener(FastArgs a) {
       VY yu[I];
       VV vu[J];
 #pragma unroll
-      for (int m = 0; m < I; ++m) yu[m] = y[((size_t)m * pt.F + f) * row + k];
+      for (int m = 0; m < I; ++m) yu[m] = y[m * rstr + k];
 #pragma unroll
-      for (int j = 0; j < J; ++j) vu[j] = v[((size_t)j * pt.F + f) * row + k];
+      for (int j = 0; j < J; ++j) vu[j] = v[j * rstr + k];
       VY o[J][I];
 #pragma unroll
       for (int e = 0; e < FU; ++e) {
-        const bool valid = k * FU + e < a.N;
+        const bool valid = k * FU + e < Np;
         cpx<T> yt[I];
 #pragma unroll
         for (int i = 0; i < I; ++i) {
@@ -540,7 +549,7 @@ __global__ void __launch_bounds__(kBlock) k_wiener(FastArgs a) {
 #pragma unroll
       for (int j = 0; j < J; ++j)
 #pragma unroll
-        for (int r = 0; r < I; ++r) out[(((size_t)j * I + r) * pt.F + f) * row + k] = o[j][r];
+        for (int r = 0; r < I; ++r) out[(j * I + r) * rstr + k] = o[j][r];
     }
     u += k1 - k0;
   }

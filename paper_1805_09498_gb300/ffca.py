@@ -631,6 +631,16 @@ class FastFCABatch:
         """L2 of every mixture (host array of M values)."""
         return ffca_batch_loglik(self.ctx, self.M)
 
+    def wiener(self, out=None):
+        """Multichannel Wiener filter of every mixture: flat [J I F ld] of y's
+        dtype, mixture m's block [J, I, F, ld_m] at element J I F offsets[m]
+        (batch_views(out, J * I, F, offsets) gives the blocks)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.J * self.I * self.F * self.ld, dtype=self.y.dtype, device=self.y.device)
+        ffca_wiener(self.ctx, out.data_ptr())
+        return out
+
     def autotune(self, rounds: int = 1):
         """Pick the fastest work partition of each pass on real iterations
         (rounds x ffca_batch_config_count() of them, advancing the estimate)."""

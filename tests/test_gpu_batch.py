@@ -171,9 +171,11 @@ def test_invalid_batches_are_rejected():
     with pytest.raises(ffca.FFCAError):
         ffca.FastFCABatch(y, v, lam, P, [13, 20], offsets=off)  # mixture 0 overruns its rows
     est = ffca.FastFCABatch(y, v, lam, P, Ns)
-    out = torch.empty((2, 2, 3, int(off[-1])), dtype=y.dtype, device=y.device)
-    with pytest.raises(ffca.FFCAError) as ei:
-        ffca.ffca_wiener(est.ctx, out.data_ptr())
+    dv = torch.zeros_like(v)
+    dl = torch.empty_like(lam)
+    dP = torch.empty_like(P)
+    with pytest.raises(ffca.FFCAError) as ei:  # gradients: single-mixture contexts only
+        ffca.ffca_nll_grad(est.ctx, dv.data_ptr(), dl.data_ptr(), dP.data_ptr())
     assert ei.value.status == 7
     est.close()
 
@@ -229,3 +231,32 @@ def test_fixed_config_is_reproducible():
             est.close()
     a, b = outs[3]
     assert all(np.array_equal(x, z) for x, z in zip(a, b))
+
+
+@pytest.mark.parametrize("prec,I", [("mixed", 3), ("fp64", 3), ("mixed", 4), ("mixed", 8)])
+def test_batch_wiener_matches_oracle(prec, I):
+    """The Wiener filter of a batch context (Eq. MMSE0 per mixture): each
+    mixture's block equals the oracle's filter of that mixture after the same
+    iterations, the images sum to the mixture, and padding frames are zero."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    J = 6 if I == 8 else 3
+    kw = dict(alpha=0.2, kappa=50.0) if I == 8 else {}
+    probs = make_batch(I, J, 4, [37, 203, 8, 130], seed=12, **kw)
+    y, v, lam, P, Ns, off = ffca.batch_to_device([p.y for p in probs], [p.v0 for p in probs],
+                                                 [p.lam0 for p in probs], [p.P0 for p in probs],
+                                                 prec=prec)
+    est = ffca.FastFCABatch(y, v, lam, P, Ns)
+    est.iterate(2, trace=False)
+    out = est.wiener()
+    torch.cuda.synchronize()
+    tol = TOL[prec]["par"]
+    vh = ffca.batch_views(v.double().cpu(), J, 4, off)
+    for m, (p, blk) in enumerate(zip(probs, ffca.batch_views(out.cpu(), J * I, 4, off))):
+        n = int(Ns[m])
+        xh = blk.view(J, I, 4, -1).numpy()
+        ref = ffa.wiener(p.y, vh[m][:, :, :n].numpy(), lam[m].cpu().numpy(), P[m].cpu().numpy())
+        assert per_f_relerr(xh[..., :n], ref, 2) <= tol, m
+        assert per_f_relerr(xh[..., :n].sum(axis=0), p.y, 1) <= tol, m
+        assert np.all(xh[..., n:] == 0), m
+    est.close()
