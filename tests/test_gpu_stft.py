@@ -101,3 +101,36 @@ def test_bad_arguments_are_rejected():
     assert L.ffca_stft(x.data_ptr(), 1, so.L, out.data_ptr() + 8, 4, s) == 1   # misaligned output
     assert L.ffca_stft(x.data_ptr(), 1, so.L - 1, out.data_ptr(), 4, s) == 0   # no frame: no-op
     assert L.ffca_istft(out.data_ptr(), 1, 5, 4, x.data_ptr(), s) == 1         # ld < N
+
+
+def test_time_domain_pipeline():
+    """Time-domain mixture -> STFT -> FastFCA-AS iterations -> Wiener filter ->
+    overlap-add: the separated images of the J sources sum back to the
+    mixture on the samples two frames cover (the Wiener gains sum to one per
+    point, Eq. MMSE0)."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    from paper_1805_09498_gb300.synth import make_problem
+    I, J, F, N = 3, 3, so.F, 64
+    p = make_problem(I, J, F, N, seed=21)
+    # a consistent mixture: the time signal of the model's mixture spectra
+    xt = so.istft(p.y)                                     # [I, (N+1) H]
+    xd = torch.from_numpy(xt.astype(np.float32)).cuda()
+    Y, Ng = ffca.stft(xd)                                  # [I, F, ld] c64, Ng = N
+    assert Ng == N
+    v = torch.ones((J, F, Y.shape[2]), dtype=torch.float32, device="cuda")
+    v[:, :, :N] = torch.from_numpy(p.v0.astype(np.float32)).cuda()
+    lam = torch.from_numpy(p.lam0).cuda()
+    P = torch.from_numpy(p.P0).cuda()
+    est = ffca.FastFCA(Y, v, lam, P, N=N)
+    tr = est.iterate(5)
+    X = est.wiener()                                       # [J, I, F, ld]
+    imgs = ffca.istft(X.view(J * I, F, -1).contiguous(), N)  # [J I, (N+1) H]
+    torch.cuda.synchronize()
+    est.close()
+    assert np.all(np.isfinite(tr))
+    s = imgs.view(J, I, -1).sum(dim=0).cpu().numpy()
+    mix = ffca.istft(Y, N).cpu().numpy()
+    lo, hi = so.H, N * so.H
+    err = np.linalg.norm(s[:, lo:hi] - mix[:, lo:hi], axis=1) / np.linalg.norm(mix[:, lo:hi], axis=1)
+    assert float(err.max()) <= TOL
