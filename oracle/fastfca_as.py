@@ -125,6 +125,42 @@ def grad_P_conj(y, v, lam, P):
     return N * (PinvH - VP)
 
 
+# ------------------------------------ alternative updates of P (Sec. 4.6) ----
+# Sec. 4.6 names the gradient and natural gradient methods as replacements of
+# the fixed-point iteration without stating them.  Readings: both ascend L2
+# (Eq. L2) with the V_i of Eq. FPI held fixed (sigma from the new v and
+# Lambda, as for the fixed point), take K steps of a caller-chosen size mu
+# per iteration, and scale Eq. partialP by 1/N so that mu does not depend on
+# the number of frames.
+def gradient_P(P, V, mu, K=1, counter=COUNTER):
+    """K steps of gradient ascent on L2 along Eq. partialP:
+    P <- P + mu (P^{-H} - [V_1 p_1, ..., V_I p_I]) = P + (mu / N) dL2/dP^*.
+    One matrix inversion (P^{-H}) per frequency per step."""
+    F = P.shape[0]
+    P = P.copy()
+    for _ in range(K):
+        PinvH = np.linalg.inv(P).conj().transpose(0, 2, 1)
+        counter.inversions += F
+        VP = np.einsum("fiab,fbi->fai", V, P)     # column i: V_i p_i
+        P = P + mu * (PinvH - VP)
+    return P
+
+
+def natural_gradient_P(P, V, mu, K=1):
+    """K steps of the natural (relative) gradient method.  With the
+    demixing matrix W = P^H (y~ = W y, Eq. mutilde0) and
+    C = (1/N) sum_n D^{-1} y~ y~^H, i.e. C_ik = p_i^H V_i p_k, the step is
+    W <- W + mu (I - C) W, so P <- P + mu P (I - C)^H.  It equals
+    P + (mu / N) P P^H dL2/dP^* and needs no matrix inversion."""
+    F, I, _ = P.shape
+    P = P.copy()
+    eye = np.eye(I)[None]
+    for _ in range(K):
+        C = np.einsum("fai,fiab,fbk->fik", P.conj(), V, P)
+        P = P + mu * (P @ (eye - C).conj().transpose(0, 2, 1))
+    return P
+
+
 # --------------------------------------------------------- log-likelihood ----
 def loglik_terms(y, v, lam, P):
     """Per-(n,f) value of ln N(y; 0, P^{-H} D P^{-1}) in Eq. L2, D = sum_j v_j Lambda_j.
@@ -158,23 +194,32 @@ def em_half(y, v, lam, P):
     return v_new, lam_new
 
 
-def hybrid_iteration(y, v, lam, P, K=1, counter=COUNTER):
+def hybrid_iteration(y, v, lam, P, K=1, counter=COUNTER, p_update="fpi", mu=0.0):
     """One iteration of the hybrid algorithm (Sec. 4.4): the EM half, then the
-    fixed-point update of P (Eq. FPI, K sweeps) with the new v and Lambda."""
+    update of P with the new v and Lambda: the fixed-point iteration (Eq. FPI,
+    K sweeps) or, with p_update = "gradient" / "natural_gradient", K steps of
+    size mu of one of the alternatives named in Sec. 4.6."""
     v, lam = em_half(y, v, lam, P)
     V = weighted_covariances(y, v, lam)
-    P = fixed_point_P(P, V, K, counter)
+    if p_update == "fpi":
+        P = fixed_point_P(P, V, K, counter)
+    elif p_update == "gradient":
+        P = gradient_P(P, V, mu, K, counter)
+    elif p_update == "natural_gradient":
+        P = natural_gradient_P(P, V, mu, K)
+    else:
+        raise ValueError(p_update)
     return v, lam, P
 
 
-def iterate(y, v, lam, P, iters, K=1, counter=COUNTER):
+def iterate(y, v, lam, P, iters, K=1, counter=COUNTER, p_update="fpi", mu=0.0):
     """Run `iters` hybrid iterations.  Returns (v, lam, P, trace) where
     trace[t] is L2 of the state entering iteration t and trace[iters] is L2
     of the final state (length iters + 1)."""
     trace = []
     for _ in range(iters):
         trace.append(loglik(y, v, lam, P))
-        v, lam, P = hybrid_iteration(y, v, lam, P, K, counter)
+        v, lam, P = hybrid_iteration(y, v, lam, P, K, counter, p_update, mu)
     trace.append(loglik(y, v, lam, P))
     return v, lam, P, np.array(trace)
 
