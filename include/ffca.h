@@ -132,9 +132,34 @@ ffca_status ffca_sync(ffca_ctx* ctx);
  * index is that of the problem, m F + f. */
 int ffca_error_frequency(const ffca_ctx* ctx);
 
-/* Number of per-frequency I x I inversions the fixed-point update has
- * performed since ffca_init ((I+1) F K per iteration, Sec. 4.5).  Syncs. */
+/* Number of per-frequency I x I inversions the update of P has performed
+ * since ffca_init ((I+1) F K per iteration for the fixed point, Sec. 4.5;
+ * see ffca_set_p_update for the others).  Syncs. */
 ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
+
+/* Update of P in each hybrid iteration.  FFCA_P_FIXED_POINT (the default)
+ * is Eq. FPI.  The other two are alternatives the paper names without
+ * stating them (Sec. 4.6), read as K ascent steps on L2 of step size mu with
+ * the V_i of Eq. FPI held fixed, along G / N for G = dL2/dP^* (Eq. partialP):
+ *   FFCA_P_GRADIENT          p_i <- p_i + mu ([P^{-H}]_i - V_i p_i)
+ *   FFCA_P_NATURAL_GRADIENT  p_i <- p_i + mu (p_i - P P^H V_i p_i)
+ * The natural (relative) gradient is P P^H G / N; it inverts no matrix and
+ * is equivariant under a change of microphone basis.  The gradient method
+ * inverts P once per step.  ffca_inversion_count counts F K per iteration
+ * for the gradient and nothing for the natural gradient.  Neither method
+ * guarantees an increase of L2 for a large mu: the trace monitors it. */
+typedef enum {
+  FFCA_P_FIXED_POINT = 0,
+  FFCA_P_GRADIENT = 1,
+  FFCA_P_NATURAL_GRADIENT = 2
+} ffca_p_update;
+
+/* Select the update of P for later iterations of a single or batch context.
+ * mu: step size, finite and > 0 for the gradient methods (ignored for the
+ * fixed point).  Drops a captured graph.  FFCA_ERR_ARG for an unknown method
+ * or an invalid mu (the context keeps its previous choice).  The
+ * allocation-free call always uses the fixed point. */
+ffca_status ffca_set_p_update(ffca_ctx* ctx, int method, double mu);
 
 /* Host-buffer transfers for callers whose data live in host memory: copy
  * y, v, lambda and P (same layouts as the device arrays; any may be NULL to

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstdio>
@@ -233,6 +234,9 @@ struct ffca_ctx {
   unsigned* gcntB;
   unsigned long long* ops;
   int err_f;
+  // update of P (kPFixedPoint unless ffca_set_p_update chose a gradient method) and its step size
+  int pmode;
+  double mu;
   // profiling
   int timing;
   unsigned long long launches[FFCA_KERNEL_KINDS];
@@ -264,6 +268,8 @@ FastArgs base_args(const ffca_ctx* c) {
   a.tabA = c->ws + c->plan.off_tabA;
   a.tabB = c->ws + c->plan.off_tabB;
   a.inv_n = 1.0 / c->d.N;
+  a.pmode = c->pmode;
+  a.mu = c->mu;
   return a;
 }
 
@@ -329,6 +335,11 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
 
+// The P step of the context's update of P.
+const void* p_step_kernel(const ffca_ctx* c) {
+  return c->pmode == kPFixedPoint ? c->kern->psolve : c->kern->pgrad;
+}
+
 int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
 
 // CTAs of a streaming pass: each runs stream_groups virtual blocks of the partition.
@@ -378,7 +389,7 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
     const int G = 32 / c->d.I;  // problems per warp
-    if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
+    if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
   }
   return FFCA_OK;
 }
@@ -567,7 +578,7 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       const int G = 32 / c->d.I;  // frequencies per warp
-      if ((st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK)
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
@@ -1099,7 +1110,7 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
       cudaEventRecord(ev[q][2], c->stream);
       const int G = 32 / c->d.I;
       if (st == FFCA_OK)
-        st = launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve, (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem);
+        st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem);
     }
     if (st == FFCA_OK && !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) st = FFCA_ERR_CUDA;
     for (int q = 0; q < kCands && st == FFCA_OK; ++q) {
@@ -1129,6 +1140,24 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
 }
 
 void ffca_batch_destroy(ffca_batch_ctx* c) { ffca_destroy(c); }
+
+static_assert(FFCA_P_FIXED_POINT == kPFixedPoint && FFCA_P_GRADIENT == kPGradient &&
+                  FFCA_P_NATURAL_GRADIENT == kPNatural,
+              "the ABI's P-update codes are the kernels' modes");
+
+ffca_status ffca_set_p_update(ffca_ctx* c, int method, double mu) {
+  if (!c) return FFCA_ERR_ARG;
+  if (method != FFCA_P_FIXED_POINT && method != FFCA_P_GRADIENT && method != FFCA_P_NATURAL_GRADIENT)
+    return FFCA_ERR_ARG;
+  if (method != FFCA_P_FIXED_POINT && !(std::isfinite(mu) && mu > 0.0)) return FFCA_ERR_ARG;
+  c->pmode = method;
+  c->mu = method == FFCA_P_FIXED_POINT ? 0.0 : mu;
+  if (c->graph) {  // the captured launches hold the previous arguments
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return FFCA_OK;
+}
 
 ffca_status ffca_set_graph(ffca_ctx* c, int enable) {
   if (!c) return FFCA_ERR_ARG;

@@ -224,7 +224,69 @@ __device__ double pinvh_from_columns(cpx<double> (&x)[I], cpx<double>* M, int g,
   return det2;
 }
 
-template <typename T, int I, int J>
+// The gradient updates of P (Sec. 4.6) for lane (g, i): on entry dv and lo
+// hold V_i (real diagonal, strictly lower entries V_rc, r > c) and x column
+// i of P^{-H} of the current P; on return x holds column i of the new P.
+// K steps with V_i fixed; the natural gradient forms P (P^H w) one column of
+// P at a time, broadcast from its lane.
+template <int I>
+__device__ void gradient_steps(const FastArgs& a, int f, const double (&dv)[I],
+                               const cpx<double> (&lo)[I * (I - 1) / 2], cpx<double> (&x)[I],
+                               cpx<double>* M, int g, int i, bool& singular) {
+  cpx<double> p[I];  // column i of the current P
+#pragma unroll
+  for (int r = 0; r < I; ++r) {
+    const double2 q = __ldcg(reinterpret_cast<const double2*>(a.P) + (size_t)f * I * I + r * I + i);
+    p[r] = mk(q.x, q.y);
+  }
+  for (int step = 0; step < a.K; ++step) {
+    cpx<double> w[I];  // V_i p_i
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      cpx<double> s = mk(dv[r] * p[r].re, dv[r] * p[r].im);
+#pragma unroll
+      for (int c = 0; c < I; ++c) {
+        if (c < r) cfma(s, lo[lo_index(r, c)], p[c]);
+        if (c > r) cfmac(s, lo[lo_index(c, r)], p[c]);  // V_rc = conj(V_cr)
+      }
+      w[r] = s;
+    }
+    if (a.pmode == kPGradient) {
+      if (step > 0) {  // P^{-H} of the intermediate P
+#pragma unroll
+        for (int r = 0; r < I; ++r) x[r] = p[r];
+        pinvh_from_columns<I>(x, M, g, i, singular);
+      }
+#pragma unroll
+      for (int r = 0; r < I; ++r)
+        p[r] = mk(p[r].re + a.mu * (x[r].re - w[r].re), p[r].im + a.mu * (x[r].im - w[r].im));
+    } else {
+      cpx<double> u[I];  // P (P^H w)
+#pragma unroll
+      for (int r = 0; r < I; ++r) u[r] = mk(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < I; ++k) {
+        cpx<double> pk[I];
+#pragma unroll
+        for (int r = 0; r < I; ++r) pk[r] = shfl_c(p[r], g * I + k);
+        cpx<double> ck = mk(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < I; ++r) cfmac(ck, pk[r], w[r]);  // p_k^H w
+#pragma unroll
+        for (int r = 0; r < I; ++r) cfma(u[r], pk[r], ck);
+      }
+#pragma unroll
+      for (int r = 0; r < I; ++r)
+        p[r] = mk(p[r].re + a.mu * (p[r].re - u[r].re), p[r].im + a.mu * (p[r].im - u[r].im));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < I; ++r) x[r] = p[r];
+}
+
+// GRAD selects the gradient updates (a separate kernel, so that the
+// fixed-point one keeps its registers).
+template <typename T, int I, int J, bool GRAD = false>
 __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
   using BL = BigLane<I>;
   constexpr int G = BL::G;
@@ -310,18 +372,22 @@ __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
         m += 2;
       }
   }
-  double d0[I];
+  bool singular = false;
+  if constexpr (GRAD) {
+    gradient_steps<I>(a, f, dv, lo, x, M, g, i, singular);
+  } else {
+    double d0[I];
 #pragma unroll
-  for (int r = 0; r < I; ++r) d0[r] = dv[r];
-  bool singular = !ldl_factor<I>(dv, lo, rd);
+    for (int r = 0; r < I; ++r) d0[r] = dv[r];
+    singular = !ldl_factor<I>(dv, lo, rd);
 #pragma unroll
-  for (int r = 0; r < I; ++r) singular |= !(dv[r] > kCholRtol * d0[r]);  // dv holds the pivots D
-
-  double det2 = 0.0;
-  for (int sweep = 0; sweep < a.K; ++sweep) {
-    ldl_solve<I>(lo, rd, x);  // p_i = V_i^{-1} [P^{-H}]_i
-    if (sweep + 1 < a.K) pinvh_from_columns<I>(x, M, g, i, singular);  // P^{-H} of the intermediate P
+    for (int r = 0; r < I; ++r) singular |= !(dv[r] > kCholRtol * d0[r]);  // dv holds the pivots D
+    for (int sweep = 0; sweep < a.K; ++sweep) {
+      ldl_solve<I>(lo, rd, x);  // p_i = V_i^{-1} [P^{-H}]_i
+      if (sweep + 1 < a.K) pinvh_from_columns<I>(x, M, g, i, singular);  // P^{-H} of the intermediate P
+    }
   }
+  double det2 = 0.0;
   if (active) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
@@ -338,7 +404,7 @@ __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
       reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(x[r].re, x[r].im);
     if (singular) raise_status(a.status, kDevSingular, f);
     if (i == 0) {
-      atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
+      atomicAdd(a.ops, p_update_inversions(a, I));
       a.logdet[f] = log(det2);
     }
   }

@@ -18,6 +18,7 @@ struct FastKernels {
   int params_b_bytes;        // bytes per frequency of the pass-B parameter table
   int solve_smem;            // dynamic shared memory of psolve and prep
   int pinv_step;             // 1: the P step starts from P^{-H} (prep computes it) and leaves the next one
+  const void* pgrad;         // the P step with the gradient updates in place of the fixed point
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

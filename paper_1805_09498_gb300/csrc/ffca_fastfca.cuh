@@ -44,7 +44,26 @@ struct FastArgs {
   double* lam_next;          // [F][J][I] the new Lambda, written during pass B, committed by k_psolve
   Partition prev_part;       // pass B reads pass A's slots: their partition
   const double* prev_buf;    // and buffer
+  int pmode;                 // update of P: kPFixedPoint, kPGradient or kPNatural
+  double mu;                 // step size of the gradient updates
 };
+
+// Updates of P: the fixed-point iteration (Eq. FPI), or K ascent steps on L2
+// with the V_i of Eq. FPI held fixed (the alternatives of Sec. 4.6), of size
+// mu along G / N, G = dL2/dP^* of Eq. partialP:
+//   gradient  p_i <- p_i + mu ([P^{-H}]_i - V_i p_i)
+//   natural   p_i <- p_i + mu (p_i - P P^H V_i p_i)   (P P^H G / N)
+constexpr int kPFixedPoint = 0;
+constexpr int kPGradient = 1;
+constexpr int kPNatural = 2;
+
+// Matrix inversions per problem of one P update: (I+1) K for the fixed
+// point (Sec. 4.5), one P^{-H} per gradient step, none for the natural
+// gradient.
+__device__ inline unsigned long long p_update_inversions(const FastArgs& a, int I) {
+  return a.pmode == kPFixedPoint ? (unsigned long long)(I + 1) * a.K
+                                 : (a.pmode == kPGradient ? (unsigned long long)a.K : 0ull);
+}
 
 // Per-frequency parameters in the per-point precision T, laid out as they
 // travel to the streaming kernels (one bulk copy per tile, 16-byte padded).
@@ -295,7 +314,9 @@ __device__ inline void gather_columns(const cpx<double> (&col)[I], int g, cpx<do
 // (independent, shallow products; 4 x 4 through shared 2 x 2 minors) with one
 // division per sweep, register-only indexing.  It ends with ln|det P|^2 of
 // the new P, which the next iteration's L2 needs (Eq. L2).
-template <typename T, int I, int J>
+// GRAD selects the gradient updates (a separate kernel, so that the
+// fixed-point one keeps its registers).
+template <typename T, int I, int J, bool GRAD = false>
 __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
   constexpr int G = Lanes<I>::G;
   constexpr int NV = I * I * I;
@@ -345,44 +366,98 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
     for (int c = 0; c < I; ++c)
       A[r][c] = mk(a.P[((size_t)f * I * I + r * I + c) * 2], a.P[((size_t)f * I * I + r * I + c) * 2 + 1]);
 
-  // V_i^{-1} = adj(V_i) / det V_i with adj(V) = C_V^T (cofactors, once per
-  // iteration), so that one division per sweep remains on the critical path:
-  //   p_i = V_i^{-1} [P^{-H}]_i = adj(V_i) conj(C_P[., i]) / (det V_i conj(det P))
-  // since [P^{-H}]_{r i} = conj((P^{-1})_{i r}) = conj(C_P[r][i]) / conj(det P).
-  cpx<double> CV[I][I];
-  const double detV = cofactors<I>(V, CV).re;  // real for Hermitian V
-  double diagprod = 1.0;
+  bool singular = false;
+  if constexpr (GRAD) {
+    // the gradient steps: V_i is multiplied, not inverted
+    for (int sweep = 0; sweep < a.K; ++sweep) {
+      cpx<double> p[I], w[I], col[I];
 #pragma unroll
-  for (int r = 0; r < I; ++r) diagprod *= V[r][r].re;
-  // Hadamard: 0 < det V <= prod V_rr for positive definite V; a ratio at
-  // rounding level means rank deficiency
-  bool singular = !(detV > kCholRtol * diagprod) || !isfinite(detV);
-  for (int sweep = 0; sweep < a.K; ++sweep) {
-    cpx<double> C[I][I];
-    const cpx<double> detP = cofactors<I>(A, C);
-    cpx<double> num[I];
-#pragma unroll
-    for (int r = 0; r < I; ++r) {
-      cpx<double> s = mk(0.0, 0.0);
-#pragma unroll
-      for (int q = 0; q < I; ++q) {
-        cpx<double> cqi = C[q][0];  // column i of C_P, selected by predicate
+      for (int r = 0; r < I; ++r) {
+        p[r] = A[r][0];
 #pragma unroll
         for (int c = 1; c < I; ++c)
-          if (c == i) cqi = C[q][c];
-        cfma(s, CV[q][r], cconj(cqi));  // adj(V)_{rq} = CV_{qr}
+          if (c == i) p[r] = A[r][c];
       }
-      num[r] = s;
-    }
-    const cpx<double> den = mk(detV * detP.re, -detV * detP.im);  // det V conj(det P)
-    const double d2 = cabs2(den);
-    singular |= !(cabs2(detP) > 0.0) || !isfinite(d2);
-    const double inv = 1.0 / d2;
-    const cpx<double> rden = mk(den.re * inv, -den.im * inv);
-    cpx<double> col[I];
 #pragma unroll
-    for (int r = 0; r < I; ++r) col[r] = cmul(num[r], rden);
-    gather_columns<I>(col, g, A);
+      for (int r = 0; r < I; ++r) {  // w = V_i p_i
+        w[r] = mk(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < I; ++c) cfma(w[r], V[r][c], p[c]);
+      }
+      if (a.pmode == kPGradient) {  // [P^{-H}]_{ri} = conj(C_P[r][i] / det P)
+        cpx<double> C[I][I];
+        const cpx<double> detP = cofactors<I>(A, C);
+        const double d2 = cabs2(detP);
+        singular |= !(d2 > 0.0) || !isfinite(d2);
+        const double inv = 1.0 / d2;
+        const cpx<double> rdet = mk(detP.re * inv, -detP.im * inv);
+#pragma unroll
+        for (int r = 0; r < I; ++r) {
+          cpx<double> cri = C[r][0];
+#pragma unroll
+          for (int c = 1; c < I; ++c)
+            if (c == i) cri = C[r][c];
+          const cpx<double> x = cconj(cmul(cri, rdet));
+          col[r] = mk(p[r].re + a.mu * (x.re - w[r].re), p[r].im + a.mu * (x.im - w[r].im));
+        }
+      } else {  // natural: P (P^H w) with column k of P in A[., k]
+        cpx<double> u[I];
+#pragma unroll
+        for (int r = 0; r < I; ++r) u[r] = mk(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+          cpx<double> ck = mk(0.0, 0.0);
+#pragma unroll
+          for (int q = 0; q < I; ++q) cfma(ck, cconj(A[q][k]), w[q]);
+#pragma unroll
+          for (int r = 0; r < I; ++r) cfma(u[r], A[r][k], ck);
+        }
+#pragma unroll
+        for (int r = 0; r < I; ++r)
+          col[r] = mk(p[r].re + a.mu * (p[r].re - u[r].re), p[r].im + a.mu * (p[r].im - u[r].im));
+      }
+      gather_columns<I>(col, g, A);
+    }
+  } else {
+    // V_i^{-1} = adj(V_i) / det V_i with adj(V) = C_V^T (cofactors, once per
+    // iteration), so that one division per sweep remains on the critical path:
+    //   p_i = V_i^{-1} [P^{-H}]_i = adj(V_i) conj(C_P[., i]) / (det V_i conj(det P))
+    // since [P^{-H}]_{r i} = conj((P^{-1})_{i r}) = conj(C_P[r][i]) / conj(det P).
+    cpx<double> CV[I][I];
+    const double detV = cofactors<I>(V, CV).re;  // real for Hermitian V
+    double diagprod = 1.0;
+#pragma unroll
+    for (int r = 0; r < I; ++r) diagprod *= V[r][r].re;
+    // Hadamard: 0 < det V <= prod V_rr for positive definite V; a ratio at
+    // rounding level means rank deficiency
+    singular = !(detV > kCholRtol * diagprod) || !isfinite(detV);
+    for (int sweep = 0; sweep < a.K; ++sweep) {
+      cpx<double> C[I][I];
+      const cpx<double> detP = cofactors<I>(A, C);
+      cpx<double> num[I];
+#pragma unroll
+      for (int r = 0; r < I; ++r) {
+        cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < I; ++q) {
+          cpx<double> cqi = C[q][0];  // column i of C_P, selected by predicate
+#pragma unroll
+          for (int c = 1; c < I; ++c)
+            if (c == i) cqi = C[q][c];
+          cfma(s, CV[q][r], cconj(cqi));  // adj(V)_{rq} = CV_{qr}
+        }
+        num[r] = s;
+      }
+      const cpx<double> den = mk(detV * detP.re, -detV * detP.im);  // det V conj(det P)
+      const double d2 = cabs2(den);
+      singular |= !(cabs2(detP) > 0.0) || !isfinite(d2);
+      const double inv = 1.0 / d2;
+      const cpx<double> rden = mk(den.re * inv, -den.im * inv);
+      cpx<double> col[I];
+#pragma unroll
+      for (int r = 0; r < I; ++r) col[r] = cmul(num[r], rden);
+      gather_columns<I>(col, g, A);
+    }
   }
   if (active) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
@@ -398,7 +473,7 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
     }
     if (singular) raise_status(a.status, kDevSingular, f);
     if (i == 0) {
-      atomicAdd(a.ops, (unsigned long long)(I + 1) * a.K);
+      atomicAdd(a.ops, p_update_inversions(a, I));
       const double d2 = cabs2(determinant<I>(A));
       if (!(d2 > 0.0) || !isfinite(d2)) raise_status(a.status, kDevSingular, f);
       a.logdet[f] = log(d2);

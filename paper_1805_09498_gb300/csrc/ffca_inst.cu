@@ -39,13 +39,16 @@ static const FastKernels* table_entry() {
   constexpr bool BIG = FFCA_I > 4;            // per-point parameters read from the stage, per-source Wiener
   constexpr bool LDL = FFCA_I >= FFCA_LDL_MIN_I;
   const void* psolve;
+  const void* pgrad;
   const void* prep;
   const void* wiener;
   if constexpr (LDL) {
     psolve = (const void*)k_psolve_ldl<Real, FFCA_I, J>;
+    pgrad = (const void*)k_psolve_ldl<Real, FFCA_I, J, true>;
     prep = (const void*)k_prep_gj<Real, FFCA_I, J>;
   } else {
     psolve = (const void*)k_psolve<Real, FFCA_I, J>;
+    pgrad = (const void*)k_psolve<Real, FFCA_I, J, true>;
     prep = (const void*)k_prep<Real, FFCA_I, J>;
   }
   if constexpr (BIG) wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
@@ -64,6 +67,7 @@ static const FastKernels* table_entry() {
       ParamsB<Real, FFCA_I, J>::BYTES,
       LDL ? BigLane<FFCA_I>::SMEM : 0,
       LDL ? 1 : 0,
+      pgrad,
   };
   return &k;
 }

@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         "ffca_batch_iterate": (ci, [vp, ci, dp]),
         "ffca_batch_loglik": (ci, [vp, dp]),
         "ffca_set_graph": (ci, [vp, ci]),
+        "ffca_set_p_update": (ci, [vp, ci, ctypes.c_double]),
         "ffca_batch_config_count": (ci, []),
         "ffca_batch_autotune": (ci, [vp, ci, P(ci), P(ci), dp, dp]),
         "ffca_batch_set_config": (ci, [vp, ci, ci]),
@@ -391,6 +392,17 @@ def ffca_set_graph(ctx, enable: bool) -> None:
     _check(ctx, lib().ffca_set_graph(ctx, 1 if enable else 0), "ffca_set_graph")
 
 
+# Updates of P (ffca_p_update): the fixed point of Eq. FPI, or the gradient
+# methods of Sec. 4.6 with step size mu.
+P_UPDATES = {"fixed_point": 0, "gradient": 1, "natural_gradient": 2}
+
+
+def ffca_set_p_update(ctx, method: str, mu: float = 0.0) -> None:
+    if method not in P_UPDATES:
+        raise ValueError(f"unknown update of P {method!r}; one of {sorted(P_UPDATES)}")
+    _check(ctx, lib().ffca_set_p_update(ctx, P_UPDATES[method], float(mu)), "ffca_set_p_update")
+
+
 def ffca_batch_destroy(ctx) -> None:
     lib().ffca_batch_destroy(ctx)
 
@@ -455,6 +467,11 @@ class FastFCA:
     def set_graph(self, enable: bool = True):
         """Replay trace-less iterate() calls from a CUDA graph."""
         ffca_set_graph(self.ctx, enable)
+
+    def set_p_update(self, method: str = "fixed_point", mu: float = 0.0):
+        """Update of P in later iterations: "fixed_point" (Eq. FPI),
+        "gradient" or "natural_gradient" (Sec. 4.6) with step size mu."""
+        ffca_set_p_update(self.ctx, method, mu)
 
     def loglik(self) -> float:
         return ffca_loglik(self.ctx)
@@ -626,6 +643,10 @@ class FastFCABatch:
 
     def iterate(self, iters: int, trace: bool = True):
         return ffca_batch_iterate(self.ctx, iters, trace)
+
+    def set_p_update(self, method: str = "fixed_point", mu: float = 0.0):
+        """Update of P in later iterations (as FastFCA.set_p_update)."""
+        ffca_set_p_update(self.ctx, method, mu)
 
     def loglik(self) -> np.ndarray:
         """L2 of every mixture (host array of M values)."""

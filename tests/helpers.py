@@ -14,8 +14,9 @@ def per_f_relerr(a, b, f_axis):
     return float(np.max(num / np.maximum(den, 1e-300))) if F else 0.0
 
 
-def run_gpu(y, v, lam, P, iters, prec, K=1, ld=None, pad_value=None):
-    """Run `iters` iterations through the C-ABI; returns (v, lam, P, trace) as numpy."""
+def run_gpu(y, v, lam, P, iters, prec, K=1, ld=None, pad_value=None, p_update=None, mu=0.0):
+    """Run `iters` iterations through the C-ABI; returns (v, lam, P, trace) as numpy.
+    p_update: None (the default fixed point) or a name of ffca.P_UPDATES."""
     import torch
     from paper_1805_09498_gb300 import ffca
     yd, vd, ld_, Pd, N = ffca.to_device(y, v, lam, P, prec=prec, ld=ld)
@@ -23,6 +24,8 @@ def run_gpu(y, v, lam, P, iters, prec, K=1, ld=None, pad_value=None):
         yd[:, :, N:] = pad_value
         vd[:, :, N:] = pad_value
     est = ffca.FastFCA(yd, vd, ld_, Pd, N=N, K=K)
+    if p_update is not None:
+        est.set_p_update(p_update, mu)
     tr = est.iterate(iters)
     torch.cuda.synchronize()
     out = (vd[:, :, :N].double().cpu().numpy(), ld_.cpu().numpy(), Pd.cpu().numpy(), tr)

@@ -58,3 +58,14 @@ def test_null_context_is_an_argument_error(L):
     assert L.ffca_wiener(None, None) == 1
     assert L.ffca_sync(None) == 1
     assert L.ffca_error_frequency(None) == -1
+    assert L.ffca_set_p_update(None, 0, 0.0) == 1
+
+
+def test_p_update_codes_match_the_header(L):
+    """The binding's names of the updates of P carry the header's codes."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(ffca.__file__), "..", "include", "ffca.h")).read()
+    codes = dict((m.group(1), int(m.group(2)))
+                 for m in re.finditer(r"FFCA_P_(\w+) = (\d+)", hdr))
+    assert codes == {k.upper(): v for k, v in ffca.P_UPDATES.items()}

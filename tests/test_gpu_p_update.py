@@ -1,0 +1,166 @@
+"""GPU parity of the alternative updates of P (Sec. 4.6: the gradient and
+natural gradient methods, ffca_set_p_update) against the FP64 oracle, for
+single mixtures at every compiled I, with K > 1 steps, on batches and under
+graph replay; the inversion counts and the argument checks.
+
+Tolerances as for the fixed point (normwise relative error per frequency,
+max over f): FP64 1e-9 on v, Lambda, P and L2; mixed 1e-4 on the
+parameters and 1e-5 nats per point on L2.
+"""
+import numpy as np
+import pytest
+
+from oracle import fastfca_as as ffa
+from oracle.fastfca_as import OpCounter
+from paper_1805_09498_gb300.synth import make_batch, make_problem
+
+from helpers import per_f_relerr, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(par=1e-9, ll_rel=1e-9), "mixed": dict(par=1e-4, ll_tf=1e-5)}
+STEP = {"gradient": 0.05, "natural_gradient": 0.2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1805_09498_gb300 import build
+    build.build()
+
+
+def _compare(prec, ref, got, N, F):
+    v_r, l_r, P_r, t_r = ref
+    v_g, l_g, P_g, t_g = got
+    e = dict(v=per_f_relerr(v_g, v_r, 1), lam=per_f_relerr(l_g, l_r, 0), P=per_f_relerr(P_g, P_r, 0))
+    for k, x in e.items():
+        assert x <= TOL[prec]["par"], (k, x, e)
+    if prec == "fp64":
+        assert np.all(np.abs(t_g - t_r) <= TOL[prec]["ll_rel"] * np.abs(t_r)), (t_g, t_r)
+    else:
+        assert np.all(np.abs(t_g - t_r) <= TOL[prec]["ll_tf"] * N * F), (t_g - t_r) / (N * F)
+
+
+SHAPES = [(1, 2, 3, 41), (2, 3, 4, 50), (3, 3, 5, 137), (4, 3, 3, 301), (3, 6, 2, 123), (8, 6, 3, 260)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("method", ["gradient", "natural_gradient"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_iterations_match_oracle(prec, method, shape):
+    """Three hybrid iterations with K = 1, from the perturbed truth."""
+    I, J, F, N = shape
+    p = make_problem(I, J, F, N, seed=200 + 10 * I + J)
+    mu = STEP[method]
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 3, counter=OpCounter(), p_update=method, mu=mu)
+    assert np.all(np.diff(ref[3]) > 0)  # an ascent at these step sizes
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 3, prec, p_update=method, mu=mu)
+    _compare(prec, ref, got, N, F)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("method", ["gradient", "natural_gradient"])
+@pytest.mark.parametrize("I", [2, 3, 8])
+def test_several_steps_per_iteration(prec, method, I):
+    """K = 3 steps per iteration with V_i fixed (the gradient method forms
+    P^{-H} of each intermediate P).  Smaller steps than above: at I = 8 three
+    gradient steps of 0.05 overshoot and L2 falls (-7.7e3 to -5.0e4 in two
+    iterations), a trajectory that amplifies the rounding of the mixed path."""
+    J = 3
+    p = make_problem(I, J, 4, 90, seed=300 + I)
+    mu = {"gradient": 0.02, "natural_gradient": 0.1}[method]
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, K=3, counter=OpCounter(), p_update=method, mu=mu)
+    assert np.all(np.diff(ref[3]) > 0)
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec, K=3, p_update=method, mu=mu)
+    _compare(prec, ref, got, 90, 4)
+
+
+@pytest.mark.parametrize("method,per_iter", [("gradient", lambda I, K: K), ("natural_gradient", lambda I, K: 0),
+                                             ("fixed_point", lambda I, K: (I + 1) * K)])
+@pytest.mark.parametrize("I", [2, 4])
+def test_inversion_counts(method, per_iter, I):
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(I, 2, 7, 40, seed=5)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N, K=2)
+    est.set_p_update(method, 0.1)
+    est.iterate(3, trace=False)
+    assert est.inversion_count() == 3 * 7 * per_iter(I, 2)
+    est.close()
+
+
+def test_argument_checks_keep_the_previous_update():
+    """An unknown method or a step size that is not finite and positive is
+    an argument error; the context keeps its update (here the natural
+    gradient chosen before)."""
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(3, 3, 4, 60, seed=9)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
+    est.set_p_update("natural_gradient", 0.2)
+    L = ffca.lib()
+    for method, mu in [(3, 0.1), (-1, 0.1), (1, 0.0), (2, -0.5), (1, float("nan")), (2, float("inf"))]:
+        assert L.ffca_set_p_update(est.ctx, method, mu) == 1
+    with pytest.raises(ValueError):
+        est.set_p_update("newton", 0.1)
+    tr = est.iterate(2)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter(), p_update="natural_gradient", mu=0.2)
+    got = (vd[:, :, :N].cpu().numpy(), ld_.cpu().numpy(), Pd.cpu().numpy(), tr)
+    _compare("fp64", ref, got, N, 4)
+    est.close()
+
+
+def test_switching_drops_the_captured_graph():
+    """Graph replays hold their launch arguments: after a change of the
+    update the next replay runs the new one.  Two iterations with the fixed
+    point (captured, replayed), then two with the gradient method."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(3, 3, 5, 80, seed=12)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
+    est.set_graph(True)
+    est.iterate(2, trace=False)
+    est.set_p_update("gradient", 0.05)
+    est.iterate(2, trace=False)
+    torch.cuda.synchronize()
+    v, lam, P, _ = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter())
+    ref = ffa.iterate(p.y, v, lam, P, 2, counter=OpCounter(), p_update="gradient", mu=0.05)
+    got = (vd[:, :, :N].cpu().numpy(), ld_.cpu().numpy(), Pd.cpu().numpy(), ref[3])
+    _compare("fp64", ref, got, N, 5)
+    est.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("I,J", [(4, 3), (2, 2), (8, 6)])
+def test_batch_natural_gradient_matches_oracle(prec, I, J):
+    """A ragged batch with the natural gradient, per mixture against the
+    oracle."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    Ns = [37, 200, 9, 129, 64]
+    probs = make_batch(I, J, 3, Ns, seed=70 + I)
+    mu = STEP["natural_gradient"]
+    refs = [ffa.iterate(q.y, q.v0, q.lam0, q.P0, 3, counter=OpCounter(), p_update="natural_gradient", mu=mu)
+            for q in probs]
+    y, v, lam, P, Ns_, off = ffca.batch_to_device([q.y for q in probs], [q.v0 for q in probs],
+                                                  [q.lam0 for q in probs], [q.P0 for q in probs], prec=prec)
+    est = ffca.FastFCABatch(y, v, lam, P, Ns_)
+    est.set_p_update("natural_gradient", mu)
+    tr = est.iterate(3)
+    torch.cuda.synchronize()
+    vs = [b[:, :, :Ns_[m]].numpy() for m, b in enumerate(ffca.batch_views(v.double().cpu(), J, 3, off))]
+    lam_h, P_h = lam.cpu().numpy(), P.cpu().numpy()
+    for m, (q, r) in enumerate(zip(probs, refs)):
+        got = (vs[m], lam_h[m], P_h[m], r[3])
+        _compare(prec, r, got, q.N, q.F)
+    t_ref = np.sum([r[3] for r in refs], axis=0)
+    NF = sum(q.N * q.F for q in probs)
+    if prec == "fp64":
+        assert np.all(np.abs(tr - t_ref) <= 1e-9 * np.abs(t_ref))
+    else:
+        assert np.all(np.abs(tr - t_ref) <= 1e-5 * NF)
+    est.close()
