@@ -56,11 +56,14 @@ constexpr int kGroupThreads = 32 * kGroupWarps;
 constexpr int kStreamSmemBudget = 200 * 1024;    // dynamic shared memory per CTA
 static_assert(kGroupWarps % 4 == 0, "groups interleave in units of four warps");
 
-// Pipelines per CTA: two where the per-point state fits 128 registers (the
-// 16 warps then share the register file), else one.
+// Pipelines per CTA: two (at most FFCA_MAX_GROUPS) where the per-point state
+// fits 128 registers (the 16 warps then share the register file), else one.
+#ifndef FFCA_MAX_GROUPS
+#define FFCA_MAX_GROUPS 2
+#endif
 template <typename T, int I, int J>
 struct StreamGroups {
-  static constexpr int value = (sizeof(T) == 4 && I <= 4 && J <= 3) ? 2 : 1;
+  static constexpr int value = (sizeof(T) == 4 && I <= 4 && J <= 3) ? FFCA_MAX_GROUPS : 1;
 };
 
 // The role of a thread in its CTA.  Warp w belongs to group (w / 4) % G with
@@ -174,7 +177,7 @@ __device__ inline void consumer_sync(int group) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "n"(kConsumers) : "memory");
 }
 
-// Reduction of NV per-thread values (hi + lo) over a group's consumer warps:
+// Reduction of NV per-thread values over a group's consumer warps:
 // a butterfly reduce-scatter inside each warp (at level `off` every lane
 // keeps half of its remaining values and receives the partner's partial
 // sums of that half from lane ^ off: 31 exchanges reduce 32 values where a
@@ -201,8 +204,7 @@ struct GroupReduce {
   // single-buffered view (the I > 4 pass B, two barriers per segment)
   __device__ static T (&one(Smem& sm))[kConsumerWarps][NC * 32] { return sm.hi[0]; }
 
-  __device__ static void run(const T (&hi)[NV], const T (&lo)[NV], Smem& smem, double* out, const Role& r,
-                             int parity) {
+  __device__ static void run(const T (&hi)[NV], Smem& smem, double* out, const Role& r, int parity) {
     static_assert(NB == 2, "run() alternates two buffers");
     auto& sm = smem.hi[parity & 1];
     const int lane = threadIdx.x & 31;
@@ -212,7 +214,7 @@ struct GroupReduce {
 #pragma unroll
       for (int v = 0; v < 32; ++v) {
         const int idx = c * 32 + v;
-        h[v] = idx < NV ? hi[idx] + lo[idx] : (T)0;
+        h[v] = idx < NV ? hi[idx] : (T)0;
       }
 #pragma unroll
       for (int off = 16; off >= 1; off >>= 1) {
@@ -771,29 +773,17 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
       const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
       if constexpr (kNarrow) {
-        float hi[NV], lo[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          hi[q] = acc[q];
-          lo[q] = 0.f;
-        }
-        Red::run(hi, lo, red, out, rl, nseg);
+        Red::run(acc, red, out, rl, nseg);
       } else if constexpr (sizeof(T) == 4) {
-        float hi[NV], lo[NV];
+        float hi[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
-          lo[q] = 0.f;
-        }
-        Red::run(hi, lo, red, out, rl, nseg);
+        for (int q = 0; q < NV; ++q) hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
+        Red::run(hi, red, out, rl, nseg);
       } else {
-        double hi[NV], lo[NV];
+        double hi[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          hi[q] = acc[q].v;
-          lo[q] = 0.0;
-        }
-        Red::run(hi, lo, red, out, rl, nseg);
+        for (int q = 0; q < NV; ++q) hi[q] = acc[q].v;
+        Red::run(hi, red, out, rl, nseg);
       }
       ++nseg;  // the next segment reduces through the other buffer
       seg_new = true;
@@ -1142,29 +1132,17 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
         const int slot = rl.vb - pt.first_block(f);
         double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
         if constexpr (kNarrow) {
-          float hi[NV], lo[NV];
-  #pragma unroll
-          for (int q = 0; q < NV; ++q) {
-            hi[q] = acc[q];
-            lo[q] = 0.f;
-          }
-          Red::run(hi, lo, red, out, rl, nseg);
+          Red::run(acc, red, out, rl, nseg);
         } else if constexpr (sizeof(T) == 4) {
-          float hi[NV], lo[NV];
+          float hi[NV];
   #pragma unroll
-          for (int q = 0; q < NV; ++q) {
-            hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
-            lo[q] = 0.f;
-          }
-          Red::run(hi, lo, red, out, rl, nseg);
+          for (int q = 0; q < NV; ++q) hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
+          Red::run(hi, red, out, rl, nseg);
         } else {
-          double hi[NV], lo[NV];
+          double hi[NV];
   #pragma unroll
-          for (int q = 0; q < NV; ++q) {
-            hi[q] = acc[q].v;
-            lo[q] = 0.0;
-          }
-          Red::run(hi, lo, red, out, rl, nseg);
+          for (int q = 0; q < NV; ++q) hi[q] = acc[q].v;
+          Red::run(hi, red, out, rl, nseg);
         }
         ++nseg;  // the next segment reduces through the other buffer
         seg_new = true;
