@@ -198,8 +198,11 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
  *         one is minus Eq. partialP's dL2/dP^*)
  *   loss  host double or NULL: the loss value (the call then synchronises)
  * s: device [J][I][F][ld] complex of the precision's type (the layout of the
- * ffca_wiener output).  Enqueued on the context stream.  FFCA_ERR_UNSUPPORTED
- * for batch contexts and for I = 8. */
+ * ffca_wiener output).  Enqueued on the context stream.  For a batch context
+ * every array takes the batch layout (dv that of v, dlam and dP stacked per
+ * mixture as lambda and P, s that of the batch Wiener output), N is each
+ * mixture's N[m], and loss is the sum over the mixtures.
+ * FFCA_ERR_UNSUPPORTED for I = 8. */
 ffca_status ffca_nll_grad(ffca_ctx* ctx, void* dv, double* dlam, double* dP, double* loss);
 ffca_status ffca_wiener_se_grad(ffca_ctx* ctx, const void* s, void* dv, double* dlam, double* dP,
                                 double* loss);

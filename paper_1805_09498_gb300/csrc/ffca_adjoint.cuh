@@ -17,8 +17,8 @@
 //     dSE/dP^* = sum_n sum_j (y (g_j * b_j)^H - x^_j b_j^H)
 // dP is the conjugate Wirtinger derivative: dLoss = 2 Re sum conj(dP) dP.
 //
-// k_adj streams y, v (and s) once: one CTA per contiguous unit range of the
-// uniform partition, 256 threads, per-thread sums over the range's frames of
+// k_adj streams y, v (and s) once: one CTA per contiguous unit range of pass
+// A's partition (uniform for one mixture, ragged for a batch), 256 threads, per-thread sums over the range's frames of
 // each frequency, a block reduction per frequency segment into that
 // frequency's slot (deterministic, no atomics).  k_adj_final sums the slots
 // per frequency (FP64, slot order) and adds the closed-form terms.
@@ -28,21 +28,23 @@
 
 namespace ffca {
 
+// Problems p = (mixture, frequency) of pass A's partition: uniform for one
+// mixture, ragged for a batch (mixture-major blocks, as the estimation).
 struct AdjArgs {
-  Partition part;        // uniform: F problems of Uf units (the N frames)
+  Partition part;        // pass A's: F problems (frames, rows and offsets per problem)
   int F, N, ld;
-  const void* y;         // [I][F][ld] complex
-  const void* v;         // [J][F][ld] real
+  const void* y;         // per mixture [I][Fm][ld_m] complex
+  const void* v;         // per mixture [J][Fm][ld_m] real
   const double* lam;     // [F][J][I]
   const double* P;       // [F][I][I] complex
   const double* pinvH;   // [F][I][I] complex, P^{-H} (k_prep)
   const double* logdet;  // [F] ln|det P|^2 (k_prep)
-  const void* s;         // SE: [J][I][F][ld] complex reference source images
-  void* dv;              // [J][F][ld] real: frames < N written (and the rest of their vector units as 0)
+  const void* s;         // SE: per mixture [J][I][Fm][ld_m] complex reference source images
+  void* dv;              // as v: frames < N_m written (and the rest of their vector units as 0)
   double* dlam;          // [F][J][I]
   double* dP;            // [F][I][I] complex
   double* part_buf;      // [F][max_slots][NV]
-  double* lossf;         // [F] per-frequency loss
+  double* lossf;         // [F] per-problem loss
   double* loss;          // [1] total
   unsigned* gcnt;        // arrival counter of k_adj_final
   unsigned* status;
@@ -77,9 +79,22 @@ __global__ void __launch_bounds__(kBlock) k_adj(AdjArgs a) {
   VV* __restrict__ dv = reinterpret_cast<VV*>(a.dv);
 
   for (long long u = u0; u < u1;) {
-    const int f = (int)(u / pt.Uf);
-    const int k0 = (int)(u - (long long)f * pt.Uf);
-    const int k1 = (int)min((long long)pt.Uf, k0 + (u1 - u));
+    // problem f (a frequency of one mixture) and its rows: mixture-major
+    // blocks at frame offset `off`, rows of rlen units (the single-mixture
+    // case: off = 0, rlen = ld / FU, Fm = F)
+    const int f = pt.problem_of(u);
+    const long long us = pt.start(f);
+    const int k0 = (int)(u - us);
+    const int k1 = (int)(min(pt.start(f + 1), u1) - us);
+    const int Np = pt.frames(f);
+    const long long rlen = pt.row_len(f, row * FU) / FU;
+    const long long off = pt.frame_off(f) / FU;
+    const long long r0 = (long long)pt.freq(f) * rlen;
+    const size_t rstr = (size_t)pt.Fm * rlen;  // from one mic's (source's) row to the next
+    const VY* __restrict__ yf = y + (size_t)I * pt.Fm * off + r0;
+    const VV* __restrict__ vf = v + (size_t)J * pt.Fm * off + r0;
+    const VY* __restrict__ sf = SE ? s + (size_t)J * I * pt.Fm * off + r0 : nullptr;
+    VV* __restrict__ dvf = dv + (size_t)J * pt.Fm * off + r0;
     __syncthreads();
     if (threadIdx.x < I * I) {
       const int r = threadIdx.x / I, c = threadIdx.x % I;
@@ -106,12 +121,12 @@ __global__ void __launch_bounds__(kBlock) k_adj(AdjArgs a) {
       VY yu[I];
       VV vu[J], dvu[J];
 #pragma unroll
-      for (int m = 0; m < I; ++m) yu[m] = y[((size_t)m * pt.F + f) * row + k];
+      for (int m = 0; m < I; ++m) yu[m] = yf[m * rstr + k];
 #pragma unroll
-      for (int j = 0; j < J; ++j) vu[j] = v[((size_t)j * pt.F + f) * row + k];
+      for (int j = 0; j < J; ++j) vu[j] = vf[j * rstr + k];
 #pragma unroll
       for (int e = 0; e < FU; ++e) {
-        const bool valid = k * FU + e < a.N;
+        const bool valid = k * FU + e < Np;
         cpx<T> ym[I], yt[I];
 #pragma unroll
         for (int m = 0; m < I; ++m) ym[m] = valid ? yframe(yu[m], e) : mk<T>(0, 0);
@@ -170,7 +185,7 @@ __global__ void __launch_bounds__(kBlock) k_adj(AdjArgs a) {
           for (int j = 0; j < J; ++j) {
             VY su[I];
 #pragma unroll
-            for (int m = 0; m < I; ++m) su[m] = s[(((size_t)j * I + m) * pt.F + f) * row + k];
+            for (int m = 0; m < I; ++m) su[m] = sf[(size_t)(j * I + m) * rstr + k];
 #pragma unroll
             for (int i = 0; i < I; ++i) g[j][i] = vj[j] * lam[j][i] * r[i];
             cpx<T> err[I];
@@ -232,7 +247,7 @@ __global__ void __launch_bounds__(kBlock) k_adj(AdjArgs a) {
         }
       }
 #pragma unroll
-      for (int j = 0; j < J; ++j) dv[((size_t)j * pt.F + f) * row + k] = dvu[j];
+      for (int j = 0; j < J; ++j) dvf[j * rstr + k] = dvu[j];
     }
     // the segment's sums into slot (f, this CTA)
     const int slot = (int)blockIdx.x - pt.first_block(f);
@@ -265,7 +280,7 @@ __global__ void __launch_bounds__(128) k_adj_final(AdjArgs a) {
       a.dlam[(size_t)f * NA + q] = t;
     } else if (q < NA + NP) {
       const int idx = q - NA;  // 2 (m I + i) + part
-      if constexpr (!SE) t -= (double)a.N * a.pinvH[(size_t)f * I * I * 2 + idx];
+      if constexpr (!SE) t -= (double)pt.frames(f) * a.pinvH[(size_t)f * I * I * 2 + idx];
       a.dP[(size_t)f * I * I * 2 + idx] = t;
     } else if constexpr (SE) {
       lossv += t;
@@ -278,7 +293,7 @@ __global__ void __launch_bounds__(128) k_adj_final(AdjArgs a) {
   for (int off = 16; off > 0; off >>= 1) lossv += __shfl_xor_sync(0xffffffffu, lossv, off);
   if (lane == 0) {
     double lf = lossv;
-    if constexpr (!SE) lf += (double)a.N * ((double)I * kLnPi - __ldcg(a.logdet + f));
+    if constexpr (!SE) lf += (double)pt.frames(f) * ((double)I * kLnPi - __ldcg(a.logdet + f));
     if (!isfinite(lf)) raise_status(a.status, kDevNonfinite, f);
     a.lossf[f] = lf;
     __threadfence();

@@ -465,7 +465,6 @@ __global__ void k_mixture_sums(const double* llf, int F, double* out) {
 // streaming adjoint pass, the per-frequency finalisation.
 ffca_status adjoint(ffca_ctx* c, bool se, const void* s, void* dv, double* dlam, double* dP, double* loss) {
   if (!c) return FFCA_ERR_ARG;
-  if (c->plan.off_info) return FFCA_ERR_UNSUPPORTED;  // batch contexts: not provided
   if (c->d.F == 0) {
     if (loss) *loss = 0.0;
     return FFCA_OK;

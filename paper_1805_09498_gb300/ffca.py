@@ -648,6 +648,28 @@ class FastFCABatch:
         """Update of P in later iterations (as FastFCA.set_p_update)."""
         ffca_set_p_update(self.ctx, method, mu)
 
+    def nll_grad(self):
+        """(NLL summed over the mixtures, dv, dlam, dPc) at the current state,
+        in the batch layouts of v, lam and P; dPc = dNLL/dP^*."""
+        import torch
+        dv = torch.zeros_like(self.v)
+        dlam = torch.empty_like(self.lam)
+        dP = torch.empty_like(self.P)
+        loss = ffca_nll_grad(self.ctx, dv.data_ptr(), dlam.data_ptr(), dP.data_ptr())
+        return loss, dv, dlam, dP
+
+    def wiener_se_grad(self, s):
+        """(SE summed over the mixtures, dv, dlam, dPc) of sum |x^ - s|^2;
+        s flat, in the layout of wiener()'s output, of y's dtype."""
+        import torch
+        if s.dtype != self.y.dtype or s.numel() != self.J * self.I * self.F * self.ld or not s.is_contiguous():
+            raise ValueError("s must be a contiguous tensor in the batch Wiener layout of y's dtype")
+        dv = torch.zeros_like(self.v)
+        dlam = torch.empty_like(self.lam)
+        dP = torch.empty_like(self.P)
+        loss = ffca_wiener_se_grad(self.ctx, s.data_ptr(), dv.data_ptr(), dlam.data_ptr(), dP.data_ptr())
+        return loss, dv, dlam, dP
+
     def loglik(self) -> np.ndarray:
         """L2 of every mixture (host array of M values)."""
         return ffca_batch_loglik(self.ctx, self.M)

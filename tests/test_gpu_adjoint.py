@@ -167,17 +167,3 @@ def test_autograd_functions():
     assert per_f_relerr(lam3.grad.cpu().numpy(), rl, 0) < 1e-9
     assert per_f_relerr(P3.grad.cpu().numpy(), 2.0 * rP, 0) < 1e-9
 
-
-def test_adjoint_rejects_batch_contexts():
-    from paper_1805_09498_gb300 import ffca
-    from paper_1805_09498_gb300.synth import make_batch
-    import torch
-    probs = make_batch(2, 2, 3, [10, 20], seed=1)
-    y, v, lam, P, Ns, off = ffca.batch_to_device([q.y for q in probs], [q.v0 for q in probs],
-                                                 [q.lam0 for q in probs], [q.P0 for q in probs])
-    est = ffca.FastFCABatch(y, v, lam, P, Ns)
-    buf = torch.empty(4096, dtype=torch.float64, device=y.device)
-    with pytest.raises(ffca.FFCAError) as ei:
-        ffca.ffca_nll_grad(est.ctx, buf.data_ptr(), buf.data_ptr(), buf.data_ptr())
-    assert ei.value.status == 7
-    est.close()

@@ -174,9 +174,9 @@ def test_invalid_batches_are_rejected():
     dv = torch.zeros_like(v)
     dl = torch.empty_like(lam)
     dP = torch.empty_like(P)
-    with pytest.raises(ffca.FFCAError) as ei:  # gradients: single-mixture contexts only
-        ffca.ffca_nll_grad(est.ctx, dv.data_ptr(), dl.data_ptr(), dP.data_ptr())
-    assert ei.value.status == 7
+    with pytest.raises(ffca.FFCAError) as ei:  # gradient outputs must be 16-byte aligned
+        ffca.ffca_nll_grad(est.ctx, dv.data_ptr() + 4, dl.data_ptr(), dP.data_ptr())
+    assert ei.value.status == 1
     est.close()
 
 
