@@ -100,7 +100,7 @@ struct Plan {
   size_t off_ustartW, off_bstartW;        // batch: the Wiener pass's unit starts and block ranges
   size_t off_bstartA[kCands], off_slotsA[kCands], off_bstartB[kCands], off_slotsB[kCands];  // batch candidates
   size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
-  size_t off_cntA, off_cntB, off_logdet, off_llf, off_tpart, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
+  size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t bytes;
 };
 
@@ -170,7 +170,6 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_cntB = off; off = align_up(off + sizeof(unsigned) * P);
   p->off_logdet = off; off = align_up(off + sizeof(double) * P);
   p->off_llf = off; off = align_up(off + sizeof(double) * P);
-  p->off_tpart = off; off = align_up(off + sizeof(double) * P);  // per-block trace sums of the P step
   p->off_trace = off; off = align_up(off + sizeof(double) * kTraceCap);
   p->off_pinvH = off; off = align_up(off + sizeof(double) * 2 * I * I * (size_t)P);
   p->off_partA = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2));
@@ -262,7 +261,6 @@ FastArgs base_args(const ffca_ctx* c) {
   a.logdet = reinterpret_cast<double*>(c->ws + c->plan.off_logdet);
   a.llf = reinterpret_cast<double*>(c->ws + c->plan.off_llf);
   a.trace = reinterpret_cast<double*>(c->ws + c->plan.off_trace);
-  a.tpart = reinterpret_cast<double*>(c->ws + c->plan.off_tpart);
   a.status = c->status;
   a.ops = c->ops;
   a.tabA = c->ws + c->plan.off_tabA;
@@ -335,6 +333,12 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
 
+// Blocks of the P step: one warp per 32 / I problems, plus the trace's block.
+int p_step_grid(const ffca_ctx* c, const FastArgs& b) {
+  const int G = 32 / c->d.I;
+  return (c->d.F + G - 1) / G + (b.trace ? 1 : 0);
+}
+
 // The P step of the context's update of P.
 const void* p_step_kernel(const ffca_ctx* c) {
   return c->pmode == kPFixedPoint ? c->kern->psolve : c->kern->pgrad;
@@ -384,12 +388,11 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
     FastArgs b = pass_b_args(c, slot);
-    b.trace = nullptr;  // no trace: k_psolve skips the sum over problems
+    b.trace = nullptr;  // no trace: no trace block in the P step
     if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
-    const int G = 32 / c->d.I;  // problems per warp
-    if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
+    if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
   }
   return FFCA_OK;
 }
@@ -572,12 +575,11 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
       FastArgs b = pass_b_args(c, slot);
-      if (!ll_trace) b.trace = nullptr;  // k_psolve skips the sum over problems
+      if (!ll_trace) b.trace = nullptr;  // no trace block in the P step
       if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
                       c->kern->stream_smem)) != FFCA_OK)
         return st;
-      const int G = 32 / c->d.I;  // frequencies per warp
-      if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem)) != FFCA_OK)
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
@@ -1107,9 +1109,8 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
         st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
                     c->kern->stream_smem);
       cudaEventRecord(ev[q][2], c->stream);
-      const int G = 32 / c->d.I;
       if (st == FFCA_OK)
-        st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), (c->d.F + G - 1) / G, 32, b, c->kern->solve_smem);
+        st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem);
     }
     if (st == FFCA_OK && !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) st = FFCA_ERR_CUDA;
     for (int q = 0; q < kCands && st == FFCA_OK; ++q) {

@@ -293,6 +293,7 @@ __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
   constexpr int NV = I * I * I;
   constexpr int NL = I * (I - 1) / 2;
   extern __shared__ __align__(16) unsigned char big_smem[];
+  if (trace_block(a)) return;
   const int lane = threadIdx.x;
   const int g = lane / I, i = lane % I;
   const int f0 = blockIdx.x * G + g;
@@ -408,8 +409,6 @@ __global__ void __launch_bounds__(32) k_psolve_ldl(FastArgs a) {
       a.logdet[f] = log(det2);
     }
   }
-  // the trace: per-block sums of the problems' log-likelihoods, then the last block
-  if (a.trace) trace_by_blocks(a, (active && i == 0) ? __ldcg(a.llf + f) : 0.0);
 }
 
 // ln|det P|^2, P^{-H} (always: the P step starts from it) and the pass-A

@@ -32,7 +32,6 @@ struct FastArgs {
   double* logdet;            // [F] ln|det P(f)|^2 of the current P
   double* llf;               // [F] per-frequency log-likelihood
   double* trace;             // [kTraceCap]
-  double* tpart;             // [blocks of the P step] per-block sums of llf for the trace
   int trace_slot;
   unsigned* status;          // [2] first error code, its frequency
   unsigned long long* ops;   // matrix inversions performed by the P update
@@ -187,28 +186,14 @@ __device__ inline void finalize_trace(const FastArgs& a) {
   if ((threadIdx.x & 31) == 0) a.trace[a.trace_slot] = t;
 }
 
-// The trace from the P step's blocks (one warp each): every block adds the
-// log-likelihoods of its problems (own: this lane's share, summed over the
-// warp in a fixed tree) into tpart[block]; the last block to finish sums
-// the blocks' partial sums in block order into the trace slot.  No block
-// waits on another.
-__device__ inline void trace_by_blocks(const FastArgs& a, double own) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) own += __shfl_xor_sync(0xffffffffu, own, off);
-  unsigned last = 0;
-  if (lane == 0) {
-    a.tpart[blockIdx.x] = own;
-    __threadfence();
-    last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
-    if (last) *a.gcnt = 0u;
-  }
-  last = __shfl_sync(0xffffffffu, last, 0);
-  if (last) {
-    __threadfence();
-    const double t = warp_sum_fixed(a.tpart, gridDim.x);
-    if (lane == 0) a.trace[a.trace_slot] = t;
-  }
+// With a trace, the P step is launched with one block (one warp) beyond its
+// problems' blocks: that block sums the problems' log-likelihoods of the
+// state entering the iteration (complete since pass B) into the trace slot,
+// beside the problems' blocks instead of after them.
+__device__ inline bool trace_block(const FastArgs& a) {
+  if (!a.trace || blockIdx.x != gridDim.x - 1) return false;
+  finalize_trace(a);
+  return true;
 }
 
 // -------------------------------------------------------------- pass A finalise
@@ -320,6 +305,7 @@ template <typename T, int I, int J, bool GRAD = false>
 __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
   constexpr int G = Lanes<I>::G;
   constexpr int NV = I * I * I;
+  if (trace_block(a)) return;
   const int lane = threadIdx.x;
   const int g = lane / I, i = lane % I;
   const int f0 = blockIdx.x * G + g;
@@ -479,8 +465,6 @@ __global__ void __launch_bounds__(32) k_psolve(FastArgs a) {
       a.logdet[f] = log(d2);
     }
   }
-  // the trace: per-block sums of the problems' log-likelihoods, then the last block
-  if (a.trace) trace_by_blocks(a, (active && i == 0) ? __ldcg(a.llf + f) : 0.0);
 }
 
 // -------------------------------------------------------------- prep
