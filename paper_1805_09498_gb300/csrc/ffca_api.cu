@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ffca.h"
 #include "ffca_adjoint.cuh"
 #include "ffca_dispatch.h"
@@ -296,8 +298,19 @@ FastArgs pass_b_args(const ffca_ctx* c, int slot) {
   return a;
 }
 
+// NVTX range names of the kernel kinds (FFCA_KERNEL_*): a profiler that
+// records NVTX (nsys) shows every launch under its kind; without one the
+// push and pop cost a branch.
+const char* const kKindNames[FFCA_KERNEL_KINDS] = {
+    "ffca prep", "ffca pass A", "ffca loglik", "ffca pass B", "ffca wiener",
+    "ffca P step", "ffca pass A finalise", "ffca adjoint", "ffca adjoint finalise"};
+
 template <typename Args>
 ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, Args& a, size_t smem = 0) {
+  struct Range {  // one NVTX range around the enqueue
+    explicit Range(const char* n) { nvtxRangePushA(n); }
+    ~Range() { nvtxRangePop(); }
+  } range(kKindNames[kind]);
   void* args[] = {&a};
   TimedLaunch* t = nullptr;
   if (c->timing && !c->use_graph) {
