@@ -1,0 +1,160 @@
+"""Planted mistakes in the FP64 oracle, one at a time and on the CPU only,
+each of which some pin must catch.
+
+The pins (dense covariance algebra, the Q-function, the Kronecker form of
+Eq. FPI, finite differences, the Wiener identities, the closed forms, the
+scale gauge and the FCA correspondence) do not share the oracle's code, so a
+plausible slip in any step of it (a transposed or unconjugated operand, a
+dropped term, a wrong normalisation, the wrong (v, Lambda) in an update)
+has to fail at least one of them.  This guards the pins themselves: a pin
+that a mistake slips past is no pin.
+"""
+import numpy as np
+import pytest
+
+from oracle import fastfca_as as ffa
+
+import test_oracle_p_updates as pu
+import test_oracle_pins as pins
+
+LN_PI = np.log(np.pi)
+
+
+def _bt_no_conj(y, P):  # P^T y instead of P^H y
+    return np.einsum("fai,afn->ifn", P, y)
+
+
+def _sigma_wrong_source(v, lam):  # lambda of the wrong source
+    return np.einsum("jfn,fji->ifn", v, lam[:, ::-1, :])
+
+
+def _estep_no_correction(y, v, lam, P):  # Phi~ without its second term
+    yt = ffa.basis_transform(y, P)
+    sigma = ffa.model_variances(v, lam)
+    vl = v[:, None] * lam.transpose(1, 2, 0)[:, :, :, None]
+    return vl / sigma[None] * yt[None], vl
+
+
+def _estep_conj_mean(y, v, lam, P):  # conj(y~) in the posterior mean
+    yt = ffa.basis_transform(y, P)
+    sigma = ffa.model_variances(v, lam)
+    vl = v[:, None] * lam.transpose(1, 2, 0)[:, :, :, None]
+    return vl / sigma[None] * yt.conj()[None], vl - vl * vl / sigma[None]
+
+
+def _v_over_J(mu, phi, lam):  # 1/J instead of 1/I
+    q = np.abs(mu) ** 2 + phi
+    return np.einsum("jifn,fji->jfn", q, 1.0 / lam) / mu.shape[0]
+
+
+def _v_times_lambda(mu, phi, lam):  # Lambda instead of Lambda^{-1}
+    q = np.abs(mu) ** 2 + phi
+    return np.einsum("jifn,fji->jfn", q, lam) / mu.shape[1]
+
+
+def _lambda_over_n_minus_1(mu, phi, v):
+    q = np.abs(mu) ** 2 + phi
+    return np.einsum("jifn->fji", q / v[:, None]) / (mu.shape[3] - 1)
+
+
+def _cov_transposed(y, v, lam):  # conj(y) y^T instead of y y^H
+    sigma = ffa.model_variances(v, lam)
+    return np.einsum("afn,bfn,ifn->fiab", y.conj(), y, 1.0 / sigma) / y.shape[2]
+
+
+def _fpi_no_conj(P, V, K=1, counter=ffa.COUNTER):  # P^{-T} instead of P^{-H}
+    for _ in range(K):
+        Q = np.linalg.inv(P).transpose(0, 2, 1)
+        P = np.stack([np.linalg.solve(V[:, i], Q[:, :, i][..., None])[..., 0] for i in range(P.shape[1])], axis=2)
+    return P
+
+
+def _fpi_v_transposed(P, V, K=1, counter=ffa.COUNTER):  # V_i^T instead of V_i
+    for _ in range(K):
+        Q = np.linalg.inv(P).conj().transpose(0, 2, 1)
+        P = np.stack([np.linalg.solve(V[:, i].transpose(0, 2, 1), Q[:, :, i][..., None])[..., 0]
+                      for i in range(P.shape[1])], axis=2)
+    return P
+
+
+def _ll_no_pi(y, v, lam, P):  # the -I ln(pi) constant dropped
+    yt = ffa.basis_transform(y, P)
+    sigma = ffa.model_variances(v, lam)
+    _, la = np.linalg.slogdet(P)
+    return 2.0 * la[:, None] - np.sum(np.log(sigma) + np.abs(yt) ** 2 / sigma, axis=0)
+
+
+def _ll_det_once(y, v, lam, P):  # ln|det P| instead of ln|det P|^2
+    yt = ffa.basis_transform(y, P)
+    sigma = ffa.model_variances(v, lam)
+    _, la = np.linalg.slogdet(P)
+    return -y.shape[0] * LN_PI + la[:, None] - np.sum(np.log(sigma) + np.abs(yt) ** 2 / sigma, axis=0)
+
+
+def _wiener_p_inverse(y, v, lam, P):  # P^{-1} instead of P^{-H}
+    mu, _ = ffa.e_step(y, v, lam, P)
+    return np.einsum("fab,jbfn->jafn", np.linalg.inv(P), mu)
+
+
+def _em_lambda_with_old_v(y, v, lam, P):  # Eq. Lambdaupdate with the old v
+    mu, phi = ffa.e_step(y, v, lam, P)
+    return ffa.m_step_v(mu, phi, lam), ffa.m_step_lambda(mu, phi, v)
+
+
+def _grad_no_conj(P, V, mu, K=1, counter=ffa.COUNTER):  # P^{-T} in the gradient step
+    for _ in range(K):
+        P = P + mu * (np.linalg.inv(P).transpose(0, 2, 1) - np.einsum("fiab,fbi->fai", V, P))
+    return P
+
+
+def _natgrad_no_h(P, V, mu, K=1):  # (I - C) instead of (I - C)^H
+    eye = np.eye(P.shape[1])[None]
+    for _ in range(K):
+        C = np.einsum("fai,fiab,fbk->fik", P.conj(), V, P)
+        P = P + mu * (P @ (eye - C))
+    return P
+
+
+MUTANTS = [
+    ("basis_transform", _bt_no_conj), ("model_variances", _sigma_wrong_source),
+    ("e_step", _estep_no_correction), ("e_step", _estep_conj_mean),
+    ("m_step_v", _v_over_J), ("m_step_v", _v_times_lambda), ("m_step_lambda", _lambda_over_n_minus_1),
+    ("weighted_covariances", _cov_transposed), ("fixed_point_P", _fpi_no_conj),
+    ("fixed_point_P", _fpi_v_transposed), ("loglik_terms", _ll_no_pi), ("loglik_terms", _ll_det_once),
+    ("wiener", _wiener_p_inverse), ("em_half", _em_lambda_with_old_v),
+    ("gradient_P", _grad_no_conj), ("natural_gradient_P", _natgrad_no_h),
+]
+
+# every pin on one of its cases (two where I = J would hide a mix-up of I and J)
+PINS = [
+    (pins.test_loglik_equals_dense_density, dict(shape=pins.SHAPES[0])),
+    (pins.test_estep_equals_dense_posterior, dict(shape=pins.SHAPES[0])),
+    (pins.test_mstep_maximises_q_function, dict(shape=(3, 3, 2, 5))),
+    (pins.test_mstep_maximises_q_function, dict(shape=(2, 3, 2, 4))),  # I != J
+    (pins.test_wiener_identities, dict(shape=pins.SHAPES[0])),
+    (pins.test_fixed_point_equals_kronecker_form, dict(shape=pins.SHAPES[0])),
+    (pins.test_gradient_matches_finite_differences, dict(shape=(3, 3, 1, 6))),
+    (pins.test_fixed_point_scalar_closed_form, {}),
+    (pins.test_em_half_does_not_decrease_loglik, dict(seed=0)),
+    (pins.test_fca_and_fastfca_agree_from_joint_state, dict(shape=(3, 3, 2, 9))),
+    (pins.test_scale_gauge_equivariance, {}),
+    (pu.test_gradient_step_is_the_scaled_wirtinger_gradient, dict(shape=pu.SHAPES[0])),
+    (pu.test_natural_gradient_step_slope, dict(shape=pu.SHAPES[0])),
+    (pu.test_natural_gradient_is_equivariant, {}),
+]
+
+
+@pytest.mark.parametrize("name,mutant", MUTANTS, ids=[m.__name__.strip("_") for _, m in MUTANTS])
+def test_a_pin_catches_the_planted_mistake(monkeypatch, name, mutant):
+    monkeypatch.setattr(ffa, name, mutant)
+    for pin, kw in PINS:
+        try:
+            pin(**kw)
+        except AssertionError:
+            return  # caught
+    pytest.fail(f"no pin caught {mutant.__name__} in {name}")
+
+
+def test_the_pins_pass_on_the_oracle():
+    for pin, kw in PINS:
+        pin(**kw)
