@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import fastfca_as as ffa
+from oracle import fca
 
 import test_oracle_p_updates as pu
 import test_oracle_pins as pins
@@ -115,6 +116,29 @@ def _natgrad_no_h(P, V, mu, K=1):  # (I - C) instead of (I - C)^H
     return P
 
 
+def _fca_phi_plus(y, v, S, counter=ffa.COUNTER):  # Phi_j = R_j + R_j R^{-1} R_j
+    Rj = v[:, :, :, None, None] * S.transpose(1, 0, 2, 3)[:, :, None, :, :]
+    RjRinv = Rj @ np.linalg.inv(Rj.sum(axis=0))[None]
+    mu = np.einsum("jfnab,fnb->jfna", RjRinv, y.transpose(1, 2, 0))
+    return mu, Rj + RjRinv @ Rj
+
+
+def _fca_v_without_inverse(mu, Phi, S, counter=ffa.COUNTER):  # tr(S_j C) instead of tr(S_j^{-1} C)
+    J, F, N, I = mu.shape
+    C = mu[..., :, None] * mu[..., None, :].conj() + Phi
+    v = np.einsum("fjab,jfnba->jfn", S, C).real / I
+    return v, np.einsum("jfnab->fjab", C / v[..., None, None]) / N
+
+
+def _fca_outer_transposed(mu, Phi, S, counter=ffa.COUNTER):  # mu^* mu^T instead of mu mu^H
+    J, F, N, I = mu.shape
+    C = mu[..., :, None].conj() * mu[..., None, :] + Phi
+    v = np.einsum("fjab,jfnba->jfn", np.linalg.inv(S), C).real / I
+    return v, np.einsum("jfnab->fjab", C / v[..., None, None]) / N
+
+
+FCA_MUTANTS = [("e_step", _fca_phi_plus), ("m_step", _fca_v_without_inverse), ("m_step", _fca_outer_transposed)]
+
 MUTANTS = [
     ("basis_transform", _bt_no_conj), ("model_variances", _sigma_wrong_source),
     ("e_step", _estep_no_correction), ("e_step", _estep_conj_mean),
@@ -155,6 +179,24 @@ def test_a_pin_catches_the_planted_mistake(monkeypatch, name, mutant):
     pytest.fail(f"no pin caught {mutant.__name__} in {name}")
 
 
+FCA_PINS = [
+    (pins.test_fca_loglik_monotone, dict(seed=0)),
+    (pins.test_fca_dense_loglik, dict(shape=(3, 3, 2, 6))),
+    (pins.test_fca_and_fastfca_agree_from_joint_state, dict(shape=(3, 3, 2, 9))),
+]
+
+
+@pytest.mark.parametrize("name,mutant", FCA_MUTANTS, ids=[m.__name__.strip("_") for _, m in FCA_MUTANTS])
+def test_a_pin_catches_the_planted_fca_mistake(monkeypatch, name, mutant):
+    monkeypatch.setattr(fca, name, mutant)
+    for pin, kw in FCA_PINS:
+        try:
+            pin(**kw)
+        except AssertionError:
+            return
+    pytest.fail(f"no pin caught {mutant.__name__} in fca.{name}")
+
+
 def test_the_pins_pass_on_the_oracle():
-    for pin, kw in PINS:
+    for pin, kw in PINS + FCA_PINS:
         pin(**kw)
