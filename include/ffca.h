@@ -161,6 +161,18 @@ typedef enum {
  * allocation-free call always uses the fixed point. */
 ffca_status ffca_set_p_update(ffca_ctx* ctx, int method, double mu);
 
+/* Fault injection for tests of failure detection (no GPU fault is made).
+ * FFCA_FAULT_PASS_A_NO_COPIES: from the next call on, the producer warps of
+ * pass A issue none of their copies, so its consumers' bounded waits run
+ * out (after about a second), latch FFCA_ERR_TIMEOUT and skip their tiles;
+ * every kernel still ends and the GPU context stays usable.  The context's
+ * status then stays latched and its state is not meaningful: release it and
+ * make a new context.  FFCA_FAULT_NONE switches the fault off.  Drops a
+ * captured graph.  FFCA_ERR_ARG for an unknown kind. */
+#define FFCA_FAULT_NONE 0
+#define FFCA_FAULT_PASS_A_NO_COPIES 1
+ffca_status ffca_test_fault(ffca_ctx* ctx, int kind);
+
 /* Host-buffer transfers for callers whose data live in host memory: copy
  * y, v, lambda and P (same layouts as the device arrays; any may be NULL to
  * skip it) from host to the context's device arrays, or v, lambda and P back

@@ -238,6 +238,7 @@ struct ffca_ctx {
   // update of P (kPFixedPoint unless ffca_set_p_update chose a gradient method) and its step size
   int pmode;
   double mu;
+  int fault;  // injected fault for tests (kFaultNone unless ffca_test_fault set one)
   // profiling
   int timing;
   unsigned long long launches[FFCA_KERNEL_KINDS];
@@ -270,6 +271,7 @@ FastArgs base_args(const ffca_ctx* c) {
   a.inv_n = 1.0 / c->d.N;
   a.pmode = c->pmode;
   a.mu = c->mu;
+  a.fault = c->fault;
   return a;
 }
 
@@ -1165,6 +1167,19 @@ ffca_status ffca_set_p_update(ffca_ctx* c, int method, double mu) {
   if (method != FFCA_P_FIXED_POINT && !(std::isfinite(mu) && mu > 0.0)) return FFCA_ERR_ARG;
   c->pmode = method;
   c->mu = method == FFCA_P_FIXED_POINT ? 0.0 : mu;
+  if (c->graph) {  // the captured launches hold the previous arguments
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return FFCA_OK;
+}
+
+static_assert(FFCA_FAULT_NONE == kFaultNone && FFCA_FAULT_PASS_A_NO_COPIES == kFaultPassANoCopies,
+              "the ABI's fault codes are the kernels'");
+
+ffca_status ffca_test_fault(ffca_ctx* c, int kind) {
+  if (!c || (kind != FFCA_FAULT_NONE && kind != FFCA_FAULT_PASS_A_NO_COPIES)) return FFCA_ERR_ARG;
+  c->fault = kind;
   if (c->graph) {  // the captured launches hold the previous arguments
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;

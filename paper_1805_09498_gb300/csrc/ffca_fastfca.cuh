@@ -45,7 +45,14 @@ struct FastArgs {
   const double* prev_buf;    // and buffer
   int pmode;                 // update of P: kPFixedPoint, kPGradient or kPNatural
   double mu;                 // step size of the gradient updates
+  int fault;                 // injected fault (tests of failure detection): kFault*
 };
+
+// Faults a test can inject (ffca_test_fault): with kFaultPassANoCopies the
+// producers of pass A issue no copies, so that its consumers' bounded waits
+// run out and latch the time-out status.
+constexpr int kFaultNone = 0;
+constexpr int kFaultPassANoCopies = 1;
 
 // Updates of P: the fixed-point iteration (Eq. FPI), or K ascent steps on L2
 // with the V_i of Eq. FPI held fixed (the alternatives of Sec. 4.6), of size

@@ -614,7 +614,9 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   const Pipe<TC::S> pp = setup_pipe<G, TC::S>(smem, TC::STAGE, rl.group, aborts);
 
   if (!rl.consumer) {
-    if ((threadIdx.x & 31) == 0) produce<T, I, J, false>(a, pp, u0, u1, row, rl.vb, abort);
+    // an injected fault: no copies, the consumers' waits run out
+    if ((threadIdx.x & 31) == 0 && a.fault != kFaultPassANoCopies)
+      produce<T, I, J, false>(a, pp, u0, u1, row, rl.vb, abort);
     return;
   }
 

@@ -109,6 +109,7 @@ def lib() -> ctypes.CDLL:
         "ffca_batch_loglik": (ci, [vp, dp]),
         "ffca_set_graph": (ci, [vp, ci]),
         "ffca_set_p_update": (ci, [vp, ci, ctypes.c_double]),
+        "ffca_test_fault": (ci, [vp, ci]),
         "ffca_batch_config_count": (ci, []),
         "ffca_batch_autotune": (ci, [vp, ci, P(ci), P(ci), dp, dp]),
         "ffca_batch_set_config": (ci, [vp, ci, ci]),
@@ -401,6 +402,14 @@ def ffca_set_p_update(ctx, method: str, mu: float = 0.0) -> None:
     if method not in P_UPDATES:
         raise ValueError(f"unknown update of P {method!r}; one of {sorted(P_UPDATES)}")
     _check(ctx, lib().ffca_set_p_update(ctx, P_UPDATES[method], float(mu)), "ffca_set_p_update")
+
+
+# Injected faults (tests of failure detection; see ffca_test_fault).
+FAULT_NONE, FAULT_PASS_A_NO_COPIES = 0, 1
+
+
+def ffca_test_fault(ctx, kind: int) -> None:
+    _check(ctx, lib().ffca_test_fault(ctx, int(kind)), "ffca_test_fault")
 
 
 def ffca_batch_destroy(ctx) -> None:

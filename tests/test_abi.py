@@ -69,3 +69,8 @@ def test_p_update_codes_match_the_header(L):
     codes = dict((m.group(1), int(m.group(2)))
                  for m in re.finditer(r"FFCA_P_(\w+) = (\d+)", hdr))
     assert codes == {k.upper(): v for k, v in ffca.P_UPDATES.items()}
+
+
+def test_fault_injection_argument_checks(L):
+    assert L.ffca_test_fault(None, 0) == 1
+    assert L.ffca_test_fault(None, 1) == 1
