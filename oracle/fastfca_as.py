@@ -161,6 +161,53 @@ def natural_gradient_P(P, V, mu, K=1):
     return P
 
 
+def _real_basis(I):
+    """The 2 I^2 real directions of C^{I x I}: E_k = e_a e_i^T (k < I^2) and
+    i e_a e_i^T (k >= I^2), k = a I + i within each half."""
+    E = np.zeros((2 * I * I, I, I), dtype=np.complex128)
+    for k in range(I * I):
+        E[k, k // I, k % I] = 1.0
+        E[I * I + k, k // I, k % I] = 1j
+    return E
+
+
+def newton_P(P, V, mu=1.0, K=1, counter=COUNTER):
+    """K steps of Newton's method on L2 / N as a function of P with the V_i
+    of Eq. FPI fixed (another of the alternatives named in Sec. 4.6; reading:
+    the exact Newton step in the 2 I^2 real coordinates of P, scaled by mu).
+
+    With l(P) = ln|det P|^2 - sum_i p_i^H V_i p_i (L2 / N up to terms free
+    of P), the first and second differentials along complex directions D,
+    D' are
+        dl[D]      = 2 Re tr(G^H D),  G = P^{-H} - [V_1 p_1, ..., V_I p_I]
+        d2l[D, D'] = -2 Re tr(P^{-1} D P^{-1} D') - 2 Re sum_i d_i^H V_i d'_i
+    (from ln det(P + D) = ln det P + tr(P^{-1} D) - tr(P^{-1} D P^{-1} D) / 2
+    + ...).  In the real basis E_k the gradient is g_k = dl[E_k] and the
+    Hessian H_kl = d2l[E_k, E_l]; the step is the minimum-norm solution of
+    H s = -g (the pseudo-inverse of H) and moves P by mu sum_k s_k E_k.
+    Reading: l is invariant under p_i -> e^{i theta} p_i, so H is singular
+    along the I directions i p_i (the gradient has no component there) and
+    the step leaves the column phases alone.  Two inversions per frequency
+    per step: P and the 2 I^2 x 2 I^2 Hessian.  Newton's method converges
+    quadratically near a nondegenerate stationary point and is not globally
+    convergent (H is indefinite away from it); mu damps the step."""
+    F, I, _ = P.shape
+    E = _real_basis(I)
+    P = P.copy()
+    for _ in range(K):
+        Pinv = np.linalg.inv(P)
+        counter.inversions += F
+        G = Pinv.conj().transpose(0, 2, 1) - np.einsum("fiab,fbi->fai", V, P)
+        g = 2.0 * np.real(np.einsum("fai,kai->fk", G.conj(), E))
+        A = np.einsum("fab,kbc->fkac", Pinv, E)                   # P^{-1} E_k
+        H = -2.0 * np.real(np.einsum("fkab,flba->fkl", A, A))     # -2 Re tr(P^{-1}E_k P^{-1}E_l)
+        H -= 2.0 * np.real(np.einsum("kai,fiab,lbi->fkl", E.conj(), V, E))
+        s = np.einsum("fkl,fl->fk", np.linalg.pinv(H, rcond=1e-10, hermitian=True), -g)
+        counter.inversions += F  # the 2 I^2 x 2 I^2 system
+        P = P + mu * np.einsum("fk,kai->fai", s, E)
+    return P
+
+
 # --------------------------------------------------------- log-likelihood ----
 def loglik_terms(y, v, lam, P):
     """Per-(n,f) value of ln N(y; 0, P^{-H} D P^{-1}) in Eq. L2, D = sum_j v_j Lambda_j.
@@ -207,6 +254,8 @@ def hybrid_iteration(y, v, lam, P, K=1, counter=COUNTER, p_update="fpi", mu=0.0)
         P = gradient_P(P, V, mu, K, counter)
     elif p_update == "natural_gradient":
         P = natural_gradient_P(P, V, mu, K)
+    elif p_update == "newton":
+        P = newton_P(P, V, mu if mu else 1.0, K, counter)
     else:
         raise ValueError(p_update)
     return v, lam, P

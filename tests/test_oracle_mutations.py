@@ -137,6 +137,17 @@ def _fca_outer_transposed(mu, Phi, S, counter=ffa.COUNTER):  # mu^* mu^T instead
     return v, np.einsum("jfnab->fjab", C / v[..., None, None]) / N
 
 
+def _newton_no_logdet_curvature(P, V, mu=1.0, K=1, counter=ffa.COUNTER):  # Hessian without ln|det P|^2
+    F, I, _ = P.shape
+    E = ffa._real_basis(I)
+    for _ in range(K):
+        G = np.linalg.inv(P).conj().transpose(0, 2, 1) - np.einsum("fiab,fbi->fai", V, P)
+        g = 2.0 * np.real(np.einsum("fai,kai->fk", G.conj(), E))
+        H = -2.0 * np.real(np.einsum("kai,fiab,lbi->fkl", E.conj(), V, E))
+        P = P + mu * np.einsum("fk,kai->fai", np.linalg.solve(H, -g[..., None])[..., 0], E)
+    return P
+
+
 FCA_MUTANTS = [("e_step", _fca_phi_plus), ("m_step", _fca_v_without_inverse), ("m_step", _fca_outer_transposed)]
 
 MUTANTS = [
@@ -147,6 +158,7 @@ MUTANTS = [
     ("fixed_point_P", _fpi_v_transposed), ("loglik_terms", _ll_no_pi), ("loglik_terms", _ll_det_once),
     ("wiener", _wiener_p_inverse), ("em_half", _em_lambda_with_old_v),
     ("gradient_P", _grad_no_conj), ("natural_gradient_P", _natgrad_no_h),
+    ("newton_P", _newton_no_logdet_curvature),
 ]
 
 # every pin on one of its cases (two where I = J would hide a mix-up of I and J)
@@ -165,6 +177,7 @@ PINS = [
     (pu.test_gradient_step_is_the_scaled_wirtinger_gradient, dict(shape=pu.SHAPES[0])),
     (pu.test_natural_gradient_step_slope, dict(shape=pu.SHAPES[0])),
     (pu.test_natural_gradient_is_equivariant, {}),
+    (pu.test_newton_step_zeroes_the_linearised_gradient, dict(shape=(3, 3, 2, 60))),
 ]
 
 

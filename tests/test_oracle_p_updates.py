@@ -1,5 +1,5 @@
-"""Pins of the oracle's alternative updates of P (Sec. 4.6: the gradient
-and natural gradient methods in place of the fixed-point iteration).
+"""Pins of the oracle's alternative updates of P (Sec. 4.6: the gradient,
+natural gradient and Newton methods in place of the fixed-point iteration).
 
 The paper names these methods without stating them; the oracle's readings
 (ascent on L2 with the V_i of Eq. FPI held fixed, K steps of size mu, Eq.
@@ -8,7 +8,9 @@ the directional derivative of L2 along each step (central differences of
 the log-likelihood, itself pinned against the dense density), the closed
 forms at I = 1, the equivariance of the natural gradient under a change of
 the microphone basis, stationarity at a stationary point of L2, and the
-inversion counts.
+inversion counts; for Newton's method, the stationarity of its quadratic
+model checked by central differences of the gradient, its quadratic
+convergence and its closed form at I = 1.
 """
 import numpy as np
 import pytest
@@ -128,3 +130,68 @@ def test_inversion_counts():
     c = OpCounter()
     ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, K=3, counter=c, p_update="natural_gradient", mu=0.1)
     assert c.inversions == 0
+
+
+# ------------------------------------------------------------ Newton's method
+def _stationary(seed=8):
+    """A stationary point of L2 in P at fixed V (as in the fixed-point pins)."""
+    p = make_problem(3, 3, 2, 400, seed=seed)
+    V = ffa.weighted_covariances(p.y, p.v_true, p.lam_true)
+    P = p.P0.copy()
+    for _ in range(1500):
+        P = ffa.fixed_point_P(P, V, K=1, counter=OpCounter())
+        d = np.einsum("fai,fiab,fbi->fi", P.conj(), V, P).real
+        P = P / np.sqrt(d)[:, None, :]
+    return P, V
+
+
+def _G(P, V):
+    """Eq. partialP / N with V fixed: P^{-H} - [V_1 p_1, ..., V_I p_I]."""
+    return np.linalg.inv(P).conj().transpose(0, 2, 1) - np.einsum("fiab,fbi->fai", V, P)
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 2, 60), (2, 3, 3, 40), (4, 2, 2, 80)])
+def test_newton_step_zeroes_the_linearised_gradient(shape):
+    """The Newton step D satisfies G(P) + dG[D] = 0 (the stationarity of the
+    second-order model), with dG[D] by central differences of the gradient
+    of Eq. partialP, independent of the Hessian the oracle assembles."""
+    I, J, F, N = shape
+    p = make_problem(I, J, F, N, seed=81 + I)
+    V = ffa.weighted_covariances(p.y, p.v0, p.lam0)
+    D = ffa.newton_P(p.P0, V, 1.0, counter=OpCounter()) - p.P0
+    h = 1e-6 / np.abs(D).max()
+    dG = (_G(p.P0 + h * D, V) - _G(p.P0 - h * D, V)) / (2 * h)
+    G0 = _G(p.P0, V)
+    assert np.abs(G0 + dG).max() <= 1e-6 * np.abs(G0).max()
+
+
+def test_newton_converges_quadratically_near_a_stationary_point():
+    Ps, V = _stationary()
+    rng = np.random.default_rng(0)
+    P = Ps * (1 + 0.05 * (rng.standard_normal(Ps.shape) + 1j * rng.standard_normal(Ps.shape)))
+    err = []
+    for _ in range(4):
+        P = ffa.newton_P(P, V, 1.0, counter=OpCounter())
+        err.append(np.abs(_G(P, V)).max())
+    assert err[1] < 1e-2 and err[2] < 1e-5 and err[3] < 1e-10, err
+    assert err[3] < 1e3 * err[2] ** 2 + 1e-13  # quadratic (a linear rate would leave ~1e-8)
+    np.testing.assert_allclose(ffa.newton_P(Ps, V, 1.0, counter=OpCounter()), Ps, rtol=1e-10, atol=1e-12)
+
+
+def test_newton_scalar_closed_form():
+    """I = 1: l = ln|p|^2 - V |p|^2 depends on r = |p| only; Newton in r is
+    r <- r - l'(r) / l''(r) = 2 r / (1 + V r^2), the phase unchanged."""
+    p = make_problem(1, 2, 4, 23, seed=91)
+    sigma = np.einsum("jfn,fj->fn", p.v0, p.lam0[:, :, 0])
+    Vs = np.mean(np.abs(p.y[0]) ** 2 / sigma, axis=1)
+    q = p.P0[:, 0, 0]
+    V = ffa.weighted_covariances(p.y, p.v0, p.lam0)
+    got = ffa.newton_P(p.P0, V, 1.0, counter=OpCounter())[:, 0, 0]
+    np.testing.assert_allclose(got, q * 2.0 / (1.0 + Vs * np.abs(q) ** 2), rtol=1e-10)
+
+
+def test_newton_inversion_count():
+    p = make_problem(3, 3, 5, 30, seed=72)
+    c = OpCounter()
+    ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, K=3, counter=c, p_update="newton", mu=1.0)
+    assert c.inversions == 2 * 3 * 5 * 2
