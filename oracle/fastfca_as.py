@@ -174,7 +174,8 @@ def _real_basis(I):
 def newton_P(P, V, mu=1.0, K=1, counter=COUNTER):
     """K steps of Newton's method on L2 / N as a function of P with the V_i
     of Eq. FPI fixed (another of the alternatives named in Sec. 4.6; reading:
-    the exact Newton step in the 2 I^2 real coordinates of P, scaled by mu).
+    the Newton step in the 2 I^2 real coordinates of P, restricted to the
+    directions that change L2, scaled by mu).
 
     With l(P) = ln|det P|^2 - sum_i p_i^H V_i p_i (L2 / N up to terms free
     of P), the first and second differentials along complex directions D,
@@ -183,16 +184,19 @@ def newton_P(P, V, mu=1.0, K=1, counter=COUNTER):
         d2l[D, D'] = -2 Re tr(P^{-1} D P^{-1} D') - 2 Re sum_i d_i^H V_i d'_i
     (from ln det(P + D) = ln det P + tr(P^{-1} D) - tr(P^{-1} D P^{-1} D) / 2
     + ...).  In the real basis E_k the gradient is g_k = dl[E_k] and the
-    Hessian H_kl = d2l[E_k, E_l]; the step is the minimum-norm solution of
-    H s = -g (the pseudo-inverse of H) and moves P by mu sum_k s_k E_k.
-    Reading: l is invariant under p_i -> e^{i theta} p_i, so H is singular
-    along the I directions i p_i (the gradient has no component there) and
-    the step leaves the column phases alone.  Two inversions per frequency
-    per step: P and the 2 I^2 x 2 I^2 Hessian.  Newton's method converges
-    quadratically near a nondegenerate stationary point and is not globally
-    convergent (H is indefinite away from it); mu damps the step."""
+    Hessian H_kl = d2l[E_k, E_l].  l does not change when a column turns in
+    phase (p_i -> e^{i theta} p_i), so the I directions i p_i carry no
+    information (g is orthogonal to them, and at a stationary point H is
+    singular along them): with Pi the orthogonal projector onto them and
+    Q = 1 - Pi, the step solves (Q H Q - Pi) s = -Q g, i.e. the Newton step
+    within the directions orthogonal to the phase turns, and moves P by
+    mu sum_k s_k E_k.  Two inversions per frequency per step: P and the
+    2 I^2 x 2 I^2 system.  Newton's method converges quadratically near a
+    nondegenerate stationary point and is not globally convergent (H is
+    indefinite away from it); mu damps the step."""
     F, I, _ = P.shape
     E = _real_basis(I)
+    eye = np.eye(2 * I * I)[None]
     P = P.copy()
     for _ in range(K):
         Pinv = np.linalg.inv(P)
@@ -202,7 +206,15 @@ def newton_P(P, V, mu=1.0, K=1, counter=COUNTER):
         A = np.einsum("fab,kbc->fkac", Pinv, E)                   # P^{-1} E_k
         H = -2.0 * np.real(np.einsum("fkab,flba->fkl", A, A))     # -2 Re tr(P^{-1}E_k P^{-1}E_l)
         H -= 2.0 * np.real(np.einsum("kai,fiab,lbi->fkl", E.conj(), V, E))
-        s = np.einsum("fkl,fl->fk", np.linalg.pinv(H, rcond=1e-10, hermitian=True), -g)
+        # the phase-turn directions i p_i in real coordinates, orthonormalised
+        turn = np.zeros((F, I, I, I), dtype=np.complex128)      # [f, column i, a, c]
+        for i in range(I):
+            turn[:, i, :, i] = 1j * P[:, :, i]
+        Nt = np.concatenate([turn.real.reshape(F, I, -1), turn.imag.reshape(F, I, -1)], axis=2)
+        Qn, _ = np.linalg.qr(Nt.transpose(0, 2, 1))               # [F, 2 I^2, I]
+        Pi = Qn @ Qn.transpose(0, 2, 1)
+        Qp = eye - Pi
+        s = np.linalg.solve(Qp @ H @ Qp - Pi, -np.einsum("fkl,fl->fk", Qp, g)[..., None])[..., 0]
         counter.inversions += F  # the 2 I^2 x 2 I^2 system
         P = P + mu * np.einsum("fk,kai->fai", s, E)
     return P

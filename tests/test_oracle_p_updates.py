@@ -150,19 +150,36 @@ def _G(P, V):
     return np.linalg.inv(P).conj().transpose(0, 2, 1) - np.einsum("fiab,fbi->fai", V, P)
 
 
+def _real(D):
+    """Real coordinates of complex I x I matrices (real parts, then imaginary)."""
+    F = D.shape[0]
+    return np.concatenate([D.real.reshape(F, -1), D.imag.reshape(F, -1)], axis=1)
+
+
 @pytest.mark.parametrize("shape", [(3, 3, 2, 60), (2, 3, 3, 40), (4, 2, 2, 80)])
 def test_newton_step_zeroes_the_linearised_gradient(shape):
-    """The Newton step D satisfies G(P) + dG[D] = 0 (the stationarity of the
-    second-order model), with dG[D] by central differences of the gradient
-    of Eq. partialP, independent of the Hessian the oracle assembles."""
+    """The Newton step D makes the second-order model stationary in every
+    direction that changes L2: the first-order change of the gradient along
+    D, dG[D] by central differences of Eq. partialP (independent of the
+    Hessian the oracle assembles), cancels G up to the column-phase
+    directions i p_i, and D has no component along those."""
     I, J, F, N = shape
     p = make_problem(I, J, F, N, seed=81 + I)
     V = ffa.weighted_covariances(p.y, p.v0, p.lam0)
-    D = ffa.newton_P(p.P0, V, 1.0, counter=OpCounter()) - p.P0
+    P = p.P0
+    D = ffa.newton_P(P, V, 1.0, counter=OpCounter()) - P
     h = 1e-6 / np.abs(D).max()
-    dG = (_G(p.P0 + h * D, V) - _G(p.P0 - h * D, V)) / (2 * h)
-    G0 = _G(p.P0, V)
-    assert np.abs(G0 + dG).max() <= 1e-6 * np.abs(G0).max()
+    R = _G(P, V) + (_G(P + h * D, V) - _G(P - h * D, V)) / (2 * h)   # dl-residual, Wirtinger form
+    def turn(i):  # the direction that turns column i in phase: i p_i in column i, zero elsewhere
+        T = np.zeros_like(P)
+        T[:, :, i] = 1j * P[:, :, i]
+        return _real(T)
+    turns = np.stack([turn(i) for i in range(I)], axis=2)         # [F, 2 I^2, I]
+    Qn, _ = np.linalg.qr(turns)
+    Qp = np.eye(2 * I * I)[None] - Qn @ Qn.transpose(0, 2, 1)
+    r = np.einsum("fkl,fl->fk", Qp, _real(R))                   # residual off the phase directions
+    assert np.abs(r).max() <= 1e-6 * np.abs(_G(P, V)).max()
+    assert np.abs(np.einsum("fki,fk->fi", Qn, _real(D))).max() <= 1e-10 * np.abs(D).max()
 
 
 def test_newton_converges_quadratically_near_a_stationary_point():
