@@ -161,6 +161,29 @@ def natural_gradient_P(P, V, mu, K=1):
     return P
 
 
+def em_covariances(y, v, lam, P, v_new, lam_new):
+    """The matrices of the M-step for P in the normal EM algorithm (the other
+    alternative named in Sec. 4.6).  Reading: the complete data are the
+    source images x_j of Eq. fullrank, x_j ~ CN(0, v_j P^{-H} Lambda_j P^{-1})
+    (Eq. diagconst); the expected complete-data log-likelihood is, over P,
+        J N ln|det P|^2 - sum_i p_i^H W_i p_i,
+        W_i = sum_{n,j} E[x_j x_j^H | y] / (v_j lambda_ji)
+    with the posterior of the current (v, Lambda, P) and the new v, Lambda of
+    Eqs. updatev and Lambdaupdate (whose updates are the same in the normal
+    EM).  E[x_j x_j^H | y] = P^{-H} (mu~_j mu~_j^H + diag(phi~_j)) P^{-1}
+    with mu~, phi~ of Eqs. mutilde0 / Phitilde0.  Setting the derivative in
+    P^* to zero gives Eq. FPI's form with V_i replaced by W_i / (J N), which
+    is returned, [F, I(i), I, I]."""
+    J, I, F, N = v.shape[0], y.shape[0], y.shape[1], y.shape[2]
+    mu, phi = e_step(y, v, lam, P)                                     # [J, I, F, N]
+    T = np.einsum("jafn,jbfn,jfn->fjab", mu, mu.conj(), 1.0 / v_new)  # sum_n mu~ mu~^H / v_j
+    T[:, :, np.arange(I), np.arange(I)] += np.einsum("jafn,jfn->fja", phi, 1.0 / v_new)
+    Om = np.einsum("fjab,fji->fiab", T, 1.0 / lam_new)                 # sum_j T_j / lambda_ji
+    PinvH = np.linalg.inv(P).conj().transpose(0, 2, 1)
+    W = np.einsum("fac,ficd,fbd->fiab", PinvH, Om, PinvH.conj())       # P^{-H} Om_i P^{-1}
+    return W / (J * N)
+
+
 def _real_basis(I):
     """The 2 I^2 real directions of C^{I x I}: E_k = e_a e_i^T (k < I^2) and
     i e_a e_i^T (k >= I^2), k = a I + i within each half."""
@@ -258,6 +281,10 @@ def hybrid_iteration(y, v, lam, P, K=1, counter=COUNTER, p_update="fpi", mu=0.0)
     update of P with the new v and Lambda: the fixed-point iteration (Eq. FPI,
     K sweeps) or, with p_update = "gradient" / "natural_gradient", K steps of
     size mu of one of the alternatives named in Sec. 4.6."""
+    if p_update == "em":  # the normal EM: Eq. FPI's form on the M-step's matrices
+        v_new, lam_new = em_half(y, v, lam, P)
+        P = fixed_point_P(P, em_covariances(y, v, lam, P, v_new, lam_new), K, counter)
+        return v_new, lam_new, P
     v, lam = em_half(y, v, lam, P)
     V = weighted_covariances(y, v, lam)
     if p_update == "fpi":

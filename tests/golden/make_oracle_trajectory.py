@@ -20,7 +20,7 @@ from oracle.fastfca_as import OpCounter  # noqa: E402
 from paper_1805_09498_gb300.synth import make_problem  # noqa: E402
 
 CASE = dict(I=3, J=3, F=3, N=64, seed=123, iters=5, K=1)
-UPDATES = [("fpi", 0.0), ("gradient", 0.05), ("natural_gradient", 0.2), ("newton", 1.0)]
+UPDATES = [("fpi", 0.0), ("gradient", 0.05), ("natural_gradient", 0.2), ("newton", 1.0), ("em", 0.0)]
 
 
 def trajectories():

@@ -150,6 +150,15 @@ def _newton_no_logdet_curvature(P, V, mu=1.0, K=1, counter=ffa.COUNTER):  # Hess
 
 FCA_MUTANTS = [("e_step", _fca_phi_plus), ("m_step", _fca_v_without_inverse), ("m_step", _fca_outer_transposed)]
 
+def _em_no_phi(y, v, lam, P, v_new, lam_new):  # the posterior covariance term dropped
+    J, I, N = v.shape[0], y.shape[0], y.shape[2]
+    mu, _ = ffa.e_step(y, v, lam, P)
+    T = np.einsum("jafn,jbfn,jfn->fjab", mu, mu.conj(), 1.0 / v_new)
+    Om = np.einsum("fjab,fji->fiab", T, 1.0 / lam_new)
+    PinvH = np.linalg.inv(P).conj().transpose(0, 2, 1)
+    return np.einsum("fac,ficd,fbd->fiab", PinvH, Om, PinvH.conj()) / (J * N)
+
+
 MUTANTS = [
     ("basis_transform", _bt_no_conj), ("model_variances", _sigma_wrong_source),
     ("e_step", _estep_no_correction), ("e_step", _estep_conj_mean),
@@ -158,7 +167,7 @@ MUTANTS = [
     ("fixed_point_P", _fpi_v_transposed), ("loglik_terms", _ll_no_pi), ("loglik_terms", _ll_det_once),
     ("wiener", _wiener_p_inverse), ("em_half", _em_lambda_with_old_v),
     ("gradient_P", _grad_no_conj), ("natural_gradient_P", _natgrad_no_h),
-    ("newton_P", _newton_no_logdet_curvature),
+    ("newton_P", _newton_no_logdet_curvature), ("em_covariances", _em_no_phi),
 ]
 
 # every pin on one of its cases (two where I = J would hide a mix-up of I and J)
@@ -178,6 +187,7 @@ PINS = [
     (pu.test_natural_gradient_step_slope, dict(shape=pu.SHAPES[0])),
     (pu.test_natural_gradient_is_equivariant, {}),
     (pu.test_newton_step_zeroes_the_linearised_gradient, dict(shape=(3, 3, 2, 60))),
+    (pu.test_em_matrices_are_the_dense_posterior_moments, dict(shape=(3, 3, 2, 7))),
 ]
 
 

@@ -212,3 +212,52 @@ def test_newton_inversion_count():
     c = OpCounter()
     ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, K=3, counter=c, p_update="newton", mu=1.0)
     assert c.inversions == 2 * 3 * 5 * 2
+
+
+# ------------------------------------------------------- the normal EM for P
+@pytest.mark.parametrize("shape", [(3, 3, 2, 7), (2, 3, 2, 6), (4, 2, 1, 9), (1, 2, 2, 5)])
+def test_em_matrices_are_the_dense_posterior_moments(shape):
+    """W_i / (J N) of the normal EM from the transformed posterior equals the
+    sum over n, j of the dense posterior second moments E[x_j x_j^H | y] =
+    mu_j mu_j^H + Phi_j (the FCA oracle's Eqs. MMSE / postquadexp with
+    S_j = P^{-H} Lambda_j P^{-1}) over v_j^new lambda_ji^new."""
+    from oracle import fca
+    I, J, F, N = shape
+    p = make_problem(I, J, F, N, seed=101 + I)
+    vn, ln = ffa.em_half(p.y, p.v0, p.lam0, p.P0)
+    W = ffa.em_covariances(p.y, p.v0, p.lam0, p.P0, vn, ln)
+    mu, Phi = fca.e_step(p.y, p.v0, fca.spatial_from_joint(p.P0, p.lam0), counter=OpCounter())
+    C = mu[..., :, None] * mu[..., None, :].conj() + Phi
+    ref = np.einsum("jfnab,jfn,fji->fiab", C, 1.0 / vn, 1.0 / ln) / (J * N)
+    np.testing.assert_allclose(W, ref, rtol=1e-11, atol=1e-13 * np.abs(ref).max())
+
+
+def test_em_m_step_for_p_ascends_and_the_em_step_does_not_decrease_loglik():
+    """With the M-step for P run to its stationary point (Eq. FPI on the
+    M-step's matrices, with the column rescaling of the fixed-point pins),
+    the expected complete-data log-likelihood rises over P and the whole EM
+    step does not decrease L2 (the EM guarantee)."""
+    p = make_problem(3, 3, 3, 120, seed=111)
+    vn, ln = ffa.em_half(p.y, p.v0, p.lam0, p.P0)
+    W = ffa.em_covariances(p.y, p.v0, p.lam0, p.P0, vn, ln)
+
+    def q(P):  # the P-dependent part of the expected complete-data log-likelihood / (J N)
+        _, la = np.linalg.slogdet(P)
+        return 2 * la - np.einsum("fai,fiab,fbi->f", P.conj(), W, P).real
+
+    P = p.P0.copy()
+    for _ in range(800):
+        P = ffa.fixed_point_P(P, W, K=1, counter=OpCounter())
+        d = np.einsum("fai,fiab,fbi->fi", P.conj(), W, P).real
+        P = P / np.sqrt(d)[:, None, :]
+    G = np.linalg.inv(P).conj().transpose(0, 2, 1) - np.einsum("fiab,fbi->fai", W, P)
+    assert np.abs(G).max() < 1e-9
+    assert np.all(q(P) >= q(p.P0) - 1e-12)
+    assert ffa.loglik(p.y, vn, ln, P) >= ffa.loglik(p.y, p.v0, p.lam0, p.P0)
+
+
+def test_em_iterations_rise():
+    """K = 1 sweep per M-step (the hybrid's budget): monitored, L2 rises."""
+    p = make_problem(3, 3, 4, 200, seed=121)
+    _, _, _, tr = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 6, counter=OpCounter(), p_update="em")
+    assert np.all(np.diff(tr) > 0), np.diff(tr)
