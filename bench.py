@@ -45,6 +45,20 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def sources_hash() -> str:
+    """Hash of the CUDA sources and the C header (names and contents): the
+    key under which measured DRAM traffic is stored, so that figures taken on
+    other kernel sources are not reported."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_1805_09498_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for f in sorted(os.listdir(d)):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources; else None."""
@@ -54,7 +68,6 @@ def _ncu_traffic(kernel: str):
     except OSError:
         return None
     k = t.get("kernels", {}).get(kernel)
-    from paper_1805_09498_gb300.profile_traffic import sources_hash
     if not k or t.get("csrc_sha") != sources_hash():
         return None
     return k.get("dram_bytes_per_launch")
@@ -734,6 +747,42 @@ def cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_gpu):
                       "(numpy FP64, one thread)", "seconds": dt, "error_vs_oracle": err}
 
 
+# ---------------------------------------------------------------- profiling case
+def run_case(a):
+    """One fixed, small run for kernel profiling (e.g. under ncu), not timed:
+    `iters` hybrid iterations and one Wiener pass of a seeded mixture of the
+    given shape (P drawn with alpha = 0.3, cond < 10, or alpha = 0.2,
+    cond < 50 for I = 8), or with --case-batch M, a batch of M mixtures with
+    lengths uniform in [200, 4000] through the batch API."""
+    import torch
+    from paper_1805_09498_gb300 import build as _build
+    from paper_1805_09498_gb300 import ffca
+    _build.build()
+    alpha, kappa = (0.2, 50.0) if a.case_I == 8 else (0.3, 10.0)
+    if a.case_batch:
+        cdt = torch.complex64 if a.case_prec == "mixed" else torch.complex128
+        Ns = batch_lengths(a.case_batch, 200, 4000, seed=17)
+        y, v, lam, P, Ns, _ = make_batch_device(a.case_I, a.case_J, a.case_F, Ns, seed=23, device="cuda",
+                                                alpha=alpha, kappa=kappa, complex_dtype=cdt)
+        est = ffca.FastFCABatch(y, v, lam, P, Ns)
+        if a.case_p_update != "fixed_point":
+            est.set_p_update(a.case_p_update, a.case_mu)
+        tr = est.iterate(a.case_iters)
+        torch.cuda.synchronize()
+        est.close()
+    else:
+        p = make_problem(a.case_I, a.case_J, a.case_F, a.case_N, seed=0, alpha=alpha, kappa=kappa)
+        yd, vd, lamd, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec=a.case_prec)
+        est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+        if a.case_p_update != "fixed_point":
+            est.set_p_update(a.case_p_update, a.case_mu)
+        tr = est.iterate(a.case_iters)
+        est.wiener()
+        torch.cuda.synchronize()
+        est.close()
+    print("case done; L2 trace:", tr[0], "->", tr[-1])
+
+
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, cfg, rank, ws):
     """The FP64 oracle on the host cores as the reference arm: each step is one
@@ -777,7 +826,21 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--case", action="store_true",
+                    help="run one small untimed case for profiling (the --case-* options) and exit")
+    ap.add_argument("--case-I", type=int, default=3)
+    ap.add_argument("--case-J", type=int, default=3)
+    ap.add_argument("--case-F", type=int, default=513)
+    ap.add_argument("--case-N", type=int, default=8000)
+    ap.add_argument("--case-iters", type=int, default=2)
+    ap.add_argument("--case-prec", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--case-batch", type=int, default=0, help="mixtures of a batch (0: one mixture)")
+    ap.add_argument("--case-p-update", default="fixed_point")
+    ap.add_argument("--case-mu", type=float, default=0.0)
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     cfg = CONFIGS[WORKLOAD]
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

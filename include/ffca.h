@@ -250,8 +250,12 @@ ffca_status ffca_timing_read(ffca_ctx* ctx, double* ms, unsigned long long* laun
  *  - desc: as for ffca_init; desc->workspace and desc->workspace_bytes are
  *    ignored.  Problems whose workspace (ffca_workspace_size) exceeds
  *    FFCA_NOALLOC_SCRATCH_BYTES are rejected with FFCA_ERR_ARG.
- *  - iters, ll_trace: as for ffca_iterate.  The call always synchronises
- *    desc->stream and returns the device status.
+ *  - iters, ll_trace: as for ffca_iterate.  Once the call has enqueued
+ *    work it waits for desc->stream before it returns, on success (then
+ *    returning the device status) and on every error alike, so that none of
+ *    its kernels still uses the shared array when the next call clears it.
+ *    Errors found before anything is enqueued (bad sizes, too large a
+ *    problem) return at once.
  *  - The first call on a device looks up the array's device address (once
  *    per device, with that device current); make that first call before any
  *    stream capture.

@@ -277,10 +277,22 @@ def em_half(y, v, lam, P):
 
 
 def hybrid_iteration(y, v, lam, P, K=1, counter=COUNTER, p_update="fpi", mu=0.0):
-    """One iteration of the hybrid algorithm (Sec. 4.4): the EM half, then the
-    update of P with the new v and Lambda: the fixed-point iteration (Eq. FPI,
-    K sweeps) or, with p_update = "gradient" / "natural_gradient", K steps of
-    size mu of one of the alternatives named in Sec. 4.6."""
+    """One iteration of the hybrid algorithm (Sec. 4.4): the EM half, then an
+    update of P.  p_update selects it (the four alternatives are those Sec.
+    4.6 names in place of the fixed-point iteration):
+
+      "fpi"               Eq. FPI, K sweeps with the V_i of the new v, Lambda;
+                          mu is not used.
+      "gradient"          K gradient-ascent steps of size mu (gradient_P).
+      "natural_gradient"  K natural-gradient steps of size mu
+                          (natural_gradient_P).
+      "newton"            K Newton steps scaled by mu (newton_P); mu = 0 is
+                          taken as the undamped step mu = 1.
+      "em"                the normal EM: K sweeps of Eq. FPI's form on the
+                          M-step matrices W_i / (J N) of em_covariances, which
+                          use the posterior of the entering state; mu is not
+                          used.
+    """
     if p_update == "em":  # the normal EM: Eq. FPI's form on the M-step's matrices
         v_new, lam_new = em_half(y, v, lam, P)
         P = fixed_point_P(P, em_covariances(y, v, lam, P, v_new, lam_new), K, counter)

@@ -840,6 +840,8 @@ extern "C" ffca_status ffca_iterate_noalloc(const ffca_desc* d, int iters, doubl
   c.gcntB = reinterpret_cast<unsigned*>(c.ws + 20);
   c.ops = reinterpret_cast<unsigned long long*>(c.ws + 32);
   c.err_f = -1;
+  c.M = 1;  // as ffca_init: one mixture of F frequencies
+  c.Fm = dd.F;
   if (dd.F == 0) {
     if (ll_trace)
       for (int t = 0; t <= iters; ++t) ll_trace[t] = 0.0;
@@ -847,9 +849,18 @@ extern "C" ffca_status ffca_iterate_noalloc(const ffca_desc* d, int iters, doubl
   }
   // The previous call left its partials, counters and status in the shared
   // scratch: the counters and the status word must start at zero.
-  if (cudaMemsetAsync(c.ws, 0, p.bytes, c.stream) != cudaSuccess) return FFCA_ERR_CUDA;
+  // Every return after the first enqueue waits for the stream first, so that
+  // no kernel of this call still uses the shared scratch when the next call
+  // clears it (the wait's own result is not the call's error).
+  if (cudaMemsetAsync(c.ws, 0, p.bytes, c.stream) != cudaSuccess) {
+    cudaStreamSynchronize(c.stream);
+    return FFCA_ERR_CUDA;
+  }
   st = ffca_iterate(&c, iters, ll_trace);
-  if (st != FFCA_OK) return st;
+  if (st != FFCA_OK) {
+    cudaStreamSynchronize(c.stream);
+    return st;
+  }
   return read_status(&c);
 }
 
