@@ -151,6 +151,64 @@ def _sample_freqs(F: int, S: int) -> np.ndarray:
     return np.unique(np.linspace(0, F - 1, S).round().astype(int))
 
 
+# ---------------------------------------------------------------- the oracle on the host cores
+def _oracle_job(job):
+    """One worker's share of an oracle run (a block of frequencies; the
+    frequencies of the method are independent problems).  Returns the
+    oracle's outputs and the worker's own seconds."""
+    from oracle import fastfca_as as ffa
+    from oracle import fca
+    from oracle.fastfca_as import OpCounter
+    kind, args = job
+    t = time.perf_counter()
+    if kind == "fastfca":
+        y, v, lam, P, iters, p_update = args
+        out = ffa.iterate(y, v, lam, P, iters, counter=OpCounter(), p_update=p_update)
+    else:
+        y, v, S, iters = args
+        out = fca.iterate(y, v, S, iters, counter=OpCounter())
+    return out, time.perf_counter() - t
+
+
+class OraclePool:
+    """Worker processes for the FP64 oracle on the host cores, one numpy
+    thread each.  Started with `spawn` (the parent has a CUDA context, which a
+    forked child must not inherit); jobs are blocks of frequencies."""
+
+    def __init__(self, workers: int | None = None):
+        import multiprocessing as mp
+        self.workers = workers or os.cpu_count() or 1
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"  # inherited by the spawned workers
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.workers)
+            self.pool.map(_oracle_job, [("fastfca", (np.ones((1, 1, 4), complex), np.ones((1, 1, 4)),
+                                                     np.ones((1, 1, 1)), np.ones((1, 1, 1), complex), 1, "fpi"))]
+                          * self.workers)  # import the oracle in every worker before timing
+        finally:
+            for k, val in saved.items():
+                if val is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = val
+
+    def run(self, jobs):
+        """Runs the jobs over the workers; returns (results, wall seconds)."""
+        t = time.perf_counter()
+        res = self.pool.map(_oracle_job, jobs, chunksize=1)
+        return res, time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _fastfca_jobs(y, v, lam, P, iters, blocks, p_update="fpi"):
+    fb = np.array_split(np.arange(y.shape[1]), blocks)
+    return [("fastfca", (y[:, b], v[:, b], lam[b], P[b], iters, p_update)) for b in fb if len(b)]
+
+
 # ---------------------------------------------------------------- ours
 def run_ours(args, cfg, rank, ws, local, dist):
     import torch
@@ -354,6 +412,9 @@ def run_ours(args, cfg, rank, ws, local, dist):
 
     if rank != 0:
         return None
+    pool = OraclePool()
+    plain = run_plain_fp64(args, dev, pool)
+    em = run_em(args, p, cfg, dev)
     batched = run_batched(args, dev)
     large = run_large_array(args, dev)
     adjoint = run_adjoint(dev)
@@ -383,7 +444,8 @@ def run_ours(args, cfg, rank, ws, local, dist):
 
     cpu = None
     if ws == 1:
-        cpu = cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_acc)
+        cpu = cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_acc, pool)
+    pool.close()
 
     launches = int(sum(n for _, n in counts.values()))
     kernels["timing"] = ("CUDA events around every launch over a second run of the same steps "
@@ -404,11 +466,226 @@ def run_ours(args, cfg, rank, ws, local, dist):
         "speedup_mixed_vs_fp64_gpu": (value / ws / fp64["value"]) if fp64 else None,
         "fca_gpu": fca_line,
         "speedup_vs_fca_gpu": (value / ws / fca_line["value"]) if fca_line else None,
+        "plain_fp64": plain,
+        "em_update": em,
+        "paper_context": ("the paper reports FastFCA-AS more than 420 times faster than conventional FCA "
+                          "in parameter estimation (real-time factor; Sec. 5, MATLAB R2013a on an Intel "
+                          "i7-2600 at 3.4 GHz, I = J = 3, 8 s mixtures at 16 kHz, 20 iterations): context "
+                          "only, other hardware and software"),
+        "host_cores": os.cpu_count(),
+        "l2_per_point_after_fixed_point": float(tr_acc[-1] / (N * F)),
         "batched": batched,
         "large_array": large,
         "adjoint": adjoint,
         "stft_front_end": front,
     }
+
+
+def _ncu_fp64(kernel: str):
+    """FP64 operations per launch of `kernel` (2 per DFMA, 1 per DMUL / DADD,
+    from ncu's executed-instruction counters) in the committed summary, if it
+    was taken on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_fp64.json")) as fh:
+            t = json.load(fh)
+    except OSError:
+        return None
+    k = t.get("kernels", {}).get(kernel)
+    if not k or t.get("csrc_sha") != sources_hash():
+        return None
+    return k
+
+
+def run_plain_fp64(args, dev, pool):
+    """The plain FP64 workload: I = J = 3, F = 257, N = 600, 20 iterations,
+    every per-point operation in FP64; launch-bound at this size, so the
+    timed runs replay the iteration loop from a CUDA graph (and, beside it,
+    plain launches with the L2 trace).  The conventional FCA EM on the GPU on
+    the same data and precision; the FP64 oracle (FastFCA-AS and FCA) on the
+    whole workload on one host core and on all of them; the FP64-ALU fraction
+    of the two streaming passes against the measured FP64 rate."""
+    import torch
+    from oracle import fastfca_as as ffa
+    from oracle import fca
+    from oracle.fastfca_as import OpCounter
+    from paper_1805_09498_gb300 import ffca
+    cfg = CONFIGS["plain_fp64"]
+    I, J, F, N, iters = cfg["I"], cfg["J"], cfg["F"], cfg["N"], cfg["iters"]
+    p = make_problem(I, J, F, N, seed=2, alpha=cfg["alpha"], kappa=cfg["kappa"])
+    yd, vd, lamd, Pd, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64", device=dev)
+    v0, l0, P0 = vd.clone(), lamd.clone(), Pd.clone()
+    stream = torch.cuda.current_stream(dev)
+    units = N * F * iters
+
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def reset():
+        vd.copy_(v0); lamd.copy_(l0); Pd.copy_(P0)
+
+    est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+    tr = est.iterate(iters)
+    vg, lg, Pg = vd[:, :, :N].cpu().numpy(), lamd.cpu().numpy(), Pd.cpu().numpy()
+    t0 = time.perf_counter()
+    rv, rl, rP, rt = ffa.iterate(p.y, p.v0, p.lam0, p.P0, iters, counter=OpCounter())
+    one_core_s = time.perf_counter() - t0
+    _, all_s = pool.run(_fastfca_jobs(p.y, p.v0, p.lam0, p.P0, iters, pool.workers))
+
+    def relerr(a_, b_, ax):
+        a_ = np.moveaxis(a_, ax, 0).reshape(F, -1)
+        b_ = np.moveaxis(b_, ax, 0).reshape(F, -1)
+        return float(np.max(np.linalg.norm(a_ - b_, axis=1) / np.linalg.norm(b_, axis=1)))
+    err = {"v": relerr(vg, rv, 1), "lambda": relerr(lg, rl, 0), "P": relerr(Pg, rP, 0),
+           "loglik_rel": float(np.max(np.abs(tr - rt) / np.abs(rt))),
+           "measure": f"all {F} frequencies after {iters} iterations; normwise relative per frequency (max); "
+                      "L2 trace relative (max over the trace)"}
+    reps = 20
+    est.set_graph(True)
+    reset()
+    for _ in range(3):
+        est.iterate(iters, trace=False)
+    ms_graph = timed(lambda: est.iterate(iters, trace=False), reps)
+    est.set_graph(False)
+    ms_trace = timed(lambda: est.iterate(iters), 5)
+    ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, True)
+    est.iterate(iters, trace=False)
+    kt = ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, False)
+    est.close()
+    peak64 = ffca.ffca_peak_fp64(stream)
+    kernels = {}
+    for k, kname, bpt in (("estep", "k_estep<double, 3, 3, 1, 0>", I * 16 + 2 * J * 8),
+                          ("wcov", "k_wcov<double, 3, 3>", I * 16 + J * 8), ("psolve", None, 0)):
+        kms, kn = kt[k]
+        if not kn:
+            continue
+        us = kms / kn * 1e3
+        kernels[k] = {"launches": kn, "avg_us": us}
+        if bpt:
+            kernels[k]["hbm_gbs"] = bpt * N * F / (us * 1e-6) / 1e9
+            ops = _ncu_fp64(kname)
+            if ops:
+                ach = ops["fp64_flops_per_launch"] / (us * 1e-6) / 1e9
+                kernels[k]["fp64"] = {"achieved_gflops": ach, "peak_gflops": peak64, "frac": ach / peak64,
+                                      "flops_per_launch": ops["fp64_flops_per_launch"],
+                                      "ncu_fp64_pipe_pct": ops.get("fp64_pipe_pct"),
+                                      "peak": "measured by ffca_peak_fp64 in this run"}
+    # the conventional FCA EM on the GPU, same data, FP64 (S_j = P^{-H} Lambda_j P^{-1} of the initial state)
+    S0h = fca.spatial_from_joint(p.P0, p.lam0)
+    S0 = torch.from_numpy(S0h).to(dev)
+    vf = v0.clone()
+    ef = ffca.FCA(yd, vf, S0, N=N)
+    trf = ef.iterate(iters)
+    fv, fS = vf[:, :, :N].cpu().numpy(), S0.cpu().numpy()
+    t0 = time.perf_counter()
+    frv, frS, frt = fca.iterate(p.y, p.v0, S0h, iters, counter=OpCounter())
+    fca_one_s = time.perf_counter() - t0
+    _, fca_all_s = pool.run([("fca", (p.y[:, b], p.v0[:, b], S0h[b], iters))
+                             for b in np.array_split(np.arange(F), pool.workers) if len(b)])
+    fca_err = {"v": relerr(fv, frv, 1), "S": relerr(fS, frS, 0),
+               "loglik_rel": float(np.max(np.abs(trf - frt) / np.abs(frt)))}
+    vf.copy_(v0); S0.copy_(torch.from_numpy(S0h).to(dev))
+    ef.iterate(1, trace=False)
+    ms_fca = timed(lambda: ef.iterate(iters, trace=False), 5)
+    ef.close()
+    del yd, vd, lamd, Pd, v0, l0, P0, vf, S0
+    torch.cuda.empty_cache()
+    return {"workload": f"plain_fp64: I={I} J={J} F={F} N={N}, c128, FP64 throughout, {iters} iterations",
+            "value": units / (ms_graph * 1e-3), "unit": UNIT, "ms_per_run": ms_graph,
+            "timing": "graph replay of the 20 iterations (launch-bound size), CUDA events, 20 runs",
+            "with_trace": {"value": units / (ms_trace * 1e-3), "ms_per_run": ms_trace,
+                           "how": "plain launches, L2 trace copied back"},
+            "kernels": kernels, "fp64_peak_gflops_measured": peak64,
+            "error_vs_oracle": err,
+            "oracle": {"one_core": {"value": units / one_core_s, "seconds": one_core_s, "cores": 1},
+                       "all_cores": {"value": units / all_s, "seconds": all_s, "cores": pool.workers},
+                       "sample": "the whole workload (every frequency, frame and iteration)"},
+            "fca_gpu": {"value": units / (ms_fca * 1e-3), "ms_per_run": ms_fca, "error_vs_oracle": fca_err,
+                        "precision": "fp64"},
+            "fca_oracle": {"one_core": {"value": units / fca_one_s, "seconds": fca_one_s, "cores": 1},
+                           "all_cores": {"value": units / fca_all_s, "seconds": fca_all_s,
+                                         "cores": pool.workers}},
+            "speedup_vs_fca_gpu": ms_fca / ms_graph,
+            "speedup_vs_oracle_all_cores": (units / (ms_graph * 1e-3)) / (units / all_s),
+            "speedup_oracle_fastfca_vs_fca": fca_one_s / one_core_s}
+
+
+def run_em(args, p, cfg, dev):
+    """The normal EM update of P (Sec. 4.6) on the long mixture: the same
+    iterations per step with one streaming pass each (pass A with the EM
+    sums, 48 B per point at I = J = 3) and the per-problem EM step instead
+    of pass B and the fixed point; timed like the headline (trace copied
+    back every step).  Beside it the error against the FP64 oracle's EM
+    iterations on sampled frequencies and the L2 per point reached by both
+    updates after the same iterations."""
+    import torch
+    from oracle import fastfca_as as ffa
+    from oracle.fastfca_as import OpCounter
+    from paper_1805_09498_gb300 import ffca
+    I, J, F, N, iters = cfg["I"], cfg["J"], cfg["F"], cfg["N"], cfg["iters"]
+    yd, vd, lamd, Pd, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed", device=dev)
+    v0, l0, P0 = vd.clone(), lamd.clone(), Pd.clone()
+    stream = torch.cuda.current_stream(dev)
+    est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
+    est.set_p_update("em")
+    tr = est.iterate(iters)
+    fs = _sample_freqs(F, 4)
+    vg, lg, Pg = vd[:, fs, :N].double().cpu().numpy(), lamd[fs].cpu().numpy(), Pd[fs].cpu().numpy()
+    t0 = time.perf_counter()
+    rv, rl, rP, rt = ffa.iterate(p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs], iters, counter=OpCounter(),
+                                 p_update="em")
+    oracle_s = time.perf_counter() - t0
+
+    def relerr(a_, b_, ax):
+        a_ = np.moveaxis(a_, ax, 0).reshape(len(fs), -1)
+        b_ = np.moveaxis(b_, ax, 0).reshape(len(fs), -1)
+        return float(np.max(np.linalg.norm(a_ - b_, axis=1) / np.linalg.norm(b_, axis=1)))
+    err = {"v": relerr(vg, rv, 1), "lambda": relerr(lg, rl, 0), "P": relerr(Pg, rP, 0),
+           "loglik_per_point": abs(ffa.loglik(p.y[:, fs], vg, lg, Pg) - rt[-1]) / (len(fs) * N),
+           "measure": f"after {iters} EM iterations from the same initial state, on {len(fs)} sampled "
+                      "frequencies; normwise relative error per frequency (max)"}
+    vd.copy_(v0); lamd.copy_(l0); Pd.copy_(P0)
+    for _ in range(max(args.warmup, 3)):
+        est.iterate(iters)
+    reps = max(3, min(args.steps, 20))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        est.iterate(iters)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, True)
+    est.iterate(iters)
+    kt = ffca.ffca_timing_read(est.ctx)
+    ffca.ffca_timing_enable(est.ctx, False)
+    est.close()
+    peaks, _ = _peaks()
+    bpt = I * 8 + 2 * J * 4
+    kms, kn = kt["estep"]
+    em_us = kms / kn * 1e3
+    gbs = bpt * N * F / (em_us * 1e-6) / 1e9
+    out = {"workload": f"long mixture with the normal EM update of P: I={I} J={J} F={F} N={N}, c64, "
+                       f"{iters} iterations with the L2 trace",
+           "value": N * F * iters / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms, "runs_timed": reps,
+           "kernels": {"em_pass": {"avg_us": em_us, "bytes_per_launch": bpt * N * F, "achieved_gbs": gbs,
+                                   "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]},
+                       "em_step": {"avg_us": kt["psolve"][0] / kt["psolve"][1] * 1e3}},
+           "l2_per_point_after": tr[-1] / (N * F),
+           "error_vs_oracle": err, "oracle_em_seconds": oracle_s}
+    del yd, vd, lamd, Pd, v0, l0, P0
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_adjoint(dev):
@@ -720,17 +997,21 @@ def run_batched(args, dev):
             "speedup_vs_sequential_fp64": ms_seq / ms, "error_vs_fp64": e}
 
 
-def cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_gpu):
-    """The FP64 oracle on a bounded sample of the workload (CPU_SAMPLE_F
-    frequencies, all frames, all iterations), timed on the host, and the
-    GPU result's error against it on those frequencies."""
+def cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_gpu, pool):
+    """The FP64 oracle on bounded samples of the workload (all frames, all
+    iterations), timed on the host: on one core over CPU_SAMPLE_F
+    frequencies, and on all cores (one worker process per core, a block of
+    frequencies each) over CPU_SAMPLE_F frequencies per worker; and the GPU
+    result's error against the one-core run on its frequencies."""
     from oracle import fastfca_as as ffa
     from oracle.fastfca_as import OpCounter
-    iters, N = cfg["iters"], cfg["N"]
+    iters, N, F = cfg["iters"], cfg["N"], cfg["F"]
     t = time.perf_counter()
     v, lam, P, tr = ffa.iterate(p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs], iters,
                                 counter=OpCounter())
     dt = time.perf_counter() - t
+    fa = _sample_freqs(F, min(F, CPU_SAMPLE_F * pool.workers))
+    _, dt_all = pool.run(_fastfca_jobs(p.y[:, fa], p.v0[:, fa], p.lam0[fa], p.P0[fa], iters, pool.workers))
 
     def relerr(a, b, ax):
         a = np.moveaxis(a, ax, 0).reshape(len(fs), -1)
@@ -742,9 +1023,13 @@ def cpu_baseline_and_error(p, cfg, fs, gpu_state, tr_gpu):
            "loglik_per_point": abs(ffa.loglik(p.y[:, fs], vg, lg, Pg) - tr[-1]) / (len(fs) * N),
            "measure": f"after {iters} iterations from the same initial state, on the sampled "
                       "frequencies; normwise relative error per frequency (max)"}
-    return {"value": len(fs) * N * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(fs)} of {cfg['F']} frequencies x {N} frames x {iters} iterations "
-                      "(numpy FP64, one thread)", "seconds": dt, "error_vs_oracle": err}
+    return {"value": len(fa) * N * iters / dt_all, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+            "sample": f"{len(fa)} of {F} frequencies x {N} frames x {iters} iterations, numpy FP64, "
+                      f"{pool.workers} worker processes of one thread (a block of frequencies each)",
+            "seconds": dt_all,
+            "one_core": {"value": len(fs) * N * iters / dt, "cores": 1, "seconds": dt,
+                         "sample": f"{len(fs)} of {F} frequencies x {N} frames x {iters} iterations"},
+            "error_vs_oracle": err}
 
 
 # ---------------------------------------------------------------- profiling case
@@ -784,38 +1069,72 @@ def run_case(a):
 
 
 # ---------------------------------------------------------------- reference arm
-def run_reference(args, cfg, rank, ws):
-    """The FP64 oracle on the host cores as the reference arm: each step is one
-    hybrid iteration with its L2 on a sample of the workload's frequencies."""
-    if rank != 0:
-        return None
+def _reference_worker(conn, y, v, lam, P):
+    """One host core of the reference arm: holds its block of frequencies and
+    runs one hybrid iteration with its L2 per message."""
     from oracle import fastfca_as as ffa
     from oracle.fastfca_as import OpCounter
-    I, J, F, N = cfg["I"], cfg["J"], cfg["F"], cfg["N"]
-    p = make_problem(I, J, F, N, seed=0, alpha=cfg["alpha"], kappa=cfg["kappa"])
-    fs = _sample_freqs(F, CPU_SAMPLE_F)
-    y, v, lam, P = p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs]
     cnt = OpCounter()
-
-    def step(v, lam, P):
+    conn.send("ready")
+    while conn.recv() is not None:
         ffa.loglik(y, v, lam, P)
-        return ffa.hybrid_iteration(y, v, lam, P, 1, cnt)
+        v, lam, P = ffa.hybrid_iteration(y, v, lam, P, 1, cnt)
+        conn.send("done")
+
+
+def run_reference(args, cfg, rank, ws):
+    """The FP64 oracle on the host cores as the reference arm: one worker
+    process per core (one numpy thread each, started with spawn), each
+    holding a block of CPU_SAMPLE_F of the workload's frequencies; a step is
+    one hybrid iteration with its L2 on every block, the workers in
+    parallel."""
+    if rank != 0:
+        return None
+    import multiprocessing as mp
+    I, J, F, N = cfg["I"], cfg["J"], cfg["F"], cfg["N"]
+    workers = os.cpu_count() or 1
+    p = make_problem(I, J, F, N, seed=0, alpha=cfg["alpha"], kappa=cfg["kappa"])
+    fs = _sample_freqs(F, min(F, CPU_SAMPLE_F * workers))
+    blocks = [b for b in np.array_split(fs, workers) if len(b)]
+    ctx = mp.get_context("spawn")
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    procs, conns = [], []
+    for b in blocks:
+        a, c = ctx.Pipe()
+        pr = ctx.Process(target=_reference_worker, args=(c, p.y[:, b], p.v0[:, b], p.lam0[b], p.P0[b]),
+                         daemon=True)
+        pr.start()
+        procs.append(pr)
+        conns.append(a)
+    for c in conns:
+        c.recv()
+
+    def step():
+        for c in conns:
+            c.send(1)
+        for c in conns:
+            c.recv()
 
     for _ in range(args.warmup):
-        v, lam, P = step(v, lam, P)
+        step()
     t = time.perf_counter()
     for _ in range(args.steps):
-        v, lam, P = step(v, lam, P)
+        step()
     dt = time.perf_counter() - t
+    for c in conns:
+        c.send(None)
+    for pr in procs:
+        pr.join(timeout=30)
     value = len(fs) * N * args.steps / dt
-    sample = (f"{len(fs)} of {F} frequencies x {N} frames, one hybrid iteration + L2 per step "
-              "(numpy FP64, one thread)")
+    sample = (f"{len(fs)} of {F} frequencies x {N} frames, one hybrid iteration + L2 per step, numpy FP64, "
+              f"{len(blocks)} worker processes of one thread (a block of frequencies each)")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: I={I} J={J} F={F} N={N}", "parallelism": "cpu"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(blocks), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -148,17 +148,32 @@ ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
  * inverts P once per step.  ffca_inversion_count counts F K per iteration
  * for the gradient and nothing for the natural gradient.  Neither method
  * guarantees an increase of L2 for a large mu: the trace monitors it. */
+/* FFCA_P_EM is the normal EM algorithm for P, the fourth alternative of
+ * Sec. 4.6, read with the source images x_j of Eq. fullrank as complete data:
+ * the M-step for P has Eq. FPI's form with V_i replaced by W_i / (J N),
+ *   W_i = P^{-H} (sum_j T_j / lambda_ji^new) P^{-1},
+ *   T_j = sum_n (mu~_j mu~_j^H + diag phi~_j) / v_j^new
+ * (posterior of the entering state, Eqs. mutilde0 / Phitilde0; the new v and
+ * Lambda of Eqs. updatev / Lambdaupdate), K sweeps of it per iteration.  Its
+ * sums come from pass A, so an iteration streams y and v once (no pass B);
+ * it counts (I+1) F K inversions per iteration like the fixed point, ignores
+ * mu and guarantees an L2 that does not decrease (an EM step).  Compiled for
+ * I <= 4 (FFCA_ERR_UNSUPPORTED at I = 8). */
 typedef enum {
   FFCA_P_FIXED_POINT = 0,
   FFCA_P_GRADIENT = 1,
-  FFCA_P_NATURAL_GRADIENT = 2
+  FFCA_P_NATURAL_GRADIENT = 2,
+  FFCA_P_EM = 3
 } ffca_p_update;
 
 /* Select the update of P for later iterations of a single or batch context.
  * mu: step size, finite and > 0 for the gradient methods (ignored for the
- * fixed point).  Drops a captured graph.  FFCA_ERR_ARG for an unknown method
- * or an invalid mu (the context keeps its previous choice).  The
- * allocation-free call always uses the fixed point. */
+ * fixed point and the EM).  Drops a captured graph.  FFCA_ERR_ARG for an
+ * unknown method or an invalid mu, FFCA_ERR_UNSUPPORTED for the EM at I = 8
+ * (the context keeps its previous choice).  With the EM, ffca_timing_read
+ * counts its streaming pass as FFCA_KERNEL_ESTEP and its per-problem step as
+ * FFCA_KERNEL_PSOLVE, and ffca_batch_autotune tunes the EM pass on pass A's
+ * candidates.  The allocation-free call always uses the fixed point. */
 ffca_status ffca_set_p_update(ffca_ctx* ctx, int method, double mu);
 
 /* Fault injection for tests of failure detection (no GPU fault is made).
@@ -401,6 +416,15 @@ void ffca_fca_destroy(ffca_fca_ctx* ctx);
  * FFCA_ERR_ARG on bad sizes, strides or alignment; C and N of 0 are no-ops. */
 ffca_status ffca_stft(const float* x, int C, long long S, void* out, int ld, void* stream);
 ffca_status ffca_istft(const void* in, int C, int N, int ld, float* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Measurement (not part of the method).  ffca_peak_fp64 runs a kernel of
+ * independent FP64 FMA chains over every SM of the current device on
+ * `stream` (a cudaStream_t) and writes the best of three timed launches as
+ * GFLOP/s (2 flops per FMA) to *gflops (host); it synchronises the stream.
+ * This is the measured FP64 peak the FP64 path's ALU roofline is reported
+ * against. */
+ffca_status ffca_peak_fp64(void* stream, double* gflops);
 
 const char* ffca_status_str(ffca_status s);
 

@@ -103,6 +103,7 @@ struct Plan {
   size_t off_bstartA[kCands], off_slotsA[kCands], off_bstartB[kCands], off_slotsB[kCands];  // batch candidates
   size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
+  size_t off_partE;  // the normal EM's pass-A slots (pass A's partition, em_nv sums each)
   size_t bytes;
 };
 
@@ -139,6 +140,12 @@ ffca_status query_occupancy(const FastKernels* k, Occupancy* o) {
     if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->stream_smem),
                  "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"))
       return FFCA_ERR_CUDA;
+  if (k->estep_em &&
+      (!cuda_ok(cudaFuncSetAttribute(k->estep_em, cudaFuncAttributeMaxDynamicSharedMemorySize, k->em_smem),
+                "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, EM pass)") ||
+       !cuda_ok(cudaFuncSetAttribute(k->psolve_em, cudaFuncAttributeMaxDynamicSharedMemorySize, k->em_solve_smem),
+                "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, EM step)")))
+    return FFCA_ERR_CUDA;
   if (k->solve_smem > 0)
     for (const void* fn : {k->psolve, k->prep})
       if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->solve_smem),
@@ -179,6 +186,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_tabA = off; off = align_up(off + (size_t)P * k->params_a_bytes);
   p->off_tabB = off; off = align_up(off + (size_t)P * k->params_b_bytes);
   p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)P * J * I);
+  p->off_partE = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * k->em_nv);
   // the adjoint kernels use pass A's partition; J I + 2 I^2 + 2 sums per slot at most
   p->off_partAdj = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2 * I * I + 2));
   p->off_lossf = off; off = align_up(off + sizeof(double) * (size_t)P);
@@ -361,6 +369,27 @@ const void* p_step_kernel(const ffca_ctx* c) {
 
 int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
 
+// One iteration with the normal EM update of P: pass A with the EM sums
+// (on pass A's partition, em_groups pipeline groups per CTA) and the
+// per-problem EM step; no pass B.  With `trace` the step's
+// last block sums the problems' L2 of the entering state into trace slot
+// `slot`.
+ffca_status launch_em_iteration(ffca_ctx* c, int slot, bool trace) {
+  FastArgs a = base_args(c);
+  a.part = c->plan.pA;
+  a.part_buf = reinterpret_cast<double*>(c->ws + c->plan.off_partE);
+  a.trace_slot = slot;
+  a.pinvH = reinterpret_cast<double*>(c->ws + c->plan.off_pinvH);
+  a.gcnt = reinterpret_cast<unsigned*>(c->ws + 28);
+  if (!trace) a.trace = nullptr;
+  const int eg = c->kern->em_groups;
+  ffca_status st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_em, (a.part.nblocks + eg - 1) / eg,
+                          kGroupThreads * eg, a, c->kern->em_smem);
+  if (st != FFCA_OK) return st;
+  const int G = 32 / c->d.I;
+  return launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve_em, (c->d.F + G - 1) / G, 32, a, c->kern->em_solve_smem);
+}
+
 // CTAs of a streaming pass: each runs stream_groups virtual blocks of the partition.
 int stream_grid(const ffca_ctx* c, const Partition& p) {
   return (p.nblocks + c->kern->stream_groups - 1) / c->kern->stream_groups;
@@ -398,6 +427,10 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
   if (st != FFCA_OK) return st;
   for (int t = 0; t < iters; ++t) {
     const int slot = t % kTraceCap;
+    if (c->pmode == kPEM) {
+      if ((st = launch_em_iteration(c, slot, false)) != FFCA_OK) return st;
+      continue;
+    }
     FastArgs a = pass_a_args(c, slot);
     if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, stream_grid(c, a.part), stream_threads(c), a,
                      c->kern->stream_smem)) != FFCA_OK)
@@ -454,7 +487,7 @@ ffca_status iterate_graph(ffca_ctx* c, int iters) {
   if (!cuda_ok(cudaGraphLaunch(c->graph, c->stream), "cudaGraphLaunch")) return FFCA_ERR_CUDA;
   c->launches[FFCA_KERNEL_PREP] += 1;
   c->launches[FFCA_KERNEL_ESTEP] += iters;
-  c->launches[FFCA_KERNEL_WCOV] += iters;
+  if (c->pmode != kPEM) c->launches[FFCA_KERNEL_WCOV] += iters;
   c->launches[FFCA_KERNEL_PSOLVE] += iters;
   return FFCA_OK;
 }
@@ -584,7 +617,9 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
   int flushed = 0;  // first trace index not yet copied to the host
   for (int t = 0; t <= iters; ++t) {
     const int slot = t % kTraceCap;
-    if (t < iters) {
+    if (t < iters && c->pmode == kPEM) {
+      if ((st = launch_em_iteration(c, slot, ll_trace != nullptr)) != FFCA_OK) return st;
+    } else if (t < iters) {
       FastArgs a = pass_a_args(c, slot);
       if ((st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_update, stream_grid(c, a.part), stream_threads(c), a,
                       c->kern->stream_smem)) != FFCA_OK)
@@ -1123,6 +1158,13 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
   for (int r = 0; r < rounds && st == FFCA_OK; ++r) {
     for (int q = 0; q < kCands && st == FFCA_OK; ++q) {
       use_candidates(c, q, q);
+      if (c->pmode == kPEM) {  // the EM pass (on pass A's partition) and its step; no pass B
+        cudaEventRecord(ev[q][0], c->stream);
+        st = launch_em_iteration(c, 0, false);
+        cudaEventRecord(ev[q][1], c->stream);
+        cudaEventRecord(ev[q][2], c->stream);
+        continue;
+      }
       // one hybrid iteration, pass A and pass B bracketed by events
       FastArgs a = pass_a_args(c, 0);
       cudaEventRecord(ev[q][0], c->stream);
@@ -1168,16 +1210,19 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
 void ffca_batch_destroy(ffca_batch_ctx* c) { ffca_destroy(c); }
 
 static_assert(FFCA_P_FIXED_POINT == kPFixedPoint && FFCA_P_GRADIENT == kPGradient &&
-                  FFCA_P_NATURAL_GRADIENT == kPNatural,
+                  FFCA_P_NATURAL_GRADIENT == kPNatural && FFCA_P_EM == kPEM,
               "the ABI's P-update codes are the kernels' modes");
 
 ffca_status ffca_set_p_update(ffca_ctx* c, int method, double mu) {
   if (!c) return FFCA_ERR_ARG;
-  if (method != FFCA_P_FIXED_POINT && method != FFCA_P_GRADIENT && method != FFCA_P_NATURAL_GRADIENT)
+  if (method != FFCA_P_FIXED_POINT && method != FFCA_P_GRADIENT && method != FFCA_P_NATURAL_GRADIENT &&
+      method != FFCA_P_EM)
     return FFCA_ERR_ARG;
-  if (method != FFCA_P_FIXED_POINT && !(std::isfinite(mu) && mu > 0.0)) return FFCA_ERR_ARG;
+  const bool stepped = method == FFCA_P_GRADIENT || method == FFCA_P_NATURAL_GRADIENT;
+  if (stepped && !(std::isfinite(mu) && mu > 0.0)) return FFCA_ERR_ARG;
+  if (method == FFCA_P_EM && !c->kern->estep_em) return FFCA_ERR_UNSUPPORTED;
   c->pmode = method;
-  c->mu = method == FFCA_P_FIXED_POINT ? 0.0 : mu;
+  c->mu = stepped ? mu : 0.0;
   if (c->graph) {  // the captured launches hold the previous arguments
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;

@@ -1,6 +1,7 @@
 // Device helpers shared by the FastFCA-AS and FCA kernels: complex scalars,
-// compensated FP32 accumulation, the balanced (f, n) work partition, the
-// deterministic block reduction, and small FP64 dense solves.
+// compensated FP32 accumulation (Kahan sums, double-float pair sums), the
+// balanced (f, n) work partition, the deterministic block reduction, and
+// small FP64 dense solves.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -77,33 +78,25 @@ __device__ inline float logx(float x) { return __logf(x); }
 __device__ inline double logx(double x) { return log(x); }
 
 // ------------------------------------------------------------ accumulation
-// Sum over frames.  FP64: plain.  FP32: Kahan-compensated (value = s - c),
-// fed once per loop trip with the plain sum of that trip's few frames.
-template <typename T>
-struct Acc;
-
-template <>
-struct Acc<double> {
-  double s;
-  __device__ inline void zero() { s = 0.0; }
-  __device__ inline void add(double x) { s += x; }
-  __device__ inline double value_hi() const { return s; }
-  __device__ inline double value_lo() const { return 0.0; }
-};
-
-template <>
-struct Acc<float> {
-  float s, c;
-  __device__ inline void zero() { s = 0.f; c = 0.f; }
-  __device__ inline void add(float x) {
-    float y = x - c;
-    float t = s + y;
-    c = (t - s) - y;
-    s = t;
+// Compensated (Kahan) sum over frames in FP32 held in two floats: h, the
+// running total, and p, the partial of the frames added since the last fold,
+// which starts from the rounding error the previous fold left behind.  Frames
+// are added to p (a few per fold: the units a thread takes from a few tiles);
+// fold() is one Kahan step, h + p = t exactly up to the error e it returns in
+// p (t = h + p, e = p - (t - h)), so that the error of the whole sum is that
+// of the short partials plus O(u^2) terms, independent of the number of
+// frames.  The two floats take the registers of the packed pair that held a
+// plain sum per frame lane.  value() is the compensated total.
+struct KSum {
+  float h, p;
+  __device__ inline void zero() { h = 0.f; p = 0.f; }
+  __device__ inline void add(float x) { p += x; }
+  __device__ inline void fold() {
+    const float t = __fadd_rn(h, p);
+    p = __fsub_rn(p, __fsub_rn(t, h));
+    h = t;
   }
-  // the compensated value as an unevaluated pair (hi, lo)
-  __device__ inline float value_hi() const { return s; }
-  __device__ inline float value_lo() const { return -c; }
+  __device__ inline float value() const { return __fadd_rn(h, p); }
 };
 
 // Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.

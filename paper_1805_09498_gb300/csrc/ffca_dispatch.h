@@ -19,6 +19,13 @@ struct FastKernels {
   int solve_smem;            // dynamic shared memory of psolve and prep
   int pinv_step;             // 1: the P step starts from P^{-H} (prep computes it) and leaves the next one
   const void* pgrad;         // the P step with the gradient updates in place of the fixed point
+  // the normal EM update of P (nullptr where not compiled: I > 4)
+  const void* estep_em;      // pass A with the EM sums (one pipeline group per CTA)
+  const void* psolve_em;     // its per-problem step (no pass B)
+  int em_smem;               // dynamic shared memory of estep_em
+  int em_solve_smem;         // dynamic shared memory of psolve_em
+  int em_nv;                 // sums per slot of estep_em
+  int em_groups;             // pipeline groups per CTA of estep_em
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

@@ -1,0 +1,262 @@
+// The normal EM update of P (Sec. 4.6 names it as an alternative to the
+// fixed-point iteration of Eq. FPI), per problem after pass A in its EM form
+// (k_estep<..., EM = true>), which streams y and v once per iteration: there
+// is no pass B.
+//
+// Complete data: the source images x_j of Eq. fullrank, x_j ~ CN(0, v_j
+// P^{-H} Lambda_j P^{-1}) (Eq. diagconst).  Over P the expected complete-data
+// log-likelihood is J N ln|det P|^2 - sum_i p_i^H W_i p_i with
+//     W_i = sum_{n,j} E[x_j x_j^H | y] / (v_j^new lambda_ji^new)
+//         = P^{-H} Omega_i P^{-1},   Omega_i = sum_j T_j / lambda_ji^new,
+//     T_j = sum_n (mu~_j mu~_j^H + diag phi~_j) / v_j^new
+// (posterior of the entering state, Eqs. mutilde0 / Phitilde0; the new v and
+// Lambda of Eqs. updatev / Lambdaupdate).  Its stationarity condition has
+// Eq. FPI's form with V_i replaced by W_i / (J N); K sweeps of that map from
+// the entering P (all columns from one P_k^{-H} per sweep):
+//     p_i <- (W_i / (J N))^{-1} [P_k^{-H}]_i = J N P Omega_i^{-1} P^H [P_k^{-H}]_i,
+// which for the first sweep (P_0 = P) is J N P Omega_i^{-1} e_i: no inverse
+// of P is needed to form it.  Pass A gives the diagonal of T_j as the
+// Lambda sums (T_j[a][a] = N lambda_ja^new) and its off-diagonal entries as
+// T_j[a][b] = I lambda_ja lambda_jb sum_n u_j z_a conj(z_b) (old Lambda).
+//
+//   k_psolve_em  one warp per 32 / I problems, lane (g, i) owning column i
+//                of problem g: the slot sums (the whole warp, through shared
+//                memory), the new Lambda and the problem's L2 of the
+//                entering state (the work pass B's producer does in the
+//                fixed-point iteration), Omega_i = L D L^H, the K sweeps, then
+//                P^{-H} and ln|det P|^2 of the new P; with a trace, the last
+//                block to finish sums the problems' L2.
+#pragma once
+
+#include "ffca_big.cuh"
+
+namespace ffca {
+
+template <int I, int J>
+struct EmShape {
+  static constexpr int NA = J * I;                 // Lambda sums (as pass A)
+  static constexpr int NPAIR = I * (I - 1) / 2;    // entries a < b of T_j
+  static constexpr int NV = NA + 2 + 2 * J * NPAIR;  // + the two L2 sums, + (re, im) per j and pair
+  static constexpr int G = 32 / I;                 // problems per warp
+  static constexpr int NL = NPAIR > 0 ? NPAIR : 1; // storage of the strictly lower entries
+  static constexpr int SMEM = BigLane<I>::SMEM + G * NV * (int)sizeof(double);
+};
+
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
+  using ES = EmShape<I, J>;
+  constexpr int G = ES::G;
+  constexpr int NV = ES::NV, NA = ES::NA, NPAIR = ES::NPAIR;
+  extern __shared__ __align__(16) unsigned char em_smem[];
+  const int lane = threadIdx.x;
+  const int g = lane / I, i = lane % I;
+  const int f0 = blockIdx.x * G + g;
+  const bool active = g < G && f0 < a.F;
+  const int f = active ? f0 : 0;  // idle lanes shadow problem 0 and write nothing
+  cpx<double>* M = reinterpret_cast<cpx<double>*>(em_smem) + (size_t)(g < G ? g : G) * I * BigLane<I>::LDM;
+  double* sums = reinterpret_cast<double*>(em_smem + BigLane<I>::SMEM);  // [G][NV]
+  const Partition pt = a.part;
+
+  // the slot sums of the block's problems (slot order), spread over the
+  // whole warp: lane l takes the values l + 32 c of the flattened [G][NV]
+  // sums and issues its loads of one slot together
+  {
+    constexpr int PER = (G * NV + 31) / 32;
+    const double* src[PER];
+    int ns[PER];
+    double acc[PER];
+    int nsmax = 0;
+#pragma unroll
+    for (int c = 0; c < PER; ++c) {
+      const int x = lane + 32 * c;
+      const int ff = blockIdx.x * G + x / NV;
+      const bool ok = x < G * NV && ff < a.F;
+      ns[c] = ok ? pt.nslots(ff) : 0;
+      src[c] = a.part_buf + ((size_t)(ok ? ff : 0) * pt.max_slots) * NV + x % NV;
+      acc[c] = 0.0;
+      nsmax = max(nsmax, ns[c]);
+    }
+    for (int k = 0; k < nsmax; ++k)
+#pragma unroll
+      for (int c = 0; c < PER; ++c)
+        if (k < ns[c]) acc[c] += __ldcg(src[c] + (size_t)k * NV);
+#pragma unroll
+    for (int c = 0; c < PER; ++c)
+      if (lane + 32 * c < G * NV) sums[lane + 32 * c] = acc[c];
+  }
+  // the entering P (all columns) and Lambda of this lane's problem
+  cpx<double> P0[I][I];
+#pragma unroll
+  for (int r = 0; r < I; ++r)
+#pragma unroll
+    for (int c = 0; c < I; ++c) {
+      const double2 q = __ldcg(reinterpret_cast<const double2*>(a.P) + (size_t)f * I * I + r * I + c);
+      P0[r][c] = mk(q.x, q.y);
+    }
+  double lold[J][I];
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int c = 0; c < I; ++c) lold[j][c] = __ldcg(a.lam + (size_t)f * J * I + j * I + c);
+  const double logdet_old = __ldcg(a.logdet + f);
+  __syncwarp();  // sums complete; every lane has read P and Lambda before any lane writes them
+  const double* tot = sums + (size_t)(g < G ? g : 0) * NV;
+  const int n = pt.frames(f);
+  const double nd = (double)n;
+
+  // the new Lambda (Eq. Lambdaupdate: lambda_ja I sum_n t_ja / s_j / N)
+  double lnew[J][I];
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < J; ++j)
+#pragma unroll
+    for (int c = 0; c < I; ++c) {
+      lnew[j][c] = lold[j][c] * ((double)I * pt.inv_n(f)) * tot[j * I + c];
+      bad |= !(lnew[j][c] > 0.0) || !isfinite(lnew[j][c]);
+    }
+  // L2 of the entering state (Eq. L2)
+  const double lf = -(double)I * nd * kLnPi + nd * logdet_old - tot[NA] - 0.69314718055994530942 * tot[NA + 1];
+  bad |= !isfinite(lf);
+
+  // Omega_i: diagonal sum_j N lambda_ja^new / lambda_ji^new; above it
+  // sum_j I lambda_ja lambda_jb S_j[a][b] / lambda_ji^new (old Lambda in the
+  // products, S_j the pass-A sums); kept as the real diagonal and the
+  // strictly lower entries Omega_ba = conj(Omega_ab)
+  double rl[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    double lji = lnew[j][0];
+#pragma unroll
+    for (int c = 1; c < I; ++c)
+      if (c == i) lji = lnew[j][c];
+    rl[j] = 1.0 / lji;
+  }
+  double dv[I], d0[I], rd[I];
+  cpx<double> lo[ES::NL];
+#pragma unroll
+  for (int c = 0; c < I; ++c) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) s = fma(nd * lnew[j][c], rl[j], s);
+    dv[c] = s;
+    d0[c] = s;
+  }
+  {
+    int pq = 0;
+#pragma unroll
+    for (int aa = 0; aa < I; ++aa)
+#pragma unroll
+      for (int bb = aa + 1; bb < I; ++bb, ++pq) {
+        cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const double w = (double)I * lold[j][aa] * lold[j][bb] * rl[j];
+          const double* t = tot + NA + 2 + 2 * (j * NPAIR + pq);
+          s.re = fma(w, t[0], s.re);
+          s.im = fma(w, t[1], s.im);
+        }
+        lo[lo_index(bb, aa)] = cconj(s);
+      }
+  }
+  bool singular = false;
+#pragma unroll
+  for (int c = 0; c < I; ++c) bad |= !isfinite(dv[c]);
+#pragma unroll
+  for (int c = 0; c < NPAIR; ++c) bad |= !isfinite(lo[c].re) || !isfinite(lo[c].im);
+  if constexpr (I == 1) {
+    singular = !(dv[0] > 0.0) || !isfinite(dv[0]);
+    rd[0] = 1.0 / dv[0];
+  } else {
+    singular = !ldl_factor<I>(dv, lo, rd);
+#pragma unroll
+    for (int c = 0; c < I; ++c) singular |= !(dv[c] > kCholRtol * d0[c]);  // dv holds the pivots D
+  }
+
+  // commit the new Lambda (column i of the problem's Lambda entries)
+  if (active) {
+    ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      double l = lnew[j][0];
+#pragma unroll
+      for (int c = 1; c < I; ++c)
+        if (c == i) l = lnew[j][c];
+      a.lam[(size_t)f * J * I + j * I + i] = l;
+      ta->set_lam(j, i, (T)l);
+    }
+    if (i == 0) a.llf[f] = lf;
+    if (bad) raise_status(a.status, kDevNonfinite, f);
+  }
+
+  // K sweeps; col holds column i of the current P
+  const double jn = (double)J * nd;
+  cpx<double> col[I];
+  for (int sweep = 0; sweep < a.K; ++sweep) {
+    cpx<double> x[I];
+    if (sweep == 0) {
+#pragma unroll
+      for (int r = 0; r < I; ++r) x[r] = mk(r == i ? 1.0 : 0.0, 0.0);  // P^H P^{-H} e_i
+    } else {
+      cpx<double> q[I];  // column i of the current P's P^{-H}
+#pragma unroll
+      for (int r = 0; r < I; ++r) q[r] = col[r];
+      pinvh_from_columns<I>(q, M, g, i, singular);
+#pragma unroll
+      for (int c = 0; c < I; ++c) {  // x = P^H q with the entering P
+        cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+        for (int r = 0; r < I; ++r) cfmac(s, P0[r][c], q[r]);
+        x[c] = s;
+      }
+    }
+    if constexpr (I == 1) {
+      x[0] = cscale(x[0], rd[0]);
+    } else {
+      ldl_solve<I>(lo, rd, x);  // x <- Omega_i^{-1} x
+    }
+#pragma unroll
+    for (int r = 0; r < I; ++r) {  // column i = J N P x
+      cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < I; ++c) cfma(s, P0[r][c], x[c]);
+      col[r] = cscale(s, jn);
+    }
+  }
+  if (active) {
+    ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+      reinterpret_cast<double2*>(a.P)[(size_t)f * I * I + r * I + i] = make_double2(col[r].re, col[r].im);
+      ta->set_p(r, i, (T)col[r].re, (T)col[r].im);
+    }
+  }
+  // P^{-H} and ln|det P|^2 of the new P (the next iteration's L2 needs it)
+  const double det2 = pinvh_from_columns<I>(col, M, g, i, singular);
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+      reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(col[r].re, col[r].im);
+    if (singular) raise_status(a.status, kDevSingular, f);
+    if (i == 0) {
+      atomicAdd(a.ops, p_update_inversions(a, I));
+      a.logdet[f] = log(det2);
+    }
+  }
+  // with a trace: the last block to finish sums the problems' L2
+  if (a.trace) {
+    __threadfence();
+    __syncwarp();
+    unsigned last = 0;
+    if (lane == 0) {
+      last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
+      if (last) *a.gcnt = 0u;  // ready for the next launch
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      finalize_trace(a);
+    }
+  }
+}
+
+}  // namespace ffca

@@ -43,7 +43,7 @@ struct FastArgs {
   double* lam_next;          // [F][J][I] the new Lambda, written during pass B, committed by k_psolve
   Partition prev_part;       // pass B reads pass A's slots: their partition
   const double* prev_buf;    // and buffer
-  int pmode;                 // update of P: kPFixedPoint, kPGradient or kPNatural
+  int pmode;                 // update of P: kPFixedPoint, kPGradient, kPNatural or kPEM
   double mu;                 // step size of the gradient updates
   int fault;                 // injected fault (tests of failure detection): kFault*
 };
@@ -59,16 +59,19 @@ constexpr int kFaultPassANoCopies = 1;
 // mu along G / N, G = dL2/dP^* of Eq. partialP:
 //   gradient  p_i <- p_i + mu ([P^{-H}]_i - V_i p_i)
 //   natural   p_i <- p_i + mu (p_i - P P^H V_i p_i)   (P P^H G / N)
+// The normal EM (kPEM, ffca_em.cuh) replaces the V_i of Eq. FPI by the
+// M-step matrices W_i / (J N) and needs no pass B.
 constexpr int kPFixedPoint = 0;
 constexpr int kPGradient = 1;
 constexpr int kPNatural = 2;
+constexpr int kPEM = 3;
 
 // Matrix inversions per problem of one P update: (I+1) K for the fixed
-// point (Sec. 4.5), one P^{-H} per gradient step, none for the natural
-// gradient.
+// point (Sec. 4.5) and for the normal EM (the same map on other matrices),
+// one P^{-H} per gradient step, none for the natural gradient.
 __device__ inline unsigned long long p_update_inversions(const FastArgs& a, int I) {
-  return a.pmode == kPFixedPoint ? (unsigned long long)(I + 1) * a.K
-                                 : (a.pmode == kPGradient ? (unsigned long long)a.K : 0ull);
+  return (a.pmode == kPFixedPoint || a.pmode == kPEM) ? (unsigned long long)(I + 1) * a.K
+                                                      : (a.pmode == kPGradient ? (unsigned long long)a.K : 0ull);
 }
 
 // Per-frequency parameters in the per-point precision T, laid out as they

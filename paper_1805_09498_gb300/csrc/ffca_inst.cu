@@ -5,6 +5,7 @@
 #include "ffca_adjoint.cuh"
 #include "ffca_big.cuh"
 #include "ffca_dispatch.h"
+#include "ffca_em.cuh"
 #include "ffca_fca.cuh"
 #include "ffca_fca_big.cuh"
 #include "ffca_stream.cuh"
@@ -53,6 +54,17 @@ static const FastKernels* table_entry() {
   }
   if constexpr (BIG) wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
   else wiener = (const void*)k_wiener<Real, FFCA_I, J>;
+  const void* estep_em = nullptr;
+  const void* psolve_em = nullptr;
+  int em_smem = 0, em_solve_smem = 0, em_nv = 0, em_groups = 1;
+  if constexpr (!BIG) {
+    estep_em = (const void*)k_estep<Real, FFCA_I, J, true, true>;
+    psolve_em = (const void*)k_psolve_em<Real, FFCA_I, J>;
+    em_groups = EmGroups<Real, FFCA_I, J>::value;
+    em_smem = em_groups * Tile<Real, FFCA_I, J, EmGroups<Real, FFCA_I, J>::value>::GROUP;
+    em_solve_smem = EmShape<FFCA_I, J>::SMEM;
+    em_nv = EmShape<FFCA_I, J>::NV;
+  }
   static const FastKernels k = {
       Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
       StreamGroups<Real, FFCA_I, J>::value,
@@ -68,6 +80,12 @@ static const FastKernels* table_entry() {
       LDL ? BigLane<FFCA_I>::SMEM : 0,
       LDL ? 1 : 0,
       pgrad,
+      estep_em,
+      psolve_em,
+      em_smem,
+      em_solve_smem,
+      em_nv,
+      em_groups,
   };
   return &k;
 }

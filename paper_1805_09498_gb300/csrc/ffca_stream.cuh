@@ -93,9 +93,9 @@ __device__ inline Role role() {
 // one or two units per consumer thread (always even).  Each stage also
 // carries the tile's per-frequency parameters (a ParamsA or ParamsB record),
 // so a consumer starting a new frequency finds them already in shared memory.
-template <typename R, int I, int J>
+template <typename R, int I, int J, int GG = StreamGroups<R, I, J>::value>
 struct Tile {
-  static constexpr int G = StreamGroups<R, I, J>::value;
+  static constexpr int G = GG;  // pipeline groups per CTA
   static constexpr int UB = 16 * I + 8 * J;                      // bytes per unit over all rows
   static constexpr int PARAMS = ParamsA<double, I, J>::BYTES;     // room for either record
   // FFCA_TILE_UNITS_PER_THREAD units per consumer thread where three stages
@@ -119,6 +119,18 @@ struct Tile {
   static constexpr int S = S_FIT < 2 ? 2 : (S_FIT > FFCA_MAX_STAGES ? FFCA_MAX_STAGES : S_FIT);  // stages
   static constexpr int GROUP = S * STAGE + 2 * S * 8;             // + mbarriers
   static_assert(G * GROUP + (I > 4 ? 32 * 1024 : 0) <= 227 * 1024, "stages exceed the shared memory of a CTA");
+};
+
+// Pipelines per CTA of pass A in its EM form (k_estep<..., EM = true>):
+// with P and Lambda read from the stage's record at each use (not held in
+// registers), the FP32 form fits two groups of 128 registers for I <= 3,
+// J <= 3; else one group.
+#ifndef FFCA_EM_GROUPS
+#define FFCA_EM_GROUPS 2
+#endif
+template <typename T, int I, int J>
+struct EmGroups {
+  static constexpr int value = (sizeof(T) == 4 && I <= 3 && J <= 3) ? FFCA_EM_GROUPS : 1;
 };
 
 // Register cap of the streaming kernels: 128 for two groups per CTA, else
@@ -204,7 +216,10 @@ struct GroupReduce {
   // single-buffered view (the I > 4 pass B, two barriers per segment)
   __device__ static T (&one(Smem& sm))[kConsumerWarps][NC * 32] { return sm.hi[0]; }
 
-  __device__ static void run(const T (&hi)[NV], Smem& smem, double* out, const Role& r, int parity) {
+  // add: add the values to out[] (a later flush of the same segment) instead
+  // of storing them
+  __device__ static void run(const T (&hi)[NV], Smem& smem, double* out, const Role& r, int parity,
+                             bool add = false) {
     static_assert(NB == 2, "run() alternates two buffers");
     auto& sm = smem.hi[parity & 1];
     const int lane = threadIdx.x & 31;
@@ -240,10 +255,25 @@ struct GroupReduce {
           h += sm[w][t];
         }
       }
-      out[t] = (double)h + (double)l;
+      const double x = (double)h + (double)l;
+      out[t] = add ? out[t] + x : x;
     }
   }
 };
+
+// Flushes of the per-thread FP32 sums that cannot be compensated in
+// registers (more sums than the register file holds twice): a group reduces
+// its sums into its slot every kFlushUnits units per thread of a segment,
+// adding to what earlier flushes of the segment stored (FP64), so that no
+// thread's plain FP32 sum runs over more than kFlushUnits units, however
+// long the problem is.  Tile trips between flushes for UPT units per thread
+// per trip:
+constexpr int kFlushUnits = 64;
+// Tile trips between the Kahan steps of the compensated sums (KSum): a
+// thread's partial covers at most this many trips' units (two per trip at
+// most) before it is folded into the running total.
+constexpr int kFoldTiles = 4;
+__host__ __device__ constexpr int flush_tiles(int upt) { return kFlushUnits / upt > 0 ? kFlushUnits / upt : 1; }
 
 // Tiles of a CTA's unit range [u0, u1) of the flattened unit space: at most
 // T units each, never crossing a problem boundary (tile = problem f, first
@@ -389,10 +419,10 @@ __device__ void finalize_pass_a(const FastArgs& a, int f, const FinIn<I, J>& in,
 // 16-byte aligned and a multiple of 16 bytes.  Each stage also receives the
 // tile's parameter record: copied from the pass-A table (pass A), or computed
 // from pass A's slots (pass B).
-template <typename T, int I, int J, bool PASS_B>
-__device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J>::S>& pp, long long u0, long long u1,
+template <typename T, int I, int J, bool PASS_B, int G = StreamGroups<T, I, J>::value>
+__device__ void produce(const FastArgs& a, const Pipe<Tile<T, I, J, G>::S>& pp, long long u0, long long u1,
                         long long row, int vb, volatile int* abort) {
-  using TC = Tile<T, I, J>;
+  using TC = Tile<T, I, J, G>;
   constexpr int kStages = TC::S;
   using PA = ParamsA<T, I, J>;
   using PB = ParamsB<T, I, J>;
@@ -586,20 +616,33 @@ struct Lane<double> {
 // kernel accumulates sum_n t_ji / s_j and k_afinal scales it.  The
 // log-likelihood terms are sum_n sum_i (ln sigma_i + |y~_i|^2 r_i) (Eq. L2),
 // accumulated as the quadratic part and the base-2 log part.
-template <typename T, int I, int J, bool UPDATE>
-__global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
+//
+// EM (the normal EM update of P, Sec. 4.6) adds the sums its M-step for P
+// needs beyond these: with z_a = r_a y~_a and u_j = v_j / s_j, the
+// off-diagonal entries of T_j = sum_n (mu~_j mu~_j^H + diag phi~_j) / v_j^new
+// are T_j[a][b] = I lambda_ja lambda_jb sum_n u_j z_a conj(z_b) (mu~_ja =
+// a_ja r_a y~_a, v_j^new = v_j s_j / I), so the kernel sums
+// u_j z_a conj(z_b) for every j and a < b (re, im); the diagonal of T_j is
+// sum_n q_ja / v_j^new = N lambda_ja^new, which the Lambda sums give.  The
+// larger per-point state runs one pipeline group per CTA.
+template <typename T, int I, int J, bool UPDATE, bool EM = false>
+__global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : StreamRegs<T, I, J>::value))
+    k_estep(FastArgs a) {
+  static_assert(!EM || (UPDATE && I <= 4), "the EM sums are laid out for I <= 4");
   using VY = typename Vec<T>::Y;
   using VV = typename Vec<T>::V;
   using LN = Lane<T>;
   using L = typename LN::L;
-  using TC = Tile<T, I, J>;
+  constexpr int G = EM ? EmGroups<T, I, J>::value : StreamGroups<T, I, J>::value;
+  using TC = Tile<T, I, J, G>;
   constexpr int FU = Vec<T>::FU;
   constexpr int NA = UPDATE ? J * I : 0;  // sum_n t_ji / s_j
-  constexpr int NV = NA + 2;              // then the quadratic and log2 parts of L2
+  constexpr int NPAIR = I * (I - 1) / 2;  // EM: entries a < b of T_j
+  constexpr int NE = EM ? 2 * J * NPAIR : 0;
+  constexpr int NV = NA + 2 + NE;         // then the quadratic and log2 parts of L2, then the EM sums
   using Red = GroupReduce<T, NV>;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int G = StreamGroups<T, I, J>::value;
   __shared__ typename Red::Smem red_all[G];
   __shared__ int aborts[G];
   using PA = ParamsA<T, I, J>;
@@ -616,7 +659,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   if (!rl.consumer) {
     // an injected fault: no copies, the consumers' waits run out
     if ((threadIdx.x & 31) == 0 && a.fault != kFaultPassANoCopies)
-      produce<T, I, J, false>(a, pp, u0, u1, row, rl.vb, abort);
+      produce<T, I, J, false, G>(a, pp, u0, u1, row, rl.vb, abort);
     return;
   }
 
@@ -625,13 +668,15 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
   // I <= 4: P and Lambda in registers for the segment; I > 4 (BIG): read
   // from the stage's parameter record at each use (I^2 complex values would
   // not fit the register file)
+  // (EM: as well, which frees their registers for the EM sums)
   constexpr bool BIG = I > 4;
-  constexpr int RI = BIG ? 1 : I, RJ = BIG ? 1 : J;
+  constexpr bool PSMEM = BIG || EM;  // P and Lambda read from the stage's record
+  constexpr int RI = PSMEM ? 1 : I, RJ = PSMEM ? 1 : J;
   L pre_r[RI][RI], pim_r[RI][RI], lam_r[RJ][RI];
   const PA* spc = nullptr;
   // (re, im) of P_mi as frame-lane operands
   auto PP = [&](int m, int i, L& pr, L& pi) {
-    if constexpr (BIG) {
+    if constexpr (PSMEM) {
       pr = LN::bc(spc->pre(m, i));
       pi = LN::bc(spc->pim(m, i));
     } else {
@@ -640,20 +685,41 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     }
   };
   auto LAM = [&](int j, int i) -> L {
-    if constexpr (BIG) return LN::bc(spc->lam(j, i)); else return lam_r[j][i];
+    if constexpr (PSMEM) return LN::bc(spc->lam(j, i)); else return lam_r[j][i];
   };
-  // FP32 with more than 32 sums: one float per value (both frames of a unit
-  // go into it) instead of a packed pair
+  // FP32: Kahan-compensated sums (KSum, folded once per tile trip); with
+  // more than 32 sums one plain float per value instead (both frames of a
+  // unit go into it), which keeps them in registers.  FP64: plain sums.
   constexpr bool kNarrow = sizeof(T) == 4 && NV > 32;
-  using A = std::conditional_t<kNarrow, float, L>;
+  constexpr bool kComp = sizeof(T) == 4 && !kNarrow;
+  using A = std::conditional_t<kNarrow, float, std::conditional_t<kComp, KSum, L>>;
   A acc[NV];
   auto ACC = [&](int q, L x) {
-    if constexpr (kNarrow) acc[q] += x.v.x + x.v.y; else acc[q] = acc[q] + x;
+    if constexpr (kNarrow) {
+      acc[q] += x.v.x + x.v.y;
+    } else if constexpr (kComp) {
+      acc[q].add(x.v.x);
+      acc[q].add(x.v.y);
+    } else {
+      acc[q] = acc[q] + x;
+    }
+  };
+  auto ACCF = [&](int q, L x, L y) {  // sum of x y over the unit's frames
+    if constexpr (kNarrow) {
+      acc[q] = fmaf(x.v.y, y.v.y, fmaf(x.v.x, y.v.x, acc[q]));
+    } else if constexpr (kComp) {
+      acc[q].p = fmaf(x.v.y, y.v.y, fmaf(x.v.x, y.v.x, acc[q].p));
+    } else {
+      acc[q] = vfma(x, y, acc[q]);
+    }
   };
 
   TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
-  int nseg = 0;  // segments reduced so far (reduction buffer parity)
+  int nseg = 0;           // reductions so far (reduction buffer parity)
+  int ntile = 0;          // tile trips since the segment's start or last flush
+  int nfold = 0;          // tile trips since the last Kahan step
+  bool flushed = false;   // the segment has flushed into its slot
   int Np = 0;               // the segment's problem: frames,
   long long rlen = 0;       // units per row of its block,
   VV* __restrict__ vrow = vg;  // and its v row 0 (looked up once per segment)
@@ -663,6 +729,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         if constexpr (kNarrow) acc[q] = 0.f;
+        else if constexpr (kComp) acc[q].zero();
         else acc[q] = LN::bc(0);
       }
       Np = pt.frames(f);
@@ -672,7 +739,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     if (consumer_acquire(a, pp, t, f, abort)) {
       const unsigned char* st = pp.smem + (size_t)(t % TC::S) * TC::STAGE;
       spc = reinterpret_cast<const PA*>(st + TC::ROFF);  // every stage carries the record
-      if constexpr (!BIG) {
+      if constexpr (!PSMEM) {
         if (seg_new) {  // this frequency's P and Lambda arrived with the tile
 #pragma unroll
           for (int r = 0; r < I; ++r)
@@ -704,6 +771,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         for (int j = 0; j < J; ++j) vv[j] = LN::real(vs[j * TC::T + q]);
         const bool full = n0 + FU <= Np;
         L r[I], e2[I];
+        L ztr[EM ? I : 1], zti[EM ? I : 1];  // EM: z_i = r_i y~_i
         L quad = LN::bc(0), lg = LN::bc(0);
 #pragma unroll
         for (int i = 0; i < I; ++i) {
@@ -728,6 +796,10 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           e2[i] = vfma(tr, tr, ti * ti);
           quad = vfma(e2[i], r[i], quad);
           lg = lg + vlog2(sg);
+          if constexpr (EM) {
+            ztr[i] = r[i] * tr;
+            zti[i] = r[i] * ti;
+          }
         }
         if (full) {
           ACC(NA, quad);
@@ -740,6 +812,7 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
           L w[I];
 #pragma unroll
           for (int i = 0; i < I; ++i) w[i] = r[i] * vfma(r[i], e2[i], LN::bc(-1));
+          L uj[EM ? J : 1];  // EM: u_j = v_j / s_j
 #pragma unroll
           for (int j = 0; j < J; ++j) {
             L tj[I];
@@ -750,13 +823,11 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
               sj = sj + tj[i];
             }
             const L rs = vrcp(sj);
+            if constexpr (EM) uj[j] = vv[j] * rs;
             const L vn = vv[j] * sj * LN::bc((T)(1.0 / I));
             if (full) {
 #pragma unroll
-              for (int i = 0; i < I; ++i) {
-                if constexpr (kNarrow) ACC(j * I + i, tj[i] * rs);
-                else acc[j * I + i] = vfma(tj[i], rs, acc[j * I + i]);
-              }
+              for (int i = 0; i < I; ++i) ACCF(j * I + i, tj[i], rs);
               vrow[(size_t)j * pt.Fm * rlen + k] = LN::store(vn);
             } else {
 #pragma unroll
@@ -764,6 +835,35 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
               vrow[(size_t)j * pt.Fm * rlen + k] = LN::store(LN::pick(vn, vv[j], n0, Np));
             }
           }
+          if constexpr (EM) {
+            // z_a conj(z_b) for a < b in row order, then u_j times it for every j
+            int pq = 0;
+#pragma unroll
+            for (int aa = 0; aa < I; ++aa)
+#pragma unroll
+              for (int bb = aa + 1; bb < I; ++bb, ++pq) {
+                const L zre = vfma(ztr[aa], ztr[bb], zti[aa] * zti[bb]);
+                const L zim = vfma(zti[aa], ztr[bb], (ztr[aa] * zti[bb]) * LN::bc(-1));
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                  const int q0 = NA + 2 + 2 * (j * NPAIR + pq);
+                  if (full) {
+                    ACCF(q0, uj[j], zre);
+                    ACCF(q0 + 1, uj[j], zim);
+                  } else {  // padding frames may hold anything: select, do not multiply
+                    ACC(q0, LN::keep(uj[j] * zre, n0, Np));
+                    ACC(q0 + 1, LN::keep(uj[j] * zim, n0, Np));
+                  }
+                }
+              }
+          }
+        }
+      }
+      if constexpr (kComp) {  // one Kahan step every kFoldTiles tile trips
+        if (++nfold == kFoldTiles) {
+          nfold = 0;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) acc[q].fold();
         }
       }
     }
@@ -771,15 +871,18 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
     seg_new = false;
     consumer_release(pp, t);
 
-    if (it.seg_end) {
+    // plain FP32 sums (kNarrow) are flushed into the slot every kFlushUnits
+    // units per thread; the same tiles reach every consumer of the group
+    const bool flush = kNarrow && !it.seg_end && ++ntile == flush_tiles(TC::T / kConsumers);
+    if (it.seg_end || flush) {
       const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
       if constexpr (kNarrow) {
-        Red::run(acc, red, out, rl, nseg);
-      } else if constexpr (sizeof(T) == 4) {
+        Red::run(acc, red, out, rl, nseg, flushed);
+      } else if constexpr (kComp) {
         float hi[NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
+        for (int q = 0; q < NV; ++q) hi[q] = acc[q].value();
         Red::run(hi, red, out, rl, nseg);
       } else {
         double hi[NV];
@@ -787,8 +890,18 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_estep(FastArgs a) {
         for (int q = 0; q < NV; ++q) hi[q] = acc[q].v;
         Red::run(hi, red, out, rl, nseg);
       }
-      ++nseg;  // the next segment reduces through the other buffer
-      seg_new = true;
+      ++nseg;  // the next reduction goes through the other buffer
+      ntile = 0;
+      if (flush) {
+        if constexpr (kNarrow) {
+#pragma unroll
+          for (int q = 0; q < NV; ++q) acc[q] = 0.f;
+        }
+        flushed = true;
+      } else {
+        flushed = false;
+        seg_new = true;
+      }
     }
   }
 }
@@ -868,6 +981,8 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
   };
   TileIter it(u0, u1, pt, TC::T, true);
   bool seg_new = true;
+  int ntile = 0;         // tile trips since the segment's start or last flush
+  bool flushed = false;  // the segment has flushed into its slot
   int Np = 0;  // frames of the segment's problem (looked up once per segment)
   for (int t = 0; it.next(); ++t) {
     const int f = it.f;
@@ -948,7 +1063,10 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
     seg_new = false;
     consumer_release(pp, t);
 
-    if (it.seg_end) {
+    // FP32: the plain sums are flushed into the slot every kFlushUnits units
+    // per thread (every lane of the group takes the same tile trips)
+    const bool flush = sizeof(T) == 4 && !it.seg_end && ++ntile == flush_tiles(TC::T / IG);
+    if (it.seg_end || flush) {
       const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * (I * I * I);
       T h[BE::NVT], l[BE::NVT];
@@ -992,10 +1110,24 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
           if constexpr (sizeof(T) == 4) df_add(sh, sl, Red::one(red)[w2][x], (T)0);
           else sh += Red::one(red)[w2][x];
         }
-        out[BE::out_index(x)] = (double)sh + (double)sl;
+        const double xv = (double)sh + (double)sl;
+        double& o = out[BE::out_index(x)];
+        o = flushed ? o + xv : xv;
       }
       consumer_sync(rl.group);
-      seg_new = true;
+      ntile = 0;
+      if (flush) {
+#pragma unroll
+        for (int i = 0; i < I; ++i) {
+          accd[i] = LN::bc(0);
+#pragma unroll
+          for (int k = 0; k < SL; ++k) acco[k][i] = T2{0, 0};
+        }
+        flushed = true;
+      } else {
+        flushed = false;
+        seg_new = true;
+      }
     }
   }
 }
@@ -1041,21 +1173,27 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
   } else {
     const int tid = rl.ctid;
     L lam[J][I];
-    // FP32 with I^3 > 32 sums: one float per value (both frames of a unit go
-    // into it) instead of a packed pair, which keeps the sums in registers
+    // FP32: Kahan-compensated sums (KSum, folded once per tile trip); with
+    // I^3 > 32 sums one plain float per value instead (both frames of a unit
+    // go into it), which keeps them in registers.  FP64: plain sums.
     constexpr bool kNarrow = sizeof(T) == 4 && NV > 32;
-    using A = std::conditional_t<kNarrow, float, L>;
+    constexpr bool kComp = sizeof(T) == 4 && !kNarrow;
+    using A = std::conditional_t<kNarrow, float, std::conditional_t<kComp, KSum, L>>;
     A acc[NV];
 
     TileIter it(u0, u1, pt, TC::T, true);
     bool seg_new = true;
-    int nseg = 0;  // segments reduced so far (reduction buffer parity)
+    int nseg = 0;          // reductions so far (reduction buffer parity)
+    int ntile = 0;         // tile trips since the segment's start or last flush
+    int nfold = 0;         // tile trips since the last Kahan step
+    bool flushed = false;  // the segment has flushed into its slot
     for (int t = 0; it.next(); ++t) {
       const int f = it.f;
       if (seg_new) {
   #pragma unroll
         for (int q = 0; q < NV; ++q) {
           if constexpr (kNarrow) acc[q] = 0.f;
+          else if constexpr (kComp) acc[q].zero();
           else acc[q] = LN::bc(0);
         }
       }
@@ -1109,6 +1247,8 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
             for (int i = 0; i < I; ++i) {
               if constexpr (kNarrow)
                 acc[i * I2 + mm] = fmaf(w[i].v.y, x.v.y, fmaf(w[i].v.x, x.v.x, acc[i * I2 + mm]));
+              else if constexpr (kComp)
+                acc[i * I2 + mm].p = fmaf(w[i].v.y, x.v.y, fmaf(w[i].v.x, x.v.x, acc[i * I2 + mm].p));
               else
                 acc[i * I2 + mm] = vfma(w[i], x, acc[i * I2 + mm]);
             }
@@ -1125,20 +1265,30 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
             }
           }
         }
+        if constexpr (kComp) {  // one Kahan step every kFoldTiles tile trips
+          if (++nfold == kFoldTiles) {
+            nfold = 0;
+  #pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q].fold();
+          }
+        }
       }
 
       seg_new = false;
       consumer_release(pp, t);
 
-      if (it.seg_end) {
+      // plain FP32 sums (kNarrow) are flushed into the slot every
+      // kFlushUnits units per thread (as in pass A)
+      const bool flush = kNarrow && !it.seg_end && ++ntile == flush_tiles(TC::T / kConsumers);
+      if (it.seg_end || flush) {
         const int slot = rl.vb - pt.first_block(f);
         double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * NV;
         if constexpr (kNarrow) {
-          Red::run(acc, red, out, rl, nseg);
-        } else if constexpr (sizeof(T) == 4) {
+          Red::run(acc, red, out, rl, nseg, flushed);
+        } else if constexpr (kComp) {
           float hi[NV];
   #pragma unroll
-          for (int q = 0; q < NV; ++q) hi[q] = acc[q].v.x + acc[q].v.y;  // the two frame lanes
+          for (int q = 0; q < NV; ++q) hi[q] = acc[q].value();
           Red::run(hi, red, out, rl, nseg);
         } else {
           double hi[NV];
@@ -1146,8 +1296,18 @@ __global__ void __maxnreg__((StreamRegs<T, I, J>::value)) k_wcov(FastArgs a) {
           for (int q = 0; q < NV; ++q) hi[q] = acc[q].v;
           Red::run(hi, red, out, rl, nseg);
         }
-        ++nseg;  // the next segment reduces through the other buffer
-        seg_new = true;
+        ++nseg;  // the next reduction goes through the other buffer
+        ntile = 0;
+        if (flush) {
+          if constexpr (kNarrow) {
+  #pragma unroll
+            for (int q = 0; q < NV; ++q) acc[q] = 0.f;
+          }
+          flushed = true;
+        } else {
+          flushed = false;
+          seg_new = true;
+        }
       }
     }
   }

@@ -124,6 +124,7 @@ def lib() -> ctypes.CDLL:
         "ffca_stft": (ci, [vp, ci, ctypes.c_longlong, vp, ci, vp]),
         "ffca_istft": (ci, [vp, ci, ci, ci, vp, vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
+        "ffca_peak_fp64": (ci, [vp, dp]),
         "ffca_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
@@ -280,6 +281,18 @@ def ffca_status_str(status: int) -> str:
     return lib().ffca_status_str(status).decode()
 
 
+def ffca_peak_fp64(stream=None) -> float:
+    """Measured FP64 rate of the current device in GFLOP/s (an FMA-chain
+    kernel on every SM, best of three launches); synchronises the stream."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    st = lib().ffca_peak_fp64(ctypes.c_void_p(s.cuda_stream), ctypes.byref(out))
+    if st != FFCA_OK:
+        raise FFCAError(st, "ffca_peak_fp64")
+    return out.value
+
+
 # ------------------------------------------------------------ conventional FCA
 def ffca_fca_workspace_size(desc: ffca_fca_desc) -> int:
     return int(lib().ffca_fca_workspace_size(ctypes.byref(desc)))
@@ -395,7 +408,7 @@ def ffca_set_graph(ctx, enable: bool) -> None:
 
 # Updates of P (ffca_p_update): the fixed point of Eq. FPI, or the gradient
 # methods of Sec. 4.6 with step size mu.
-P_UPDATES = {"fixed_point": 0, "gradient": 1, "natural_gradient": 2}
+P_UPDATES = {"fixed_point": 0, "gradient": 1, "natural_gradient": 2, "em": 3}
 
 
 def ffca_set_p_update(ctx, method: str, mu: float = 0.0) -> None:
@@ -479,7 +492,8 @@ class FastFCA:
 
     def set_p_update(self, method: str = "fixed_point", mu: float = 0.0):
         """Update of P in later iterations: "fixed_point" (Eq. FPI),
-        "gradient" or "natural_gradient" (Sec. 4.6) with step size mu."""
+        "gradient" or "natural_gradient" (Sec. 4.6) with step size mu, or
+        "em" (the normal EM of Sec. 4.6; mu unused)."""
         ffca_set_p_update(self.ctx, method, mu)
 
     def loglik(self) -> float:

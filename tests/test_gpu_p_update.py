@@ -1,7 +1,7 @@
 """GPU parity of the alternative updates of P (Sec. 4.6: the gradient and
-natural gradient methods, ffca_set_p_update) against the FP64 oracle, for
-single mixtures at every compiled I, with K > 1 steps, on batches and under
-graph replay; the inversion counts and the argument checks.
+natural gradient methods and the normal EM, ffca_set_p_update) against the
+FP64 oracle, for single mixtures at every compiled I, with K > 1 steps, on
+batches and under graph replay; the inversion counts and the argument checks.
 
 Tolerances as for the fixed point (normwise relative error per frequency,
 max over f): FP64 1e-9 on v, Lambda, P and L2; mixed 1e-4 on the
@@ -102,10 +102,10 @@ def test_argument_checks_keep_the_previous_update():
     est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
     est.set_p_update("natural_gradient", 0.2)
     L = ffca.lib()
-    for method, mu in [(3, 0.1), (-1, 0.1), (1, 0.0), (2, -0.5), (1, float("nan")), (2, float("inf"))]:
+    for method, mu in [(9, 0.1), (-1, 0.1), (1, 0.0), (2, -0.5), (1, float("nan")), (2, float("inf"))]:
         assert L.ffca_set_p_update(est.ctx, method, mu) == 1
     with pytest.raises(ValueError):
-        est.set_p_update("newton", 0.1)
+        est.set_p_update("bogus", 0.1)
     tr = est.iterate(2)
     ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter(), p_update="natural_gradient", mu=0.2)
     got = (vd[:, :, :N].cpu().numpy(), ld_.cpu().numpy(), Pd.cpu().numpy(), tr)
@@ -163,4 +163,136 @@ def test_batch_natural_gradient_matches_oracle(prec, I, J):
         assert np.all(np.abs(tr - t_ref) <= 1e-9 * np.abs(t_ref))
     else:
         assert np.all(np.abs(tr - t_ref) <= 1e-5 * NF)
+    est.close()
+
+
+# ------------------------------------------------------------ normal EM
+EM_SHAPES = [(1, 2, 3, 41), (2, 3, 4, 50), (3, 3, 5, 137), (4, 3, 3, 301), (3, 6, 2, 123), (2, 1, 3, 77),
+             (4, 5, 2, 96)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", EM_SHAPES)
+def test_em_iterations_match_oracle(prec, shape):
+    """Three iterations of the hybrid with the normal EM update of P (one
+    streaming pass per iteration), K = 1, from the perturbed truth; an EM
+    step, so L2 does not decrease."""
+    I, J, F, N = shape
+    p = make_problem(I, J, F, N, seed=400 + 10 * I + J)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 3, counter=OpCounter(), p_update="em")
+    assert np.all(np.diff(ref[3]) >= -1e-9 * np.abs(ref[3][1:]))
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 3, prec, p_update="em")
+    _compare(prec, ref, got, N, F)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("I", [2, 3, 4])
+def test_em_several_sweeps(prec, I):
+    """K = 3 sweeps of the M-step map per iteration (P^{-H} of each
+    intermediate P, the W_i of the entering state), on a ragged length with
+    NaN in the padding frames."""
+    p = make_problem(I, 3, 4, 91, seed=500 + I)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, K=3, counter=OpCounter(), p_update="em")
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec, K=3, p_update="em", ld=100, pad_value=float("nan"))
+    _compare(prec, ref, got, 91, 4)
+
+
+@pytest.mark.parametrize("I", [2, 4])
+def test_em_inversion_count_and_launches(I):
+    """(I+1) F K inversions per iteration, as the fixed point; one streaming
+    pass per iteration (no pass B launch)."""
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(I, 2, 7, 40, seed=6)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N, K=2)
+    est.set_p_update("em")
+    ffca.ffca_timing_read(est.ctx)
+    est.iterate(3, trace=False)
+    counts = ffca.ffca_timing_read(est.ctx)
+    assert est.inversion_count() == 3 * 7 * (I + 1) * 2
+    assert counts["estep"][1] == 3 and counts["wcov"][1] == 0 and counts["psolve"][1] == 3
+    est.close()
+
+
+def test_em_unsupported_at_eight_mics():
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(8, 6, 2, 40, seed=8, alpha=0.2, kappa=50.0)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
+    with pytest.raises(ffca.FFCAError):
+        est.set_p_update("em")
+    est.close()
+
+
+def test_em_graph_replay_and_switch():
+    """Two fixed-point iterations, then three EM iterations replayed from a
+    captured graph, against the oracle."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(3, 3, 5, 80, seed=13)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
+    est.set_graph(True)
+    est.iterate(2, trace=False)
+    est.set_p_update("em")
+    est.iterate(3, trace=False)
+    torch.cuda.synchronize()
+    v, lam, P, _ = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter())
+    ref = ffa.iterate(p.y, v, lam, P, 3, counter=OpCounter(), p_update="em")
+    got = (vd[:, :, :N].cpu().numpy(), ld_.cpu().numpy(), Pd.cpu().numpy(), ref[3])
+    _compare("fp64", ref, got, N, 5)
+    est.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("I,J", [(4, 3), (2, 2), (3, 3)])
+def test_batch_em_matches_oracle(prec, I, J):
+    """A ragged batch with the normal EM, per mixture against the oracle,
+    with the trace (the step's last block sums the problems' L2)."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    Ns = [37, 200, 9, 129, 64]
+    probs = make_batch(I, J, 3, Ns, seed=90 + I)
+    refs = [ffa.iterate(q.y, q.v0, q.lam0, q.P0, 3, counter=OpCounter(), p_update="em") for q in probs]
+    y, v, lam, P, Ns_, off = ffca.batch_to_device([q.y for q in probs], [q.v0 for q in probs],
+                                                  [q.lam0 for q in probs], [q.P0 for q in probs], prec=prec)
+    est = ffca.FastFCABatch(y, v, lam, P, Ns_)
+    est.set_p_update("em")
+    tr = est.iterate(3)
+    torch.cuda.synchronize()
+    vs = [b[:, :, :Ns_[m]].numpy() for m, b in enumerate(ffca.batch_views(v.double().cpu(), J, 3, off))]
+    lam_h, P_h = lam.cpu().numpy(), P.cpu().numpy()
+    for m, (q, r) in enumerate(zip(probs, refs)):
+        got = (vs[m], lam_h[m], P_h[m], r[3])
+        _compare(prec, r, got, q.N, q.F)
+    t_ref = np.sum([r[3] for r in refs], axis=0)
+    NF = sum(q.N * q.F for q in probs)
+    if prec == "fp64":
+        assert np.all(np.abs(tr - t_ref) <= 1e-9 * np.abs(t_ref))
+    else:
+        assert np.all(np.abs(tr - t_ref) <= 1e-5 * NF)
+    est.close()
+
+
+def test_batch_em_autotune_and_graph():
+    """Autotuning with the EM selected times the EM pass on pass A's
+    candidates; iterations replayed from a graph afterwards match the oracle
+    per mixture (the tuning iterations included)."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    Ns = [120, 33, 250]
+    probs = make_batch(4, 3, 4, Ns, seed=123)
+    y, v, lam, P, Ns_, off = ffca.batch_to_device([q.y for q in probs], [q.v0 for q in probs],
+                                                  [q.lam0 for q in probs], [q.P0 for q in probs], prec="fp64")
+    est = ffca.FastFCABatch(y, v, lam, P, Ns_, graph=True)
+    est.set_p_update("em")
+    rounds = 1
+    est.autotune(rounds=rounds)
+    n_tune = rounds * ffca.lib().ffca_batch_config_count()
+    est.iterate(2, trace=False)
+    torch.cuda.synchronize()
+    vs = [b[:, :, :Ns_[m]].numpy() for m, b in enumerate(ffca.batch_views(v.cpu(), 3, 4, off))]
+    for m, q in enumerate(probs):
+        r = ffa.iterate(q.y, q.v0, q.lam0, q.P0, n_tune + 2, counter=OpCounter(), p_update="em")
+        _compare("fp64", r, (vs[m], lam[m].cpu().numpy(), P[m].cpu().numpy(), r[3]), q.N, q.F)
     est.close()
