@@ -45,17 +45,21 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def sources_hash() -> str:
-    """Hash of the CUDA sources and the C header (names and contents): the
-    key under which measured DRAM traffic is stored, so that figures taken on
-    other kernel sources are not reported."""
+# The sources the streaming passes are compiled from (and the build flags).
+STREAM_SOURCES = ("paper_1805_09498_gb300/csrc/ffca_common.cuh", "paper_1805_09498_gb300/csrc/ffca_fastfca.cuh",
+                  "paper_1805_09498_gb300/csrc/ffca_stream.cuh", "paper_1805_09498_gb300/build.py")
+
+
+def sources_hash(files=STREAM_SOURCES) -> str:
+    """Hash of the given source files (names and contents): the key under
+    which figures measured by ncu are stored, so that figures taken on other
+    kernel sources are not reported."""
     import hashlib
     h = hashlib.sha256()
-    for d in (os.path.join(ROOT, "paper_1805_09498_gb300", "csrc"), os.path.join(ROOT, "include")):
-        for f in sorted(os.listdir(d)):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode())
-                h.update(fh.read())
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

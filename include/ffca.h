@@ -159,18 +159,27 @@ ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
  * it counts (I+1) F K inversions per iteration like the fixed point, ignores
  * mu and guarantees an L2 that does not decrease (an EM step).  Compiled for
  * I <= 4 (FFCA_ERR_UNSUPPORTED at I = 8). */
+/* FFCA_P_NEWTON is Newton's method on L2 with the V_i of Eq. FPI held fixed
+ * (Sec. 4.6 names it), in the 2 I^2 real coordinates of P, off the I
+ * directions p_i -> e^{i t} p_i along which L2 does not change: K steps of
+ * size mu per iteration, each solving (Q' H Q' - Pi) s = -Q' g (H and g the
+ * Hessian and gradient of L2 / N, Pi the projector on those directions, Q' =
+ * 1 - Pi) and moving P by mu s; two inversions per step (P and the system).
+ * It converges quadratically near a maximum and is not globally convergent
+ * (mu damps it).  Compiled for I <= 4 (FFCA_ERR_UNSUPPORTED at I = 8). */
 typedef enum {
   FFCA_P_FIXED_POINT = 0,
   FFCA_P_GRADIENT = 1,
   FFCA_P_NATURAL_GRADIENT = 2,
-  FFCA_P_EM = 3
+  FFCA_P_EM = 3,
+  FFCA_P_NEWTON = 4
 } ffca_p_update;
 
 /* Select the update of P for later iterations of a single or batch context.
- * mu: step size, finite and > 0 for the gradient methods (ignored for the
- * fixed point and the EM).  Drops a captured graph.  FFCA_ERR_ARG for an
- * unknown method or an invalid mu, FFCA_ERR_UNSUPPORTED for the EM at I = 8
- * (the context keeps its previous choice).  With the EM, ffca_timing_read
+ * mu: step size, finite and > 0 for the gradient methods and Newton's
+ * (ignored for the fixed point and the EM).  Drops a captured graph.
+ * FFCA_ERR_ARG for an unknown method or an invalid mu, FFCA_ERR_UNSUPPORTED
+ * for the EM or Newton at I = 8 (the context keeps its previous choice).  With the EM, ffca_timing_read
  * counts its streaming pass as FFCA_KERNEL_ESTEP and its per-problem step as
  * FFCA_KERNEL_PSOLVE, and ffca_batch_autotune tunes the EM pass on pass A's
  * candidates.  The allocation-free call always uses the fixed point. */

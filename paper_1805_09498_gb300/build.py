@@ -25,7 +25,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
 I_VALUES = (1, 2, 3, 4, 8)      # FastFCA-AS, conventional FCA
-I_VALUES_SMALL = (1, 2, 3, 4)   # adjoint
+I_VALUES_SMALL = (1, 2, 3, 4)   # adjoint, normal EM, Newton
 
 
 def _nvcc():
@@ -39,7 +39,7 @@ def _units():
     """(source, object, extra flags) for every translation unit."""
     units = [("ffca_api.cu", "ffca_api.o", []), ("ffca_fca_api.cu", "ffca_fca_api.o", []),
              ("ffca_stft.cu", "ffca_stft.o", []), ("ffca_probe.cu", "ffca_probe.o", [])]
-    for part in (0, 1, 2):  # FastFCA-AS, conventional FCA, adjoint
+    for part in (0, 1, 2, 3, 4):  # FastFCA-AS, conventional FCA, adjoint, normal EM, Newton
         for prec in (0, 1):
             for i in (I_VALUES if part in (0, 1) else I_VALUES_SMALL):
                 units.append(("ffca_inst.cu", f"ffca_inst_k{part}_p{prec}_i{i}.o",

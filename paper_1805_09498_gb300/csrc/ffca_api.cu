@@ -136,10 +136,13 @@ ffca_status query_occupancy(const FastKernels* k, Occupancy* o) {
   if (!cuda_ok(cudaDeviceGetAttribute(&o->nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute"))
     return FFCA_ERR_CUDA;
   // the streaming passes take more than the default 48 KB of dynamic shared memory
-  for (const void* fn : {k->estep_update, k->estep_eval, k->wcov})
+  for (const void* fn : {k->estep_update, k->estep_eval})
     if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->stream_smem),
                  "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)"))
       return FFCA_ERR_CUDA;
+  if (!cuda_ok(cudaFuncSetAttribute(k->wcov, cudaFuncAttributeMaxDynamicSharedMemorySize, k->wcov_smem),
+               "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, pass B)"))
+    return FFCA_ERR_CUDA;
   if (k->estep_em &&
       (!cuda_ok(cudaFuncSetAttribute(k->estep_em, cudaFuncAttributeMaxDynamicSharedMemorySize, k->em_smem),
                 "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, EM pass)") ||
@@ -155,7 +158,8 @@ ffca_status query_occupancy(const FastKernels* k, Occupancy* o) {
   const int sthreads = kGroupThreads * k->stream_groups;
   if (!cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occA, k->estep_update, sthreads, k->stream_smem),
                "occupancy(pass A)") ||
-      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occB, k->wcov, sthreads, k->stream_smem),
+      !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occB, k->wcov, kGroupThreads * k->wcov_groups,
+                                                             k->wcov_smem),
                "occupancy(pass B)") ||
       !cuda_ok(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o->occW, k->wiener, kBlock, 0), "occupancy(Wiener)"))
     return FFCA_ERR_CUDA;
@@ -207,7 +211,7 @@ ffca_status make_plan(const ffca_desc* d, const FastKernels* k, Plan* p) {
   const int F = d->F > 0 ? d->F : 1;
   // the streaming partitions count virtual blocks: stream_groups pipelines per CTA
   p->pA = make_partition(F, Uf, o.nsm * o.occA * k->stream_groups * FFCA_GRID_WAVES, d->N);
-  p->pB = make_partition(F, Uf, o.nsm * o.occB * k->stream_groups * FFCA_GRID_WAVES, d->N);
+  p->pB = make_partition(F, Uf, o.nsm * o.occB * k->wcov_groups * FFCA_GRID_WAVES, d->N);
   // the Wiener pass also covers the padding frames (it writes them as zero)
   p->pW = make_partition(F, d->ld / FU, o.nsm * o.occW, d->N);
   p->pA.F = p->pB.F = p->pW.F = d->F;
@@ -356,15 +360,17 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
 
-// Blocks of the P step: one warp per 32 / I problems, plus the trace's block.
+// Blocks of the P step: one warp per 32 / I problems (Newton: one warp per
+// problem), plus the trace's block.
 int p_step_grid(const ffca_ctx* c, const FastArgs& b) {
-  const int G = 32 / c->d.I;
+  const int G = c->pmode == kPNewton ? 1 : 32 / c->d.I;
   return (c->d.F + G - 1) / G + (b.trace ? 1 : 0);
 }
 
-// The P step of the context's update of P.
+// The P step of the context's update of P (after pass B).
 const void* p_step_kernel(const ffca_ctx* c) {
-  return c->pmode == kPFixedPoint ? c->kern->psolve : c->kern->pgrad;
+  if (c->pmode == kPNewton) return c->kern->pnewton;
+  return c->pmode == kPGradient || c->pmode == kPNatural ? c->kern->pgrad : c->kern->psolve;
 }
 
 int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
@@ -390,11 +396,16 @@ ffca_status launch_em_iteration(ffca_ctx* c, int slot, bool trace) {
   return launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve_em, (c->d.F + G - 1) / G, 32, a, c->kern->em_solve_smem);
 }
 
-// CTAs of a streaming pass: each runs stream_groups virtual blocks of the partition.
+// CTAs of a streaming pass: each runs stream_groups (pass A) or wcov_groups
+// (pass B) virtual blocks of the partition.
 int stream_grid(const ffca_ctx* c, const Partition& p) {
   return (p.nblocks + c->kern->stream_groups - 1) / c->kern->stream_groups;
 }
 int stream_threads(const ffca_ctx* c) { return kGroupThreads * c->kern->stream_groups; }
+int wcov_grid(const ffca_ctx* c, const Partition& p) {
+  return (p.nblocks + c->kern->wcov_groups - 1) / c->kern->wcov_groups;
+}
+int wcov_threads(const ffca_ctx* c) { return kGroupThreads * c->kern->wcov_groups; }
 
 void drop_timed(ffca_ctx* c) {
   for (size_t k = 0; k < c->ntimed; ++k) {
@@ -437,8 +448,8 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
       return st;
     FastArgs b = pass_b_args(c, slot);
     b.trace = nullptr;  // no trace: no trace block in the P step
-    if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
-                     c->kern->stream_smem)) != FFCA_OK)
+    if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, wcov_grid(c, b.part), wcov_threads(c), b,
+                     c->kern->wcov_smem)) != FFCA_OK)
       return st;
     if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
   }
@@ -626,8 +637,8 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
         return st;
       FastArgs b = pass_b_args(c, slot);
       if (!ll_trace) b.trace = nullptr;  // no trace block in the P step
-      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
-                      c->kern->stream_smem)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, wcov_grid(c, b.part), wcov_threads(c), b,
+                      c->kern->wcov_smem)) != FFCA_OK)
         return st;
       if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem)) != FFCA_OK)
         return st;
@@ -964,7 +975,7 @@ ffca_status batch_plan(const ffca_batch_desc* d, const FastKernels* k, Plan* p, 
   t->candW = make_partition_ragged(P, d->F, t->ustartW.data(), o.nsm * o.occW, 0, t->bstartW.data(),
                                    t->slotsW.data());
   t->bstartW.resize(t->candW.nblocks + 1);
-  const int slotsA = o.nsm * o.occA * k->stream_groups, slotsB = o.nsm * o.occB * k->stream_groups;
+  const int slotsA = o.nsm * o.occA * k->stream_groups, slotsB = o.nsm * o.occB * k->wcov_groups;
   int msA = 1, msB = 1;
   for (int c = 0; c < kCands; ++c) {
     const int maxA = slotsA * kCandA[c].waves, maxB = slotsB * kCandB[c].waves;
@@ -1174,8 +1185,8 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
       FastArgs b = pass_b_args(c, 0);
       b.trace = nullptr;
       if (st == FFCA_OK)
-        st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, stream_grid(c, b.part), stream_threads(c), b,
-                    c->kern->stream_smem);
+        st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, wcov_grid(c, b.part), wcov_threads(c), b,
+                    c->kern->wcov_smem);
       cudaEventRecord(ev[q][2], c->stream);
       if (st == FFCA_OK)
         st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem);
@@ -1210,17 +1221,18 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
 void ffca_batch_destroy(ffca_batch_ctx* c) { ffca_destroy(c); }
 
 static_assert(FFCA_P_FIXED_POINT == kPFixedPoint && FFCA_P_GRADIENT == kPGradient &&
-                  FFCA_P_NATURAL_GRADIENT == kPNatural && FFCA_P_EM == kPEM,
+                  FFCA_P_NATURAL_GRADIENT == kPNatural && FFCA_P_EM == kPEM && FFCA_P_NEWTON == kPNewton,
               "the ABI's P-update codes are the kernels' modes");
 
 ffca_status ffca_set_p_update(ffca_ctx* c, int method, double mu) {
   if (!c) return FFCA_ERR_ARG;
   if (method != FFCA_P_FIXED_POINT && method != FFCA_P_GRADIENT && method != FFCA_P_NATURAL_GRADIENT &&
-      method != FFCA_P_EM)
+      method != FFCA_P_EM && method != FFCA_P_NEWTON)
     return FFCA_ERR_ARG;
-  const bool stepped = method == FFCA_P_GRADIENT || method == FFCA_P_NATURAL_GRADIENT;
+  const bool stepped = method == FFCA_P_GRADIENT || method == FFCA_P_NATURAL_GRADIENT || method == FFCA_P_NEWTON;
   if (stepped && !(std::isfinite(mu) && mu > 0.0)) return FFCA_ERR_ARG;
   if (method == FFCA_P_EM && !c->kern->estep_em) return FFCA_ERR_UNSUPPORTED;
+  if (method == FFCA_P_NEWTON && !c->kern->pnewton) return FFCA_ERR_UNSUPPORTED;
   c->pmode = method;
   c->mu = stepped ? mu : 0.0;
   if (c->graph) {  // the captured launches hold the previous arguments

@@ -26,6 +26,9 @@ struct FastKernels {
   int em_solve_smem;         // dynamic shared memory of psolve_em
   int em_nv;                 // sums per slot of estep_em
   int em_groups;             // pipeline groups per CTA of estep_em
+  const void* pnewton;       // the P step with Newton's method (one warp per problem; nullptr for I > 4)
+  int wcov_groups;           // pipeline groups per CTA of pass B (stream_groups: pass A)
+  int wcov_smem;             // dynamic shared memory of pass B (stream_smem: pass A)
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.
@@ -71,5 +74,21 @@ FFCA_DECLARE_TABLE(1, 3)
 FFCA_DECLARE_TABLE(1, 4)
 FFCA_DECLARE_TABLE(1, 8)
 #undef FFCA_DECLARE_TABLE
+
+// The normal EM and Newton kernels of one precision and I <= 4 (compiled in
+// their own translation units).
+#define FFCA_DECLARE_ALT(P, I) \
+  const void* em_estep_p##P##_i##I(int J); \
+  const void* em_psolve_p##P##_i##I(int J); \
+  const void* newton_p##P##_i##I(int J);
+FFCA_DECLARE_ALT(0, 1)
+FFCA_DECLARE_ALT(0, 2)
+FFCA_DECLARE_ALT(0, 3)
+FFCA_DECLARE_ALT(0, 4)
+FFCA_DECLARE_ALT(1, 1)
+FFCA_DECLARE_ALT(1, 2)
+FFCA_DECLARE_ALT(1, 3)
+FFCA_DECLARE_ALT(1, 4)
+#undef FFCA_DECLARE_ALT
 
 }  // namespace ffca

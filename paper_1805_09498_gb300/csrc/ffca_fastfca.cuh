@@ -43,7 +43,7 @@ struct FastArgs {
   double* lam_next;          // [F][J][I] the new Lambda, written during pass B, committed by k_psolve
   Partition prev_part;       // pass B reads pass A's slots: their partition
   const double* prev_buf;    // and buffer
-  int pmode;                 // update of P: kPFixedPoint, kPGradient, kPNatural or kPEM
+  int pmode;                 // update of P: kPFixedPoint, kPGradient, kPNatural, kPEM or kPNewton
   double mu;                 // step size of the gradient updates
   int fault;                 // injected fault (tests of failure detection): kFault*
 };
@@ -65,13 +65,17 @@ constexpr int kPFixedPoint = 0;
 constexpr int kPGradient = 1;
 constexpr int kPNatural = 2;
 constexpr int kPEM = 3;
+constexpr int kPNewton = 4;  // K Newton steps of size mu (ffca_newton.cuh)
 
 // Matrix inversions per problem of one P update: (I+1) K for the fixed
 // point (Sec. 4.5) and for the normal EM (the same map on other matrices),
-// one P^{-H} per gradient step, none for the natural gradient.
+// one P^{-H} per gradient step, none for the natural gradient, two per
+// Newton step (P and the 2 I^2 system).
 __device__ inline unsigned long long p_update_inversions(const FastArgs& a, int I) {
-  return (a.pmode == kPFixedPoint || a.pmode == kPEM) ? (unsigned long long)(I + 1) * a.K
-                                                      : (a.pmode == kPGradient ? (unsigned long long)a.K : 0ull);
+  if (a.pmode == kPFixedPoint || a.pmode == kPEM) return (unsigned long long)(I + 1) * a.K;
+  if (a.pmode == kPGradient) return (unsigned long long)a.K;
+  if (a.pmode == kPNewton) return 2ull * a.K;
+  return 0ull;
 }
 
 // Per-frequency parameters in the per-point precision T, laid out as they
@@ -111,6 +115,24 @@ struct ParamsA {
     }
   }
 };
+// Pass A's record of problem f for a J known only at run time (the layout
+// of ParamsA<T, I, J> with single values): P's real parts, its imaginary
+// parts, then Lambda.
+template <typename T, int I>
+struct ParamsARun {
+  T* v;
+  __device__ ParamsARun(void* tab, int J, int f) {
+    const size_t bytes = (sizeof(T) * (2 * I * I + (size_t)J * I) + 15) / 16 * 16;
+    v = reinterpret_cast<T*>(static_cast<char*>(tab) + (size_t)f * bytes);
+  }
+  __device__ void set_p(int r, int c, T re, T im) {
+    v[r * I + c] = re;
+    v[I * I + r * I + c] = im;
+  }
+  __device__ void set_lam(int j, int i, T l) { v[2 * I * I + j * I + i] = l; }
+};
+static_assert(!ParamsA<float, 1, 1>::DUP, "ParamsARun assumes single values");
+
 template <typename T, int I, int J>
 struct ParamsB {  // pass B: the new Lambda(f)
   T lam[J][I];

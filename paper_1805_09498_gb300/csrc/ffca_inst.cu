@@ -1,6 +1,8 @@
 // Explicit instantiations of the FastFCA-AS kernels (FFCA_PART 0), of the
-// conventional FCA kernels (FFCA_PART 1) or of the adjoint kernels
-// (FFCA_PART 2) for one precision and one microphone count, J = 1..6.
+// conventional FCA kernels (FFCA_PART 1), of the adjoint kernels
+// (FFCA_PART 2), of the normal EM update of P (FFCA_PART 3) or of Newton's
+// method for P (FFCA_PART 4) for one precision and one microphone count,
+// J = 1..6 (parts 3 and 4: I <= 4).
 // Compiled once per (FFCA_PART, FFCA_PREC, FFCA_I).
 #include "ffca_adjoint.cuh"
 #include "ffca_big.cuh"
@@ -8,6 +10,7 @@
 #include "ffca_em.cuh"
 #include "ffca_fca.cuh"
 #include "ffca_fca_big.cuh"
+#include "ffca_newton.cuh"
 #include "ffca_stream.cuh"
 
 #ifndef FFCA_PREC
@@ -17,8 +20,11 @@
 #error "FFCA_I must be defined"
 #endif
 #ifndef FFCA_PART
-#error "FFCA_PART must be defined (0 = FastFCA-AS, 1 = FCA, 2 = adjoint)"
+#error "FFCA_PART must be defined (0 = FastFCA-AS, 1 = FCA, 2 = adjoint, 3 = normal EM, 4 = Newton)"
 #endif
+
+#define FFCA_CAT2(a, b, c, d) a##b##c##d
+#define FFCA_CAT(a, b, c, d) FFCA_CAT2(a, b, c, d)
 
 namespace ffca {
 
@@ -54,17 +60,21 @@ static const FastKernels* table_entry() {
   }
   if constexpr (BIG) wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
   else wiener = (const void*)k_wiener<Real, FFCA_I, J>;
+  // the normal EM and Newton kernels are compiled in translation units of
+  // their own (FFCA_PART 3 and 4), so that they build in parallel
   const void* estep_em = nullptr;
   const void* psolve_em = nullptr;
+  const void* pnewton = nullptr;
   int em_smem = 0, em_solve_smem = 0, em_nv = 0, em_groups = 1;
-  if constexpr (!BIG) {
-    estep_em = (const void*)k_estep<Real, FFCA_I, J, true, true>;
-    psolve_em = (const void*)k_psolve_em<Real, FFCA_I, J>;
-    em_groups = EmGroups<Real, FFCA_I, J>::value;
-    em_smem = em_groups * Tile<Real, FFCA_I, J, EmGroups<Real, FFCA_I, J>::value>::GROUP;
-    em_solve_smem = EmShape<FFCA_I, J>::SMEM;
-    em_nv = EmShape<FFCA_I, J>::NV;
-  }
+#if FFCA_I <= 4
+  estep_em = FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(J);
+  psolve_em = FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(J);
+  em_groups = EmGroups<Real, FFCA_I, J>::value;
+  em_smem = em_groups * Tile<Real, FFCA_I, J, EmGroups<Real, FFCA_I, J>::value>::GROUP;
+  em_solve_smem = EmShape<FFCA_I, J>::SMEM;
+  em_nv = EmShape<FFCA_I, J>::NV;
+  pnewton = FFCA_CAT(newton_p, FFCA_PREC, _i, FFCA_I)(J);
+#endif
   static const FastKernels k = {
       Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
       StreamGroups<Real, FFCA_I, J>::value,
@@ -86,6 +96,9 @@ static const FastKernels* table_entry() {
       em_solve_smem,
       em_nv,
       em_groups,
+      pnewton,
+      WcovGroups<Real, FFCA_I, J>::value,
+      WcovGroups<Real, FFCA_I, J>::value * Tile<Real, FFCA_I, J, WcovGroups<Real, FFCA_I, J>::value>::GROUP,
   };
   return &k;
 }
@@ -142,8 +155,6 @@ static const AdjKernels* adj_entry() {
 
 #endif
 
-#define FFCA_CAT2(a, b, c, d) a##b##c##d
-#define FFCA_CAT(a, b, c, d) FFCA_CAT2(a, b, c, d)
 
 #if FFCA_PART == 0
 const FastKernels* FFCA_CAT(fast_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
@@ -185,6 +196,33 @@ const AdjKernels* FFCA_CAT(adj_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
     case 6: return adj_entry<6>();
     default: return nullptr;
   }
+}
+#endif
+
+#if FFCA_PART == 3
+template <int J>
+static const void* em_pair(bool step) {
+  return step ? (const void*)k_psolve_em<Real, FFCA_I, J> : (const void*)k_estep<Real, FFCA_I, J, true, true>;
+}
+static const void* em_select(int J, bool step) {
+  switch (J) {
+    case 1: return em_pair<1>(step);
+    case 2: return em_pair<2>(step);
+    case 3: return em_pair<3>(step);
+    case 4: return em_pair<4>(step);
+    case 5: return em_pair<5>(step);
+    case 6: return em_pair<6>(step);
+    default: return nullptr;
+  }
+}
+const void* FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, false); }
+const void* FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, true); }
+#endif
+
+#if FFCA_PART == 4
+// one kernel for every J (J is read from the arguments)
+const void* FFCA_CAT(newton_p, FFCA_PREC, _i, FFCA_I)(int J) {
+  return (J >= 1 && J <= 6) ? (const void*)k_psolve_newton<Real, FFCA_I> : nullptr;
 }
 #endif
 

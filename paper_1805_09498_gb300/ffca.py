@@ -408,7 +408,7 @@ def ffca_set_graph(ctx, enable: bool) -> None:
 
 # Updates of P (ffca_p_update): the fixed point of Eq. FPI, or the gradient
 # methods of Sec. 4.6 with step size mu.
-P_UPDATES = {"fixed_point": 0, "gradient": 1, "natural_gradient": 2, "em": 3}
+P_UPDATES = {"fixed_point": 0, "gradient": 1, "natural_gradient": 2, "em": 3, "newton": 4}
 
 
 def ffca_set_p_update(ctx, method: str, mu: float = 0.0) -> None:
@@ -492,8 +492,8 @@ class FastFCA:
 
     def set_p_update(self, method: str = "fixed_point", mu: float = 0.0):
         """Update of P in later iterations: "fixed_point" (Eq. FPI),
-        "gradient" or "natural_gradient" (Sec. 4.6) with step size mu, or
-        "em" (the normal EM of Sec. 4.6; mu unused)."""
+        "gradient", "natural_gradient" or "newton" (Sec. 4.6) with step size
+        mu, or "em" (the normal EM of Sec. 4.6; mu unused)."""
         ffca_set_p_update(self.ctx, method, mu)
 
     def loglik(self) -> float:

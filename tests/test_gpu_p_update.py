@@ -296,3 +296,85 @@ def test_batch_em_autotune_and_graph():
         r = ffa.iterate(q.y, q.v0, q.lam0, q.P0, n_tune + 2, counter=OpCounter(), p_update="em")
         _compare("fp64", r, (vs[m], lam[m].cpu().numpy(), P[m].cpu().numpy(), r[3]), q.N, q.F)
     est.close()
+
+
+# ------------------------------------------------------------ Newton's method
+def _fpi_then(p, fpi_iters, method, iters, mu, K=1):
+    """Oracle: fixed-point iterations to come near a maximum, then `iters`
+    iterations with `method` (Newton converges only locally)."""
+    v, lam, P, _ = ffa.iterate(p.y, p.v0, p.lam0, p.P0, fpi_iters, counter=OpCounter())
+    return (v, lam, P), ffa.iterate(p.y, v, lam, P, iters, K=K, counter=OpCounter(), p_update=method, mu=mu)
+
+
+def _gpu_from(y, state, iters, prec, method, mu, K=1, N=None):
+    return run_gpu(y, *state, iters, prec, K=K, p_update=method, mu=mu)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(1, 2, 3, 41), (2, 3, 4, 150), (3, 3, 5, 237), (4, 3, 3, 301), (3, 6, 2, 223)])
+def test_newton_iterations_match_oracle(prec, shape):
+    """Six fixed-point iterations (oracle), then three hybrid iterations with
+    Newton's method for P (mu = 1) from that state on both sides.  Newton's
+    method converges only locally: the cases are ones where the oracle's L2
+    rises, so that rounding is not amplified by a diverging step."""
+    I, J, F, N = shape
+    p = make_problem(I, J, F, N, seed=600 + 10 * I + J)
+    state, ref = _fpi_then(p, 6, "newton", 3, 1.0)
+    assert np.all(np.diff(ref[3]) > 0)
+    got = _gpu_from(p.y, state, 3, prec, "newton", 1.0)
+    _compare(prec, ref, got, N, F)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("I", [2, 3, 4])
+def test_newton_several_steps_damped(prec, I):
+    """K = 2 damped Newton steps (mu = 0.5) per iteration, after twenty
+    fixed-point iterations (at I = 4 six leave the oracle's Newton steps
+    lowering L2)."""
+    p = make_problem(I, 3, 4, 180, seed=700 + I)
+    state, ref = _fpi_then(p, 20, "newton", 2, 0.5, K=2)
+    assert np.all(np.diff(ref[3]) > 0)
+    got = run_gpu(p.y, *state, 2, prec, K=2, p_update="newton", mu=0.5)
+    _compare(prec, ref, got, 180, 4)
+
+
+def test_newton_inversion_count_and_checks():
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(3, 2, 7, 60, seed=7)
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N, K=2)
+    L = ffca.lib()
+    assert L.ffca_set_p_update(est.ctx, 4, 0.0) == 1  # Newton needs a step size > 0
+    est.set_p_update("newton", 0.5)
+    est.iterate(2, trace=False)
+    assert est.inversion_count() == 2 * 7 * 2 * 2
+    est.close()
+    q = make_problem(8, 6, 2, 40, seed=8, alpha=0.2, kappa=50.0)
+    yd, vd, ld_, Pd, N = ffca.to_device(q.y, q.v0, q.lam0, q.P0, prec="mixed")
+    e8 = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
+    with pytest.raises(ffca.FFCAError):
+        e8.set_p_update("newton", 1.0)
+    e8.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_newton_matches_oracle(prec):
+    """A ragged batch: six fixed-point iterations, then two Newton
+    iterations, per mixture against the oracle."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    I, J = 3, 3
+    Ns = [137, 300, 64, 210]
+    probs = make_batch(I, J, 3, Ns, seed=140)
+    y, v, lam, P, Ns_, off = ffca.batch_to_device([q.y for q in probs], [q.v0 for q in probs],
+                                                  [q.lam0 for q in probs], [q.P0 for q in probs], prec=prec)
+    est = ffca.FastFCABatch(y, v, lam, P, Ns_)
+    est.iterate(6, trace=False)
+    est.set_p_update("newton", 1.0)
+    tr = est.iterate(2)
+    torch.cuda.synchronize()
+    vs = [b[:, :, :Ns_[m]].numpy() for m, b in enumerate(ffca.batch_views(v.double().cpu(), J, 3, off))]
+    for m, q in enumerate(probs):
+        _, r = _fpi_then(q, 6, "newton", 2, 1.0)
+        _compare(prec, r, (vs[m], lam[m].cpu().numpy(), P[m].cpu().numpy(), r[3]), q.N, q.F)
+    est.close()
