@@ -41,9 +41,18 @@
  * Precision (ffca_precision):
  *  - FFCA_PREC_FP64:  every per-(n,f) operation and reduction in FP64.
  *  - FFCA_PREC_MIXED: per-(n,f) arithmetic in FP32 on complex64/float data;
- *    reductions over n are compensated (Kahan / TwoSum double-float) in FP32
- *    and finished in FP64; Lambda, P, the per-frequency I x I solves and the
- *    log-likelihood totals are FP64.
+ *    Lambda, P, the per-frequency I x I solves and the log-likelihood totals
+ *    are FP64.  Sums over the frames n: each thread's running sum is
+ *    Kahan-compensated in FP32 (folded every few tiles) where a thread holds
+ *    at most 32 sums, so that the registers hold a compensation term for
+ *    each (pass A for I <= 4, pass B for I <= 3, the normal EM's pass when
+ *    J I^2 + 2 <= 32); elsewhere (pass B at I = 4, both passes at I = 8, the
+ *    normal EM's pass with more sums) a thread's plain FP32 sum is flushed
+ *    into the FP64 partial sums every 64 (pass B at I = 8: 128) units of two
+ *    frames, so that no FP32 sum runs over more frames than that however long
+ *    the mixture is.  The 32 lanes
+ *    of a warp are then summed by a five-level pairwise tree in FP32, the
+ *    warps' sums in double-float (TwoSum), and the partial sums in FP64.
  *
  * Supported shapes: I in {1, 2, 3, 4, 8}, 1 <= J <= 6 (FFCA_ERR_UNSUPPORTED
  * otherwise; the gradients take I <= 4 only), N >= 1, F >= 0 (F == 0 is a
@@ -184,6 +193,28 @@ typedef enum {
  * FFCA_KERNEL_PSOLVE, and ffca_batch_autotune tunes the EM pass on pass A's
  * candidates.  The allocation-free call always uses the fixed point. */
 ffca_status ffca_set_p_update(ffca_ctx* ctx, int method, double mu);
+
+/* Mask-based initialisation (Sec. 5 initialises the parameters by mask-based
+ * covariance matrix estimation from time-frequency masks; the masks are the
+ * caller's, the masking method is not part of this library).  Writes the
+ * context's v, lambda and P from its mixture y and the masks:
+ *  1. R_j(f) = sum_n m_j(n,f) y y^H / sum_n m_j(n,f)  (FP64 sums);
+ *  2. P(f) the generalized eigenvectors of (R_1, R_y), R_y = sum_j R_j, in
+ *     ascending order of their eigenvalues, each column turned in phase so
+ *     that its entry of largest magnitude is real and positive (the GEVD that
+ *     gives P and Lambda for two sources, Sec. 4.1; exact for any J whenever
+ *     the R_j are jointly diagonalisable), then `sweeps` alternations
+ *     lambda_ji = p_i^H R_j p_i, p_i <- V_i^{-1} [P^{-H}]_i with
+ *     V_i = (1/J) sum_j R_j / lambda_ji (Eq. FPI on the covariances), and
+ *     lambda_ji = p_i^H R_j p_i of the final P;
+ *  3. v_j(n,f) = max(m_j(n,f), delta) (1/I) sum_i |[P^H y]_i|^2 / lambda_ji
+ *     (frames n >= N untouched).
+ * masks: device, the layout and real type of v ([J][F][ld]; a batch: the
+ * batch layout of v), 16-byte aligned, m_j >= 0 with sum_n m_j(n,f) > 0 for
+ * every (j, f).  sweeps: 0 .. 1000 (10 is a good start); delta in (0, 1].
+ * Synchronises and returns the device status: FFCA_ERR_NONFINITE for an
+ * all-zero mask row, FFCA_ERR_SINGULAR for a singular R_y or sweep. */
+ffca_status ffca_mask_init(ffca_ctx* ctx, const void* masks, int sweeps, double delta);
 
 /* Fault injection for tests of failure detection (no GPU fault is made).
  * FFCA_FAULT_PASS_A_NO_COPIES: from the next call on, the producer warps of

@@ -38,7 +38,8 @@ def _nvcc():
 def _units():
     """(source, object, extra flags) for every translation unit."""
     units = [("ffca_api.cu", "ffca_api.o", []), ("ffca_fca_api.cu", "ffca_fca_api.o", []),
-             ("ffca_stft.cu", "ffca_stft.o", []), ("ffca_probe.cu", "ffca_probe.o", [])]
+             ("ffca_stft.cu", "ffca_stft.o", []), ("ffca_probe.cu", "ffca_probe.o", []),
+             ("ffca_mask.cu", "ffca_mask.o", [])]
     for part in (0, 1, 2, 3, 4):  # FastFCA-AS, conventional FCA, adjoint, normal EM, Newton
         for prec in (0, 1):
             for i in (I_VALUES if part in (0, 1) else I_VALUES_SMALL):

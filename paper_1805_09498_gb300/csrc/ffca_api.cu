@@ -16,6 +16,7 @@
 #include "ffca.h"
 #include "ffca_adjoint.cuh"
 #include "ffca_dispatch.h"
+#include "ffca_mask.cuh"
 #include "ffca_stream.cuh"
 
 using namespace ffca;
@@ -104,6 +105,7 @@ struct Plan {
   size_t off_partAdj, off_lossf, off_loss;  // adjoint: slots, per-frequency and total loss
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t off_partE;  // the normal EM's pass-A slots (pass A's partition, em_nv sums each)
+  size_t off_maskR;  // the masked covariances of ffca_mask_init [problems][J][I][I] complex
   size_t bytes;
 };
 
@@ -191,6 +193,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_tabB = off; off = align_up(off + (size_t)P * k->params_b_bytes);
   p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)P * J * I);
   p->off_partE = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * k->em_nv);
+  p->off_maskR = off; off = align_up(off + sizeof(double) * 2 * (size_t)P * J * I * I);
   // the adjoint kernels use pass A's partition; J I + 2 I^2 + 2 sums per slot at most
   p->off_partAdj = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2 * I * I + 2));
   p->off_lossf = off; off = align_up(off + sizeof(double) * (size_t)P);
@@ -1240,6 +1243,36 @@ ffca_status ffca_set_p_update(ffca_ctx* c, int method, double mu) {
     c->graph = nullptr;
   }
   return FFCA_OK;
+}
+
+ffca_status ffca_mask_init(ffca_ctx* c, const void* masks, int sweeps, double delta) {
+  if (!c || sweeps < 0 || sweeps > 1000 || !(delta > 0.0 && delta <= 1.0)) return FFCA_ERR_ARG;
+  if (c->d.F == 0) return FFCA_OK;
+  if (!masks || (reinterpret_cast<uintptr_t>(masks) % 16) != 0) return FFCA_ERR_ARG;
+  if (c->d.J > kMaskMaxJ) return FFCA_ERR_UNSUPPORTED;
+  MaskArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.part = c->plan.pA;  // problems: frames, rows, offsets
+  a.I = c->d.I;
+  a.J = c->d.J;
+  a.ld = c->d.ld;
+  a.y = c->d.y;
+  a.m = masks;
+  a.v = c->d.v;
+  a.lam = c->d.lambda;
+  a.P = c->d.P;
+  a.R = reinterpret_cast<double*>(c->ws + c->plan.off_maskR);
+  a.sweeps = sweeps;
+  a.delta = delta;
+  a.status = c->status;
+  {
+    struct Range {
+      Range() { nvtxRangePushA("ffca mask init"); }
+      ~Range() { nvtxRangePop(); }
+    } range;
+    if (!cuda_ok(launch_mask_init(c->d.prec, a, c->d.F, c->stream), "launch_mask_init")) return FFCA_ERR_CUDA;
+  }
+  return read_status(c);
 }
 
 static_assert(FFCA_FAULT_NONE == kFaultNone && FFCA_FAULT_PASS_A_NO_COPIES == kFaultPassANoCopies,

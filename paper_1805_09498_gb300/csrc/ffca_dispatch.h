@@ -1,6 +1,8 @@
 // Host-side table of the compiled kernel instantiations.
 #pragma once
 
+#include <cuda_runtime.h>
+
 namespace ffca {
 
 // Every FastFCA-AS kernel takes one FastArgs by value.
@@ -33,6 +35,11 @@ struct FastKernels {
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.
 const FastKernels* fast_kernels(int prec, int I, int J);
+
+// The three launches of the mask-based initialisation (ffca_mask.cuh) on
+// stream s for `problems` problems; prec as above.
+struct MaskArgs;
+cudaError_t launch_mask_init(int prec, const MaskArgs& a, int problems, cudaStream_t s);
 
 // Conventional FCA EM baseline: every kernel takes one FcaArgs by value.
 struct FcaKernels {

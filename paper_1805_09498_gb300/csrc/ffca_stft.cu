@@ -2,17 +2,19 @@
 // the paper's experiments (Table 1: frame length L = 1024, shift H = 512,
 // square root of the Hann window; bins up to the Nyquist frequency, F = 513,
 // Sec. 2).  The frame's 1024 real samples are transformed as one 512-point
-// complex FFT of z(t) = x(2t) + i x(2t+1) (radix-8 Stockham, three stages in
-// shared memory, 64 threads per transform), then split into the spectrum of
+// complex FFT of z(t) = x(2t) + i x(2t+1), then split into the spectrum of
 // the real frame:
 //     X[k] = E[k] + e^{-2 pi i k/1024} O[k],  E[k] = (Z[k] + conj Z[512-k]) / 2,
 //     O[k] = (Z[k] - conj Z[512-k]) / (2i),   k = 0 .. 512 (Z[512] = Z[0]).
 // The inverse runs the same steps backwards.  FP32 data, twiddles and window
 // rounded from FP64 values computed on the host.
 //
-// A CTA takes kFrames consecutive frames of one channel: the overlapping
-// samples are read once, and the spectra leave as runs of kFrames
-// consecutive frames of one bin (the frame-contiguous mic-planar layout).
+// One warp transforms one frame, in registers and across its lanes by
+// shuffles (fft512_warp: 512 = 16 x 32, a 16-point DFT per lane and a
+// 32-point DFT over the lanes), so no barrier separates the stages; a CTA
+// takes kFrames consecutive frames of one channel and moves the spectra
+// through shared memory as runs of kFrames frames per bin (the
+// frame-contiguous mic-planar layout), 128 bytes per bin row.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,9 +29,8 @@ constexpr int kL = 1024;        // frame length
 constexpr int kH = 512;         // frame shift
 constexpr int kM = 512;         // complex FFT size (two real samples per point)
 constexpr int kF = kL / 2 + 1;  // bins up to Nyquist
-constexpr int kFrames = 8;      // frames per CTA
-constexpr int kThreads = 256;   // four 64-thread transform groups
-constexpr int kGroups = kThreads / 64;
+constexpr int kFrames = 16;     // frames per CTA: one per warp
+constexpr int kThreads = 32 * kFrames;
 constexpr int kMaxDev = 64;
 
 __device__ float2 g_tw512[kM];   // e^{-2 pi i m / 512}
@@ -78,76 +79,86 @@ __device__ inline void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
   a3 = csub(t1, t3);
 }
 
-// 8-point DFT in registers: two 4-point DFTs of the even and odd entries,
-// joined with the twiddles e^{-2 pi i q / 8}.
-__device__ inline void dft8(float2 (&u)[8]) {
-  float2 e0 = u[0], e1 = u[2], e2 = u[4], e3 = u[6];
-  float2 o0 = u[1], o1 = u[3], o2 = u[5], o3 = u[7];
-  dft4(e0, e1, e2, e3);
-  dft4(o0, o1, o2, o3);
-  const float r = 0.70710678118654752f;
-  o1 = make_float2(r * (o1.x + o1.y), r * (o1.y - o1.x));    // * (1 - i) / sqrt 2
-  o2 = mul_mi(o2);                                           // * (-i)
-  o3 = make_float2(r * (o3.y - o3.x), -r * (o3.x + o3.y));   // * (-1 - i) / sqrt 2
-  u[0] = cadd(e0, o0);
-  u[4] = csub(e0, o0);
-  u[1] = cadd(e1, o1);
-  u[5] = csub(e1, o1);
-  u[2] = cadd(e2, o2);
-  u[6] = csub(e2, o2);
-  u[3] = cadd(e3, o3);
-  u[7] = csub(e3, o3);
-}
-
-// Forward 512-point DFT of a[0..511] by one 64-thread group (thread j):
-// three radix-8 Stockham stages a -> b -> a -> b (result in b).  At stage p
-// (sub-transform size p = 1, 8, 64) thread j takes u_r = src[j + 64 r],
-// twiddles u_r by e^{-2 pi i r k / (8 p)} (k = j mod p), transforms, and
-// writes dst[(j - k) 8 + k + p r].  group_sync() separates the stages.
-template <typename Sync>
-__device__ void fft512(float2* a, float2* b, const float2* tw, int j, Sync group_sync) {
-  float2* src = a;
-  float2* dst = b;
+// 16-point DFT of u[0..15] in registers (forward): with n = 4 n1 + n2 and
+// k = k1 + 4 k2, X[k] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 W4^(n1 k1) u[4 n1 + n2]:
+// four 4-point DFTs over n1, the twiddles W16^(n2 k1) (from the 512-point
+// table: W16^m = W512^(32 m)), four 4-point DFTs over n2.  Output in
+// natural order.
+__device__ inline void dft16(float2 (&u)[16], const float2* __restrict__ tw) {
+  float2 y[4][4];  // [n2][k1]
 #pragma unroll
-  for (int s = 0; s < 3; ++s) {
-    const int p = s == 0 ? 1 : (s == 1 ? 8 : 64);
-    const int k = j & (p - 1);
-    float2 u[8];
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 a0 = u[n2], a1 = u[4 + n2], a2 = u[8 + n2], a3 = u[12 + n2];
+    dft4(a0, a1, a2, a3);
+    y[n2][0] = a0;
+    y[n2][1] = a1;
+    y[n2][2] = a2;
+    y[n2][3] = a3;
+  }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) u[r] = src[j + 64 * r];
-    if (s > 0) {
+  for (int n2 = 1; n2 < 4; ++n2)
 #pragma unroll
-      for (int r = 1; r < 8; ++r) u[r] = cmul(u[r], tw[(r * k * (64 / p)) & (kM - 1)]);
-    }
-    dft8(u);
-    const int base = (j - k) * 8 + k;
+    for (int k1 = 1; k1 < 4; ++k1) y[n2][k1] = cmul(y[n2][k1], __ldg(tw + 32 * n2 * k1));
 #pragma unroll
-    for (int r = 0; r < 8; ++r) dst[base + p * r] = u[r];
-    group_sync();
-    float2* t = src;
-    src = dst;
-    dst = t;
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1], a3 = y[3][k1];
+    dft4(a0, a1, a2, a3);
+    u[k1] = a0;
+    u[k1 + 4] = a1;
+    u[k1 + 8] = a2;
+    u[k1 + 12] = a3;
   }
 }
 
-// Shared memory of one CTA (floats/float2 arrays carved from one buffer).
-struct StftSmem {
-  float2 tw512[kM];
-  float2 tw1024[kF + 3];
-  float win[kL];
-  float2 fft[kGroups][2][kM];
-  float2 spec[kF][kFrames];   // the CTA's spectra, bin-major
-  float samp[(kFrames + 1) * kH];
-};
-
-template <typename Smem>
-__device__ inline void load_tables(Smem& sm) {
-  for (int t = threadIdx.x; t < kM; t += kThreads) sm.tw512[t] = g_tw512[t];
-  for (int t = threadIdx.x; t < kF; t += kThreads) sm.tw1024[t] = g_tw1024[t];
-  for (int t = threadIdx.x; t < kL; t += kThreads) sm.win[t] = g_win[t];
+// 512-point forward DFT by one warp.  Lane l enters with u[q] = z[l + 32 q]
+// (q = 0..15).  Writing k = r + 16 k2 (r = 0..15, k2 = 0..31):
+//   Z[r + 16 k2] = sum_l W32^(l k2) W512^(l r) sum_q W16^(q r) z[l + 32 q],
+// so every lane transforms its sixteen values (dft16), multiplies entry r by
+// W512^(l r), and the warp runs the 32-point DFT over l for every r as five
+// radix-2 decimation-in-frequency stages across the lanes (partner lane
+// l ^ h; the upper lane takes (partner - own) W_2h^(l mod h)).  On return
+// lane l holds u[r] = Z[r + 16 rev5(l)], rev5 the 5-bit reversal.
+__device__ inline void fft512_warp(float2 (&u)[16], int lane, const float2* __restrict__ tw) {
+  dft16(u, tw);
+#pragma unroll
+  for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], __ldg(tw + ((lane * r) & (kM - 1))));
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = (lane & h) != 0;
+    const float2 w = __ldg(tw + (lane & (h - 1)) * (256 / h));  // W_2h^(l mod h) = W512^((l mod h) 256 / h)
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, u[r].x, h), __shfl_xor_sync(0xffffffffu, u[r].y, h));
+      u[r] = upper ? cmul(csub(o, u[r]), w) : cadd(u[r], o);
+    }
+  }
 }
 
-// x [C][S] float -> out [C][F][ld] complex64 (frames 0 .. N-1, then zero to ld).
+__device__ inline int rev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
+
+// Padded index of Z[k] in a warp's buffer: k mod 16 + 17 (k / 16), so that
+// the lanes' writes of u[r] and their reads of consecutive k hit distinct
+// banks (up to two-way).
+__device__ inline int zpad(int k) { return (k & 15) + 17 * (k >> 4); }
+constexpr int kZPad = 17 * (kM / 16);
+
+// Padded index of sample s of a half frame (one float of padding per 32), so
+// that the lanes' scalar stores of samples 2t, 2t+1 at t = r + 16 rev5(l)
+// fall in distinct banks.
+__device__ inline int spad(int s) { return s + (s >> 5); }
+constexpr int kHalfPad = kH + kH / 32;
+
+// Shared memory of one CTA.
+struct StftSmem {
+  float2 z[kFrames][kZPad];        // each warp's Z (forward: the real split reads Z[k], Z[512 - k])
+  float2 spec[kF][kFrames];        // the CTA's spectra, bin-major (forward: out; inverse: in)
+};
+// The inverse keeps the windowed halves of its frames where the forward
+// transform keeps Z.
+static_assert(sizeof(StftSmem::z) >= 2 * kFrames * kHalfPad * sizeof(float), "halves fit in z");
+
+// x [C][S] float -> out [C][F][ld] complex64 (frames 0 .. N-1, then zero to
+// ld).  Warp w of the CTA transforms frame n0 + w of channel blockIdx.y.
 __global__ void __launch_bounds__(kThreads) k_stft(const float* __restrict__ x, long long S, int N,
                                                    float2* __restrict__ out, int ld) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,35 +166,31 @@ __global__ void __launch_bounds__(kThreads) k_stft(const float* __restrict__ x, 
   const int c = blockIdx.y;
   const int n0 = blockIdx.x * kFrames;
   const int nf = min(kFrames, N - n0);
-  const float* xc = x + (size_t)c * S;
-  load_tables(sm);
-  // samples n0 H .. (n0 + nf - 1) H + L - 1, all inside the signal
-  const int ns = (nf + 1) * kH;
-  for (int t = threadIdx.x; t < ns; t += kThreads) sm.samp[t] = __ldg(xc + (size_t)n0 * kH + t);
-  __syncthreads();
-  const int grp = threadIdx.x / 64, j = threadIdx.x % 64;
-  auto sync = [] { __syncthreads(); };
-  for (int fb = 0; fb < kFrames; fb += kGroups) {  // every thread runs every round (barriers)
-    const int fr = fb + grp;
-    const bool on = fr < nf;
-    float2* A = sm.fft[grp][0];
-    float2* B = sm.fft[grp][1];
-    for (int t = j; t < kM; t += 64) {
-      const int s0 = fr * kH + 2 * t;
-      A[t] = on ? make_float2(sm.win[2 * t] * sm.samp[s0], sm.win[2 * t + 1] * sm.samp[s0 + 1])
-                : make_float2(0.f, 0.f);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < nf) {
+    const float* xf = x + (size_t)c * S + (size_t)(n0 + w) * kH;  // samples n H .. n H + L - 1 (inside the signal)
+    float2 u[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {  // z(t) = w(2t) x(2t) + i w(2t+1) x(2t+1), t = l + 32 q
+      const int t = lane + 32 * q;
+      u[q] = make_float2(__ldg(g_win + 2 * t) * __ldg(xf + 2 * t), __ldg(g_win + 2 * t + 1) * __ldg(xf + 2 * t + 1));
     }
-    __syncthreads();
-    fft512(A, B, sm.tw512, j, sync);  // Z in B
-    for (int k = j; k < kF; k += 64) {
-      const float2 zk = B[k & (kM - 1)];
-      const float2 zm = cconj(B[(kM - k) & (kM - 1)]);
+    fft512_warp(u, lane, g_tw512);
+    float2* zb = sm.z[w];
+    const int base = 16 * rev5(lane);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) zb[zpad(base + r)] = u[r];
+    __syncwarp();
+    // X[k] = E[k] + W1024^k O[k], E = (Z[k] + conj Z[512-k]) / 2, O = (Z[k] - conj Z[512-k]) / (2i)
+    for (int k = lane; k < kF; k += 32) {
+      const float2 zk = zb[zpad(k & (kM - 1))];
+      const float2 zm = cconj(zb[zpad((kM - k) & (kM - 1))]);
       const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
       const float2 o = mul_mi(make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y - zm.y)));
-      if (on) sm.spec[k][fr] = cadd(e, cmul(sm.tw1024[k], o));
+      sm.spec[k][w] = cadd(e, cmul(__ldg(g_tw1024 + k), o));
     }
-    __syncthreads();
   }
+  __syncthreads();
   // runs of consecutive frames per bin
   float2* oc = out + (size_t)c * kF * ld;
   for (int t = threadIdx.x; t < kF * kFrames; t += kThreads) {
@@ -200,75 +207,67 @@ __global__ void __launch_bounds__(kThreads) k_stft(const float* __restrict__ x, 
   }
 }
 
-// in [C][F][ld] complex64 (frames 0 .. N-1) -> out [C][(N + 1) H] float: the
-// CTA writes samples k H .. k H + H - 1 for k = k0 .. k0 + kFrames - 1 (k <=
-// N), each the second half of frame k - 1 plus the first half of frame k
-// (windowed inverse DFTs; a missing frame adds nothing).
+// in [C][F][ld] complex64 (frames 0 .. N-1) -> out [C][(N + 1) H] float.  A
+// CTA writes the kFrames - 1 output blocks k = k0 .. k0 + kFrames - 2 of H
+// samples (k <= N), block k being the second half of frame k - 1 plus the
+// first half of frame k: warp w inverts frame m0 + w (m0 = k0 - 1; a missing
+// frame adds nothing).  The spectra arrive as runs of kFrames consecutive
+// frames per bin (coalesced), staged in spec; the windowed halves go to z.
 __global__ void __launch_bounds__(kThreads) k_istft(const float2* __restrict__ in, int N, int ld,
                                                     float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StftSmem& sm = *reinterpret_cast<StftSmem*>(smem_raw);
-  // the windowed halves of frames m0 .. m0 + kFrames: first halves in samp[],
-  // second halves in spec[] (unused by the inverse otherwise).  Staging the
-  // spectra in shared memory for coalesced loads needs another 37 KB, which
-  // halves the resident CTAs and measured slower (0.91 against 0.58 ms for
-  // nine channels of 20000 frames).
-  static_assert(sizeof(StftSmem::spec) / sizeof(float) >= (kFrames + 1) * kH, "second halves fit");
-  static_assert(sizeof(StftSmem::samp) / sizeof(float) >= (kFrames + 1) * kH, "first halves fit");
   const int c = blockIdx.y;
-  const int k0 = blockIdx.x * kFrames;
-  const int m0 = k0 - 1;  // frames m0 .. m0 + kFrames
+  const int k0 = blockIdx.x * (kFrames - 1);
+  const int m0 = k0 - 1;  // frames m0 .. m0 + kFrames - 1
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float2* ic = in + (size_t)c * kF * ld;
-  float* first = sm.samp;                              // [kFrames + 1][H]
-  float* second = reinterpret_cast<float*>(sm.spec);   // [kFrames + 1][H]
-  load_tables(sm);
-  __syncthreads();
-  const int grp = threadIdx.x / 64, j = threadIdx.x % 64;
-  auto sync = [] { __syncthreads(); };
-  for (int fb = 0; fb < kFrames + 1; fb += kGroups) {
-    const int fr = fb + grp;  // local frame index 0 .. kFrames
-    const int m = m0 + fr;
-    const bool on = fr <= kFrames && m >= 0 && m < N;
-    float2* A = sm.fft[grp][0];
-    float2* B = sm.fft[grp][1];
-    // Z[k] = E[k] + i O[k] from X[k] and X[512 - k], conjugated for the
-    // forward transform (IDFT(Z) = conj(DFT(conj Z)) / 512)
-    for (int k = j; k < kM; k += 64) {
-      float2 z = make_float2(0.f, 0.f);
-      if (on) {
-        float2 xk = __ldg(ic + (size_t)k * ld + m);
-        float2 xm = cconj(__ldg(ic + (size_t)(kM - k) * ld + m));
-        if (k == 0) {  // bins 0 and L/2 of a real signal's spectrum are real: their imaginary parts are ignored
-          xk.y = 0.f;
-          xm.y = 0.f;
-        }
-        const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
-        const float2 o = cmul(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y - xm.y)), cconj(sm.tw1024[k]));
-        z = cconj(make_float2(e.x - o.y, e.y + o.x));  // conj(E + i O)
-      }
-      A[k] = z;
-    }
-    __syncthreads();
-    fft512(A, B, sm.tw512, j, sync);  // DFT(conj Z) in B
-    if (fr <= kFrames) {
-      const float sc = 1.0f / kM;
-      for (int t = j; t < kM; t += 64) {
-        const float2 zt = B[t];  // z(t) = conj(zt) / 512: x(2t) = Re, x(2t+1) = Im
-        const float x0 = zt.x * sc, x1 = -zt.y * sc;
-        const int s = 2 * t;
-        float* dst = s < kH ? first + fr * kH + s : second + fr * kH + (s - kH);
-        dst[0] = on ? sm.win[s] * x0 : 0.f;
-        dst[1] = on ? sm.win[s + 1] * x1 : 0.f;
-      }
-    }
-    __syncthreads();
+  for (int t = threadIdx.x; t < kF * kFrames; t += kThreads) {
+    const int f = t / kFrames, fr = t % kFrames, m = m0 + fr;
+    sm.spec[f][fr] = (m >= 0 && m < N) ? __ldg(ic + (size_t)f * ld + m) : make_float2(0.f, 0.f);
   }
+  __syncthreads();
+  const int m = m0 + w;
+  const bool on = m >= 0 && m < N;
+  float2 u[16];
+  // Z[k] = E[k] + i O[k] from X[k] and X[512 - k] (bins 0 and L/2 of a real
+  // signal's spectrum are real: their imaginary parts are ignored), conjugated
+  // for the forward transform: IDFT(Z) = conj(DFT(conj Z)) / 512
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int k = lane + 32 * q;
+    float2 xk = sm.spec[k][w];
+    float2 xm = cconj(sm.spec[kM - k][w]);
+    if (k == 0) {
+      xk.y = 0.f;
+      xm.y = 0.f;
+    }
+    const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
+    const float2 o = cmul(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y - xm.y)), cconj(__ldg(g_tw1024 + k)));
+    u[q] = cconj(make_float2(e.x - o.y, e.y + o.x));
+  }
+  fft512_warp(u, lane, g_tw512);  // lane l: DFT(conj Z) at t = r + 16 rev5(l)
+  float* first = reinterpret_cast<float*>(sm.z);  // [kFrames][kHalfPad]
+  float* second = first + kFrames * kHalfPad;     // [kFrames][kHalfPad]
+  const int base = 16 * rev5(lane);
+  const float sc = 1.0f / kM;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {  // x(2t) = Re / 512, x(2t+1) = -Im / 512, windowed
+    const int s = 2 * (base + r);
+    const float x0 = on ? __ldg(g_win + s) * u[r].x * sc : 0.f;
+    const float x1 = on ? -__ldg(g_win + s + 1) * u[r].y * sc : 0.f;
+    float* half = s < kH ? first + w * kHalfPad : second + w * kHalfPad;
+    const int sh = s < kH ? s : s - kH;
+    half[spad(sh)] = x0;
+    half[spad(sh + 1)] = x1;
+  }
+  __syncthreads();
   // samples k H + u: second half of frame k - 1 (local k - k0) + first half of frame k (local k - k0 + 1)
   float* oc = out + (size_t)c * ((size_t)N + 1) * kH;
-  const int nk = min(kFrames, N + 1 - k0);
+  const int nk = min(kFrames - 1, N + 1 - k0);
   for (int t = threadIdx.x; t < nk * kH; t += kThreads) {
-    const int kk = t / kH, u = t % kH;
-    oc[(size_t)(k0 + kk) * kH + u] = second[kk * kH + u] + first[(kk + 1) * kH + u];
+    const int kk = t / kH, uu = t % kH;
+    oc[(size_t)(k0 + kk) * kH + uu] = second[kk * kHalfPad + spad(uu)] + first[(kk + 1) * kHalfPad + spad(uu)];
   }
 }
 
@@ -308,7 +307,7 @@ ffca_status ffca_istft(const void* in, int C, int N, int ld, float* out, void* s
   const size_t smem = sizeof(StftSmem);
   if (cudaFuncSetAttribute(k_istft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return FFCA_ERR_CUDA;
-  const dim3 grid((N + 1 + kFrames - 1) / kFrames, C);
+  const dim3 grid((N + 1 + kFrames - 2) / (kFrames - 1), C);
   k_istft<<<grid, kThreads, smem, as_stream(stream)>>>(static_cast<const float2*>(in), N, ld, out);
   return cudaGetLastError() == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
 }

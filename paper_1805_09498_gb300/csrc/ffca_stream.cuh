@@ -133,11 +133,12 @@ struct EmGroups {
   static constexpr int value = (sizeof(T) == 4 && I <= 3 && J <= 3) ? FFCA_EM_GROUPS : 1;
 };
 
-// Pipelines per CTA of pass B: as pass A, except at I = 8 in FP32, where the
-// sixteen-thread entry split (wcov_consume_big) fits two groups of 128
-// registers.
+// Pipelines per CTA of pass B: as pass A (at I = 8 one group: the
+// per-thread sums of wcov_consume_big take 222 registers; a sixteen-thread
+// entry split that fits two groups of 128 registers ran slower, 157.8 against
+// 137 us at I = 8, J = 6, F = 513, N = 4000).
 #ifndef FFCA_BIG_B_GROUPS
-#define FFCA_BIG_B_GROUPS 2
+#define FFCA_BIG_B_GROUPS 1
 #endif
 template <typename T, int I, int J>
 struct WcovGroups {
@@ -917,26 +918,25 @@ __global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : 
   }
 }
 
-// Pass B consumers for I = 8: the I^3 = 512 sums per point do not fit one
-// thread's registers, so sixteen threads share a unit and split the 64
-// entry reals of y y^H (in the packed order of V_i: the real diagonal, then
-// (re, im) of the 28 entries above it in row order), thread e taking entry
-// reals 4e .. 4e+3 against all eight weights 1/sigma_i: threads 0 and 1 the
-// diagonal |y_r|^2 of four rows each, threads 2 .. 15 re and im of
-// y_r conj(y_c) of two pairs each.  Both kinds are formed as two "slots" of
-// two reals each, branch-free (selects pick the operands).  Thread e forms
-// 1/sigma_(e mod 8) for the unit's frames and the threads exchange the eight
-// weights by shuffles.  At a segment's end (FP32: also every kFlushUnits
-// units per thread) the two units of a warp are summed by one shuffle, then
-// the warps through shared memory in double-float; thread e's value k of
-// weight i is packed entry 4e + k of V_i.
+// Pass B consumers for I > 4: the I^3 sums per point do not fit one thread's
+// registers, so each unit is shared by I = 8 threads that split the entries
+// of y y^H, not the weights: thread e of a unit accumulates the diagonal
+// entry |y_e|^2 and the off-diagonal entries y_r conj(y_c) of the pairs
+// p = 4e .. 4e+3 (row order over r < c; thread 7 only its diagonal), each
+// against all I weights 1/sigma_i.  Thread e forms sigma_e and 1/sigma_e for
+// the unit's frames and the I threads exchange them by shuffles, so every
+// weight is computed once.  An off-diagonal entry is accumulated as one
+// (re, im) pair per weight with the packed f32x2 FMA.  At a segment's end
+// the lanes with the same e (equal mod 8) are summed by shuffles, then the
+// warps through shared memory, in double-float; the values go out in the
+// packed Hermitian order of V_i (diagonal, then (re, im) above it).
 template <int I>
-struct BigSplit {
+struct BigEntries {
+  static constexpr int PAIRS = I * (I - 1) / 2;         // off-diagonal entries
+  static constexpr int SLOTS = (PAIRS + I - 1) / I;     // per thread (4 at I = 8)
+  static constexpr int NVT = I + 2 * I * SLOTS;         // values per thread: diagonal + slots
   static_assert(I == 8, "the entry split is laid out for I = 8");
-  static constexpr int EPT = 16;            // threads per unit
-  static constexpr int NE = I * I;          // entry reals of y y^H
-  static constexpr int PER = NE / EPT;      // entry reals per thread (two slots of two)
-  // (r, c) of pair p (row order over r < c)
+  // packed-order index of pair p (row order over r < c) and its (r, c)
   __device__ static void decode(int p, int& r, int& c) {
     r = 0;
     int q = p;
@@ -946,17 +946,15 @@ struct BigSplit {
     }
     c = r + 1 + q;
   }
-  // slot s of thread e: rows (ra, rb); a pair (re, im of y_ra conj(y_rb)) or
-  // two diagonal entries (|y_ra|^2, |y_rb|^2)
-  __device__ static void slot(int e, int s, int& ra, int& rb, bool& pair) {
-    if (e < 2) {
-      ra = 4 * e + 2 * s;
-      rb = ra + 1;
-      pair = false;
-    } else {
-      decode(2 * (e - 2) + s, ra, rb);
-      pair = true;
-    }
+  // reduction index of thread e's value v (threads below I - 1 keep all NVT
+  // values, thread I - 1 only its I diagonal sums): I^3 indices in all
+  __device__ static int red_index(int e, int v) { return e * NVT + v; }
+  // output index (weight i, packed entry m) of reduction index x
+  __device__ static int out_index(int x) {
+    const int e = x / NVT, v = x % NVT;
+    if (v < I) return v * I * I + e;  // diagonal |y_e|^2 against weight v
+    const int k = (v - I) / (2 * I), i = ((v - I) % (2 * I)) / 2, comp = (v - I) % 2;
+    return i * I * I + I + 2 * (SLOTS * e + k) + comp;
   }
 };
 
@@ -969,23 +967,30 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
   using L = typename LN::L;
   using TC = Tile<T, I, J, G>;
   using PB = ParamsB<T, I, J>;
-  using BS = BigSplit<I>;
+  using BE = BigEntries<I>;
+  using T2 = std::conditional_t<sizeof(T) == 4, float2, double2>;
   constexpr int FU = Vec<T>::FU;
-  constexpr int EPT = BS::EPT;
-  constexpr int IG = kConsumers / EPT;  // units in flight per group
-  static_assert(kConsumers % EPT == 0 && 32 % EPT == 0, "the unit's threads must divide the consumers and the warp");
-  static_assert(TC::T % IG == 0, "tiles hold whole rounds of units");
+  constexpr int SL = BE::SLOTS;
+  constexpr int IG = kConsumers / I;  // units in flight per group
+  static_assert(kConsumers % I == 0 && 32 % I == 0, "I must divide the consumer count and the warp");
   const Partition& pt = a.part;
   const int tid = rl.ctid, lane = threadIdx.x & 31;
-  const int e = tid % EPT, ul = tid / EPT;
-  const int gl = lane & ~(EPT - 1);  // first lane of this unit's threads
-  const int ew = e % I;              // the weight this thread forms
-  int ra[2], rb[2];
-  bool pr[2];
+  const int e = tid % I, ul = tid / I;
+  const int gl = lane & ~(I - 1);  // first lane of this unit's I threads
+  int sr[SL], sc[SL];
 #pragma unroll
-  for (int sl = 0; sl < 2; ++sl) BS::slot(e, sl, ra[sl], rb[sl], pr[sl]);
+  for (int k = 0; k < SL; ++k) {
+    const int p = SL * e + k;
+    if (p < BE::PAIRS) BE::decode(p, sr[k], sc[k]);
+    else { sr[k] = 0; sc[k] = 1; }  // thread I - 1: unused slots
+  }
   L lame[J];
-  L acc[2][2][I];  // [slot][real][weight], per frame lane
+  L accd[I];        // diagonal |y_e|^2 / sigma_i, per frame lane
+  T2 acco[SL][I];   // off-diagonal (re, im) / sigma_i
+  auto fma2 = [](T w, T xr, T xi, T2 acc) -> T2 {
+    if constexpr (sizeof(T) == 4) return __ffma2_rn(make_float2(w, w), make_float2(xr, xi), acc);
+    else return make_double2(fma(w, xr, acc.x), fma(w, xi, acc.y));
+  };
   TileIter it(u0, u1, pt, TC::T, true);
   bool seg_new = true;
   int ntile = 0;         // tile trips since the segment's start or last flush
@@ -995,11 +1000,11 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
     const int f = it.f;
     if (seg_new) {
 #pragma unroll
-      for (int sl = 0; sl < 2; ++sl)
+      for (int i = 0; i < I; ++i) {
+        accd[i] = LN::bc(0);
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-          for (int i = 0; i < I; ++i) acc[sl][k][i] = LN::bc(0);
+        for (int k = 0; k < SL; ++k) acco[k][i] = T2{0, 0};
+      }
       Np = pt.frames(f);
     }
     if (consumer_acquire(a, pp, t, f, abort)) {
@@ -1007,7 +1012,7 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
       if (seg_new) {
         const PB& sp = *reinterpret_cast<const PB*>(st + TC::ROFF);
 #pragma unroll
-        for (int j = 0; j < J; ++j) lame[j] = LN::bc(sp.lam[j][ew]);
+        for (int j = 0; j < J; ++j) lame[j] = LN::bc(sp.lam[j][e]);
       }
       const VY* ys = reinterpret_cast<const VY*>(st);
       const VV* vs = reinterpret_cast<const VV*>(st + TC::VOFF);
@@ -1034,24 +1039,35 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
         }
         if (!unit_ok) continue;  // after the shuffles: nothing below involves other lanes
         const bool ragged = n0 + FU > Np;
-#pragma unroll
-        for (int sl = 0; sl < 2; ++sl) {
-          L xr, xi, zr, zi;
-          LN::split(ys[ra[sl] * TC::YP + q], xr, xi);
-          LN::split(ys[rb[sl] * TC::YP + q], zr, zi);
-          // pair: (x z^*) = (xr zr + xi zi, xi zr - xr zi); diagonal: (|x|^2, |z|^2)
-          const L ur = pr[sl] ? zr : xr, ui = pr[sl] ? zi : xi;
-          const L sr = pr[sl] ? xi : zr, si = pr[sl] ? xr * LN::bc(-1) : zi;
-          L v0 = vfma(xr, ur, xi * ui);
-          L v1 = vfma(sr, zr, si * zi);
+        // the diagonal entry |y_e|^2 (per frame lane)
+        {
+          L yr, yi;
+          LN::split(ys[e * TC::YP + q], yr, yi);
           if (ragged) {
-            v0 = LN::keep(v0, n0, Np);
-            v1 = LN::keep(v1, n0, Np);
+            yr = LN::keep(yr, n0, Np);
+            yi = LN::keep(yi, n0, Np);
           }
+          const L d2 = vfma(yr, yr, yi * yi);
 #pragma unroll
-          for (int i = 0; i < I; ++i) {
-            acc[sl][0][i] = vfma(wi[i], v0, acc[sl][0][i]);
-            acc[sl][1][i] = vfma(wi[i], v1, acc[sl][1][i]);
+          for (int i = 0; i < I; ++i) accd[i] = vfma(wi[i], d2, accd[i]);
+        }
+#pragma unroll
+        for (int k = 0; k < SL; ++k) {
+          const VY xu = ys[sr[k] * TC::YP + q];
+          const VY yu = ys[sc[k] * TC::YP + q];
+#pragma unroll
+          for (int fr = 0; fr < FU; ++fr) {
+            if (ragged && n0 + fr >= Np) continue;
+            const cpx<T> x = yframe(xu, fr), y = yframe(yu, fr);
+            const T pr = fma(x.re, y.re, x.im * y.im);   // re(y_r conj(y_c))
+            const T pi = fma(x.im, y.re, -(x.re * y.im)); // im(y_r conj(y_c))
+#pragma unroll
+            for (int i = 0; i < I; ++i) {
+              T wf;
+              if constexpr (sizeof(T) == 4) wf = fr == 0 ? wi[i].v.x : wi[i].v.y;
+              else wf = wi[i].v;
+              acco[k][i] = fma2(wf, pr, pi, acco[k][i]);
+            }
           }
         }
       }
@@ -1059,27 +1075,45 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
     seg_new = false;
     consumer_release(pp, t);
 
-    // FP32: the plain sums are flushed into the slot every kFlushUnits units
-    // per thread (every lane of the group takes the same tile trips)
-    const bool flush = sizeof(T) == 4 && !it.seg_end && ++ntile == flush_tiles(TC::T / IG);
+    // FP32: the plain sums are flushed into the slot every 2 kFlushUnits
+    // units per thread (a flush reduces all I^3 sums of the group: twice the
+    // interval of the other passes halves its cost); every lane of the group
+    // takes the same tile trips
+    const bool flush = sizeof(T) == 4 && !it.seg_end && ++ntile == 2 * flush_tiles(TC::T / IG);
     if (it.seg_end || flush) {
       const int slot = rl.vb - pt.first_block(f);
       double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * (I * I * I);
-      constexpr int NT = 2 * 2 * I;  // values per thread: [slot][real][weight]
-      T h[NT];
+      T h[BE::NVT], l[BE::NVT];
 #pragma unroll
-      for (int sl = 0; sl < 2; ++sl)
+      for (int i = 0; i < I; ++i) {
+        if constexpr (sizeof(T) == 4) {
+          h[i] = accd[i].v.x + accd[i].v.y;  // the two frame lanes
+          l[i] = 0.f;
+        } else {
+          h[i] = accd[i].v;
+          l[i] = 0;
+        }
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < SL; ++k) {
+          h[I + k * 2 * I + 2 * i] = acco[k][i].x;
+          h[I + k * 2 * I + 2 * i + 1] = acco[k][i].y;
+          l[I + k * 2 * I + 2 * i] = 0;
+          l[I + k * 2 * I + 2 * i + 1] = 0;
+        }
+      }
+      // the lanes with the same e (offsets I, 2 I, ... within the warp), in
+      // plain arithmetic; the warps' sums then compensated, as GroupReduce
 #pragma unroll
-          for (int i = 0; i < I; ++i) h[(2 * sl + k) * I + i] = LN::hsum(acc[sl][k][i]);  // the frame lanes
-      // the two units of the warp (same e at lane ^ 16), in plain arithmetic;
-      // the warps' sums then compensated, as GroupReduce
+      for (int v = 0; v < BE::NVT; ++v) h[v] += l[v];
 #pragma unroll
-      for (int v = 0; v < NT; ++v) h[v] += __shfl_xor_sync(0xffffffffu, h[v], EPT);
-      if (lane < EPT) {
+      for (int off = I; off < 32; off <<= 1)
 #pragma unroll
-        for (int v = 0; v < NT; ++v) Red::one(red)[rl.cwarp][e * NT + v] = h[v];
+        for (int v = 0; v < BE::NVT; ++v) h[v] += __shfl_xor_sync(0xffffffffu, h[v], off);
+      if (lane < I) {
+        const int nv = lane < I - 1 ? BE::NVT : I;
+#pragma unroll
+        for (int v = 0; v < BE::NVT; ++v)
+          if (v < nv) Red::one(red)[rl.cwarp][BE::red_index(lane, v)] = h[v];
       }
       consumer_sync(rl.group);
       for (int x = tid; x < I * I * I; x += kConsumers) {
@@ -1090,21 +1124,19 @@ __device__ void wcov_consume_big(const FastArgs& a, const Pipe<S>& pp, long long
           if constexpr (sizeof(T) == 4) df_add(sh, sl, Red::one(red)[w2][x], (T)0);
           else sh += Red::one(red)[w2][x];
         }
-        // x = e NT + k I + i: entry real 4 e + k of V_i
-        const int ee = x / NT, k = (x % NT) / I, i = x % I;
         const double xv = (double)sh + (double)sl;
-        double& o = out[i * (I * I) + BS::PER * ee + k];
+        double& o = out[BE::out_index(x)];
         o = flushed ? o + xv : xv;
       }
       consumer_sync(rl.group);
       ntile = 0;
       if (flush) {
 #pragma unroll
-        for (int sl = 0; sl < 2; ++sl)
+        for (int i = 0; i < I; ++i) {
+          accd[i] = LN::bc(0);
 #pragma unroll
-          for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int i = 0; i < I; ++i) acc[sl][k][i] = LN::bc(0);
+          for (int k = 0; k < SL; ++k) acco[k][i] = T2{0, 0};
+        }
         flushed = true;
       } else {
         flushed = false;

@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
         "ffca_istft": (ci, [vp, ci, ci, ci, vp, vp]),
         "ffca_status_str": (ctypes.c_char_p, [ci]),
         "ffca_peak_fp64": (ci, [vp, dp]),
+        "ffca_mask_init": (ci, [vp, vp, ci, ctypes.c_double]),
         "ffca_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
@@ -279,6 +280,11 @@ def ffca_destroy(ctx) -> None:
 
 def ffca_status_str(status: int) -> str:
     return lib().ffca_status_str(status).decode()
+
+
+def ffca_mask_init(ctx, masks_ptr: int, sweeps: int = 10, delta: float = 1e-3) -> None:
+    _check(ctx, lib().ffca_mask_init(ctx, ctypes.c_void_p(masks_ptr), int(sweeps), float(delta)),
+           "ffca_mask_init")
 
 
 def ffca_peak_fp64(stream=None) -> float:
@@ -499,6 +505,13 @@ class FastFCA:
     def loglik(self) -> float:
         return ffca_loglik(self.ctx)
 
+    def mask_init(self, masks, sweeps: int = 10, delta: float = 1e-3):
+        """Initialise v, lam and P in place from time-frequency masks (a device
+        tensor of v's shape and dtype), ffca_mask_init."""
+        if masks.shape != self.v.shape or masks.dtype != self.v.dtype or not masks.is_contiguous():
+            raise ValueError("masks must be a contiguous tensor of v's shape and dtype")
+        ffca_mask_init(self.ctx, masks.data_ptr(), sweeps, delta)
+
     def wiener(self, out=None):
         import torch
         if out is None:
@@ -696,6 +709,13 @@ class FastFCABatch:
     def loglik(self) -> np.ndarray:
         """L2 of every mixture (host array of M values)."""
         return ffca_batch_loglik(self.ctx, self.M)
+
+    def mask_init(self, masks, sweeps: int = 10, delta: float = 1e-3):
+        """Initialise every mixture's v, lam and P in place from masks in the
+        batch layout of v (ffca_mask_init)."""
+        if masks.shape != self.v.shape or masks.dtype != self.v.dtype or not masks.is_contiguous():
+            raise ValueError("masks must be a contiguous tensor of v's shape and dtype")
+        ffca_mask_init(self.ctx, masks.data_ptr(), sweeps, delta)
 
     def wiener(self, out=None):
         """Multichannel Wiener filter of every mixture: flat [J I F ld] of y's
