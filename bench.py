@@ -45,9 +45,9 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# The sources the streaming passes are compiled from (and the build flags).
+# The sources the streaming passes are compiled from.
 STREAM_SOURCES = ("paper_1805_09498_gb300/csrc/ffca_common.cuh", "paper_1805_09498_gb300/csrc/ffca_fastfca.cuh",
-                  "paper_1805_09498_gb300/csrc/ffca_stream.cuh", "paper_1805_09498_gb300/build.py")
+                  "paper_1805_09498_gb300/csrc/ffca_stream.cuh")
 
 
 def sources_hash(files=STREAM_SOURCES) -> str:
@@ -1042,12 +1042,25 @@ def run_case(a):
     `iters` hybrid iterations and one Wiener pass of a seeded mixture of the
     given shape (P drawn with alpha = 0.3, cond < 10, or alpha = 0.2,
     cond < 50 for I = 8), or with --case-batch M, a batch of M mixtures with
-    lengths uniform in [200, 4000] through the batch API."""
+    lengths uniform in [200, 4000] through the batch API, or with --case-stft,
+    `iters` rounds of the STFT of I channels of N frames and its inverse."""
     import torch
     from paper_1805_09498_gb300 import build as _build
     from paper_1805_09498_gb300 import ffca
     _build.build()
     alpha, kappa = (0.2, 50.0) if a.case_I == 8 else (0.3, 10.0)
+    if a.case_stft:
+        S = (a.case_N - 1) * ffca.STFT_H + ffca.STFT_L
+        g = torch.Generator(device="cuda")
+        g.manual_seed(31)
+        x = torch.randn((a.case_I, S), generator=g, device="cuda", dtype=torch.float32)
+        for _ in range(a.case_iters):
+            X, n = ffca.stft(x)
+            xr = ffca.istft(X, n)
+        torch.cuda.synchronize()
+        err = float((xr[:, ffca.STFT_L:S - ffca.STFT_L] - x[:, ffca.STFT_L:S - ffca.STFT_L]).abs().max())
+        print("case done; STFT round trip max error:", err)
+        return
     if a.case_batch:
         cdt = torch.complex64 if a.case_prec == "mixed" else torch.complex128
         Ns = batch_lengths(a.case_batch, 200, 4000, seed=17)
@@ -1160,6 +1173,8 @@ def main():
     ap.add_argument("--case-batch", type=int, default=0, help="mixtures of a batch (0: one mixture)")
     ap.add_argument("--case-p-update", default="fixed_point")
     ap.add_argument("--case-mu", type=float, default=0.0)
+    ap.add_argument("--case-stft", action="store_true",
+                    help="the STFT of I channels of N frames and the inverse of I spectra instead")
     args = ap.parse_args()
     if args.case:
         run_case(args)

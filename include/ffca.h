@@ -216,6 +216,21 @@ ffca_status ffca_set_p_update(ffca_ctx* ctx, int method, double mu);
  * all-zero mask row, FFCA_ERR_SINGULAR for a singular R_y or sweep. */
 ffca_status ffca_mask_init(ffca_ctx* ctx, const void* masks, int sweeps, double delta);
 
+/* With enable != 0, later calls of ffca_iterate / ffca_batch_iterate (with
+ * the fixed-point update of P) run the hybrid iterations with each problem
+ * resident on chip: one CTA per problem holds the problem's y and v in shared
+ * memory for up to 32 iterations per launch (pass A, the new Lambda and L2,
+ * pass B, the P step, all inside the CTA), so that a short problem streams
+ * its data from HBM once per launch instead of twice per iteration and an
+ * iteration costs no launch.  Same results as the streaming kernels up to
+ * the order of the floating-point sums; the trace as ffca_iterate.  For
+ * I <= 4 and problems of at most the frames the shared memory holds (about
+ * 5600 frames at I = J = 3 in the mixed precision, half in FP64):
+ * FFCA_ERR_UNSUPPORTED otherwise (the context keeps streaming).  With another
+ * update of P selected the iterations stream as usual.  Drops a captured
+ * graph. */
+ffca_status ffca_set_resident(ffca_ctx* ctx, int enable);
+
 /* Fault injection for tests of failure detection (no GPU fault is made).
  * FFCA_FAULT_PASS_A_NO_COPIES: from the next call on, the producer warps of
  * pass A issue none of their copies, so its consumers' bounded waits run
@@ -284,7 +299,8 @@ ffca_status ffca_wiener_se_grad(ffca_ctx* ctx, const void* s, void* dv, double* 
 #define FFCA_KERNEL_AFINAL 6    /* per-frequency finalise of pass A: Lambda, log-likelihood */
 #define FFCA_KERNEL_ADJ 7       /* adjoint streaming pass (ffca_nll_grad, ffca_wiener_se_grad) */
 #define FFCA_KERNEL_ADJ_FINAL 8 /* adjoint per-frequency finalise */
-#define FFCA_KERNEL_KINDS 9
+#define FFCA_KERNEL_RESIDENT 9  /* iterations with each problem resident on chip (ffca_set_resident) */
+#define FFCA_KERNEL_KINDS 10
 
 /* Profiling: while enabled, each kernel the context launches is bracketed by
  * two CUDA events on the context stream.  ffca_timing_read synchronises,

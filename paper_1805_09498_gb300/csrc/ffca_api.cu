@@ -17,6 +17,7 @@
 #include "ffca_adjoint.cuh"
 #include "ffca_dispatch.h"
 #include "ffca_mask.cuh"
+#include "ffca_resident.cuh"
 #include "ffca_stream.cuh"
 
 using namespace ffca;
@@ -106,6 +107,7 @@ struct Plan {
   size_t off_cntA, off_cntB, off_logdet, off_llf, off_trace, off_pinvH, off_partA, off_partB, off_tabA, off_tabB, off_lamnext;
   size_t off_partE;  // the normal EM's pass-A slots (pass A's partition, em_nv sums each)
   size_t off_maskR;  // the masked covariances of ffca_mask_init [problems][J][I][I] complex
+  size_t off_resHist;  // the resident kernel's per-iteration L2 [kResChunk][problems]
   size_t bytes;
 };
 
@@ -194,6 +196,7 @@ void layout(Plan* p, const FastKernels* k, int P, int I, int J) {
   p->off_lamnext = off; off = align_up(off + sizeof(double) * (size_t)P * J * I);
   p->off_partE = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * k->em_nv);
   p->off_maskR = off; off = align_up(off + sizeof(double) * 2 * (size_t)P * J * I * I);
+  p->off_resHist = off; off = align_up(off + sizeof(double) * (size_t)kResChunk * P);
   // the adjoint kernels use pass A's partition; J I + 2 I^2 + 2 sums per slot at most
   p->off_partAdj = off; off = align_up(off + sizeof(double) * (size_t)P * p->pA.max_slots * (J * I + 2 * I * I + 2));
   p->off_lossf = off; off = align_up(off + sizeof(double) * (size_t)P);
@@ -254,6 +257,9 @@ struct ffca_ctx {
   int pmode;
   double mu;
   int fault;  // injected fault for tests (kFaultNone unless ffca_test_fault set one)
+  int resident;      // iterate with each problem resident on chip (ffca_set_resident)
+  int max_frames;    // frames of the largest problem
+  size_t res_smem;   // dynamic shared memory of the resident kernel
   // profiling
   int timing;
   unsigned long long launches[FFCA_KERNEL_KINDS];
@@ -320,7 +326,7 @@ FastArgs pass_b_args(const ffca_ctx* c, int slot) {
 // push and pop cost a branch.
 const char* const kKindNames[FFCA_KERNEL_KINDS] = {
     "ffca prep", "ffca pass A", "ffca loglik", "ffca pass B", "ffca wiener",
-    "ffca P step", "ffca pass A finalise", "ffca adjoint", "ffca adjoint finalise"};
+    "ffca P step", "ffca pass A finalise", "ffca adjoint", "ffca adjoint finalise", "ffca resident"};
 
 template <typename Args>
 ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, Args& a, size_t smem = 0) {
@@ -377,6 +383,35 @@ const void* p_step_kernel(const ffca_ctx* c) {
 }
 
 int finals_grid(const ffca_ctx* c) { return (c->d.F + kFinalWarps - 1) / kFinalWarps; }
+
+// Iterations with each problem resident on chip: chunks of up to kResChunk
+// iterations per launch; with a trace each chunk's per-problem L2 are summed
+// into trace slots 0 .. n-1 and copied to host[t0 ..] (synchronising).
+bool resident_active(const ffca_ctx* c) { return c->resident && c->pmode == kPFixedPoint; }
+
+ffca_status enqueue_resident(ffca_ctx* c, int iters, double* host_trace) {
+  ResArgs r;
+  std::memset(&r, 0, sizeof(r));
+  r.a = base_args(c);
+  r.a.part = c->plan.pA;
+  r.a.pinvH = reinterpret_cast<double*>(c->ws + c->plan.off_pinvH);
+  r.hist = reinterpret_cast<double*>(c->ws + c->plan.off_resHist);
+  double* dtrace = reinterpret_cast<double*>(c->ws + c->plan.off_trace);
+  for (int t0 = 0; t0 < iters; t0 += kResChunk) {
+    r.iters = std::min(kResChunk, iters - t0);
+    ffca_status st = launch(c, FFCA_KERNEL_RESIDENT, c->kern->resident, c->d.F, kResThreads, r, c->res_smem);
+    if (st != FFCA_OK) return st;
+    if (host_trace) {
+      k_res_trace<<<r.iters, 32, 0, c->stream>>>(r.hist, c->d.F, dtrace, 0);
+      if (!cuda_ok(cudaGetLastError(), "k_res_trace") ||
+          !cuda_ok(cudaMemcpyAsync(host_trace + t0, dtrace, sizeof(double) * r.iters, cudaMemcpyDeviceToHost,
+                                   c->stream), "cudaMemcpyAsync(trace)") ||
+          !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"))
+        return FFCA_ERR_CUDA;
+    }
+  }
+  return FFCA_OK;
+}
 
 // One iteration with the normal EM update of P: pass A with the EM sums
 // (on pass A's partition, em_groups pipeline groups per CTA) and the
@@ -437,8 +472,9 @@ namespace {
 
 // The launches of `iters` iterations without trace copies (capturable).
 ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
-  ffca_status st = launch_prep(c, false);
+  ffca_status st = launch_prep(c, resident_active(c));
   if (st != FFCA_OK) return st;
+  if (resident_active(c)) return enqueue_resident(c, iters, nullptr);
   for (int t = 0; t < iters; ++t) {
     const int slot = t % kTraceCap;
     if (c->pmode == kPEM) {
@@ -500,6 +536,10 @@ ffca_status iterate_graph(ffca_ctx* c, int iters) {
   }
   if (!cuda_ok(cudaGraphLaunch(c->graph, c->stream), "cudaGraphLaunch")) return FFCA_ERR_CUDA;
   c->launches[FFCA_KERNEL_PREP] += 1;
+  if (resident_active(c)) {
+    c->launches[FFCA_KERNEL_RESIDENT] += (iters + kResChunk - 1) / kResChunk;
+    return FFCA_OK;
+  }
   c->launches[FFCA_KERNEL_ESTEP] += iters;
   if (c->pmode != kPEM) c->launches[FFCA_KERNEL_WCOV] += iters;
   c->launches[FFCA_KERNEL_PSOLVE] += iters;
@@ -609,6 +649,7 @@ ffca_status ffca_init(ffca_ctx** out, const ffca_desc* d) {
   c->err_f = -1;
   c->M = 1;
   c->Fm = d->F;
+  c->max_frames = d->N;
   if (d->F > 0 && cudaMemsetAsync(c->ws, 0, p.bytes, c->stream) != cudaSuccess) {
     std::free(c);
     return FFCA_ERR_CUDA;
@@ -625,6 +666,22 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
     return FFCA_OK;
   }
   if (c->use_graph && !ll_trace) return iterate_graph(c, iters);
+  if (resident_active(c)) {
+    ffca_status st = launch_prep(c, true);
+    if (st == FFCA_OK) st = enqueue_resident(c, iters, ll_trace);
+    if (st != FFCA_OK) return st;
+    if (!ll_trace) return cudaGetLastError() == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
+    // L2 of the final state
+    FastArgs a = pass_a_args(c, 0);
+    if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, stream_grid(c, a.part), stream_threads(c), a,
+                     c->kern->stream_smem)) != FFCA_OK ||
+        (st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) != FFCA_OK)
+      return st;
+    if (!cuda_ok(cudaMemcpyAsync(ll_trace + iters, a.trace, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                 "cudaMemcpyAsync(trace)"))
+      return FFCA_ERR_CUDA;
+    return read_status(c);
+  }
   ffca_status st = launch_prep(c, false);
   if (st != FFCA_OK) return st;
   const double* dtrace = reinterpret_cast<const double*>(c->ws + c->plan.off_trace);
@@ -1081,6 +1138,7 @@ ffca_status ffca_batch_init(ffca_batch_ctx** out, const ffca_batch_desc* d) {
   c->plan = p;
   c->M = d->M;
   c->Fm = d->F;
+  c->max_frames = *std::max_element(d->N, d->N + d->M);
   c->stream = static_cast<cudaStream_t>(d->stream);
   c->ws = static_cast<char*>(d->workspace);
   c->status = reinterpret_cast<unsigned*>(c->ws);
@@ -1273,6 +1331,24 @@ ffca_status ffca_mask_init(ffca_ctx* c, const void* masks, int sweeps, double de
     if (!cuda_ok(launch_mask_init(c->d.prec, a, c->d.F, c->stream), "launch_mask_init")) return FFCA_ERR_CUDA;
   }
   return read_status(c);
+}
+
+ffca_status ffca_set_resident(ffca_ctx* c, int enable) {
+  if (!c) return FFCA_ERR_ARG;
+  if (enable) {
+    if (!c->kern->resident || c->max_frames > c->kern->res_max_frames) return FFCA_ERR_UNSUPPORTED;
+    const size_t smem = (size_t)((c->max_frames + 3) / 4 * 4) * c->kern->res_bytes_per_frame;
+    if (!cuda_ok(cudaFuncSetAttribute(c->kern->resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                 "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, resident)"))
+      return FFCA_ERR_CUDA;
+    c->res_smem = smem;
+  }
+  c->resident = enable ? 1 : 0;
+  if (c->graph) {  // the captured launches are the other form's
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return FFCA_OK;
 }
 
 static_assert(FFCA_FAULT_NONE == kFaultNone && FFCA_FAULT_PASS_A_NO_COPIES == kFaultPassANoCopies,

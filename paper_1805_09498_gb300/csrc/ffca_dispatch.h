@@ -31,6 +31,10 @@ struct FastKernels {
   const void* pnewton;       // the P step with Newton's method (one warp per problem; nullptr for I > 4)
   int wcov_groups;           // pipeline groups per CTA of pass B (stream_groups: pass A)
   int wcov_smem;             // dynamic shared memory of pass B (stream_smem: pass A)
+  // iterations with each problem resident in shared memory (nullptr for I > 4)
+  const void* resident;
+  int res_bytes_per_frame;   // shared memory per frame of a problem
+  int res_max_frames;        // frames of the largest problem it takes
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

@@ -11,6 +11,7 @@
 #include "ffca_fca.cuh"
 #include "ffca_fca_big.cuh"
 #include "ffca_newton.cuh"
+#include "ffca_resident.cuh"
 #include "ffca_stream.cuh"
 
 #ifndef FFCA_PREC
@@ -66,7 +67,12 @@ static const FastKernels* table_entry() {
   const void* psolve_em = nullptr;
   const void* pnewton = nullptr;
   int em_smem = 0, em_solve_smem = 0, em_nv = 0, em_groups = 1;
+  const void* resident = nullptr;
+  int res_bpf = 0, res_max = 0;
 #if FFCA_I <= 4
+  resident = (const void*)k_resident<Real, FFCA_I, J>;
+  res_bpf = ResShape<Real, FFCA_I, J>::BYTES_PER_FRAME;
+  res_max = ResShape<Real, FFCA_I, J>::max_frames();
   estep_em = FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(J);
   psolve_em = FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(J);
   em_groups = EmGroups<Real, FFCA_I, J>::value;
@@ -99,6 +105,9 @@ static const FastKernels* table_entry() {
       pnewton,
       WcovGroups<Real, FFCA_I, J>::value,
       WcovGroups<Real, FFCA_I, J>::value * Tile<Real, FFCA_I, J, WcovGroups<Real, FFCA_I, J>::value>::GROUP,
+      resident,
+      res_bpf,
+      res_max,
   };
   return &k;
 }

@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
         "ffca_status_str": (ctypes.c_char_p, [ci]),
         "ffca_peak_fp64": (ci, [vp, dp]),
         "ffca_mask_init": (ci, [vp, vp, ci, ctypes.c_double]),
+        "ffca_set_resident": (ci, [vp, ci]),
         "ffca_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
@@ -249,7 +250,7 @@ def ffca_wiener_host(ctx, out_dev_ptr: int, out_host_ptr: int) -> None:
                                        ctypes.c_void_p(out_host_ptr)), "ffca_wiener_host")
 
 
-KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener", "psolve", "afinal", "adj", "adj_final")
+KERNEL_KINDS = ("prep", "estep", "loglik", "wcov", "wiener", "psolve", "afinal", "adj", "adj_final", "resident")
 
 
 def ffca_timing_enable(ctx, enable: bool) -> None:
@@ -505,6 +506,10 @@ class FastFCA:
     def loglik(self) -> float:
         return ffca_loglik(self.ctx)
 
+    def set_resident(self, enable: bool = True):
+        """Iterations with each problem resident on chip (ffca_set_resident)."""
+        _check(self.ctx, lib().ffca_set_resident(self.ctx, 1 if enable else 0), "ffca_set_resident")
+
     def mask_init(self, masks, sweeps: int = 10, delta: float = 1e-3):
         """Initialise v, lam and P in place from time-frequency masks (a device
         tensor of v's shape and dtype), ffca_mask_init."""
@@ -709,6 +714,10 @@ class FastFCABatch:
     def loglik(self) -> np.ndarray:
         """L2 of every mixture (host array of M values)."""
         return ffca_batch_loglik(self.ctx, self.M)
+
+    def set_resident(self, enable: bool = True):
+        """Iterations with each problem resident on chip (ffca_set_resident)."""
+        _check(self.ctx, lib().ffca_set_resident(self.ctx, 1 if enable else 0), "ffca_set_resident")
 
     def mask_init(self, masks, sweeps: int = 10, delta: float = 1e-3):
         """Initialise every mixture's v, lam and P in place from masks in the

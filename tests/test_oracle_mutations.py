@@ -223,3 +223,72 @@ def test_a_pin_catches_the_planted_fca_mistake(monkeypatch, name, mutant):
 def test_the_pins_pass_on_the_oracle():
     for pin, kw in PINS + FCA_PINS:
         pin(**kw)
+
+
+# ---------------------------------------------------- the mask-based initialisation
+from oracle import mask_init as mi  # noqa: E402
+
+import test_oracle_mask_init as mpins  # noqa: E402
+
+
+def _mcov_over_n(y, m):  # divided by the frame count instead of the mask's sum
+    return np.einsum("jfn,afn,bfn->fjab", m, y, y.conj()) / y.shape[2]
+
+
+def _mcov_transposed(y, m):  # conj(y) y^T instead of y y^H
+    num = np.einsum("jfn,afn,bfn->fjab", m, y.conj(), y)
+    return num / np.sum(m, axis=2).T[:, :, None, None]
+
+
+def _gevd_wrong_side(R):  # L^{-H} R_1 L^{-1} instead of L^{-1} R_1 L^{-H}, no phase rule
+    L = np.linalg.cholesky(R.sum(axis=1))
+    Li = np.linalg.inv(L)
+    W = Li.conj().transpose(0, 2, 1) @ R[:, 0] @ Li
+    _, U = np.linalg.eigh(W)
+    return Li.conj().transpose(0, 2, 1) @ U
+
+
+def _powers_no_conj(R, P):  # p_i^T R_j p_i
+    return np.einsum("fai,fjab,fbi->fji", P, R, P).real
+
+
+def _v_mask_squared(y, m, P, lam, delta=mi.DELTA):  # m^2 and no floor
+    I = y.shape[0]
+    e2 = np.abs(ffa.basis_transform(y, P)) ** 2
+    return m ** 2 * np.einsum("ifn,fji->jfn", e2, 1.0 / lam) / I
+
+
+def _ajd_times_lambda(R, sweeps=mi.SWEEPS):  # V_i = sum_j R_j lambda_ji / J
+    J = R.shape[1]
+    P = mi.gevd_start(R)
+    for _ in range(sweeps):
+        lam = mi.diag_powers(R, P)
+        P = ffa.fixed_point_P(P, np.einsum("fjab,fji->fiab", R, lam) / J, 1, ffa.OpCounter())
+    return P, mi.diag_powers(R, P)
+
+
+MASK_MUTANTS = [("masked_covariances", _mcov_over_n), ("masked_covariances", _mcov_transposed),
+                ("gevd_start", _gevd_wrong_side), ("diag_powers", _powers_no_conj),
+                ("initial_v", _v_mask_squared), ("joint_diagonaliser", _ajd_times_lambda)]
+MASK_PINS = [(mpins.test_masked_covariance_is_the_weighted_second_moment, {}),
+             (mpins.test_two_sources_are_diagonalised_exactly, {}),
+             (mpins.test_jointly_diagonalisable_sources_are_recovered, {}),
+             (mpins.test_an_exact_joint_diagonaliser_is_a_fixed_point, {}),
+             (mpins.test_sweeps_raise_the_criterion, {}),
+             (mpins.test_initial_v_is_the_masked_quadratic_form, {})]
+
+
+@pytest.mark.parametrize("name,mutant", MASK_MUTANTS, ids=[m.__name__.strip("_") for _, m in MASK_MUTANTS])
+def test_a_pin_catches_the_planted_mask_init_mistake(monkeypatch, name, mutant):
+    monkeypatch.setattr(mi, name, mutant)
+    for pin, kw in MASK_PINS:
+        try:
+            pin(**kw)
+        except (AssertionError, np.linalg.LinAlgError):
+            return
+    pytest.fail(f"no pin caught {mutant.__name__} in mask_init.{name}")
+
+
+def test_the_mask_init_pins_pass_on_the_oracle():
+    for pin, kw in MASK_PINS:
+        pin(**kw)
