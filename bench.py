@@ -564,6 +564,43 @@ def run_plain_fp64(args, dev, pool):
     kt = ffca.ffca_timing_read(est.ctx)
     ffca.ffca_timing_enable(est.ctx, False)
     est.close()
+
+    def resident_and_mixed():
+        """The same workload with each problem resident on chip (one CTA per
+        frequency, all 20 iterations in one launch), and both forms in the
+        mixed precision at the same shape: rate and error against the oracle."""
+        out = {}
+        for prec in ("fp64", "mixed"):
+            yq, vq, lq, Pq, _ = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec=prec, device=dev)
+            v0q, l0q, P0q = vq.clone(), lq.clone(), Pq.clone()
+            for form in ("resident", "streaming") if prec == "mixed" else ("resident",):
+                vq.copy_(v0q); lq.copy_(l0q); Pq.copy_(P0q)
+                e = ffca.FastFCA(yq, vq, lq, Pq, N=N)
+                if form == "resident":
+                    e.set_resident(True)
+                trq = e.iterate(iters)
+                errq = {"v": relerr(vq[:, :, :N].double().cpu().numpy(), rv, 1), "lambda": relerr(lq.cpu().numpy(), rl, 0),
+                        "P": relerr(Pq.cpu().numpy(), rP, 0)}
+                if prec == "fp64":
+                    errq["loglik_rel"] = float(np.max(np.abs(trq - rt) / np.abs(rt)))
+                else:
+                    errq["loglik_per_point"] = float(np.max(np.abs(trq - rt)) / (N * F))
+                e.set_graph(True)
+                for _ in range(3):
+                    e.iterate(iters, trace=False)
+                msq = timed(lambda: e.iterate(iters, trace=False), reps)
+                e.set_graph(False)
+                msqt = timed(lambda: e.iterate(iters), 5)
+                e.close()
+                out[f"{form}_{prec}"] = {"value": units / (msq * 1e-3), "ms_per_run": msq,
+                                         "with_trace": {"value": units / (msqt * 1e-3), "ms_per_run": msqt},
+                                         "error_vs_oracle": errq}
+            del yq, vq, lq, Pq, v0q, l0q, P0q
+        out["how"] = ("graph replay of the 20 iterations, CUDA events, 20 runs (with_trace: plain launches, "
+                      "L2 trace copied back); resident: ffca_set_resident, one launch per 20 iterations")
+        return out
+
+    forms = resident_and_mixed()
     peak64 = ffca.ffca_peak_fp64(stream)
     kernels = {}
     for k, kname, bpt in (("estep", "k_estep<double, 3, 3, 1, 0>", I * 16 + 2 * J * 8),
@@ -608,7 +645,7 @@ def run_plain_fp64(args, dev, pool):
             "with_trace": {"value": units / (ms_trace * 1e-3), "ms_per_run": ms_trace,
                            "how": "plain launches, L2 trace copied back"},
             "kernels": kernels, "fp64_peak_gflops_measured": peak64,
-            "error_vs_oracle": err,
+            "error_vs_oracle": err, "forms": forms,
             "oracle": {"one_core": {"value": units / one_core_s, "seconds": one_core_s, "cores": 1},
                        "all_cores": {"value": units / all_s, "seconds": all_s, "cores": pool.workers},
                        "sample": "the whole workload (every frequency, frame and iteration)"},

@@ -9,10 +9,12 @@
 //   k_resident  per iteration, the whole CTA: pass A (y~, sigma, the
 //               posterior powers, v in place, the sums of Eq. Lambdaupdate
 //               and of Eq. L2; per-point arithmetic in T, every thread's
-//               sums over a few frames, then a block reduction in FP64), the
+//               sums over ceil(N / 256) frames in T, a butterfly over each
+//               warp's lanes in T, the warps added in FP64), the
 //               new Lambda and the problem's L2 of the entering state (FP64),
-//               pass B as I sub-passes (V_i for one i each), then warp 0 runs
-//               the P step of k_psolve_ldl (L D L^H of V_i, the columns
+//               pass B (the outer product of each frame once, weighted into
+//               every V_i; two sub-passes of two V_i in FP64 at I = 4, one
+//               otherwise), then warp 0 runs the P step of k_psolve_ldl (L D L^H of V_i, the columns
 //               V_i^{-1} [P^{-H}]_i, K sweeps, the inverse of the new P for
 //               ln|det P|^2 and the next P^{-H}).  At the end v, Lambda, P,
 //               P^{-H}, ln|det P|^2 and the pass-A table go back to global
@@ -36,10 +38,53 @@ struct ResArgs {
   int iters;       // iterations of this launch (<= kResChunk)
 };
 
+// Block sum of NV per-thread values in T: a butterfly reduce-scatter in
+// each warp (31 exchanges per 32 values; lane l ends with value l of its
+// chunk), then the warps' results added in FP64 in warp order.  Thread
+// t < NV writes value t to out[t].  Called by the whole CTA.
+template <typename T, int NV>
+struct ResReduce {
+  static constexpr int NC = (NV + 31) / 32;
+  struct Smem {
+    T v[kResWarps][NC * 32];
+  };
+  __device__ static void run(const T (&x)[NV], Smem& sm, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T h[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) h[k] = c * 32 + k < NV ? x[c * 32 + k] : (T)0;
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < off; ++k) {
+          const T keep = up ? h[k + off] : h[k];
+          const T send = up ? h[k] : h[k + off];
+          h[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      sm.v[warp][c * 32 + lane] = h[0];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < NV; t += kResThreads) {
+      double s = (double)sm.v[0][t];
+#pragma unroll
+      for (int w = 1; w < kResWarps; ++w) s += (double)sm.v[w][t];
+      out[t] = s;
+    }
+    __syncthreads();
+  }
+};
+
 template <typename T, int I, int J>
 struct ResShape {
   static constexpr int NVA = J * I + 2;  // Lambda sums, then the quadratic and log2 parts of L2
   static constexpr int NVB = I * I;      // V_i of one i (packed Hermitian)
+  // V_i summed together in one sub-pass of pass B (the FP64 I = 4 form takes
+  // two sub-passes of two, to keep its accumulators in registers)
+  static constexpr int IB = (sizeof(T) == 8 && I == 4) ? 2 : I;
   // bytes of shared memory per frame
   static constexpr int BYTES_PER_FRAME = I * (int)sizeof(cpx<T>) + J * (int)sizeof(T);
   static constexpr int max_frames() { return (kResSmemBudget / BYTES_PER_FRAME) / 4 * 4; }
@@ -49,11 +94,11 @@ template <typename T, int I, int J>
 __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
   using RS = ResShape<T, I, J>;
   using C = cpx<T>;
-  constexpr int NVA = RS::NVA, NVB = RS::NVB, NA = J * I;
+  constexpr int NVA = RS::NVA, NVB = RS::NVB, NA = J * I, IB = RS::IB;
   extern __shared__ __align__(16) unsigned char res_smem[];
-  __shared__ typename BlockReduce<double, NVA, kResWarps>::Smem redA;
-  __shared__ typename BlockReduce<double, NVB, kResWarps>::Smem redB;
-  __shared__ double sumsA[NVA], sumsB[NVB];
+  __shared__ typename ResReduce<T, NVA>::Smem redA;
+  __shared__ typename ResReduce<T, IB * NVB>::Smem redB;
+  __shared__ double sumsA[NVA], sumsB[IB * NVB];
   __shared__ double sV[I][NVB];          // V_i / N, packed Hermitian per i
   __shared__ double sLam[J][I];          // current Lambda (FP64)
   __shared__ T sLamT[J][I];              // and in T
@@ -104,7 +149,6 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
   bool singular = false;  // warp 0, lanes < I
   for (int it = 0; it < ra.iters; ++it) {
     // ---------------------------------------------------------- pass A
-    double ha[NVA], la[NVA];
     {
       T acc[NVA];
 #pragma unroll
@@ -117,6 +161,8 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
 #pragma unroll
         for (int j = 0; j < J; ++j) vj[j] = v[j * np + t];
         T r[I], e2[I];
+        T lm = (T)1;  // FP64: product of the sigmas' mantissas and sum of their exponents
+        int le = 0;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
           C s = mk<T>(0, 0);
@@ -128,9 +174,15 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
           r[i] = recip(sg);
           e2[i] = cabs2(s);
           acc[NA] = fma(e2[i], r[i], acc[NA]);
-          if constexpr (sizeof(T) == 4) acc[NA + 1] += __log2f(sg);
-          else acc[NA + 1] += log2(sg);
+          if constexpr (sizeof(T) == 4) {
+            acc[NA + 1] += __log2f(sg);
+          } else {  // one software log2 per frame: the sigmas' mantissas multiplied, their exponents added
+            int k;
+            lm *= frexp(sg, &k);
+            le += k;
+          }
         }
+        if constexpr (sizeof(T) == 8) acc[NA + 1] += log2(lm) + (double)le;
 #pragma unroll
         for (int j = 0; j < J; ++j) {  // Eqs. updatev and Lambdaupdate in the form of k_estep
           T tj[I], sj = (T)0;
@@ -146,14 +198,8 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
           v[j * np + t] = vj[j] * sj * (T)(1.0 / I);
         }
       }
-#pragma unroll
-      for (int q = 0; q < NVA; ++q) {
-        ha[q] = (double)acc[q];
-        la[q] = 0.0;
-      }
+      ResReduce<T, NVA>::run(acc, redA, sumsA);
     }
-    BlockReduce<double, NVA, kResWarps>::run(ha, la, redA, sumsA);
-    __syncthreads();
     // the new Lambda and the problem's L2 of the entering state (FP64)
     if (tid < NA) {
       const int j = tid / I, i = tid % I;
@@ -168,42 +214,44 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
     }
     __syncthreads();
     // ---------------------------------------------------------- pass B
+    // V_i for IB values of i per sub-pass: the frame's outer product y y^H
+    // once, weighted by 1 / sigma_i for each i of the sub-pass
 #pragma unroll 1
-    for (int i = 0; i < I; ++i) {
-      double hb[NVB], lb[NVB];
-      {
-        T acc[NVB];
+    for (int i0 = 0; i0 < I; i0 += IB) {
+      T acc[IB * NVB];
 #pragma unroll
-        for (int q = 0; q < NVB; ++q) acc[q] = (T)0;
-        for (int t = tid; t < n; t += kResThreads) {
-          T sg = v[t] * sLamT[0][i];
+      for (int q = 0; q < IB * NVB; ++q) acc[q] = (T)0;
+      for (int t = tid; t < n; t += kResThreads) {
+        C ym[I];
 #pragma unroll
-          for (int j = 1; j < J; ++j) sg = fma(v[j * np + t], sLamT[j][i], sg);
-          const T w = recip(sg);
-          C ym[I];
-#pragma unroll
-          for (int m = 0; m < I; ++m) ym[m] = y[m * np + t];
+        for (int m = 0; m < I; ++m) ym[m] = y[m * np + t];
+        T o[NVB];  // |y_r|^2, then (Re, Im) of y_r conj(y_c) for r < c
+        {
           int q = I;
 #pragma unroll
           for (int rr = 0; rr < I; ++rr) {
-            acc[rr] = fma(w, cabs2(ym[rr]), acc[rr]);
+            o[rr] = cabs2(ym[rr]);
 #pragma unroll
-            for (int c = rr + 1; c < I; ++c) {  // y_r conj(y_c)
-              acc[q] = fma(w, ym[rr].re * ym[c].re + ym[rr].im * ym[c].im, acc[q]);
-              acc[q + 1] = fma(w, ym[rr].im * ym[c].re - ym[rr].re * ym[c].im, acc[q + 1]);
+            for (int c = rr + 1; c < I; ++c) {
+              o[q] = ym[rr].re * ym[c].re + ym[rr].im * ym[c].im;
+              o[q + 1] = ym[rr].im * ym[c].re - ym[rr].re * ym[c].im;
               q += 2;
             }
           }
         }
 #pragma unroll
-        for (int q = 0; q < NVB; ++q) {
-          hb[q] = (double)acc[q];
-          lb[q] = 0.0;
+        for (int ib = 0; ib < IB; ++ib) {
+          const int i = i0 + ib;
+          T sg = v[t] * sLamT[0][i];
+#pragma unroll
+          for (int j = 1; j < J; ++j) sg = fma(v[j * np + t], sLamT[j][i], sg);
+          const T w = recip(sg);
+#pragma unroll
+          for (int q = 0; q < NVB; ++q) acc[ib * NVB + q] = fma(w, o[q], acc[ib * NVB + q]);
         }
       }
-      BlockReduce<double, NVB, kResWarps>::run(hb, lb, redB, sumsB);
-      __syncthreads();
-      if (tid < NVB) sV[i][tid] = sumsB[tid] * pt.inv_n(p);
+      ResReduce<T, IB * NVB>::run(acc, redB, sumsB);
+      if (tid < IB * NVB) sV[i0 + tid / NVB][tid % NVB] = sumsB[tid] * pt.inv_n(p);
       __syncthreads();
     }
     // ---------------------------------------------------------- P step (warp 0)

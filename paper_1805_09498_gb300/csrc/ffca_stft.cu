@@ -9,17 +9,21 @@
 // The inverse runs the same steps backwards.  FP32 data, twiddles and window
 // rounded from FP64 values computed on the host.
 //
-// One warp transforms one frame, in registers and across its lanes by
-// shuffles (fft512_warp: 512 = 16 x 32, a 16-point DFT per lane and a
-// 32-point DFT over the lanes), so no barrier separates the stages; a CTA
-// takes kFrames consecutive frames of one channel and moves the spectra
-// through shared memory as runs of kFrames frames per bin (the
-// frame-contiguous mic-planar layout), 64 bytes per bin row.  Sixteen frames
-// per CTA (128-byte runs) measured no faster forward and slower inverse
-// (2.45 against 1.71 ms): their 135 KB of shared memory leave one CTA per SM,
-// whose load, transform and store phases then do not overlap another's.
+// One warp transforms one frame (fft512_warp: 512 = 16 x 32, a 16-point DFT
+// per lane, one transpose through the warp's shared-memory buffer, then a
+// radix-2 step and a second 16-point DFT per lane), so no barrier separates
+// the stages and no value crosses lanes by shuffles.  The real split pairs
+// bins k and 512 - k (one pair of reads makes both).  Both directions run
+// persistent CTAs of kFrames warps over groups of kFrames frames: the next
+// group's input is copied into a second shared-memory stage (cp.async)
+// while the current group is transformed.  The spectra move through shared
+// memory with swizzled bin rows (conflict-free per-bin stores, 16-byte
+// loads) as runs of kFrames frames per bin: the frame-contiguous mic-planar
+// layout, 64 bytes per bin row, two frames per 16-byte store.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -32,13 +36,15 @@ constexpr int kL = 1024;        // frame length
 constexpr int kH = 512;         // frame shift
 constexpr int kM = 512;         // complex FFT size (two real samples per point)
 constexpr int kF = kL / 2 + 1;  // bins up to Nyquist
-constexpr int kFrames = 8;      // frames per CTA: one per warp (68 KB of shared memory: three CTAs per SM)
+constexpr int kFrames = 8;      // frames per group: one per warp of a CTA (about 100 KB of shared memory: two CTAs per SM)
 constexpr int kThreads = 32 * kFrames;
 constexpr int kMaxDev = 64;
 
 __device__ float2 g_tw512[kM];   // e^{-2 pi i m / 512}
 __device__ float2 g_tw1024[kF];  // e^{-2 pi i k / 1024}, k = 0 .. 512
-__device__ float g_win[kL];      // sin(pi t / 1024): the square root of the periodic Hann window
+__constant__ float2 c_w32[32];   // e^{-2 pi i m / 32}: indexed by compile-time constants only (operands of the
+                                 // arithmetic, no loads); W16^m = W32^(2m)
+__device__ __align__(16) float g_win[kL];  // sin(pi t / 1024): the square root of the periodic Hann window
 
 std::mutex g_tab_mutex;
 bool g_tab_ready[kMaxDev];
@@ -49,7 +55,7 @@ ffca_status ensure_tables() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return FFCA_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_tab_mutex);
   if (g_tab_ready[dev]) return FFCA_OK;
-  static float2 tw512[kM], tw1024[kF];
+  static float2 tw512[kM], tw1024[kF], w32[32];
   static float win[kL];
   const double pi = 3.14159265358979323846;
   for (int m = 0; m < kM; ++m)
@@ -57,9 +63,11 @@ ffca_status ensure_tables() {
   for (int k = 0; k < kF; ++k)
     tw1024[k] = make_float2((float)std::cos(2.0 * pi * k / kL), (float)-std::sin(2.0 * pi * k / kL));
   for (int t = 0; t < kL; ++t) win[t] = (float)std::sin(pi * t / kL);
+  for (int m = 0; m < 32; ++m) w32[m] = make_float2((float)std::cos(2.0 * pi * m / 32), (float)-std::sin(2.0 * pi * m / 32));
   if (cudaMemcpyToSymbol(g_tw512, tw512, sizeof(tw512)) != cudaSuccess ||
       cudaMemcpyToSymbol(g_tw1024, tw1024, sizeof(tw1024)) != cudaSuccess ||
-      cudaMemcpyToSymbol(g_win, win, sizeof(win)) != cudaSuccess)
+      cudaMemcpyToSymbol(g_win, win, sizeof(win)) != cudaSuccess ||
+      cudaMemcpyToSymbol(c_w32, w32, sizeof(w32)) != cudaSuccess)
     return FFCA_ERR_CUDA;
   g_tab_ready[dev] = true;
   return FFCA_OK;
@@ -84,10 +92,9 @@ __device__ inline void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
 
 // 16-point DFT of u[0..15] in registers (forward): with n = 4 n1 + n2 and
 // k = k1 + 4 k2, X[k] = sum_n2 W4^(n2 k2) W16^(n2 k1) sum_n1 W4^(n1 k1) u[4 n1 + n2]:
-// four 4-point DFTs over n1, the twiddles W16^(n2 k1) (from the 512-point
-// table: W16^m = W512^(32 m)), four 4-point DFTs over n2.  Output in
-// natural order.
-__device__ inline void dft16(float2 (&u)[16], const float2* __restrict__ tw) {
+// four 4-point DFTs over n1, the twiddles W16^(n2 k1) (constant operands:
+// W16^m = W32^(2m)), four 4-point DFTs over n2.  Output in natural order.
+__device__ inline void dft16(float2 (&u)[16]) {
   float2 y[4][4];  // [n2][k1]
 #pragma unroll
   for (int n2 = 0; n2 < 4; ++n2) {
@@ -101,7 +108,7 @@ __device__ inline void dft16(float2 (&u)[16], const float2* __restrict__ tw) {
 #pragma unroll
   for (int n2 = 1; n2 < 4; ++n2)
 #pragma unroll
-    for (int k1 = 1; k1 < 4; ++k1) y[n2][k1] = cmul(y[n2][k1], __ldg(tw + 32 * n2 * k1));
+    for (int k1 = 1; k1 < 4; ++k1) y[n2][k1] = cmul(y[n2][k1], c_w32[2 * n2 * k1]);
 #pragma unroll
   for (int k1 = 0; k1 < 4; ++k1) {
     float2 a0 = y[0][k1], a1 = y[1][k1], a2 = y[2][k1], a3 = y[3][k1];
@@ -113,165 +120,312 @@ __device__ inline void dft16(float2 (&u)[16], const float2* __restrict__ tw) {
   }
 }
 
+// Per-warp work buffer: the transpose of fft512_warp (32 rows of 16 values,
+// pitch 17, so that the lanes' row writes fall in distinct banks), then the
+// 512 values of Z (forward) or the frame's two windowed halves (inverse).
+constexpr int kBufPitch = 17;
+constexpr int kBuf = 32 * kBufPitch;
+
 // 512-point forward DFT by one warp.  Lane l enters with u[q] = z[l + 32 q]
-// (q = 0..15).  Writing k = r + 16 k2 (r = 0..15, k2 = 0..31):
-//   Z[r + 16 k2] = sum_l W32^(l k2) W512^(l r) sum_q W16^(q r) z[l + 32 q],
-// so every lane transforms its sixteen values (dft16), multiplies entry r by
-// W512^(l r), and the warp runs the 32-point DFT over l for every r as five
-// radix-2 decimation-in-frequency stages across the lanes (partner lane
-// l ^ h; the upper lane takes (partner - own) W_2h^(l mod h)).  On return
-// lane l holds u[r] = Z[r + 16 rev5(l)], rev5 the 5-bit reversal.
-__device__ inline void fft512_warp(float2 (&u)[16], int lane, const float2* __restrict__ tw) {
-  dft16(u, tw);
+// (q = 0..15).  With k = r + 16 k2 (r = 0..15, k2 = 0..31):
+//   Z[r + 16 k2] = sum_l W32^(l k2) a_l[r],  a_l[r] = W512^(l r) sum_q W16^(q r) z[l + 32 q].
+// Every lane forms its a_l (dft16 and its twiddles tw1[r - 1] = W512^(l r),
+// held in registers by the caller) and writes it to row l of the buffer.
+// Lane L then takes r = L mod 16 and g = L / 16 and splits the 32-point DFT
+// over l by the parity of k2 = 2 j + g (decimation in frequency):
+// Z[r + 16 (2 j + g)] = sum_{m<16} W16^(m j) W32^(m g) (a_m[r] + (-1)^g a_{m+16}[r]),
+// a 16-point DFT of sixteen values it reads from the buffer.  On return lane
+// L holds u[j] = Z[r + 16 (2 j + g)] = Z[L + 32 j], and the buffer is free.
+__device__ inline void fft512_warp(float2 (&u)[16], int lane, float2* __restrict__ buf, const float2 (&tw1)[15]) {
+  dft16(u);
 #pragma unroll
-  for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], __ldg(tw + ((lane * r) & (kM - 1))));
+  for (int r = 1; r < 16; ++r) u[r] = cmul(u[r], tw1[r - 1]);
 #pragma unroll
-  for (int h = 16; h >= 1; h >>= 1) {
-    const bool upper = (lane & h) != 0;
-    const float2 w = __ldg(tw + (lane & (h - 1)) * (256 / h));  // W_2h^(l mod h) = W512^((l mod h) 256 / h)
+  for (int r = 0; r < 16; ++r) buf[lane * kBufPitch + r] = u[r];
+  __syncwarp();
+  const int r = lane & 15;
+  const bool odd = lane >= 16;  // g = 1
+  const float sgn = odd ? -1.f : 1.f;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, u[r].x, h), __shfl_xor_sync(0xffffffffu, u[r].y, h));
-      u[r] = upper ? cmul(csub(o, u[r]), w) : cadd(u[r], o);
-    }
+  for (int m = 0; m < 16; ++m) {
+    const float2 p = buf[m * kBufPitch + r], q = buf[(m + 16) * kBufPitch + r];
+    u[m] = make_float2(fmaf(sgn, q.x, p.x), fmaf(sgn, q.y, p.y));
   }
+#pragma unroll
+  for (int m = 1; m < 16; ++m) {  // W32^(m g)
+    const float2 t = cmul(u[m], c_w32[m]);
+    u[m] = odd ? t : u[m];
+  }
+  __syncwarp();
+  dft16(u);
 }
 
-__device__ inline int rev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
+// The first-stage twiddles of lane l, W512^(l r) for r = 1..15.
+__device__ inline void lane_twiddles(int lane, float2 (&tw1)[15]) {
+#pragma unroll
+  for (int r = 1; r < 16; ++r) tw1[r - 1] = __ldg(g_tw512 + ((lane * r) & (kM - 1)));
+}
 
-// Padded index of Z[k] in a warp's buffer: k mod 16 + 17 (k / 16), so that
-// the lanes' writes of u[r] and their reads of consecutive k hit distinct
-// banks (up to two-way).
-__device__ inline int zpad(int k) { return (k & 15) + 17 * (k >> 4); }
-constexpr int kZPad = 17 * (kM / 16);
+// The spectra of a CTA's frames, bin-major: row k holds the kFrames frames
+// of bin k, frame w at position w ^ swz(k).  The swizzle spreads a warp's
+// stores of one frame's 32 consecutive bins over all banks (two wavefronts
+// for 64-bit stores) and keeps every pair of frames (2p, 2p + 1) in one
+// aligned 16-byte slot (in swapped order when swz(k) is odd), so that the
+// rows leave in 16-byte loads and stores.
+__device__ inline int swz(int k) { return (k >> 1) & (kFrames - 1); }
 
-// Padded index of sample s of a half frame (one float of padding per 32), so
-// that the lanes' scalar stores of samples 2t, 2t+1 at t = r + 16 rev5(l)
-// fall in distinct banks.
-__device__ inline int spad(int s) { return s + (s >> 5); }
-constexpr int kHalfPad = kH + kH / 32;
+// Samples of a CTA's group of kFrames frames: frames n0 .. n0 + 7 span
+// (kFrames + 1) H consecutive samples.
+constexpr int kGroupSamples = (kFrames + 1) * kH;
 
 // Shared memory of one CTA.
 struct StftSmem {
-  float2 z[kFrames][kZPad];        // each warp's Z (forward: the real split reads Z[k], Z[512 - k])
-  float2 spec[kF][kFrames];        // the CTA's spectra, bin-major (forward: out; inverse: in)
+  float2 buf[kFrames][kBuf];  // each warp's work buffer
+  float2 spec[kF][kFrames];   // the CTA's spectra (swizzled rows)
 };
-// The inverse keeps the windowed halves of its frames where the forward
-// transform keeps Z.
-static_assert(sizeof(StftSmem::z) >= 2 * kFrames * kHalfPad * sizeof(float), "halves fit in z");
+// Forward: two stages of input samples besides.
+struct StftFwdSmem {
+  StftSmem s;
+  float x[2][kGroupSamples];
+};
+// The inverse keeps its frame's two windowed halves in the warp's buffer.
+static_assert(kBuf * sizeof(float2) >= 2 * kH * sizeof(float), "halves fit in the buffer");
+static_assert((kBuf * sizeof(float2)) % 16 == 0 && sizeof(StftSmem) % 16 == 0, "16-byte alignment");
 
-// x [C][S] float -> out [C][F][ld] complex64 (frames 0 .. N-1, then zero to
-// ld).  Warp w of the CTA transforms frame n0 + w of channel blockIdx.y.
-__global__ void __launch_bounds__(kThreads) k_stft(const float* __restrict__ x, long long S, int N,
-                                                   float2* __restrict__ out, int ld) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  StftSmem& sm = *reinterpret_cast<StftSmem*>(smem_raw);
-  const int c = blockIdx.y;
-  const int n0 = blockIdx.x * kFrames;
-  const int nf = min(kFrames, N - n0);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (w < nf) {
-    const float* xf = x + (size_t)c * S + (size_t)(n0 + w) * kH;  // samples n H .. n H + L - 1 (inside the signal)
-    float2 u[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {  // z(t) = w(2t) x(2t) + i w(2t+1) x(2t+1), t = l + 32 q
-      const int t = lane + 32 * q;
-      u[q] = make_float2(__ldg(g_win + 2 * t) * __ldg(xf + 2 * t), __ldg(g_win + 2 * t + 1) * __ldg(xf + 2 * t + 1));
-    }
-    fft512_warp(u, lane, g_tw512);
-    float2* zb = sm.z[w];
-    const int base = 16 * rev5(lane);
-#pragma unroll
-    for (int r = 0; r < 16; ++r) zb[zpad(base + r)] = u[r];
-    __syncwarp();
-    // X[k] = E[k] + W1024^k O[k], E = (Z[k] + conj Z[512-k]) / 2, O = (Z[k] - conj Z[512-k]) / (2i)
-    for (int k = lane; k < kF; k += 32) {
-      const float2 zk = zb[zpad(k & (kM - 1))];
-      const float2 zm = cconj(zb[zpad((kM - k) & (kM - 1))]);
-      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
-      const float2 o = mul_mi(make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y - zm.y)));
-      sm.spec[k][w] = cadd(e, cmul(__ldg(g_tw1024 + k), o));
-    }
-  }
-  __syncthreads();
-  // runs of consecutive frames per bin
-  float2* oc = out + (size_t)c * kF * ld;
-  for (int t = threadIdx.x; t < kF * kFrames; t += kThreads) {
-    const int f = t / kFrames, n = t % kFrames;
-    if (n < nf) oc[(size_t)f * ld + n0 + n] = sm.spec[f][n];
-  }
-  // padding frames N .. ld - 1 of each row: written by the last CTA
-  if (n0 + kFrames >= N) {
-    const int pad = ld - N;
-    for (int t = threadIdx.x; t < kF * pad; t += kThreads) {
-      const int f = t / pad, n = N + t % pad;
-      oc[(size_t)f * ld + n] = make_float2(0.f, 0.f);
-    }
-  }
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ inline void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ inline void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+// 8 bytes from src, or zeros (nothing read) when !valid
+__device__ inline void cp_async8z(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)),
+               "l"(__cvta_generic_to_global(src)), "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
 }
 
-// in [C][F][ld] complex64 (frames 0 .. N-1) -> out [C][(N + 1) H] float.  A
-// CTA writes the kFrames - 1 output blocks k = k0 .. k0 + kFrames - 2 of H
-// samples (k <= N), block k being the second half of frame k - 1 plus the
-// first half of frame k: warp w inverts frame m0 + w (m0 = k0 - 1; a missing
-// frame adds nothing).  The spectra arrive as runs of kFrames consecutive
-// frames per bin (coalesced), staged in spec; the windowed halves go to z.
-__global__ void __launch_bounds__(kThreads) k_istft(const float2* __restrict__ in, int N, int ld,
-                                                    float* __restrict__ out) {
+// x [C][S] float -> out [C][F][ld] complex64 (frames 0 .. N-1, then zero to
+// ld).  Persistent: a CTA takes the groups of kFrames frames it = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of the C x ceil(N / kFrames) groups (channel
+// it / G, frames kFrames (it mod G) ..), and copies the next group's samples
+// into the other input stage (cp.async) while it transforms this one; warp
+// w transforms frame w of the group.  VEC: x and S allow 16-byte copies.
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads, 2) k_stft(const float* __restrict__ x, int C, long long S, int N,
+                                                      float2* __restrict__ out, int ld) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  StftSmem& sm = *reinterpret_cast<StftSmem*>(smem_raw);
-  const int c = blockIdx.y;
-  const int k0 = blockIdx.x * (kFrames - 1);
-  const int m0 = k0 - 1;  // frames m0 .. m0 + kFrames - 1
+  StftFwdSmem& sm = *reinterpret_cast<StftFwdSmem*>(smem_raw);
+  const int G = (N + kFrames - 1) / kFrames, items = C * G;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float2* ic = in + (size_t)c * kF * ld;
-  for (int t = threadIdx.x; t < kF * kFrames; t += kThreads) {
-    const int f = t / kFrames, fr = t % kFrames, m = m0 + fr;
-    sm.spec[f][fr] = (m >= 0 && m < N) ? __ldg(ic + (size_t)f * ld + m) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  const int m = m0 + w;
-  const bool on = m >= 0 && m < N;
-  float2 u[16];
-  // Z[k] = E[k] + i O[k] from X[k] and X[512 - k] (bins 0 and L/2 of a real
-  // signal's spectrum are real: their imaginary parts are ignored), conjugated
-  // for the forward transform: IDFT(Z) = conj(DFT(conj Z)) / 512
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int k = lane + 32 * q;
-    float2 xk = sm.spec[k][w];
-    float2 xm = cconj(sm.spec[kM - k][w]);
-    if (k == 0) {
-      xk.y = 0.f;
-      xm.y = 0.f;
+  // copy the samples of group `item` into stage st
+  auto fetch = [&](int item, int st) {
+    const int c = item / G, n0 = (item % G) * kFrames, nf = min(kFrames, N - n0);
+    const float* src = x + (size_t)c * S + (size_t)n0 * kH;
+    const int len = (nf + 1) * kH;  // samples, a multiple of 512
+    if (VEC) {
+      for (int t = threadIdx.x; t < len / 4; t += kThreads) cp_async16(sm.x[st] + 4 * t, src + 4 * t);
+    } else {
+      for (int t = threadIdx.x; t < len; t += kThreads) cp_async4(sm.x[st] + t, src + t);
     }
-    const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
-    const float2 o = cmul(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y - xm.y)), cconj(__ldg(g_tw1024 + k)));
-    u[q] = cconj(make_float2(e.x - o.y, e.y + o.x));
-  }
-  fft512_warp(u, lane, g_tw512);  // lane l: DFT(conj Z) at t = r + 16 rev5(l)
-  float* first = reinterpret_cast<float*>(sm.z);  // [kFrames][kHalfPad]
-  float* second = first + kFrames * kHalfPad;     // [kFrames][kHalfPad]
-  const int base = 16 * rev5(lane);
-  const float sc = 1.0f / kM;
+  };
+  int it = blockIdx.x;
+  if (it >= items) return;
+  float2 tw1[15];
+  lane_twiddles(lane, tw1);
+  const float2 wl = __ldg(g_tw1024 + lane);  // W1024^l
+  fetch(it, 0);
+  cp_async_commit();
+  for (int st = 0; it < items; it += gridDim.x, st ^= 1) {
+    if (it + (int)gridDim.x < items) fetch(it + gridDim.x, st ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this group's copies (all but the newest group) have landed
+    __syncthreads();
+    const int c = it / G, n0 = (it % G) * kFrames, nf = min(kFrames, N - n0);
+    if (w < nf) {
+      const float2* xf = reinterpret_cast<const float2*>(sm.x[st] + w * kH);  // frame n0 + w
+      const float2* win = reinterpret_cast<const float2*>(g_win);
+      float2 u[16];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {  // x(2t) = Re / 512, x(2t+1) = -Im / 512, windowed
-    const int s = 2 * (base + r);
-    const float x0 = on ? __ldg(g_win + s) * u[r].x * sc : 0.f;
-    const float x1 = on ? -__ldg(g_win + s + 1) * u[r].y * sc : 0.f;
-    float* half = s < kH ? first + w * kHalfPad : second + w * kHalfPad;
-    const int sh = s < kH ? s : s - kH;
-    half[spad(sh)] = x0;
-    half[spad(sh + 1)] = x1;
+      for (int q = 0; q < 16; ++q) {  // z(t) = w(2t) x(2t) + i w(2t+1) x(2t+1), t = l + 32 q
+        const int t = lane + 32 * q;
+        const float2 xv = xf[t], wv = __ldg(win + t);
+        u[q] = make_float2(wv.x * xv.x, wv.y * xv.y);
+      }
+      float2* zb = sm.s.buf[w];
+      fft512_warp(u, lane, zb, tw1);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) zb[lane + 32 * j] = u[j];  // Z[k] at k
+      __syncwarp();
+      // X[k] = E + W1024^k O and X[512 - k] = conj(E - W1024^k O), with
+      // E = (Z[k] + conj Z[512-k]) / 2, O = (Z[k] - conj Z[512-k]) / (2i), k = 0 .. 256
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int k = lane + 32 * i;
+        if (i < 8 || k == kM / 2) {
+          const float2 zk = zb[k];
+          const float2 zm = cconj(zb[(kM - k) & (kM - 1)]);
+          const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
+          const float2 o = mul_mi(make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y - zm.y)));
+          const float2 t = cmul(cmul(wl, c_w32[i]), o);  // W1024^k = W1024^l W32^i
+          sm.s.spec[k][w ^ swz(k)] = cadd(e, t);
+          if (k < kM / 2) sm.s.spec[kL / 2 - k][w ^ swz(kL / 2 - k)] = cconj(csub(e, t));
+        }
+      }
+    }
+    __syncthreads();
+    // runs of consecutive frames per bin, two frames per 16-byte store
+    float2* oc = out + (size_t)c * kF * ld;
+    {
+      // thread t stores frames n, n + 1 (n = 2 (t mod 4)) of the bins f0 + 64 i (f0 = t / 4); swz(f0 + 64 i) = swz(f0)
+      constexpr int kPairs = kFrames / 2, kRows = kThreads / kPairs;
+      const int n = 2 * (threadIdx.x % kPairs), f0 = threadIdx.x / kPairs, sw = swz(f0);
+      const float4* srow = reinterpret_cast<const float4*>(&sm.s.spec[f0][(n ^ sw) & ~1]);
+      float2* dst = oc + (size_t)f0 * ld + n0 + n;
+      if (n < nf) {
+#pragma unroll
+        for (int i = 0; i < (kF + kRows - 1) / kRows; ++i) {
+          if (f0 + i * kRows < kF) {
+            const float4 v = srow[i * kRows * kFrames / 2];
+            const float2 a = (sw & 1) ? make_float2(v.z, v.w) : make_float2(v.x, v.y);   // frame n
+            const float2 b2 = (sw & 1) ? make_float2(v.x, v.y) : make_float2(v.z, v.w);  // frame n + 1
+            if (n + 1 < nf) *reinterpret_cast<float4*>(dst) = make_float4(a.x, a.y, b2.x, b2.y);
+            else *dst = a;
+          }
+          dst += (size_t)kRows * ld;
+        }
+      }
+    }
+    // padding frames N .. ld - 1 of each row: written with the channel's last group
+    if (n0 + kFrames >= N) {
+      const int pad = ld - N;
+      for (int t = threadIdx.x; t < kF * pad; t += kThreads) {
+        const int f = t / pad, n = N + t % pad;
+        oc[(size_t)f * ld + n] = make_float2(0.f, 0.f);
+      }
+    }
   }
-  __syncthreads();
-  // samples k H + u: second half of frame k - 1 (local k - k0) + first half of frame k (local k - k0 + 1)
-  float* oc = out + (size_t)c * ((size_t)N + 1) * kH;
-  const int nk = min(kFrames - 1, N + 1 - k0);
-  for (int t = threadIdx.x; t < nk * kH; t += kThreads) {
-    const int kk = t / kH, uu = t % kH;
-    oc[(size_t)(k0 + kk) * kH + uu] = second[kk * kHalfPad + spad(uu)] + first[(kk + 1) * kHalfPad + spad(uu)];
+  cp_async_wait<0>();
+}
+
+// in [C][F][ld] complex64 (frames 0 .. N-1) -> out [C][(N + 1) H] float.
+// Persistent over the C x ceil((N + 1) / (kFrames - 1)) groups of output
+// blocks: group b of channel c writes the kFrames - 1 blocks k = k0 ..
+// k0 + kFrames - 2 of H samples (k0 = (kFrames - 1) b, k <= N), block k
+// being the second half of frame k - 1 plus the first half of frame k; warp
+// w inverts frame m0 + w (m0 = k0 - 1; a missing frame adds nothing).  The
+// next group's spectra (runs of kFrames frames per bin) are copied into the
+// other input stage (cp.async, zeros for missing frames) while this group is
+// transformed; each warp leaves its frame's windowed halves in its buffer.
+// VEC: out allows 16-byte stores.
+struct StftInvSmem {
+  float2 buf[kFrames][kBuf];
+  float2 in[2][kF][kFrames];  // swizzled rows, as the forward's spectra
+};
+
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads, 2) k_istft(const float2* __restrict__ in, int C, int N, int ld,
+                                                       float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  StftInvSmem& sm = *reinterpret_cast<StftInvSmem*>(smem_raw);
+  const int B = (N + 1 + kFrames - 2) / (kFrames - 1), items = C * B;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto fetch = [&](int item, int st) {
+    const int c = item / B, m0 = (item % B) * (kFrames - 1) - 1;
+    const float2* ic = in + (size_t)c * kF * ld;
+    // thread t copies frame fr = t mod 8 of the bins f0 + 32 i (f0 = t / 8); swz(f0 + 32 i) = swz(f0)
+    const int fr = threadIdx.x % kFrames, f0 = threadIdx.x / kFrames, m = m0 + fr;
+    const bool ok = m >= 0 && m < N;
+    const float2* src = ok ? ic + (size_t)f0 * ld + m : ic;
+    const size_t step = ok ? (size_t)(kThreads / kFrames) * ld : 0;
+    float2* dst = &sm.in[st][f0][fr ^ swz(f0)];
+#pragma unroll
+    for (int i = 0; i < (kF + kThreads / kFrames - 1) / (kThreads / kFrames); ++i) {
+      if (f0 + i * (kThreads / kFrames) < kF) cp_async8z(dst, src, ok);
+      src += step;
+      dst += (kThreads / kFrames) * kFrames;
+    }
+  };
+  int it = blockIdx.x;
+  if (it >= items) return;
+  float2 tw1[15];
+  lane_twiddles(lane, tw1);
+  const float2 wl = __ldg(g_tw1024 + lane);  // W1024^l
+  fetch(it, 0);
+  cp_async_commit();
+  const float2* win = reinterpret_cast<const float2*>(g_win);
+  const float sc = 1.0f / kM;
+  for (int st = 0; it < items; it += gridDim.x, st ^= 1) {
+    if (it + (int)gridDim.x < items) fetch(it + gridDim.x, st ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const int c = it / B, k0 = (it % B) * (kFrames - 1), m = k0 - 1 + w;
+    const bool on = m >= 0 && m < N;
+    float2 u[16];
+    // Z[k] = E[k] + i O[k] from X[k] and X[512 - k] (bins 0 and L/2 of a real
+    // signal's spectrum are real: their imaginary parts are ignored), conjugated
+    // for the forward transform: IDFT(Z) = conj(DFT(conj Z)) / 512
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int k = lane + 32 * q;
+      float2 xk = sm.in[st][k][w ^ swz(k)];
+      float2 xm = cconj(sm.in[st][kM - k][w ^ swz(kM - k)]);
+      if (k == 0) {
+        xk.y = 0.f;
+        xm.y = 0.f;
+      }
+      const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
+      const float2 o = cmul(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y - xm.y)), cconj(cmul(wl, c_w32[q])));
+      u[q] = cconj(make_float2(e.x - o.y, e.y + o.x));
+    }
+    fft512_warp(u, lane, sm.buf[w], tw1);  // lane l: DFT(conj Z) at t = l + 32 j in u[j]
+    float2* half = sm.buf[w];                  // the frame's 1024 windowed samples, as pairs
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {  // x(2t) = Re / 512, x(2t+1) = -Im / 512, windowed
+      const int t = lane + 32 * j;
+      const float2 wv = __ldg(win + t);
+      half[t] = on ? make_float2(wv.x * u[j].x * sc, -wv.y * u[j].y * sc) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // samples k H + s: second half of frame k - 1 (local k - k0) + first half of frame k (local k - k0 + 1)
+    float* oc = out + (size_t)c * ((size_t)N + 1) * kH;
+    const int nk = min(kFrames - 1, N + 1 - k0);
+    if (VEC) {
+      for (int t = threadIdx.x; t < nk * (kH / 4); t += kThreads) {
+        const int kk = t / (kH / 4), s4 = t % (kH / 4);
+        const float4 a = reinterpret_cast<const float4*>(sm.buf[kk])[kH / 4 + s4];
+        const float4 b2 = reinterpret_cast<const float4*>(sm.buf[kk + 1])[s4];
+        reinterpret_cast<float4*>(oc + (size_t)(k0 + kk) * kH)[s4] =
+            make_float4(a.x + b2.x, a.y + b2.y, a.z + b2.z, a.w + b2.w);
+      }
+    } else {
+      for (int t = threadIdx.x; t < nk * kH; t += kThreads) {
+        const int kk = t / kH, s1 = t % kH;
+        oc[(size_t)(k0 + kk) * kH + s1] =
+            reinterpret_cast<const float*>(sm.buf[kk])[kH + s1] + reinterpret_cast<const float*>(sm.buf[kk + 1])[s1];
+      }
+    }
   }
+  cp_async_wait<0>();
+}
+
+// Persistent grid: as many CTAs as are resident at once, at most one per work item.
+template <typename K>
+int resident_grid(K kernel, size_t smem, long long items) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, smem) != cudaSuccess || per < 1)
+    return 0;
+  return (int)std::min<long long>(items, (long long)sms * per);
 }
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
@@ -286,32 +440,39 @@ ffca_status ffca_stft(const float* x, int C, long long S, void* out, int ld, voi
   if (Nl > (1 << 30)) return FFCA_ERR_ARG;
   const int N = (int)Nl;
   if (C == 0 || N == 0) return FFCA_OK;
+  const long long items = (long long)C * ((N + kFrames - 1) / kFrames);
   if (ld < N || (ld % 4) != 0 || !x || !out || (reinterpret_cast<uintptr_t>(out) % 16) != 0 ||
-      (reinterpret_cast<uintptr_t>(x) % 4) != 0 || C > 65535)
+      (reinterpret_cast<uintptr_t>(x) % 4) != 0 || C > 65535 || items > INT32_MAX / 2)
     return FFCA_ERR_ARG;
   ffca_status st = ensure_tables();
   if (st != FFCA_OK) return st;
-  const size_t smem = sizeof(StftSmem);
-  if (cudaFuncSetAttribute(k_stft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  const size_t smem = sizeof(StftFwdSmem);
+  const bool vec = (reinterpret_cast<uintptr_t>(x) % 16) == 0 && (S % 4) == 0;
+  auto kern = vec ? k_stft<true> : k_stft<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return FFCA_ERR_CUDA;
-  const dim3 grid((N + kFrames - 1) / kFrames, C);
-  k_stft<<<grid, kThreads, smem, as_stream(stream)>>>(x, S, N, static_cast<float2*>(out), ld);
+  const int grid = resident_grid(kern, smem, items);
+  if (grid < 1) return FFCA_ERR_CUDA;
+  kern<<<grid, kThreads, smem, as_stream(stream)>>>(x, C, S, N, static_cast<float2*>(out), ld);
   return cudaGetLastError() == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
 }
 
 ffca_status ffca_istft(const void* in, int C, int N, int ld, float* out, void* stream) {
   if (C < 0 || N < 0 || ld < 0) return FFCA_ERR_ARG;
   if (C == 0 || N == 0) return FFCA_OK;
+  const long long items = (long long)C * ((N + 1 + kFrames - 2) / (kFrames - 1));
   if (ld < N || !in || !out || (reinterpret_cast<uintptr_t>(in) % 16) != 0 ||
-      (reinterpret_cast<uintptr_t>(out) % 4) != 0 || C > 65535 || N > (1 << 30) - 2)
+      (reinterpret_cast<uintptr_t>(out) % 4) != 0 || C > 65535 || N > (1 << 30) - 2 || items > INT32_MAX / 2)
     return FFCA_ERR_ARG;
   ffca_status st = ensure_tables();
   if (st != FFCA_OK) return st;
-  const size_t smem = sizeof(StftSmem);
-  if (cudaFuncSetAttribute(k_istft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  const size_t smem = sizeof(StftInvSmem);
+  auto kern = (reinterpret_cast<uintptr_t>(out) % 16) == 0 ? k_istft<true> : k_istft<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return FFCA_ERR_CUDA;
-  const dim3 grid((N + 1 + kFrames - 2) / (kFrames - 1), C);
-  k_istft<<<grid, kThreads, smem, as_stream(stream)>>>(static_cast<const float2*>(in), N, ld, out);
+  const int grid = resident_grid(kern, smem, items);
+  if (grid < 1) return FFCA_ERR_CUDA;
+  kern<<<grid, kThreads, smem, as_stream(stream)>>>(static_cast<const float2*>(in), C, N, ld, out);
   return cudaGetLastError() == cudaSuccess ? FFCA_OK : FFCA_ERR_CUDA;
 }
 

@@ -581,6 +581,31 @@ __device__ inline D1 vfma(D1 a, D1 b, D1 c) { return {fma(a.v, b.v, c.v)}; }
 __device__ inline D1 vrcp(D1 x) { return {1.0 / x.v}; }
 __device__ inline D1 vlog2(D1 x) { return {log2(x.v)}; }
 
+// sum_i log2 sigma_i of one point.  FP32 lanes take one hardware log2 per
+// sigma; FP64 takes the one log2 of the product of the sigmas' mantissas
+// (each in [1/2, 1), so that the product of up to eight neither overflows
+// nor underflows) plus the sum of their binary exponents: one software
+// logarithm per point instead of I.
+template <typename L>
+struct Log2Sum;
+template <>
+struct Log2Sum<F2> {
+  F2 s = {make_float2(0.f, 0.f)};
+  __device__ inline void add(F2 x) { s = s + vlog2(x); }
+  __device__ inline F2 value() const { return s; }
+};
+template <>
+struct Log2Sum<D1> {
+  double m = 1.0;
+  int e = 0;
+  __device__ inline void add(D1 x) {
+    int k;
+    m *= frexp(x.v, &k);
+    e += k;
+  }
+  __device__ inline D1 value() const { return {log2(m) + (double)e}; }
+};
+
 template <typename T>
 struct Lane;
 template <>
@@ -784,7 +809,8 @@ __global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : 
         const bool full = n0 + FU <= Np;
         L r[I], e2[I];
         L ztr[EM ? I : 1], zti[EM ? I : 1];  // EM: z_i = r_i y~_i
-        L quad = LN::bc(0), lg = LN::bc(0);
+        L quad = LN::bc(0);
+        Log2Sum<L> lgs;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
           // y~_i = sum_m conj(P_mi) y_m: re = Pr yr + Pi yi, im = Pr yi - Pi yr
@@ -807,12 +833,13 @@ __global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : 
           r[i] = vrcp(sg);
           e2[i] = vfma(tr, tr, ti * ti);
           quad = vfma(e2[i], r[i], quad);
-          lg = lg + vlog2(sg);
+          lgs.add(sg);
           if constexpr (EM) {
             ztr[i] = r[i] * tr;
             zti[i] = r[i] * ti;
           }
         }
+        const L lg = lgs.value();
         if (full) {
           ACC(NA, quad);
           ACC(NA + 1, lg);

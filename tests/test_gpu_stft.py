@@ -90,6 +90,40 @@ def test_round_trip_and_benchmark_length():
         assert _relerr_bins(got, ref) <= TOL
 
 
+def test_persistent_loop_and_unaligned_buffers():
+    """More groups of frames than resident CTAs (several per CTA, each
+    CTA's next group copied while it transforms one), with a signal that
+    starts 4 bytes past a 16-byte boundary and an odd length (4-byte
+    copies), and an inverse written 4 bytes past a 16-byte boundary
+    (scalar stores), against the oracle."""
+    import ctypes
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    C, N = 2, 3001
+    S = (N - 1) * so.H + so.L + 3
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((C, S)).astype(np.float32)
+    flat = torch.zeros(C * S + 1, dtype=torch.float32, device="cuda")
+    flat[1:] = torch.from_numpy(x.ravel()).cuda()
+    xd = flat[1:].view(C, S)
+    X, Ng = ffca.stft(xd)
+    torch.cuda.synchronize()
+    assert Ng == N
+    Xg = X.cpu().numpy()
+    for n in (0, 1, 8, 1500, N - 2, N - 1):
+        seg = x[:, n * so.H: n * so.H + so.L].astype(np.float64) * so.window()[None]
+        assert _relerr_bins(Xg[:, :, n], np.fft.rfft(seg, axis=-1)) <= TOL
+    assert np.all(Xg[:, :, N:] == 0)
+    out = torch.full((C * (N + 1) * so.H + 1,), float("nan"), dtype=torch.float32, device="cuda")
+    L = ffca.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.ffca_istft(X.data_ptr(), C, N, X.shape[2], ctypes.c_void_p(out.data_ptr() + 4), s) == 0
+    torch.cuda.synchronize()
+    y = out[1:].view(C, -1).cpu().numpy()
+    ref = so.istft(Xg[:, :, :N].astype(np.complex128))
+    assert float(np.max(np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1))) <= TOL
+
+
 def test_bad_arguments_are_rejected():
     import torch
     from paper_1805_09498_gb300 import ffca
