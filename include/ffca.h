@@ -48,9 +48,9 @@
  *    each (pass A for I <= 4, pass B for I <= 3, the normal EM's pass when
  *    J I^2 + 2 <= 32); elsewhere (pass B at I = 4, both passes at I = 8, the
  *    normal EM's pass with more sums) a thread's plain FP32 sum is flushed
- *    into the FP64 partial sums every 64 (pass B at I = 8: 128) units of two
- *    frames, so that no FP32 sum runs over more frames than that however long
- *    the mixture is.  The 32 lanes
+ *    into the FP64 partial sums every 64 (pass B and the normal EM's pass at
+ *    I = 8: 128) units of two frames, so that no FP32 sum runs over more
+ *    frames than that however long the mixture is.  The 32 lanes
  *    of a warp are then summed by a five-level pairwise tree in FP32, the
  *    warps' sums in double-float (TwoSum), and the partial sums in FP64.
  *
@@ -166,8 +166,9 @@ ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
  * Lambda of Eqs. updatev / Lambdaupdate), K sweeps of it per iteration.  Its
  * sums come from pass A, so an iteration streams y and v once (no pass B);
  * it counts (I+1) F K inversions per iteration like the fixed point, ignores
- * mu and guarantees an L2 that does not decrease (an EM step).  Compiled for
- * I <= 4 (FFCA_ERR_UNSUPPORTED at I = 8). */
+ * mu and guarantees an L2 that does not decrease (an EM step).  At I = 8
+ * each unit of the pass is shared by eight threads (the 336 sums of T_j's
+ * off-diagonal entries at J = 6 split over them). */
 /* FFCA_P_NEWTON is Newton's method on L2 with the V_i of Eq. FPI held fixed
  * (Sec. 4.6 names it), in the 2 I^2 real coordinates of P, off the I
  * directions p_i -> e^{i t} p_i along which L2 does not change: K steps of

@@ -86,20 +86,25 @@ FFCA_DECLARE_TABLE(1, 4)
 FFCA_DECLARE_TABLE(1, 8)
 #undef FFCA_DECLARE_TABLE
 
-// The normal EM and Newton kernels of one precision and I <= 4 (compiled in
-// their own translation units).
-#define FFCA_DECLARE_ALT(P, I) \
+// The normal EM kernels of one precision (I <= 4 and 8) and the Newton
+// kernels (I <= 4), compiled in translation units of their own.
+#define FFCA_DECLARE_EM(P, I) \
   const void* em_estep_p##P##_i##I(int J); \
-  const void* em_psolve_p##P##_i##I(int J); \
+  const void* em_psolve_p##P##_i##I(int J);
+#define FFCA_DECLARE_ALT(P, I) \
+  FFCA_DECLARE_EM(P, I) \
   const void* newton_p##P##_i##I(int J);
 FFCA_DECLARE_ALT(0, 1)
 FFCA_DECLARE_ALT(0, 2)
 FFCA_DECLARE_ALT(0, 3)
 FFCA_DECLARE_ALT(0, 4)
+FFCA_DECLARE_EM(0, 8)
 FFCA_DECLARE_ALT(1, 1)
 FFCA_DECLARE_ALT(1, 2)
 FFCA_DECLARE_ALT(1, 3)
 FFCA_DECLARE_ALT(1, 4)
+FFCA_DECLARE_EM(1, 8)
 #undef FFCA_DECLARE_ALT
+#undef FFCA_DECLARE_EM
 
 }  // namespace ffca

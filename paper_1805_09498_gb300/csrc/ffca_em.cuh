@@ -20,8 +20,10 @@
 // T_j[a][b] = I lambda_ja lambda_jb sum_n u_j z_a conj(z_b) (old Lambda).
 //
 //   k_psolve_em  one warp per 32 / I problems, lane (g, i) owning column i
-//                of problem g: the slot sums (the whole warp, through shared
-//                memory), the new Lambda and the problem's L2 of the
+//                of problem g (I = 8: the entering P and both Lambdas in the
+//                problem's shared record, not in registers): the slot sums
+//                (the whole warp, through shared memory), the new Lambda and
+//                the problem's L2 of the
 //                entering state (the work pass B's producer does in the
 //                fixed-point iteration), Omega_i = L D L^H, the K sweeps, then
 //                P^{-H} and ln|det P|^2 of the new P; with a trace, the last
@@ -39,7 +41,11 @@ struct EmShape {
   static constexpr int NV = NA + 2 + 2 * J * NPAIR;  // + the two L2 sums, + (re, im) per j and pair
   static constexpr int G = 32 / I;                 // problems per warp
   static constexpr int NL = NPAIR > 0 ? NPAIR : 1; // storage of the strictly lower entries
-  static constexpr int SMEM = BigLane<I>::SMEM + G * NV * (int)sizeof(double);
+  // I > 4: the entering P and both Lambdas of each problem in shared memory
+  // (as registers they would take more than a lane holds)
+  static constexpr bool BIG = I > 4;
+  static constexpr int PSM = BIG ? G * (I * I * 2 + 2 * J * I) : 0;  // doubles
+  static constexpr int SMEM = BigLane<I>::SMEM + G * NV * (int)sizeof(double) + PSM * (int)sizeof(double);
 };
 
 template <typename T, int I, int J>
@@ -60,8 +66,8 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
   // the slot sums of the block's problems (slot order), spread over the
   // whole warp: lane l takes the values l + 32 c of the flattened [G][NV]
   // sums and issues its loads of one slot together
-  {
-    constexpr int PER = (G * NV + 31) / 32;
+  constexpr int PER = (G * NV + 31) / 32;
+  if constexpr (PER <= 16) {
     const double* src[PER];
     int ns[PER];
     double acc[PER];
@@ -83,21 +89,78 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
 #pragma unroll
     for (int c = 0; c < PER; ++c)
       if (lane + 32 * c < G * NV) sums[lane + 32 * c] = acc[c];
-  }
-  // the entering P (all columns) and Lambda of this lane's problem
-  cpx<double> P0[I][I];
+  } else {  // I > 4: eight values of a lane at a time
+    constexpr int CH = 8;
+    for (int c0 = 0; c0 < PER; c0 += CH) {
+      const double* src[CH];
+      int ns[CH];
+      double acc[CH];
+      int nsmax = 0;
 #pragma unroll
-  for (int r = 0; r < I; ++r)
+      for (int c = 0; c < CH; ++c) {
+        const int x = lane + 32 * (c0 + c);
+        const int ff = blockIdx.x * G + x / NV;
+        const bool ok = c0 + c < PER && x < G * NV && ff < a.F;
+        ns[c] = ok ? pt.nslots(ff) : 0;
+        src[c] = a.part_buf + ((size_t)(ok ? ff : 0) * pt.max_slots) * NV + (ok ? x % NV : 0);
+        acc[c] = 0.0;
+        nsmax = max(nsmax, ns[c]);
+      }
+      for (int k = 0; k < nsmax; ++k)
 #pragma unroll
-    for (int c = 0; c < I; ++c) {
-      const double2 q = __ldcg(reinterpret_cast<const double2*>(a.P) + (size_t)f * I * I + r * I + c);
-      P0[r][c] = mk(q.x, q.y);
+        for (int c = 0; c < CH; ++c)
+          if (k < ns[c]) acc[c] += __ldcg(src[c] + (size_t)k * NV);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int x = lane + 32 * (c0 + c);
+        if (c0 + c < PER && x < G * NV) sums[x] = acc[c];
+      }
     }
-  double lold[J][I];
+  }
+  // the entering P (all columns) and Lambda of this lane's problem: in
+  // registers for I <= 4, else in the problem's shared record (each lane
+  // loads its column)
+  constexpr bool BIG = ES::BIG;
+  constexpr int RP = BIG ? 1 : I, RJ = BIG ? 1 : J;
+  constexpr int REC = I * I * 2 + 2 * J * I;  // doubles of a problem's record: P, old Lambda, new Lambda
+  double* rec = reinterpret_cast<double*>(em_smem + BigLane<I>::SMEM + G * NV * sizeof(double)) +
+                (size_t)(g < G ? g : 0) * REC;
+  cpx<double> P0r[RP][RP];
+  double lold_r[RJ][RP], lnew_r[RJ][RP];
+  if constexpr (BIG) {
+    if (g < G) {
 #pragma unroll
-  for (int j = 0; j < J; ++j)
+      for (int r = 0; r < I; ++r) {
+        const double2 q = __ldcg(reinterpret_cast<const double2*>(a.P) + (size_t)f * I * I + r * I + i);
+        rec[2 * (r * I + i)] = q.x;
+        rec[2 * (r * I + i) + 1] = q.y;
+      }
 #pragma unroll
-    for (int c = 0; c < I; ++c) lold[j][c] = __ldcg(a.lam + (size_t)f * J * I + j * I + c);
+      for (int j = 0; j < J; ++j) rec[2 * I * I + j * I + i] = __ldcg(a.lam + (size_t)f * J * I + j * I + i);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < I; ++r)
+#pragma unroll
+      for (int c = 0; c < I; ++c) {
+        const double2 q = __ldcg(reinterpret_cast<const double2*>(a.P) + (size_t)f * I * I + r * I + c);
+        P0r[r][c] = mk(q.x, q.y);
+      }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int c = 0; c < I; ++c) lold_r[j][c] = __ldcg(a.lam + (size_t)f * J * I + j * I + c);
+  }
+  auto P0 = [&](int r, int c) -> cpx<double> {
+    if constexpr (BIG) return mk(rec[2 * (r * I + c)], rec[2 * (r * I + c) + 1]);
+    else return P0r[r][c];
+  };
+  auto LOLD = [&](int j, int c) -> double {
+    if constexpr (BIG) return rec[2 * I * I + j * I + c]; else return lold_r[j][c];
+  };
+  auto LNEW = [&](int j, int c) -> double {
+    if constexpr (BIG) return rec[2 * I * I + J * I + j * I + c]; else return lnew_r[j][c];
+  };
   const double logdet_old = __ldcg(a.logdet + f);
   __syncwarp();  // sums complete; every lane has read P and Lambda before any lane writes them
   const double* tot = sums + (size_t)(g < G ? g : 0) * NV;
@@ -105,15 +168,24 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
   const double nd = (double)n;
 
   // the new Lambda (Eq. Lambdaupdate: lambda_ja I sum_n t_ja / s_j / N)
-  double lnew[J][I];
   bool bad = false;
+  if constexpr (BIG) {  // column i by this lane
 #pragma unroll
-  for (int j = 0; j < J; ++j)
-#pragma unroll
-    for (int c = 0; c < I; ++c) {
-      lnew[j][c] = lold[j][c] * ((double)I * pt.inv_n(f)) * tot[j * I + c];
-      bad |= !(lnew[j][c] > 0.0) || !isfinite(lnew[j][c]);
+    for (int j = 0; j < J; ++j) {
+      const double l = LOLD(j, i) * ((double)I * pt.inv_n(f)) * tot[j * I + i];
+      bad |= !(l > 0.0) || !isfinite(l);
+      if (g < G) rec[2 * I * I + J * I + j * I + i] = l;
     }
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+      for (int c = 0; c < I; ++c) {
+        lnew_r[j][c] = LOLD(j, c) * ((double)I * pt.inv_n(f)) * tot[j * I + c];
+        bad |= !(lnew_r[j][c] > 0.0) || !isfinite(lnew_r[j][c]);
+      }
+  }
   // L2 of the entering state (Eq. L2)
   const double lf = -(double)I * nd * kLnPi + nd * logdet_old - tot[NA] - 0.69314718055994530942 * tot[NA + 1];
   bad |= !isfinite(lf);
@@ -125,10 +197,15 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
   double rl[J];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
-    double lji = lnew[j][0];
+    double lji;
+    if constexpr (BIG) {
+      lji = LNEW(j, i);
+    } else {
+      lji = LNEW(j, 0);
 #pragma unroll
-    for (int c = 1; c < I; ++c)
-      if (c == i) lji = lnew[j][c];
+      for (int c = 1; c < I; ++c)
+        if (c == i) lji = LNEW(j, c);
+    }
     rl[j] = 1.0 / lji;
   }
   double dv[I], d0[I], rd[I];
@@ -137,7 +214,7 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
   for (int c = 0; c < I; ++c) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < J; ++j) s = fma(nd * lnew[j][c], rl[j], s);
+    for (int j = 0; j < J; ++j) s = fma(nd * LNEW(j, c), rl[j], s);
     dv[c] = s;
     d0[c] = s;
   }
@@ -150,7 +227,7 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
         cpx<double> s = mk(0.0, 0.0);
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-          const double w = (double)I * lold[j][aa] * lold[j][bb] * rl[j];
+          const double w = (double)I * LOLD(j, aa) * LOLD(j, bb) * rl[j];
           const double* t = tot + NA + 2 + 2 * (j * NPAIR + pq);
           s.re = fma(w, t[0], s.re);
           s.im = fma(w, t[1], s.im);
@@ -177,10 +254,15 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-      double l = lnew[j][0];
+      double l;
+      if constexpr (BIG) {
+        l = LNEW(j, i);
+      } else {
+        l = LNEW(j, 0);
 #pragma unroll
-      for (int c = 1; c < I; ++c)
-        if (c == i) l = lnew[j][c];
+        for (int c = 1; c < I; ++c)
+          if (c == i) l = LNEW(j, c);
+      }
       a.lam[(size_t)f * J * I + j * I + i] = l;
       ta->set_lam(j, i, (T)l);
     }
@@ -205,7 +287,7 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
       for (int c = 0; c < I; ++c) {  // x = P^H q with the entering P
         cpx<double> s = mk(0.0, 0.0);
 #pragma unroll
-        for (int r = 0; r < I; ++r) cfmac(s, P0[r][c], q[r]);
+        for (int r = 0; r < I; ++r) cfmac(s, P0(r, c), q[r]);
         x[c] = s;
       }
     }
@@ -218,7 +300,7 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
     for (int r = 0; r < I; ++r) {  // column i = J N P x
       cpx<double> s = mk(0.0, 0.0);
 #pragma unroll
-      for (int c = 0; c < I; ++c) cfma(s, P0[r][c], x[c]);
+      for (int c = 0; c < I; ++c) cfma(s, P0(r, c), x[c]);
       col[r] = cscale(s, jn);
     }
   }

@@ -69,16 +69,16 @@ static const FastKernels* table_entry() {
   int em_smem = 0, em_solve_smem = 0, em_nv = 0, em_groups = 1;
   const void* resident = nullptr;
   int res_bpf = 0, res_max = 0;
-#if FFCA_I <= 4
-  resident = (const void*)k_resident<Real, FFCA_I, J>;
-  res_bpf = ResShape<Real, FFCA_I, J>::BYTES_PER_FRAME;
-  res_max = ResShape<Real, FFCA_I, J>::max_frames();
   estep_em = FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(J);
   psolve_em = FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(J);
   em_groups = EmGroups<Real, FFCA_I, J>::value;
   em_smem = em_groups * Tile<Real, FFCA_I, J, EmGroups<Real, FFCA_I, J>::value>::GROUP;
   em_solve_smem = EmShape<FFCA_I, J>::SMEM;
   em_nv = EmShape<FFCA_I, J>::NV;
+#if FFCA_I <= 4
+  resident = (const void*)k_resident<Real, FFCA_I, J>;
+  res_bpf = ResShape<Real, FFCA_I, J>::BYTES_PER_FRAME;
+  res_max = ResShape<Real, FFCA_I, J>::max_frames();
   pnewton = FFCA_CAT(newton_p, FFCA_PREC, _i, FFCA_I)(J);
 #endif
   static const FastKernels k = {
@@ -211,7 +211,11 @@ const AdjKernels* FFCA_CAT(adj_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
 #if FFCA_PART == 3
 template <int J>
 static const void* em_pair(bool step) {
+#if FFCA_I > 4
+  return step ? (const void*)k_psolve_em<Real, FFCA_I, J> : (const void*)k_estep_em_big<Real, FFCA_I, J>;
+#else
   return step ? (const void*)k_psolve_em<Real, FFCA_I, J> : (const void*)k_estep<Real, FFCA_I, J, true, true>;
+#endif
 }
 static const void* em_select(int J, bool step) {
   switch (J) {

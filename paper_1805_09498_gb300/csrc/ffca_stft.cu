@@ -82,12 +82,17 @@ __device__ inline float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ inline float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
 
 // 4-point DFT (forward: e^{-2 pi i q r / 4}).
+// The sums and differences of whole complex values as paired FP32
+// operations (one f32x2 instruction each); the -i rotation of the odd
+// outputs in plain FP32.
+__device__ inline float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ inline float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ inline void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_mi(csub(a1, a3));
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  const float2 t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3), d = psub(a1, a3);
+  a0 = padd(t0, t2);
+  a2 = psub(t0, t2);
+  a1 = make_float2(t1.x + d.y, t1.y - d.x);  // t1 + (-i) d
+  a3 = make_float2(t1.x - d.y, t1.y + d.x);  // t1 - (-i) d
 }
 
 // 16-point DFT of u[0..15] in registers (forward): with n = 4 n1 + n2 and
@@ -149,7 +154,7 @@ __device__ inline void fft512_warp(float2 (&u)[16], int lane, float2* __restrict
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
     const float2 p = buf[m * kBufPitch + r], q = buf[(m + 16) * kBufPitch + r];
-    u[m] = make_float2(fmaf(sgn, q.x, p.x), fmaf(sgn, q.y, p.y));
+    u[m] = __ffma2_rn(make_float2(sgn, sgn), q, p);
   }
 #pragma unroll
   for (int m = 1; m < 16; ++m) {  // W32^(m g)

@@ -643,6 +643,321 @@ struct Lane<double> {
   __device__ static double hsum(L x) { return x.v; }
 };
 
+// -------------------------------------------------------------- shuffles of frame lanes
+__device__ inline F2 shfl_xor_l(F2 x, int off) {
+  return {make_float2(__shfl_xor_sync(0xffffffffu, x.v.x, off), __shfl_xor_sync(0xffffffffu, x.v.y, off))};
+}
+__device__ inline D1 shfl_xor_l(D1 x, int off) { return {__shfl_xor_sync(0xffffffffu, x.v, off)}; }
+__device__ inline F2 shfl_l(F2 x, int src) {
+  return {make_float2(__shfl_sync(0xffffffffu, x.v.x, src), __shfl_sync(0xffffffffu, x.v.y, src))};
+}
+__device__ inline D1 shfl_l(D1 x, int src) { return {__shfl_sync(0xffffffffu, x.v, src)}; }
+__device__ inline float lane_of(F2 x, int fr) { return fr == 0 ? x.v.x : x.v.y; }
+__device__ inline double lane_of(D1 x, int) { return x.v; }
+
+// -------------------------------------------------------------- pass A, EM form, I > 4
+// The normal EM update of P (Sec. 4.6) needs, beyond pass A's sums, the
+// J I (I - 1) sums u_j z_a conj(z_b) (a < b; z_a = r_a y~_a, u_j = v_j / s_j,
+// as in k_estep) per point: 336 at I = 8, J = 6, more than one thread holds.
+// So each unit is shared by I threads, as in pass B's I > 4 form: thread e
+// of a unit forms y~_e = sum_m conj(P_me) y_m, sigma_e, r_e and t_je
+// (Eq. updatev's terms of i = e); the unit's threads add t_je over e by a
+// butterfly (s_j in every lane); thread e < J writes v_e^new; each thread
+// keeps the Lambda sums of its column e (sum_n t_je / s_j), the L2 terms of
+// i = e, and the EM sums of the pairs p = SL e .. SL e + SL - 1 (row order
+// over a < b; thread I - 1 none), taking z_a and z_b of a pair from their
+// lanes by shuffles.  The slot holds the I <= 4 form's layout: the Lambda
+// sums, the two L2 sums, then (re, im) per j and pair.
+template <int I, int J>
+struct EmBig {
+  static constexpr int PAIRS = I * (I - 1) / 2;
+  static constexpr int SL = (PAIRS + I - 1) / I;      // pair slots per thread (4 at I = 8)
+  static constexpr int NVT = J + 2 + 2 * J * SL;      // values per thread
+  static constexpr int NA = J * I;
+  static constexpr int NV = NA + 2 + 2 * J * PAIRS;   // values per slot
+  // row and column of pair p (row order over a < b)
+  __device__ static void decode(int p, int& ra, int& cb) {
+    ra = 0;
+    int q = p;
+    while (q >= I - 1 - ra) {
+      q -= I - 1 - ra;
+      ++ra;
+    }
+    cb = ra + 1 + q;
+  }
+  // slot index of thread e's value v, or -1 (an unused pair slot; the L2
+  // parts of the threads e > 0, which the reduction leaves in thread 0)
+  __device__ static int out_index(int e, int v) {
+    if (v < J) return v * I + e;
+    if (v < J + 2) return e == 0 ? NA + (v - J) : -1;
+    const int w = v - J - 2, k = w / (2 * J), j = (w % (2 * J)) / 2, comp = w % 2;
+    const int p = SL * e + k;
+    return p < PAIRS ? NA + 2 + 2 * (j * PAIRS + p) + comp : -1;
+  }
+};
+
+template <typename T, int I, int J, typename Red, int S, int G>
+__device__ void estep_consume_big_em(const FastArgs& a, const Pipe<S>& pp, long long u0, long long u1,
+                                     const Role& rl, volatile int* abort, typename Red::Smem& red) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  using LN = Lane<T>;
+  using L = typename LN::L;
+  using TC = Tile<T, I, J, G>;
+  using PA = ParamsA<T, I, J>;
+  using EB = EmBig<I, J>;
+  using T2 = std::conditional_t<sizeof(T) == 4, float2, double2>;
+  constexpr int FU = Vec<T>::FU;
+  constexpr int SL = EB::SL, NVT = EB::NVT;
+  constexpr int IG = kConsumers / I;  // units in flight per group
+  static_assert(kConsumers % I == 0 && 32 % I == 0 && J <= I, "I must divide the consumer count and the warp");
+  const Partition& pt = a.part;
+  const int tid = rl.ctid, lane = threadIdx.x & 31;
+  const int e = tid % I, ul = tid / I;
+  const int gl = lane & ~(I - 1);  // first lane of this unit's I threads
+  int sa[SL], sb[SL];
+#pragma unroll
+  for (int k = 0; k < SL; ++k) {
+    const int p = SL * e + k;
+    if (p < EB::PAIRS) EB::decode(p, sa[k], sb[k]);
+    else { sa[k] = 0; sb[k] = 1; }  // thread I - 1: unused slots
+  }
+  auto fma2 = [](T w, T xr, T xi, T2 acc) -> T2 {
+    if constexpr (sizeof(T) == 4) return __ffma2_rn(make_float2(w, w), make_float2(xr, xi), acc);
+    else return make_double2(fma(w, xr, acc.x), fma(w, xi, acc.y));
+  };
+  VV* __restrict__ vg = reinterpret_cast<VV*>(a.v);
+  const long long row = a.ld / FU;
+  T pre[I], pim[I], lame[J];  // column e of P and lambda_je of the segment's problem
+  T lacc[J], qacc, gacc;      // Lambda sums of column e, L2 parts of i = e
+  T2 eacc[SL][J];             // (re, im) of u_j z_a conj(z_b) per pair slot
+  TileIter it(u0, u1, pt, TC::T);
+  bool seg_new = true;
+  int ntile = 0;         // tile trips since the segment's start or last flush
+  bool flushed = false;  // the segment has flushed into its slot
+  int Np = 0;
+  long long rlen = 0;
+  VV* __restrict__ vrow = vg;
+  for (int t = 0; it.next(); ++t) {
+    const int f = it.f;
+    if (seg_new) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        lacc[j] = (T)0;
+#pragma unroll
+        for (int k = 0; k < SL; ++k) eacc[k][j] = T2{0, 0};
+      }
+      qacc = (T)0;
+      gacc = (T)0;
+      Np = pt.frames(f);
+      rlen = pt.row_len(f, row * FU) / FU;
+      vrow = vg + (size_t)J * pt.Fm * (pt.frame_off(f) / FU) + (size_t)pt.freq(f) * rlen;
+    }
+    if (consumer_acquire(a, pp, t, f, abort)) {
+      const unsigned char* st = pp.smem + (size_t)(t % S) * TC::STAGE;
+      if (seg_new) {
+        const PA& sp = *reinterpret_cast<const PA*>(st + TC::ROFF);
+#pragma unroll
+        for (int m = 0; m < I; ++m) {
+          pre[m] = sp.pre(m, e);
+          pim[m] = sp.pim(m, e);
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) lame[j] = sp.lam(j, e);
+      }
+      const VY* ys = reinterpret_cast<const VY*>(st);
+      const VV* vs = reinterpret_cast<const VV*>(st + TC::VOFF);
+      // every lane runs the same trips (the shuffles need the whole warp);
+      // units beyond the tile get neutral data and add nothing
+#pragma unroll 1
+      for (int qb = 0; qb < it.n; qb += IG) {
+        const int q = qb + ul;  // < T: it.n <= T and T is a multiple of IG
+        const int k = it.k + q;
+        const int n0 = k * FU;
+        const bool unit_ok = q < it.n && n0 < Np;
+        const bool full = n0 + FU <= Np;
+        // y~_e = sum_m conj(P_me) y_m: re = Pr yr + Pi yi, im = Pr yi - Pi yr
+        L tr = LN::bc(0), ti = LN::bc(0);
+#pragma unroll
+        for (int m = 0; m < I; ++m) {
+          L yr = LN::bc(0), yi = LN::bc(0);
+          if (unit_ok) LN::split(ys[m * TC::YP + q], yr, yi);
+          const L pr = LN::bc(pre[m]), pi = LN::bc(pim[m]);
+          tr = vfma(pr, yr, vfma(pi, yi, tr));
+          ti = vfma(pr, yi, vfma(pi * LN::bc(-1), yr, ti));
+        }
+        L vv[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) vv[j] = unit_ok ? LN::real(vs[j * TC::T + q]) : LN::bc(1);
+        L sg = vv[0] * LN::bc(lame[0]);
+#pragma unroll
+        for (int j = 1; j < J; ++j) sg = vfma(vv[j], LN::bc(lame[j]), sg);
+        const L r = vrcp(sg);
+        const L e2 = vfma(tr, tr, ti * ti);
+        const L w = r * vfma(r, e2, LN::bc(-1));
+        L tj[J], sj[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          tj[j] = vfma(vv[j] * LN::bc(lame[j]), w, LN::bc(1));
+          sj[j] = tj[j];
+        }
+#pragma unroll
+        for (int off = 1; off < I; off <<= 1)  // s_j = sum over the unit's I threads
+#pragma unroll
+          for (int j = 0; j < J; ++j) sj[j] = sj[j] + shfl_xor_l(sj[j], off);
+        L rs[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) rs[j] = vrcp(sj[j]);
+        const L zr = r * tr, zi = r * ti;
+        L zar[SL], zai[SL], zbr[SL], zbi[SL];
+#pragma unroll
+        for (int kk = 0; kk < SL; ++kk) {
+          zar[kk] = shfl_l(zr, gl | sa[kk]);
+          zai[kk] = shfl_l(zi, gl | sa[kk]);
+          zbr[kk] = shfl_l(zr, gl | sb[kk]);
+          zbi[kk] = shfl_l(zi, gl | sb[kk]);
+        }
+        if (!unit_ok) continue;  // after the shuffles: nothing below involves other lanes
+        if (e < J) {  // v^new of source e (the padding frames of a ragged unit keep their values)
+          L ve = vv[0], se = sj[0];
+#pragma unroll
+          for (int j = 1; j < J; ++j)
+            if (j == e) {
+              ve = vv[j];
+              se = sj[j];
+            }
+          const L vn = ve * se * LN::bc((T)(1.0 / I));
+          vrow[(size_t)e * pt.Fm * rlen + k] = LN::store(full ? vn : LN::pick(vn, ve, n0, Np));
+        }
+        L uj[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          uj[j] = vv[j] * rs[j];
+          L x = tj[j] * rs[j];
+          if (!full) {  // padding frames may hold anything: select, do not multiply
+            x = LN::keep(x, n0, Np);
+            uj[j] = LN::keep(uj[j], n0, Np);
+          }
+          lacc[j] += LN::hsum(x);
+        }
+        {
+          L qd = e2 * r, lg = vlog2(sg);
+          if (!full) {
+            qd = LN::keep(qd, n0, Np);
+            lg = LN::keep(lg, n0, Np);
+          }
+          qacc += LN::hsum(qd);
+          gacc += LN::hsum(lg);
+        }
+#pragma unroll
+        for (int kk = 0; kk < SL; ++kk) {
+          const L pr = vfma(zar[kk], zbr[kk], zai[kk] * zbi[kk]);                 // re(z_a conj(z_b))
+          const L pi = vfma(zai[kk], zbr[kk], (zar[kk] * zbi[kk]) * LN::bc(-1));  // im(z_a conj(z_b))
+#pragma unroll
+          for (int fr = 0; fr < FU; ++fr) {
+            if (!full && n0 + fr >= Np) continue;  // a padding frame: its values may be anything
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+              eacc[kk][j] = fma2(lane_of(uj[j], fr), lane_of(pr, fr), lane_of(pi, fr), eacc[kk][j]);
+          }
+        }
+      }
+    }
+    seg_new = false;
+    consumer_release(pp, t);
+
+    // FP32: the plain sums are flushed into the slot every 2 kFlushUnits
+    // units per thread, as pass B's I > 4 form
+    const bool flush = sizeof(T) == 4 && !it.seg_end && ++ntile == 2 * flush_tiles(TC::T / IG);
+    if (it.seg_end || flush) {
+      const int slot = rl.vb - pt.first_block(f);
+      double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * EB::NV;
+      T h[NVT];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        h[j] = lacc[j];
+#pragma unroll
+        for (int kk = 0; kk < SL; ++kk) {
+          h[J + 2 + 2 * (kk * J + j)] = eacc[kk][j].x;
+          h[J + 2 + 2 * (kk * J + j) + 1] = eacc[kk][j].y;
+        }
+      }
+      h[J] = qacc;
+      h[J + 1] = gacc;
+#pragma unroll
+      for (int off = 1; off < I; off <<= 1) {  // the L2 parts over the unit's threads
+        h[J] += __shfl_xor_sync(0xffffffffu, h[J], off);
+        h[J + 1] += __shfl_xor_sync(0xffffffffu, h[J + 1], off);
+      }
+#pragma unroll
+      for (int off = I; off < 32; off <<= 1)  // the lanes with the same e
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) h[v] += __shfl_xor_sync(0xffffffffu, h[v], off);
+      if (lane < I) {
+#pragma unroll
+        for (int v = 0; v < NVT; ++v) Red::one(red)[rl.cwarp][lane * NVT + v] = h[v];
+      }
+      consumer_sync(rl.group);
+      for (int x = tid; x < I * NVT; x += kConsumers) {
+        const int o = EB::out_index(x / NVT, x % NVT);
+        if (o < 0) continue;
+        T sh = Red::one(red)[0][x];
+        T sl = (T)0;
+#pragma unroll
+        for (int w2 = 1; w2 < kConsumerWarps; ++w2) {
+          if constexpr (sizeof(T) == 4) df_add(sh, sl, Red::one(red)[w2][x], (T)0);
+          else sh += Red::one(red)[w2][x];
+        }
+        const double xv = (double)sh + (double)sl;
+        out[o] = flushed ? out[o] + xv : xv;
+      }
+      consumer_sync(rl.group);
+      ntile = 0;
+      if (flush) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          lacc[j] = (T)0;
+#pragma unroll
+          for (int kk = 0; kk < SL; ++kk) eacc[kk][j] = T2{0, 0};
+        }
+        qacc = (T)0;
+        gacc = (T)0;
+        flushed = true;
+      } else {
+        flushed = false;
+        seg_new = true;
+      }
+    }
+  }
+}
+
+// Pass A in its EM form for I > 4: the producer of k_estep, the consumers of
+// estep_consume_big_em; one pipeline group per CTA.
+template <typename T, int I, int J>
+__global__ void __maxnreg__(255) k_estep_em_big(FastArgs a) {
+  static_assert(I > 4 && EmGroups<T, I, J>::value == 1, "the I > 4 EM form runs one group per CTA");
+  constexpr int G = 1;
+  using TC = Tile<T, I, J, G>;
+  constexpr int FU = Vec<T>::FU;
+  using Red = GroupReduce<T, I * EmBig<I, J>::NVT, 1>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ typename Red::Smem red_all[G];
+  __shared__ int aborts[G];
+  const Role rl = role<G>();
+  volatile int* abort = &aborts[rl.group];
+  const Partition pt = a.part;
+  const long long u0 = pt.block_start(rl.vb);
+  const long long u1 = pt.block_start(rl.vb + 1);
+  const long long row = a.ld / FU;
+  const Pipe<TC::S> pp = setup_pipe<G, TC::S>(smem, TC::STAGE, rl.group, aborts);
+  if (!rl.consumer) {
+    if ((threadIdx.x & 31) == 0 && a.fault != kFaultPassANoCopies)
+      produce<T, I, J, false, G>(a, pp, u0, u1, row, rl.vb, abort);
+    return;
+  }
+  estep_consume_big_em<T, I, J, Red, TC::S, G>(a, pp, u0, u1, rl, abort, red_all[rl.group]);
+}
+
 // -------------------------------------------------------------- pass A
 // Per frame, with r_i = 1/sigma_i and a_ji = v_j lambda_ji, the posterior
 // power is q_ji = |mu~_ji|^2 + phi~_ji = a_ji t_ji with

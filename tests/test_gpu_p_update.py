@@ -1,5 +1,6 @@
 """GPU parity of the alternative updates of P (Sec. 4.6: the gradient and
-natural gradient methods and the normal EM, ffca_set_p_update) against the
+natural gradient methods, the normal EM (I <= 4 and 8) and Newton's method
+(I <= 4), ffca_set_p_update) against the
 FP64 oracle, for single mixtures at every compiled I, with K > 1 steps, on
 batches and under graph replay; the inversion counts and the argument checks.
 
@@ -168,7 +169,7 @@ def test_batch_natural_gradient_matches_oracle(prec, I, J):
 
 # ------------------------------------------------------------ normal EM
 EM_SHAPES = [(1, 2, 3, 41), (2, 3, 4, 50), (3, 3, 5, 137), (4, 3, 3, 301), (3, 6, 2, 123), (2, 1, 3, 77),
-             (4, 5, 2, 96)]
+             (4, 5, 2, 96), (8, 6, 3, 260), (8, 3, 2, 157), (8, 1, 2, 64)]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -186,7 +187,7 @@ def test_em_iterations_match_oracle(prec, shape):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("I", [2, 3, 4])
+@pytest.mark.parametrize("I", [2, 3, 4, 8])
 def test_em_several_sweeps(prec, I):
     """K = 3 sweeps of the M-step map per iteration (P^{-H} of each
     intermediate P, the W_i of the entering state), on a ragged length with
@@ -197,7 +198,7 @@ def test_em_several_sweeps(prec, I):
     _compare(prec, ref, got, 91, 4)
 
 
-@pytest.mark.parametrize("I", [2, 4])
+@pytest.mark.parametrize("I", [2, 4, 8])
 def test_em_inversion_count_and_launches(I):
     """(I+1) F K inversions per iteration, as the fixed point; one streaming
     pass per iteration (no pass B launch)."""
@@ -211,16 +212,6 @@ def test_em_inversion_count_and_launches(I):
     counts = ffca.ffca_timing_read(est.ctx)
     assert est.inversion_count() == 3 * 7 * (I + 1) * 2
     assert counts["estep"][1] == 3 and counts["wcov"][1] == 0 and counts["psolve"][1] == 3
-    est.close()
-
-
-def test_em_unsupported_at_eight_mics():
-    from paper_1805_09498_gb300 import ffca
-    p = make_problem(8, 6, 2, 40, seed=8, alpha=0.2, kappa=50.0)
-    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed")
-    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
-    with pytest.raises(ffca.FFCAError):
-        est.set_p_update("em")
     est.close()
 
 
@@ -245,7 +236,7 @@ def test_em_graph_replay_and_switch():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("I,J", [(4, 3), (2, 2), (3, 3)])
+@pytest.mark.parametrize("I,J", [(4, 3), (2, 2), (3, 3), (8, 6)])
 def test_batch_em_matches_oracle(prec, I, J):
     """A ragged batch with the normal EM, per mixture against the oracle,
     with the trace (the step's last block sums the problems' L2)."""
