@@ -73,7 +73,16 @@ __device__ inline float recip(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r * fmaf(-x, r, 2.0f);
 }
-__device__ inline double recip(double x) { return 1.0 / x; }
+// FP64: the hardware estimate refined by two Newton-Raphson steps
+// r <- r + r (1 - x r) (each step doubles the correct bits; the result is
+// within an ulp or two of 1/x, not correctly rounded).  Zero, infinite and
+// subnormal x give a non-finite result, which the kernels report.
+__device__ inline double recip(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
 __device__ inline float logx(float x) { return __logf(x); }
 __device__ inline double logx(double x) { return log(x); }
 

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
       if (lane + 32 * c < G * NV) sums[lane + 32 * c] = acc[c];
   } else {  // I > 4: eight values of a lane at a time
     constexpr int CH = 8;
+#pragma unroll 1
     for (int c0 = 0; c0 < PER; c0 += CH) {
       const double* src[CH];
       int ns[CH];
@@ -208,15 +209,20 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
     }
     rl[j] = 1.0 / lji;
   }
-  double dv[I], d0[I], rd[I];
-  cpx<double> lo[ES::NL];
-#pragma unroll
-  for (int c = 0; c < I; ++c) {
+  // Omega_i's diagonal entry c (formed again for the pivot check: I > 4
+  // keeps no copy in registers)
+  auto omega_diag = [&](int c) -> double {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < J; ++j) s = fma(nd * LNEW(j, c), rl[j], s);
-    dv[c] = s;
-    d0[c] = s;
+    return s;
+  };
+  double dv[I], d0[BIG ? 1 : I], rd[I];
+  cpx<double> lo[ES::NL];
+#pragma unroll
+  for (int c = 0; c < I; ++c) {
+    dv[c] = omega_diag(c);
+    if constexpr (!BIG) d0[c] = dv[c];
   }
   {
     int pq = 0;
@@ -246,7 +252,10 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
   } else {
     singular = !ldl_factor<I>(dv, lo, rd);
 #pragma unroll
-    for (int c = 0; c < I; ++c) singular |= !(dv[c] > kCholRtol * d0[c]);  // dv holds the pivots D
+    for (int c = 0; c < I; ++c) {  // dv holds the pivots D
+      if constexpr (BIG) singular |= !(dv[c] > kCholRtol * omega_diag(c));
+      else singular |= !(dv[c] > kCholRtol * d0[c]);
+    }
   }
 
   // commit the new Lambda (column i of the problem's Lambda entries)
@@ -270,39 +279,46 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
     if (bad) raise_status(a.status, kDevNonfinite, f);
   }
 
-  // K sweeps; col holds column i of the current P
+  // K sweeps; col holds column i of the current P.  The first (x = P^H
+  // P^{-H} e_i = e_i) is written out before the loop of the later ones, so
+  // that K = 1 runs none of the loop's register traffic (at I = 8 the loop
+  // state does not fit the registers).
   const double jn = (double)J * nd;
   cpx<double> col[I];
-  for (int sweep = 0; sweep < a.K; ++sweep) {
-    cpx<double> x[I];
-    if (sweep == 0) {
-#pragma unroll
-      for (int r = 0; r < I; ++r) x[r] = mk(r == i ? 1.0 : 0.0, 0.0);  // P^H P^{-H} e_i
-    } else {
-      cpx<double> q[I];  // column i of the current P's P^{-H}
-#pragma unroll
-      for (int r = 0; r < I; ++r) q[r] = col[r];
-      pinvh_from_columns<I>(q, M, g, i, singular);
-#pragma unroll
-      for (int c = 0; c < I; ++c) {  // x = P^H q with the entering P
-        cpx<double> s = mk(0.0, 0.0);
-#pragma unroll
-        for (int r = 0; r < I; ++r) cfmac(s, P0(r, c), q[r]);
-        x[c] = s;
-      }
-    }
+  auto sweep_tail = [&](cpx<double> (&x)[I]) {  // col = J N P Omega_i^{-1} x
     if constexpr (I == 1) {
       x[0] = cscale(x[0], rd[0]);
     } else {
-      ldl_solve<I>(lo, rd, x);  // x <- Omega_i^{-1} x
+      ldl_solve<I>(lo, rd, x);
     }
 #pragma unroll
-    for (int r = 0; r < I; ++r) {  // column i = J N P x
+    for (int r = 0; r < I; ++r) {
       cpx<double> s = mk(0.0, 0.0);
 #pragma unroll
       for (int c = 0; c < I; ++c) cfma(s, P0(r, c), x[c]);
       col[r] = cscale(s, jn);
     }
+  };
+  {
+    cpx<double> x[I];
+#pragma unroll
+    for (int r = 0; r < I; ++r) x[r] = mk(r == i ? 1.0 : 0.0, 0.0);
+    sweep_tail(x);
+  }
+  for (int sweep = 1; sweep < a.K; ++sweep) {
+    cpx<double> q[I];  // column i of the current P's P^{-H}
+#pragma unroll
+    for (int r = 0; r < I; ++r) q[r] = col[r];
+    pinvh_from_columns<I>(q, M, g, i, singular);
+    cpx<double> x[I];
+#pragma unroll
+    for (int c = 0; c < I; ++c) {  // x = P^H q with the entering P
+      cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+      for (int r = 0; r < I; ++r) cfmac(s, P0(r, c), q[r]);
+      x[c] = s;
+    }
+    sweep_tail(x);
   }
   if (active) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);

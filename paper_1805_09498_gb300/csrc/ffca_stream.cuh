@@ -578,7 +578,7 @@ struct D1 {
 __device__ inline D1 operator+(D1 a, D1 b) { return {a.v + b.v}; }
 __device__ inline D1 operator*(D1 a, D1 b) { return {a.v * b.v}; }
 __device__ inline D1 vfma(D1 a, D1 b, D1 c) { return {fma(a.v, b.v, c.v)}; }
-__device__ inline D1 vrcp(D1 x) { return {1.0 / x.v}; }
+__device__ inline D1 vrcp(D1 x) { return {recip(x.v)}; }
 __device__ inline D1 vlog2(D1 x) { return {log2(x.v)}; }
 
 // sum_i log2 sigma_i of one point.  FP32 lanes take one hardware log2 per
