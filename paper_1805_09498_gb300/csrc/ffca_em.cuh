@@ -45,7 +45,12 @@ struct EmShape {
   // (as registers they would take more than a lane holds)
   static constexpr bool BIG = I > 4;
   static constexpr int PSM = BIG ? G * (I * I * 2 + 2 * J * I) : 0;  // doubles
-  static constexpr int SMEM = BigLane<I>::SMEM + G * NV * (int)sizeof(double) + PSM * (int)sizeof(double);
+  // I > 4 with K > 1: each lane's L D L^H factor of Omega_i, kept in shared
+  // memory between the sweeps (held in registers across the sweep loop it
+  // would not fit)
+  static constexpr int FAC = BIG ? 2 * NL + I : 0;  // doubles per lane
+  static constexpr int SMEM =
+      BigLane<I>::SMEM + G * NV * (int)sizeof(double) + PSM * (int)sizeof(double) + 32 * FAC * (int)sizeof(double);
 };
 
 template <typename T, int I, int J>
@@ -305,6 +310,19 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
     for (int r = 0; r < I; ++r) x[r] = mk(r == i ? 1.0 : 0.0, 0.0);
     sweep_tail(x);
   }
+  double* fac = reinterpret_cast<double*>(em_smem + BigLane<I>::SMEM + G * NV * sizeof(double) +
+                                          ES::PSM * sizeof(double)) + (size_t)lane * ES::FAC;
+  if constexpr (BIG) {
+    if (a.K > 1) {
+#pragma unroll
+      for (int c = 0; c < ES::NL; ++c) {
+        fac[2 * c] = lo[c].re;
+        fac[2 * c + 1] = lo[c].im;
+      }
+#pragma unroll
+      for (int c = 0; c < I; ++c) fac[2 * ES::NL + c] = rd[c];
+    }
+  }
   for (int sweep = 1; sweep < a.K; ++sweep) {
     cpx<double> q[I];  // column i of the current P's P^{-H}
 #pragma unroll
@@ -318,7 +336,24 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
       for (int r = 0; r < I; ++r) cfmac(s, P0(r, c), q[r]);
       x[c] = s;
     }
-    sweep_tail(x);
+    if constexpr (BIG) {  // the factor back from shared memory
+      cpx<double> lo2[ES::NL];
+      double rd2[I];
+#pragma unroll
+      for (int c = 0; c < ES::NL; ++c) lo2[c] = mk(fac[2 * c], fac[2 * c + 1]);
+#pragma unroll
+      for (int c = 0; c < I; ++c) rd2[c] = fac[2 * ES::NL + c];
+      ldl_solve<I>(lo2, rd2, x);
+#pragma unroll
+      for (int r = 0; r < I; ++r) {
+        cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < I; ++c) cfma(s, P0(r, c), x[c]);
+        col[r] = cscale(s, jn);
+      }
+    } else {
+      sweep_tail(x);
+    }
   }
   if (active) {
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);

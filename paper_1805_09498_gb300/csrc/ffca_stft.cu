@@ -321,19 +321,58 @@ __global__ void __launch_bounds__(kThreads, 2) k_stft(const float* __restrict__ 
   cp_async_wait<0>();
 }
 
+// One frame's inverse by a warp: the spectrum X[k] = x_of(k), k = 0 .. 512,
+// to the frame's 1024 windowed samples, left in the warp's buffer as pairs
+// (zeros where !on).  Z[k] = E[k] + i O[k] from X[k] and X[512 - k] (bins 0
+// and L/2 of a real signal's spectrum are real: their imaginary parts are
+// ignored), conjugated for the forward transform:
+// IDFT(Z) = conj(DFT(conj Z)) / 512.
+template <typename X>
+__device__ inline void inverse_frame(X x_of, bool on, int lane, float2* __restrict__ buf, const float2 (&tw1)[15],
+                                     float2 wl) {
+  float2 u[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int k = lane + 32 * q;
+    float2 xk = x_of(k);
+    float2 xm = cconj(x_of(kM - k));
+    if (k == 0) {
+      xk.y = 0.f;
+      xm.y = 0.f;
+    }
+    const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
+    const float2 o = cmul(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y - xm.y)), cconj(cmul(wl, c_w32[q])));
+    u[q] = cconj(make_float2(e.x - o.y, e.y + o.x));
+  }
+  fft512_warp(u, lane, buf, tw1);  // lane l: DFT(conj Z) at t = l + 32 j in u[j]
+  const float2* win = reinterpret_cast<const float2*>(g_win);
+  const float sc = 1.0f / kM;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {  // x(2t) = Re / 512, x(2t+1) = -Im / 512, windowed
+    const int t = lane + 32 * j;
+    const float2 wv = __ldg(win + t);
+    buf[t] = on ? make_float2(wv.x * u[j].x * sc, -wv.y * u[j].y * sc) : make_float2(0.f, 0.f);
+  }
+}
+
 // in [C][F][ld] complex64 (frames 0 .. N-1) -> out [C][(N + 1) H] float.
-// Persistent over the C x ceil((N + 1) / (kFrames - 1)) groups of output
-// blocks: group b of channel c writes the kFrames - 1 blocks k = k0 ..
-// k0 + kFrames - 2 of H samples (k0 = (kFrames - 1) b, k <= N), block k
-// being the second half of frame k - 1 plus the first half of frame k; warp
-// w inverts frame m0 + w (m0 = k0 - 1; a missing frame adds nothing).  The
-// next group's spectra (runs of kFrames frames per bin) are copied into the
-// other input stage (cp.async, zeros for missing frames) while this group is
-// transformed; each warp leaves its frame's windowed halves in its buffer.
-// VEC: out allows 16-byte stores.
+// Output block k (samples k H .. k H + H - 1, k = 0 .. N) is the second half
+// of frame k - 1 plus the first half of frame k.  Group b of a channel holds
+// the blocks and the frames 8 b .. 8 b + 7: warp w inverts frame 8 b + w
+// (a missing frame adds nothing), and block 8 b + w adds its first half to
+// the second half of frame 8 b + w - 1, which for w = 0 is the last frame of
+// group b - 1.  Persistent CTAs take contiguous ranges of the
+// C x ceil((N + 1) / 8) groups and carry that half from one group to the
+// next (two alternating buffers; zeros at a channel's first group); at the
+// start of a range with b > 0, warp 0 first inverts frame 8 b - 1 for it.
+// The next group's spectra (runs of 8 frames per bin, zeros beyond N) are
+// copied into the other input stage (cp.async) while this group is
+// transformed.  VEC: out allows 16-byte stores.
 struct StftInvSmem {
   float2 buf[kFrames][kBuf];
   float2 in[2][kF][kFrames];  // swizzled rows, as the forward's spectra
+  float carry[2][kH];         // second half of the frame before the group
+  float2 pro[kF];             // the spectrum of the frame before a range's first group
 };
 
 template <bool VEC>
@@ -341,14 +380,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_istft(const float2* __restrict_
                                                        float* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   StftInvSmem& sm = *reinterpret_cast<StftInvSmem*>(smem_raw);
-  const int B = (N + 1 + kFrames - 2) / (kFrames - 1), items = C * B;
+  const int B = (N + kFrames) / kFrames, items = C * B;
+  const int per = (items + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int it0 = blockIdx.x * per, it1 = min(items, it0 + per);
+  if (it0 >= it1) return;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto fetch = [&](int item, int st) {
-    const int c = item / B, m0 = (item % B) * (kFrames - 1) - 1;
+    const int c = item / B, m0 = (item % B) * kFrames;
     const float2* ic = in + (size_t)c * kF * ld;
     // thread t copies frame fr = t mod 8 of the bins f0 + 32 i (f0 = t / 8); swz(f0 + 32 i) = swz(f0)
     const int fr = threadIdx.x % kFrames, f0 = threadIdx.x / kFrames, m = m0 + fr;
-    const bool ok = m >= 0 && m < N;
+    const bool ok = m < N;
     const float2* src = ok ? ic + (size_t)f0 * ld + m : ic;
     const size_t step = ok ? (size_t)(kThreads / kFrames) * ld : 0;
     float2* dst = &sm.in[st][f0][fr ^ swz(f0)];
@@ -359,66 +401,63 @@ __global__ void __launch_bounds__(kThreads, 2) k_istft(const float2* __restrict_
       dst += (kThreads / kFrames) * kFrames;
     }
   };
-  int it = blockIdx.x;
-  if (it >= items) return;
   float2 tw1[15];
   lane_twiddles(lane, tw1);
   const float2 wl = __ldg(g_tw1024 + lane);  // W1024^l
-  fetch(it, 0);
+  fetch(it0, 0);
   cp_async_commit();
-  const float2* win = reinterpret_cast<const float2*>(g_win);
-  const float sc = 1.0f / kM;
-  for (int st = 0; it < items; it += gridDim.x, st ^= 1) {
-    if (it + (int)gridDim.x < items) fetch(it + gridDim.x, st ^ 1);
+  {  // the carried half before the range's first group
+    const int c0 = it0 / B, b0 = it0 % B;
+    if (b0 > 0) {
+      const float2* col = in + (size_t)c0 * kF * ld + (kFrames * b0 - 1);  // frame 8 b0 - 1 < N
+      for (int t = threadIdx.x; t < kF; t += kThreads) sm.pro[t] = __ldg(col + (size_t)t * ld);
+      __syncthreads();
+      if (w == 0) {
+        inverse_frame([&](int k) { return sm.pro[k]; }, true, lane, sm.buf[0], tw1, wl);
+        __syncwarp();
+        const float* h = reinterpret_cast<const float*>(sm.buf[0]);
+        for (int t = lane; t < kH; t += 32) sm.carry[0][t] = h[kH + t];
+      }
+    }
+  }
+  int par = 0;  // the carry buffer of the current group
+  for (int it = it0, st = 0; it < it1; ++it, st ^= 1) {
+    if (it + 1 < it1) fetch(it + 1, st ^ 1);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    const int c = it / B, k0 = (it % B) * (kFrames - 1), m = k0 - 1 + w;
-    const bool on = m >= 0 && m < N;
-    float2 u[16];
-    // Z[k] = E[k] + i O[k] from X[k] and X[512 - k] (bins 0 and L/2 of a real
-    // signal's spectrum are real: their imaginary parts are ignored), conjugated
-    // for the forward transform: IDFT(Z) = conj(DFT(conj Z)) / 512
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int k = lane + 32 * q;
-      float2 xk = sm.in[st][k][w ^ swz(k)];
-      float2 xm = cconj(sm.in[st][kM - k][w ^ swz(kM - k)]);
-      if (k == 0) {
-        xk.y = 0.f;
-        xm.y = 0.f;
-      }
-      const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
-      const float2 o = cmul(make_float2(0.5f * (xk.x - xm.x), 0.5f * (xk.y - xm.y)), cconj(cmul(wl, c_w32[q])));
-      u[q] = cconj(make_float2(e.x - o.y, e.y + o.x));
-    }
-    fft512_warp(u, lane, sm.buf[w], tw1);  // lane l: DFT(conj Z) at t = l + 32 j in u[j]
-    float2* half = sm.buf[w];                  // the frame's 1024 windowed samples, as pairs
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {  // x(2t) = Re / 512, x(2t+1) = -Im / 512, windowed
-      const int t = lane + 32 * j;
-      const float2 wv = __ldg(win + t);
-      half[t] = on ? make_float2(wv.x * u[j].x * sc, -wv.y * u[j].y * sc) : make_float2(0.f, 0.f);
-    }
+    const int c = it / B, b = it % B, m = kFrames * b + w;
+    inverse_frame([&](int k) { return sm.in[st][k][w ^ swz(k)]; }, m < N, lane, sm.buf[w], tw1, wl);
     __syncthreads();
-    // samples k H + s: second half of frame k - 1 (local k - k0) + first half of frame k (local k - k0 + 1)
-    float* oc = out + (size_t)c * ((size_t)N + 1) * kH;
-    const int nk = min(kFrames - 1, N + 1 - k0);
+    // blocks 8 b + kk: second half of frame 8 b + kk - 1 (the carry for kk = 0, none at b = 0)
+    // plus the first half of frame 8 b + kk
+    float* oc = out + (size_t)c * ((size_t)N + 1) * kH + (size_t)kFrames * b * kH;
+    const int nk = min(kFrames, N + 1 - kFrames * b);
+    const bool first = b == 0;
     if (VEC) {
       for (int t = threadIdx.x; t < nk * (kH / 4); t += kThreads) {
         const int kk = t / (kH / 4), s4 = t % (kH / 4);
-        const float4 a = reinterpret_cast<const float4*>(sm.buf[kk])[kH / 4 + s4];
-        const float4 b2 = reinterpret_cast<const float4*>(sm.buf[kk + 1])[s4];
-        reinterpret_cast<float4*>(oc + (size_t)(k0 + kk) * kH)[s4] =
-            make_float4(a.x + b2.x, a.y + b2.y, a.z + b2.z, a.w + b2.w);
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kk > 0) a = reinterpret_cast<const float4*>(sm.buf[kk - 1])[kH / 4 + s4];
+        else if (!first) a = reinterpret_cast<const float4*>(sm.carry[par])[s4];
+        const float4 b2 = reinterpret_cast<const float4*>(sm.buf[kk])[s4];
+        reinterpret_cast<float4*>(oc + (size_t)kk * kH)[s4] = make_float4(a.x + b2.x, a.y + b2.y, a.z + b2.z, a.w + b2.w);
       }
     } else {
       for (int t = threadIdx.x; t < nk * kH; t += kThreads) {
         const int kk = t / kH, s1 = t % kH;
-        oc[(size_t)(k0 + kk) * kH + s1] =
-            reinterpret_cast<const float*>(sm.buf[kk])[kH + s1] + reinterpret_cast<const float*>(sm.buf[kk + 1])[s1];
+        float a = 0.f;
+        if (kk > 0) a = reinterpret_cast<const float*>(sm.buf[kk - 1])[kH + s1];
+        else if (!first) a = sm.carry[par][s1];
+        oc[(size_t)kk * kH + s1] = a + reinterpret_cast<const float*>(sm.buf[kk])[s1];
       }
     }
+    // the next group's carry: the second half of frame 8 b + 7
+    {
+      const float* h = reinterpret_cast<const float*>(sm.buf[kFrames - 1]);
+      for (int t = threadIdx.x; t < kH; t += kThreads) sm.carry[par ^ 1][t] = h[kH + t];
+    }
+    par ^= 1;
   }
   cp_async_wait<0>();
 }
@@ -465,7 +504,7 @@ ffca_status ffca_stft(const float* x, int C, long long S, void* out, int ld, voi
 ffca_status ffca_istft(const void* in, int C, int N, int ld, float* out, void* stream) {
   if (C < 0 || N < 0 || ld < 0) return FFCA_ERR_ARG;
   if (C == 0 || N == 0) return FFCA_OK;
-  const long long items = (long long)C * ((N + 1 + kFrames - 2) / (kFrames - 1));
+  const long long items = (long long)C * ((N + kFrames) / kFrames);
   if (ld < N || !in || !out || (reinterpret_cast<uintptr_t>(in) % 16) != 0 ||
       (reinterpret_cast<uintptr_t>(out) % 4) != 0 || C > 65535 || N > (1 << 30) - 2 || items > INT32_MAX / 2)
     return FFCA_ERR_ARG;
