@@ -55,7 +55,7 @@
  *    warps' sums in double-float (TwoSum), and the partial sums in FP64.
  *
  * Supported shapes: I in {1, 2, 3, 4, 8}, 1 <= J <= 6 (FFCA_ERR_UNSUPPORTED
- * otherwise; the gradients take I <= 4 only), N >= 1, F >= 0 (F == 0 is a
+ * otherwise; Newton's method for P takes I <= 4 only), N >= 1, F >= 0 (F == 0 is a
  * no-op).
  */
 #ifndef FFCA_H
@@ -189,7 +189,7 @@ typedef enum {
  * mu: step size, finite and > 0 for the gradient methods and Newton's
  * (ignored for the fixed point and the EM).  Drops a captured graph.
  * FFCA_ERR_ARG for an unknown method or an invalid mu, FFCA_ERR_UNSUPPORTED
- * for the EM or Newton at I = 8 (the context keeps its previous choice).  With the EM, ffca_timing_read
+ * for Newton at I = 8 (the context keeps its previous choice).  With the EM, ffca_timing_read
  * counts its streaming pass as FFCA_KERNEL_ESTEP and its per-problem step as
  * FFCA_KERNEL_PSOLVE, and ffca_batch_autotune tunes the EM pass on pass A's
  * candidates.  The allocation-free call always uses the fixed point. */
@@ -284,8 +284,9 @@ ffca_status ffca_wiener_host(ffca_ctx* ctx, void* out_dev, void* out_host);
  * ffca_wiener output).  Enqueued on the context stream.  For a batch context
  * every array takes the batch layout (dv that of v, dlam and dP stacked per
  * mixture as lambda and P, s that of the batch Wiener output), N is each
- * mixture's N[m], and loss is the sum over the mixtures.
- * FFCA_ERR_UNSUPPORTED for I = 8. */
+ * mixture's N[m], and loss is the sum over the mixtures.  At I = 8 each
+ * unit of the pass is shared by eight threads (thread e: y~_e, sigma_e and
+ * column e of dP^*). */
 ffca_status ffca_nll_grad(ffca_ctx* ctx, void* dv, double* dlam, double* dP, double* loss);
 ffca_status ffca_wiener_se_grad(ffca_ctx* ctx, const void* s, void* dv, double* dlam, double* dP,
                                 double* loss);

@@ -260,6 +260,241 @@ __global__ void __launch_bounds__(kBlock) k_adj(AdjArgs a) {
   }
 }
 
+// The adjoint for I > 4: the per-point state (I^2 + J I sums of dP^* and
+// dLambda, the Wiener estimates of J sources) does not fit one thread, so
+// each unit is shared by I threads as in pass B's I > 4 form.  Thread e owns
+// index i = e: y~_e, sigma_e, r_e, the Lambda sums of column e, column e of
+// dP^* (I complex sums), and the loss parts of i = e.  Sums over i (dv_j;
+// the Wiener estimates x^_j = Q (g_j * y~) and b_j = Q^H e_j of the squared
+// error) go through the unit's lanes by shuffles: thread e forms row e of
+// x^_j from the gathered g_ji y~_i, and its entry b_je from the gathered
+// rows of e_j.  The slot layout is k_adj's: dlambda, dP^* (re, im) [a][i],
+// then the loss parts.
+template <int I, int J, bool SE>
+struct AdjBig {
+  using S = AdjShape<I, J, SE>;
+  static constexpr int NVT = J + 2 * I + S::NL;  // values per thread
+  // slot index of thread e's value v, or -1 (the loss parts of threads
+  // e > 0, which the reduction leaves in thread 0)
+  __device__ static int out_index(int e, int v) {
+    if (v < J) return v * I + e;
+    if (v < J + 2 * I) {
+      const int m = (v - J) / 2, comp = (v - J) % 2;
+      return S::NA + 2 * (m * I + e) + comp;
+    }
+    return e == 0 ? S::NA + S::NP + (v - J - 2 * I) : -1;
+  }
+};
+
+template <typename T>
+__device__ inline cpx<T> shfl_cx(cpx<T> z, int src) {
+  return mk<T>(__shfl_sync(0xffffffffu, z.re, src), __shfl_sync(0xffffffffu, z.im, src));
+}
+
+template <typename T, int I, int J, bool SE>
+__global__ void __launch_bounds__(kBlock) k_adj_big(AdjArgs a) {
+  using VY = typename Vec<T>::Y;
+  using VV = typename Vec<T>::V;
+  constexpr int FU = Vec<T>::FU;
+  using S = AdjShape<I, J, SE>;
+  using AB = AdjBig<I, J, SE>;
+  constexpr int NVT = AB::NVT;
+  constexpr int UG = kBlock / I;  // units in flight per CTA
+  static_assert(kBlock % I == 0 && 32 % I == 0 && J <= I, "I must divide the block and the warp");
+  __shared__ T red[kWarps][I * NVT];
+  __shared__ double sP[I][I][2], sQ[I][I][2];
+  __shared__ double sLam[J][I];
+
+  const Partition pt = a.part;
+  const long long u0 = pt.block_start(blockIdx.x), u1 = pt.block_start(blockIdx.x + 1);
+  const long long row = a.ld / FU;
+  const VY* __restrict__ y = reinterpret_cast<const VY*>(a.y);
+  const VV* __restrict__ v = reinterpret_cast<const VV*>(a.v);
+  const VY* __restrict__ s = reinterpret_cast<const VY*>(a.s);
+  VV* __restrict__ dv = reinterpret_cast<VV*>(a.dv);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = threadIdx.x % I, ul = threadIdx.x / I;
+  const int gl = lane & ~(I - 1);  // first lane of this unit's I threads
+
+  for (long long u = u0; u < u1;) {
+    const int f = pt.problem_of(u);
+    const long long us = pt.start(f);
+    const int k0 = (int)(u - us);
+    const int k1 = (int)(min(pt.start(f + 1), u1) - us);
+    const int Np = pt.frames(f);
+    const long long rlen = pt.row_len(f, row * FU) / FU;
+    const long long off = pt.frame_off(f) / FU;
+    const long long r0 = (long long)pt.freq(f) * rlen;
+    const size_t rstr = (size_t)pt.Fm * rlen;
+    const VY* __restrict__ yf = y + (size_t)I * pt.Fm * off + r0;
+    const VV* __restrict__ vf = v + (size_t)J * pt.Fm * off + r0;
+    const VY* __restrict__ sf = SE ? s + (size_t)J * I * pt.Fm * off + r0 : nullptr;
+    VV* __restrict__ dvf = dv + (size_t)J * pt.Fm * off + r0;
+    __syncthreads();
+    if (threadIdx.x < I * I) {
+      const int r = threadIdx.x / I, c = threadIdx.x % I;
+      sP[r][c][0] = a.P[((size_t)f * I * I + threadIdx.x) * 2];
+      sP[r][c][1] = a.P[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+      sQ[r][c][0] = a.pinvH[((size_t)f * I * I + threadIdx.x) * 2];
+      sQ[r][c][1] = a.pinvH[((size_t)f * I * I + threadIdx.x) * 2 + 1];
+    }
+    if (threadIdx.x < J * I) sLam[threadIdx.x / I][threadIdx.x % I] = a.lam[(size_t)f * J * I + threadIdx.x];
+    __syncthreads();
+    cpx<T> pcol[I];  // column e of P
+    T lam_e[J];      // lambda_je
+#pragma unroll
+    for (int m = 0; m < I; ++m) pcol[m] = mk<T>((T)sP[m][e][0], (T)sP[m][e][1]);
+#pragma unroll
+    for (int j = 0; j < J; ++j) lam_e[j] = (T)sLam[j][e];
+    auto Qc = [&](int r, int c) { return mk<T>((T)sQ[r][c][0], (T)sQ[r][c][1]); };
+
+    T acc[NVT];
+#pragma unroll
+    for (int q = 0; q < NVT; ++q) acc[q] = (T)0;
+
+    // every lane takes the same trips (the shuffles need the whole warp)
+    for (int kb = k0; kb < k1; kb += UG) {
+      const int k = kb + ul;
+      const bool unit_ok = k < k1;
+      VY yu[I];
+      VV vu[J], dvu;
+#pragma unroll
+      for (int m = 0; m < I; ++m) yu[m] = unit_ok ? yf[m * rstr + k] : VY{};
+#pragma unroll
+      for (int j = 0; j < J; ++j) vu[j] = unit_ok ? vf[j * rstr + k] : VV{};
+      dvu = VV{};
+#pragma unroll
+      for (int fr = 0; fr < FU; ++fr) {
+        const bool valid = unit_ok && k * FU + fr < Np;
+        const T z = valid ? (T)1 : (T)0;  // padding frames contribute nothing
+        cpx<T> ym[I];
+#pragma unroll
+        for (int m = 0; m < I; ++m) ym[m] = valid ? yframe(yu[m], fr) : mk<T>(0, 0);
+        cpx<T> yte = mk<T>(0, 0);  // y~_e = sum_m conj(P_me) y_m
+#pragma unroll
+        for (int m = 0; m < I; ++m) cfmac(yte, pcol[m], ym[m]);
+        T vj[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) vj[j] = valid ? vframe(vu[j], fr) : (T)1;
+        T sg = vj[0] * lam_e[0];
+#pragma unroll
+        for (int j = 1; j < J; ++j) sg = fma(vj[j], lam_e[j], sg);
+        const T re = recip(sg);
+        T dvo[J];  // this thread's term of dv_j (summed over the unit's threads below)
+        if constexpr (!SE) {
+          const T e2 = cabs2(yte);
+          const T te = z * re * fma(-e2, re, (T)1);
+          acc[J + 2 * I] = fma(e2, re * z, acc[J + 2 * I]);
+          acc[J + 2 * I + 1] += z * (sizeof(T) == 4 ? (T)__log2f((float)sg) : (T)log2((double)sg));
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            dvo[j] = lam_e[j] * te;
+            acc[j] = fma(vj[j], te, acc[j]);
+          }
+          // column e of sum_n y y^H P diag(1/sigma): y_m conj(y~_e) / sigma_e
+#pragma unroll
+          for (int m = 0; m < I; ++m) {
+            const cpx<T> c = cmulc(yte, ym[m]);  // conj(y~_e) y_m
+            acc[J + 2 * m] = fma(c.re, re, acc[J + 2 * m]);
+            acc[J + 2 * m + 1] = fma(c.im, re, acc[J + 2 * m + 1]);
+          }
+        } else {
+          // row e of x^_j = Q (g_j * y~), g_ji = v_j lambda_ji r_i, from the gathered y~_i and r_i
+          cpx<T> xh[J];
+#pragma unroll
+          for (int j = 0; j < J; ++j) xh[j] = mk<T>(0, 0);
+#pragma unroll
+          for (int i = 0; i < I; ++i) {
+            const cpx<T> yti = shfl_cx(yte, gl | i);
+            const T ri = __shfl_sync(0xffffffffu, re, gl | i);
+            const cpx<T> q = Qc(e, i);
+#pragma unroll
+            for (int j = 0; j < J; ++j) cfma(xh[j], q, cscale(yti, vj[j] * (T)sLam[j][i] * ri));
+          }
+          // e_je = x^_je - s_je; b_je = sum_m conj(Q_me) e_jm from the gathered rows
+          cpx<T> err[J], b[J];
+          T se = (T)0;
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            const cpx<T> sv = valid ? yframe(sf[(size_t)(j * I + e) * rstr + k], fr) : mk<T>(0, 0);
+            err[j] = csub(xh[j], sv);
+            se = fma(z, cabs2(err[j]), se);
+            b[j] = mk<T>(0, 0);
+          }
+          acc[J + 2 * I] += se;
+#pragma unroll
+          for (int m = 0; m < I; ++m) {
+            const cpx<T> q = Qc(m, e);
+#pragma unroll
+            for (int j = 0; j < J; ++j) cfmac(b[j], q, shfl_cx(err[j], gl | m));
+          }
+          T g[J], G[J], h = (T)0;
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            g[j] = vj[j] * lam_e[j] * re;
+            G[j] = (T)2 * cmulc(b[j], yte).re;  // 2 Re(conj(b_je) y~_e)
+            h = fma(G[j], g[j], h);
+          }
+#pragma unroll
+          for (int j = 0; j < J; ++j) {
+            const T w = z * (G[j] - h) * re;
+            dvo[j] = lam_e[j] * w;
+            acc[j] = fma(vj[j], w, acc[j]);
+          }
+          // column e of sum_j (y (g_j * b_j)^H - x^_j b_j^H): entry [a][e], x^_ja from row a's lane
+#pragma unroll
+          for (int aa = 0; aa < I; ++aa) {
+            cpx<T> t = mk<T>(0, 0);
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+              const cpx<T> bc = cconj(b[j]);
+              t = cadd(t, cmul(ym[aa], cscale(bc, g[j])));
+              t = csub(t, cmul(shfl_cx(xh[j], gl | aa), bc));
+            }
+            acc[J + 2 * aa] = fma(z, t.re, acc[J + 2 * aa]);
+            acc[J + 2 * aa + 1] = fma(z, t.im, acc[J + 2 * aa + 1]);
+          }
+        }
+        // dv_j = sum over the unit's threads; thread j keeps frame fr of dv_j
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          T d = dvo[j];
+#pragma unroll
+          for (int off = 1; off < I; off <<= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+          if (j == e) vset(dvu, fr, d);
+        }
+      }
+      if (unit_ok && e < J) dvf[e * rstr + k] = dvu;
+    }
+    // the segment's sums into slot (f, this CTA): the loss parts over the
+    // unit's threads, the lanes with the same e, then the warps (FP64)
+#pragma unroll
+    for (int q = J + 2 * I; q < NVT; ++q)
+#pragma unroll
+      for (int off = 1; off < I; off <<= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+#pragma unroll
+    for (int off = I; off < 32; off <<= 1)
+#pragma unroll
+      for (int q = 0; q < NVT; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], off);
+    if (lane < I) {
+#pragma unroll
+      for (int q = 0; q < NVT; ++q) red[warp][lane * NVT + q] = acc[q];
+    }
+    __syncthreads();
+    const int slot = (int)blockIdx.x - pt.first_block(f);
+    double* out = a.part_buf + ((size_t)f * pt.max_slots + slot) * S::NV;
+    for (int x = threadIdx.x; x < I * NVT; x += kBlock) {
+      const int o = AB::out_index(x / NVT, x % NVT);
+      if (o < 0) continue;
+      double t = 0.0;
+#pragma unroll
+      for (int w2 = 0; w2 < kWarps; ++w2) t += (double)red[w2][x];
+      out[o] = t;
+    }
+    u += k1 - k0;
+  }
+}
+
 // One warp per frequency: slot sums (FP64, slot order) into dlam, dP and the
 // frequency's loss; the last warp adds the losses.
 template <typename T, int I, int J, bool SE>

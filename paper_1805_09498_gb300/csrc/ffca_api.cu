@@ -52,6 +52,7 @@ const AdjKernels* adj_kernels(int prec, int I, int J) {
       case 2: return adj_kernels_p0_i2(J);
       case 3: return adj_kernels_p0_i3(J);
       case 4: return adj_kernels_p0_i4(J);
+      case 8: return adj_kernels_p0_i8(J);
     }
   } else if (prec == 1) {
     switch (I) {
@@ -59,6 +60,7 @@ const AdjKernels* adj_kernels(int prec, int I, int J) {
       case 2: return adj_kernels_p1_i2(J);
       case 3: return adj_kernels_p1_i3(J);
       case 4: return adj_kernels_p1_i4(J);
+      case 8: return adj_kernels_p1_i8(J);
     }
   }
   return nullptr;

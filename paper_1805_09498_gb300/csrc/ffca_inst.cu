@@ -152,6 +152,15 @@ static const FcaKernels* fca_entry() {
 #if FFCA_PART == 2
 template <int J>
 static const AdjKernels* adj_entry() {
+#if FFCA_I > 4
+  static const AdjKernels k = {
+      (const void*)k_adj_big<Real, FFCA_I, J, false>,
+      (const void*)k_adj_final<Real, FFCA_I, J, false>,
+      (const void*)k_adj_big<Real, FFCA_I, J, true>,
+      (const void*)k_adj_final<Real, FFCA_I, J, true>,
+      AdjShape<FFCA_I, J, false>::NV,
+  };
+#else
   static const AdjKernels k = {
       (const void*)k_adj<Real, FFCA_I, J, false>,
       (const void*)k_adj_final<Real, FFCA_I, J, false>,
@@ -159,6 +168,7 @@ static const AdjKernels* adj_entry() {
       (const void*)k_adj_final<Real, FFCA_I, J, true>,
       AdjShape<FFCA_I, J, false>::NV,
   };
+#endif
   return &k;
 }
 

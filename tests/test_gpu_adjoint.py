@@ -73,7 +73,8 @@ def _compare(prec, p, ref_loss, ref, got, p_zero=False):
         assert abs(loss - ref_loss) <= tol["loss_tf"] * p.N * p.F, (loss, ref_loss)
 
 
-SHAPES = [(4, 4, 5, 37), (3, 3, 4, 50), (2, 3, 3, 33), (1, 2, 3, 17), (4, 2, 3, 1030), (3, 6, 2, 64)]
+SHAPES = [(4, 4, 5, 37), (3, 3, 4, 50), (2, 3, 3, 33), (1, 2, 3, 17), (4, 2, 3, 1030), (3, 6, 2, 64),
+          (8, 6, 3, 61), (8, 3, 2, 300), (8, 2, 2, 45)]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -93,6 +94,29 @@ def test_wiener_se_gradient_matches_oracle(prec, shape):
     got = _gpu_grads(p, prec, se=True)
     _compare(prec, p, adj.wiener_se(p.y, p.x, p.v0, p.lam0, p.P0),
              adj.wiener_se_grad(p.y, p.x, p.v0, p.lam0, p.P0), got, p_zero=(I == 1))
+
+
+@pytest.mark.parametrize("se", [False, True])
+def test_large_array_gradients_match_central_differences(se):
+    """I = 8, J = 6 (the large-array shape, eight threads per unit) on a
+    16-frame slice: FP64 GPU gradients against central differences of the
+    oracle's loss along random directions."""
+    p = make_problem(8, 6, 3, 16, seed=78, keep_images=True, alpha=0.2, kappa=50.0)
+    loss, gv, gl, gP = _gpu_grads(p, "fp64", se=se)
+    if se:
+        L = lambda v, lam, P: adj.wiener_se(p.y, p.x, v, lam, P)  # noqa: E731
+    else:
+        L = lambda v, lam, P: adj.nll(p.y, v, lam, P)  # noqa: E731
+    rng = np.random.default_rng(6)
+    h = 1e-6
+    for _ in range(3):
+        dv = p.v0 * rng.standard_normal(p.v0.shape)
+        dl = p.lam0 * rng.standard_normal(p.lam0.shape)
+        dP = rng.standard_normal(p.P0.shape) + 1j * rng.standard_normal(p.P0.shape)
+        fd = (L(p.v0 + h * dv, p.lam0 + h * dl, p.P0 + h * dP)
+              - L(p.v0 - h * dv, p.lam0 - h * dl, p.P0 - h * dP)) / (2 * h)
+        pred = np.sum(gv * dv) + np.sum(gl * dl) + 2.0 * np.real(np.sum(gP.conj() * dP))
+        assert abs(fd - pred) <= 1e-6 * abs(fd), (fd, pred)
 
 
 @pytest.mark.parametrize("se", [False, True])

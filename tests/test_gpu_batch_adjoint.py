@@ -84,14 +84,14 @@ def _check(prec, probs, got, se):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("I,J", [(4, 3), (3, 3), (2, 2), (1, 2), (4, 4)])
+@pytest.mark.parametrize("I,J", [(4, 3), (3, 3), (2, 2), (1, 2), (4, 4), (8, 6)])
 def test_batch_nll_gradient_matches_oracle(prec, I, J):
     probs = _batch(I, J, 3, 500 + 10 * I + J, se=False)
     _check(prec, probs, _run(probs, prec, se=False), se=False)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("I,J", [(4, 3), (3, 3), (2, 2), (1, 2)])
+@pytest.mark.parametrize("I,J", [(4, 3), (3, 3), (2, 2), (1, 2), (8, 3)])
 def test_batch_wiener_se_gradient_matches_oracle(prec, I, J):
     probs = _batch(I, J, 3, 600 + 10 * I + J, se=True)
     _check(prec, probs, _run(probs, prec, se=True), se=True)
