@@ -55,7 +55,7 @@
  *    warps' sums in double-float (TwoSum), and the partial sums in FP64.
  *
  * Supported shapes: I in {1, 2, 3, 4, 8}, 1 <= J <= 6 (FFCA_ERR_UNSUPPORTED
- * otherwise; Newton's method for P takes I <= 4 only), N >= 1, F >= 0 (F == 0 is a
+ * otherwise), N >= 1, F >= 0 (F == 0 is a
  * no-op).
  */
 #ifndef FFCA_H
@@ -176,7 +176,8 @@ ffca_status ffca_inversion_count(ffca_ctx* ctx, unsigned long long* count);
  * Hessian and gradient of L2 / N, Pi the projector on those directions, Q' =
  * 1 - Pi) and moving P by mu s; two inversions per step (P and the system).
  * It converges quadratically near a maximum and is not globally convergent
- * (mu damps it).  Compiled for I <= 4 (FFCA_ERR_UNSUPPORTED at I = 8). */
+ * (mu damps it).  At I = 8 one CTA per problem holds the 128 x 128 system
+ * in shared memory (a thread per column). */
 typedef enum {
   FFCA_P_FIXED_POINT = 0,
   FFCA_P_GRADIENT = 1,
@@ -188,8 +189,8 @@ typedef enum {
 /* Select the update of P for later iterations of a single or batch context.
  * mu: step size, finite and > 0 for the gradient methods and Newton's
  * (ignored for the fixed point and the EM).  Drops a captured graph.
- * FFCA_ERR_ARG for an unknown method or an invalid mu, FFCA_ERR_UNSUPPORTED
- * for Newton at I = 8 (the context keeps its previous choice).  With the EM, ffca_timing_read
+ * FFCA_ERR_ARG for an unknown method or an invalid mu (the context keeps
+ * its previous choice).  With the EM, ffca_timing_read
  * counts its streaming pass as FFCA_KERNEL_ESTEP and its per-problem step as
  * FFCA_KERNEL_PSOLVE, and ffca_batch_autotune tunes the EM pass on pass A's
  * candidates.  The allocation-free call always uses the fixed point. */

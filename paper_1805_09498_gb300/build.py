@@ -24,8 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
-I_VALUES = (1, 2, 3, 4, 8)      # FastFCA-AS, conventional FCA, adjoint, normal EM
-I_VALUES_SMALL = (1, 2, 3, 4)   # Newton
+I_VALUES = (1, 2, 3, 4, 8)
 
 
 def _nvcc():
@@ -42,7 +41,7 @@ def _units():
              ("ffca_mask.cu", "ffca_mask.o", [])]
     for part in (0, 1, 2, 3, 4):  # FastFCA-AS, conventional FCA, adjoint, normal EM, Newton
         for prec in (0, 1):
-            for i in (I_VALUES if part in (0, 1, 2, 3) else I_VALUES_SMALL):
+            for i in I_VALUES:
                 units.append(("ffca_inst.cu", f"ffca_inst_k{part}_p{prec}_i{i}.o",
                               [f"-DFFCA_PART={part}", f"-DFFCA_PREC={prec}", f"-DFFCA_I={i}"]))
     return units

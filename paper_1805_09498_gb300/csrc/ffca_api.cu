@@ -155,6 +155,10 @@ ffca_status query_occupancy(const FastKernels* k, Occupancy* o) {
        !cuda_ok(cudaFuncSetAttribute(k->psolve_em, cudaFuncAttributeMaxDynamicSharedMemorySize, k->em_solve_smem),
                 "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, EM step)")))
     return FFCA_ERR_CUDA;
+  if (k->pnewton && k->newton_smem > 0 &&
+      !cuda_ok(cudaFuncSetAttribute(k->pnewton, cudaFuncAttributeMaxDynamicSharedMemorySize, k->newton_smem),
+               "cudaFuncSetAttribute(MaxDynamicSharedMemorySize, Newton step)"))
+    return FFCA_ERR_CUDA;
   if (k->solve_smem > 0)
     for (const void* fn : {k->psolve, k->prep})
       if (!cuda_ok(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k->solve_smem),
@@ -378,6 +382,10 @@ int p_step_grid(const ffca_ctx* c, const FastArgs& b) {
   return (c->d.F + G - 1) / G + (b.trace ? 1 : 0);
 }
 
+// Threads and dynamic shared memory of the P step's blocks.
+int p_step_threads(const ffca_ctx* c) { return c->pmode == kPNewton ? c->kern->newton_threads : 32; }
+size_t p_step_smem(const ffca_ctx* c) { return c->pmode == kPNewton ? c->kern->newton_smem : c->kern->solve_smem; }
+
 // The P step of the context's update of P (after pass B).
 const void* p_step_kernel(const ffca_ctx* c) {
   if (c->pmode == kPNewton) return c->kern->pnewton;
@@ -492,7 +500,7 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
     if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, wcov_grid(c, b.part), wcov_threads(c), b,
                      c->kern->wcov_smem)) != FFCA_OK)
       return st;
-    if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem)) != FFCA_OK) return st;
+    if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), p_step_threads(c), b, p_step_smem(c))) != FFCA_OK) return st;
   }
   return FFCA_OK;
 }
@@ -702,7 +710,7 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
       if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, wcov_grid(c, b.part), wcov_threads(c), b,
                       c->kern->wcov_smem)) != FFCA_OK)
         return st;
-      if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem)) != FFCA_OK)
+      if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), p_step_threads(c), b, p_step_smem(c))) != FFCA_OK)
         return st;
     } else if (ll_trace) {
       FastArgs a = pass_a_args(c, slot);
@@ -1252,7 +1260,7 @@ ffca_status ffca_batch_autotune(ffca_batch_ctx* c, int rounds, int* cand_a, int*
                     c->kern->wcov_smem);
       cudaEventRecord(ev[q][2], c->stream);
       if (st == FFCA_OK)
-        st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), 32, b, c->kern->solve_smem);
+        st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), p_step_threads(c), b, p_step_smem(c));
     }
     if (st == FFCA_OK && !cuda_ok(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize")) st = FFCA_ERR_CUDA;
     for (int q = 0; q < kCands && st == FFCA_OK; ++q) {

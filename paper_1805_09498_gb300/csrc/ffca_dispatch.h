@@ -28,7 +28,9 @@ struct FastKernels {
   int em_solve_smem;         // dynamic shared memory of psolve_em
   int em_nv;                 // sums per slot of estep_em
   int em_groups;             // pipeline groups per CTA of estep_em
-  const void* pnewton;       // the P step with Newton's method (one warp per problem; nullptr for I > 4)
+  const void* pnewton;       // the P step with Newton's method (one block per problem)
+  int newton_threads;        // its block: a warp for I <= 4, 2 I^2 + 32 threads for I = 8
+  int newton_smem;           // its dynamic shared memory (the I = 8 system)
   int wcov_groups;           // pipeline groups per CTA of pass B (stream_groups: pass A)
   int wcov_smem;             // dynamic shared memory of pass B (stream_smem: pass A)
   // iterations with each problem resident in shared memory (nullptr for I > 4)
@@ -86,25 +88,22 @@ FFCA_DECLARE_TABLE(1, 4)
 FFCA_DECLARE_TABLE(1, 8)
 #undef FFCA_DECLARE_TABLE
 
-// The normal EM kernels of one precision (I <= 4 and 8) and the Newton
-// kernels (I <= 4), compiled in translation units of their own.
-#define FFCA_DECLARE_EM(P, I) \
-  const void* em_estep_p##P##_i##I(int J); \
-  const void* em_psolve_p##P##_i##I(int J);
+// The normal EM and Newton kernels of one precision, compiled in
+// translation units of their own.
 #define FFCA_DECLARE_ALT(P, I) \
-  FFCA_DECLARE_EM(P, I) \
+  const void* em_estep_p##P##_i##I(int J); \
+  const void* em_psolve_p##P##_i##I(int J); \
   const void* newton_p##P##_i##I(int J);
 FFCA_DECLARE_ALT(0, 1)
 FFCA_DECLARE_ALT(0, 2)
 FFCA_DECLARE_ALT(0, 3)
 FFCA_DECLARE_ALT(0, 4)
-FFCA_DECLARE_EM(0, 8)
+FFCA_DECLARE_ALT(0, 8)
 FFCA_DECLARE_ALT(1, 1)
 FFCA_DECLARE_ALT(1, 2)
 FFCA_DECLARE_ALT(1, 3)
 FFCA_DECLARE_ALT(1, 4)
-FFCA_DECLARE_EM(1, 8)
+FFCA_DECLARE_ALT(1, 8)
 #undef FFCA_DECLARE_ALT
-#undef FFCA_DECLARE_EM
 
 }  // namespace ffca

@@ -65,7 +65,9 @@ static const FastKernels* table_entry() {
   // their own (FFCA_PART 3 and 4), so that they build in parallel
   const void* estep_em = nullptr;
   const void* psolve_em = nullptr;
-  const void* pnewton = nullptr;
+  const void* pnewton = FFCA_CAT(newton_p, FFCA_PREC, _i, FFCA_I)(J);
+  const int newton_threads = FFCA_I > 4 ? NewtonBig<FFCA_I>::THREADS : 32;
+  const int newton_smem = FFCA_I > 4 ? NewtonBig<FFCA_I>::BYTES : 0;
   int em_smem = 0, em_solve_smem = 0, em_nv = 0, em_groups = 1;
   const void* resident = nullptr;
   int res_bpf = 0, res_max = 0;
@@ -79,7 +81,6 @@ static const FastKernels* table_entry() {
   resident = (const void*)k_resident<Real, FFCA_I, J>;
   res_bpf = ResShape<Real, FFCA_I, J>::BYTES_PER_FRAME;
   res_max = ResShape<Real, FFCA_I, J>::max_frames();
-  pnewton = FFCA_CAT(newton_p, FFCA_PREC, _i, FFCA_I)(J);
 #endif
   static const FastKernels k = {
       Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
@@ -103,6 +104,8 @@ static const FastKernels* table_entry() {
       em_nv,
       em_groups,
       pnewton,
+      newton_threads,
+      newton_smem,
       WcovGroups<Real, FFCA_I, J>::value,
       WcovGroups<Real, FFCA_I, J>::value * Tile<Real, FFCA_I, J, WcovGroups<Real, FFCA_I, J>::value>::GROUP,
       resident,
@@ -245,7 +248,11 @@ const void* FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_sele
 #if FFCA_PART == 4
 // one kernel for every J (J is read from the arguments)
 const void* FFCA_CAT(newton_p, FFCA_PREC, _i, FFCA_I)(int J) {
+#if FFCA_I > 4
+  return (J >= 1 && J <= 6) ? (const void*)k_psolve_newton_big<Real, FFCA_I> : nullptr;
+#else
   return (J >= 1 && J <= 6) ? (const void*)k_psolve_newton<Real, FFCA_I> : nullptr;
+#endif
 }
 #endif
 

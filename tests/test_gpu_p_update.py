@@ -1,6 +1,6 @@
 """GPU parity of the alternative updates of P (Sec. 4.6: the gradient and
-natural gradient methods, the normal EM (I <= 4 and 8) and Newton's method
-(I <= 4), ffca_set_p_update) against the
+natural gradient methods, the normal EM and Newton's method,
+ffca_set_p_update) against the
 FP64 oracle, for single mixtures at every compiled I, with K > 1 steps, on
 batches and under graph replay; the inversion counts and the argument checks.
 
@@ -343,9 +343,25 @@ def test_newton_inversion_count_and_checks():
     q = make_problem(8, 6, 2, 40, seed=8, alpha=0.2, kappa=50.0)
     yd, vd, ld_, Pd, N = ffca.to_device(q.y, q.v0, q.lam0, q.P0, prec="mixed")
     e8 = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
-    with pytest.raises(ffca.FFCAError):
-        e8.set_p_update("newton", 1.0)
+    e8.set_p_update("newton", 1.0)
+    e8.iterate(1, trace=False)
+    assert e8.inversion_count() == 2 * 2
     e8.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("I,J,F,N,fpi,mu,K", [(8, 6, 2, 400, 20, 1.0, 1), (8, 3, 3, 300, 20, 1.0, 1),
+                                              (8, 6, 2, 400, 20, 0.5, 2)])
+def test_newton_large_array_matches_oracle(prec, I, J, F, N, fpi, mu, K):
+    """Newton's method at I = 8 (a CTA per problem, the 128 x 128 system in
+    shared memory) after fixed-point iterations, in cases where the oracle's
+    L2 rises, against the oracle."""
+    p = make_problem(I, J, F, N, seed=600 + 10 * I + J, alpha=0.2, kappa=50.0)
+    v, lam, P, _ = ffa.iterate(p.y, p.v0, p.lam0, p.P0, fpi, counter=OpCounter())
+    ref = ffa.iterate(p.y, v, lam, P, 3, K=K, counter=OpCounter(), p_update="newton", mu=mu)
+    assert np.all(np.diff(ref[3]) > 0)
+    got = run_gpu(p.y, v, lam, P, 3, prec, K=K, p_update="newton", mu=mu)
+    _compare(prec, ref, got, N, F)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
