@@ -226,8 +226,8 @@ ffca_status ffca_mask_init(ffca_ctx* ctx, const void* masks, int sweeps, double 
  * its data from HBM once per launch instead of twice per iteration and an
  * iteration costs no launch.  Same results as the streaming kernels up to
  * the order of the floating-point sums; the trace as ffca_iterate.  For
- * I <= 4 and problems of at most the frames the shared memory holds (about
- * 5600 frames at I = J = 3 in the mixed precision, half in FP64):
+ * problems of at most the frames the shared memory holds (about 5600 frames
+ * at I = J = 3 in the mixed precision, 2300 at I = 8, J = 6; half in FP64):
  * FFCA_ERR_UNSUPPORTED otherwise (the context keeps streaming).  With another
  * update of P selected the iterations stream as usual.  Drops a captured
  * graph. */

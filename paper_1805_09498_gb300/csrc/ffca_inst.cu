@@ -77,11 +77,9 @@ static const FastKernels* table_entry() {
   em_smem = em_groups * Tile<Real, FFCA_I, J, EmGroups<Real, FFCA_I, J>::value>::GROUP;
   em_solve_smem = EmShape<FFCA_I, J>::SMEM;
   em_nv = EmShape<FFCA_I, J>::NV;
-#if FFCA_I <= 4
   resident = (const void*)k_resident<Real, FFCA_I, J>;
   res_bpf = ResShape<Real, FFCA_I, J>::BYTES_PER_FRAME;
   res_max = ResShape<Real, FFCA_I, J>::max_frames();
-#endif
   static const FastKernels k = {
       Tile<Real, FFCA_I, J>::G * Tile<Real, FFCA_I, J>::GROUP,
       StreamGroups<Real, FFCA_I, J>::value,

@@ -14,7 +14,8 @@
 //               new Lambda and the problem's L2 of the entering state (FP64),
 //               pass B (the outer product of each frame once, weighted into
 //               every V_i; two sub-passes of two V_i in FP64 at I = 4, one
-//               otherwise), then warp 0 runs the P step of k_psolve_ldl (L D L^H of V_i, the columns
+//               sub-pass per V_i at I = 8, one in all otherwise), then warp 0
+//               runs the P step of k_psolve_ldl (L D L^H of V_i, the columns
 //               V_i^{-1} [P^{-H}]_i, K sweeps, the inverse of the new P for
 //               ln|det P|^2 and the next P^{-H}).  At the end v, Lambda, P,
 //               P^{-H}, ln|det P|^2 and the pass-A table go back to global
@@ -82,9 +83,10 @@ template <typename T, int I, int J>
 struct ResShape {
   static constexpr int NVA = J * I + 2;  // Lambda sums, then the quadratic and log2 parts of L2
   static constexpr int NVB = I * I;      // V_i of one i (packed Hermitian)
-  // V_i summed together in one sub-pass of pass B (the FP64 I = 4 form takes
-  // two sub-passes of two, to keep its accumulators in registers)
-  static constexpr int IB = (sizeof(T) == 8 && I == 4) ? 2 : I;
+  // V_i summed together in one sub-pass of pass B, to keep the accumulators
+  // in registers: all I for I <= 4 (FP64 I = 4: two sub-passes of two), one
+  // at a time for I = 8 (64 sums each)
+  static constexpr int IB = I > 4 ? 1 : ((sizeof(T) == 8 && I == 4) ? 2 : I);
   // bytes of shared memory per frame
   static constexpr int BYTES_PER_FRAME = I * (int)sizeof(cpx<T>) + J * (int)sizeof(T);
   static constexpr int max_frames() { return (kResSmemBudget / BYTES_PER_FRAME) / 4 * 4; }

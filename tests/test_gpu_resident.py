@@ -70,7 +70,8 @@ def _compare(prec, ref, got, N, F, trace=True):
 
 
 SHAPES = [(3, 3, 5, 37), (2, 3, 4, 50), (1, 2, 3, 17), (4, 2, 3, 41), (3, 1, 2, 33), (2, 4, 3, 29),
-          (4, 3, 7, 301), (3, 3, 3, 1030), (3, 6, 2, 123), (4, 6, 2, 257), (2, 5, 3, 64)]
+          (4, 3, 7, 301), (3, 3, 3, 1030), (3, 6, 2, 123), (4, 6, 2, 257), (2, 5, 3, 64), (8, 6, 2, 300),
+          (8, 3, 3, 150)]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -177,10 +178,10 @@ def test_batch_matches_oracle(prec):
 
 
 def test_unsupported_forms():
-    """I = 8, or a problem longer than the shared memory holds, is refused
-    and the context keeps streaming; another update of P streams."""
+    """A problem longer than the shared memory holds is refused and the
+    context keeps streaming; another update of P streams."""
     from paper_1805_09498_gb300 import ffca
-    p = make_problem(8, 6, 2, 40, seed=8, alpha=0.2, kappa=50.0)
+    p = make_problem(8, 6, 2, 2400, seed=8, alpha=0.2, kappa=50.0)
     yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="mixed")
     est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
     with pytest.raises(ffca.FFCAError) as e:
