@@ -207,3 +207,41 @@ def test_unsupported_forms():
     c = ffca.ffca_timing_read(est.ctx)
     assert c["resident"][1] == 0 and c["estep"][1] == 2
     est.close()
+
+
+@pytest.mark.parametrize("I", [3, 8])
+def test_singular_bin_is_reported(I):
+    """A frequency whose mixture is all zeros has singular V_i: the resident
+    form reports FFCA_ERR_SINGULAR at that frequency, as the streaming one
+    does."""
+    from paper_1805_09498_gb300 import ffca
+    kw = dict(alpha=0.2, kappa=50.0) if I == 8 else {}
+    p = make_problem(I, 3, 4, 60, seed=16, **kw)
+    p.y[:, 2, :] = 0.0
+    yd, vd, ld_, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec="fp64")
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=N)
+    est.set_resident(True)
+    with pytest.raises(ffca.FFCAError) as ei:
+        est.iterate(1)
+    assert ei.value.status == 4 and ei.value.frequency == 2
+    est.close()
+
+
+@pytest.mark.parametrize("prec,N", [("mixed", 5688), ("fp64", 2844)])
+def test_largest_problem_that_fits(prec, N):
+    """The longest problem the shared memory holds at I = J = 3 (200 KB at
+    36 bytes per frame in the mixed precision, 72 in FP64), two iterations,
+    against the oracle; one frame more is refused."""
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(3, 3, 2, N, seed=17)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter())
+    got = _run(p, 2, prec)
+    _compare(prec, ref, got, N, 2)
+    assert got["counts"]["resident"][1] == 1
+    q = make_problem(3, 3, 2, N + 1, seed=17)
+    yd, vd, ld_, Pd, n1 = ffca.to_device(q.y, q.v0, q.lam0, q.P0, prec=prec)
+    est = ffca.FastFCA(yd, vd, ld_, Pd, N=n1)
+    with pytest.raises(ffca.FFCAError) as e:
+        est.set_resident(True)
+    assert e.value.status == 7
+    est.close()
