@@ -1142,6 +1142,8 @@ def run_case(a):
         est = ffca.FastFCA(yd, vd, lamd, Pd, N=N)
         if a.case_p_update != "fixed_point":
             est.set_p_update(a.case_p_update, a.case_mu)
+        if a.case_resident:
+            est.set_resident(True)
         tr = est.iterate(a.case_iters)
         est.wiener()
         torch.cuda.synchronize()
@@ -1237,6 +1239,8 @@ def main():
     ap.add_argument("--case-batch", type=int, default=0, help="mixtures of a batch (0: one mixture)")
     ap.add_argument("--case-p-update", default="fixed_point")
     ap.add_argument("--case-mu", type=float, default=0.0)
+    ap.add_argument("--case-resident", action="store_true",
+                    help="iterate with each problem resident on chip (ffca_set_resident)")
     ap.add_argument("--case-stft", action="store_true",
                     help="the STFT of I channels of N frames and the inverse of I spectra instead")
     args = ap.parse_args()
