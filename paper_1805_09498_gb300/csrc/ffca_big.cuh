@@ -88,7 +88,7 @@ __device__ double gj_inverse_cols(cpx<double> (&a)[I], int g, int c) {
     for (int r = 0; r < I; ++r) col[r] = shfl_c(a[r], owner);
     const double d2 = cabs2(col[k]);
     det2 *= d2;
-    const double rd = 1.0 / d2;
+    const double rd = recip(d2);
     const cpx<double> inv = mk(col[k].re * rd, -col[k].im * rd);
     const bool piv = (c == k);
     const cpx<double> t = piv ? inv : cmul(a[k], inv);
@@ -126,7 +126,7 @@ __device__ bool ldl_factor(double (&dv)[I], cpx<double> (&lo)[I * (I - 1) / 2], 
   for (int k = 0; k < I; ++k) {
     const double d = dv[k];
     ok &= isfinite(d) && d > 0.0;
-    const double inv = 1.0 / d;
+    const double inv = recip(d);
     rd[k] = inv;
     cpx<double> l[I];
 #pragma unroll
@@ -195,7 +195,7 @@ __device__ double pinvh_cofactors(cpx<double> (&x)[I], int g, int c, bool& singu
   det = shfl_c(det, g * I);  // the expansion of lane (g, 0), for every lane of the problem
   const double d2 = cabs2(det);
   singular |= !(d2 > 0.0) || !isfinite(d2);
-  const double inv = 1.0 / d2;
+  const double inv = recip(d2);
   const cpx<double> rdet = mk(det.re * inv, -det.im * inv);  // 1 / det
 #pragma unroll
   for (int r = 0; r < I; ++r) x[r] = cconj(cmul(C[r], rdet));
