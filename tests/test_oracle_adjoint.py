@@ -29,7 +29,7 @@ def _directional(loss, grads, args, rng, h=1e-6):
     return fd, pred
 
 
-SHAPES = [(1, 1, 2, 6), (2, 1, 3, 7), (2, 3, 2, 9), (3, 2, 2, 8), (3, 3, 3, 5), (4, 3, 2, 6), (4, 4, 2, 5)]
+SHAPES = [(1, 1, 2, 6), (2, 1, 3, 7), (2, 3, 2, 9), (3, 2, 2, 8), (3, 3, 3, 5), (4, 3, 2, 6), (4, 4, 2, 5), (8, 3, 2, 6)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)

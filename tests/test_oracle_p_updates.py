@@ -156,7 +156,7 @@ def _real(D):
     return np.concatenate([D.real.reshape(F, -1), D.imag.reshape(F, -1)], axis=1)
 
 
-@pytest.mark.parametrize("shape", [(3, 3, 2, 60), (2, 3, 3, 40), (4, 2, 2, 80)])
+@pytest.mark.parametrize("shape", [(3, 3, 2, 60), (2, 3, 3, 40), (4, 2, 2, 80), (8, 3, 1, 80)])
 def test_newton_step_zeroes_the_linearised_gradient(shape):
     """The Newton step D makes the second-order model stationary in every
     direction that changes L2: the first-order change of the gradient along
@@ -215,7 +215,7 @@ def test_newton_inversion_count():
 
 
 # ------------------------------------------------------- the normal EM for P
-@pytest.mark.parametrize("shape", [(3, 3, 2, 7), (2, 3, 2, 6), (4, 2, 1, 9), (1, 2, 2, 5)])
+@pytest.mark.parametrize("shape", [(3, 3, 2, 7), (2, 3, 2, 6), (4, 2, 1, 9), (1, 2, 2, 5), (8, 2, 1, 12)])
 def test_em_matrices_are_the_dense_posterior_moments(shape):
     """W_i / (J N) of the normal EM from the transformed posterior equals the
     sum over n, j of the dense posterior second moments E[x_j x_j^H | y] =
