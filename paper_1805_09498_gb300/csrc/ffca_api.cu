@@ -375,10 +375,12 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
 
-// Blocks of the P step: one warp per 32 / I problems (Newton: one warp per
-// problem), plus the trace's block.
+// Blocks of the P step: one warp per 32 / I problems (Newton and the fixed
+// point at I = 8: one block per problem), plus the trace's block.
 int p_step_grid(const ffca_ctx* c, const FastArgs& b) {
-  const int G = c->pmode == kPNewton ? 1 : 32 / c->d.I;
+  const int G = c->pmode == kPNewton                                ? 1
+                : (c->pmode == kPGradient || c->pmode == kPNatural) ? 32 / c->d.I
+                                                                    : c->kern->psolve_problems;
   return (c->d.F + G - 1) / G + (b.trace ? 1 : 0);
 }
 

@@ -11,6 +11,7 @@
 #include "ffca_fca.cuh"
 #include "ffca_fca_big.cuh"
 #include "ffca_newton.cuh"
+#include "ffca_psolve_wide.cuh"
 #include "ffca_resident.cuh"
 #include "ffca_stream.cuh"
 
@@ -38,7 +39,8 @@ using Real = float;
 #if FFCA_PART == 0
 // The P step by Gauss-Jordan and LDL^H (k_psolve_ldl, which carries P^{-H}
 // from one step to the next) from FFCA_LDL_MIN_I microphones up; below it
-// the cofactor forms of k_psolve.
+// the cofactor forms of k_psolve.  For I > 4 the fixed point runs
+// k_psolve_wide (one warp per problem, the same P^{-H} bits).
 #ifndef FFCA_LDL_MIN_I
 #define FFCA_LDL_MIN_I 3
 #endif
@@ -50,7 +52,11 @@ static const FastKernels* table_entry() {
   const void* pgrad;
   const void* prep;
   const void* wiener;
-  if constexpr (LDL) {
+  if constexpr (BIG) {  // one warp per problem
+    psolve = (const void*)k_psolve_wide<Real, FFCA_I, J>;
+    pgrad = (const void*)k_psolve_ldl<Real, FFCA_I, J, true>;
+    prep = (const void*)k_prep_gj<Real, FFCA_I, J>;
+  } else if constexpr (LDL) {
     psolve = (const void*)k_psolve_ldl<Real, FFCA_I, J>;
     pgrad = (const void*)k_psolve_ldl<Real, FFCA_I, J, true>;
     prep = (const void*)k_prep_gj<Real, FFCA_I, J>;
@@ -109,6 +115,7 @@ static const FastKernels* table_entry() {
       resident,
       res_bpf,
       res_max,
+      BIG ? 1 : 32 / FFCA_I,
   };
   return &k;
 }

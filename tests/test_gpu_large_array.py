@@ -65,6 +65,20 @@ def test_trajectory_large_array(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_resumable_bit_exact_large_array(prec):
+    """2 + 2 iterations in two calls equal 4 in one, bit for bit: the P^{-H}
+    that the fixed-point step carries to the next step (one warp per problem
+    at I = 8) has the bits of the one a call recomputes from P at its start."""
+    p = make_problem(8, 6, 5, 300, seed=21, alpha=0.2, kappa=50.0)
+    a = run_gpu(p.y, p.v0, p.lam0, p.P0, 4, prec)
+    b1 = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec)
+    b = run_gpu(p.y, b1[0], b1[1], b1[2], 2, prec)
+    for x, z in zip(a[:3], b[:3]):
+        assert np.array_equal(x, z)
+    assert np.array_equal(a[3][2:], b[3])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_loglik_and_wiener_large_array(prec):
     import torch
     from paper_1805_09498_gb300 import ffca
