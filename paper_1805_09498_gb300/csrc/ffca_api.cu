@@ -375,22 +375,35 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
 
-// Blocks of the P step: one warp per 32 / I problems (Newton and the fixed
-// point at I = 8: one block per problem), plus the trace's block.
+// The fixed-point step with one warp per problem (k_psolve_wide) up to this
+// many problems.  Its FP64 instructions per problem are 1.5x (I = 8) to 6x
+// (I = 3) those of the packed form (32 / I problems per warp), but the
+// packed form's few warps leave most FP64 units idle: per the instruction
+// counts of the two, the wide form is the faster up to about 2000 problems.
+constexpr int kWideMaxProblems = 2048;
+
+bool p_step_wide(const ffca_ctx* c) {
+  return c->pmode == kPFixedPoint && c->kern->psolve_wide != nullptr && c->d.F <= kWideMaxProblems;
+}
+
+// Blocks of the P step: one warp per 32 / I problems (Newton and the wide
+// fixed point: one block per problem), plus the trace's block.
 int p_step_grid(const ffca_ctx* c, const FastArgs& b) {
-  const int G = c->pmode == kPNewton                                ? 1
-                : (c->pmode == kPGradient || c->pmode == kPNatural) ? 32 / c->d.I
-                                                                    : c->kern->psolve_problems;
+  const int G = (c->pmode == kPNewton || p_step_wide(c)) ? 1 : 32 / c->d.I;
   return (c->d.F + G - 1) / G + (b.trace ? 1 : 0);
 }
 
 // Threads and dynamic shared memory of the P step's blocks.
 int p_step_threads(const ffca_ctx* c) { return c->pmode == kPNewton ? c->kern->newton_threads : 32; }
-size_t p_step_smem(const ffca_ctx* c) { return c->pmode == kPNewton ? c->kern->newton_smem : c->kern->solve_smem; }
+size_t p_step_smem(const ffca_ctx* c) {
+  if (p_step_wide(c)) return 0;  // static shared memory only
+  return c->pmode == kPNewton ? c->kern->newton_smem : c->kern->solve_smem;
+}
 
 // The P step of the context's update of P (after pass B).
 const void* p_step_kernel(const ffca_ctx* c) {
   if (c->pmode == kPNewton) return c->kern->pnewton;
+  if (p_step_wide(c)) return c->kern->psolve_wide;
   return c->pmode == kPGradient || c->pmode == kPNatural ? c->kern->pgrad : c->kern->psolve;
 }
 

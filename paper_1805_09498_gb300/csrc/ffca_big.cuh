@@ -166,6 +166,31 @@ __device__ void ldl_solve(const cpx<double> (&lo)[I * (I - 1) / 2], const double
     }
 }
 
+// Complex arithmetic that the compiler may not contract or fuse: every
+// product and sum rounded as written.  The cofactor inverse below is formed
+// by kernels that lay out its terms differently (one lane per column, or
+// one lane per entry) and must agree bit for bit.
+__device__ inline cpx<double> cmul_rn(cpx<double> a, cpx<double> b) {
+  return mk(__fma_rn(a.re, b.re, -__dmul_rn(a.im, b.im)), __fma_rn(a.re, b.im, __dmul_rn(a.im, b.re)));
+}
+__device__ inline cpx<double> cadd_rn(cpx<double> a, cpx<double> b) {
+  return mk(__dadd_rn(a.re, b.re), __dadd_rn(a.im, b.im));
+}
+__device__ inline cpx<double> csub_rn(cpx<double> a, cpx<double> b) {
+  return mk(__dsub_rn(a.re, b.re), __dsub_rn(a.im, b.im));
+}
+__device__ inline double cabs2_rn(cpx<double> a) { return __fma_rn(a.re, a.re, __dmul_rn(a.im, a.im)); }
+
+// The 2 x 2 minor a d - b c of a 3 x 3 cofactor, and the cofactor inverse's
+// final values from the cofactor C and det P (rounded as written).
+__device__ inline cpx<double> minor2_rn(cpx<double> a, cpx<double> b, cpx<double> c, cpx<double> d) {
+  return csub_rn(cmul_rn(a, d), cmul_rn(b, c));
+}
+__device__ inline cpx<double> inv_from_cofactor(cpx<double> C, cpx<double> det, double rd2) {
+  const cpx<double> rdet = mk(__dmul_rn(det.re, rd2), -__dmul_rn(det.im, rd2));  // 1 / det
+  return cconj(cmul_rn(C, rdet));
+}
+
 // Column c of P^{-H} and |det P|^2 from the columns of P (lane (g, c) holds
 // column c of P in x[]), for I <= 4 by cofactors: one division instead of I
 // dependent pivot steps.  The lane gathers P with its columns rotated,
@@ -188,17 +213,22 @@ __device__ double pinvh_cofactors(cpx<double> (&x)[I], int g, int c, bool& singu
   cpx<double> det = mk(0.0, 0.0);
 #pragma unroll
   for (int r = 0; r < I; ++r) {
-    const cpx<double> m = minor_det<I>(A, r, 0);
+    cpx<double> m;
+    if constexpr (I == 3) {
+      const int r0 = r == 0 ? 1 : 0, r1 = r == 2 ? 1 : 2;  // rows of the minor, columns 1 and 2
+      m = minor2_rn(A[r0][1], A[r0][2], A[r1][1], A[r1][2]);
+    } else {
+      m = minor_det<I>(A, r, 0);
+    }
     C[r] = ((((r + c) & 1) != 0) != flip) ? mk(-m.re, -m.im) : m;
-    det = cadd(det, cmul(A[r][0], C[r]));
+    det = cadd_rn(det, cmul_rn(A[r][0], C[r]));
   }
   det = shfl_c(det, g * I);  // the expansion of lane (g, 0), for every lane of the problem
-  const double d2 = cabs2(det);
+  const double d2 = cabs2_rn(det);
   singular |= !(d2 > 0.0) || !isfinite(d2);
   const double inv = recip(d2);
-  const cpx<double> rdet = mk(det.re * inv, -det.im * inv);  // 1 / det
 #pragma unroll
-  for (int r = 0; r < I; ++r) x[r] = cconj(cmul(C[r], rdet));
+  for (int r = 0; r < I; ++r) x[r] = inv_from_cofactor(C[r], det, inv);
   return (d2 > 0.0 && isfinite(d2)) ? d2 : 0.0;
 }
 

@@ -37,7 +37,7 @@ struct FastKernels {
   const void* resident;
   int res_bytes_per_frame;   // shared memory per frame of a problem
   int res_max_frames;        // frames of the largest problem it takes
-  int psolve_problems;       // problems per 32-thread block of psolve (32 / I; 1 for the wide form at I = 8)
+  const void* psolve_wide;   // the fixed-point step with one warp per problem (I = 3 and 8; else nullptr)
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

@@ -39,8 +39,9 @@ using Real = float;
 #if FFCA_PART == 0
 // The P step by Gauss-Jordan and LDL^H (k_psolve_ldl, which carries P^{-H}
 // from one step to the next) from FFCA_LDL_MIN_I microphones up; below it
-// the cofactor forms of k_psolve.  For I > 4 the fixed point runs
-// k_psolve_wide (one warp per problem, the same P^{-H} bits).
+// the cofactor forms of k_psolve.  At I = 3 and 8 the fixed point of up to
+// kWideMaxProblems problems runs k_psolve_wide (one warp per problem, the
+// same P^{-H} bits).
 #ifndef FFCA_LDL_MIN_I
 #define FFCA_LDL_MIN_I 3
 #endif
@@ -52,11 +53,7 @@ static const FastKernels* table_entry() {
   const void* pgrad;
   const void* prep;
   const void* wiener;
-  if constexpr (BIG) {  // one warp per problem
-    psolve = (const void*)k_psolve_wide<Real, FFCA_I, J>;
-    pgrad = (const void*)k_psolve_ldl<Real, FFCA_I, J, true>;
-    prep = (const void*)k_prep_gj<Real, FFCA_I, J>;
-  } else if constexpr (LDL) {
+  if constexpr (LDL) {
     psolve = (const void*)k_psolve_ldl<Real, FFCA_I, J>;
     pgrad = (const void*)k_psolve_ldl<Real, FFCA_I, J, true>;
     prep = (const void*)k_prep_gj<Real, FFCA_I, J>;
@@ -65,6 +62,8 @@ static const FastKernels* table_entry() {
     pgrad = (const void*)k_psolve<Real, FFCA_I, J, true>;
     prep = (const void*)k_prep<Real, FFCA_I, J>;
   }
+  const void* psolve_wide = nullptr;
+  if constexpr (FFCA_I == 3 || FFCA_I == 8) psolve_wide = (const void*)k_psolve_wide<Real, FFCA_I, J>;
   if constexpr (BIG) wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
   else wiener = (const void*)k_wiener<Real, FFCA_I, J>;
   // the normal EM and Newton kernels are compiled in translation units of
@@ -115,7 +114,7 @@ static const FastKernels* table_entry() {
       resident,
       res_bpf,
       res_max,
-      BIG ? 1 : 32 / FFCA_I,
+      psolve_wide,
   };
   return &k;
 }

@@ -1,30 +1,35 @@
-// The P step of Eq. FPI for eight microphones with one warp per problem.
+// The P step of Eq. FPI with one warp per problem, for I = 3 and I = 8.
 //
 // An FP64 warp instruction occupies its SM sub-partition's FP64 unit for 64
 // cycles on this part (2 FP64 FMAs per clock per SM, 4 sub-partitions), with
-// any number of active lanes.  The lane-per-column form (k_psolve_ldl: four
-// problems per warp, each lane factoring and solving its own 8 x 8 V_i)
-// issues about 1500 FP64 instructions per warp on 130 warps for 513
-// problems: one warp per SM, three of every four sub-partitions idle.  Here
-// each problem has a warp of its own, lane (i, q) = (lane % 8, lane / 8),
-// and the work inside each matrix is spread over the lanes:
+// any number of active lanes.  The packed forms (k_psolve_ldl: 32 / I
+// problems per warp, lane (g, i) factoring and solving its own V_i) issue
+// about 1500 (I = 8) or 250 (I = 3) FP64 instructions per warp on 130 or 52
+// warps for 513 problems: one warp per SM at most, three of every four
+// sub-partitions idle, the time set by one warp's dependent chain.  Here
+// each problem has a warp of its own, lane (i, q) = (lane % I, lane / I) for
+// q < Q (Q = 4 at I = 8, 3 at I = 3; the other lanes only join the
+// shuffles), and the work inside each matrix is spread over the lanes:
 //
-//   L D L^H of V_i   the four lanes q of V_i share the entries of each
-//                    step's trailing triangle (row-major order, entry
-//                    q + 4 m); the matrices live in shared memory;
+//   L D L^H of V_i   the Q lanes of V_i share the entries of each step's
+//                    trailing triangle (row-major order, entry q + Q m);
+//                    the matrices live in shared memory;
 //   the solves       V_i p_i = [P^{-H}]_i, rows of each substitution step
-//                    over the four lanes;
-//   P^{-H}           Gauss-Jordan with partial pivoting on P^H, lane (c, h)
-//                    holding rows h and h + 4 of column c (gj_inverse_wide):
-//                    every entry takes the same operations, in the same
-//                    order, as in gj_inverse_cols (the routine that k_prep_gj
-//                    and the other P updates use), so the P^{-H} carried to
-//                    the next step has the same bits as the one recomputed
-//                    from P at the start of a call.
+//                    over the Q lanes;
+//   P^{-H}           I = 8: Gauss-Jordan with partial pivoting on P^H, lane
+//                    (c, h) holding rows h and h + 4 of column c
+//                    (gj_inverse_wide8); I = 3: cofactors, one per lane
+//                    (pinvh_wide3).  Every entry takes the same operations,
+//                    in the same order, as in gj_inverse_cols and
+//                    pinvh_cofactors (the routines of k_prep_gj and the
+//                    other P updates), so the P^{-H} carried to the next
+//                    step has the same bits as the one recomputed from P at
+//                    the start of a call.
 //
-// So a warp issues about a third of the FP64 instructions of the
-// lane-per-column form, and the 513 warps of a 513-problem step use every
-// sub-partition of the GPU.
+// A warp issues fewer FP64 instructions than a packed warp, on shorter
+// chains, and the 513 warps of a 513-problem step use every sub-partition.
+// Per problem the FP64 work is larger, so the packed forms stay in use for
+// many problems (the host picks by the problem count).
 #pragma once
 
 #include "ffca_big.cuh"
@@ -33,12 +38,12 @@ namespace ffca {
 
 template <int I>
 struct WideP {
-  static_assert(I == 8, "the wide P step is laid out for I = 8");
-  static constexpr int Q = 32 / I;         // lanes per matrix
-  static constexpr int VS = I * I + 1;     // stride of one V_i (complex entries; the pad skews the banks)
-  static constexpr int XS = I + 1;         // stride of one vector
-  static constexpr int NV = I * I * I;     // values per slot of pass B's partial sums
-  static constexpr int PAIRS = I * (I - 1) / 2;
+  static_assert(I == 3 || I == 8, "the wide P step is laid out for I = 3 and I = 8");
+  static constexpr int Q = I == 8 ? 4 : I;   // lanes per matrix (lanes I Q and up idle)
+  static constexpr int R = (I + Q - 1) / Q;  // rows of a column per lane (2 at I = 8, 1 at I = 3)
+  static constexpr int VS = I * I + 1;       // stride of one V_i (complex entries; the pad skews the banks)
+  static constexpr int XS = I + 1;           // stride of one vector
+  static constexpr int NV = I * I * I;       // values per slot of pass B's partial sums
 };
 
 // Entry e of a lower triangle (diagonal included) in row-major order:
@@ -143,24 +148,55 @@ __device__ inline double gj_inverse_wide8(cpx<double>& a0, cpx<double>& a1, int 
   return (det2 > 0.0 && isfinite(det2)) ? det2 : 0.0;
 }
 
-// P^{-H} of the P whose column i is sX[i][0 .. 7], and |det P|^2: lane
-// (c, h) gathers rows h, h + 4 of column c of P^H (conj(P[c][r])), inverts,
-// and leaves (P^{-H})[h][c], [h + 4][c] in q0, q1.
-__device__ inline double pinvh_wide8(const cpx<double> (*sX)[WideP<8>::XS], int c, int h, cpx<double>& q0,
-                                     cpx<double>& q1) {
-  q0 = cconj(sX[h][c]);
-  q1 = cconj(sX[h + 4][c]);
-  return gj_inverse_wide8(q0, q1, c, h);
+// Column c of P^{-H} and |det P|^2 for I = 3 by cofactors, lane (c, r) =
+// (lane % 3, lane / 3) for lanes 0 .. 8 (the others shadow row 0), P's
+// column c in sX[c][0 .. 2].  Every value takes the operations of
+// pinvh_cofactors, each rounded as written (cmul_rn and its kin): with the columns of P rotated by c (A[x][k] =
+// P[x][(c + k) mod 3]) the lane forms the minor of A without row r and
+// column 0 and its signed cofactor C; det P is the expansion along column 0
+// of lane c = 0's rotation, with the cofactors of lanes (0, 0 .. 2) in row
+// order; the lane's value is (P^{-H})[r][c] = conj(C / det P).
+__device__ inline double pinvh_wide3(const cpx<double> (*sX)[WideP<3>::XS], int c, int r, cpx<double>& out) {
+  constexpr int I = 3;
+  const int rr = r < I ? r : 0;
+  const int r0 = rr == 0 ? 1 : 0, r1 = rr == 2 ? 1 : 2;  // rows of the minor
+  const int c1 = (c + 1) % I, c2 = (c + 2) % I;         // columns 1, 2 of A
+  // P[x][y] = sX[y][x]
+  const cpx<double> m = minor2_rn(sX[c1][r0], sX[c2][r0], sX[c1][r1], sX[c2][r1]);
+  const bool flip = ((c * (I - 1 - c)) & 1) != 0;
+  const cpx<double> C = ((((rr + c) & 1) != 0) != flip) ? mk(-m.re, -m.im) : m;
+  // det P = sum_x P[x][0] C_x over lane c = 0's cofactors
+  cpx<double> det = mk(0.0, 0.0);
+#pragma unroll
+  for (int x = 0; x < I; ++x) det = cadd_rn(det, cmul_rn(sX[0][x], shfl_c(C, I * x)));
+  const double d2 = cabs2_rn(det);
+  out = inv_from_cofactor(C, det, recip(d2));
+  return (d2 > 0.0 && isfinite(d2)) ? d2 : 0.0;
 }
 
-// k_psolve_wide: one P step of Eq. FPI (K sweeps) for I = 8, one warp per
-// problem (blocks of 32 threads; with a trace the last block sums it).  The
-// outputs are those of k_psolve_ldl: the new Lambda committed, P and its
-// pass-A table, P^{-H}, ln|det P|^2, the inversion count and the status.
+// P^{-H} of the P whose column i is sX[i][0 .. I-1] and |det P|^2: lane
+// (i, q) receives (P^{-H})[q + Q m][i], m < R.  I = 8: Gauss-Jordan on P^H,
+// (P^H)[x][y] = conj(P[y][x]); I = 3: cofactors.
+template <int I>
+__device__ inline double pinvh_wide(const cpx<double> (*sX)[WideP<I>::XS], int i, int q,
+                                    cpx<double> (&out)[WideP<I>::R]) {
+  if constexpr (I == 8) {
+    out[0] = cconj(sX[q][i]);
+    out[1] = cconj(sX[q + 4][i]);
+    return gj_inverse_wide8(out[0], out[1], i, q);
+  } else {
+    return pinvh_wide3(sX, i, q, out[0]);
+  }
+}
+
+// k_psolve_wide: one P step of Eq. FPI (K sweeps) for I = 3 or 8, one warp
+// per problem (blocks of 32 threads; with a trace the last block sums it).
+// The outputs are those of k_psolve_ldl: the new Lambda committed, P and
+// its pass-A table, P^{-H}, ln|det P|^2, the inversion count and the status.
 template <typename T, int I, int J>
 __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
   using W = WideP<I>;
-  constexpr int Q = W::Q;
+  constexpr int Q = W::Q, R = W::R;
   __shared__ cpx<double> sV[I][W::VS];   // V_i, then its unit lower factor L_i (row-major, lower part)
   __shared__ cpx<double> sX[I][W::XS];   // column i of P^{-H}, then p_i
   __shared__ cpx<double> sL[I][W::XS];   // scaled column k of the factorisation step
@@ -169,32 +205,38 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
   const int f = blockIdx.x;
   if (f >= a.F) return;
   const int lane = threadIdx.x;
-  const int i = lane % I, q = lane / I;  // matrix / column i, quarter q (as (c, h) in the inverse)
+  const int i = lane % I, q = lane / I;  // matrix / column i and its lane q (as (c, h) in the inverse)
+  const bool live = q < Q;               // lanes I Q and up only join the shuffles
   const Partition pt = a.part;
 
-  // every global load first: the new Lambda, column i of P^{-H} (rows q,
-  // q + 4) and a quarter of V_i's slots (eight 16-byte units of each)
-  double lnext[(J + Q - 1) / Q];
+  // every global load first: the new Lambda, column i of P^{-H} (rows
+  // q + Q m) and the slots of the V_i
+  constexpr int JL = (J + Q - 1) / Q;
+  double lnext[JL];
   if (a.lam_next) {
 #pragma unroll
-    for (int m = 0; m < (J + Q - 1) / Q; ++m) {
+    for (int m = 0; m < JL; ++m) {
       const int j = q + Q * m;
-      lnext[m] = j < J ? __ldcg(a.lam_next + (size_t)f * J * I + j * I + i) : 0.0;
+      lnext[m] = live && j < J ? __ldcg(a.lam_next + (size_t)f * J * I + j * I + i) : 0.0;
     }
   }
-  cpx<double> x0, x1;
-  {
-    const double2* ph = reinterpret_cast<const double2*>(a.pinvH) + (size_t)f * I * I;
-    const double2 u0 = __ldcg(ph + q * I + i), u1 = __ldcg(ph + (q + 4) * I + i);
-    x0 = mk(u0.x, u0.y);
-    x1 = mk(u1.x, u1.y);
+  cpx<double> xr[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int r = q + Q * m;
+    double2 u = make_double2(0.0, 0.0);
+    if (live && r < I) u = __ldcg(reinterpret_cast<const double2*>(a.pinvH) + (size_t)f * I * I + r * I + i);
+    xr[m] = mk(u.x, u.y);
   }
-  constexpr int U = I * I / 2 / Q;  // 16-byte units of V_i per lane
-  double2 pk[U];
-  {
-    const int ns = pt.nslots(f);  // >= 1: every problem has a slot
-    const double2* b2 =
-        reinterpret_cast<const double2*>(a.part_buf + (size_t)f * pt.max_slots * W::NV + i * I * I) + q * U;
+  const int ns = pt.nslots(f);  // >= 1: every problem has a slot
+  const double* slots = a.part_buf + (size_t)f * pt.max_slots * W::NV;
+  bool bad = false;
+  if constexpr (I == 8) {
+    // lane (i, q): eight 16-byte units of V_i's packed values (I diagonal
+    // values, then (re, im) of V_rc, r < c, in row order)
+    constexpr int U = I * I / 2 / Q;
+    double2 pk[U];
+    const double2* b2 = reinterpret_cast<const double2*>(slots + i * I * I) + q * U;
 #pragma unroll
     for (int m = 0; m < U; ++m) pk[m] = __ldcg(b2 + m);
     for (int k = 1; k < ns; ++k) {
@@ -205,11 +247,46 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
         pk[m].y += v2.y;
       }
     }
+    const double sc = pt.inv_n(f);
+#pragma unroll
+    for (int m = 0; m < U; ++m) {
+      pk[m].x *= sc;
+      pk[m].y *= sc;
+      bad |= !isfinite(pk[m].x) || !isfinite(pk[m].y);
+      const int u = q * U + m;  // 16-byte unit of V_i
+      if (u < I / 2) {
+        sV[i][2 * u * (I + 1)] = mk(pk[m].x, 0.0);
+        sV[i][(2 * u + 1) * (I + 1)] = mk(pk[m].y, 0.0);
+      } else {  // the lower entry V_cr = conj(V_rc) goes to the factor's place
+        int r, c;
+        upper_decode<I>(u - I / 2, r, c);
+        sV[i][c * I + r] = mk(pk[m].x, -pk[m].y);
+      }
+    }
+  } else {
+    // one packed value per lane (I^3 <= 32)
+    static_assert(W::NV <= 32, "one value per lane");
+    if (lane < W::NV) {
+      double v = __ldcg(slots + lane);
+      for (int k = 1; k < ns; ++k) v += __ldcg(slots + (size_t)k * W::NV + lane);
+      v *= pt.inv_n(f);
+      bad = !isfinite(v);
+      const int vi = lane / (I * I), m = lane % (I * I);
+      if (m < I) {
+        sV[vi][m * (I + 1)] = mk(v, 0.0);
+      } else {
+        int r, c;
+        upper_decode<I>((m - I) / 2, r, c);
+        if ((m - I) % 2 == 0) sV[vi][c * I + r].re = v;
+        else sV[vi][c * I + r].im = -v;
+      }
+    }
   }
-  if (a.lam_next) {  // commit the new Lambda (computed during pass B)
+  if (bad) raise_status(a.status, kDevNonfinite, f);
+  if (a.lam_next && live) {  // commit the new Lambda (computed during pass B)
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
-    for (int m = 0; m < (J + Q - 1) / Q; ++m) {
+    for (int m = 0; m < JL; ++m) {
       const int j = q + Q * m;
       if (j < J) {
         a.lam[(size_t)f * J * I + j * I + i] = lnext[m];
@@ -217,32 +294,10 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
       }
     }
   }
-  sX[i][q] = x0;
-  sX[i][q + 4] = x1;
-  {
-    const double sc = pt.inv_n(f);
-    bool bad = false;
 #pragma unroll
-    for (int m = 0; m < U; ++m) {
-      pk[m].x *= sc;
-      pk[m].y *= sc;
-      bad |= !isfinite(pk[m].x) || !isfinite(pk[m].y);
-    }
-    if (bad) raise_status(a.status, kDevNonfinite, f);
-    // packed Hermitian V_i: I diagonal values, then (re, im) of V_rc, r < c,
-    // in row order; the lower entry V_cr = conj(V_rc) goes to the factor's place
-#pragma unroll
-    for (int m = 0; m < U; ++m) {
-      const int u = q * U + m;  // 16-byte unit of V_i
-      if (u < I / 2) {
-        sV[i][2 * u * (I + 1)] = mk(pk[m].x, 0.0);
-        sV[i][(2 * u + 1) * (I + 1)] = mk(pk[m].y, 0.0);
-      } else {
-        int r, c;
-        upper_decode<I>(u - I / 2, r, c);
-        sV[i][c * I + r] = mk(pk[m].x, -pk[m].y);
-      }
-    }
+  for (int m = 0; m < R; ++m) {
+    const int r = q + Q * m;
+    if (live && r < I) sX[i][r] = xr[m];
   }
   __syncwarp();
   double d0[I];  // the diagonal before the factorisation
@@ -250,7 +305,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
   for (int k = 0; k < I; ++k) d0[k] = sV[i][k * (I + 1)].re;
 
   // L D L^H in place (right-looking, no square roots).  Lane q takes the
-  // entries q + 4 m of each step's trailing triangle; their places relative
+  // entries q + Q m of each step's trailing triangle; their places relative
   // to the triangle's corner are the same at every step (the row-major
   // order of a triangle starts with that of every smaller one).
   constexpr int ME = (I * (I - 1) / 2 + Q - 1) / Q;  // entries per lane at the first step
@@ -258,7 +313,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
 #pragma unroll
   for (int m = 0; m < ME; ++m) {
     int rr, cc;
-    tri_decode(q + Q * m, rr, cc);
+    tri_decode(live ? q + Q * m : 0, rr, cc);
     e_rc[m] = rr * I + cc;
     e_r[m] = rr * I;
     e_c[m] = cc;
@@ -276,7 +331,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
 #pragma unroll
     for (int m = 0; m < (NR + Q - 1) / Q; ++m) {
       const int r = k + 1 + q + Q * m;
-      if (r < I) {
+      if (live && r < I) {
         lr[m] = cscale(V[r * I + k], inv);
         sL[i][r] = lr[m];
       }
@@ -285,7 +340,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < (NT + Q - 1) / Q; ++m) {
-      if (q + Q * m < NT) {  // V_rc -= V_rk conj(l_c), k < c <= r (the diagonal's real part is |V_rk|^2 / d)
+      if (live && q + Q * m < NT) {  // V_rc -= V_rk conj(l_c), k < c <= r (the diagonal's real part is |V_rk|^2 / d)
         const int corner = (k + 1) * (I + 1);  // entry (k + 1, k + 1)
         const cpx<double> vrk = V[corner - 1 + e_r[m]], lc = sL[i][k + 1 + e_c[m]];
         cpx<double> v = V[corner + e_rc[m]];
@@ -298,10 +353,11 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
 #pragma unroll
     for (int m = 0; m < (NR + Q - 1) / Q; ++m) {  // column k becomes L's
       const int r = k + 1 + q + Q * m;
-      if (r < I) V[r * I + k] = lr[m];
+      if (live && r < I) V[r * I + k] = lr[m];
     }
   }
   __syncwarp();
+
   // K sweeps from the one factorisation: p_i = V_i^{-1} [P^{-H}]_i
   const cpx<double>* L = sV[i];
   bool sing_mid = false;
@@ -313,7 +369,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
 #pragma unroll
       for (int m = 0; m < (NR + Q - 1) / Q; ++m) {
         const int r = k + 1 + q + Q * m;
-        if (r < I) {
+        if (live && r < I) {
           const cpx<double> l = L[r * I + k];
           cpx<double> v = sX[i][r];
           cfma(v, mk(-l.re, -l.im), zk);
@@ -322,8 +378,11 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
       }
       __syncwarp();
     }
-    sX[i][q] = cscale(sX[i][q], sRd[i][q]);
-    sX[i][q + 4] = cscale(sX[i][q + 4], sRd[i][q + 4]);
+#pragma unroll
+    for (int m = 0; m < R; ++m) {  // z = D^{-1} z
+      const int r = q + Q * m;
+      if (live && r < I) sX[i][r] = cscale(sX[i][r], sRd[i][r]);
+    }
     __syncwarp();
 #pragma unroll
     for (int k = I - 1; k > 0; --k) {  // L^H p = z: (L^H)_rk = conj(L_kr)
@@ -331,7 +390,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
 #pragma unroll
       for (int m = 0; m < (k + Q - 1) / Q; ++m) {
         const int r = q + Q * m;
-        if (r < k) {
+        if (live && r < k) {
           const cpx<double> l = L[k * I + r];
           cpx<double> v = sX[i][r];
           cfma(v, mk(-l.re, l.im), zk);
@@ -341,31 +400,39 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
       __syncwarp();
     }
     if (sweep + 1 < a.K) {  // P^{-H} of the intermediate P
-      cpx<double> t0, t1;
-      sing_mid |= !(pinvh_wide8(sX, i, q, t0, t1) > 0.0);
+      cpx<double> t[R];
+      sing_mid |= !(pinvh_wide<I>(sX, i, q, t) > 0.0);
       __syncwarp();
-      sX[i][q] = t0;
-      sX[i][q + 4] = t1;
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int r = q + Q * m;
+        if (live && r < I) sX[i][r] = t[m];
+      }
       __syncwarp();
     }
   }
-  {  // the new P: rows q, q + 4 of column i
+  if (live) {  // the new P: rows q + Q m of column i
     ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int r = q + 4 * m;
-      const cpx<double> pv = sX[i][r];
-      reinterpret_cast<double2*>(a.P)[(size_t)f * I * I + r * I + i] = make_double2(pv.re, pv.im);
-      ta->set_p(r, i, (T)pv.re, (T)pv.im);
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      if (r < I) {
+        const cpx<double> pv = sX[i][r];
+        reinterpret_cast<double2*>(a.P)[(size_t)f * I * I + r * I + i] = make_double2(pv.re, pv.im);
+        ta->set_p(r, i, (T)pv.re, (T)pv.im);
+      }
     }
   }
   // the next step's P^{-H} and ln|det P|^2 of the new P (Eq. L2)
-  cpx<double> q0, q1;
-  const double det2 = pinvh_wide8(sX, i, q, q0, q1);
-  {
-    double2* ph = reinterpret_cast<double2*>(a.pinvH) + (size_t)f * I * I;
-    ph[q * I + i] = make_double2(q0.re, q0.im);
-    ph[(q + 4) * I + i] = make_double2(q1.re, q1.im);
+  cpx<double> ph[R];
+  const double det2 = pinvh_wide<I>(sX, i, q, ph);
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      if (r < I)
+        reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(ph[m].re, ph[m].im);
+    }
   }
   const bool singular = __any_sync(0xffffffffu, !ok || sing_mid) || !(det2 > 0.0);
   if (lane == 0) {
