@@ -387,7 +387,11 @@ ffca_status ffca_batch_loglik(ffca_batch_ctx* ctx, double* ll);
  * the whole launch sequence of the call from a CUDA graph, captured (on a
  * private stream) on the first call for a given iteration count and
  * launched on the context stream; per-kernel timing is not recorded for
- * replays, launch counts are.  Works on single and batch contexts. */
+ * replays, launch counts are.  Works on single and batch contexts.  On a
+ * single context ffca_iterate with a trace replays too (iters < 4096, not
+ * with the resident form): the graph writes the trace into the workspace,
+ * then one copy brings it to ll_trace and the call synchronises and reads
+ * the status, as without the graph. */
 ffca_status ffca_set_graph(ffca_ctx* ctx, int enable);
 /* Batch work partitions: ffca_batch_config_count() candidates per streaming
  * pass, each a choice of the per-problem cost the CTA ranges balance and of

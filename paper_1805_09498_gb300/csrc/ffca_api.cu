@@ -251,6 +251,7 @@ struct ffca_ctx {
   // CUDA graph of the iteration loop (batch API)
   int use_graph;
   int graph_iters;
+  int graph_traced;  // the cached graph writes the log-likelihood trace
   cudaGraphExec_t graph;
   cudaStream_t stream;
   char* ws;
@@ -495,15 +496,18 @@ ffca_status read_status(ffca_ctx* c) {
 
 namespace {
 
-// The launches of `iters` iterations without trace copies (capturable).
-ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
+// The launches of `iters` iterations, without host copies (capturable).
+// traced (not with the resident form; iters < kTraceCap): the
+// log-likelihood of the state entering iteration t goes to device trace
+// slot t and that of the final state to slot iters.
+ffca_status enqueue_iterations(ffca_ctx* c, int iters, bool traced = false) {
   ffca_status st = launch_prep(c, resident_active(c));
   if (st != FFCA_OK) return st;
   if (resident_active(c)) return enqueue_resident(c, iters, nullptr);
   for (int t = 0; t < iters; ++t) {
     const int slot = t % kTraceCap;
     if (c->pmode == kPEM) {
-      if ((st = launch_em_iteration(c, slot, false)) != FFCA_OK) return st;
+      if ((st = launch_em_iteration(c, slot, traced)) != FFCA_OK) return st;
       continue;
     }
     FastArgs a = pass_a_args(c, slot);
@@ -511,19 +515,30 @@ ffca_status enqueue_iterations(ffca_ctx* c, int iters) {
                      c->kern->stream_smem)) != FFCA_OK)
       return st;
     FastArgs b = pass_b_args(c, slot);
-    b.trace = nullptr;  // no trace: no trace block in the P step
+    if (!traced) b.trace = nullptr;  // no trace: no trace block in the P step
     if ((st = launch(c, FFCA_KERNEL_WCOV, c->kern->wcov, wcov_grid(c, b.part), wcov_threads(c), b,
                      c->kern->wcov_smem)) != FFCA_OK)
       return st;
     if ((st = launch(c, FFCA_KERNEL_PSOLVE, p_step_kernel(c), p_step_grid(c, b), p_step_threads(c), b, p_step_smem(c))) != FFCA_OK) return st;
   }
+  if (traced) {  // the log-likelihood of the final state
+    FastArgs a = pass_a_args(c, iters % kTraceCap);
+    if ((st = launch(c, FFCA_KERNEL_LOGLIK, c->kern->estep_eval, stream_grid(c, a.part), stream_threads(c), a,
+                     c->kern->stream_smem)) != FFCA_OK)
+      return st;
+    if ((st = launch(c, FFCA_KERNEL_AFINAL, c->kern->afinal_eval, finals_grid(c), 32 * kFinalWarps, a)) != FFCA_OK)
+      return st;
+  }
   return FFCA_OK;
 }
 
 // Iterations replayed from a CUDA graph of the whole launch sequence,
-// captured on the first call for a given iteration count.
-ffca_status iterate_graph(ffca_ctx* c, int iters) {
-  if (!c->graph || c->graph_iters != iters) {
+// captured on the first call for a given iteration count (and trace or
+// none).  With ll_trace the graph writes the trace slots, which are then
+// copied to ll_trace[0 .. iters] (synchronising, with the status).
+ffca_status iterate_graph(ffca_ctx* c, int iters, double* ll_trace = nullptr) {
+  const bool traced = ll_trace != nullptr;
+  if (!c->graph || c->graph_iters != iters || c->graph_traced != (traced ? 1 : 0)) {
     if (c->graph) {
       cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
@@ -541,7 +556,7 @@ ffca_status iterate_graph(ffca_ctx* c, int iters) {
     c->stream = cap;
     unsigned long long saved[FFCA_KERNEL_KINDS];
     std::memcpy(saved, c->launches, sizeof(saved));
-    ffca_status st = enqueue_iterations(c, iters);
+    ffca_status st = enqueue_iterations(c, iters, traced);
     std::memcpy(c->launches, saved, sizeof(saved));  // captured, not yet run
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cap, &g);
@@ -558,6 +573,7 @@ ffca_status iterate_graph(ffca_ctx* c, int iters) {
       return FFCA_ERR_CUDA;
     }
     c->graph_iters = iters;
+    c->graph_traced = traced ? 1 : 0;
   }
   if (!cuda_ok(cudaGraphLaunch(c->graph, c->stream), "cudaGraphLaunch")) return FFCA_ERR_CUDA;
   c->launches[FFCA_KERNEL_PREP] += 1;
@@ -568,7 +584,14 @@ ffca_status iterate_graph(ffca_ctx* c, int iters) {
   c->launches[FFCA_KERNEL_ESTEP] += iters;
   if (c->pmode != kPEM) c->launches[FFCA_KERNEL_WCOV] += iters;
   c->launches[FFCA_KERNEL_PSOLVE] += iters;
-  return FFCA_OK;
+  if (!traced) return FFCA_OK;
+  c->launches[FFCA_KERNEL_LOGLIK] += 1;
+  c->launches[FFCA_KERNEL_AFINAL] += 1;
+  const double* dtrace = reinterpret_cast<const double*>(c->ws + c->plan.off_trace);
+  if (!cuda_ok(cudaMemcpyAsync(ll_trace, dtrace, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, c->stream),
+               "cudaMemcpyAsync(trace)"))
+    return FFCA_ERR_CUDA;
+  return read_status(c);
 }
 
 // Per-mixture sums of the per-problem log-likelihoods (block m sums the F
@@ -690,7 +713,8 @@ ffca_status ffca_iterate(ffca_ctx* c, int iters, double* ll_trace) {
       for (int t = 0; t <= iters; ++t) ll_trace[t] = 0.0;
     return FFCA_OK;
   }
-  if (c->use_graph && !ll_trace) return iterate_graph(c, iters);
+  if (c->use_graph && (!ll_trace || (iters < kTraceCap && !resident_active(c))))
+    return iterate_graph(c, iters, ll_trace);
   if (resident_active(c)) {
     ffca_status st = launch_prep(c, true);
     if (st == FFCA_OK) st = enqueue_resident(c, iters, ll_trace);

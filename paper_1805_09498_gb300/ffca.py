@@ -494,7 +494,8 @@ class FastFCA:
         return ffca_iterate(self.ctx, iters, trace)
 
     def set_graph(self, enable: bool = True):
-        """Replay trace-less iterate() calls from a CUDA graph."""
+        """Replay iterate() calls from a CUDA graph (with a trace too, for
+        fewer than 4096 iterations and without the resident form)."""
         ffca_set_graph(self.ctx, enable)
 
     def set_p_update(self, method: str = "fixed_point", mu: float = 0.0):

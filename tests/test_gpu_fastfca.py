@@ -146,6 +146,33 @@ def test_deterministic_and_resumable(prec):
     assert np.array_equal(a[3][3:], b[3])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("p_update", [None, "em"])
+def test_traced_graph_replay_is_bit_exact(prec, p_update):
+    """iterate() with a trace replayed from a CUDA graph gives the state and
+    the trace of the plain launches bit for bit, on the first replay (the
+    capture) and on a later one; the cached graph without a trace is kept
+    apart from the traced one."""
+    import torch
+    from paper_1805_09498_gb300 import ffca
+    p = make_problem(3, 3, 6, 300, seed=14)
+    outs = []
+    for graph in (False, True):
+        yd, vd, lam_d, Pd, N = ffca.to_device(p.y, p.v0, p.lam0, p.P0, prec=prec)
+        est = ffca.FastFCA(yd, vd, lam_d, Pd, N=N)
+        if p_update is not None:
+            est.set_p_update(p_update)
+        est.set_graph(graph)
+        t1 = est.iterate(3)
+        est.iterate(2, trace=False)
+        t2 = est.iterate(3)
+        torch.cuda.synchronize()
+        outs.append((vd.cpu().numpy(), lam_d.cpu().numpy(), Pd.cpu().numpy(), t1, t2))
+        est.close()
+    for x, z in zip(outs[0], outs[1]):
+        assert np.array_equal(x, z)
+
+
 def test_resume_mixed_in_place():
     """Mixed path: resuming from the device state is bitwise equal too."""
     import torch
