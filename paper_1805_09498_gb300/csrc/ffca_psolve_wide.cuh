@@ -165,10 +165,12 @@ __device__ inline double pinvh_wide3(const cpx<double> (*sX)[WideP<3>::XS], int 
   const cpx<double> m = minor2_rn(sX[c1][r0], sX[c2][r0], sX[c1][r1], sX[c2][r1]);
   const bool flip = ((c * (I - 1 - c)) & 1) != 0;
   const cpx<double> C = ((((rr + c) & 1) != 0) != flip) ? mk(-m.re, -m.im) : m;
-  // det P = sum_x P[x][0] C_x over lane c = 0's cofactors
+  // det P = sum_x P[x][0] C_x over lane c = 0's cofactors: lane (0, x)
+  // forms term x, every lane sums the terms in row order
+  const cpx<double> term = cmul_rn(sX[c][rr], C);
   cpx<double> det = mk(0.0, 0.0);
 #pragma unroll
-  for (int x = 0; x < I; ++x) det = cadd_rn(det, cmul_rn(sX[0][x], shfl_c(C, I * x)));
+  for (int x = 0; x < I; ++x) det = cadd_rn(det, shfl_c(term, I * x));
   const double d2 = cabs2_rn(det);
   out = inv_from_cofactor(C, det, recip(d2));
   return (d2 > 0.0 && isfinite(d2)) ? d2 : 0.0;
