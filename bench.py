@@ -700,6 +700,7 @@ def run_em(args, p, cfg, dev):
            "measure": f"after {iters} EM iterations from the same initial state, on {len(fs)} sampled "
                       "frequencies; normwise relative error per frequency (max)"}
     vd.copy_(v0); lamd.copy_(l0); Pd.copy_(P0)
+    est.set_graph(True)  # traced iterations replayed from a CUDA graph (captured in the warm-up)
     for _ in range(max(args.warmup, 3)):
         est.iterate(iters)
     reps = max(3, min(args.steps, 20))
@@ -711,6 +712,7 @@ def run_em(args, p, cfg, dev):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / reps
+    est.set_graph(False)  # events around every launch need the plain launches
     ffca.ffca_timing_read(est.ctx)
     ffca.ffca_timing_enable(est.ctx, True)
     est.iterate(iters)
@@ -723,7 +725,7 @@ def run_em(args, p, cfg, dev):
     em_us = kms / kn * 1e3
     gbs = bpt * N * F / (em_us * 1e-6) / 1e9
     out = {"workload": f"long mixture with the normal EM update of P: I={I} J={J} F={F} N={N}, c64, "
-                       f"{iters} iterations with the L2 trace",
+                       f"{iters} iterations with the L2 trace, replayed from a CUDA graph",
            "value": N * F * iters / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms, "runs_timed": reps,
            "kernels": {"em_pass": {"avg_us": em_us, "bytes_per_launch": bpt * N * F, "achieved_gbs": gbs,
                                    "frac_of_measured_hbm": gbs / peaks["hbm_gbs"]},
@@ -834,11 +836,13 @@ def run_large_array(args, dev):
            "measure": f"after {iters} iterations from the same initial state, on {len(fs)} sampled "
                       "frequencies; normwise relative error per frequency (max)"}
 
+    est.set_graph(True)  # traced iterations replayed from a CUDA graph (captured in the warm-up)
     for _ in range(max(args.warmup, 3)):
-        est.iterate(iters, trace=False)
+        est.iterate(iters)
     reps = 5
     ffca.ffca_timing_read(est.ctx)
     ms = timed(lambda: est.iterate(iters), reps)
+    est.set_graph(False)  # events around every launch need the plain launches
     ffca.ffca_timing_read(est.ctx)  # drop the counts of the untimed runs
     ffca.ffca_timing_enable(est.ctx, True)
     est.iterate(iters)
@@ -855,7 +859,7 @@ def run_large_array(args, dev):
                 kernels[k]["achieved_gbs"] = bpt * N * F / (kms / kn * 1e-3) / 1e9
     units = N * F * iters
     out = {"workload": f"large_array: I={I} J={J} F={F} N={N}, c64 storage, mixed FP32/FP64, "
-                       f"{iters} iterations with the L2 trace",
+                       f"{iters} iterations with the L2 trace, replayed from a CUDA graph",
            "value": units / (ms * 1e-3), "unit": UNIT, "ms_per_run": ms, "runs_timed": reps,
            "kernels": kernels, "error_vs_oracle": err}
 
@@ -867,9 +871,11 @@ def run_large_array(args, dev):
     vg, lg, Pg = vd[:, fs, :N].double().cpu().numpy(), lamd[fs].cpu().numpy(), Pd[fs].cpu().numpy()
     mv, ml, mP, mt = ffa.iterate(p.y[:, fs], p.v0[:, fs], p.lam0[fs], p.P0[fs], iters, counter=OpCounter(),
                                  p_update="em")
+    eem.set_graph(True)
     for _ in range(3):
-        eem.iterate(iters, trace=False)
+        eem.iterate(iters)
     ms_em = timed(lambda: eem.iterate(iters), reps)
+    eem.set_graph(False)
     ffca.ffca_timing_read(eem.ctx)
     ffca.ffca_timing_enable(eem.ctx, True)
     eem.iterate(iters)
