@@ -378,13 +378,18 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
 
 // The fixed-point step with one warp per problem (k_psolve_wide) up to this
 // many problems.  Its FP64 instructions per problem are 1.5x (I = 8) to 6x
-// (I = 3) those of the packed form (32 / I problems per warp), but the
-// packed form's few warps leave most FP64 units idle: per the instruction
-// counts of the two, the wide form is the faster up to about 2000 problems.
-constexpr int kWideMaxProblems = 2048;
+// (I = 3) those of the packed form (32 / I problems per warp), whose few
+// warps leave most FP64 units idle while the problems are few.  Measured
+// (mixed precision, N = 64): the packed step takes 13 - 14.5 us at I = 3
+// and 55 - 62 us at I = 8 from 929 to 2048 problems; the wide one 12.1 /
+// 14.5 us at 513 / 928 problems (I = 3) and 31 / 41 / 58 us at 513 / 1024
+// / 1664 (I = 8).  They cross near 780 problems at I = 3 and 1580 at I = 8.
+constexpr int kWideMaxProblems3 = 768;
+constexpr int kWideMaxProblems8 = 1536;
 
 bool p_step_wide(const ffca_ctx* c) {
-  return c->pmode == kPFixedPoint && c->kern->psolve_wide != nullptr && c->d.F <= kWideMaxProblems;
+  const int most = c->d.I == 8 ? kWideMaxProblems8 : kWideMaxProblems3;
+  return c->pmode == kPFixedPoint && c->kern->psolve_wide != nullptr && c->d.F <= most;
 }
 
 // Blocks of the P step: one warp per 32 / I problems (Newton and the wide

@@ -40,8 +40,8 @@ using Real = float;
 // The P step by Gauss-Jordan and LDL^H (k_psolve_ldl, which carries P^{-H}
 // from one step to the next) from FFCA_LDL_MIN_I microphones up; below it
 // the cofactor forms of k_psolve.  At I = 3 and 8 the fixed point of up to
-// kWideMaxProblems problems runs k_psolve_wide (one warp per problem, the
-// same P^{-H} bits).
+// about a thousand problems (ffca_api.cu) runs k_psolve_wide (one warp per
+// problem, the same P^{-H} bits).
 #ifndef FFCA_LDL_MIN_I
 #define FFCA_LDL_MIN_I 3
 #endif

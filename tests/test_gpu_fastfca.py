@@ -147,6 +147,22 @@ def test_deterministic_and_resumable(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("F", [768, 769])
+def test_p_step_forms_either_side_of_the_switch(prec, F):
+    """The fixed-point step runs one warp per problem up to 768 problems at
+    I = 3 and packs ten problems in a warp above: both forms against the
+    oracle over two iterations, and 2 + 1 iterations equal 3 bit for bit."""
+    p = make_problem(3, 3, F, 24, seed=15)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter())
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec)
+    _compare(prec, ref, got, 24, F)
+    a = run_gpu(p.y, p.v0, p.lam0, p.P0, 3, prec)
+    b = run_gpu(p.y, got[0], got[1], got[2], 1, prec)
+    for x, z in zip(a[:3], b[:3]):
+        assert np.array_equal(x, z)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("p_update", [None, "em"])
 def test_traced_graph_replay_is_bit_exact(prec, p_update):
     """iterate() with a trace replayed from a CUDA graph gives the state and
