@@ -155,6 +155,11 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
       T acc[NVA];
 #pragma unroll
       for (int q = 0; q < NVA; ++q) acc[q] = (T)0;
+      // FP64: the sigmas' binary mantissas multiplied over all of the
+      // thread's frames (renormalised after each frame) and their exponents
+      // added; one software log2 per thread and iteration
+      T lm = (T)1;
+      int le = 0;
       for (int t = tid; t < n; t += kResThreads) {
         C ym[I];
 #pragma unroll
@@ -163,8 +168,6 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
 #pragma unroll
         for (int j = 0; j < J; ++j) vj[j] = v[j * np + t];
         T r[I], e2[I];
-        T lm = (T)1;  // FP64: product of the sigmas' mantissas and sum of their exponents
-        int le = 0;
 #pragma unroll
         for (int i = 0; i < I; ++i) {
           C s = mk<T>(0, 0);
@@ -178,13 +181,17 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
           acc[NA] = fma(e2[i], r[i], acc[NA]);
           if constexpr (sizeof(T) == 4) {
             acc[NA + 1] += __log2f(sg);
-          } else {  // one software log2 per frame: the sigmas' mantissas multiplied, their exponents added
+          } else {
             int k;
             lm *= frexp(sg, &k);
             le += k;
           }
         }
-        if constexpr (sizeof(T) == 8) acc[NA + 1] += log2(lm) + (double)le;
+        if constexpr (sizeof(T) == 8) {
+          int k;
+          lm = frexp(lm, &k);
+          le += k;
+        }
 #pragma unroll
         for (int j = 0; j < J; ++j) {  // Eqs. updatev and Lambdaupdate in the form of k_estep
           T tj[I], sj = (T)0;
@@ -200,6 +207,7 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
           v[j * np + t] = vj[j] * sj * (T)(1.0 / I);
         }
       }
+      if constexpr (sizeof(T) == 8) acc[NA + 1] += log2(lm) + (double)le;
       ResReduce<T, NVA>::run(acc, redA, sumsA);
     }
     // the new Lambda and the problem's L2 of the entering state (FP64)

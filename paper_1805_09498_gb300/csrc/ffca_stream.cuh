@@ -581,11 +581,10 @@ __device__ inline D1 vfma(D1 a, D1 b, D1 c) { return {fma(a.v, b.v, c.v)}; }
 __device__ inline D1 vrcp(D1 x) { return {recip(x.v)}; }
 __device__ inline D1 vlog2(D1 x) { return {log2(x.v)}; }
 
-// sum_i log2 sigma_i of one point.  FP32 lanes take one hardware log2 per
-// sigma; FP64 takes the one log2 of the product of the sigmas' mantissas
-// (each in [1/2, 1), so that the product of up to eight neither overflows
-// nor underflows) plus the sum of their binary exponents: one software
-// logarithm per point instead of I.
+// sum_i log2 sigma_i of one point in FP32 lanes: one hardware log2 per
+// sigma.  (FP64 keeps a running product of the sigmas' binary mantissas
+// over a thread's points instead, with one software logarithm per segment:
+// see the pass-A consumer.)
 template <typename L>
 struct Log2Sum;
 template <>
@@ -595,16 +594,7 @@ struct Log2Sum<F2> {
   __device__ inline F2 value() const { return s; }
 };
 template <>
-struct Log2Sum<D1> {
-  double m = 1.0;
-  int e = 0;
-  __device__ inline void add(D1 x) {
-    int k;
-    m *= frexp(x.v, &k);
-    e += k;
-  }
-  __device__ inline D1 value() const { return {log2(m) + (double)e}; }
-};
+struct Log2Sum<D1> {};  // unused: FP64 takes the running product
 
 template <typename T>
 struct Lane;
@@ -1066,6 +1056,12 @@ __global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : 
     }
   };
 
+  // FP64: sum_n log2 of the product of the sigmas over the thread's points
+  // of the segment, as one running product of binary mantissas (renormalised
+  // after every point, so it stays in [1/2, 1)) and a sum of exponents; its
+  // logarithm is taken once, when the segment's sums are reduced
+  double lg_m = 1.0;
+  int lg_e = 0;
   TileIter it(u0, u1, pt, TC::T);
   bool seg_new = true;
   int nseg = 0;           // reductions so far (reduction buffer parity)
@@ -1148,19 +1144,32 @@ __global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : 
           r[i] = vrcp(sg);
           e2[i] = vfma(tr, tr, ti * ti);
           quad = vfma(e2[i], r[i], quad);
-          lgs.add(sg);
+          if constexpr (sizeof(T) == 8) {
+            int ke;
+            lg_m *= frexp(LN::hsum(sg), &ke);
+            lg_e += ke;
+          } else {
+            lgs.add(sg);
+          }
           if constexpr (EM) {
             ztr[i] = r[i] * tr;
             zti[i] = r[i] * ti;
           }
         }
-        const L lg = lgs.value();
-        if (full) {
+        if constexpr (sizeof(T) == 8) {  // one frame per unit: always full
+          int ke;
+          lg_m = frexp(lg_m, &ke);
+          lg_e += ke;
           ACC(NA, quad);
-          ACC(NA + 1, lg);
         } else {
-          ACC(NA, LN::keep(quad, n0, Np));
-          ACC(NA + 1, LN::keep(lg, n0, Np));
+          const L lg = lgs.value();
+          if (full) {
+            ACC(NA, quad);
+            ACC(NA + 1, lg);
+          } else {
+            ACC(NA, LN::keep(quad, n0, Np));
+            ACC(NA + 1, LN::keep(lg, n0, Np));
+          }
         }
         if constexpr (UPDATE) {
           L w[I];
@@ -1242,6 +1251,9 @@ __global__ void __maxnreg__((EM ? (EmGroups<T, I, J>::value == 2 ? 128 : 255) : 
         double hi[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) hi[q] = acc[q].v;
+        hi[NA + 1] += log2(lg_m) + (double)lg_e;
+        lg_m = 1.0;
+        lg_e = 0;
         Red::run(hi, red, out, rl, nseg);
       }
       ++nseg;  // the next reduction goes through the other buffer
