@@ -392,6 +392,13 @@ bool p_step_wide(const ffca_ctx* c) {
   return c->pmode == kPFixedPoint && c->kern->psolve_wide != nullptr && c->d.F <= most;
 }
 
+// The EM step with one warp per problem (k_psolve_em_wide), on the same
+// problem counts.
+bool em_step_wide(const ffca_ctx* c) {
+  const int most = c->d.I == 8 ? kWideMaxProblems8 : kWideMaxProblems3;
+  return c->kern->psolve_em_wide != nullptr && c->d.F <= most;
+}
+
 // Blocks of the P step: one warp per 32 / I problems (Newton and the wide
 // fixed point: one block per problem), plus the trace's block.
 int p_step_grid(const ffca_ctx* c, const FastArgs& b) {
@@ -461,6 +468,7 @@ ffca_status launch_em_iteration(ffca_ctx* c, int slot, bool trace) {
   ffca_status st = launch(c, FFCA_KERNEL_ESTEP, c->kern->estep_em, (a.part.nblocks + eg - 1) / eg,
                           kGroupThreads * eg, a, c->kern->em_smem);
   if (st != FFCA_OK) return st;
+  if (em_step_wide(c)) return launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve_em_wide, c->d.F, 32, a, 0);
   const int G = 32 / c->d.I;
   return launch(c, FFCA_KERNEL_PSOLVE, c->kern->psolve_em, (c->d.F + G - 1) / G, 32, a, c->kern->em_solve_smem);
 }

@@ -24,6 +24,7 @@ struct FastKernels {
   // the normal EM update of P (nullptr where not compiled: I > 4)
   const void* estep_em;      // pass A with the EM sums (one pipeline group per CTA)
   const void* psolve_em;     // its per-problem step (no pass B)
+  const void* psolve_em_wide;  // the same step with one warp per problem (I = 3 and 8; else nullptr)
   int em_smem;               // dynamic shared memory of estep_em
   int em_solve_smem;         // dynamic shared memory of psolve_em
   int em_nv;                 // sums per slot of estep_em
@@ -94,6 +95,7 @@ FFCA_DECLARE_TABLE(1, 8)
 #define FFCA_DECLARE_ALT(P, I) \
   const void* em_estep_p##P##_i##I(int J); \
   const void* em_psolve_p##P##_i##I(int J); \
+  const void* em_psolve_wide_p##P##_i##I(int J); \
   const void* newton_p##P##_i##I(int J);
 FFCA_DECLARE_ALT(0, 1)
 FFCA_DECLARE_ALT(0, 2)

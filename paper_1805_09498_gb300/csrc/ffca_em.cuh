@@ -31,6 +31,7 @@
 #pragma once
 
 #include "ffca_big.cuh"
+#include "ffca_psolve_wide.cuh"
 
 namespace ffca {
 
@@ -374,6 +375,210 @@ __global__ void __launch_bounds__(32) k_psolve_em(FastArgs a) {
       atomicAdd(a.ops, p_update_inversions(a, I));
       a.logdet[f] = log(det2);
     }
+  }
+  // with a trace: the last block to finish sums the problems' L2
+  if (a.trace) {
+    __threadfence();
+    __syncwarp();
+    unsigned last = 0;
+    if (lane == 0) {
+      last = atomicAdd(a.gcnt, 1u) == gridDim.x - 1;
+      if (last) *a.gcnt = 0u;  // ready for the next launch
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      finalize_trace(a);
+    }
+  }
+}
+
+// k_psolve_em_wide: the EM step above for I = 3 or 8 with one warp per
+// problem (lane (i, q) as in k_psolve_wide), for a few hundred problems,
+// where the packed form leaves most FP64 units idle: the slot sums, the new
+// Lambda and the entering state's L2 spread over the warp; Omega_i formed
+// entry by entry into shared memory and factored by wide_ldl; the sweeps by
+// wide_solve and the products with the entering P by rows; P^{-H} and
+// ln|det P|^2 by pinvh_wide (the bits of pinvh_from_columns).  With a
+// trace the last block to finish sums the problems' L2.
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(32) k_psolve_em_wide(FastArgs a) {
+  using W = WideP<I>;
+  using ES = EmShape<I, J>;
+  constexpr int Q = W::Q, R = W::R;
+  constexpr int NV = ES::NV, NA = ES::NA, NPAIR = ES::NPAIR;
+  constexpr int NTRI = I * (I + 1) / 2;  // entries of a lower triangle with its diagonal
+  __shared__ cpx<double> sV[I][W::VS];   // Omega_i, then its factor
+  __shared__ cpx<double> sX[I][W::XS];   // x_i, then column i of the new P
+  __shared__ cpx<double> sL[I][W::XS];   // factorisation scratch, then P^{-H} columns
+  __shared__ double sRd[I][W::XS];
+  __shared__ double sSum[NV];            // the problem's slot sums
+  __shared__ cpx<double> sP0[I][I];      // the entering P
+  __shared__ double sLold[J][I], sLnew[J][I], sRl[I][J];  // Lambda old and new, 1 / lambda_ji^new
+  const int f = blockIdx.x;
+  if (f >= a.F) return;
+  const int lane = threadIdx.x;
+  const int i = lane % I, q = lane / I;
+  const bool live = q < Q;
+  const Partition pt = a.part;
+
+  // the slot sums (slot order), the entering P and Lambda
+  {
+    const int ns = pt.nslots(f);
+    const double* base = a.part_buf + (size_t)f * pt.max_slots * NV;
+    for (int x = lane; x < NV; x += 32) {
+      double acc = __ldcg(base + x);
+      for (int k = 1; k < ns; ++k) acc += __ldcg(base + (size_t)k * NV + x);
+      sSum[x] = acc;
+    }
+    for (int e = lane; e < I * I; e += 32) {
+      const double2 u = __ldcg(reinterpret_cast<const double2*>(a.P) + (size_t)f * I * I + e);
+      sP0[e / I][e % I] = mk(u.x, u.y);
+    }
+    for (int e = lane; e < J * I; e += 32) sLold[e / I][e % I] = __ldcg(a.lam + (size_t)f * J * I + e);
+  }
+  const double logdet_old = __ldcg(a.logdet + f);
+  const double nd = (double)pt.frames(f);
+  __syncwarp();
+
+  // the new Lambda (Eq. Lambdaupdate) and the entering state's L2 (Eq. L2)
+  bool bad = false;
+  ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+  for (int e = lane; e < J * I; e += 32) {
+    const int j = e / I, c = e % I;
+    const double l = sLold[j][c] * ((double)I * pt.inv_n(f)) * sSum[j * I + c];
+    bad |= !(l > 0.0) || !isfinite(l);
+    sLnew[j][c] = l;
+    a.lam[(size_t)f * J * I + e] = l;
+    ta->set_lam(j, c, (T)l);
+  }
+  {
+    const double lf = -(double)I * nd * kLnPi + nd * logdet_old - sSum[NA] - 0.69314718055994530942 * sSum[NA + 1];
+    bad |= !isfinite(lf);
+    if (lane == 0) a.llf[f] = lf;
+  }
+  __syncwarp();
+  for (int e = lane; e < J * I; e += 32) sRl[e % I][e / I] = 1.0 / sLnew[e / I][e % I];
+  __syncwarp();
+
+  // Omega_i: diagonal sum_j N lambda_jc^new / lambda_ji^new; below it
+  // conj(sum_j I lambda_ja lambda_jb S_j[a][b] / lambda_ji^new), a < b (old
+  // Lambda in the products, S_j the pass-A sums)
+  for (int e = lane; e < I * NTRI; e += 32) {
+    const int ii = e / NTRI;
+    int rr, cc;
+    tri_decode(e % NTRI, rr, cc);
+    cpx<double> o;
+    if (rr == cc) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < J; ++j) s = fma(nd * sLnew[j][cc], sRl[ii][j], s);
+      o = mk(s, 0.0);
+    } else {
+      const int aa = cc, bb = rr;
+      const int pq = aa * (2 * I - aa - 1) / 2 + (bb - aa - 1);  // pair (aa, bb) in row order
+      cpx<double> s = mk(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const double w = (double)I * sLold[j][aa] * sLold[j][bb] * sRl[ii][j];
+        const double* t = sSum + NA + 2 + 2 * (j * NPAIR + pq);
+        s.re = fma(w, t[0], s.re);
+        s.im = fma(w, t[1], s.im);
+      }
+      o = cconj(s);
+    }
+    bad |= !isfinite(o.re) || !isfinite(o.im);
+    sV[ii][rr * I + cc] = o;
+  }
+  if (bad) raise_status(a.status, kDevNonfinite, f);
+  __syncwarp();
+  const bool ok = wide_ldl<I>(sV, sL, sRd, i, q);
+
+  // K sweeps; the first from x_i = P^H P^{-H} e_i = e_i
+  const double jn = (double)J * nd;
+  bool sing_mid = false;
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int r = q + Q * m;
+    if (live && r < I) sX[i][r] = mk(r == i ? 1.0 : 0.0, 0.0);
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < a.K; ++sweep) {
+    if (sweep > 0) {  // x_i = P^H [P_k^{-H}]_i with the entering P
+      cpx<double> t[R];
+      sing_mid |= !(pinvh_wide<I>(sX, i, q, t) > 0.0);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int r = q + Q * m;
+        if (live && r < I) sL[i][r] = t[m];
+      }
+      __syncwarp();
+      cpx<double> xr[R];
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int c = q + Q * m;
+        cpx<double> s = mk(0.0, 0.0);
+        if (live && c < I) {
+#pragma unroll
+          for (int r = 0; r < I; ++r) cfmac(s, sP0[r][c], sL[i][r]);
+        }
+        xr[m] = s;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        const int c = q + Q * m;
+        if (live && c < I) sX[i][c] = xr[m];
+      }
+      __syncwarp();
+    }
+    wide_solve<I>(sV, sRd, sX, i, q);
+    cpx<double> cr[R];  // column i of the new P: J N P Omega_i^{-1} x_i
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      cpx<double> s = mk(0.0, 0.0);
+      if (live && r < I) {
+#pragma unroll
+        for (int c = 0; c < I; ++c) cfma(s, sP0[r][c], sX[i][c]);
+      }
+      cr[m] = cscale(s, jn);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      if (live && r < I) sX[i][r] = cr[m];
+    }
+    __syncwarp();
+  }
+  if (live) {  // the new P: rows q + Q m of column i
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      if (r < I) {
+        const cpx<double> pv = sX[i][r];
+        reinterpret_cast<double2*>(a.P)[(size_t)f * I * I + r * I + i] = make_double2(pv.re, pv.im);
+        ta->set_p(r, i, (T)pv.re, (T)pv.im);
+      }
+    }
+  }
+  // P^{-H} and ln|det P|^2 of the new P (the next iteration's L2 needs it)
+  cpx<double> ph[R];
+  const double det2 = pinvh_wide<I>(sX, i, q, ph);
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      if (r < I)
+        reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(ph[m].re, ph[m].im);
+    }
+  }
+  const bool singular = __any_sync(0xffffffffu, !ok || sing_mid) || !(det2 > 0.0);
+  if (lane == 0) {
+    if (singular) raise_status(a.status, kDevSingular, f);
+    atomicAdd(a.ops, p_update_inversions(a, I));
+    a.logdet[f] = log(det2);
   }
   // with a trace: the last block to finish sums the problems' L2
   if (a.trace) {

@@ -78,6 +78,7 @@ static const FastKernels* table_entry() {
   int res_bpf = 0, res_max = 0;
   estep_em = FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(J);
   psolve_em = FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(J);
+  const void* psolve_em_wide = FFCA_CAT(em_psolve_wide_p, FFCA_PREC, _i, FFCA_I)(J);
   em_groups = EmGroups<Real, FFCA_I, J>::value;
   em_smem = em_groups * Tile<Real, FFCA_I, J, EmGroups<Real, FFCA_I, J>::value>::GROUP;
   em_solve_smem = EmShape<FFCA_I, J>::SMEM;
@@ -102,6 +103,7 @@ static const FastKernels* table_entry() {
       pgrad,
       estep_em,
       psolve_em,
+      psolve_em_wide,
       em_smem,
       em_solve_smem,
       em_nv,
@@ -226,27 +228,34 @@ const AdjKernels* FFCA_CAT(adj_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
 #endif
 
 #if FFCA_PART == 3
+// kind 0: the EM pass; 1: the packed EM step; 2: the wide EM step (I = 3, 8)
 template <int J>
-static const void* em_pair(bool step) {
+static const void* em_kernel(int kind) {
+  if (kind == 1) return (const void*)k_psolve_em<Real, FFCA_I, J>;
+  if (kind == 2) {
+    if constexpr (FFCA_I == 3 || FFCA_I == 8) return (const void*)k_psolve_em_wide<Real, FFCA_I, J>;
+    return nullptr;
+  }
 #if FFCA_I > 4
-  return step ? (const void*)k_psolve_em<Real, FFCA_I, J> : (const void*)k_estep_em_big<Real, FFCA_I, J>;
+  return (const void*)k_estep_em_big<Real, FFCA_I, J>;
 #else
-  return step ? (const void*)k_psolve_em<Real, FFCA_I, J> : (const void*)k_estep<Real, FFCA_I, J, true, true>;
+  return (const void*)k_estep<Real, FFCA_I, J, true, true>;
 #endif
 }
-static const void* em_select(int J, bool step) {
+static const void* em_select(int J, int kind) {
   switch (J) {
-    case 1: return em_pair<1>(step);
-    case 2: return em_pair<2>(step);
-    case 3: return em_pair<3>(step);
-    case 4: return em_pair<4>(step);
-    case 5: return em_pair<5>(step);
-    case 6: return em_pair<6>(step);
+    case 1: return em_kernel<1>(kind);
+    case 2: return em_kernel<2>(kind);
+    case 3: return em_kernel<3>(kind);
+    case 4: return em_kernel<4>(kind);
+    case 5: return em_kernel<5>(kind);
+    case 6: return em_kernel<6>(kind);
     default: return nullptr;
   }
 }
-const void* FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, false); }
-const void* FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, true); }
+const void* FFCA_CAT(em_estep_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, 0); }
+const void* FFCA_CAT(em_psolve_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, 1); }
+const void* FFCA_CAT(em_psolve_wide_p, FFCA_PREC, _i, FFCA_I)(int J) { return em_select(J, 2); }
 #endif
 
 #if FFCA_PART == 4

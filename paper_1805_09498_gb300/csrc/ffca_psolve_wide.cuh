@@ -151,9 +151,10 @@ __device__ inline double gj_inverse_wide8(cpx<double>& a0, cpx<double>& a1, int 
 // Column c of P^{-H} and |det P|^2 for I = 3 by cofactors, lane (c, r) =
 // (lane % 3, lane / 3) for lanes 0 .. 8 (the others shadow row 0), P's
 // column c in sX[c][0 .. 2].  Every value takes the operations of
-// pinvh_cofactors, each rounded as written (cmul_rn and its kin): with the columns of P rotated by c (A[x][k] =
-// P[x][(c + k) mod 3]) the lane forms the minor of A without row r and
-// column 0 and its signed cofactor C; det P is the expansion along column 0
+// pinvh_cofactors, each rounded as written (cmul_rn and its kin): with the
+// columns of P rotated by c (A[x][k] = P[x][(c + k) mod 3]) the lane forms
+// the minor of A without row r and column 0 and its signed cofactor C;
+// det P is the expansion along column 0
 // of lane c = 0's rotation, with the cofactors of lanes (0, 0 .. 2) in row
 // order; the lane's value is (P^{-H})[r][c] = conj(C / det P).
 __device__ inline double pinvh_wide3(const cpx<double> (*sX)[WideP<3>::XS], int c, int r, cpx<double>& out) {
@@ -188,6 +189,125 @@ __device__ inline double pinvh_wide(const cpx<double> (*sX)[WideP<I>::XS], int i
     return gj_inverse_wide8(out[0], out[1], i, q);
   } else {
     return pinvh_wide3(sX, i, q, out[0]);
+  }
+}
+
+// L D L^H (right-looking, no square roots) of the I matrices sV[i] in
+// place by lanes (i, q), q < Q (the other lanes only join the barriers):
+// sV[i] holds V_i's real diagonal and strictly lower entries (row-major,
+// stride I); on return its strictly lower part holds the unit factor L_i
+// and sRd[i] the reciprocals of D_i.  sL is scratch.  Returns false for a
+// pivot at or below kCholRtol times its diagonal entry, or not finite.
+// The caller has synchronised the warp after writing sV.
+template <int I>
+__device__ inline bool wide_ldl(cpx<double> (*sV)[WideP<I>::VS], cpx<double> (*sL)[WideP<I>::XS],
+                                double (*sRd)[WideP<I>::XS], int i, int q) {
+  constexpr int Q = WideP<I>::Q;
+  const bool live = q < Q;
+  double d0[I];  // the diagonal before the factorisation
+#pragma unroll
+  for (int k = 0; k < I; ++k) d0[k] = sV[i][k * (I + 1)].re;
+
+  // L D L^H in place (right-looking, no square roots).  Lane q takes the
+  // entries q + Q m of each step's trailing triangle; their places relative
+  // to the triangle's corner are the same at every step (the row-major
+  // order of a triangle starts with that of every smaller one).
+  constexpr int ME = (I * (I - 1) / 2 + Q - 1) / Q;  // entries per lane at the first step
+  int e_rc[ME], e_r[ME], e_c[ME];                   // rr * I + cc, rr * I, cc
+#pragma unroll
+  for (int m = 0; m < ME; ++m) {
+    int rr, cc;
+    tri_decode(live ? q + Q * m : 0, rr, cc);
+    e_rc[m] = rr * I + cc;
+    e_r[m] = rr * I;
+    e_c[m] = cc;
+  }
+  cpx<double>* V = sV[i];
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < I; ++k) {
+    const double d = V[k * (I + 1)].re;
+    ok &= isfinite(d) && d > 0.0 && d > kCholRtol * d0[k];
+    const double inv = recip(d);
+    const int NR = I - 1 - k;          // rows below the pivot
+    const int NT = NR * (NR + 1) / 2;  // entries of the trailing triangle
+    cpx<double> lr[(I - 1 + Q - 1) / Q];  // this lane's rows of the scaled column
+#pragma unroll
+    for (int m = 0; m < (NR + Q - 1) / Q; ++m) {
+      const int r = k + 1 + q + Q * m;
+      if (live && r < I) {
+        lr[m] = cscale(V[r * I + k], inv);
+        sL[i][r] = lr[m];
+      }
+    }
+    if (q == 0) sRd[i][k] = inv;
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < (NT + Q - 1) / Q; ++m) {
+      if (live && q + Q * m < NT) {  // V_rc -= V_rk conj(l_c), k < c <= r (the diagonal's real part is |V_rk|^2 / d)
+        const int corner = (k + 1) * (I + 1);  // entry (k + 1, k + 1)
+        const cpx<double> vrk = V[corner - 1 + e_r[m]], lc = sL[i][k + 1 + e_c[m]];
+        cpx<double> v = V[corner + e_rc[m]];
+        v.re = fma(-vrk.re, lc.re, fma(-vrk.im, lc.im, v.re));
+        v.im = fma(-vrk.im, lc.re, fma(vrk.re, lc.im, v.im));
+        V[corner + e_rc[m]] = v;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < (NR + Q - 1) / Q; ++m) {  // column k becomes L's
+      const int r = k + 1 + q + Q * m;
+      if (live && r < I) V[r * I + k] = lr[m];
+    }
+  }
+  __syncwarp();
+  return ok;
+}
+
+// x_i <- (L_i D_i L_i^H)^{-1} x_i for the I vectors sX[i], with the factors
+// of wide_ldl: the rows of each substitution step over the lanes (i, q).
+template <int I>
+__device__ inline void wide_solve(const cpx<double> (*sV)[WideP<I>::VS], const double (*sRd)[WideP<I>::XS],
+                                  cpx<double> (*sX)[WideP<I>::XS], int i, int q) {
+  constexpr int Q = WideP<I>::Q, R = WideP<I>::R;
+  const bool live = q < Q;
+  const cpx<double>* L = sV[i];
+#pragma unroll
+  for (int k = 0; k < I - 1; ++k) {  // L z = x
+    const cpx<double> zk = sX[i][k];
+    const int NR = I - 1 - k;
+#pragma unroll
+    for (int m = 0; m < (NR + Q - 1) / Q; ++m) {
+      const int r = k + 1 + q + Q * m;
+      if (live && r < I) {
+        const cpx<double> l = L[r * I + k];
+        cpx<double> v = sX[i][r];
+        cfma(v, mk(-l.re, -l.im), zk);
+        sX[i][r] = v;
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int m = 0; m < R; ++m) {  // z = D^{-1} z
+    const int r = q + Q * m;
+    if (live && r < I) sX[i][r] = cscale(sX[i][r], sRd[i][r]);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = I - 1; k > 0; --k) {  // L^H p = z: (L^H)_rk = conj(L_kr)
+    const cpx<double> zk = sX[i][k];
+#pragma unroll
+    for (int m = 0; m < (k + Q - 1) / Q; ++m) {
+      const int r = q + Q * m;
+      if (live && r < k) {
+        const cpx<double> l = L[k * I + r];
+        cpx<double> v = sX[i][r];
+        cfma(v, mk(-l.re, l.im), zk);
+        sX[i][r] = v;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -302,105 +422,12 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
     if (live && r < I) sX[i][r] = xr[m];
   }
   __syncwarp();
-  double d0[I];  // the diagonal before the factorisation
-#pragma unroll
-  for (int k = 0; k < I; ++k) d0[k] = sV[i][k * (I + 1)].re;
-
-  // L D L^H in place (right-looking, no square roots).  Lane q takes the
-  // entries q + Q m of each step's trailing triangle; their places relative
-  // to the triangle's corner are the same at every step (the row-major
-  // order of a triangle starts with that of every smaller one).
-  constexpr int ME = (I * (I - 1) / 2 + Q - 1) / Q;  // entries per lane at the first step
-  int e_rc[ME], e_r[ME], e_c[ME];                   // rr * I + cc, rr * I, cc
-#pragma unroll
-  for (int m = 0; m < ME; ++m) {
-    int rr, cc;
-    tri_decode(live ? q + Q * m : 0, rr, cc);
-    e_rc[m] = rr * I + cc;
-    e_r[m] = rr * I;
-    e_c[m] = cc;
-  }
-  cpx<double>* V = sV[i];
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < I; ++k) {
-    const double d = V[k * (I + 1)].re;
-    ok &= isfinite(d) && d > 0.0 && d > kCholRtol * d0[k];
-    const double inv = recip(d);
-    const int NR = I - 1 - k;          // rows below the pivot
-    const int NT = NR * (NR + 1) / 2;  // entries of the trailing triangle
-    cpx<double> lr[(I - 1 + Q - 1) / Q];  // this lane's rows of the scaled column
-#pragma unroll
-    for (int m = 0; m < (NR + Q - 1) / Q; ++m) {
-      const int r = k + 1 + q + Q * m;
-      if (live && r < I) {
-        lr[m] = cscale(V[r * I + k], inv);
-        sL[i][r] = lr[m];
-      }
-    }
-    if (q == 0) sRd[i][k] = inv;
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < (NT + Q - 1) / Q; ++m) {
-      if (live && q + Q * m < NT) {  // V_rc -= V_rk conj(l_c), k < c <= r (the diagonal's real part is |V_rk|^2 / d)
-        const int corner = (k + 1) * (I + 1);  // entry (k + 1, k + 1)
-        const cpx<double> vrk = V[corner - 1 + e_r[m]], lc = sL[i][k + 1 + e_c[m]];
-        cpx<double> v = V[corner + e_rc[m]];
-        v.re = fma(-vrk.re, lc.re, fma(-vrk.im, lc.im, v.re));
-        v.im = fma(-vrk.im, lc.re, fma(vrk.re, lc.im, v.im));
-        V[corner + e_rc[m]] = v;
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int m = 0; m < (NR + Q - 1) / Q; ++m) {  // column k becomes L's
-      const int r = k + 1 + q + Q * m;
-      if (live && r < I) V[r * I + k] = lr[m];
-    }
-  }
-  __syncwarp();
+  const bool ok = wide_ldl<I>(sV, sL, sRd, i, q);
 
   // K sweeps from the one factorisation: p_i = V_i^{-1} [P^{-H}]_i
-  const cpx<double>* L = sV[i];
   bool sing_mid = false;
   for (int sweep = 0; sweep < a.K; ++sweep) {
-#pragma unroll
-    for (int k = 0; k < I - 1; ++k) {  // L z = x
-      const cpx<double> zk = sX[i][k];
-      const int NR = I - 1 - k;
-#pragma unroll
-      for (int m = 0; m < (NR + Q - 1) / Q; ++m) {
-        const int r = k + 1 + q + Q * m;
-        if (live && r < I) {
-          const cpx<double> l = L[r * I + k];
-          cpx<double> v = sX[i][r];
-          cfma(v, mk(-l.re, -l.im), zk);
-          sX[i][r] = v;
-        }
-      }
-      __syncwarp();
-    }
-#pragma unroll
-    for (int m = 0; m < R; ++m) {  // z = D^{-1} z
-      const int r = q + Q * m;
-      if (live && r < I) sX[i][r] = cscale(sX[i][r], sRd[i][r]);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int k = I - 1; k > 0; --k) {  // L^H p = z: (L^H)_rk = conj(L_kr)
-      const cpx<double> zk = sX[i][k];
-#pragma unroll
-      for (int m = 0; m < (k + Q - 1) / Q; ++m) {
-        const int r = q + Q * m;
-        if (live && r < k) {
-          const cpx<double> l = L[k * I + r];
-          cpx<double> v = sX[i][r];
-          cfma(v, mk(-l.re, l.im), zk);
-          sX[i][r] = v;
-        }
-      }
-      __syncwarp();
-    }
+    wide_solve<I>(sV, sRd, sX, i, q);
     if (sweep + 1 < a.K) {  // P^{-H} of the intermediate P
       cpx<double> t[R];
       sing_mid |= !(pinvh_wide<I>(sX, i, q, t) > 0.0);

@@ -148,16 +148,18 @@ def test_deterministic_and_resumable(prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("F", [768, 769])
-def test_p_step_forms_either_side_of_the_switch(prec, F):
-    """The fixed-point step runs one warp per problem up to 768 problems at
-    I = 3 and packs ten problems in a warp above: both forms against the
-    oracle over two iterations, and 2 + 1 iterations equal 3 bit for bit."""
+@pytest.mark.parametrize("p_update", [None, "em"])
+def test_p_step_forms_either_side_of_the_switch(prec, F, p_update):
+    """The fixed-point and EM steps run one warp per problem up to 768
+    problems at I = 3 and pack ten problems in a warp above: both forms
+    against the oracle over two iterations, and 2 + 1 iterations equal 3 bit
+    for bit."""
     p = make_problem(3, 3, F, 24, seed=15)
-    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter())
-    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 2, counter=OpCounter(), p_update=p_update or "fpi")
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec, p_update=p_update)
     _compare(prec, ref, got, 24, F)
-    a = run_gpu(p.y, p.v0, p.lam0, p.P0, 3, prec)
-    b = run_gpu(p.y, got[0], got[1], got[2], 1, prec)
+    a = run_gpu(p.y, p.v0, p.lam0, p.P0, 3, prec, p_update=p_update)
+    b = run_gpu(p.y, got[0], got[1], got[2], 1, prec, p_update=p_update)
     for x, z in zip(a[:3], b[:3]):
         assert np.array_equal(x, z)
 

@@ -79,12 +79,13 @@ def test_resumable_bit_exact_large_array(prec):
 
 
 @pytest.mark.parametrize("F", [1536, 1537])
-def test_p_step_forms_either_side_of_the_switch_large_array(F):
-    """At I = 8 the fixed-point step runs one warp per problem up to 1536
-    problems and packs four in a warp above: both against the oracle."""
+@pytest.mark.parametrize("p_update", [None, "em"])
+def test_p_step_forms_either_side_of_the_switch_large_array(F, p_update):
+    """At I = 8 the fixed-point and EM steps run one warp per problem up to
+    1536 problems and pack four in a warp above: both against the oracle."""
     p = make_problem(8, 6, F, 12, seed=16, alpha=0.2, kappa=50.0)
-    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 1, counter=OpCounter())
-    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 1, "fp64")
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 1, counter=OpCounter(), p_update=p_update or "fpi")
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 1, "fp64", p_update=p_update)
     _compare("fp64", ref, got, 12, F)
 
 
