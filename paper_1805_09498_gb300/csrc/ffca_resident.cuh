@@ -17,7 +17,9 @@
 //               sub-pass per V_i at I = 8, one in all otherwise), then warp 0
 //               runs the P step of k_psolve_ldl (L D L^H of V_i, the columns
 //               V_i^{-1} [P^{-H}]_i, K sweeps, the inverse of the new P for
-//               ln|det P|^2 and the next P^{-H}).  At the end v, Lambda, P,
+//               ln|det P|^2 and the next P^{-H}); at I = 3 in the layout of
+//               k_psolve_wide, the work inside each V_i over the lanes, with
+//               the same P^{-H} bits.  At the end v, Lambda, P,
 //               P^{-H}, ln|det P|^2 and the pass-A table go back to global
 //               memory; each iteration's L2 of the problem goes to hist.
 //   k_res_trace one block per iteration: the problems' L2 summed in a fixed
@@ -25,6 +27,7 @@
 #pragma once
 
 #include "ffca_big.cuh"
+#include "ffca_psolve_wide.cuh"
 
 namespace ffca {
 
@@ -108,6 +111,10 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
   __shared__ double sP[I][I][2], sQ[I][I][2];  // P and P^{-H} (FP64)
   __shared__ double sLogdet;
   __shared__ cpx<double> sM[(BigLane<I>::G + 1) * I * BigLane<I>::LDM];  // the P step's transposes
+  // I = 3: the P step with the whole of warp 0 (k_psolve_wide's layout)
+  constexpr int IW = I == 3 ? I : 1;
+  __shared__ cpx<double> sWV[IW][WideP<3>::VS], sWX[IW][WideP<3>::XS], sWL[IW][WideP<3>::XS];
+  __shared__ double sWRd[IW][WideP<3>::XS];
   __shared__ int sBad;
 
   const FastArgs& a = ra.a;
@@ -265,7 +272,54 @@ __global__ void __launch_bounds__(kResThreads) k_resident(ResArgs ra) {
       __syncthreads();
     }
     // ---------------------------------------------------------- P step (warp 0)
-    if (warp == 0) {
+    if constexpr (I == 3) {
+      if (warp == 0) {  // lane (i, q): k_psolve_wide's factorisation, substitutions and P^{-H}
+        constexpr int Q = WideP<I>::Q;
+        const int i = lane % I, q = lane / I;
+        const bool live = q < Q;
+        for (int e = lane; e < I * NVB; e += 32) {  // V_i: the diagonal, the conjugated upper entries below it
+          const int vi = e / NVB, m = e % NVB;
+          if (m < I) {
+            sWV[vi][m * (I + 1)] = mk(sV[vi][m], 0.0);
+          } else if ((m - I) % 2 == 0) {
+            int r, c;
+            upper_decode<I>((m - I) / 2, r, c);
+            sWV[vi][c * I + r] = mk(sV[vi][m], -sV[vi][m + 1]);
+          }
+        }
+        if (live) sWX[i][q] = mk(sQ[q][i][0], sQ[q][i][1]);  // column i of P^{-H}
+        __syncwarp();
+        const bool ok = wide_ldl<I>(sWV, sWL, sWRd, i, q);
+        bool sing = false;
+        for (int sweep = 0; sweep < a.K; ++sweep) {
+          wide_solve<I>(sWV, sWRd, sWX, i, q);
+          if (sweep + 1 < a.K) {
+            cpx<double> t[1];
+            sing |= !(pinvh_wide<I>(sWX, i, q, t) > 0.0);
+            __syncwarp();
+            if (live) sWX[i][q] = t[0];
+            __syncwarp();
+          }
+        }
+        if (live) {
+          const cpx<double> pv = sWX[i][q];
+          sP[q][i][0] = pv.re;
+          sP[q][i][1] = pv.im;
+          sPT[q][i] = mk<T>((T)pv.re, (T)pv.im);
+        }
+        cpx<double> ph[1];
+        const double det2 = pinvh_wide<I>(sWX, i, q, ph);
+        if (live) {
+          sQ[q][i][0] = ph[0].re;
+          sQ[q][i][1] = ph[0].im;
+        }
+        singular |= __any_sync(0xffffffffu, !ok || sing) || !(det2 > 0.0);
+        if (lane == 0) {
+          sLogdet = log(det2);
+          atomicAdd(a.ops, p_update_inversions(a, I));
+        }
+      }
+    } else if (warp == 0) {
       const int g = lane / I, i = lane % I;  // problem group g = 0 is this problem; others shadow it
       cpx<double>* M = sM + (size_t)(g < BigLane<I>::G ? g : BigLane<I>::G) * I * BigLane<I>::LDM;
       double dv[I], d0[I], rd[I];
