@@ -29,7 +29,9 @@
 // A warp issues fewer FP64 instructions than a packed warp, on shorter
 // chains, and the 513 warps of a 513-problem step use every sub-partition.
 // Per problem the FP64 work is larger, so the packed forms stay in use for
-// many problems (the host picks by the problem count).
+// many problems (the host picks by the problem count).  The factorisation,
+// substitution and P^{-H} helpers here also serve the EM step with one warp
+// per problem (k_psolve_em_wide) and the resident form's P step at I = 3.
 #pragma once
 
 #include "ffca_big.cuh"
