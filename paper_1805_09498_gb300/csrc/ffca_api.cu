@@ -368,10 +368,13 @@ ffca_status launch(ffca_ctx* c, int kind, const void* fn, int grid, int block, A
   return FFCA_OK;
 }
 
+bool prep_wide(const ffca_ctx* c);
+
 ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
   FastArgs a = base_args(c);
   // always where the P step starts from P^{-H}
   a.pinvH = (want_pinv || c->kern->pinv_step) ? reinterpret_cast<double*>(c->ws + c->plan.off_pinvH) : nullptr;
+  if (prep_wide(c)) return launch(c, FFCA_KERNEL_PREP, c->kern->prep_wide, c->d.F, 32, a, 0);
   const int G = 32 / c->d.I;  // frequencies per warp
   return launch(c, FFCA_KERNEL_PREP, c->kern->prep, (c->d.F + G - 1) / G, 32, a, c->kern->solve_smem);
 }
@@ -380,23 +383,30 @@ ffca_status launch_prep(ffca_ctx* c, bool want_pinv) {
 // many problems.  Its FP64 instructions per problem are 1.5x (I = 8) to 6x
 // (I = 3) those of the packed form (32 / I problems per warp), whose few
 // warps leave most FP64 units idle while the problems are few.  Measured
-// (mixed precision, N = 64): the packed step takes 13 - 14.5 us at I = 3
-// and 55 - 62 us at I = 8 from 929 to 2048 problems; the wide one 12.1 /
-// 14.5 us at 513 / 928 problems (I = 3) and 31 / 41 / 58 us at 513 / 1024
-// / 1664 (I = 8).  They cross near 780 problems at I = 3 and 1580 at I = 8.
+// (mixed precision, N = 64): the packed step takes 13 - 14.5 us at I = 3,
+// 18.3 - 18.7 us at I = 4 and 55 - 62 us at I = 8 from about a thousand to
+// 2048 problems; the wide one 12.1 / 14.5 us at 513 / 928 problems (I = 3),
+// 14.5 / 18.5 us at 513 / 1024 (I = 4) and 31 / 41 / 58 us at 513 / 1024 /
+// 1664 (I = 8).  They cross near 780, 1020 and 1580 problems.
 constexpr int kWideMaxProblems3 = 768;
+constexpr int kWideMaxProblems4 = 1024;
 constexpr int kWideMaxProblems8 = 1536;
 
-bool p_step_wide(const ffca_ctx* c) {
-  const int most = c->d.I == 8 ? kWideMaxProblems8 : kWideMaxProblems3;
-  return c->pmode == kPFixedPoint && c->kern->psolve_wide != nullptr && c->d.F <= most;
+int wide_max_problems(int I) {
+  return I == 8 ? kWideMaxProblems8 : (I == 4 ? kWideMaxProblems4 : kWideMaxProblems3);
 }
 
-// The EM step with one warp per problem (k_psolve_em_wide), on the same
-// problem counts.
+bool p_step_wide(const ffca_ctx* c) {
+  return c->pmode == kPFixedPoint && c->kern->psolve_wide != nullptr && c->d.F <= wide_max_problems(c->d.I);
+}
+
+// The EM step and prep with one warp per problem (k_psolve_em_wide,
+// k_prep_wide), on the same problem counts.
 bool em_step_wide(const ffca_ctx* c) {
-  const int most = c->d.I == 8 ? kWideMaxProblems8 : kWideMaxProblems3;
-  return c->kern->psolve_em_wide != nullptr && c->d.F <= most;
+  return c->kern->psolve_em_wide != nullptr && c->d.F <= wide_max_problems(c->d.I);
+}
+bool prep_wide(const ffca_ctx* c) {
+  return c->kern->prep_wide != nullptr && c->d.F <= wide_max_problems(c->d.I);
 }
 
 // Blocks of the P step: one warp per 32 / I problems (Newton and the wide

@@ -24,7 +24,7 @@ struct FastKernels {
   // the normal EM update of P (nullptr where not compiled: I > 4)
   const void* estep_em;      // pass A with the EM sums (one pipeline group per CTA)
   const void* psolve_em;     // its per-problem step (no pass B)
-  const void* psolve_em_wide;  // the same step with one warp per problem (I = 3 and 8; else nullptr)
+  const void* psolve_em_wide;  // the same step with one warp per problem (I = 3, 4, 8; else nullptr)
   int em_smem;               // dynamic shared memory of estep_em
   int em_solve_smem;         // dynamic shared memory of psolve_em
   int em_nv;                 // sums per slot of estep_em
@@ -38,7 +38,8 @@ struct FastKernels {
   const void* resident;
   int res_bytes_per_frame;   // shared memory per frame of a problem
   int res_max_frames;        // frames of the largest problem it takes
-  const void* psolve_wide;   // the fixed-point step with one warp per problem (I = 3 and 8; else nullptr)
+  const void* psolve_wide;   // the fixed-point step with one warp per problem (I = 3, 4, 8; else nullptr)
+  const void* prep_wide;     // prep with one warp per problem (I = 3, 4, 8; else nullptr)
 };
 
 // prec: 0 = FP64, 1 = mixed.  nullptr if (I, J) is not compiled.

@@ -39,9 +39,9 @@ using Real = float;
 #if FFCA_PART == 0
 // The P step by Gauss-Jordan and LDL^H (k_psolve_ldl, which carries P^{-H}
 // from one step to the next) from FFCA_LDL_MIN_I microphones up; below it
-// the cofactor forms of k_psolve.  At I = 3 and 8 the fixed point of up to
-// about a thousand problems (ffca_api.cu) runs k_psolve_wide (one warp per
-// problem, the same P^{-H} bits).
+// the cofactor forms of k_psolve.  At I = 3, 4 and 8 the fixed point and
+// prep of up to about a thousand problems (ffca_api.cu) run k_psolve_wide
+// and k_prep_wide (one warp per problem, the same P^{-H} bits).
 #ifndef FFCA_LDL_MIN_I
 #define FFCA_LDL_MIN_I 3
 #endif
@@ -63,7 +63,11 @@ static const FastKernels* table_entry() {
     prep = (const void*)k_prep<Real, FFCA_I, J>;
   }
   const void* psolve_wide = nullptr;
-  if constexpr (FFCA_I == 3 || FFCA_I == 8) psolve_wide = (const void*)k_psolve_wide<Real, FFCA_I, J>;
+  const void* prep_wide = nullptr;
+  if constexpr (FFCA_I == 3 || FFCA_I == 4 || FFCA_I == 8) {
+    psolve_wide = (const void*)k_psolve_wide<Real, FFCA_I, J>;
+    prep_wide = (const void*)k_prep_wide<Real, FFCA_I, J>;
+  }
   if constexpr (BIG) wiener = (const void*)k_wiener_big<Real, FFCA_I, J>;
   else wiener = (const void*)k_wiener<Real, FFCA_I, J>;
   // the normal EM and Newton kernels are compiled in translation units of
@@ -117,6 +121,7 @@ static const FastKernels* table_entry() {
       res_bpf,
       res_max,
       psolve_wide,
+      prep_wide,
   };
   return &k;
 }
@@ -228,12 +233,12 @@ const AdjKernels* FFCA_CAT(adj_kernels_p, FFCA_PREC, _i, FFCA_I)(int J) {
 #endif
 
 #if FFCA_PART == 3
-// kind 0: the EM pass; 1: the packed EM step; 2: the wide EM step (I = 3, 8)
+// kind 0: the EM pass; 1: the packed EM step; 2: the wide EM step (I = 3, 4, 8)
 template <int J>
 static const void* em_kernel(int kind) {
   if (kind == 1) return (const void*)k_psolve_em<Real, FFCA_I, J>;
   if (kind == 2) {
-    if constexpr (FFCA_I == 3 || FFCA_I == 8) return (const void*)k_psolve_em_wide<Real, FFCA_I, J>;
+    if constexpr (FFCA_I == 3 || FFCA_I == 4 || FFCA_I == 8) return (const void*)k_psolve_em_wide<Real, FFCA_I, J>;
     return nullptr;
   }
 #if FFCA_I > 4

@@ -1,4 +1,4 @@
-// The P step of Eq. FPI with one warp per problem, for I = 3 and I = 8.
+// The P step of Eq. FPI with one warp per problem, for I = 3, 4 and 8.
 //
 // An FP64 warp instruction occupies its SM sub-partition's FP64 unit for 64
 // cycles on this part (2 FP64 FMAs per clock per SM, 4 sub-partitions), with
@@ -8,8 +8,8 @@
 // warps for 513 problems: one warp per SM at most, three of every four
 // sub-partitions idle, the time set by one warp's dependent chain.  Here
 // each problem has a warp of its own, lane (i, q) = (lane % I, lane / I) for
-// q < Q (Q = 4 at I = 8, 3 at I = 3; the other lanes only join the
-// shuffles), and the work inside each matrix is spread over the lanes:
+// q < Q (Q = 4 at I = 8, else I; the other lanes only join the shuffles),
+// and the work inside each matrix is spread over the lanes:
 //
 //   L D L^H of V_i   the Q lanes of V_i share the entries of each step's
 //                    trailing triangle (row-major order, entry q + Q m);
@@ -18,7 +18,8 @@
 //                    over the Q lanes;
 //   P^{-H}           I = 8: Gauss-Jordan with partial pivoting on P^H, lane
 //                    (c, h) holding rows h and h + 4 of column c
-//                    (gj_inverse_wide8); I = 3: cofactors, one per lane
+//                    (gj_inverse_wide8); I = 4: the same, one entry per
+//                    lane (gj_inverse_wide4); I = 3: cofactors, one per lane
 //                    (pinvh_wide3).  Every entry takes the same operations,
 //                    in the same order, as in gj_inverse_cols and
 //                    pinvh_cofactors (the routines of k_prep_gj and the
@@ -40,9 +41,9 @@ namespace ffca {
 
 template <int I>
 struct WideP {
-  static_assert(I == 3 || I == 8, "the wide P step is laid out for I = 3 and I = 8");
+  static_assert(I == 3 || I == 4 || I == 8, "the wide P step is laid out for I = 3, 4 and 8");
   static constexpr int Q = I == 8 ? 4 : I;   // lanes per matrix (lanes I Q and up idle)
-  static constexpr int R = (I + Q - 1) / Q;  // rows of a column per lane (2 at I = 8, 1 at I = 3)
+  static constexpr int R = (I + Q - 1) / Q;  // rows of a column per lane (2 at I = 8, else 1)
   static constexpr int VS = I * I + 1;       // stride of one V_i (complex entries; the pad skews the banks)
   static constexpr int XS = I + 1;           // stride of one vector
   static constexpr int NV = I * I * I;       // values per slot of pass B's partial sums
@@ -61,12 +62,16 @@ __device__ inline void tri_decode(int e, int& r, int& c) {
 }
 
 // Packed order of the upper entries (r < c) of pass B's slots: row order.
+// p < I (I - 1) / 2; the loop is bounded whatever p is.
 template <int I>
 __device__ inline void upper_decode(int p, int& r, int& c) {
   r = 0;
-  while (p >= I - 1 - r) {
-    p -= I - 1 - r;
-    ++r;
+#pragma unroll
+  for (int k = 0; k < I - 2; ++k) {
+    if (p >= I - 1 - r) {
+      p -= I - 1 - r;
+      ++r;
+    }
   }
   c = r + 1 + p;
 }
@@ -150,6 +155,57 @@ __device__ inline double gj_inverse_wide8(cpx<double>& a0, cpx<double>& a1, int 
   return (det2 > 0.0 && isfinite(det2)) ? det2 : 0.0;
 }
 
+// The same Gauss-Jordan inverse for a 4 x 4 matrix, one entry per lane:
+// lane (c, h) = (lane % 4, lane / 4) holds a = A[h][c] for lanes 0 .. 15
+// (lanes 16 .. 31 hold nothing of A and only join the shuffles).  Every
+// entry takes the operations of gj_inverse_cols<4> in the same order.
+__device__ inline double gj_inverse_wide4(cpx<double>& a, int c, int h) {
+  constexpr int I = 4;
+  const unsigned full = 0xffffffffu;
+  int perm[I];
+  double det2 = 1.0;
+#pragma unroll
+  for (int k = 0; k < I; ++k) {
+    unsigned long long key = 0ull;
+    int row = I;  // no candidate
+    if (h >= k && h < I) {
+      key = pivot_key(a);
+      row = h;
+    }
+#pragma unroll
+    for (int s = 4; s <= 8; s <<= 1) {
+      const unsigned long long ok = __shfl_xor_sync(full, key, s);
+      const int orow = __shfl_xor_sync(full, row, s);
+      if (ok > key || (ok == key && orow < row)) {
+        key = ok;
+        row = orow;
+      }
+    }
+    const int p = __shfl_sync(full, row, k);  // column k's result (lane (k, 0))
+    perm[k] = p;
+    const cpx<double> vk = shfl_c(a, c + 4 * k);  // entries (k, c) and (p, c)
+    const cpx<double> vp = shfl_c(a, c + 4 * p);
+    if (h == k) a = vp;
+    if (h == p) a = vk;
+    const cpx<double> col = shfl_c(a, k + 4 * (h & 3));  // entry (h, k) after the exchange
+    const cpx<double> piv = shfl_c(vp, k);
+    const double d2 = cabs2(piv);
+    det2 *= d2;
+    const double rd = recip(d2);
+    const cpx<double> inv = mk(piv.re * rd, -piv.im * rd);
+    const bool pc = (c == k);
+    const cpx<double> t = pc ? inv : cmul(vp, inv);
+    cpx<double> v = pc ? mk(0.0, 0.0) : a;
+    cfma(v, mk(-col.re, -col.im), t);
+    a = (h == k) ? t : v;
+  }
+  int j = c;
+#pragma unroll
+  for (int k = 0; k < I; ++k) j = (j == k) ? perm[k] : (j == perm[k] ? k : j);
+  a = shfl_c(a, j + 4 * (h & 3));
+  return (det2 > 0.0 && isfinite(det2)) ? det2 : 0.0;
+}
+
 // Column c of P^{-H} and |det P|^2 for I = 3 by cofactors, lane (c, r) =
 // (lane % 3, lane / 3) for lanes 0 .. 8 (the others shadow row 0), P's
 // column c in sX[c][0 .. 2].  Every value takes the operations of
@@ -180,8 +236,8 @@ __device__ inline double pinvh_wide3(const cpx<double> (*sX)[WideP<3>::XS], int 
 }
 
 // P^{-H} of the P whose column i is sX[i][0 .. I-1] and |det P|^2: lane
-// (i, q) receives (P^{-H})[q + Q m][i], m < R.  I = 8: Gauss-Jordan on P^H,
-// (P^H)[x][y] = conj(P[y][x]); I = 3: cofactors.
+// (i, q) receives (P^{-H})[q + Q m][i], m < R.  I = 8 and 4: Gauss-Jordan
+// on P^H, (P^H)[x][y] = conj(P[y][x]); I = 3: cofactors.
 template <int I>
 __device__ inline double pinvh_wide(const cpx<double> (*sX)[WideP<I>::XS], int i, int q,
                                     cpx<double> (&out)[WideP<I>::R]) {
@@ -189,6 +245,9 @@ __device__ inline double pinvh_wide(const cpx<double> (*sX)[WideP<I>::XS], int i
     out[0] = cconj(sX[q][i]);
     out[1] = cconj(sX[q + 4][i]);
     return gj_inverse_wide8(out[0], out[1], i, q);
+  } else if constexpr (I == 4) {
+    out[0] = q < I ? cconj(sX[q][i]) : mk(0.0, 0.0);
+    return gj_inverse_wide4(out[0], i, q);
   } else {
     return pinvh_wide3(sX, i, q, out[0]);
   }
@@ -355,15 +414,16 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
   const int ns = pt.nslots(f);  // >= 1: every problem has a slot
   const double* slots = a.part_buf + (size_t)f * pt.max_slots * W::NV;
   bool bad = false;
-  if constexpr (I == 8) {
-    // lane (i, q): eight 16-byte units of V_i's packed values (I diagonal
-    // values, then (re, im) of V_rc, r < c, in row order)
+  if constexpr (I % 2 == 0) {
+    // lane (i, q): I I / (2 Q) 16-byte units of V_i's packed values (I
+    // diagonal values, then (re, im) of V_rc, r < c, in row order)
+    // (lanes q >= Q, present at I = 4, hold no units)
     constexpr int U = I * I / 2 / Q;
     double2 pk[U];
-    const double2* b2 = reinterpret_cast<const double2*>(slots + i * I * I) + q * U;
+    const double2* b2 = reinterpret_cast<const double2*>(slots + i * I * I) + (live ? q : 0) * U;
 #pragma unroll
-    for (int m = 0; m < U; ++m) pk[m] = __ldcg(b2 + m);
-    for (int k = 1; k < ns; ++k) {
+    for (int m = 0; m < U; ++m) pk[m] = live ? __ldcg(b2 + m) : make_double2(0.0, 0.0);
+    for (int k = 1; k < (live ? ns : 1); ++k) {
 #pragma unroll
       for (int m = 0; m < U; ++m) {
         const double2 v2 = __ldcg(b2 + (size_t)k * (W::NV / 2) + m);
@@ -374,6 +434,7 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
     const double sc = pt.inv_n(f);
 #pragma unroll
     for (int m = 0; m < U; ++m) {
+      if (!live) break;
       pk[m].x *= sc;
       pk[m].y *= sc;
       bad |= !isfinite(pk[m].x) || !isfinite(pk[m].y);
@@ -469,6 +530,47 @@ __global__ void __launch_bounds__(32) k_psolve_wide(FastArgs a) {
   if (lane == 0) {
     if (singular) raise_status(a.status, kDevSingular, f);
     atomicAdd(a.ops, p_update_inversions(a, I));
+    a.logdet[f] = log(det2);
+  }
+}
+
+// k_prep_wide: what k_prep_gj computes (ln|det P|^2, P^{-H} and the pass-A
+// table of the current P and Lambda), one warp per problem, with the
+// P^{-H} routine of k_psolve_wide (the bits of pinvh_from_columns).
+template <typename T, int I, int J>
+__global__ void __launch_bounds__(32) k_prep_wide(FastArgs a) {
+  using W = WideP<I>;
+  constexpr int Q = W::Q, R = W::R;
+  __shared__ cpx<double> sX[I][W::XS];
+  const int f = blockIdx.x;
+  if (f >= a.F) return;
+  const int lane = threadIdx.x;
+  const int i = lane % I, q = lane / I;
+  const bool live = q < Q;
+  ParamsA<T, I, J>* ta = tab_a<T, I, J>(a, f);
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    const int r = q + Q * m;
+    if (live && r < I) {
+      const double2 u = reinterpret_cast<const double2*>(a.P)[(size_t)f * I * I + r * I + i];
+      sX[i][r] = mk(u.x, u.y);
+      ta->set_p(r, i, (T)u.x, (T)u.y);
+    }
+  }
+  for (int e = lane; e < J * I; e += 32) ta->set_lam(e / I, e % I, (T)a.lam[(size_t)f * J * I + e]);
+  __syncwarp();
+  cpx<double> ph[R];
+  const double det2 = pinvh_wide<I>(sX, i, q, ph);
+  if (a.pinvH && live) {
+#pragma unroll
+    for (int m = 0; m < R; ++m) {
+      const int r = q + Q * m;
+      if (r < I)
+        reinterpret_cast<double2*>(a.pinvH)[(size_t)f * I * I + r * I + i] = make_double2(ph[m].re, ph[m].im);
+    }
+  }
+  if (lane == 0) {
+    if (!(det2 > 0.0)) raise_status(a.status, kDevSingular, f);
     a.logdet[f] = log(det2);
   }
 }

@@ -165,6 +165,34 @@ def test_p_step_forms_either_side_of_the_switch(prec, F, p_update):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("p_update,mu", [(None, 0.0), ("gradient", 0.05), ("em", 0.0)])
+def test_resumable_bit_exact_i4(prec, p_update, mu):
+    """I = 4: 2 + 2 iterations in two calls equal 4 in one, bit for bit.  The
+    P^{-H} that a step carries (one warp per problem for the fixed point and
+    the EM, four problems per warp for the gradient) has the bits of the one
+    that the next call's prep (one warp per problem) forms from P."""
+    p = make_problem(4, 3, 7, 150, seed=17)
+    a = run_gpu(p.y, p.v0, p.lam0, p.P0, 4, prec, p_update=p_update, mu=mu)
+    b1 = run_gpu(p.y, p.v0, p.lam0, p.P0, 2, prec, p_update=p_update, mu=mu)
+    b = run_gpu(p.y, b1[0], b1[1], b1[2], 2, prec, p_update=p_update, mu=mu)
+    for x, z in zip(a[:3], b[:3]):
+        assert np.array_equal(x, z)
+    assert np.array_equal(a[3][2:], b[3])
+
+
+@pytest.mark.parametrize("F", [1024, 1025])
+@pytest.mark.parametrize("p_update", [None, "em"])
+def test_p_step_forms_either_side_of_the_switch_i4(F, p_update):
+    """At I = 4 the fixed-point step, the EM step and prep run one warp per
+    problem up to 1024 problems and pack eight in a warp above: both
+    against the oracle."""
+    p = make_problem(4, 3, F, 12, seed=18)
+    ref = ffa.iterate(p.y, p.v0, p.lam0, p.P0, 1, counter=OpCounter(), p_update=p_update or "fpi")
+    got = run_gpu(p.y, p.v0, p.lam0, p.P0, 1, "fp64", p_update=p_update)
+    _compare("fp64", ref, got, 12, F)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("p_update", [None, "em"])
 def test_traced_graph_replay_is_bit_exact(prec, p_update):
     """iterate() with a trace replayed from a CUDA graph gives the state and
